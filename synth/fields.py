@@ -1,0 +1,268 @@
+"""Seeded generators for PDE-shaped snapshot matrices A (m snapshots x n dofs).
+
+Layout shared by every consumer: A is row-major, one snapshot per row, and the
+dofs of a Cartesian grid are vectorised with x fastest:
+    2-D: idx = y*Nx + x            3-D: idx = (z*Ny + y)*Nx + x
+
+Everything is drawn from numpy's PCG64 (``default_rng(seed)``) and computed in
+float64, then rounded once to the storage type:
+  * f64  -- kept as drawn,
+  * f32  -- round-to-nearest-even from float64 (numpy ``astype``),
+  * bf16 -- round-to-nearest-even from float64 to 8 significant bits, stored
+            as the upper 16 bits of the equal float32 (uint16 bit patterns).
+
+Fields (the paper's data sets are not available, so these stand in for them):
+  heat_field       sum of decaying sine modes, the 2-D/3-D heat equation on
+                   the unit square/cube with homogeneous Dirichlet walls,
+                   interior grid x_p = p/(N+1), p = 1..N.
+  blob_field       Gaussian blobs advected with constant velocity on the
+                   periodic unit square and spread by diffusion.
+  tanh_front_field travelling tanh fronts (slow singular-value decay).
+  low_rank_matrix  exact rank-r products with a prescribed spectrum.
+  pivot_gap_matrix rows scaled so that column-pivoted QR has a clear gap.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import numpy as np
+
+
+# ----------------------------------------------------------------------------
+# grid description shared by generators, oracle and GPU binding (plain data)
+# ----------------------------------------------------------------------------
+@dataclass(frozen=True)
+class GridSpec:
+    """Fine grid N[0..ndim-1] (x first) with a per-axis coarsening factor s."""
+    N: tuple
+    s: tuple
+    kind: str = "inject"          # "inject" | "fullweight" | "blockavg"
+
+    @property
+    def ndim(self) -> int:
+        return len(self.N)
+
+    @property
+    def n(self) -> int:
+        return int(np.prod(self.N))
+
+    @property
+    def Nc(self) -> tuple:
+        return tuple(Nd // sd for Nd, sd in zip(self.N, self.s))
+
+    @property
+    def l(self) -> int:
+        return int(np.prod(self.Nc))
+
+
+# ----------------------------------------------------------------------------
+# storage rounding
+# ----------------------------------------------------------------------------
+def to_bf16_bits(x: np.ndarray) -> np.ndarray:
+    """Round float64 to bfloat16 (RNE, 8 significant bits); return uint16 bits."""
+    x = np.asarray(x, dtype=np.float64)
+    mant, expo = np.frexp(x)                      # x = mant * 2**expo, |mant| in [0.5,1)
+    r = np.ldexp(np.rint(mant * 256.0), expo - 8)  # rint = round half to even
+    f32 = r.astype(np.float32)                     # exact: r has 8 significant bits
+    return (f32.view(np.uint32) >> 16).astype(np.uint16)
+
+
+def bf16_bits_to_f64(b: np.ndarray) -> np.ndarray:
+    """Exact decode of bfloat16 bit patterns to float64."""
+    u = np.asarray(b, dtype=np.uint16).astype(np.uint32) << 16
+    return u.view(np.float32).astype(np.float64)
+
+
+def _store(a64: np.ndarray, dtype: str) -> np.ndarray:
+    if dtype == "f64":
+        return np.ascontiguousarray(a64, dtype=np.float64)
+    if dtype == "f32":
+        return np.ascontiguousarray(a64.astype(np.float32))
+    if dtype == "bf16":
+        return np.ascontiguousarray(to_bf16_bits(a64))
+    raise ValueError(dtype)
+
+
+# ----------------------------------------------------------------------------
+# heat equation field
+# ----------------------------------------------------------------------------
+def heat_params(m: int, d: int, K: int, seed: int, nu: float = 0.01):
+    """Draws of the heat field: sorted times t ~ U[0,1], coefficients
+    c_ij(l) ~ N(0,1)/(1+i+j(+l))^2 and decay rates nu*pi^2*|mode|^2."""
+    rng = np.random.default_rng(seed)
+    t = np.sort(rng.uniform(0.0, 1.0, m))
+    modes = np.stack(np.meshgrid(*[np.arange(1, K + 1)] * d, indexing="ij"), -1)
+    modes = modes.reshape(-1, d)                        # (K^d, d): (i, j[, l]) with i the x mode
+    c = rng.standard_normal(len(modes)) / (1.0 + modes.sum(1)) ** 2
+    lam = nu * np.pi ** 2 * (modes ** 2).sum(1)
+    return t, modes, c, lam
+
+
+def heat_field(m: int, N: int, d: int, K: int, seed: int, dtype: str = "f64",
+               rows: slice | None = None) -> np.ndarray:
+    """u(x,t) = sum_modes c e^{-lam t} prod_axis sin(mode_axis * pi * x_axis).
+
+    Returns rows ``rows`` (default all) of the m x N^d matrix in ``dtype``.
+    """
+    t, modes, c, lam = heat_params(m, d, K, seed)
+    if rows is not None:
+        t = t[rows]
+    x = np.arange(1, N + 1) / (N + 1.0)
+    S = np.sin(np.pi * np.outer(np.arange(1, K + 1), x))        # (K, N): S[i-1, p]
+    coef = np.exp(-np.outer(t, lam)) * c                         # (mt, K^d)
+    mt = len(t)
+    if d == 2:
+        C = coef.reshape(mt, K, K)                               # [t, i(x), j(y)]
+        # A[t, y, x] = sum_{i,j} C[t,i,j] S[j,y] S[i,x]
+        tmp = np.einsum("tij,jy->tiy", C, S)
+        A = np.einsum("tiy,ix->tyx", tmp, S).reshape(mt, N * N)
+    elif d == 3:
+        C = coef.reshape(mt, K, K, K)                            # [t, i(x), j(y), l(z)]
+        A = np.empty((mt, N * N * N), dtype=np.float64)
+        for r0 in range(0, mt, 8):
+            Cb = C[r0:r0 + 8]
+            t1 = np.einsum("tijl,lz->tijz", Cb, S)
+            t2 = np.einsum("tijz,jy->tizy", t1, S)
+            t3 = np.einsum("tizy,ix->tzyx", t2, S)
+            A[r0:r0 + len(Cb)] = t3.reshape(len(Cb), -1)
+    else:
+        raise ValueError("heat_field supports d = 2 or 3")
+    return _store(A, dtype)
+
+
+# ----------------------------------------------------------------------------
+# advected / diffused Gaussian blobs on the periodic unit square
+# ----------------------------------------------------------------------------
+def blob_params(nblobs: int, seed: int):
+    rng = np.random.default_rng(seed)
+    c0 = rng.uniform(0.0, 1.0, (nblobs, 2))
+    vel = rng.uniform(-1.0, 1.0, (nblobs, 2))
+    width = rng.uniform(0.02, 0.1, nblobs)
+    amp = rng.standard_normal(nblobs)
+    return c0, vel, width, amp
+
+
+def blob_field(m: int, N: int, nblobs: int, seed: int, kappa: float = 1e-5,
+               dtype: str = "f32", rows: slice | None = None) -> np.ndarray:
+    """Blob b at time t_i = i/(m-1): centre c0 + v t (mod 1), variance
+    w^2 + 2 kappa t, amplitude a w^2/(w^2 + 2 kappa t) (mass kept by diffusion).
+    Grid: cell centres (p + 1/2)/N, minimum-image distance per axis."""
+    c0, vel, width, amp = blob_params(nblobs, seed)
+    t = np.linspace(0.0, 1.0, m) if m > 1 else np.zeros(1)
+    if rows is not None:
+        t = t[rows]
+    xs = (np.arange(N) + 0.5) / N
+    out = np.empty((len(t), N * N), dtype=np.float64)
+    for r0 in range(0, len(t), 64):
+        tb = t[r0:r0 + 64]
+        var = width[None, :] ** 2 + 2.0 * kappa * tb[:, None]            # (mt, B)
+        cx = (c0[None, :, 0] + vel[None, :, 0] * tb[:, None]) % 1.0
+        cy = (c0[None, :, 1] + vel[None, :, 1] * tb[:, None]) % 1.0
+        dx = (xs[None, None, :] - cx[:, :, None] + 0.5) % 1.0 - 0.5      # (mt, B, N)
+        dy = (xs[None, None, :] - cy[:, :, None] + 0.5) % 1.0 - 0.5
+        gx = np.exp(-dx ** 2 / (2.0 * var[:, :, None]))
+        gy = np.exp(-dy ** 2 / (2.0 * var[:, :, None]))
+        a = amp[None, :] * width[None, :] ** 2 / var                      # (mt, B)
+        # A[t, y, x] = sum_b a[t,b] gy[t,b,y] gx[t,b,x]
+        blk = np.matmul((gy * a[:, :, None]).transpose(0, 2, 1), gx)     # (mt, N, N)
+        out[r0:r0 + len(tb)] = blk.reshape(len(tb), -1)
+    return _store(out, dtype)
+
+
+# ----------------------------------------------------------------------------
+# travelling tanh fronts (slow decay)
+# ----------------------------------------------------------------------------
+def tanh_front_field(m: int, N: int, nfronts: int, seed: int, dtype: str = "f32") -> np.ndarray:
+    """Fronts tanh(k (n . x - x0 - c t)) with sharpness k ~ U[10, 200]."""
+    rng = np.random.default_rng(seed)
+    ang = rng.uniform(0, 2 * np.pi, nfronts)
+    sharp = rng.uniform(10.0, 200.0, nfronts)
+    x0 = rng.uniform(0.2, 0.8, nfronts)
+    speed = rng.uniform(-0.5, 0.5, nfronts)
+    amp = rng.standard_normal(nfronts)
+    t = np.linspace(0.0, 1.0, m)
+    xs = (np.arange(N) + 0.5) / N
+    X, Yg = np.meshgrid(xs, xs, indexing="xy")           # X[y, x] = x
+    out = np.zeros((m, N * N))
+    for f in range(nfronts):
+        proj = (np.cos(ang[f]) * X + np.sin(ang[f]) * Yg).ravel()
+        out += amp[f] * np.tanh(sharp[f] * (proj[None, :] - x0[f] - speed[f] * t[:, None]))
+    return _store(out, dtype)
+
+
+# ----------------------------------------------------------------------------
+# matrices with known structure (for pins)
+# ----------------------------------------------------------------------------
+def low_rank_matrix(m: int, n: int, r: int, seed: int, decay: float = 0.7,
+                    dtype: str = "f64"):
+    """A = U diag(sigma) V^T with orthonormal U (m x r), V (n x r) and
+    sigma_i = decay**i.  Returns (A, sigma)."""
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.standard_normal((m, r)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, r)))
+    sig = decay ** np.arange(r)
+    return _store((U * sig) @ V.T, dtype), sig
+
+
+def pivot_gap_matrix(m: int, n: int, seed: int, ratio: float = 0.8,
+                     dtype: str = "f64") -> np.ndarray:
+    """Gaussian rows scaled by ratio**perm(i): with row norms spread
+    geometrically the pivot choice of a column-pivoted QR of A^T has a clear
+    margin at every step (checked by the tests, not assumed)."""
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((m, n))
+    G /= np.linalg.norm(G, axis=1, keepdims=True)
+    scale = ratio ** rng.permutation(m)
+    return _store(G * scale[:, None], dtype)
+
+
+# ----------------------------------------------------------------------------
+# named workloads (sizes of the paper-shaped configurations)
+# ----------------------------------------------------------------------------
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    field: str
+    m: int
+    N: int
+    d: int
+    dtype: str
+    grid: GridSpec
+    k: int
+    q: int
+    gram: GridSpec | None = None      # C-PWR column subsample I (injection grid)
+    params: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return self.N ** self.d
+
+
+def _wl(name, field_, m, N, d, dtype, kind, s, k, q, s_gram=None, **params):
+    grid = GridSpec(N=(N,) * d, s=(s,) * d, kind=kind)
+    gram = GridSpec(N=(N,) * d, s=(s_gram,) * d, kind="inject") if s_gram else None
+    return Workload(name, field_, m, N, d, dtype, grid, k, q, gram, dict(params))
+
+
+WORKLOADS = {
+    # 200 snapshots of the 2-D heat field on 64^2, FP64, 4x injection (l = 256), k = 20
+    "heat2d_m200_64x64_f64": _wl("heat2d_m200_64x64_f64", "heat", 200, 64, 2, "f64",
+                                 "inject", 4, 20, 0, K=16, seed=0),
+    # 2000 blob snapshots on 512^2, FP32, full weighting onto 32^2 (l = 1024), k = 50, q = 1
+    "blob2d_m2000_512x512_f32": _wl("blob2d_m2000_512x512_f32", "blob", 2000, 512, 2, "f32",
+                                    "fullweight", 16, 50, 1, s_gram=4, nblobs=8, seed=1,
+                                    kappa=1e-5),
+    # 500 snapshots of the 3-D heat field on 256^3, BF16, injection onto 8^3 (l = 512), k = 64
+    "heat3d_m500_256c_bf16": _wl("heat3d_m500_256c_bf16", "heat", 500, 256, 3, "bf16",
+                                 "inject", 32, 64, 0, K=12, seed=2),
+}
+
+
+def make_workload(w: Workload, rows: slice | None = None) -> np.ndarray:
+    """Materialise (rows of) a workload's A in its storage dtype."""
+    p = w.params
+    if w.field == "heat":
+        return heat_field(w.m, w.N, w.d, p["K"], p["seed"], w.dtype, rows=rows)
+    if w.field == "blob":
+        return blob_field(w.m, w.N, p["nblobs"], p["seed"], p.get("kappa", 1e-5), w.dtype,
+                          rows=rows)
+    raise ValueError(w.field)
