@@ -1,0 +1,361 @@
+"""Benchmark of the deterministic-sketch low-rank path on GB300.
+
+One step = one rank-k decomposition of one snapshot matrix through the C ABI:
+  SVD: lrs_power_pass (sketch + C-PWR, re-orthonormalised) -> lrs_range_find
+       -> lrs_svd_k            (paper Algs. 7 and 2)
+  ID : lrs_power_pass (C-PWR without re-orthonormalisation) -> lrs_id_k
+                               (paper Alg. 4)
+The default workload is the 2000-snapshot blob field on a 512^2 grid (FP32,
+full weighting onto 32^2, l = 1024, k = 50, q = 1).  The matrix (2.1 GB) is
+larger than L2 (129 MB), so no flush is needed between steps.
+
+Under torchrun (N > 1) every rank decomposes its own matrix (independent
+problems, no data-path collective): weak scaling, value = all ranks' units /
+max-over-ranks time.
+
+--impl reference times the FP64 CPU oracle (there is no reference code: the
+paper ships none) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "A-pass HBM GB/s (% of peak); rank-k SVD/ID per sec at stated rel. error"
+UNIT = "decomps/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="blob2d_m2000_512x512_f32")
+    p.add_argument("--prec", default="auto", choices=["auto", "fp64", "fp32", "split_bf16", "bf16x3"])
+    p.add_argument("--rtol", type=float, default=None)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--phases", action="store_true", help="print a per-call time breakdown to stderr")
+    return p.parse_args()
+
+
+def workload_params(name):
+    import synth
+    w = synth.WORKLOADS[name]
+    rtol = {"f64": 1e-14, "f32": 1e-6, "bf16": 1e-12}[w.dtype]
+    return w, rtol
+
+
+def cfg_dict(w, rtol, prec_name):
+    return {
+        "workload": w.name, "m": w.m, "n": w.n, "grid": "x".join([str(w.N)] * w.d),
+        "sketch": f"{w.grid.kind} s={w.grid.s[0]} (l={w.grid.l})",
+        "gram": (f"inject s={w.gram.s[0]} (|I|={w.gram.l})" if w.gram else None),
+        "k": w.k, "q": w.q, "rtol": rtol, "prec": prec_name, "storage": w.dtype,
+        "l2": "inputs larger than L2, no flush" if w.m * w.n * {"f64": 8, "f32": 4, "bf16": 2}[w.dtype] > 129e6
+        else "L2 flushed between steps",
+    }
+
+
+# ---------------------------------------------------------------------------
+def clocks_start(dev):
+    f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+    try:
+        pr = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                               "-lms", "200", "-i", str(dev)], stdout=f, stderr=subprocess.DEVNULL)
+    except Exception:
+        pr = None
+    return pr, f
+
+
+def clocks_stop(h):
+    pr, f = h
+    if pr is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    pr.terminate()
+    try:
+        pr.wait(timeout=5)
+    except Exception:
+        pr.kill()
+    f.seek(0)
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in f.read().splitlines():
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 7:
+            continue
+        try:
+            sm.append(float(parts[0])); mx.append(float(parts[1]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[3:7]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    f.close()
+    os.unlink(f.name)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    """FP64 CPU oracle on a bounded sample: the first m_s snapshots."""
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    w, rtol = workload_params(args.workload)
+    ms = min(w.m, 200)
+    A = synth.make_workload(w, rows=slice(0, ms))
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+    def one():
+        oracle.svd_path(A, w.grid, w.k, q=w.q, gram_grid=w.gram, rtol=rtol)
+        oracle.id_path(A, w.grid, w.k, q=w.q, gram_grid=w.gram, rtol=rtol)
+
+    for _ in range(args.warmup):
+        one()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        one()
+    dt = (time.perf_counter() - t0) / args.steps
+    value = (ms / w.m) / dt
+    sample = f"first {ms} of {w.m} snapshots per step, value scaled by {ms}/{w.m}"
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": cfg_dict(w, rtol, "oracle fp64"),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def cpu_baseline(w, rtol, budget_s=25.0):
+    import oracle
+    import synth
+    ms = min(w.m, 200)
+    A = synth.make_workload(w, rows=slice(0, ms))
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.svd_path(A, w.grid, w.k, q=w.q, gram_grid=w.gram, rtol=rtol)
+        oracle.id_path(A, w.grid, w.k, q=w.q, gram_grid=w.gram, rtol=rtol)
+        reps += 1
+        if time.perf_counter() - t0 > budget_s / 3 or reps >= 3:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": (ms / w.m) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{reps} run(s) on the first {ms} of {w.m} snapshots, scaled by {ms}/{w.m}"}
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2105_01271_gb300 import binding, path
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    w, rtol = workload_params(args.workload)
+    if args.rtol is not None:
+        rtol = args.rtol
+    prec_map = {"fp64": binding.LRS_PREC_FP64, "fp32": binding.LRS_PREC_FP32,
+                "split_bf16": binding.LRS_PREC_SPLIT_BF16, "bf16x3": binding.LRS_PREC_BF16X3}
+    prec_name = args.prec if args.prec != "auto" else ("fp64" if w.dtype == "f64" else "fp32")
+    prec = prec_map[prec_name]
+
+    A_np = synth.make_workload(w)
+    tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.int16}[w.dtype]
+    A_h = torch.from_numpy(A_np.view(np.int16) if w.dtype == "bf16" else A_np).pin_memory()
+    del A_np
+    stream = torch.cuda.Stream(device=dev)
+    ctx = binding.load(dev, stream)
+    A_d = torch.empty(A_h.shape, dtype=tdt, device=f"cuda:{dev}")
+    with torch.cuda.stream(stream):
+        A_d.copy_(A_h, non_blocking=True)
+        bufs = path.Buffers(w.m, w.n, w.grid.l, w.k, A_d.device, prec == binding.LRS_PREC_FP64)
+    stream.synchronize()
+
+    def step():
+        s = path.svd_path(ctx, A_d, w.dtype, w.grid, w.k, q=w.q, gram=w.gram, rtol=rtol, prec=prec, bufs=bufs)
+        d = path.id_path(ctx, A_d, w.dtype, w.grid, w.k, q=w.q, gram=w.gram, rtol=rtol, prec=prec, bufs=bufs)
+        return s, d
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            s, d = step()
+    stream.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- timed region (device time, CUDA events on the library's stream) ----
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = clocks_start(dev)
+    barrier()
+    l0 = ctx.launches
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            s, d = step()
+        ev1.record(stream)
+    stream.synchronize()
+    barrier()
+    clocks = clocks_stop(clk)
+    launches = (ctx.launches - l0) // max(args.steps, 1)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([ms], device=f"cuda:{dev}")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    value = world * 1e3 / ms
+
+    # ---- per-call breakdown (one extra step, events around each ABI call) ----
+    phases = {}
+    with torch.cuda.stream(stream):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        gg = binding.grid_of(w.gram) if w.gram is not None and w.q > 0 else None
+        evs[0].record(stream)
+        gc = ctx.power_pass(A_d, binding.DTYPE[w.dtype], w.m, w.n, binding.grid_of(w.grid), gg, w.q, 1,
+                            rtol, prec, bufs.Y, w.grid.l, bufs.G, w.grid.l)
+        evs[1].record(stream)
+        ldq = bufs.Q.shape[1]
+        r = ctx.range_find(bufs.G, w.m, gc, w.grid.l, rtol, bufs.Q, ldq)
+        evs[2].record(stream)
+        ctx.svd_k(A_d, binding.DTYPE[w.dtype], w.m, w.n, w.n, bufs.Q, ldq, r, w.k, prec, bufs.U, w.k,
+                  bufs.S, bufs.V, w.k)
+        evs[3].record(stream)
+        ctx.power_pass(A_d, binding.DTYPE[w.dtype], w.m, w.n, binding.grid_of(w.grid), gg, w.q, 0,
+                       rtol, prec, bufs.Yid, w.grid.l, bufs.Gid, w.grid.l)
+        evs[4].record(stream)
+        ctx.id_k(bufs.Gid, w.m, w.grid.l, w.grid.l, w.k, bufs.J, bufs.P, w.k)
+        evs[5].record(stream)
+    stream.synchronize()
+    names = ["power_pass(svd)", "range_find", "svd_k", "power_pass(id)", "id_k"]
+    for i, nm in enumerate(names):
+        phases[nm] = evs[i].elapsed_time(evs[i + 1])
+
+    # ---- the A-pass kernel alone: B = Q^T A_f, same shapes, same stream ----
+    esz = {"f64": 8, "f32": 4, "bf16": 2}[w.dtype]
+    bsz = 8 if prec == binding.LRS_PREC_FP64 else 4
+    Bbuf = torch.empty((r, w.n), dtype=torch.float64 if bsz == 8 else torch.float32, device=A_d.device)
+    reps = max(args.steps, 5)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            ctx.gemm_tn(r, w.n, w.m, bufs.Q, 0, ldq, A_d, binding.DTYPE[w.dtype], w.n, Bbuf, bsz == 8, 0, w.n, prec)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.gemm_tn(r, w.n, w.m, bufs.Q, 0, ldq, A_d, binding.DTYPE[w.dtype], w.n, Bbuf, bsz == 8, 0, w.n, prec)
+        e1.record(stream)
+    stream.synchronize()
+    apass_ms = e0.elapsed_time(e1) / reps
+    alg_bytes = esz * w.m * w.n + 8 * w.m * r + bsz * r * w.n
+    alg_flops = 2.0 * w.m * w.n * r
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    # FP32 (or FP64) FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x clock
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = nsm * (128 if bsz == 4 else 2) * 2 * sm_max * 1e6 / 1e12     # TFLOP/s
+    gbs = alg_bytes / (apass_ms * 1e-3) / 1e9
+    tfl = alg_flops / (apass_ms * 1e-3) / 1e12
+    ridge_hbm_t = alg_bytes / (hbm_peak * 1e9)
+    ridge_alu_t = alg_flops / (alu_peak * 1e12)
+    if prec in (binding.LRS_PREC_FP32, binding.LRS_PREC_FP64):
+        bound = "hbm" if ridge_hbm_t >= ridge_alu_t else "alu"
+    else:
+        bound = "hbm"
+    if bound == "hbm":
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"}
+    else:
+        roof = {"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfl / alu_peak,
+                "peak_source": f"{nsm} SMs x {'128 FP32' if bsz == 4 else '2 FP64'} FMA/clk x 2 x {sm_max:.0f} MHz"}
+    roof.update({"kernel": "A-pass B = Q^T A_f (lrs_gemm_tn)", "traffic": None,
+                 "algorithmic_bytes": alg_bytes, "algorithmic_flops": alg_flops, "ms": apass_ms,
+                 "r": r, "hbm_gbs_achieved": gbs, "hbm_frac": gbs / hbm_peak})
+
+    # ---- end to end through the public API, host buffers in and out ----
+    h2d = A_h.numel() * A_h.element_size()
+    outs = [bufs.U, bufs.S, bufs.V, bufs.J, bufs.P]
+    host_outs = [torch.empty(o.shape, dtype=o.dtype, pin_memory=True) for o in outs]
+    d2h = sum(o.numel() * o.element_size() for o in outs)
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier()
+    with torch.cuda.stream(stream):
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(e2e_steps):
+            A_d.copy_(A_h, non_blocking=True)
+            step()
+            for ho, o in zip(host_outs, outs):
+                ho.copy_(o, non_blocking=True)
+        f1.record(stream)
+    stream.synchronize()
+    barrier()
+    e2e_ms = f0.elapsed_time(f1) / e2e_steps
+    te = torch.tensor([e2e_ms], device=f"cuda:{dev}")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_ms = float(te.item())
+
+    if rank != 0:
+        return
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": w.dtype if prec != binding.LRS_PREC_FP64 else "f64",
+           "data": "synthetic", "config": cfg_dict(w, rtol, prec_name),
+           "roofline": roof, "clocks": clocks, "gpu_launches": int(launches),
+           "e2e": {"value": world * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                   "d2h_bytes_per_step": int(d2h)},
+           "result": {"err_est_svd": s.err_est, "r": s.r, "err_est_id": d.err_est},
+           "phases_ms": phases}
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(w, rtol)
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,192 @@
+/*
+ * lrs.h -- C ABI of the GB300 deterministic-sketch low-rank library.
+ *
+ * Method: Dunton & Doostan, "Deterministic matrix sketches for low-rank
+ * compression of high-dimensional simulation data" (arXiv 2105.01271).
+ * A_f (m x n) holds one simulation snapshot per row (Sec. 2); the library
+ * sketches it onto a coarse grid without forming D (Sec. 2, Table 1), runs the
+ * coarse-grid power iteration C-PWR (Sec. 5, Alg. 7), finds the range (the
+ * "QR(.)" of Algs. 2/3/7), projects B = Q^T A_f and takes the SVD of B
+ * (Sec. 3.1, Alg. 2), and computes the row interpolative decomposition on the
+ * sketch (Sec. 4, Alg. 4).
+ *
+ * Conventions for every call
+ *  - Matrices are ROW-MAJOR with an explicit row stride (ld*, in elements,
+ *    >= the number of columns).  "Column-major X" below means the row-major
+ *    storage of X^T.
+ *  - Every data pointer is a DEVICE pointer on the context's device, owned by
+ *    the caller; the library never frees or keeps it.  Pointers to scalar
+ *    outputs (r_out, err_est, ...) are HOST pointers.
+ *  - Calls are stream-ordered on the context's stream.  A call that returns a
+ *    host scalar synchronises that stream before returning.
+ *  - Errors are status codes; nothing is thrown across the ABI.  Arguments
+ *    are validated on the host before any launch (LRS_EINVAL, with a message
+ *    from lrs_last_error).  LRS_ECUDA reports a CUDA error;  LRS_ETIMEOUT a
+ *    device-side wait that gave up (bounded spins, never an endless loop);
+ *    LRS_ENOMEM a failed workspace allocation.  After LRS_ECUDA/LRS_ETIMEOUT
+ *    the context stays usable only if the CUDA context is.
+ *  - The library owns one workspace per context, grown on demand with
+ *    cudaMalloc and released by lrs_destroy.
+ */
+#ifndef LRS_H_
+#define LRS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LRS_OK = 0,
+  LRS_EINVAL = 1,
+  LRS_ENOMEM = 2,
+  LRS_ECUDA = 3,
+  LRS_ERANK = 4,     /* numerical rank r < k: outputs valid at rank r */
+  LRS_ETIMEOUT = 5
+} lrs_status;
+
+/* storage type of A_f */
+typedef enum { LRS_F64 = 0, LRS_F32 = 1, LRS_BF16 = 2 } lrs_dtype;
+
+/* Sec. 2 sketches.  Per axis the coarse point j sits at fine index
+ * c_j = s*j + s/2 (integer division).
+ *  LRS_INJECT      D = 1 at c_j                           (direct injection)
+ *  LRS_FULLWEIGHT  1/4, 1/2, 1/4 at c_j-1, c_j, c_j+1;     (nearest neighbour,
+ *                  a neighbour outside the grid is zero    d = 1; needs s >= 2)
+ *  LRS_BLOCKAVG    1/s on s*j .. s*j+s-1                   (global sketch)
+ * Multi-dimensional grids use the tensor product of the per-axis operators. */
+typedef enum { LRS_INJECT = 0, LRS_FULLWEIGHT = 1, LRS_BLOCKAVG = 2 } lrs_stencil;
+
+/* arithmetic of the dense products that read A_f or its projection
+ *  LRS_PREC_FP64        FP64 FMA on CUDA cores (for FP64 data)
+ *  LRS_PREC_FP32        FP32 FMA on CUDA cores (the plain FP32 method)
+ *  LRS_PREC_SPLIT_BF16  tcgen05 tensor cores, BF16 hi+lo split of both
+ *                       operands (3 products), FP32 accumulation
+ *  LRS_PREC_BF16X3      tcgen05, 3-piece BF16 split (6 products), FP32-level */
+typedef enum {
+  LRS_PREC_FP64 = 0,
+  LRS_PREC_FP32 = 1,
+  LRS_PREC_SPLIT_BF16 = 2,
+  LRS_PREC_BF16X3 = 3
+} lrs_prec;
+
+/* Cartesian fine grid: N[0] is x (fastest), then y, z.  n = prod N[d];
+ * coarse grid N[d]/s[d] (N[d] % s[d] == 0), l = prod N[d]/s[d].  Dof index of
+ * (x,y,z) is (z*N[1] + y)*N[0] + x; coarse index likewise. */
+typedef struct {
+  int32_t ndim;       /* 1, 2 or 3 */
+  int32_t kind;       /* lrs_stencil */
+  int64_t N[3];
+  int32_t s[3];
+} lrs_grid;
+
+typedef struct lrs_ctx lrs_ctx;
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). */
+lrs_status lrs_create(lrs_ctx** out, int device, void* cuda_stream);
+void lrs_destroy(lrs_ctx* ctx);
+/* Message of the last failed call on ctx (never NULL; "" if none). */
+const char* lrs_last_error(const lrs_ctx* ctx);
+/* Build identification, e.g. "lrs sm_103a". */
+const char* lrs_version(void);
+
+/*
+ * lrs_sketch -- A_c = A_f D (Sec. 2, Table 1), D never formed.
+ *   A   m x n in `dtype` (n = grid->N product), row stride lda.
+ *   Y   m x l FP64, row stride ldy.  Accumulated in FP64; injection is an
+ *       exact copy.
+ * EINVAL: m < 1, N[d] % s[d] != 0, s[d] < 1, full weighting with s[d] < 2,
+ * lda < n, ldy < l, NULL pointers.
+ */
+lrs_status lrs_sketch(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t lda,
+                      const lrs_grid* grid, double* Y, int64_t ldy);
+
+/*
+ * lrs_power_pass -- C-PWR (Sec. 5, Alg. 7) from one touch of A_f.
+ *   Reads the sketch points (grid `sketch`) and the Gram subsample
+ *   W = A_f(:, I) (grid `gram`, injection points; |I| > k, Sec. 5 Remark),
+ *   then runs q iterations  G <- W^T G; [G <- QR(G)]; G <- W G; [G <- QR(G)]
+ *   with the bracketed re-orthonormalisations when reorth != 0.  QR(.) is the
+ *   rank-revealing range finder of lrs_range_find with tolerance rtol.  With
+ *   reorth the loop starts from QR(A_f D) (Alg. 7's Q_np), which has the same
+ *   range as A_f D up to the truncated directions.
+ *   Y   m x l FP64 (row stride ldy): the sketch A_f D.
+ *   G   m x l FP64 (row stride ldg): G_q in its first *g_cols columns (the
+ *       rank after truncation when reorth != 0, else l).
+ *   q = 0 returns G = Y.  `gram` may be NULL when q = 0.
+ *   prec: arithmetic of the W^T G and W G products (lrs_prec).
+ */
+lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t lda,
+                          const lrs_grid* sketch, const lrs_grid* gram, int32_t q,
+                          int32_t reorth, double rtol, int32_t prec,
+                          double* Y, int64_t ldy, double* G, int64_t ldg, int64_t* g_cols);
+
+/*
+ * lrs_range_find -- orthonormal basis of the numerical range of G (the
+ * "QR(A_c)" of Algs. 2/3 and "QR(G_q)" of Alg. 7), by Householder QR with
+ * column pivoting in FP64, stopped before the first step whose largest
+ * remaining column norm is <= rtol * |R_00|.
+ *   G   m x l FP64 (row stride ldg), not modified.
+ *   Q   m x r FP64 (row stride ldq >= min(m,l)); caller allocates min(m,l)
+ *       columns.  *r_out = r.
+ */
+lrs_status lrs_range_find(lrs_ctx* ctx, const double* G, int64_t m, int64_t l, int64_t ldg,
+                          double rtol, double* Q, int64_t ldq, int64_t* r_out);
+
+/*
+ * lrs_svd_k -- TPC-SVD from a range basis (Sec. 3.1, Alg. 2):
+ *   B = Q^T A_f (r x n; the one full read of A_f; ||A_f||_F^2 fused),
+ *   SVD(B) via the R factor of B^T (Householder TSQR) and one-sided Jacobi,
+ *   U_k = Q U_B(:,1:k), S_k, V_k = B^T U_B(:,1:k) S_k^{-1}.
+ *   A   m x n in dtype, row stride lda.    Q  m x r FP64, row stride ldq.
+ *   U   m x k FP64 (row stride ldu).       S  k FP64.
+ *   V   n x k (row stride ldv), FP64 when prec == LRS_PREC_FP64, else FP32.
+ *   err_est (host, may be NULL): sqrt(sum_{i>k} s_i(B)^2 / ||A_f||_F^2), the
+ *       energy of B beyond rank k.  U_k S_k V_k^T is the orthogonal projection
+ *       U_k U_k^T A_f, whose squared error is this term plus the energy of A_f
+ *       outside range(Q); err_est is therefore exact when range(Q) holds A_f
+ *       and a lower bound otherwise.  Computed from the tail singular values
+ *       (no cancellation against ||A_f||_F^2).
+ * Sign convention: the largest-magnitude entry of each U column is positive.
+ * Returns LRS_ERANK when r < k; then only the first r columns are written.
+ */
+lrs_status lrs_svd_k(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                     const double* Q, int64_t ldq, int64_t r, int32_t k, int32_t prec,
+                     double* U, int64_t ldu, double* S, void* V, int64_t ldv, double* err_est);
+
+/*
+ * lrs_id_k -- rank-k row ID of a sketch (Sec. 4, Algs. 4/5): Householder
+ * CPQR of Ysk^T in FP64 for k steps (pivot = largest remaining column norm,
+ * norms recomputed each step, ties to the lowest position), C = R_1^{-1} R_2,
+ * P = ([I | C] Z^T)^T.
+ *   Ysk m x l FP64 (row stride ldy), not modified.
+ *   J   k int32: skeleton snapshot (row) indices, in pivot order.
+ *   P   m x k FP64 (row stride ldp) with P(J,:) = I exactly.
+ *   err_est (host, may be NULL): ||R_22||_F / ||Ysk||_F, the relative error of
+ *       the coarse ID.  Lift: A_f ~ P A_f(J, :) (Alg. 4).
+ * Returns LRS_ERANK if the sketch has a zero column norm before step k.
+ */
+lrs_status lrs_id_k(lrs_ctx* ctx, const double* Ysk, int64_t m, int64_t l, int64_t ldy, int32_t k,
+                    int32_t* J, double* P, int64_t ldp, double* err_est);
+
+/*
+ * lrs_gemm_tn -- the dense contraction every A-pass uses:
+ *   C (M x N) = X^T A,   X: K x M,  A: K x N  (both row-major, K rows).
+ * Exposed for tests and benchmarks of the A-pass kernel alone.
+ *   x_dtype, a_dtype: lrs_dtype of X and A.  c_f64: C is FP64 (else FP32).
+ *   c_trans: write C^T (N x M, row stride ldc) instead of C.
+ */
+lrs_status lrs_gemm_tn(lrs_ctx* ctx, int64_t M, int64_t N, int64_t K,
+                       const void* X, int32_t x_dtype, int64_t ldx,
+                       const void* A, int32_t a_dtype, int64_t lda,
+                       void* C, int32_t c_f64, int32_t c_trans, int64_t ldc, int32_t prec);
+
+/* Number of kernel launches this context has issued (for launch accounting). */
+int64_t lrs_launch_count(const lrs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRS_H_ */

@@ -20,7 +20,7 @@ from __future__ import annotations
 import numpy as np
 
 
-def cpqr(M: np.ndarray, kmax: int | None = None, rtol: float = 0.0):
+def cpqr(M: np.ndarray, kmax: int | None = None, rtol: float = 0.0, gaps: list | None = None):
     """Pivoted Householder QR of M (p x c).
 
     Returns (Q, R, perm, r, tail) with r steps taken:
@@ -28,6 +28,8 @@ def cpqr(M: np.ndarray, kmax: int | None = None, rtol: float = 0.0):
       R    (r x c) upper trapezoidal in pivoted column order,
       perm (c,)    M[:, perm] ~ Q R  (first r entries are the pivots),
       tail         Frobenius norm of the unreduced trailing block after r steps.
+    If ``gaps`` is a list, the relative margin (best - runner-up) / best of the
+    pivot choice at every step is appended to it.
     """
     M = np.array(M, dtype=np.float64, copy=True)
     p, c = M.shape
@@ -37,6 +39,9 @@ def cpqr(M: np.ndarray, kmax: int | None = None, rtol: float = 0.0):
     for j in range(kcap):
         norms = np.sqrt(np.sum(M[j:, j:] ** 2, axis=0))
         jj = int(np.argmax(norms))
+        if gaps is not None:
+            rest = np.delete(norms, jj)
+            gaps.append(float((norms[jj] - rest.max()) / norms[jj]) if len(rest) and norms[jj] > 0 else 1.0)
         if top is None:
             top = norms[jj]
         if norms[jj] == 0.0 or (j > 0 and norms[jj] <= rtol * top):

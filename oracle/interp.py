@@ -21,10 +21,10 @@ from scipy.linalg import solve_triangular
 from .cpqr import cpqr
 
 
-def row_id(Ac: np.ndarray, k: int):
-    """Rank-k row ID of Ac (m x l).  Returns (J, P, err_est)."""
+def row_id(Ac: np.ndarray, k: int, gaps: list | None = None):
+    """Rank-k row ID of Ac (m x l).  Returns (J, P, err_est); ``gaps`` as in cpqr."""
     m = Ac.shape[0]
-    _, R, perm, r, tail = cpqr(Ac.T, kmax=k)
+    _, R, perm, r, tail = cpqr(Ac.T, kmax=k, gaps=gaps)
     if r < k:
         raise ValueError(f"numerical rank {r} < k = {k}")
     R1, R2 = R[:, :k], R[:, k:]

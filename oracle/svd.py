@@ -9,10 +9,15 @@ The rank-k approximation is A_f ~ U_k S_k V_k^T.
 Sign convention (a reading; the paper fixes none): each column of U_k has its
 largest-magnitude entry positive, and V_k's column flips with it.
 
-Error estimate (a reading): with the orthonormal factor U_k = Q U_B,k the
-approximation equals the orthogonal projection U_k U_k^T A_f, so
-||A_f - A_hat||_F^2 = ||A_f||_F^2 - sum_{i<=k} s_i^2 exactly; the returned
-err_est is sqrt(max(0, 1 - sum s_i^2 / ||A_f||_F^2)).
+Error estimate (a reading; the paper defines none for the SVD): with the
+orthonormal factor U_k = Q U_B,k the approximation is the orthogonal
+projection U_k U_k^T A_f, and
+  ||A_f - A_hat||_F^2 = ||(I - Q Q^T) A_f||_F^2 + sum_{i>k} s_i(B)^2 .
+err_est keeps the second term, the energy of B beyond rank k, relative to
+||A_f||_F^2:  err_est = sqrt(sum_{i>k} s_i^2 / ||A_f||_F^2).  It is computed
+from the tail singular values directly (no cancellation against ||A_f||^2),
+equals the relative Frobenius error when range(Q) holds A_f (E_I = 0 in
+Thm. 3.2) and is a lower bound otherwise.
 """
 from __future__ import annotations
 
@@ -47,7 +52,7 @@ def svd_of_projection(B: np.ndarray, Q: np.ndarray, k: int, fro2: float):
     V = Vbt[:kk].T
     U, V = sign_fix(U, V)
     S = s[:kk]
-    err = float(np.sqrt(max(0.0, 1.0 - np.sum(S ** 2) / fro2))) if fro2 > 0 else 0.0
+    err = float(np.sqrt(np.sum(s[kk:] ** 2) / fro2)) if fro2 > 0 else 0.0
     return U, S, V, err, s
 
 

@@ -1,0 +1,186 @@
+"""Thin ctypes binding of the C ABI in include/lrs.h.
+
+Argument marshalling only: every step of the path runs in liblrs.so.  The
+functions take torch CUDA tensors (or raw integer device pointers) plus the
+sizes of the C signatures, and raise LrsError on a non-OK status (except
+LRS_ERANK, which is returned, since the outputs are still valid at rank r).
+There is no CPU fallback: loading fails loudly if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LRS_OK, LRS_EINVAL, LRS_ENOMEM, LRS_ECUDA, LRS_ERANK, LRS_ETIMEOUT = range(6)
+LRS_F64, LRS_F32, LRS_BF16 = 0, 1, 2
+LRS_INJECT, LRS_FULLWEIGHT, LRS_BLOCKAVG = 0, 1, 2
+LRS_PREC_FP64, LRS_PREC_FP32, LRS_PREC_SPLIT_BF16, LRS_PREC_BF16X3 = 0, 1, 2, 3
+
+KIND = {"inject": LRS_INJECT, "fullweight": LRS_FULLWEIGHT, "blockavg": LRS_BLOCKAVG}
+DTYPE = {"f64": LRS_F64, "f32": LRS_F32, "bf16": LRS_BF16}
+STATUS = {0: "LRS_OK", 1: "LRS_EINVAL", 2: "LRS_ENOMEM", 3: "LRS_ECUDA", 4: "LRS_ERANK",
+          5: "LRS_ETIMEOUT"}
+
+
+class LrsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class lrs_grid(C.Structure):
+    _fields_ = [("ndim", C.c_int32), ("kind", C.c_int32), ("N", C.c_int64 * 3), ("s", C.c_int32 * 3)]
+
+
+def make_grid(N, s, kind) -> lrs_grid:
+    """lrs_grid from per-axis sizes (x first), factors and stencil name/code."""
+    g = lrs_grid()
+    g.ndim = len(N)
+    g.kind = KIND[kind] if isinstance(kind, str) else int(kind)
+    for d in range(3):
+        g.N[d] = int(N[d]) if d < len(N) else 1
+        g.s[d] = int(s[d]) if d < len(s) else 1
+    return g
+
+
+def grid_of(spec) -> lrs_grid:
+    """lrs_grid from any object with N, s and kind attributes (e.g. synth.GridSpec)."""
+    return make_grid(spec.N, spec.s, spec.kind)
+
+
+_SIG = {
+    "lrs_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p]),
+    "lrs_destroy": (None, [C.c_void_p]),
+    "lrs_last_error": (C.c_char_p, [C.c_void_p]),
+    "lrs_version": (C.c_char_p, []),
+    "lrs_launch_count": (C.c_int64, [C.c_void_p]),
+    "lrs_sketch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64,
+                             C.POINTER(lrs_grid), C.c_void_p, C.c_int64]),
+    "lrs_power_pass": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64,
+                                 C.POINTER(lrs_grid), C.POINTER(lrs_grid), C.c_int32, C.c_int32,
+                                 C.c_double, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p,
+                                 C.c_int64, C.POINTER(C.c_int64)]),
+    "lrs_range_find": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64,
+                                 C.c_double, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
+    "lrs_svd_k": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_int64,
+                            C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_void_p,
+                            C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
+    "lrs_id_k": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
+                           C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
+    "lrs_gemm_tn": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_int32,
+                              C.c_int64, C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_int32,
+                              C.c_int32, C.c_int64, C.c_int32]),
+}
+
+EXPORTS = tuple(_SIG)
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """dlopen liblrs.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"liblrs.so not found at {path}; run paper_2105_01271_gb300/build.py")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIG.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+class Context:
+    """One lrs_ctx bound to a device and a CUDA stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = load_library()
+        h = C.c_void_p()
+        sp = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+        st = self.lib.lrs_create(C.byref(h), int(device), C.c_void_p(sp))
+        if st != LRS_OK:
+            raise LrsError(st, "lrs_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lrs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, allow_rank=False):
+        if st == LRS_OK or (allow_rank and st == LRS_ERANK):
+            return st
+        raise LrsError(st, self.lib.lrs_last_error(self.h).decode())
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.lrs_launch_count(self.h))
+
+    # --- the C ABI, one wrapper per entry point -----------------------------
+    def sketch(self, A, dtype, m, lda, grid: lrs_grid, Y, ldy):
+        return self._check(self.lib.lrs_sketch(self.h, _ptr(A), dtype, m, lda, C.byref(grid),
+                                               _ptr(Y), ldy))
+
+    def power_pass(self, A, dtype, m, lda, sketch: lrs_grid, gram, q, reorth, rtol, prec,
+                   Y, ldy, G, ldg) -> int:
+        gc = C.c_int64(0)
+        gp = C.byref(gram) if gram is not None else None
+        self._check(self.lib.lrs_power_pass(self.h, _ptr(A), dtype, m, lda, C.byref(sketch), gp,
+                                            q, reorth, rtol, prec, _ptr(Y), ldy, _ptr(G), ldg,
+                                            C.byref(gc)))
+        return gc.value
+
+    def range_find(self, G, m, l, ldg, rtol, Q, ldq) -> int:
+        r = C.c_int64(0)
+        self._check(self.lib.lrs_range_find(self.h, _ptr(G), m, l, ldg, rtol, _ptr(Q), ldq,
+                                            C.byref(r)))
+        return r.value
+
+    def svd_k(self, A, dtype, m, n, lda, Q, ldq, r, k, prec, U, ldu, S, V, ldv):
+        err = C.c_double(0.0)
+        st = self._check(self.lib.lrs_svd_k(self.h, _ptr(A), dtype, m, n, lda, _ptr(Q), ldq, r, k,
+                                            prec, _ptr(U), ldu, _ptr(S), _ptr(V), ldv,
+                                            C.byref(err)), allow_rank=True)
+        return err.value, st
+
+    def id_k(self, Ysk, m, l, ldy, k, J, P, ldp):
+        err = C.c_double(0.0)
+        st = self._check(self.lib.lrs_id_k(self.h, _ptr(Ysk), m, l, ldy, k, _ptr(J), _ptr(P), ldp,
+                                           C.byref(err)), allow_rank=True)
+        return err.value, st
+
+    def gemm_tn(self, M, N, K, X, x_dtype, ldx, A, a_dtype, lda, Cm, c_f64, c_trans, ldc, prec):
+        return self._check(self.lib.lrs_gemm_tn(self.h, M, N, K, _ptr(X), x_dtype, ldx, _ptr(A),
+                                                a_dtype, lda, _ptr(Cm), c_f64, c_trans, ldc, prec))
+
+
+def load(device: int = 0, stream=None) -> Context:
+    return Context(device, stream)

@@ -1,0 +1,116 @@
+// Shared device/host helpers of the lrs library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/lrs.h"
+
+namespace lrs {
+
+// ---------------------------------------------------------------------------
+// element loads of A_f in its storage type, widened to double / float
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double ld_f64(const void* p, int32_t dt, int64_t i) {
+  if (dt == LRS_F64) return __ldg(reinterpret_cast<const double*>(p) + i);
+  if (dt == LRS_F32) return (double)__ldg(reinterpret_cast<const float*>(p) + i);
+  const unsigned short b = __ldg(reinterpret_cast<const unsigned short*>(p) + i);
+  return (double)__uint_as_float(((unsigned)b) << 16);
+}
+
+__device__ __forceinline__ size_t dtype_size(int32_t dt) {
+  return dt == LRS_F64 ? 8 : (dt == LRS_F32 ? 4 : 2);
+}
+
+// ---------------------------------------------------------------------------
+// warp / block reductions
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; `red` must hold >= 32 elements of shared memory.  All
+// threads return the total.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  T t = (threadIdx.x < nw) ? red[threadIdx.x] : T(0);
+  if (wid == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  t = red[0];
+  __syncthreads();
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// Grid barrier with a bounded wait.
+//
+// Used only by kernels launched with cudaLaunchCooperativeKernel, which
+// guarantees that all blocks are co-resident.  Each wait gives up after
+// kSpinLimit polls (about a second with the back-off below), records
+// LRS_ETIMEOUT in *err and returns false; every block then leaves the kernel
+// at its next barrier check, so a lost arrival never hangs the GPU.
+// ---------------------------------------------------------------------------
+struct GridBarrier {
+  unsigned int* count;   // arrivals in the current generation
+  unsigned int* gen;     // generation counter
+  int* err;              // 0 = ok, else an lrs_status
+};
+
+constexpr long long kSpinLimit = 20000000LL;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_volatile_s32(const int* p) {
+  return *reinterpret_cast<const volatile int*>(p);
+}
+
+__device__ __forceinline__ bool grid_sync(const GridBarrier& b) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned g = ld_acquire_u32(b.gen);
+    __threadfence();
+    const unsigned arrived = atomicAdd(b.count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(b.count, 0u);
+      __threadfence();
+      atomicAdd(b.gen, 1u);
+    } else {
+      long long it = 0;
+      while (ld_acquire_u32(b.gen) == g) {
+        if (ld_volatile_s32(b.err) != 0) break;
+        if (++it > kSpinLimit) { atomicCAS(b.err, 0, (int)LRS_ETIMEOUT); break; }
+        if (it > 64) __nanosleep(40);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ld_volatile_s32(b.err) == 0;
+}
+
+}  // namespace lrs
+
+// ---------------------------------------------------------------------------
+// host-side error plumbing
+// ---------------------------------------------------------------------------
+#define LRS_CUDA_TRY(ctx, expr)                                             \
+  do {                                                                      \
+    cudaError_t _e = (expr);                                                \
+    if (_e != cudaSuccess) {                                                \
+      return lrs_fail((ctx), LRS_ECUDA, "%s: %s (%s:%d)", #expr,            \
+                      cudaGetErrorString(_e), __FILE__, __LINE__);          \
+    }                                                                       \
+  } while (0)

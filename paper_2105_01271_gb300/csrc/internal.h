@@ -1,0 +1,103 @@
+// Internal host interface between the C ABI layer and the kernel files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/lrs.h"
+
+struct lrs_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  int coop_ok = 0;
+  char err[512] = {0};
+  // workspace: one device arena, bump-allocated per call and reset at call entry
+  char* ws = nullptr;
+  size_t ws_cap = 0;
+  size_t ws_top = 0;
+  // small pinned host buffer for scalar read-back
+  void* host_scratch = nullptr;
+  int64_t launches = 0;
+};
+
+lrs_status lrs_fail(lrs_ctx* ctx, lrs_status st, const char* fmt, ...);
+
+namespace lrs {
+
+// workspace ---------------------------------------------------------------
+lrs_status ws_reserve(lrs_ctx* ctx, size_t bytes);           // grow (only between calls)
+void* ws_alloc(lrs_ctx* ctx, size_t bytes);                   // 256-B aligned, nullptr if full
+
+// sketch.cu ----------------------------------------------------------------
+struct GridDev {
+  int ndim, kind;
+  int64_t N[3];
+  int32_t s[3];
+  int64_t Nc[3];
+  int64_t n, l;
+};
+bool grid_from_abi(const lrs_grid* g, GridDev* out, char* why, size_t nwhy);
+// Y[m x l] (FP64) = A D
+lrs_status launch_sketch(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int64_t lda,
+                         const GridDev& g, double* Y, int64_t ldy);
+// W[m x |I|] (FP64) = A(:, I)  with I the injection points of grid g
+lrs_status launch_gather(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int64_t lda,
+                         const GridDev& g, double* W, int64_t ldw);
+// sum of squares of A (m x n), FP64, added into *out (device)
+lrs_status launch_fro2(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int64_t n,
+                       int64_t lda, double* out);
+
+// gemm_simt.cu / gemm_tc.cu -----------------------------------------------
+// C (M x N) = X^T A ; X: K x M (ldx), A: K x N (lda); row-major everything.
+struct GemmArgs {
+  int64_t M, N, K;
+  const void* X; int32_t xdt; int64_t ldx;
+  const void* A; int32_t adt; int64_t lda;
+  void* C; int c_f64; int c_trans; int64_t ldc;
+  double alpha;            // C = alpha * X^T A
+};
+lrs_status launch_gemm_simt(lrs_ctx* ctx, const GemmArgs& a, int fp64);
+lrs_status launch_gemm_tc(lrs_ctx* ctx, const GemmArgs& a, int prec);
+
+// cpqr.cu --------------------------------------------------------------------
+// Householder CPQR of the p x c matrix M stored COLUMN-major (column j at
+// M + j*ldm), in place, FP64.  Stops after kmax steps or when the largest
+// remaining column norm <= rtol * |R_00|.
+struct CpqrOut {
+  int32_t* perm;     // device, c entries: position -> original column
+  double* R;         // device, kmax x c, row-major (row stride c), pivoted column order
+  double* V;         // device, Householder vectors, p x kmax column-major (unit norm)
+  double* tail2;     // device, 1: squared Frobenius norm of the trailing block
+  int32_t* rank;     // device, 1: steps taken
+};
+lrs_status launch_cpqr(lrs_ctx* ctx, double* M, int64_t p, int64_t c, int64_t ldm,
+                       int64_t kmax, double rtol, const CpqrOut& o);
+// Q (p x r, row-major ldq) = H_0 ... H_{r-1} [I_r; 0]
+lrs_status launch_form_q(lrs_ctx* ctx, const double* V, int64_t p, int64_t r,
+                         double* Q, int64_t ldq);
+// ID: P (m x k) from R (k x m, pivoted order) and perm.
+lrs_status launch_id_coeffs(lrs_ctx* ctx, const double* R, int64_t k, int64_t m,
+                            const int32_t* perm, int32_t* J, double* P, int64_t ldp);
+
+// svd_small.cu ------------------------------------------------------------------
+// R factor (r x r, row-major) of B^T where B is r x n row-major in FP32 or FP64.
+lrs_status launch_tsqr(lrs_ctx* ctx, const void* B, int b_f64, int64_t r, int64_t n,
+                       int64_t ldb, double* R);
+// one-sided Jacobi on the columns of R (r x r): R V = U_R diag(s); returns
+// V (r x r, row-major) and s (r), sorted descending.
+lrs_status launch_jacobi(lrs_ctx* ctx, double* R, int64_t r, double* V, double* s, int fp64);
+
+// misc.cu -------------------------------------------------------------------------
+// transposed copy of a row-major FP64 matrix: dst (cols x rows) = src^T
+lrs_status launch_transpose(lrs_ctx* ctx, const double* src, int64_t rows, int64_t cols,
+                            int64_t lds, double* dst, int64_t ldd);
+// U columns sign fix (largest |entry| positive), applied to U (m x k) and V (n x k)
+lrs_status launch_sign_fix(lrs_ctx* ctx, double* U, int64_t m, int64_t k, int64_t ldu,
+                           void* V, int v_f64, int64_t n, int64_t ldv);
+// W[:, j] = V[:, j] / s[j]  (r x k, FP64)
+lrs_status launch_scale_cols(lrs_ctx* ctx, const double* V, int64_t r, int64_t ldv,
+                             const double* s, int64_t k, double* W, int64_t ldw);
+
+}  // namespace lrs

@@ -1,0 +1,418 @@
+// C ABI of the library (include/lrs.h): argument validation, workspace, and
+// the order of kernel launches for each call of the paper's path.
+#include "common.cuh"
+#include "internal.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+lrs_status lrs_fail(lrs_ctx* ctx, lrs_status st, const char* fmt, ...) {
+  if (ctx) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+
+namespace lrs {
+
+static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+lrs_status ws_reserve(lrs_ctx* ctx, size_t bytes) {
+  ctx->ws_top = 0;
+  if (bytes <= ctx->ws_cap) return LRS_OK;
+  if (ctx->ws) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_cap = 0;
+  }
+  size_t cap = bytes + (bytes >> 3) + (1 << 20);
+  if (cudaMalloc((void**)&ctx->ws, cap) != cudaSuccess) {
+    cudaGetLastError();
+    return lrs_fail(ctx, LRS_ENOMEM, "cannot allocate a %zu-byte workspace", cap);
+  }
+  ctx->ws_cap = cap;
+  return LRS_OK;
+}
+
+void* ws_alloc(lrs_ctx* ctx, size_t bytes) {
+  const size_t b = align256(bytes);
+  if (ctx->ws_top + b > ctx->ws_cap) return nullptr;
+  void* p = ctx->ws + ctx->ws_top;
+  ctx->ws_top += b;
+  return p;
+}
+
+// bytes of workspace the TSQR reduction levels of an r x n matrix need
+static size_t tsqr_ws(int64_t r, int64_t n, size_t tsz) {
+  int64_t C = (int64_t)((200 * 1024) / (tsz * (size_t)r));
+  if (C > 1024) C = 1024;
+  if (C < 1) C = 1;
+  size_t b = 0;
+  int64_t cur = n;
+  for (int guard = 0; guard < 64; ++guard) {
+    const int64_t chunks = (cur + C - 1) / C;
+    if (chunks <= 1) break;
+    cur = chunks * r;
+    b += align256(tsz * (size_t)(r * cur));
+  }
+  return b;
+}
+
+// bytes of workspace one orthonormalisation of a p x c matrix needs
+static size_t orth_ws(int64_t p, int64_t c) {
+  const int64_t kmax = p < c ? p : c;
+  size_t b = 0;
+  b += align256(8 * (size_t)(p * c));            // column-major copy
+  b += align256(4 * (size_t)c);                  // perm
+  b += 2 * align256(8 * (size_t)(kmax * c));     // R, Rphys
+  b += align256(8 * (size_t)(p * kmax));         // V
+  b += align256(8 * (size_t)c) * 3 + align256((size_t)c);  // norm2, pos_of, phys_at, done
+  b += align256(8 * (size_t)p);                  // vbuf
+  b += 16 * 4096;                                // per-block scratch, barrier, scalars
+  return b;
+}
+
+// Orthonormal basis of the numerical range of Min (p x c, row-major ldi):
+// Q (p x r, row-major ldq), r returned through *r_out.  Synchronises.
+static lrs_status orth(lrs_ctx* ctx, const double* Min, int64_t p, int64_t c, int64_t ldi,
+                       double rtol, double* Q, int64_t ldq, int64_t* r_out) {
+  const int64_t kmax = p < c ? p : c;
+  double* Mc = (double*)ws_alloc(ctx, 8 * (size_t)(p * c));
+  CpqrOut o{};
+  o.perm = (int32_t*)ws_alloc(ctx, 4 * (size_t)c);
+  o.R = (double*)ws_alloc(ctx, 8 * (size_t)(kmax * c));
+  o.V = (double*)ws_alloc(ctx, 8 * (size_t)(p * kmax));
+  o.tail2 = (double*)ws_alloc(ctx, 8);
+  o.rank = (int32_t*)ws_alloc(ctx, 8);
+  if (!Mc || !o.perm || !o.R || !o.V || !o.tail2 || !o.rank)
+    return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (orth)");
+  lrs_status st = launch_transpose(ctx, Min, p, c, ldi, Mc, p);   // column-major copy
+  if (st) return st;
+  st = launch_cpqr(ctx, Mc, p, c, p, kmax, rtol, o);
+  if (st) return st;
+  int32_t r = 0;
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(&r, o.rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  st = launch_form_q(ctx, o.V, p, r, Q, ldq);
+  if (st) return st;
+  *r_out = r;
+  return LRS_OK;
+}
+
+static lrs_status gemm(lrs_ctx* ctx, int prec, int64_t M, int64_t N, int64_t K, const void* X,
+                       int32_t xdt, int64_t ldx, const void* A, int32_t adt, int64_t lda, void* C,
+                       int c_f64, int c_trans, int64_t ldc, double alpha = 1.0) {
+  GemmArgs g{M, N, K, X, xdt, ldx, A, adt, lda, C, c_f64, c_trans, ldc, alpha};
+  if (prec == LRS_PREC_FP64) return launch_gemm_simt(ctx, g, 1);
+  if (prec == LRS_PREC_FP32) return launch_gemm_simt(ctx, g, 0);
+  return launch_gemm_tc(ctx, g, prec);
+}
+
+}  // namespace lrs
+
+using namespace lrs;
+
+// ===========================================================================
+extern "C" {
+
+const char* lrs_version(void) { return "lrs 0.1 sm_103a"; }
+
+lrs_status lrs_create(lrs_ctx** out, int device, void* cuda_stream) {
+  if (!out) return LRS_EINVAL;
+  *out = nullptr;
+  lrs_ctx* ctx = new (std::nothrow) lrs_ctx();
+  if (!ctx) return LRS_ENOMEM;
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); delete ctx; return LRS_ECUDA; }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { cudaGetLastError(); delete ctx; return LRS_ECUDA; }
+  ctx->num_sms = prop.multiProcessorCount;
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
+  ctx->coop_ok = coop;
+  if (cudaMallocHost(&ctx->host_scratch, 4096) != cudaSuccess) { cudaGetLastError(); delete ctx; return LRS_ENOMEM; }
+  *out = ctx;
+  return LRS_OK;
+}
+
+void lrs_destroy(lrs_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->ws) { cudaStreamSynchronize(ctx->stream); cudaFree(ctx->ws); }
+  if (ctx->host_scratch) cudaFreeHost(ctx->host_scratch);
+  delete ctx;
+}
+
+const char* lrs_last_error(const lrs_ctx* ctx) { return ctx ? ctx->err : "NULL context"; }
+
+int64_t lrs_launch_count(const lrs_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+static bool dtype_ok(int32_t dt) { return dt == LRS_F64 || dt == LRS_F32 || dt == LRS_BF16; }
+static bool prec_ok(int32_t p) { return p >= LRS_PREC_FP64 && p <= LRS_PREC_BF16X3; }
+
+lrs_status lrs_sketch(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t lda,
+                      const lrs_grid* grid, double* Y, int64_t ldy) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  GridDev g;
+  char why[256];
+  if (!grid_from_abi(grid, &g, why, sizeof why)) return lrs_fail(ctx, LRS_EINVAL, "sketch: %s", why);
+  if (!A || !Y) return lrs_fail(ctx, LRS_EINVAL, "sketch: NULL pointer");
+  if (!dtype_ok(dtype)) return lrs_fail(ctx, LRS_EINVAL, "sketch: bad dtype %d", dtype);
+  if (m < 1) return lrs_fail(ctx, LRS_EINVAL, "sketch: m=%lld < 1", (long long)m);
+  if (lda < g.n || ldy < g.l) return lrs_fail(ctx, LRS_EINVAL, "sketch: lda/ldy too small");
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  lrs_status st = ws_reserve(ctx, 0);
+  if (st) return st;
+  return launch_sketch(ctx, A, dtype, m, lda, g, Y, ldy);
+}
+
+lrs_status lrs_range_find(lrs_ctx* ctx, const double* G, int64_t m, int64_t l, int64_t ldg,
+                          double rtol, double* Q, int64_t ldq, int64_t* r_out) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  if (!G || !Q || !r_out) return lrs_fail(ctx, LRS_EINVAL, "range_find: NULL pointer");
+  if (m < 1 || l < 1) return lrs_fail(ctx, LRS_EINVAL, "range_find: empty matrix %lldx%lld", (long long)m, (long long)l);
+  if (ldg < l || ldq < (m < l ? m : l)) return lrs_fail(ctx, LRS_EINVAL, "range_find: ldg/ldq too small");
+  if (!(rtol >= 0.0) || rtol >= 1.0) return lrs_fail(ctx, LRS_EINVAL, "range_find: rtol=%g not in [0,1)", rtol);
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  lrs_status st = ws_reserve(ctx, orth_ws(m, l));
+  if (st) return st;
+  return orth(ctx, G, m, l, ldg, rtol, Q, ldq, r_out);
+}
+
+lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t lda,
+                          const lrs_grid* sketch, const lrs_grid* gram, int32_t q, int32_t reorth,
+                          double rtol, int32_t prec, double* Y, int64_t ldy, double* G, int64_t ldg,
+                          int64_t* g_cols) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  GridDev gs, gg;
+  char why[256];
+  if (!grid_from_abi(sketch, &gs, why, sizeof why)) return lrs_fail(ctx, LRS_EINVAL, "power_pass: sketch grid: %s", why);
+  if (!A || !Y || !G || !g_cols) return lrs_fail(ctx, LRS_EINVAL, "power_pass: NULL pointer");
+  if (!dtype_ok(dtype) || !prec_ok(prec)) return lrs_fail(ctx, LRS_EINVAL, "power_pass: bad dtype/prec");
+  if (m < 1 || q < 0 || q > 16) return lrs_fail(ctx, LRS_EINVAL, "power_pass: m=%lld q=%d", (long long)m, q);
+  if (lda < gs.n || ldy < gs.l || ldg < gs.l) return lrs_fail(ctx, LRS_EINVAL, "power_pass: strides too small");
+  if (!(rtol >= 0.0) || rtol >= 1.0) return lrs_fail(ctx, LRS_EINVAL, "power_pass: rtol=%g not in [0,1)", rtol);
+  if (q > 0) {
+    if (!grid_from_abi(gram, &gg, why, sizeof why)) return lrs_fail(ctx, LRS_EINVAL, "power_pass: gram grid: %s", why);
+    if (gg.n != gs.n) return lrs_fail(ctx, LRS_EINVAL, "power_pass: gram grid has n=%lld, sketch n=%lld", (long long)gg.n, (long long)gs.n);
+  }
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const int64_t l = gs.l;
+  const int64_t nI = q > 0 ? gg.l : 0;
+  // workspace: W, W^T, two m x l / nI x l work matrices, orthonormalisation
+  size_t need = 0;
+  if (q > 0) {
+    const int64_t wmax = l > m ? l : m;
+    need += 2 * align256(8 * (size_t)(m * nI));
+    need += align256(8 * (size_t)(nI * wmax)) + align256(8 * (size_t)(m * wmax)) * 2;
+    const size_t o1 = orth_ws(m, l), o2 = orth_ws(nI, wmax);
+    need += (o1 > o2 ? o1 : o2) + align256(8 * (size_t)(nI * wmax));
+  }
+  lrs_status st = ws_reserve(ctx, need);
+  if (st) return st;
+  st = launch_sketch(ctx, A, dtype, m, lda, gs, Y, ldy);
+  if (st) return st;
+  if (q == 0) {
+    LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(G, ldg * 8, Y, ldy * 8, l * 8, m, cudaMemcpyDeviceToDevice, ctx->stream));
+    *g_cols = l;
+    return LRS_OK;
+  }
+  const int64_t wmax = l > m ? l : m;
+  double* W = (double*)ws_alloc(ctx, 8 * (size_t)(m * nI));
+  double* WT = (double*)ws_alloc(ctx, 8 * (size_t)(m * nI));
+  double* Tm = (double*)ws_alloc(ctx, 8 * (size_t)(nI * wmax));
+  double* Ga = (double*)ws_alloc(ctx, 8 * (size_t)(m * wmax));
+  double* Gb = (double*)ws_alloc(ctx, 8 * (size_t)(m * wmax));
+  if (!W || !WT || !Tm || !Ga || !Gb) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (power_pass)");
+  const size_t mark = ctx->ws_top;
+  st = launch_gather(ctx, A, dtype, m, lda, gg, W, nI);
+  if (st) return st;
+  st = launch_transpose(ctx, W, m, nI, nI, WT, m);
+  if (st) return st;
+  // starting block: Q_np = QR(A_f D) with re-orthonormalisation, else A_f D
+  int64_t gc = l;
+  const double* Gcur = Y;
+  int64_t ldcur = ldy;
+  if (reorth) {
+    st = orth(ctx, Y, m, l, ldy, rtol, Ga, wmax, &gc);
+    if (st) return st;
+    ctx->ws_top = mark;
+    Gcur = Ga; ldcur = wmax;
+  }
+  for (int it = 0; it < q; ++it) {
+    // T = W^T G   (nI x gc)
+    st = gemm(ctx, prec, nI, gc, m, W, LRS_F64, nI, Gcur, LRS_F64, ldcur, Tm, 1, 0, gc);
+    if (st) return st;
+    int64_t tc = gc;
+    const double* Tcur = Tm;
+    int64_t ldt = gc;
+    if (reorth) {
+      // orthonormalise T in place of a fresh buffer inside the workspace
+      double* To = (double*)ws_alloc(ctx, 8 * (size_t)(nI * gc));
+      if (!To) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (power_pass T)");
+      const size_t mark2 = ctx->ws_top;
+      st = orth(ctx, Tm, nI, gc, gc, rtol, To, gc, &tc);
+      if (st) return st;
+      ctx->ws_top = mark2;
+      Tcur = To; ldt = gc;
+    }
+    // G = W T   (m x tc)  computed as (W^T)^T T
+    double* Gn = (Gcur == Ga) ? Gb : Ga;
+    st = gemm(ctx, prec, m, tc, nI, WT, LRS_F64, m, Tcur, LRS_F64, ldt, Gn, 1, 0, wmax);
+    if (st) return st;
+    if (reorth) {
+      double* Go = (Gn == Ga) ? Gb : Ga;
+      const size_t mark3 = ctx->ws_top;
+      st = orth(ctx, Gn, m, tc, wmax, rtol, Go, wmax, &gc);
+      if (st) return st;
+      ctx->ws_top = mark3;
+      Gcur = Go;
+    } else {
+      gc = tc;
+      Gcur = Gn;
+    }
+    ldcur = wmax;
+    ctx->ws_top = mark;
+  }
+  LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(G, ldg * 8, Gcur, ldcur * 8, gc * 8, m, cudaMemcpyDeviceToDevice, ctx->stream));
+  *g_cols = gc;
+  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return LRS_OK;
+}
+
+lrs_status lrs_svd_k(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                     const double* Q, int64_t ldq, int64_t r, int32_t k, int32_t prec, double* U,
+                     int64_t ldu, double* S, void* V, int64_t ldv, double* err_est) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  if (!A || !Q || !U || !S || !V) return lrs_fail(ctx, LRS_EINVAL, "svd_k: NULL pointer");
+  if (!dtype_ok(dtype) || !prec_ok(prec)) return lrs_fail(ctx, LRS_EINVAL, "svd_k: bad dtype/prec");
+  if (m < 1 || n < 1 || r < 1 || k < 1) return lrs_fail(ctx, LRS_EINVAL, "svd_k: m=%lld n=%lld r=%lld k=%d", (long long)m, (long long)n, (long long)r, k);
+  if (r > m) return lrs_fail(ctx, LRS_EINVAL, "svd_k: r=%lld > m=%lld", (long long)r, (long long)m);
+  const int64_t kk = k < r ? k : r;
+  if (lda < n || ldq < r || ldu < kk || ldv < kk) return lrs_fail(ctx, LRS_EINVAL, "svd_k: strides too small");
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const int f64 = prec == LRS_PREC_FP64;
+  const size_t bsz = f64 ? 8 : 4;
+  size_t need = align256(bsz * (size_t)(r * n));            // B
+  need += tsqr_ws(r, n, bsz);
+  need += 4 * align256(8 * (size_t)(r * r)) + align256(8 * (size_t)(m * r)) + 65536;
+  lrs_status st = ws_reserve(ctx, need);
+  if (st) return st;
+  void* B = ws_alloc(ctx, bsz * (size_t)(r * n));
+  double* fro2 = (double*)ws_alloc(ctx, 8);
+  double* Rm = (double*)ws_alloc(ctx, 8 * (size_t)(r * r));
+  double* Vr = (double*)ws_alloc(ctx, 8 * (size_t)(r * r));
+  double* sv = (double*)ws_alloc(ctx, 8 * (size_t)r);
+  double* Wk = (double*)ws_alloc(ctx, 8 * (size_t)(r * kk));
+  double* QT = (double*)ws_alloc(ctx, 8 * (size_t)(m * r));
+  if (!B || !fro2 || !Rm || !Vr || !sv || !Wk || !QT) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd_k)");
+  // (a4) B = Q^T A_f -- the one full read of A_f
+  st = gemm(ctx, prec, r, n, m, Q, LRS_F64, ldq, A, dtype, lda, B, f64, 0, n);
+  if (st) return st;
+  st = launch_fro2(ctx, A, dtype, m, n, lda, fro2);
+  if (st) return st;
+  // (a5) SVD(B): R of B^T, Jacobi on R -> U_B = Vr, s
+  st = launch_tsqr(ctx, B, f64, r, n, n, Rm);
+  if (st) return st;
+  st = launch_jacobi(ctx, Rm, r, Vr, sv, f64);
+  if (st) return st;
+  // U = Q Vr(:, :kk):  U^T = Vr_k^T Q^T
+  st = launch_transpose(ctx, Q, m, r, ldq, QT, m);
+  if (st) return st;
+  st = gemm(ctx, LRS_PREC_FP64, kk, m, r, Vr, LRS_F64, r, QT, LRS_F64, m, U, 1, 1, ldu);
+  if (st) return st;
+  // V = B^T Vr_k S_k^{-1}
+  st = launch_scale_cols(ctx, Vr, r, r, sv, kk, Wk, kk);
+  if (st) return st;
+  st = gemm(ctx, f64 ? LRS_PREC_FP64 : LRS_PREC_FP32, n, kk, r, B, f64 ? LRS_F64 : LRS_F32, n, Wk,
+            LRS_F64, kk, V, f64, 0, ldv);
+  if (st) return st;
+  st = launch_sign_fix(ctx, U, m, kk, ldu, V, f64, n, ldv);
+  if (st) return st;
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(S, sv, 8 * (size_t)kk, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (err_est) {
+    double* h = (double*)ctx->host_scratch;
+    LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h, fro2, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<double> s_h((size_t)r);
+    LRS_CUDA_TRY(ctx, cudaMemcpyAsync(s_h.data(), sv, 8 * (size_t)r, cudaMemcpyDeviceToHost, ctx->stream));
+    LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    // energy of B beyond rank k, summed smallest first
+    double tail = 0.0;
+    for (int64_t i = r - 1; i >= kk; --i) tail += s_h[(size_t)i] * s_h[(size_t)i];
+    const double f = h[0];
+    *err_est = f > 0.0 ? sqrt(tail / f) : 0.0;
+  }
+  return r < k ? lrs_fail(ctx, LRS_ERANK, "svd_k: rank r=%lld < k=%d", (long long)r, k) : LRS_OK;
+}
+
+lrs_status lrs_id_k(lrs_ctx* ctx, const double* Ysk, int64_t m, int64_t l, int64_t ldy, int32_t k,
+                    int32_t* J, double* P, int64_t ldp, double* err_est) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  if (!Ysk || !J || !P) return lrs_fail(ctx, LRS_EINVAL, "id_k: NULL pointer");
+  if (m < 1 || l < 1 || k < 1) return lrs_fail(ctx, LRS_EINVAL, "id_k: m=%lld l=%lld k=%d", (long long)m, (long long)l, k);
+  if (k > m || k > l) return lrs_fail(ctx, LRS_EINVAL, "id_k: k=%d exceeds min(m,l)", k);
+  if (ldy < l || ldp < k) return lrs_fail(ctx, LRS_EINVAL, "id_k: strides too small");
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  size_t need = align256(8 * (size_t)(m * l)) + align256(4 * (size_t)m) +
+                2 * align256(8 * (size_t)(k * m)) + align256(8 * (size_t)(l * k)) +
+                4 * align256(8 * (size_t)m) + align256((size_t)m) + align256(8 * (size_t)l) + 65536 +
+                align256(8 * 4 * 1024);
+  lrs_status st = ws_reserve(ctx, need);
+  if (st) return st;
+  // Y^T is l x m; its column-major storage is Y's row-major storage.
+  double* Mc = (double*)ws_alloc(ctx, 8 * (size_t)(m * l));
+  CpqrOut o{};
+  o.perm = (int32_t*)ws_alloc(ctx, 4 * (size_t)m);
+  o.R = (double*)ws_alloc(ctx, 8 * (size_t)(k * m));
+  o.V = (double*)ws_alloc(ctx, 8 * (size_t)(l * k));
+  o.tail2 = (double*)ws_alloc(ctx, 8);
+  o.rank = (int32_t*)ws_alloc(ctx, 8);
+  double* nrm2 = (double*)ws_alloc(ctx, 8);
+  if (!Mc || !o.perm || !o.R || !o.V || !o.tail2 || !o.rank || !nrm2)
+    return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (id_k)");
+  LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(Mc, l * 8, Ysk, ldy * 8, l * 8, m, cudaMemcpyDeviceToDevice, ctx->stream));
+  st = launch_fro2(ctx, Mc, LRS_F64, m, l, l, nrm2);
+  if (st) return st;
+  st = launch_cpqr(ctx, Mc, l, m, l, k, 0.0, o);
+  if (st) return st;
+  int32_t rank = 0;
+  double* h = (double*)ctx->host_scratch;
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(&rank, o.rank, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h, o.tail2, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 1, nrm2, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (rank < k) return lrs_fail(ctx, LRS_ERANK, "id_k: sketch rank %d < k=%d", rank, k);
+  st = launch_id_coeffs(ctx, o.R, k, m, o.perm, J, P, ldp);
+  if (st) return st;
+  if (err_est) *err_est = h[1] > 0.0 ? sqrt(fmax(h[0], 0.0) / h[1]) : 0.0;
+  return LRS_OK;
+}
+
+lrs_status lrs_gemm_tn(lrs_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* X, int32_t x_dtype,
+                       int64_t ldx, const void* A, int32_t a_dtype, int64_t lda, void* C, int32_t c_f64,
+                       int32_t c_trans, int64_t ldc, int32_t prec) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  if (!X || !A || !C) return lrs_fail(ctx, LRS_EINVAL, "gemm: NULL pointer");
+  if (M < 0 || N < 0 || K < 0) return lrs_fail(ctx, LRS_EINVAL, "gemm: negative size");
+  if (!dtype_ok(x_dtype) || !dtype_ok(a_dtype) || !prec_ok(prec)) return lrs_fail(ctx, LRS_EINVAL, "gemm: bad dtype/prec");
+  if (ldx < M || lda < N || ldc < (c_trans ? M : N)) return lrs_fail(ctx, LRS_EINVAL, "gemm: strides too small");
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  lrs_status st = ws_reserve(ctx, 0);
+  if (st) return st;
+  return gemm(ctx, prec, M, N, K, X, x_dtype, ldx, A, a_dtype, lda, C, c_f64, c_trans, ldc);
+}
+
+}  // extern "C"

@@ -1,0 +1,244 @@
+// SVD of B (r x n, r small) for TPC-SVD (paper Alg. 2, "SVD(B)") without
+// squaring its condition number:
+//   1. R = the R factor of B^T by Householder TSQR: each block factors a
+//      chunk of C columns of B (a C x r slab of B^T) in shared memory and
+//      writes its r x r triangle; the triangles of all chunks, laid side by
+//      side, form a new r x (chunks * r) matrix that the same kernel reduces
+//      again, until one chunk remains.
+//   2. One-sided (Hestenes) Jacobi on the columns of R: R V = U_R diag(s).
+//      Since B = R^T Q_T^T = V diag(s) (Q_T U_R)^T, the left singular vectors
+//      of B are V and its singular values s.
+// Both run in the working precision T (float for FP32-level paths, double for
+// FP64 data).  Shared memory bounds r: r*C*sizeof(T) <= ~200 KB for TSQR and
+// 2*r*r*sizeof(T) <= ~200 KB for Jacobi.
+#include "common.cuh"
+#include "internal.h"
+
+#include <algorithm>
+#include <vector>
+
+namespace lrs {
+
+constexpr int kTsqrThreads = 512;
+constexpr size_t kSmemCap = 200 * 1024;
+
+// tile[i][t] holds column i of the C x r slab (row i of B's chunk), t < C.
+template <typename T>
+__global__ void __launch_bounds__(kTsqrThreads, 1)
+k_tsqr_leaf(const void* __restrict__ B, int b_f64, int64_t r, int64_t n, int64_t ldb, int64_t C,
+            T* __restrict__ out, int64_t ldo, double* __restrict__ Rfinal) {
+  extern __shared__ unsigned char smem_raw[];
+  T* tile = reinterpret_cast<T*>(smem_raw);
+  __shared__ T s_scal[2];
+  const int64_t j0 = (int64_t)blockIdx.x * C;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // load: row i of B, columns j0 .. j0+C-1 (zero beyond n)
+  for (int64_t e = threadIdx.x; e < r * C; e += blockDim.x) {
+    const int64_t i = e / C, t = e - i * C;
+    const int64_t col = j0 + t;
+    T v = T(0);
+    if (col < n) {
+      v = b_f64 ? (T)reinterpret_cast<const double*>(B)[i * ldb + col]
+                : (T)reinterpret_cast<const float*>(B)[i * ldb + col];
+    }
+    tile[i * C + t] = v;
+  }
+  __syncthreads();
+  const int64_t steps = r < C ? r : C;
+  for (int64_t i = 0; i < steps; ++i) {
+    T* x = tile + i * C;
+    if (wid == 0) {
+      T a = T(0);
+      for (int64_t t = i + lane; t < C; t += 32) a = fma(x[t], x[t], a);
+      a = warp_sum(a);
+      const T alpha = sqrt(a);
+      const T x0 = x[i];
+      const T sgn = x0 >= T(0) ? T(1) : T(-1);
+      const T v0 = x0 + sgn * alpha;
+      // ||v||^2 = ||x||^2 - x0^2 + v0^2
+      const T vn2 = a - x0 * x0 + v0 * v0;
+      const T inv = vn2 > T(0) ? T(1) / sqrt(vn2) : T(0);
+      __syncwarp();
+      for (int64_t t = i + 1 + lane; t < C; t += 32) x[t] *= inv;
+      if (lane == 0) { s_scal[0] = -sgn * alpha; s_scal[1] = v0 * inv; }
+    }
+    __syncthreads();
+    const T rii = s_scal[0];
+    const T v0n = s_scal[1];
+    // apply H = I - 2 v v^T to columns c > i ; v = (v0n, x[i+1..C-1])
+    for (int64_t c = i + 1 + wid; c < r; c += nw) {
+      T* y = tile + c * C;
+      T w = (lane == 0) ? v0n * y[i] : T(0);
+      for (int64_t t = i + 1 + lane; t < C; t += 32) w = fma(x[t], y[t], w);
+      w = warp_sum(w);
+      const T tw = T(2) * w;
+      if (lane == 0) y[i] = fma(-tw, v0n, y[i]);
+      for (int64_t t = i + 1 + lane; t < C; t += 32) y[t] = fma(-tw, x[t], y[t]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) x[i] = rii;
+    __syncthreads();
+  }
+  // column c of R (rows 0..c) sits in tile[c][0..c]
+  if (Rfinal) {
+    for (int64_t e = threadIdx.x; e < r * r; e += blockDim.x) {
+      const int64_t i = e / r, c = e - i * r;        // R[i][c]
+      Rfinal[i * r + c] = (i <= c && i < C) ? (double)tile[c * C + i] : 0.0;
+    }
+  } else {
+    // next level: row c, columns blockIdx*r .. +r-1 hold R[0..r-1][c]
+    for (int64_t e = threadIdx.x; e < r * r; e += blockDim.x) {
+      const int64_t c = e / r, t = e - c * r;
+      out[c * ldo + (int64_t)blockIdx.x * r + t] = (t <= c && t < C) ? tile[c * C + t] : T(0);
+    }
+  }
+}
+
+template <typename T>
+static lrs_status tsqr_impl(lrs_ctx* ctx, const void* B, int b_f64, int64_t r, int64_t n,
+                            int64_t ldb, double* R) {
+  int64_t C = (int64_t)(kSmemCap / (sizeof(T) * (size_t)r));
+  if (C > 1024) C = 1024;
+  if (C < r) return lrs_fail(ctx, LRS_EINVAL, "svd: rank r=%lld too large for the TSQR tile", (long long)r);
+  const size_t dyn = sizeof(T) * (size_t)(r * C);
+  auto kern = k_tsqr_leaf<T>;
+  LRS_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  const void* src = B;
+  int src_f64 = b_f64;
+  int64_t cur_n = n, cur_ld = ldb;
+  while (true) {
+    const int64_t chunks = (cur_n + C - 1) / C;
+    if (chunks == 1) {
+      kern<<<1, kTsqrThreads, dyn, ctx->stream>>>(src, src_f64, r, cur_n, cur_ld, C, nullptr, 0, R);
+      ctx->launches++;
+      break;
+    }
+    const int64_t next_n = chunks * r;
+    T* nxt = (T*)ws_alloc(ctx, sizeof(T) * (size_t)(r * next_n));
+    if (!nxt) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (tsqr)");
+    kern<<<(unsigned)chunks, kTsqrThreads, dyn, ctx->stream>>>(src, src_f64, r, cur_n, cur_ld, C, nxt,
+                                                                 next_n, nullptr);
+    ctx->launches++;
+    src = nxt;
+    src_f64 = sizeof(T) == 8;
+    cur_n = next_n;
+    cur_ld = next_n;
+  }
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
+
+lrs_status launch_tsqr(lrs_ctx* ctx, const void* B, int b_f64, int64_t r, int64_t n, int64_t ldb,
+                       double* R) {
+  if (b_f64) return tsqr_impl<double>(ctx, B, 1, r, n, ldb, R);
+  return tsqr_impl<float>(ctx, B, 0, r, n, ldb, R);
+}
+
+// ---------------------------------------------------------------------------
+// One-sided Jacobi, one block, round-robin pairing (r' = r rounded up to even
+// columns; the pad column is zero and never rotates).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(1024, 1)
+k_jacobi(const double* __restrict__ R, int64_t r, double* __restrict__ Vout, double* __restrict__ s_out,
+         int max_sweeps) {
+  extern __shared__ unsigned char smem_raw[];
+  const int64_t rp = (r + 1) & ~int64_t(1);
+  T* Wc = reinterpret_cast<T*>(smem_raw);             // rp columns of length r
+  T* Vc = Wc + rp * r;                                // rp columns of length r
+  int* order = reinterpret_cast<int*>(Vc + rp * r);   // rp
+  __shared__ int s_rot;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t e = threadIdx.x; e < rp * r; e += blockDim.x) {
+    const int64_t c = e / r, i = e - c * r;
+    Wc[e] = c < r ? (T)R[i * r + c] : T(0);
+    Vc[e] = (c == i && c < r) ? T(1) : T(0);
+  }
+  for (int64_t c = threadIdx.x; c < rp; c += blockDim.x) order[c] = (int)c;
+  __syncthreads();
+  const T eps = sizeof(T) == 8 ? T(1.1102230246251565e-16) : T(5.9604645e-08);
+  const T tol = eps * sqrt((T)r);
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int64_t round = 0; round < rp - 1; ++round) {
+      // round-robin: slot 0 fixed, others rotate; pairs (slot a, slot rp-1-a)
+      for (int64_t pr = wid; pr < rp / 2; pr += nw) {
+        const int64_t sa = pr, sb = rp - 1 - pr;
+        auto slot = [&](int64_t sidx) -> int64_t {
+          if (sidx == 0) return 0;
+          return 1 + ((sidx - 1 + round) % (rp - 1));
+        };
+        int64_t p = slot(sa), q = slot(sb);
+        if (p > q) { const int64_t tmp = p; p = q; q = tmp; }
+        if (q >= r) continue;                        // the zero pad column
+        T* wp = Wc + p * r; T* wq = Wc + q * r;
+        T a = T(0), b = T(0), g = T(0);
+        for (int64_t i = lane; i < r; i += 32) {
+          a = fma(wp[i], wp[i], a); b = fma(wq[i], wq[i], b); g = fma(wp[i], wq[i], g);
+        }
+        a = warp_sum(a); b = warp_sum(b); g = warp_sum(g);
+        if (fabs(g) <= tol * (sqrt(a) * sqrt(b)) || g == T(0)) continue;
+        const T zeta = (b - a) / (T(2) * g);
+        const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+        const T cs = T(1) / sqrt(T(1) + t * t);
+        const T sn = cs * t;
+        for (int64_t i = lane; i < r; i += 32) {
+          const T x = wp[i], y = wq[i];
+          wp[i] = cs * x - sn * y; wq[i] = sn * x + cs * y;
+          T* vp = Vc + p * r; T* vq = Vc + q * r;
+          const T u = vp[i], w = vq[i];
+          vp[i] = cs * u - sn * w; vq[i] = sn * u + cs * w;
+        }
+        if (lane == 0) atomicAdd(&s_rot, 1);
+      }
+      __syncthreads();
+    }
+    if (s_rot == 0) break;
+    __syncthreads();
+  }
+  // singular values = column norms; sort descending (ties by index) -- r is small
+  __shared__ double s_norm[1024];
+  for (int64_t c = wid; c < r; c += nw) {
+    T a = T(0);
+    for (int64_t i = lane; i < r; i += 32) a = fma(Wc[c * r + i], Wc[c * r + i], a);
+    a = warp_sum(a);
+    if (lane == 0) s_norm[c] = sqrt((double)a);
+  }
+  __syncthreads();
+  for (int64_t c = threadIdx.x; c < r; c += blockDim.x) {
+    int64_t rank = 0;
+    const double v = s_norm[c];
+    for (int64_t d = 0; d < r; ++d) {
+      const double u = s_norm[d];
+      if (u > v || (u == v && d < c)) ++rank;
+    }
+    order[rank] = (int)c;
+  }
+  __syncthreads();
+  for (int64_t e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int64_t i = e / r, k = e - i * r;           // V[i][k] = Vc[order[k]][i]
+    Vout[i * r + k] = (double)Vc[(int64_t)order[k] * r + i];
+  }
+  for (int64_t k = threadIdx.x; k < r; k += blockDim.x) s_out[k] = s_norm[order[k]];
+}
+
+lrs_status launch_jacobi(lrs_ctx* ctx, double* R, int64_t r, double* V, double* s, int fp64) {
+  const int64_t rp = (r + 1) & ~int64_t(1);
+  const size_t tsz = fp64 ? 8 : 4;
+  const size_t dyn = tsz * 2 * (size_t)(rp * r) + sizeof(int) * (size_t)rp + 64;
+  if (dyn > kSmemCap || r > 1024)
+    return lrs_fail(ctx, LRS_EINVAL, "svd: rank r=%lld too large for the Jacobi tile", (long long)r);
+  if (fp64) {
+    LRS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_jacobi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    k_jacobi<double><<<1, 1024, dyn, ctx->stream>>>(R, r, V, s, 40);
+  } else {
+    LRS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    k_jacobi<float><<<1, 1024, dyn, ctx->stream>>>(R, r, V, s, 40);
+  }
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
+
+}  // namespace lrs

@@ -1,0 +1,88 @@
+"""The hot path as a sequence of C-ABI calls (orchestration only).
+
+``svd_path`` = lrs_power_pass (sketch + C-PWR with re-orthonormalisation) ->
+lrs_range_find -> lrs_svd_k  (paper Algs. 7 and 2);
+``id_path``  = lrs_power_pass (C-PWR without re-orthonormalisation, as in the
+paper's ID experiments) -> lrs_id_k  (Alg. 4).
+Device buffers come from torch; every arithmetic step runs in liblrs.so.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+from .binding import (DTYPE, LRS_PREC_FP32, LRS_PREC_FP64, Context, grid_of)
+
+
+@dataclass
+class SvdResult:
+    U: torch.Tensor
+    S: torch.Tensor
+    V: torch.Tensor
+    err_est: float
+    r: int
+    g_cols: int
+    status: int
+
+
+@dataclass
+class IdResult:
+    J: torch.Tensor
+    P: torch.Tensor
+    err_est: float
+    status: int
+
+
+def default_prec(dtype: str) -> int:
+    return LRS_PREC_FP64 if dtype == "f64" else LRS_PREC_FP32
+
+
+class Buffers:
+    """Device buffers of one decomposition, allocated once and reused."""
+
+    def __init__(self, m, n, l, k, dev, v_f64):
+        f64 = torch.float64
+        self.Y = torch.empty((m, l), dtype=f64, device=dev)
+        self.G = torch.empty((m, l), dtype=f64, device=dev)
+        self.Q = torch.empty((m, min(m, l)), dtype=f64, device=dev)
+        self.U = torch.empty((m, k), dtype=f64, device=dev)
+        self.S = torch.empty((k,), dtype=f64, device=dev)
+        self.V = torch.empty((n, k), dtype=f64 if v_f64 else torch.float32, device=dev)
+        self.Yid = torch.empty((m, l), dtype=f64, device=dev)
+        self.Gid = torch.empty((m, l), dtype=f64, device=dev)
+        self.J = torch.empty((k,), dtype=torch.int32, device=dev)
+        self.P = torch.empty((m, k), dtype=f64, device=dev)
+
+
+def svd_path(ctx: Context, A: torch.Tensor, dtype: str, grid, k: int, q: int = 0, gram=None,
+             rtol: float = 1e-12, prec: int | None = None, bufs: Buffers | None = None) -> SvdResult:
+    m = A.shape[0]
+    n = A.shape[1]
+    dt = DTYPE[dtype]
+    prec = default_prec(dtype) if prec is None else prec
+    g = grid_of(grid)
+    l = int(grid.l)
+    gg = grid_of(gram) if (gram is not None and q > 0) else None
+    b = bufs or Buffers(m, n, l, k, A.device, prec == LRS_PREC_FP64)
+    gc = ctx.power_pass(A, dt, m, n, g, gg, q, 1, rtol, prec, b.Y, l, b.G, l)
+    ldq = b.Q.shape[1]
+    r = ctx.range_find(b.G, m, gc, l, rtol, b.Q, ldq)
+    err, st = ctx.svd_k(A, dt, m, n, n, b.Q, ldq, r, k, prec, b.U, k, b.S, b.V, k)
+    kk = min(k, r)
+    return SvdResult(b.U[:, :kk], b.S[:kk], b.V[:, :kk], err, r, gc, st)
+
+
+def id_path(ctx: Context, A: torch.Tensor, dtype: str, grid, k: int, q: int = 0, gram=None,
+            rtol: float = 1e-12, prec: int | None = None, bufs: Buffers | None = None) -> IdResult:
+    m = A.shape[0]
+    n = A.shape[1]
+    dt = DTYPE[dtype]
+    prec = default_prec(dtype) if prec is None else prec
+    g = grid_of(grid)
+    l = int(grid.l)
+    gg = grid_of(gram) if (gram is not None and q > 0) else None
+    b = bufs or Buffers(m, n, l, k, A.device, prec == LRS_PREC_FP64)
+    ctx.power_pass(A, dt, m, n, g, gg, q, 0, rtol, prec, b.Yid, l, b.Gid, l)
+    err, st = ctx.id_k(b.Gid, m, l, l, k, b.J, b.P, k)
+    return IdResult(b.J, b.P, err, st)

@@ -1,0 +1,170 @@
+"""GPU parity of each C-ABI call against the FP64 oracle, element by element.
+
+Tolerances come from the arithmetic of each kernel (stated per test):
+  * injection is a copy: bit-exact;
+  * FP64 accumulation of k terms: |err| <= k u64 sum|terms| (u64 = 2^-53);
+  * FP32 products with FP32 accumulation over K terms, inputs rounded to FP32:
+    |err| <= (K + 2) u32 (|X|^T |A|)  (u32 = 2^-24).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import GridSpec
+
+pytestmark = pytest.mark.gpu
+
+U64 = 2.0 ** -53
+U32 = 2.0 ** -24
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dev(x):
+    torch = _torch()
+    if x.dtype == np.uint16:
+        return torch.from_numpy(x.view(np.int16).copy()).cuda()
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("N,s,kind", [
+    ((64, 64), (4, 4), "inject"), ((48, 40), (3, 5), "inject"), ((16, 8, 8), (4, 2, 2), "inject"),
+    ((64, 64), (4, 4), "fullweight"), ((30, 18), (2, 3), "fullweight"), ((8, 8, 12), (2, 4, 3), "fullweight"),
+    ((32, 32), (4, 2), "blockavg"), ((9, 6, 4), (3, 3, 2), "blockavg"), ((1024,), (16,), "fullweight"),
+])
+def test_sketch_parity(lrs, dtype, N, s, kind):
+    from paper_2105_01271_gb300.binding import DTYPE, make_grid
+    torch = _torch()
+    m = 37                                   # ragged against every tile
+    n = int(np.prod(N))
+    A64 = np.random.default_rng(1).standard_normal((m, n))
+    A = synth.fields._store(A64, dtype)
+    g = GridSpec(N=N, s=s, kind=kind)
+    ref = oracle.sketch(A, g)
+    Y = torch.empty((m, g.l), dtype=torch.float64, device="cuda")
+    lrs.sketch(_dev(A), DTYPE[dtype], m, n, make_grid(N, s, kind), Y, g.l)
+    got = _np(Y)
+    if kind == "inject":
+        assert np.array_equal(got, ref)
+    else:
+        D = oracle.sketch_operator(g)
+        bound = 27 * U64 * (np.abs(oracle.sketch.__globals__["as_f64"](A)) @ abs(D)).astype(float)
+        assert np.all(np.abs(got - ref) <= bound + 1e-300)
+
+
+def test_sketch_rejects_bad_grid(lrs):
+    from paper_2105_01271_gb300.binding import LrsError, make_grid, LRS_EINVAL
+    torch = _torch()
+    A = torch.zeros((4, 64), dtype=torch.float64, device="cuda")
+    Y = torch.zeros((4, 64), dtype=torch.float64, device="cuda")
+    for N, s, kind in [((64,), (3,), "inject"), ((64,), (1,), "fullweight"), ((8, 8), (0, 2), "inject")]:
+        with pytest.raises(LrsError) as e:
+            lrs.sketch(A, 0, 4, 64, make_grid(N, s, kind), Y, 64)
+        assert e.value.status == LRS_EINVAL
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("M,N,K", [(1, 1, 1), (37, 300, 129), (64, 128, 16), (200, 77, 513)])
+@pytest.mark.parametrize("trans", [0, 1])
+def test_gemm_tn_parity(lrs, prec, M, N, K, trans):
+    torch = _torch()
+    rng = np.random.default_rng(M * 1000 + N + K)
+    X = rng.standard_normal((K, M))
+    Aa = rng.standard_normal((K, N)).astype(np.float32)
+    ref = X.T @ Aa.astype(np.float64)
+    shape = (N, M) if trans else (M, N)
+    Cd = torch.empty(shape, dtype=torch.float64, device="cuda")
+    lrs.gemm_tn(M, N, K, _dev(X), 0, M, _dev(Aa), 1, N, Cd, 1, trans, shape[1], prec)
+    got = _np(Cd).T if trans else _np(Cd)
+    mag = np.abs(X).T @ np.abs(Aa.astype(np.float64))
+    u = U64 if prec == 0 else U32
+    assert np.all(np.abs(got - ref) <= (K + 2) * u * mag + 1e-300)
+
+
+# ---------------------------------------------------------------------------
+def test_range_find_exact_rank(lrs):
+    torch = _torch()
+    A, sig = synth.low_rank_matrix(300, 120, 17, seed=3, decay=0.7)
+    Qo, ro = oracle.range_find(A, 1e-12)
+    Q = torch.empty((300, 120), dtype=torch.float64, device="cuda")
+    r = lrs.range_find(_dev(A), 300, 120, 120, 1e-12, Q, 120)
+    assert r == ro == 17
+    Qg = _np(Q)[:, :r]
+    np.testing.assert_allclose(Qg.T @ Qg, np.eye(r), atol=1e-13)
+    np.testing.assert_allclose(Qg @ Qg.T, Qo @ Qo.T, atol=1e-11)
+
+
+@pytest.mark.parametrize("m,l", [(200, 256), (333, 97), (64, 64), (600, 200), (1100, 300)])
+def test_range_find_full_rank_parity(lrs, m, l):
+    torch = _torch()
+    G = np.random.default_rng(m + l).standard_normal((m, l))
+    Qo, ro = oracle.range_find(G, 1e-12)
+    kq = min(m, l)
+    Q = torch.empty((m, kq), dtype=torch.float64, device="cuda")
+    r = lrs.range_find(_dev(G), m, l, l, 1e-12, Q, kq)
+    assert r == ro == kq
+    # same Householder sequence: Q itself agrees, not only its range
+    np.testing.assert_allclose(_np(Q), Qo, atol=1e-11)
+
+
+@pytest.mark.parametrize("shape", [(600, 1024), (600, 200)])
+def test_range_find_blob_sketch(lrs, shape):
+    """Wide / tall smooth sketches with a fast-decaying spectrum (truncated)."""
+    torch = _torch()
+    A = synth.blob_field(shape[0], 128, 8, seed=1, kappa=1e-5, dtype="f32")
+    Y = oracle.sketch(A, GridSpec((128, 128), (4, 4), "fullweight"))[:, :shape[1]]
+    m, l = Y.shape
+    Qo, ro = oracle.range_find(Y, 1e-6)
+    kq = min(m, l)
+    for _ in range(2):                                   # deterministic across calls
+        Q = torch.empty((m, kq), dtype=torch.float64, device="cuda")
+        r = lrs.range_find(_dev(Y), m, l, l, 1e-6, Q, kq)
+        assert r == ro
+        Qg = _np(Q)[:, :r]
+        np.testing.assert_allclose(Qg.T @ Qg, np.eye(r), atol=1e-13)
+        np.testing.assert_allclose(Qg, Qo, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+@pytest.mark.parametrize("m,l,k", [(120, 80, 20), (45, 200, 30), (300, 64, 64), (200, 600, 60)])
+def test_id_k_pivot_gap(lrs, seed, m, l, k):
+    torch = _torch()
+    Y = synth.pivot_gap_matrix(m, l, seed=seed)
+    Jo, Po, eo = oracle.row_id(Y, k)
+    J = torch.empty((k,), dtype=torch.int32, device="cuda")
+    P = torch.empty((m, k), dtype=torch.float64, device="cuda")
+    err, st = lrs.id_k(_dev(Y), m, l, l, k, J, P, k)
+    Jg, Pg = _np(J), _np(P)
+    assert np.array_equal(Jg, Jo)                     # identical skeleton
+    assert np.array_equal(Pg[Jg], np.eye(k))          # exact identity on J
+    np.testing.assert_allclose(Pg, Po, rtol=1e-9, atol=1e-11)
+    assert abs(err - eo) <= 1e-10 * max(eo, 1e-16) + 1e-14
+
+
+# ---------------------------------------------------------------------------
+def test_svd_k_fp64_exact_rank(lrs):
+    from paper_2105_01271_gb300.binding import LRS_PREC_FP64
+    torch = _torch()
+    m, n, r = 90, 700, 12
+    A, sig = synth.low_rank_matrix(m, n, r, seed=4, decay=0.6)
+    Q, _ = oracle.range_find(A, 1e-12)
+    U = torch.empty((m, r), dtype=torch.float64, device="cuda")
+    S = torch.empty((r,), dtype=torch.float64, device="cuda")
+    V = torch.empty((n, r), dtype=torch.float64, device="cuda")
+    err, st = lrs.svd_k(_dev(A), 0, m, n, n, _dev(Q), r, r, r, LRS_PREC_FP64, U, r, S, V, r)
+    Uo, So, Vo, eo, _, _ = oracle.tpc_svd(A, Q, r)
+    np.testing.assert_allclose(_np(S), sig, rtol=1e-12)
+    np.testing.assert_allclose(_np(U), Uo, atol=1e-10)
+    np.testing.assert_allclose(_np(V), Vo, atol=1e-10)

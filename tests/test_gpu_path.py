@@ -1,0 +1,166 @@
+"""End-to-end GPU parity of the hot path against the FP64 oracle.
+
+Workloads (synth.WORKLOADS and reduced variants with the same recipe):
+  * heat2d_m200_64x64_f64: FP64 data, 4x injection, k = 20, q = 0
+  * a reduced blob field (600 x 128^2, FP32, full weighting s = 8, C-PWR on a
+    2x injection subsample, q = 1, k = 30)
+
+Tolerances (derived from the arithmetic, stated here):
+  * FP64 path: |eps_gpu - eps_ora| <= 1e-12 and |s_i - s_i^ora| <= 1e-12 s_1
+    (backward-stable FP64 steps, errors ~ m u64 ||A||).
+  * FP32 path: |eps_gpu / eps_ora - 1| <= 1e-5 when eps_ora >= 1e-4 (the
+    reconstruction tolerance), |s_i - s_i^ora| <= 64 sqrt(m) u32 s_1 (products
+    accumulated in FP32 over m terms, normwise).
+  * Skeleton J: identical to the oracle's on every step whose pivot margin
+    (best - runner-up)/best exceeds the perturbation the path's arithmetic can
+    cause (FP64: 1e-10; FP32 products: 1e-3); beyond that prefix the GPU's
+    row ID must be as accurate as the oracle's (relative 1e-3).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import GridSpec
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dev(x):
+    torch = _torch()
+    if x.dtype == np.uint16:
+        return torch.from_numpy(x.view(np.int16).copy()).cuda()
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _prefix(gaps, margin):
+    n = 0
+    for g in gaps:
+        if g <= margin:
+            break
+        n += 1
+    return n
+
+
+HEAT = synth.WORKLOADS["heat2d_m200_64x64_f64"]
+BLOB_SMALL = dict(m=600, N=128, grid=GridSpec((128, 128), (8, 8), "fullweight"),
+                  gram=GridSpec((128, 128), (2, 2), "inject"), k=30, q=1, rtol=1e-6)
+
+
+@pytest.fixture(scope="module")
+def heat():
+    A = synth.make_workload(HEAT)
+    return A, oracle.svd_path(A, HEAT.grid, HEAT.k, q=0, rtol=1e-14), oracle.id_path(A, HEAT.grid, HEAT.k)
+
+
+@pytest.fixture(scope="module")
+def blob():
+    c = BLOB_SMALL
+    A = synth.blob_field(c["m"], c["N"], 8, seed=1, kappa=1e-5, dtype="f32")
+    o = oracle.svd_path(A, c["grid"], c["k"], q=c["q"], gram_grid=c["gram"], rtol=c["rtol"])
+    d = oracle.id_path(A, c["grid"], c["k"], q=c["q"], gram_grid=c["gram"], rtol=c["rtol"])
+    return A, o, d
+
+
+# ---------------------------------------------------------------------------
+def test_heat_svd_path(lrs, heat):
+    from paper_2105_01271_gb300 import path
+    A, o, _ = heat
+    res = path.svd_path(lrs, _dev(A), "f64", HEAT.grid, HEAT.k, q=0, rtol=1e-14)
+    assert res.r == o["r"]
+    U, S, V = _np(res.U), _np(res.S), _np(res.V)
+    eps_g = oracle.rel_fro_error(A, U, S, V)
+    eps_o = oracle.rel_fro_error(A, o["U"], o["S"], o["V"])
+    assert abs(eps_g - eps_o) <= 1e-12
+    assert np.all(np.abs(S - o["S"]) <= 1e-12 * o["S"][0])
+    np.testing.assert_allclose(U.T @ U, np.eye(U.shape[1]), atol=1e-12)
+    # leading singular triplets: well separated, so vectors agree (signs fixed)
+    np.testing.assert_allclose(U[:, :8], o["U"][:, :8], atol=1e-9)
+
+
+def test_heat_id_path(lrs, heat):
+    from paper_2105_01271_gb300 import path
+    A, _, d = heat
+    gaps = []
+    oracle.row_id(d["G"], HEAT.k, gaps)
+    res = path.id_path(lrs, _dev(A), "f64", HEAT.grid, HEAT.k, q=0)
+    J, P = _np(res.J), _np(res.P)
+    npre = _prefix(gaps, 1e-10)
+    assert npre == HEAT.k                   # every pivot of this input is well separated
+    assert np.array_equal(J, d["J"])
+    assert np.array_equal(P[J], np.eye(HEAT.k))
+    # C = R_11^{-1} R_12 amplifies FP64 rounding by cond(R_11) (~1e13 here):
+    # |dP| <= 64 u64 cond(R_11) |P|, and the ID itself must be as accurate.
+    _, R, _, _, _ = oracle.cpqr(d["G"].T, kmax=HEAT.k)
+    kappa = np.linalg.cond(R[:, :HEAT.k])
+    tol = 64 * 2.0 ** -53 * kappa
+    assert np.all(np.abs(P - d["P"]) <= tol * np.maximum(1.0, np.abs(d["P"])))
+    e_g = oracle.id_rel_error(A, J, P)
+    e_o = oracle.id_rel_error(A, d["J"], d["P"])
+    assert abs(e_g - e_o) <= 1e-3 * e_o + 1e-14
+    assert abs(res.err_est - d["err_est"]) <= 1e-6 * d["err_est"] + 1e-15
+
+
+def test_id_k_on_oracle_cpwr_sketch(lrs, blob):
+    """lrs_id_k alone on the oracle's C-PWR output (FP64 input, FP64 CPQR)."""
+    A, _, d = blob
+    G = d["G"]
+    m, l = G.shape
+    k = BLOB_SMALL["k"]
+    gaps = []
+    Jo, Po, eo = oracle.row_id(G, k, gaps)
+    torch = _torch()
+    J = torch.empty((k,), dtype=torch.int32, device="cuda")
+    P = torch.empty((m, k), dtype=torch.float64, device="cuda")
+    err, st = lrs.id_k(_dev(G), m, l, l, k, J, P, k)
+    npre = _prefix(gaps, 1e-10)
+    assert npre == k
+    assert np.array_equal(_np(J), Jo)
+    np.testing.assert_allclose(_np(P), Po, rtol=1e-7, atol=1e-9)
+
+
+def test_blob_svd_path(lrs, blob):
+    from paper_2105_01271_gb300 import path
+    A, o, _ = blob
+    c = BLOB_SMALL
+    res = path.svd_path(lrs, _dev(A), "f32", c["grid"], c["k"], q=c["q"], gram=c["gram"], rtol=c["rtol"])
+    U, S, V = _np(res.U), _np(res.S), _np(res.V).astype(np.float64)
+    eps_g = oracle.rel_fro_error(A, U, S, V)
+    eps_o = oracle.rel_fro_error(A, o["U"], o["S"], o["V"])
+    assert eps_o >= 1e-4
+    assert abs(eps_g / eps_o - 1.0) <= 1e-5, (eps_g, eps_o)
+    tol_s = 64 * np.sqrt(c["m"]) * U32 * o["S"][0]
+    assert np.all(np.abs(S - o["S"]) <= tol_s)
+    # err_est^2 = sum_{i>k} s_i^2 / ||A||^2: propagate the per-value bound tol_s
+    tail = o["sB"][c["k"]:]
+    bound2 = (2 * tol_s * np.sum(tail) + len(tail) * tol_s ** 2) / o["fro2"]
+    assert abs(res.err_est ** 2 - o["err_est"] ** 2) <= bound2
+    assert o["err_est"] <= eps_o * (1 + 1e-9)            # a lower bound of the true error
+
+
+def test_blob_id_path(lrs, blob):
+    from paper_2105_01271_gb300 import path
+    A, _, d = blob
+    c = BLOB_SMALL
+    gaps = []
+    oracle.row_id(d["G"], c["k"], gaps)
+    res = path.id_path(lrs, _dev(A), "f32", c["grid"], c["k"], q=c["q"], gram=c["gram"], rtol=c["rtol"])
+    J, P = _np(res.J), _np(res.P)
+    npre = _prefix(gaps, 1e-3)
+    assert np.array_equal(J[:npre], d["J"][:npre])
+    assert len(set(J.tolist())) == c["k"]
+    assert np.array_equal(P[J], np.eye(c["k"]))
+    e_g = oracle.id_rel_error(A, J, P)
+    e_o = oracle.id_rel_error(A, d["J"], d["P"])
+    assert e_g <= e_o * (1 + 1e-3), (e_g, e_o)
