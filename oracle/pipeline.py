@@ -23,7 +23,13 @@ def svd_path(A, grid, k: int, q: int = 0, gram_grid=None, rtol: float = 1e-12,
         G, _ = cpwr(Y, W, q, reorth, rtol)
     else:
         G = Y
-    Q, r = range_find(G, rtol)
+    if q > 0 and reorth:
+        # Alg. 7 with re-orthonormalisation ends with G_q <- QR(G_q): G_q already
+        # has orthonormal columns, and the QR of an orthonormal matrix returns
+        # its own range with no truncation (every |R_jj| = 1).
+        Q, r = G, G.shape[1]
+    else:
+        Q, r = range_find(G, rtol)
     U, S, V, err, s_all, fro2 = tpc_svd(A, Q, k)
     return dict(Y=Y, G=G, Q=Q, r=r, U=U, S=S, V=V, err_est=err, sB=s_all, fro2=fro2)
 
