@@ -239,10 +239,14 @@ def run_ours(args, rank, world):
         gc = ctx.power_pass(A_d, binding.DTYPE[w.dtype], w.m, w.n, binding.grid_of(w.grid), gg, w.q, 1,
                             rtol, prec, bufs.Y, w.grid.l, bufs.G, w.grid.l)
         evs[1].record(stream)
-        ldq = bufs.Q.shape[1]
-        r = ctx.range_find(bufs.G, w.m, gc, w.grid.l, rtol, bufs.Q, ldq)
+        if w.q > 0:
+            Qb, ldq, r = bufs.G, w.grid.l, gc
+        else:
+            ldq = bufs.Q.shape[1]
+            r = ctx.range_find(bufs.G, w.m, gc, w.grid.l, rtol, bufs.Q, ldq)
+            Qb = bufs.Q
         evs[2].record(stream)
-        ctx.svd_k(A_d, binding.DTYPE[w.dtype], w.m, w.n, w.n, bufs.Q, ldq, r, w.k, prec, bufs.U, w.k,
+        ctx.svd_k(A_d, binding.DTYPE[w.dtype], w.m, w.n, w.n, Qb, ldq, r, w.k, prec, bufs.U, w.k,
                   bufs.S, bufs.V, w.k)
         evs[3].record(stream)
         ctx.power_pass(A_d, binding.DTYPE[w.dtype], w.m, w.n, binding.grid_of(w.grid), gg, w.q, 0,
@@ -262,11 +266,11 @@ def run_ours(args, rank, world):
     reps = max(args.steps, 5)
     with torch.cuda.stream(stream):
         for _ in range(2):
-            ctx.gemm_tn(r, w.n, w.m, bufs.Q, 0, ldq, A_d, binding.DTYPE[w.dtype], w.n, Bbuf, bsz == 8, 0, w.n, prec)
+            ctx.gemm_tn(r, w.n, w.m, Qb, 0, ldq, A_d, binding.DTYPE[w.dtype], w.n, Bbuf, bsz == 8, 0, w.n, prec)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(reps):
-            ctx.gemm_tn(r, w.n, w.m, bufs.Q, 0, ldq, A_d, binding.DTYPE[w.dtype], w.n, Bbuf, bsz == 8, 0, w.n, prec)
+            ctx.gemm_tn(r, w.n, w.m, Qb, 0, ldq, A_d, binding.DTYPE[w.dtype], w.n, Bbuf, bsz == 8, 0, w.n, prec)
         e1.record(stream)
     stream.synchronize()
     apass_ms = e0.elapsed_time(e1) / reps

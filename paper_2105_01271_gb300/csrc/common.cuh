@@ -55,10 +55,12 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
 // Grid barrier with a bounded wait.
 //
 // Used only by kernels launched with cudaLaunchCooperativeKernel, which
-// guarantees that all blocks are co-resident.  Each wait gives up after
-// kSpinLimit polls (about a second with the back-off below), records
-// LRS_ETIMEOUT in *err and returns false; every block then leaves the kernel
-// at its next barrier check, so a lost arrival never hangs the GPU.
+// guarantees that all blocks are co-resident.  Thread 0 of each block reads
+// the generation, fences, counts itself in; the last arrival resets the count
+// and bumps the generation, the others poll the generation.  Each wait gives
+// up after kSpinLimit polls (about a second), records LRS_ETIMEOUT in *err
+// and returns false; every block then leaves the kernel at its next barrier,
+// so a lost arrival never hangs the GPU.
 // ---------------------------------------------------------------------------
 struct GridBarrier {
   unsigned int* count;   // arrivals in the current generation
@@ -90,9 +92,9 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& b) {
     } else {
       long long it = 0;
       while (ld_acquire_u32(b.gen) == g) {
-        if (ld_volatile_s32(b.err) != 0) break;
-        if (++it > kSpinLimit) { atomicCAS(b.err, 0, (int)LRS_ETIMEOUT); break; }
-        if (it > 64) __nanosleep(40);
+        if (((++it) & 63) == 0 && ld_volatile_s32(b.err) != 0) break;
+        if (it > kSpinLimit) { atomicCAS(b.err, 0, (int)LRS_ETIMEOUT); break; }
+        if (it > 256) __nanosleep(20);
       }
     }
     __threadfence();

@@ -8,47 +8,56 @@
 // lowest current position.  Reflector: R_jj = -sign(x_0) ||x||, v = x +
 // sign(x_0)||x|| e_1 normalised, H = I - 2 v v^T.
 //
-// One persistent cooperative launch runs all steps.  Each block owns a
-// contiguous range of physical columns; a step is
-//   (1) every block reduces the per-block best (norm^2, position) -> pivot,
-//   (2) the pivot's owner builds v, block 0 records the position swap,
-//       -- grid barrier --
-//   (3) every block applies H to its live columns, records row j of R and
-//       the new norms, and publishes its best candidate,
-//       -- grid barrier --
+// One persistent cooperative launch runs all steps.  The matrix is split by
+// ROWS: block b keeps rows [r_lo, r_hi) of every column (in shared memory
+// when the slab fits), so all SMs share the FP64 work whatever the aspect
+// ratio.  Column sums (norms^2, Householder dot products) are reduced across
+// blocks through per-block partials; block b owns the final sum of a
+// contiguous range of columns.  One step j:
+//   (F) every block updates its rows >= j of the live columns with the
+//       previous reflector, records row j-1 of R if it owns that row, writes
+//       partial norms^2 over rows >= j, and the owner of row j publishes row j
+//                                                          -- grid barrier --
+//   (N) column owners sum the norms^2 and their local best (norm^2, position)
+//                                                          -- grid barrier --
+//   (P) every block picks the pivot, forms its rows of v (needs only
+//       ||x||, x_0 and its own rows of x) and writes partial dots v^T M(:, c)
+//                                                          -- grid barrier --
+//   (D) column owners sum the dots                         -- grid barrier --
 // The barriers are bounded (common.cuh) and report LRS_ETIMEOUT.
 #include "common.cuh"
 #include "internal.h"
 
-#include <cooperative_groups.h>
-
 namespace lrs {
 
 struct CpqrState {
-  double* M; int64_t p, c, ldm;
+  double* M; int64_t p, c, ldm;          // column-major input (column j at M + j*ldm), read once
   int64_t kmax; double rtol;
   // outputs
   int32_t* perm; double* R; double* V; double* tail2; int32_t* rank;
   // scratch
-  double* norm2;        // c
-  int32_t* pos_of;      // c  (physical -> position)
-  int32_t* phys_at;     // c  (position -> physical)
-  uint8_t* done;        // c
+  double* slab_g;       // global per-block regions when shared memory is too small
+  double* part_n;       // nb x c partial norms^2
+  double* part_d;       // nb x c partial dot products
+  double* colsum;       // c: reduced sums (owner mode)
+  double* rowbuf;       // c: the current row j
   double* Rphys;        // kmax x c (row j, physical column)
-  double* best_val;     // nblocks
-  int32_t* best_pos;    // nblocks
-  int32_t* best_phys;   // nblocks
-  double* vbuf;         // p   (current reflector)
-  double* pivinfo;      // [0] = R_jj, [1] = top
+  double* best_val;     // nb
+  int32_t* best_pos;    // nb
+  int32_t* best_phys;   // nb
   GridBarrier bar;
-  int v_in_smem;
+  int64_t rows_b;       // rows per block
+  int64_t lds;          // slab column stride (odd: no shared-memory bank conflicts)
+  int64_t region;       // doubles per block region: lds*c (slab) + rows_b (v) + c (sums)
+  int slab_in_smem;
+  int redundant;        // 1: every block reduces every column (2 barriers per step)
 };
 
 __device__ __forceinline__ bool better(double a, int pa, double b, int pb) {
   return (a > b) || (a == b && pa < pb);
 }
 
-// block-local argmax over (val, pos, phys); writes the winner to thread 0
+// block-wide argmax over (val, pos, phys); thread 0 ends with the winner
 __device__ void block_best(double& val, int& pos, int& phys, double* sv, int* sp, int* sf) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
@@ -75,154 +84,218 @@ __device__ void block_best(double& val, int& pos, int& phys, double* sv, int* sp
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(512, 1) k_cpqr(CpqrState s) {
-  extern __shared__ double smem_v[];
+constexpr int kCpqrThreads = 512;
+
+// One warp sums part[b * c + cc] over the nb blocks (lane-strided, fixed
+// shuffle tree: the same order in every block and every run).
+__device__ __forceinline__ double warp_sum_blocks(const double* part, int64_t c, int64_t cc, int nb, int lane) {
+  double a = 0.0;
+  for (int bb = lane; bb < nb; bb += 32) a += __ldcg(part + (int64_t)bb * c + cc);
+  return warp_sum(a);
+}
+
+// The same for up to 4 columns cc0 + k*stride at once: every load is issued
+// before the first add, so the L2 latency is paid once, not once per column.
+template <int NC>
+__device__ __forceinline__ void warp_sum_blocks_n(const double* part, int64_t c, int64_t cc0, int64_t stride,
+                                                  int ncol, int nb, int lane, double (&out)[NC]) {
+  double acc[NC];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) acc[k] = 0.0;
+  for (int bb = lane; bb < nb; bb += 32) {
+    double v[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) v[k] = k < ncol ? __ldcg(part + (int64_t)bb * c + cc0 + k * stride) : 0.0;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) acc[k] += v[k];
+  }
+#pragma unroll
+  for (int k = 0; k < NC; ++k) out[k] = warp_sum(acc[k]);
+}
+
+__global__ void __launch_bounds__(kCpqrThreads, 1) k_cpqr(CpqrState s) {
+  extern __shared__ double smem_d[];
   __shared__ double sv[32];
   __shared__ int sp[32], sf[32];
-  __shared__ int s_piv_pos, s_piv_phys, s_stop;
+  __shared__ int s_piv, s_pivpos, s_stop;
+  __shared__ double s_alpha, s_sgn, s_inv, s_x0;
 
-  const int nb = gridDim.x;
-  const int64_t per = (s.c + nb - 1) / nb;
-  const int64_t c_lo = (int64_t)blockIdx.x * per;
-  const int64_t c_hi = min(s.c, c_lo + per);
+  const int nb = gridDim.x, b = blockIdx.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t r_lo = (int64_t)b * s.rows_b;
+  const int64_t r_hi = min(s.p, r_lo + s.rows_b);
+  const int64_t nr = r_hi > r_lo ? r_hi - r_lo : 0;      // rows of this block
+  const int64_t cpb = (s.c + nb - 1) / nb;                // columns owned per block (owner mode)
+  const int64_t o_lo = min(s.c, (int64_t)b * cpb), o_hi = min(s.c, o_lo + cpb);
+  const int64_t c_lo = s.redundant ? 0 : o_lo, c_hi = s.redundant ? s.c : o_hi;
+  double* slab = s.slab_in_smem ? smem_d : s.slab_g + (int64_t)b * s.region;   // column cc at slab + cc*lds
+  double* vloc = slab + s.lds * s.c;                      // this block's rows of the reflector
+  double* sums = vloc + s.rows_b;                         // reduced column sums (redundant mode)
+  // every block keeps its own copy of the pivoting bookkeeping: all blocks
+  // reach the same pivot decision, so the copies stay identical
+  int32_t* pos_of = reinterpret_cast<int32_t*>(sums + s.c);   // physical -> position
+  int32_t* phys_at = pos_of + s.c;                            // position -> physical
+  uint8_t* done = reinterpret_cast<uint8_t*>(phys_at + s.c);
+  double* pn = s.part_n + (int64_t)b * s.c;
+  double* pd = s.part_d + (int64_t)b * s.c;
 
-  // ---- init: norms of all columns, positions = identity ----------------------
-  {
-    double bv = -1.0; int bp = 0x7fffffff, bf = -1;
-    for (int64_t cc = c_lo + wid; cc < c_hi; cc += nw) {
-      const double* col = s.M + cc * s.ldm;
-      double a = 0.0;
-      for (int64_t i = lane; i < s.p; i += 32) a = fma(col[i], col[i], a);
-      a = warp_sum(a);
-      if (lane == 0) {
-        s.norm2[cc] = a; s.pos_of[cc] = (int)cc; s.phys_at[cc] = (int)cc; s.done[cc] = 0;
-      }
-      if (better(a, (int)cc, bv, bp)) { bv = a; bp = (int)cc; bf = (int)cc; }
-    }
-    block_best(bv, bp, bf, sv, sp, sf);
-    if (threadIdx.x == 0) { s.best_val[blockIdx.x] = bv; s.best_pos[blockIdx.x] = bp; s.best_phys[blockIdx.x] = bf; }
+  for (int64_t e = threadIdx.x; e < nr * s.c; e += blockDim.x) {
+    const int64_t cc = e / nr, i = e - cc * nr;
+    slab[cc * s.lds + i] = s.M[cc * s.ldm + r_lo + i];
   }
-  if (!grid_sync(s.bar)) return;
+  for (int64_t cc = threadIdx.x; cc < s.c; cc += blockDim.x) {
+    pos_of[cc] = (int)cc; phys_at[cc] = (int)cc; done[cc] = 0;
+  }
+  __syncthreads();
 
-  double top = 0.0;
   int64_t j = 0;
-  for (; j < s.kmax; ++j) {
-    // (1) global pivot (every block reduces the same data)
+  double top = 0.0;
+  for (;; ++j) {
+    // ---- (F) apply H_{j-1}; row j-1 of R; partial norms^2 over rows >= j ---
+    {
+      const int64_t i0 = max(r_lo, j - 1) - r_lo;
+      const int64_t in = max(r_lo, j) - r_lo;
+      const bool upd = j > 0;
+      const bool own_prev = upd && (j - 1) >= r_lo && (j - 1) < r_hi;
+      const bool own_cur = j >= r_lo && j < r_hi;
+      for (int64_t cc = threadIdx.x; cc < s.c; cc += blockDim.x) {
+        double nrm = 0.0;
+        double* col = slab + cc * s.lds;
+        if (!done[cc]) {
+          if (upd) {
+            const double tw = 2.0 * (s.redundant ? sums[cc] : __ldcg(s.colsum + cc));
+            for (int64_t i = i0; i < nr; ++i) col[i] = fma(-tw, vloc[i], col[i]);
+            if (own_prev) s.Rphys[(j - 1) * s.c + cc] = col[(j - 1) - r_lo];
+          }
+          for (int64_t i = in; i < nr; ++i) nrm = fma(col[i], col[i], nrm);
+        }
+        pn[cc] = nrm;
+        if (own_cur) s.rowbuf[cc] = col[j - r_lo];
+      }
+    }
+    if (!grid_sync(s.bar)) return;
+
+    // ---- (N) norms^2 and the best candidate -------------------------------
     {
       double bv = -1.0; int bp = 0x7fffffff, bf = -1;
-      for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        const double v = __ldcg(s.best_val + b);
-        const int p = __ldcg(s.best_pos + b);
-        if (better(v, p, bv, bp)) { bv = v; bp = p; bf = __ldcg(s.best_phys + b); }
+      for (int64_t cc0 = c_lo + wid; cc0 < c_hi; cc0 += 4 * nw) {
+        const int ncol = (int)min((int64_t)4, (c_hi - cc0 + nw - 1) / nw);
+        double a4[4];
+        warp_sum_blocks_n<4>(s.part_n, s.c, cc0, nw, ncol, nb, lane, a4);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int64_t cc = cc0 + k * nw;
+          if (k >= ncol || done[cc]) continue;
+          const double a = a4[k];
+          if (lane == 0) {
+            if (s.redundant) sums[cc] = a;
+            else s.colsum[cc] = a;
+          }
+          const int pc = pos_of[cc];
+          if (better(a, pc, bv, bp)) { bv = a; bp = pc; bf = (int)cc; }
+        }
       }
       block_best(bv, bp, bf, sv, sp, sf);
+      if (!s.redundant) {
+        if (threadIdx.x == 0) { s.best_val[b] = bv; s.best_pos[b] = bp; s.best_phys[b] = bf; }
+        if (!grid_sync(s.bar)) return;
+        bv = -1.0; bp = 0x7fffffff; bf = -1;
+        for (int bb = threadIdx.x; bb < nb; bb += blockDim.x) {
+          const double v = __ldcg(s.best_val + bb);
+          const int pp = __ldcg(s.best_pos + bb);
+          if (better(v, pp, bv, bp)) { bv = v; bp = pp; bf = __ldcg(s.best_phys + bb); }
+        }
+        block_best(bv, bp, bf, sv, sp, sf);
+      }
+      // thread 0 holds the global winner
       if (threadIdx.x == 0) {
-        s_piv_pos = bp; s_piv_phys = bf;
         const double nrm = sqrt(fmax(bv, 0.0));
         if (j == 0) top = nrm;
-        s_stop = (bf < 0 || bv <= 0.0 || (j > 0 && nrm <= s.rtol * top)) ? 1 : 0;
+        const bool stop = (j >= s.kmax) || bf < 0 || bv <= 0.0 || (j > 0 && nrm <= s.rtol * top);
+        s_stop = stop ? 1 : 0;
+        s_piv = bf; s_pivpos = bp;
+        if (!stop) {
+          const double x0 = __ldcg(s.rowbuf + bf);
+          const double sgn = x0 >= 0.0 ? 1.0 : -1.0;
+          const double vn2 = 2.0 * nrm * (nrm + fabs(x0));     // ||x + sgn ||x|| e_j||^2
+          s_alpha = nrm; s_sgn = sgn; s_x0 = x0;
+          s_inv = vn2 > 0.0 ? 1.0 / sqrt(vn2) : 0.0;
+        }
       }
       __syncthreads();
     }
     if (s_stop) break;
-    const int piv = s_piv_phys;
 
-    // (2) reflector by the owner of the pivot column; position swap by block 0
-    if (piv >= c_lo && piv < c_hi) {
-      double* col = s.M + (int64_t)piv * s.ldm;
-      double a = 0.0;
-      for (int64_t i = j + threadIdx.x; i < s.p; i += blockDim.x) a = fma(col[i], col[i], a);
-      a = block_sum(a, sv);
-      const double alpha = sqrt(a);
-      const double x0 = col[j];
-      const double sgn = x0 >= 0.0 ? 1.0 : -1.0;
-      const double v0 = x0 + sgn * alpha;
-      double b = 0.0;
-      for (int64_t i = j + threadIdx.x; i < s.p; i += blockDim.x) {
-        const double vi = (i == j) ? v0 : col[i];
-        b = fma(vi, vi, b);
-      }
-      b = block_sum(b, sv);
-      const double inv = b > 0.0 ? 1.0 / sqrt(b) : 0.0;
-      for (int64_t i = threadIdx.x; i < s.p; i += blockDim.x) {
-        const double vi = i < j ? 0.0 : ((i == j) ? v0 : col[i]) * inv;
-        s.vbuf[i] = vi;
-        s.V[(int64_t)j * s.p + i] = vi;
+    // ---- (P) this block's rows of v and partial dots v^T M(:, c) ------------
+    {
+      const int piv = s_piv;
+      const double inv = s_inv;
+      const double* xcol = slab + (int64_t)piv * s.lds;
+      for (int64_t i = threadIdx.x; i < nr; i += blockDim.x) {
+        const int64_t gi = r_lo + i;
+        double vi = 0.0;
+        if (gi == j) vi = (s_x0 + s_sgn * s_alpha) * inv;
+        else if (gi > j) vi = xcol[i] * inv;
+        vloc[i] = vi;
+        s.V[j * s.p + gi] = vi;
       }
       if (threadIdx.x == 0) {
-        s.done[piv] = 1;
-        s.Rphys[j * s.c + piv] = -sgn * alpha;
-        s.pivinfo[0] = -sgn * alpha;
+        const int pj = phys_at[j];
+        const int pp = s_pivpos;
+        phys_at[j] = piv; phys_at[pp] = pj;
+        pos_of[piv] = (int)j; pos_of[pj] = pp;
+        done[piv] = 1;
+        if (b == 0) s.Rphys[j * s.c + piv] = -s_sgn * s_alpha;
       }
-      // the pivot column becomes R's column: rows > j are zero (after every
-      // thread has read it above: the two loops map rows to threads differently)
       __syncthreads();
-      for (int64_t i = j + threadIdx.x; i < s.p; i += blockDim.x) col[i] = (i == j) ? -sgn * alpha : 0.0;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      const int pj = __ldcg(s.phys_at + j);  // physical column now at position j
-      const int pp = s_piv_pos;             // position of the pivot
-      s.phys_at[j] = piv; s.phys_at[pp] = pj;
-      s.pos_of[piv] = (int)j; s.pos_of[pj] = pp;
+      const int64_t i0 = max(r_lo, j) - r_lo;
+      for (int64_t cc = threadIdx.x; cc < s.c; cc += blockDim.x) {
+        double d = 0.0;
+        if (!done[cc]) {
+          const double* col = slab + cc * s.lds;
+          for (int64_t i = i0; i < nr; ++i) d = fma(vloc[i], col[i], d);
+        }
+        pd[cc] = d;
+      }
     }
     if (!grid_sync(s.bar)) return;
 
-    // (3) apply H_j = I - 2 v v^T to the live columns of this block
-    const double* v = s.vbuf;
-    if (s.v_in_smem) {
-      for (int64_t i = threadIdx.x; i < s.p; i += blockDim.x) smem_v[i] = __ldcg(s.vbuf + i);
-      __syncthreads();
-      v = smem_v;
-    }
-    double bv = -1.0; int bp = 0x7fffffff, bf = -1;
-    for (int64_t cc = c_lo + wid; cc < c_hi; cc += nw) {
-      if (s.done[cc]) continue;
-      double* col = s.M + cc * s.ldm;
-      double w = 0.0;
-      if (s.v_in_smem) {
-        for (int64_t i = j + lane; i < s.p; i += 32) w = fma(v[i], col[i], w);
-      } else {
-        for (int64_t i = j + lane; i < s.p; i += 32) w = fma(__ldcg(v + i), col[i], w);
-      }
-      w = warp_sum(w);
-      const double tw = 2.0 * w;
-      double a = 0.0;
-      for (int64_t i = j + lane; i < s.p; i += 32) {
-        const double vi = s.v_in_smem ? v[i] : __ldcg(v + i);
-        const double x = fma(-tw, vi, col[i]);
-        col[i] = x;
-        if (i > j) a = fma(x, x, a);
-      }
-      a = warp_sum(a);
+    // ---- (D) dots ------------------------------------------------------------
+    for (int64_t cc0 = c_lo + wid; cc0 < c_hi; cc0 += 4 * nw) {
+      const int ncol = (int)min((int64_t)4, (c_hi - cc0 + nw - 1) / nw);
+      double a4[4];
+      warp_sum_blocks_n<4>(s.part_d, s.c, cc0, nw, ncol, nb, lane, a4);
       if (lane == 0) {
-        s.Rphys[j * s.c + cc] = col[j];
-        s.norm2[cc] = a;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (k >= ncol) continue;
+          const int64_t cc = cc0 + k * nw;
+          if (s.redundant) sums[cc] = a4[k];
+          else s.colsum[cc] = a4[k];
+        }
       }
-      const int pc = __ldcg(s.pos_of + cc);
-      if (better(a, pc, bv, bp)) { bv = a; bp = pc; bf = (int)cc; }
     }
-    block_best(bv, bp, bf, sv, sp, sf);
-    if (threadIdx.x == 0) { s.best_val[blockIdx.x] = bv; s.best_pos[blockIdx.x] = bp; s.best_phys[blockIdx.x] = bf; }
-    if (!grid_sync(s.bar)) return;
+    if (!s.redundant) {
+      if (!grid_sync(s.bar)) return;
+    } else {
+      __syncthreads();
+    }
   }
 
   // ---- epilogue: rank, permutation, R in pivoted order, trailing norm ------
   const int64_t r = j;
-  if (blockIdx.x == 0) {
+  if (b == 0) {
     if (threadIdx.x == 0) *s.rank = (int32_t)r;
-    for (int64_t q = threadIdx.x; q < s.c; q += blockDim.x) s.perm[q] = __ldcg(s.phys_at + q);
     double t = 0.0;
     for (int64_t cc = threadIdx.x; cc < s.c; cc += blockDim.x)
-      if (!__ldcg(s.done + cc)) t += __ldcg(s.norm2 + cc);
+      if (!done[cc]) t += s.redundant ? sums[cc] : __ldcg(s.colsum + cc);
     t = block_sum(t, sv);
     if (threadIdx.x == 0) *s.tail2 = (r < min(s.p, s.c)) ? t : 0.0;
+    for (int64_t q = threadIdx.x; q < s.c; q += blockDim.x) s.perm[q] = phys_at[q];
   }
-  // R[i, q] = Rphys[i, phys_at[q]] for i < r, zero below the diagonal
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < r * s.c;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t e = (int64_t)b * blockDim.x + threadIdx.x; e < r * s.c; e += (int64_t)nb * blockDim.x) {
     const int64_t i = e / s.c, q = e - i * s.c;
-    s.R[i * s.c + q] = (q < i) ? 0.0 : __ldcg(s.Rphys + i * s.c + __ldcg(s.phys_at + q));
+    s.R[i * s.c + q] = (q < i) ? 0.0 : __ldcg(s.Rphys + i * s.c + phys_at[q]);
   }
 }
 
@@ -232,44 +305,51 @@ lrs_status launch_cpqr(lrs_ctx* ctx, double* M, int64_t p, int64_t c, int64_t ld
   CpqrState s{};
   s.M = M; s.p = p; s.c = c; s.ldm = ldm; s.kmax = kmax; s.rtol = rtol;
   s.perm = o.perm; s.R = o.R; s.V = o.V; s.tail2 = o.tail2; s.rank = o.rank;
-  const int threads = 512;
-  const size_t vbytes = sizeof(double) * (size_t)p;
-  s.v_in_smem = vbytes <= 160 * 1024 ? 1 : 0;
-  const size_t dyn = s.v_in_smem ? vbytes : 0;
+  // blocks: about 2048 matrix elements each (the FP64 work of one step per
+  // block), at most one per SM, at least 4 rows each
+  int64_t nb = (p * c + 2047) / 2048;
+  if (nb > ctx->num_sms) nb = ctx->num_sms;
+  if (nb > (p + 3) / 4) nb = (p + 3) / 4;
+  if (nb < 1) nb = 1;
+  s.rows_b = (p + nb - 1) / nb;
+  nb = (p + s.rows_b - 1) / s.rows_b;
+  s.lds = s.rows_b | 1;
+  // per block: slab, v rows, column sums, then pos_of/phys_at (int32) and done (bytes)
+  s.region = s.lds * c + s.rows_b + c + (c + (c * 8 + 7) / 8 + 1);
+  s.redundant = (nb * c <= 24576) ? 1 : 0;
+  const size_t slab_bytes = sizeof(double) * (size_t)s.region;
+  s.slab_in_smem = slab_bytes <= 200 * 1024 ? 1 : 0;
+  const size_t dyn = s.slab_in_smem ? slab_bytes : 0;
   if (dyn > 48 * 1024)
     LRS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_cpqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   int per_sm = 0;
-  LRS_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cpqr, threads, dyn));
+  LRS_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cpqr, kCpqrThreads, dyn));
   if (per_sm < 1) return lrs_fail(ctx, LRS_ECUDA, "cpqr: kernel does not fit on an SM");
-  int64_t nb = ctx->num_sms;                       // one block per SM
-  const int64_t want = (c + 15) / 16;              // at least ~16 columns per block
-  if (nb > want) nb = want < 1 ? 1 : want;
-
-  s.norm2 = (double*)ws_alloc(ctx, sizeof(double) * c);
-  s.pos_of = (int32_t*)ws_alloc(ctx, sizeof(int32_t) * c);
-  s.phys_at = (int32_t*)ws_alloc(ctx, sizeof(int32_t) * c);
-  s.done = (uint8_t*)ws_alloc(ctx, c);
+  if (!s.slab_in_smem) {
+    s.slab_g = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(nb * s.region));
+    if (!s.slab_g) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (cpqr slab)");
+  }
+  s.part_n = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(nb * c));
+  s.part_d = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(nb * c));
+  s.colsum = (double*)ws_alloc(ctx, sizeof(double) * c);
+  s.rowbuf = (double*)ws_alloc(ctx, sizeof(double) * c);
   s.Rphys = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(kmax > 0 ? kmax : 1) * c);
   s.best_val = (double*)ws_alloc(ctx, sizeof(double) * nb);
   s.best_pos = (int32_t*)ws_alloc(ctx, sizeof(int32_t) * nb);
   s.best_phys = (int32_t*)ws_alloc(ctx, sizeof(int32_t) * nb);
-  s.vbuf = (double*)ws_alloc(ctx, vbytes);
-  s.pivinfo = (double*)ws_alloc(ctx, sizeof(double) * 2);
   unsigned* bar = (unsigned*)ws_alloc(ctx, 256);
-  if (!s.norm2 || !s.pos_of || !s.phys_at || !s.done || !s.Rphys || !s.best_val || !s.best_pos ||
-      !s.best_phys || !s.vbuf || !s.pivinfo || !bar)
+  if (!s.part_n || !s.part_d || !s.colsum || !s.rowbuf || !s.Rphys || !s.best_val || !s.best_pos || !s.best_phys || !bar)
     return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (cpqr)");
   LRS_CUDA_TRY(ctx, cudaMemsetAsync(bar, 0, 256, ctx->stream));
   s.bar.count = bar; s.bar.gen = bar + 1; s.bar.err = (int*)(bar + 2);
   void* args[] = {&s};
-  LRS_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)k_cpqr, dim3((unsigned)nb), dim3(threads),
+  LRS_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)k_cpqr, dim3((unsigned)nb), dim3(kCpqrThreads),
                                                 args, dyn, ctx->stream));
   ctx->launches++;
-  // the barrier's error word is checked by the caller through lrs::check_device_error
-  int err_h = 0;
-  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(&err_h, bar + 2, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  int* h = (int*)ctx->host_scratch;
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 32, bar + 2, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-  if (err_h != 0) return lrs_fail(ctx, LRS_ETIMEOUT, "cpqr: grid barrier wait gave up");
+  if (h[32] != 0) return lrs_fail(ctx, LRS_ETIMEOUT, "cpqr: grid barrier wait gave up");
   return LRS_OK;
 }
 
@@ -277,23 +357,37 @@ lrs_status launch_cpqr(lrs_ctx* ctx, double* M, int64_t p, int64_t c, int64_t ld
 // Q = H_0 ... H_{r-1} [I_r; 0]: column c only sees H_c .. H_0 (reflectors
 // with index > c leave e_c untouched), so each block builds one column.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_form_q(const double* __restrict__ V, int64_t p, int64_t r,
+__global__ void __launch_bounds__(512) k_form_q(const double* __restrict__ V, int64_t p, int64_t r,
                                                 double* __restrict__ Q, int64_t ldq) {
   extern __shared__ double q[];
   __shared__ double red[32];
   const int64_t c = blockIdx.x;
-  for (int64_t i = threadIdx.x; i < p; i += blockDim.x) q[i] = (i == c) ? 1.0 : 0.0;
+  const int64_t bs = blockDim.x;
+  for (int64_t i = threadIdx.x; i < p; i += bs) q[i] = (i == c) ? 1.0 : 0.0;
   __syncthreads();
   for (int64_t jj = c; jj >= 0; --jj) {
     const double* v = V + jj * p;
-    double w = 0.0;
-    for (int64_t i = jj + threadIdx.x; i < p; i += blockDim.x) w = fma(v[i], q[i], w);
-    w = block_sum(w, red);
+    // four independent loads in flight per thread (the loop is latency-bound otherwise)
+    double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
+    int64_t i = jj + threadIdx.x;
+    for (; i + 3 * bs < p; i += 4 * bs) {
+      const double a0 = __ldg(v + i), a1 = __ldg(v + i + bs), a2 = __ldg(v + i + 2 * bs), a3 = __ldg(v + i + 3 * bs);
+      w0 = fma(a0, q[i], w0); w1 = fma(a1, q[i + bs], w1);
+      w2 = fma(a2, q[i + 2 * bs], w2); w3 = fma(a3, q[i + 3 * bs], w3);
+    }
+    for (; i < p; i += bs) w0 = fma(__ldg(v + i), q[i], w0);
+    const double w = block_sum((w0 + w1) + (w2 + w3), red);
     const double tw = 2.0 * w;
-    for (int64_t i = jj + threadIdx.x; i < p; i += blockDim.x) q[i] = fma(-tw, v[i], q[i]);
+    i = jj + threadIdx.x;
+    for (; i + 3 * bs < p; i += 4 * bs) {
+      const double a0 = __ldg(v + i), a1 = __ldg(v + i + bs), a2 = __ldg(v + i + 2 * bs), a3 = __ldg(v + i + 3 * bs);
+      q[i] = fma(-tw, a0, q[i]); q[i + bs] = fma(-tw, a1, q[i + bs]);
+      q[i + 2 * bs] = fma(-tw, a2, q[i + 2 * bs]); q[i + 3 * bs] = fma(-tw, a3, q[i + 3 * bs]);
+    }
+    for (; i < p; i += bs) q[i] = fma(-tw, __ldg(v + i), q[i]);
     __syncthreads();
   }
-  for (int64_t i = threadIdx.x; i < p; i += blockDim.x) Q[i * ldq + c] = q[i];
+  for (int64_t i = threadIdx.x; i < p; i += bs) Q[i * ldq + c] = q[i];
 }
 
 lrs_status launch_form_q(lrs_ctx* ctx, const double* V, int64_t p, int64_t r, double* Q, int64_t ldq) {
@@ -302,7 +396,7 @@ lrs_status launch_form_q(lrs_ctx* ctx, const double* V, int64_t p, int64_t r, do
   if (dyn > 200 * 1024) return lrs_fail(ctx, LRS_EINVAL, "form_q: p=%lld too large", (long long)p);
   if (dyn > 48 * 1024)
     LRS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_form_q, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-  k_form_q<<<(unsigned)r, 256, dyn, ctx->stream>>>(V, p, r, Q, ldq);
+  k_form_q<<<(unsigned)r, 512, dyn, ctx->stream>>>(V, p, r, Q, ldq);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
   return LRS_OK;

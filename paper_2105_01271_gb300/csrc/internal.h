@@ -45,7 +45,12 @@ lrs_status launch_sketch(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int
 // W[m x |I|] (FP64) = A(:, I)  with I the injection points of grid g
 lrs_status launch_gather(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int64_t lda,
                          const GridDev& g, double* W, int64_t ldw);
-// sum of squares of A (m x n), FP64, added into *out (device)
+// *out = sum of part[0..np) (device, one block, fixed order)
+lrs_status launch_sum(lrs_ctx* ctx, const double* part, int np, double* out);
+// W32[m x |I|] (FP32) = A(:, I): the same subsample stored in FP32 (tensor-core operands)
+lrs_status launch_gather32(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int64_t lda,
+                           const GridDev& g, float* W, int64_t ldw);
+// sum of squares of A (m x n), FP64, into *out (device)
 lrs_status launch_fro2(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int64_t n,
                        int64_t lda, double* out);
 
@@ -59,7 +64,12 @@ struct GemmArgs {
   double alpha;            // C = alpha * X^T A
 };
 lrs_status launch_gemm_simt(lrs_ctx* ctx, const GemmArgs& a, int fp64);
-lrs_status launch_gemm_tc(lrs_ctx* ctx, const GemmArgs& a, int prec);
+// fro2_out (device, may be NULL): also ||A||_F^2 of the operand A, fused (M <= 128 only)
+lrs_status launch_gemm_tc(lrs_ctx* ctx, const GemmArgs& a, int prec, double* fro2_out = nullptr);
+// workspace bytes the tensor-core path needs for an M x K operand X (0 for SIMT modes)
+size_t gemm_tc_workspace(int64_t M, int64_t K, int prec);
+// extra workspace of the split-K partial sums for an M x N x K product (0 when not split)
+size_t gemm_tc_splitk_workspace(int64_t M, int64_t N, int64_t K, int num_sms);
 
 // cpqr.cu --------------------------------------------------------------------
 // Householder CPQR of the p x c matrix M stored COLUMN-major (column j at
@@ -93,11 +103,16 @@ lrs_status launch_jacobi(lrs_ctx* ctx, double* R, int64_t r, double* V, double* 
 // transposed copy of a row-major FP64 matrix: dst (cols x rows) = src^T
 lrs_status launch_transpose(lrs_ctx* ctx, const double* src, int64_t rows, int64_t cols,
                             int64_t lds, double* dst, int64_t ldd);
-// U columns sign fix (largest |entry| positive), applied to U (m x k) and V (n x k)
-lrs_status launch_sign_fix(lrs_ctx* ctx, double* U, int64_t m, int64_t k, int64_t ldu,
-                           void* V, int v_f64, int64_t n, int64_t ldv);
-// W[:, j] = V[:, j] / s[j]  (r x k, FP64)
+lrs_status launch_transpose32(lrs_ctx* ctx, const float* src, int64_t rows, int64_t cols,
+                              int64_t lds, float* dst, int64_t ldd);
+// FP64 -> FP32 copy (round to nearest)
+lrs_status launch_to_f32(lrs_ctx* ctx, const double* src, int64_t rows, int64_t cols, int64_t lds,
+                         float* dst, int64_t ldd);
+// U columns sign fix (largest |entry| positive, lowest row on ties): flips U
+// (m x k) in place and writes the applied signs (+1/-1) to sign_out (k)
+lrs_status launch_sign_fix(lrs_ctx* ctx, double* U, int64_t m, int64_t k, int64_t ldu, double* sign_out);
+// W[:, j] = sign[j] * V[:, j] / s[j]  (r x k, FP64; sign may be NULL)
 lrs_status launch_scale_cols(lrs_ctx* ctx, const double* V, int64_t r, int64_t ldv,
-                             const double* s, int64_t k, double* W, int64_t ldw);
+                             const double* s, const double* sign, int64_t k, double* W, int64_t ldw);
 
 }  // namespace lrs

@@ -65,18 +65,30 @@ static size_t tsqr_ws(int64_t r, int64_t n, size_t tsz) {
   return b;
 }
 
+// bytes of scratch launch_cpqr takes for a p x c matrix and kmax steps
+static size_t cpqr_ws(int64_t p, int64_t c, int64_t kmax) {
+  const size_t nbmax = 1024;                      // > any SM count
+  size_t b = 0;
+  b += 2 * align256(8 * nbmax * (size_t)c);       // per-block partial sums (norms, dots)
+  b += 2 * align256(8 * (size_t)c);               // column sums, row buffer
+  b += 2 * align256(4 * (size_t)c) + align256((size_t)c);   // positions, done
+  b += align256(8 * (size_t)((kmax > 0 ? kmax : 1) * c));  // R by physical column
+  b += 4 * align256(8 * nbmax) + 256;             // per-block best, barrier
+  // slab storage when a block's rows do not fit in shared memory
+  b += align256(8 * (size_t)(p * c + 3 * nbmax * c + 2 * nbmax + p));
+  return b + 4096;
+}
+
 // bytes of workspace one orthonormalisation of a p x c matrix needs
 static size_t orth_ws(int64_t p, int64_t c) {
   const int64_t kmax = p < c ? p : c;
   size_t b = 0;
   b += align256(8 * (size_t)(p * c));            // column-major copy
   b += align256(4 * (size_t)c);                  // perm
-  b += 2 * align256(8 * (size_t)(kmax * c));     // R, Rphys
+  b += align256(8 * (size_t)(kmax * c));         // R
   b += align256(8 * (size_t)(p * kmax));         // V
-  b += align256(8 * (size_t)c) * 3 + align256((size_t)c);  // norm2, pos_of, phys_at, done
-  b += align256(8 * (size_t)p);                  // vbuf
-  b += 16 * 4096;                                // per-block scratch, barrier, scalars
-  return b;
+  b += 2 * 256;                                  // scalars
+  return b + cpqr_ws(p, c, kmax);
 }
 
 // Orthonormal basis of the numerical range of Min (p x c, row-major ldi):
@@ -209,14 +221,27 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
   LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   const int64_t l = gs.l;
   const int64_t nI = q > 0 ? gg.l : 0;
-  // workspace: W, W^T, two m x l / nI x l work matrices, orthonormalisation
+  const int64_t wmax = l > m ? l : m;
+  // Tensor-core modes split every operand into BF16 pieces (<= 24 bits), so
+  // their operands are kept in FP32 (exact for FP32/BF16 data); the CUDA-core
+  // modes read FP64 operands directly.
+  const bool tc = prec >= LRS_PREC_SPLIT_BF16;
+  const size_t wsz = tc ? 4 : 8;
   size_t need = 0;
   if (q > 0) {
-    const int64_t wmax = l > m ? l : m;
-    need += 2 * align256(8 * (size_t)(m * nI));
-    need += align256(8 * (size_t)(nI * wmax)) + align256(8 * (size_t)(m * wmax)) * 2;
+    need += 2 * align256(wsz * (size_t)(m * nI));                     // W, W^T
+    need += align256(8 * (size_t)(nI * wmax)) + 2 * align256(8 * (size_t)(m * wmax));
+    need += align256(8 * (size_t)(nI * wmax));                        // orthonormal T
+    if (tc) need += align256(4 * (size_t)(nI * wmax)) + align256(4 * (size_t)(m * wmax));  // FP32 operands
     const size_t o1 = orth_ws(m, l), o2 = orth_ws(nI, wmax);
-    need += (o1 > o2 ? o1 : o2) + align256(8 * (size_t)(nI * wmax));
+    size_t inner = o1 > o2 ? o1 : o2;
+    if (tc) {
+      const size_t t1 = gemm_tc_workspace(nI, m, prec) + gemm_tc_splitk_workspace(nI, wmax, m, ctx->num_sms);
+      const size_t t2 = gemm_tc_workspace(m, nI, prec) + gemm_tc_splitk_workspace(m, wmax, nI, ctx->num_sms);
+      const size_t t = (t1 > t2 ? t1 : t2) + 4096;
+      if (t > inner) inner = t;
+    }
+    need += inner;
   }
   lrs_status st = ws_reserve(ctx, need);
   if (st) return st;
@@ -227,17 +252,27 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
     *g_cols = l;
     return LRS_OK;
   }
-  const int64_t wmax = l > m ? l : m;
-  double* W = (double*)ws_alloc(ctx, 8 * (size_t)(m * nI));
-  double* WT = (double*)ws_alloc(ctx, 8 * (size_t)(m * nI));
+  void* W = ws_alloc(ctx, wsz * (size_t)(m * nI));
+  void* WT = ws_alloc(ctx, wsz * (size_t)(m * nI));
   double* Tm = (double*)ws_alloc(ctx, 8 * (size_t)(nI * wmax));
+  double* To = (double*)ws_alloc(ctx, 8 * (size_t)(nI * wmax));
   double* Ga = (double*)ws_alloc(ctx, 8 * (size_t)(m * wmax));
   double* Gb = (double*)ws_alloc(ctx, 8 * (size_t)(m * wmax));
-  if (!W || !WT || !Tm || !Ga || !Gb) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (power_pass)");
+  float* T32 = tc ? (float*)ws_alloc(ctx, 4 * (size_t)(nI * wmax)) : nullptr;
+  float* G32 = tc ? (float*)ws_alloc(ctx, 4 * (size_t)(m * wmax)) : nullptr;
+  if (!W || !WT || !Tm || !To || !Ga || !Gb || (tc && (!T32 || !G32)))
+    return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (power_pass)");
   const size_t mark = ctx->ws_top;
-  st = launch_gather(ctx, A, dtype, m, lda, gg, W, nI);
-  if (st) return st;
-  st = launch_transpose(ctx, W, m, nI, nI, WT, m);
+  const int32_t wdt = tc ? LRS_F32 : LRS_F64;
+  if (tc) {
+    st = launch_gather32(ctx, A, dtype, m, lda, gg, (float*)W, nI);
+    if (st) return st;
+    st = launch_transpose32(ctx, (const float*)W, m, nI, nI, (float*)WT, m);
+  } else {
+    st = launch_gather(ctx, A, dtype, m, lda, gg, (double*)W, nI);
+    if (st) return st;
+    st = launch_transpose(ctx, (const double*)W, m, nI, nI, (double*)WT, m);
+  }
   if (st) return st;
   // starting block: Q_np = QR(A_f D) with re-orthonormalisation, else A_f D
   int64_t gc = l;
@@ -251,38 +286,48 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
   }
   for (int it = 0; it < q; ++it) {
     // T = W^T G   (nI x gc)
-    st = gemm(ctx, prec, nI, gc, m, W, LRS_F64, nI, Gcur, LRS_F64, ldcur, Tm, 1, 0, gc);
-    if (st) return st;
-    int64_t tc = gc;
-    const double* Tcur = Tm;
-    int64_t ldt = gc;
-    if (reorth) {
-      // orthonormalise T in place of a fresh buffer inside the workspace
-      double* To = (double*)ws_alloc(ctx, 8 * (size_t)(nI * gc));
-      if (!To) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (power_pass T)");
-      const size_t mark2 = ctx->ws_top;
-      st = orth(ctx, Tm, nI, gc, gc, rtol, To, gc, &tc);
+    if (tc) {
+      st = launch_to_f32(ctx, Gcur, m, gc, ldcur, G32, gc);
       if (st) return st;
-      ctx->ws_top = mark2;
-      Tcur = To; ldt = gc;
+      // the orthonormalisation reads FP64; the next product reads FP32
+      if (reorth) st = gemm(ctx, prec, nI, gc, m, W, wdt, nI, G32, LRS_F32, gc, Tm, 1, 0, gc);
+      else st = gemm(ctx, prec, nI, gc, m, W, wdt, nI, G32, LRS_F32, gc, T32, 0, 0, gc);
+    } else {
+      st = gemm(ctx, prec, nI, gc, m, W, wdt, nI, Gcur, LRS_F64, ldcur, Tm, 1, 0, gc);
     }
-    // G = W T   (m x tc)  computed as (W^T)^T T
-    double* Gn = (Gcur == Ga) ? Gb : Ga;
-    st = gemm(ctx, prec, m, tc, nI, WT, LRS_F64, m, Tcur, LRS_F64, ldt, Gn, 1, 0, wmax);
     if (st) return st;
+    ctx->ws_top = mark;
+    int64_t tc_cols = gc;
+    const void* Tcur = tc ? (const void*)T32 : (const void*)Tm;
+    int32_t tdt = tc ? LRS_F32 : LRS_F64;
+    if (reorth) {
+      st = orth(ctx, Tm, nI, gc, gc, rtol, To, gc, &tc_cols);
+      if (st) return st;
+      ctx->ws_top = mark;
+      if (tc) {
+        st = launch_to_f32(ctx, To, nI, tc_cols, gc, T32, gc);
+        if (st) return st;
+        Tcur = T32; tdt = LRS_F32;
+      } else {
+        Tcur = To; tdt = LRS_F64;
+      }
+    }
+    // G = W T   (m x tc_cols)  computed as (W^T)^T T
+    double* Gn = (Gcur == Ga) ? Gb : Ga;
+    st = gemm(ctx, prec, m, tc_cols, nI, WT, wdt, m, Tcur, tdt, gc, Gn, 1, 0, wmax);
+    if (st) return st;
+    ctx->ws_top = mark;
     if (reorth) {
       double* Go = (Gn == Ga) ? Gb : Ga;
-      const size_t mark3 = ctx->ws_top;
-      st = orth(ctx, Gn, m, tc, wmax, rtol, Go, wmax, &gc);
+      st = orth(ctx, Gn, m, tc_cols, wmax, rtol, Go, wmax, &gc);
       if (st) return st;
-      ctx->ws_top = mark3;
+      ctx->ws_top = mark;
       Gcur = Go;
     } else {
-      gc = tc;
+      gc = tc_cols;
       Gcur = Gn;
     }
     ldcur = wmax;
-    ctx->ws_top = mark;
   }
   LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(G, ldg * 8, Gcur, ldcur * 8, gc * 8, m, cudaMemcpyDeviceToDevice, ctx->stream));
   *g_cols = gc;
@@ -307,6 +352,8 @@ lrs_status lrs_svd_k(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int6
   size_t need = align256(bsz * (size_t)(r * n));            // B
   need += tsqr_ws(r, n, bsz);
   need += 4 * align256(8 * (size_t)(r * r)) + align256(8 * (size_t)(m * r)) + 65536;
+  if (prec >= LRS_PREC_SPLIT_BF16)
+    need += gemm_tc_workspace(r, m, prec) + gemm_tc_splitk_workspace(r, n, m, ctx->num_sms) + 4096;
   lrs_status st = ws_reserve(ctx, need);
   if (st) return st;
   void* B = ws_alloc(ctx, bsz * (size_t)(r * n));
@@ -316,12 +363,19 @@ lrs_status lrs_svd_k(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int6
   double* sv = (double*)ws_alloc(ctx, 8 * (size_t)r);
   double* Wk = (double*)ws_alloc(ctx, 8 * (size_t)(r * kk));
   double* QT = (double*)ws_alloc(ctx, 8 * (size_t)(m * r));
-  if (!B || !fro2 || !Rm || !Vr || !sv || !Wk || !QT) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd_k)");
-  // (a4) B = Q^T A_f -- the one full read of A_f
-  st = gemm(ctx, prec, r, n, m, Q, LRS_F64, ldq, A, dtype, lda, B, f64, 0, n);
-  if (st) return st;
-  st = launch_fro2(ctx, A, dtype, m, n, lda, fro2);
-  if (st) return st;
+  double* sgn = (double*)ws_alloc(ctx, 8 * (size_t)kk);
+  if (!B || !fro2 || !Rm || !Vr || !sv || !Wk || !QT || !sgn) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd_k)");
+  // (a4) B = Q^T A_f -- the one full read of A_f (||A_f||_F^2 fused on the tensor-core path)
+  if (prec >= LRS_PREC_SPLIT_BF16 && r <= 128) {
+    GemmArgs g{r, n, m, Q, LRS_F64, ldq, A, dtype, lda, B, f64, 0, n, 1.0};
+    st = launch_gemm_tc(ctx, g, prec, fro2);
+    if (st) return st;
+  } else {
+    st = gemm(ctx, prec, r, n, m, Q, LRS_F64, ldq, A, dtype, lda, B, f64, 0, n);
+    if (st) return st;
+    st = launch_fro2(ctx, A, dtype, m, n, lda, fro2);
+    if (st) return st;
+  }
   // (a5) SVD(B): R of B^T, Jacobi on R -> U_B = Vr, s
   st = launch_tsqr(ctx, B, f64, r, n, n, Rm);
   if (st) return st;
@@ -332,13 +386,13 @@ lrs_status lrs_svd_k(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int6
   if (st) return st;
   st = gemm(ctx, LRS_PREC_FP64, kk, m, r, Vr, LRS_F64, r, QT, LRS_F64, m, U, 1, 1, ldu);
   if (st) return st;
-  // V = B^T Vr_k S_k^{-1}
-  st = launch_scale_cols(ctx, Vr, r, r, sv, kk, Wk, kk);
+  // sign convention on U, then V = B^T Vr_k diag(sign) S_k^{-1} carries the same signs
+  st = launch_sign_fix(ctx, U, m, kk, ldu, sgn);
+  if (st) return st;
+  st = launch_scale_cols(ctx, Vr, r, r, sv, sgn, kk, Wk, kk);
   if (st) return st;
   st = gemm(ctx, f64 ? LRS_PREC_FP64 : LRS_PREC_FP32, n, kk, r, B, f64 ? LRS_F64 : LRS_F32, n, Wk,
             LRS_F64, kk, V, f64, 0, ldv);
-  if (st) return st;
-  st = launch_sign_fix(ctx, U, m, kk, ldu, V, f64, n, ldv);
   if (st) return st;
   LRS_CUDA_TRY(ctx, cudaMemcpyAsync(S, sv, 8 * (size_t)kk, cudaMemcpyDeviceToDevice, ctx->stream));
   if (err_est) {
@@ -366,9 +420,8 @@ lrs_status lrs_id_k(lrs_ctx* ctx, const double* Ysk, int64_t m, int64_t l, int64
   if (ldy < l || ldp < k) return lrs_fail(ctx, LRS_EINVAL, "id_k: strides too small");
   LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   size_t need = align256(8 * (size_t)(m * l)) + align256(4 * (size_t)m) +
-                2 * align256(8 * (size_t)(k * m)) + align256(8 * (size_t)(l * k)) +
-                4 * align256(8 * (size_t)m) + align256((size_t)m) + align256(8 * (size_t)l) + 65536 +
-                align256(8 * 4 * 1024);
+                align256(8 * (size_t)(k * m)) + align256(8 * (size_t)(l * k)) + 65536 +
+                cpqr_ws(l, m, k);
   lrs_status st = ws_reserve(ctx, need);
   if (st) return st;
   // Y^T is l x m; its column-major storage is Y's row-major storage.
@@ -410,7 +463,9 @@ lrs_status lrs_gemm_tn(lrs_ctx* ctx, int64_t M, int64_t N, int64_t K, const void
   if (!dtype_ok(x_dtype) || !dtype_ok(a_dtype) || !prec_ok(prec)) return lrs_fail(ctx, LRS_EINVAL, "gemm: bad dtype/prec");
   if (ldx < M || lda < N || ldc < (c_trans ? M : N)) return lrs_fail(ctx, LRS_EINVAL, "gemm: strides too small");
   LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-  lrs_status st = ws_reserve(ctx, 0);
+  lrs_status st = ws_reserve(ctx, prec >= LRS_PREC_SPLIT_BF16
+                                      ? gemm_tc_workspace(M, K, prec) + gemm_tc_splitk_workspace(M, N, K, ctx->num_sms) + 4096
+                                      : 0);
   if (st) return st;
   return gemm(ctx, prec, M, N, K, X, x_dtype, ldx, A, a_dtype, lda, C, c_f64, c_trans, ldc);
 }

@@ -5,13 +5,14 @@
 namespace lrs {
 
 // dst (cols x rows, row stride ldd) = src^T, src rows x cols (row stride lds)
-__global__ void k_transpose(const double* __restrict__ src, int64_t rows, int64_t cols, int64_t lds,
-                            double* __restrict__ dst, int64_t ldd) {
-  __shared__ double tile[32][33];
+template <typename TI, typename TO>
+__global__ void k_transpose(const TI* __restrict__ src, int64_t rows, int64_t cols, int64_t lds,
+                            TO* __restrict__ dst, int64_t ldd) {
+  __shared__ TO tile[32][33];
   const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int64_t r = r0 + i, c = c0 + threadIdx.x;
-    tile[i][threadIdx.x] = (r < rows && c < cols) ? src[r * lds + c] : 0.0;
+    tile[i][threadIdx.x] = (r < rows && c < cols) ? (TO)src[r * lds + c] : (TO)0;
   }
   __syncthreads();
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
@@ -24,7 +25,40 @@ lrs_status launch_transpose(lrs_ctx* ctx, const double* src, int64_t rows, int64
                             double* dst, int64_t ldd) {
   if (rows <= 0 || cols <= 0) return LRS_OK;
   dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
-  k_transpose<<<grid, dim3(32, 8), 0, ctx->stream>>>(src, rows, cols, lds, dst, ldd);
+  k_transpose<double, double><<<grid, dim3(32, 8), 0, ctx->stream>>>(src, rows, cols, lds, dst, ldd);
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
+
+lrs_status launch_transpose32(lrs_ctx* ctx, const float* src, int64_t rows, int64_t cols, int64_t lds,
+                              float* dst, int64_t ldd) {
+  if (rows <= 0 || cols <= 0) return LRS_OK;
+  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+  k_transpose<float, float><<<grid, dim3(32, 8), 0, ctx->stream>>>(src, rows, cols, lds, dst, ldd);
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
+
+// dst (rows x cols, FP32, row stride ldd) = src (FP64, row stride lds), rounded to nearest
+__global__ void k_to_f32(const double* __restrict__ src, int64_t rows, int64_t cols, int64_t lds,
+                         float* __restrict__ dst, int64_t ldd) {
+  const int64_t total = rows * cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / cols, c = e - r * cols;
+    dst[r * ldd + c] = __double2float_rn(src[r * lds + c]);
+  }
+}
+
+lrs_status launch_to_f32(lrs_ctx* ctx, const double* src, int64_t rows, int64_t cols, int64_t lds,
+                         float* dst, int64_t ldd) {
+  const int64_t tot = rows * cols;
+  if (tot <= 0) return LRS_OK;
+  int64_t nb = (tot + 255) / 256;
+  if (nb > (int64_t)ctx->num_sms * 16) nb = (int64_t)ctx->num_sms * 16;
+  k_to_f32<<<(unsigned)nb, 256, 0, ctx->stream>>>(src, rows, cols, lds, dst, ldd);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
   return LRS_OK;
@@ -33,8 +67,7 @@ lrs_status launch_transpose(lrs_ctx* ctx, const double* src, int64_t rows, int64
 // One block per column: find the largest-|entry| of U[:, c] (lowest row on
 // ties); if negative flip U[:, c] and V[:, c].
 __global__ void __launch_bounds__(256) k_sign_fix(double* __restrict__ U, int64_t m, int64_t ldu,
-                                                  void* __restrict__ V, int v_f64, int64_t n,
-                                                  int64_t ldv) {
+                                                  double* __restrict__ sign_out) {
   __shared__ double sv[32];
   __shared__ int64_t si[32];
   __shared__ double s_sign;
@@ -57,43 +90,37 @@ __global__ void __launch_bounds__(256) k_sign_fix(double* __restrict__ U, int64_
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
       if (sv[w] > b || (sv[w] == b && si[w] < bj)) { b = sv[w]; bj = si[w]; }
     s_sign = (bj < m && U[bj * ldu + c] < 0.0) ? -1.0 : 1.0;
+    sign_out[c] = s_sign;
   }
   __syncthreads();
   if (s_sign > 0.0) return;
   for (int64_t i = threadIdx.x; i < m; i += blockDim.x) U[i * ldu + c] = -U[i * ldu + c];
-  if (v_f64) {
-    double* v = reinterpret_cast<double*>(V);
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) v[i * ldv + c] = -v[i * ldv + c];
-  } else {
-    float* v = reinterpret_cast<float*>(V);
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) v[i * ldv + c] = -v[i * ldv + c];
-  }
 }
 
-lrs_status launch_sign_fix(lrs_ctx* ctx, double* U, int64_t m, int64_t k, int64_t ldu, void* V,
-                           int v_f64, int64_t n, int64_t ldv) {
+lrs_status launch_sign_fix(lrs_ctx* ctx, double* U, int64_t m, int64_t k, int64_t ldu, double* sign_out) {
   if (k <= 0) return LRS_OK;
-  k_sign_fix<<<(unsigned)k, 256, 0, ctx->stream>>>(U, m, ldu, V, v_f64, n, ldv);
+  k_sign_fix<<<(unsigned)k, 256, 0, ctx->stream>>>(U, m, ldu, sign_out);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
   return LRS_OK;
 }
 
 __global__ void k_scale_cols(const double* __restrict__ V, int64_t r, int64_t ldv,
-                             const double* __restrict__ s, int64_t k, double* __restrict__ W,
-                             int64_t ldw) {
+                             const double* __restrict__ s, const double* __restrict__ sign, int64_t k,
+                             double* __restrict__ W, int64_t ldw) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= r * k) return;
   const int64_t i = e / k, c = e - i * k;
   const double sc = s[c];
-  W[i * ldw + c] = sc > 0.0 ? V[i * ldv + c] / sc : 0.0;
+  const double sg = sign ? sign[c] : 1.0;
+  W[i * ldw + c] = sc > 0.0 ? sg * V[i * ldv + c] / sc : 0.0;
 }
 
 lrs_status launch_scale_cols(lrs_ctx* ctx, const double* V, int64_t r, int64_t ldv, const double* s,
-                             int64_t k, double* W, int64_t ldw) {
+                             const double* sign, int64_t k, double* W, int64_t ldw) {
   const int64_t tot = r * k;
   if (tot <= 0) return LRS_OK;
-  k_scale_cols<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(V, r, ldv, s, k, W, ldw);
+  k_scale_cols<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(V, r, ldv, s, sign, k, W, ldw);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
   return LRS_OK;

@@ -37,9 +37,9 @@ bool grid_from_abi(const lrs_grid* g, GridDev* o, char* why, size_t nwhy) {
   return true;
 }
 
-template <int KIND>
+template <int KIND, typename OutT>
 __global__ void __launch_bounds__(256) k_sketch(const void* __restrict__ A, int32_t dt, int64_t m,
-                                                int64_t lda, GridDev g, double* __restrict__ Y,
+                                                int64_t lda, GridDev g, OutT* __restrict__ Y,
                                                 int64_t ldy) {
   const int64_t total = m * g.l;
   for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256) k_sketch(const void* __restrict__ A, int3
           for (int64_t x = g.s[0] * xc; x < g.s[0] * (xc + 1); ++x) acc += w * ld_f64(A, dt, base + x);
         }
     }
-    Y[t * ldy + j] = acc;
+    Y[t * ldy + j] = (OutT)acc;
   }
 }
 
@@ -101,9 +101,9 @@ lrs_status launch_sketch(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int
   const int th = 256;
   const int nb = grid_blocks(ctx, m * g.l, th);
   switch (g.kind) {
-    case LRS_INJECT: k_sketch<LRS_INJECT><<<nb, th, 0, ctx->stream>>>(A, dt, m, lda, g, Y, ldy); break;
-    case LRS_FULLWEIGHT: k_sketch<LRS_FULLWEIGHT><<<nb, th, 0, ctx->stream>>>(A, dt, m, lda, g, Y, ldy); break;
-    default: k_sketch<LRS_BLOCKAVG><<<nb, th, 0, ctx->stream>>>(A, dt, m, lda, g, Y, ldy); break;
+    case LRS_INJECT: k_sketch<LRS_INJECT, double><<<nb, th, 0, ctx->stream>>>(A, dt, m, lda, g, Y, ldy); break;
+    case LRS_FULLWEIGHT: k_sketch<LRS_FULLWEIGHT, double><<<nb, th, 0, ctx->stream>>>(A, dt, m, lda, g, Y, ldy); break;
+    default: k_sketch<LRS_BLOCKAVG, double><<<nb, th, 0, ctx->stream>>>(A, dt, m, lda, g, Y, ldy); break;
   }
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
@@ -117,21 +117,45 @@ lrs_status launch_gather(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int
   return launch_sketch(ctx, A, dt, m, lda, gi, W, ldw);
 }
 
+lrs_status launch_gather32(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int64_t lda,
+                           const GridDev& g, float* W, int64_t ldw) {
+  GridDev gi = g;
+  gi.kind = LRS_INJECT;
+  const int nb = grid_blocks(ctx, m * gi.l, 256);
+  k_sketch<LRS_INJECT, float><<<nb, 256, 0, ctx->stream>>>(A, dt, m, lda, gi, W, ldw);
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
+
 // ---------------------------------------------------------------------------
 // ||A||_F^2: per-block FP64 partials in a fixed order, then one block sums
 // them (deterministic for a given device).
 // ---------------------------------------------------------------------------
+// rows are walked by blocks, columns by threads; float4 loads for FP32 rows
+// aligned to 16 B, FP32 partial squares per row segment, FP64 across them.
 __global__ void __launch_bounds__(256) k_fro2_partial(const void* __restrict__ A, int32_t dt,
                                                       int64_t m, int64_t n, int64_t lda,
                                                       double* __restrict__ part) {
   __shared__ double red[32];
   double acc = 0.0;
-  const int64_t total = m * n;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t t = idx / n, j = idx - t * n;
-    const double v = ld_f64(A, dt, t * lda + j);
-    acc = fma(v, v, acc);
+  const bool vec = dt == LRS_F32 && (n % 4 == 0) && (lda % 4 == 0) &&
+                   ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+  for (int64_t t = blockIdx.x; t < m; t += gridDim.x) {
+    if (vec) {
+      const float4* row = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(A) + t * lda);
+      float s = 0.f;
+      for (int64_t j = threadIdx.x; j < n / 4; j += blockDim.x) {
+        const float4 v = __ldg(row + j);
+        s = fmaf(v.x, v.x, s); s = fmaf(v.y, v.y, s); s = fmaf(v.z, v.z, s); s = fmaf(v.w, v.w, s);
+      }
+      acc += (double)s;
+    } else {
+      for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        const double v = ld_f64(A, dt, t * lda + j);
+        acc = fma(v, v, acc);
+      }
+    }
   }
   acc = block_sum(acc, red);
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
@@ -145,9 +169,17 @@ __global__ void k_sum_partials(const double* __restrict__ part, int np, double* 
   if (threadIdx.x == 0) *out = acc;
 }
 
+lrs_status launch_sum(lrs_ctx* ctx, const double* part, int np, double* out) {
+  k_sum_partials<<<1, 256, 0, ctx->stream>>>(part, np, out);
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
+
 lrs_status launch_fro2(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int64_t n,
                        int64_t lda, double* out) {
-  const int nb = ctx->num_sms * 4;
+  int64_t nb64 = m < (int64_t)ctx->num_sms * 8 ? m : (int64_t)ctx->num_sms * 8;
+  const int nb = (int)(nb64 < 1 ? 1 : nb64);
   double* part = (double*)ws_alloc(ctx, sizeof(double) * nb);
   if (!part) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (fro2)");
   k_fro2_partial<<<nb, 256, 0, ctx->stream>>>(A, dt, m, n, lda, part);

@@ -19,7 +19,7 @@
 
 namespace lrs {
 
-constexpr int kTsqrThreads = 512;
+constexpr int kTsqrThreads = 1024;
 constexpr size_t kSmemCap = 200 * 1024;
 
 // tile[i][t] holds column i of the C x r slab (row i of B's chunk), t < C.
@@ -44,24 +44,23 @@ k_tsqr_leaf(const void* __restrict__ B, int b_f64, int64_t r, int64_t n, int64_t
     tile[i * C + t] = v;
   }
   __syncthreads();
+  __shared__ T red[32];
   const int64_t steps = r < C ? r : C;
   for (int64_t i = 0; i < steps; ++i) {
     T* x = tile + i * C;
-    if (wid == 0) {
-      T a = T(0);
-      for (int64_t t = i + lane; t < C; t += 32) a = fma(x[t], x[t], a);
-      a = warp_sum(a);
-      const T alpha = sqrt(a);
-      const T x0 = x[i];
-      const T sgn = x0 >= T(0) ? T(1) : T(-1);
-      const T v0 = x0 + sgn * alpha;
-      // ||v||^2 = ||x||^2 - x0^2 + v0^2
-      const T vn2 = a - x0 * x0 + v0 * v0;
-      const T inv = vn2 > T(0) ? T(1) / sqrt(vn2) : T(0);
-      __syncwarp();
-      for (int64_t t = i + 1 + lane; t < C; t += 32) x[t] *= inv;
-      if (lane == 0) { s_scal[0] = -sgn * alpha; s_scal[1] = v0 * inv; }
-    }
+    // ||x||^2 over the whole block
+    T a = T(0);
+    for (int64_t t = i + threadIdx.x; t < C; t += blockDim.x) a = fma(x[t], x[t], a);
+    a = block_sum(a, red);
+    const T alpha = sqrt(a);
+    const T x0 = x[i];
+    const T sgn = x0 >= T(0) ? T(1) : T(-1);
+    const T v0 = x0 + sgn * alpha;
+    // ||v||^2 = ||x||^2 - x0^2 + v0^2
+    const T vn2 = a - x0 * x0 + v0 * v0;
+    const T inv = vn2 > T(0) ? T(1) / sqrt(vn2) : T(0);
+    for (int64_t t = i + 1 + threadIdx.x; t < C; t += blockDim.x) x[t] *= inv;
+    if (threadIdx.x == 0) { s_scal[0] = -sgn * alpha; s_scal[1] = v0 * inv; }
     __syncthreads();
     const T rii = s_scal[0];
     const T v0n = s_scal[1];

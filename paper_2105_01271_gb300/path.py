@@ -66,9 +66,14 @@ def svd_path(ctx: Context, A: torch.Tensor, dtype: str, grid, k: int, q: int = 0
     gg = grid_of(gram) if (gram is not None and q > 0) else None
     b = bufs or Buffers(m, n, l, k, A.device, prec == LRS_PREC_FP64)
     gc = ctx.power_pass(A, dt, m, n, g, gg, q, 1, rtol, prec, b.Y, l, b.G, l)
-    ldq = b.Q.shape[1]
-    r = ctx.range_find(b.G, m, gc, l, rtol, b.Q, ldq)
-    err, st = ctx.svd_k(A, dt, m, n, n, b.Q, ldq, r, k, prec, b.U, k, b.S, b.V, k)
+    if q > 0:
+        # a re-orthonormalised C-PWR pass ends with QR(G_q): G_q is the basis
+        Qb, ldq, r = b.G, l, gc
+    else:
+        ldq = b.Q.shape[1]
+        r = ctx.range_find(b.G, m, gc, l, rtol, b.Q, ldq)
+        Qb = b.Q
+    err, st = ctx.svd_k(A, dt, m, n, n, Qb, ldq, r, k, prec, b.U, k, b.S, b.V, k)
     kk = min(k, r)
     return SvdResult(b.U[:, :kk], b.S[:kk], b.V[:, :kk], err, r, gc, st)
 

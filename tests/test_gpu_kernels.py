@@ -168,3 +168,54 @@ def test_svd_k_fp64_exact_rank(lrs):
     np.testing.assert_allclose(_np(S), sig, rtol=1e-12)
     np.testing.assert_allclose(_np(U), Uo, atol=1e-10)
     np.testing.assert_allclose(_np(V), Vo, atol=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# tensor-core forms of X^T A.  Splitting x into BF16 pieces leaves |x - sum| <=
+# 2^-8p |x| (p pieces); with the products i + j < p kept and FP32 accumulation
+# over K terms:  |err| <= (c_p + (K + 2) 2^-24) (|X|^T |A|),
+# c_2 = 3 * 2^-16 (two pieces), c_3 = 6 * 2^-24 (three pieces).
+TC_CASES = [
+    # (M, N, K, a_dtype)
+    (1, 1, 1, "f32"), (72, 300, 129, "f32"), (128, 128, 64, "f32"), (200, 77, 513, "f32"),
+    (72, 4099, 2000, "f32"), (300, 260, 70, "f64"), (64, 1000, 333, "bf16"),
+    (700, 72, 9000, "f32"),          # few output tiles, long K: split-K with a fixed-order reduction
+]
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("M,N,K,adt", TC_CASES)
+@pytest.mark.parametrize("trans,c64", [(0, 0), (1, 1)])
+def test_gemm_tc_parity(lrs, prec, M, N, K, adt, trans, c64):
+    from paper_2105_01271_gb300.binding import DTYPE
+    torch = _torch()
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    X = rng.standard_normal((K, M)) * np.exp(rng.uniform(-3, 3, (K, 1)))
+    A64 = rng.standard_normal((K, N))
+    A = synth.fields._store(A64, adt)
+    Ae = oracle.sketch.__globals__["as_f64"](A)
+    ref = X.T @ Ae
+    shape = (N, M) if trans else (M, N)
+    Cd = torch.full(shape, np.nan, dtype=torch.float64 if c64 else torch.float32, device="cuda")
+    lrs.gemm_tn(M, N, K, _dev(X), 0, M, _dev(A), DTYPE[adt], N, Cd, c64, trans, shape[1], prec)
+    got = _np(Cd).astype(np.float64)
+    got = got.T if trans else got
+    mag = np.abs(X).T @ np.abs(Ae)
+    cp = 3 * 2.0 ** -16 if prec == 2 else 6 * 2.0 ** -24
+    out_round = 0.0 if c64 else 2.0 ** -24
+    bound = (cp + (K + 2) * 2.0 ** -24 + out_round) * mag
+    assert np.all(np.isfinite(got))
+    assert np.all(np.abs(got - ref) <= bound + 1e-300), np.max(np.abs(got - ref) / (bound + 1e-300))
+
+
+def test_gemm_tc_deterministic(lrs):
+    torch = _torch()
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((700, 90))
+    A = rng.standard_normal((700, 3000)).astype(np.float32)
+    outs = []
+    for _ in range(3):
+        Cd = torch.empty((90, 3000), dtype=torch.float32, device="cuda")
+        lrs.gemm_tn(90, 3000, 700, _dev(X), 0, 90, _dev(A), 1, 3000, Cd, 0, 0, 3000, 2)
+        outs.append(_np(Cd))
+    assert all(np.array_equal(outs[0], o) for o in outs)
