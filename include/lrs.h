@@ -183,6 +183,28 @@ lrs_status lrs_gemm_tn(lrs_ctx* ctx, int64_t M, int64_t N, int64_t K,
                        const void* A, int32_t a_dtype, int64_t lda,
                        void* C, int32_t c_f64, int32_t c_trans, int64_t ldc, int32_t prec);
 
+/*
+ * lrs_id_k_static -- lrs_id_k for callers that cannot allocate device memory
+ * at call time (code inside a CUDA-graph capture or a real-time loop where
+ * cudaMalloc would stall or is not allowed, or a host framework that owns
+ * every allocation).  The paper has no counterpart: it is a deployment
+ * variant of the same row ID.
+ *   Same arguments, results and statuses as lrs_id_k.  All scratch lives in
+ *   one file-scope device array of LRS_ID_STATIC_SCRATCH_BYTES (32 MiB) that
+ *   every GPU loading the library keeps until the process exits; the call
+ *   makes no cudaMalloc/cudaFree and calls no allocating library routine.
+ *   Scratch needed: about 8*m*l + 16*S*m + 16*k*m + 8*k*l bytes (S = SM
+ *   count); a request above the array's size is rejected with LRS_EINVAL
+ *   before any launch.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   Every call shares the array: calls whose GPU work overlaps (two streams
+ *   or two contexts at once) race.  The call synchronises ctx's stream.
+ */
+#define LRS_ID_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+lrs_status lrs_id_k_static(lrs_ctx* ctx, const double* Ysk, int64_t m, int64_t l, int64_t ldy, int32_t k,
+                           int32_t* J, double* P, int64_t ldp, double* err_est);
+
 /* Number of kernel launches this context has issued (for launch accounting). */
 int64_t lrs_launch_count(const lrs_ctx* ctx);
 

@@ -71,6 +71,8 @@ _SIG = {
                             C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
     "lrs_id_k": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
                            C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
+    "lrs_id_k_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32,
+                                  C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
     "lrs_gemm_tn": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_int32,
                               C.c_int64, C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_int32,
                               C.c_int32, C.c_int64, C.c_int32]),
@@ -175,6 +177,12 @@ class Context:
         err = C.c_double(0.0)
         st = self._check(self.lib.lrs_id_k(self.h, _ptr(Ysk), m, l, ldy, k, _ptr(J), _ptr(P), ldp,
                                            C.byref(err)), allow_rank=True)
+        return err.value, st
+
+    def id_k_static(self, Ysk, m, l, ldy, k, J, P, ldp):
+        err = C.c_double(0.0)
+        st = self._check(self.lib.lrs_id_k_static(self.h, _ptr(Ysk), m, l, ldy, k, _ptr(J), _ptr(P), ldp,
+                                                  C.byref(err)), allow_rank=True)
         return err.value, st
 
     def gemm_tn(self, M, N, K, X, x_dtype, ldx, A, a_dtype, lda, Cm, c_f64, c_trans, ldc, prec):

@@ -299,6 +299,28 @@ __global__ void __launch_bounds__(kCpqrThreads, 1) k_cpqr(CpqrState s) {
   }
 }
 
+// Bytes launch_cpqr takes from the workspace for these sizes (the same block
+// count, slab placement and 256-byte rounding as the launch below).
+size_t cpqr_scratch_bytes(int64_t p, int64_t c, int64_t kmax, int num_sms) {
+  auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+  int64_t nb = (p * c + 2047) / 2048;
+  if (nb > num_sms) nb = num_sms;
+  if (nb > (p + 3) / 4) nb = (p + 3) / 4;
+  if (nb < 1) nb = 1;
+  const int64_t rows_b = (p + nb - 1) / nb;
+  nb = (p + rows_b - 1) / rows_b;
+  const int64_t lds = rows_b | 1;
+  const int64_t region = lds * c + rows_b + c + (c + (c * 8 + 7) / 8 + 1);
+  size_t b = 0;
+  if (sizeof(double) * (size_t)region > 200 * 1024) b += a256(sizeof(double) * (size_t)(nb * region));
+  b += 2 * a256(sizeof(double) * (size_t)(nb * c));
+  b += 2 * a256(sizeof(double) * (size_t)c);
+  b += a256(sizeof(double) * (size_t)(kmax > 0 ? kmax : 1) * c);
+  b += a256(sizeof(double) * (size_t)nb) + 2 * a256(sizeof(int32_t) * (size_t)nb);
+  b += 256;
+  return b;
+}
+
 lrs_status launch_cpqr(lrs_ctx* ctx, double* M, int64_t p, int64_t c, int64_t ldm,
                        int64_t kmax, double rtol, const CpqrOut& o) {
   if (!ctx->coop_ok) return lrs_fail(ctx, LRS_ECUDA, "device lacks cooperative launch");

@@ -84,6 +84,8 @@ struct CpqrOut {
 };
 lrs_status launch_cpqr(lrs_ctx* ctx, double* M, int64_t p, int64_t c, int64_t ldm,
                        int64_t kmax, double rtol, const CpqrOut& o);
+// exact workspace bytes launch_cpqr allocates for these sizes
+size_t cpqr_scratch_bytes(int64_t p, int64_t c, int64_t kmax, int num_sms);
 // Q (p x r, row-major ldq) = H_0 ... H_{r-1} [I_r; 0]
 lrs_status launch_form_q(lrs_ctx* ctx, const double* V, int64_t p, int64_t r,
                          double* Q, int64_t ldq);
