@@ -51,6 +51,7 @@ struct CpqrState {
   int64_t region;       // doubles per block region: lds*c (slab) + rows_b (v) + c (sums)
   int slab_in_smem;
   int redundant;        // 1: every block reduces every column (2 barriers per step)
+  int team;             // threads per column in the update and dot phases (1..8, power of 2)
 };
 
 __device__ __forceinline__ bool better(double a, int pa, double b, int pb) {
@@ -113,6 +114,29 @@ __device__ __forceinline__ void warp_sum_blocks_n(const double* part, int64_t c,
   for (int k = 0; k < NC; ++k) out[k] = warp_sum(acc[k]);
 }
 
+// Sum of part[bb * c + cc] over the nb blocks by the 4 lanes (q4 = 0..3) of
+// one column: lane q4 takes bb = q4, q4+4, ... with four loads in flight, then
+// two shuffles.  nb - 1 FP64 additions per column, the same order everywhere.
+// All 32 lanes of the warp must call it (the shuffles use the full mask).
+__device__ __forceinline__ double sum4_blocks(const double* part, int64_t c, int64_t cc, bool valid, int nb,
+                                              int q4) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  if (valid) {
+    int bb = q4;
+    for (; bb + 12 < nb; bb += 16) {
+      a0 += __ldcg(part + (int64_t)bb * c + cc);
+      a1 += __ldcg(part + (int64_t)(bb + 4) * c + cc);
+      a2 += __ldcg(part + (int64_t)(bb + 8) * c + cc);
+      a3 += __ldcg(part + (int64_t)(bb + 12) * c + cc);
+    }
+    for (; bb < nb; bb += 4) a0 += __ldcg(part + (int64_t)bb * c + cc);
+  }
+  double a = (a0 + a1) + (a2 + a3);
+  a += __shfl_xor_sync(0xffffffffu, a, 1);
+  a += __shfl_xor_sync(0xffffffffu, a, 2);
+  return a;
+}
+
 __global__ void __launch_bounds__(kCpqrThreads, 1) k_cpqr(CpqrState s) {
   extern __shared__ double smem_d[];
   __shared__ double sv[32];
@@ -148,6 +172,17 @@ __global__ void __launch_bounds__(kCpqrThreads, 1) k_cpqr(CpqrState s) {
   }
   __syncthreads();
 
+  // Threads of one column "team" share its rows in (F) and (P); teams live
+  // inside one warp (T divides 32), so team shuffles and syncs use a team mask.
+  const int T = s.team;
+  const int tm = threadIdx.x & (T - 1);
+  const int team = threadIdx.x / T, nteams = blockDim.x / T;
+  const unsigned tmask = (T == 32 ? 0xffffffffu : ((1u << T) - 1u)) << (lane & ~(T - 1));
+  auto team_sum = [&](double v) {
+    for (int o = 1; o < T; o <<= 1) v += __shfl_xor_sync(tmask, v, o);
+    return v;
+  };
+
   int64_t j = 0;
   double top = 0.0;
   for (;; ++j) {
@@ -156,21 +191,28 @@ __global__ void __launch_bounds__(kCpqrThreads, 1) k_cpqr(CpqrState s) {
       const int64_t i0 = max(r_lo, j - 1) - r_lo;
       const int64_t in = max(r_lo, j) - r_lo;
       const bool upd = j > 0;
-      const bool own_prev = upd && (j - 1) >= r_lo && (j - 1) < r_hi;
-      const bool own_cur = j >= r_lo && j < r_hi;
-      for (int64_t cc = threadIdx.x; cc < s.c; cc += blockDim.x) {
+      const int64_t lprev = (upd && (j - 1) >= r_lo && (j - 1) < r_hi) ? (j - 1) - r_lo : -1;
+      const int64_t lcur = (j >= r_lo && j < r_hi) ? j - r_lo : -1;
+      for (int64_t cc = team; cc < s.c; cc += nteams) {
         double nrm = 0.0;
         double* col = slab + cc * s.lds;
         if (!done[cc]) {
           if (upd) {
             const double tw = 2.0 * (s.redundant ? sums[cc] : __ldcg(s.colsum + cc));
-            for (int64_t i = i0; i < nr; ++i) col[i] = fma(-tw, vloc[i], col[i]);
-            if (own_prev) s.Rphys[(j - 1) * s.c + cc] = col[(j - 1) - r_lo];
+            for (int64_t i = i0 + tm; i < nr; i += T) {
+              const double x = fma(-tw, vloc[i], col[i]);
+              col[i] = x;
+              if (i == lprev) s.Rphys[(j - 1) * s.c + cc] = x;
+            }
+            __syncwarp(tmask);
           }
-          for (int64_t i = in; i < nr; ++i) nrm = fma(col[i], col[i], nrm);
+          for (int64_t i = in + tm; i < nr; i += T) nrm = fma(col[i], col[i], nrm);
         }
-        pn[cc] = nrm;
-        if (own_cur) s.rowbuf[cc] = col[j - r_lo];
+        nrm = team_sum(nrm);
+        if (tm == 0) {
+          pn[cc] = nrm;
+          if (lcur >= 0) s.rowbuf[cc] = col[lcur];
+        }
       }
     }
     if (!grid_sync(s.bar)) return;
@@ -178,16 +220,12 @@ __global__ void __launch_bounds__(kCpqrThreads, 1) k_cpqr(CpqrState s) {
     // ---- (N) norms^2 and the best candidate -------------------------------
     {
       double bv = -1.0; int bp = 0x7fffffff, bf = -1;
-      for (int64_t cc0 = c_lo + wid; cc0 < c_hi; cc0 += 4 * nw) {
-        const int ncol = (int)min((int64_t)4, (c_hi - cc0 + nw - 1) / nw);
-        double a4[4];
-        warp_sum_blocks_n<4>(s.part_n, s.c, cc0, nw, ncol, nb, lane, a4);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int64_t cc = cc0 + k * nw;
-          if (k >= ncol || done[cc]) continue;
-          const double a = a4[k];
-          if (lane == 0) {
+      const int q4 = lane & 3, slot = lane >> 2;
+      for (int64_t base = c_lo + wid * 8; base < c_hi; base += (int64_t)nw * 8) {
+        const int64_t cc = base + slot;
+        const double a = sum4_blocks(s.part_n, s.c, cc, cc < c_hi, nb, q4);
+        if (cc < c_hi && !done[cc]) {
+          if (q4 == 0) {
             if (s.redundant) sums[cc] = a;
             else s.colsum[cc] = a;
           }
@@ -249,29 +287,27 @@ __global__ void __launch_bounds__(kCpqrThreads, 1) k_cpqr(CpqrState s) {
       }
       __syncthreads();
       const int64_t i0 = max(r_lo, j) - r_lo;
-      for (int64_t cc = threadIdx.x; cc < s.c; cc += blockDim.x) {
+      for (int64_t cc = team; cc < s.c; cc += nteams) {
         double d = 0.0;
         if (!done[cc]) {
           const double* col = slab + cc * s.lds;
-          for (int64_t i = i0; i < nr; ++i) d = fma(vloc[i], col[i], d);
+          for (int64_t i = i0 + tm; i < nr; i += T) d = fma(vloc[i], col[i], d);
         }
-        pd[cc] = d;
+        d = team_sum(d);
+        if (tm == 0) pd[cc] = d;
       }
     }
     if (!grid_sync(s.bar)) return;
 
     // ---- (D) dots ------------------------------------------------------------
-    for (int64_t cc0 = c_lo + wid; cc0 < c_hi; cc0 += 4 * nw) {
-      const int ncol = (int)min((int64_t)4, (c_hi - cc0 + nw - 1) / nw);
-      double a4[4];
-      warp_sum_blocks_n<4>(s.part_d, s.c, cc0, nw, ncol, nb, lane, a4);
-      if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          if (k >= ncol) continue;
-          const int64_t cc = cc0 + k * nw;
-          if (s.redundant) sums[cc] = a4[k];
-          else s.colsum[cc] = a4[k];
+    {
+      const int q4 = lane & 3, slot = lane >> 2;
+      for (int64_t base = c_lo + wid * 8; base < c_hi; base += (int64_t)nw * 8) {
+        const int64_t cc = base + slot;
+        const double a = sum4_blocks(s.part_d, s.c, cc, cc < c_hi, nb, q4);
+        if (cc < c_hi && q4 == 0) {
+          if (s.redundant) sums[cc] = a;
+          else s.colsum[cc] = a;
         }
       }
     }
@@ -339,6 +375,7 @@ lrs_status launch_cpqr(lrs_ctx* ctx, double* M, int64_t p, int64_t c, int64_t ld
   // per block: slab, v rows, column sums, then pos_of/phys_at (int32) and done (bytes)
   s.region = s.lds * c + s.rows_b + c + (c + (c * 8 + 7) / 8 + 1);
   s.redundant = (nb * c <= 24576) ? 1 : 0;
+  s.team = c >= 512 ? 1 : (c >= 256 ? 2 : (c >= 128 ? 4 : 8));
   const size_t slab_bytes = sizeof(double) * (size_t)s.region;
   s.slab_in_smem = slab_bytes <= 200 * 1024 ? 1 : 0;
   const size_t dyn = s.slab_in_smem ? slab_bytes : 0;
