@@ -179,7 +179,9 @@ def run_ours(args, rank, world):
         rtol = args.rtol
     prec_map = {"fp64": binding.LRS_PREC_FP64, "fp32": binding.LRS_PREC_FP32,
                 "split_bf16": binding.LRS_PREC_SPLIT_BF16, "bf16x3": binding.LRS_PREC_BF16X3}
-    prec_name = args.prec if args.prec != "auto" else ("fp64" if w.dtype == "f64" else "fp32")
+    # default: FP64 data runs the FP64 path; FP32/BF16 data runs the precision
+    # form (split-BF16 tensor-core products, FP64 QR / small SVD / P solve)
+    prec_name = args.prec if args.prec != "auto" else ("fp64" if w.dtype == "f64" else "split_bf16")
     prec = prec_map[prec_name]
 
     A_np = synth.make_workload(w)
@@ -329,6 +331,33 @@ def run_ours(args, rank, world):
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_ms = float(te.item())
 
+    # ---- the plain FP32 GPU method on the same matrix, for comparison ----
+    plain = None
+    if prec in (binding.LRS_PREC_SPLIT_BF16, binding.LRS_PREC_BF16X3) and w.dtype != "f64":
+        pb = path.Buffers(w.m, w.n, w.grid.l, w.k, A_d.device, False)
+
+        def pstep():
+            a = path.svd_path(ctx, A_d, w.dtype, w.grid, w.k, q=w.q, gram=w.gram, rtol=rtol,
+                              prec=binding.LRS_PREC_FP32, bufs=pb)
+            b = path.id_path(ctx, A_d, w.dtype, w.grid, w.k, q=w.q, gram=w.gram, rtol=rtol,
+                             prec=binding.LRS_PREC_FP32, bufs=pb)
+            return a, b
+        with torch.cuda.stream(stream):
+            pstep()
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            nps = 3
+            for _ in range(nps):
+                ps_, pd_ = pstep()
+            g1.record(stream)
+        stream.synchronize()
+        pms = g0.elapsed_time(g1) / nps
+        plain = {"prec": "fp32", "value": 1e3 / pms, "ms_per_step": pms, "steps": nps,
+                 "err_est_svd": ps_.err_est, "err_est_id": pd_.err_est, "r": ps_.r,
+                 "speedup_of_headline": (1e3 / ms) / (1e3 / pms),
+                 "err_est_svd_rel_diff": abs(s.err_est / ps_.err_est - 1.0) if ps_.err_est else None}
+        del pb
+
     if rank != 0:
         return
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -340,6 +369,8 @@ def run_ours(args, rank, world):
                    "d2h_bytes_per_step": int(d2h)},
            "result": {"err_est_svd": s.err_est, "r": s.r, "err_est_id": d.err_est},
            "phases_ms": phases}
+    if plain is not None:
+        out["plain_fp32_gpu"] = plain
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(w, rtol)
     print(json.dumps(out), flush=True)

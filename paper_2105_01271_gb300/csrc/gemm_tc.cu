@@ -21,6 +21,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "tc_ptx.cuh"
+#include "bf16_split.cuh"
 
 #include <cuda_bf16.h>
 
@@ -34,50 +35,6 @@ constexpr int TBK = 64;           // K per stage (one 128-byte swizzle row of BF
 constexpr int kPieceBytes = TBM * TBK * 2;   // 16 KB per operand piece per stage
 constexpr int kConvWarps = 8;
 constexpr int kThreads = (kConvWarps + 2) * 32;
-
-// ---------------------------------------------------------------------------
-// splitting into BF16 pieces
-// ---------------------------------------------------------------------------
-template <int S>
-__device__ __forceinline__ void split_f32(float a, __nv_bfloat16 (&p)[S]) {
-  float r = a;
-#pragma unroll
-  for (int i = 0; i < S; ++i) {
-    p[i] = __float2bfloat16_rn(r);
-    r = r - __bfloat162float(p[i]);
-  }
-}
-template <int S>
-__device__ __forceinline__ void split_f64(double a, __nv_bfloat16 (&p)[S]) {
-  double r = a;
-#pragma unroll
-  for (int i = 0; i < S; ++i) {
-    p[i] = __float2bfloat16_rn((float)r);
-    r = r - (double)__bfloat162float(p[i]);
-  }
-}
-
-template <int S>
-__device__ __forceinline__ void split_any(const void* base, int32_t dt, int64_t idx, bool valid,
-                                          __nv_bfloat16 (&p)[S]) {
-  if (!valid) {
-#pragma unroll
-    for (int i = 0; i < S; ++i) p[i] = __float2bfloat16_rn(0.f);
-    return;
-  }
-  if (dt == LRS_F64) {
-    split_f64<S>(reinterpret_cast<const double*>(base)[idx], p);
-  } else if (dt == LRS_F32) {
-    split_f32<S>(reinterpret_cast<const float*>(base)[idx], p);
-  } else {
-    const unsigned short b = reinterpret_cast<const unsigned short*>(base)[idx];
-    split_f32<S>(__uint_as_float(((unsigned)b) << 16), p);
-  }
-}
-
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
 
 // ---------------------------------------------------------------------------
 // X (K x M, row-major) -> pieces in the shared-memory image:
@@ -528,7 +485,9 @@ static lrs_status run_tc(lrs_ctx* ctx, const GemmArgs& a, double* fro2_out) {
 size_t gemm_tc_workspace(int64_t M, int64_t K, int prec) {
   const int64_t Mt = (M + TBM - 1) / TBM, Kt = (K + TBK - 1) / TBK;
   const int sx = prec == LRS_PREC_BF16X3 ? 3 : 2;
-  return (size_t)(Mt * Kt * sx) * kPieceBytes + 1024 + 512;
+  const size_t generic = (size_t)(Mt * Kt * sx) * kPieceBytes + 1024 + 512;
+  const size_t narrow = apass_workspace(M, K, prec);
+  return generic > narrow ? generic : narrow;
 }
 
 lrs_status launch_gemm_tc(lrs_ctx* ctx, const GemmArgs& a, int prec, double* fro2_out) {
@@ -537,6 +496,7 @@ lrs_status launch_gemm_tc(lrs_ctx* ctx, const GemmArgs& a, int prec, double* fro
   const bool three = prec == LRS_PREC_BF16X3;
   if (prec != LRS_PREC_SPLIT_BF16 && !three)
     return lrs_fail(ctx, LRS_EINVAL, "gemm: precision mode %d is not a tensor-core mode", prec);
+  if (apass_eligible(a, prec)) return launch_apass(ctx, a, prec, fro2_out);
   switch (a.adt) {
     case LRS_F32: return three ? run_tc<LRS_F32, 3, 3>(ctx, a, fro2_out) : run_tc<LRS_F32, 2, 2>(ctx, a, fro2_out);
     case LRS_F64: return three ? run_tc<LRS_F64, 3, 3>(ctx, a, fro2_out) : run_tc<LRS_F64, 2, 2>(ctx, a, fro2_out);

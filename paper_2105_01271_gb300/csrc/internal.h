@@ -66,6 +66,12 @@ struct GemmArgs {
 lrs_status launch_gemm_simt(lrs_ctx* ctx, const GemmArgs& a, int fp64);
 // fro2_out (device, may be NULL): also ||A||_F^2 of the operand A, fused (M <= 128 only)
 lrs_status launch_gemm_tc(lrs_ctx* ctx, const GemmArgs& a, int prec, double* fro2_out = nullptr);
+// apass_tc.cu: the same product for a narrow X (M <= 256) and a wide FP32/BF16
+// A, with A's slabs staged by TMA.  launch_gemm_tc dispatches here whenever
+// apass_eligible holds.
+bool apass_eligible(const GemmArgs& a, int prec);
+size_t apass_workspace(int64_t M, int64_t K, int prec);
+lrs_status launch_apass(lrs_ctx* ctx, const GemmArgs& a, int prec, double* fro2_out);
 // workspace bytes the tensor-core path needs for an M x K operand X (0 for SIMT modes)
 size_t gemm_tc_workspace(int64_t M, int64_t K, int prec);
 // extra workspace of the split-K partial sums for an M x N x K product (0 when not split)

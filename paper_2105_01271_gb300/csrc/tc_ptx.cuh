@@ -1,5 +1,6 @@
 // Inline-PTX building blocks for the sm_103a tensor-core kernels:
-// mbarriers with bounded waits, 1-D bulk copies, TMEM allocation and loads,
+// mbarriers with bounded waits, 1-D bulk and 2-D tensor (TMA) copies, TMEM
+// allocation and loads,
 // tcgen05.mma (kind::f16, BF16 in, FP32 accumulate) and its descriptors.
 #pragma once
 #include <cuda_runtime.h>
@@ -75,6 +76,21 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
           smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+
+// 2-D tiled TMA load of one box at element coordinates (x innermost, y) of
+// the tensor map `map` (a __grid_constant__ kernel parameter) into shared
+// memory, completing on an mbarrier.  x * element size must be a multiple of
+// 16 bytes; boxes that run past the tensor's edge are zero-filled.
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* map, int32_t x, int32_t y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void prefetch_tensormap(const void* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
 // generic-proxy shared-memory writes -> visible to the tensor core (async proxy)

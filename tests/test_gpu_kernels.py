@@ -180,6 +180,9 @@ TC_CASES = [
     (1, 1, 1, "f32"), (72, 300, 129, "f32"), (128, 128, 64, "f32"), (200, 77, 513, "f32"),
     (72, 4099, 2000, "f32"), (300, 260, 70, "f64"), (64, 1000, 333, "bf16"),
     (700, 72, 9000, "f32"),          # few output tiles, long K: split-K with a fixed-order reduction
+    # narrow X, wide 16-B-aligned A: the TMA-staged A-pass kernel (ragged dof and snapshot tails)
+    (72, 4100, 2000, "f32"), (1, 256, 3, "f32"), (250, 1000, 200, "f32"), (16, 1032, 97, "bf16"),
+    (256, 384, 64, "bf16"),
 ]
 
 
