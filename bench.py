@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--rtol", type=float, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--phases", action="store_true", help="print a per-call time breakdown to stderr")
+    p.add_argument("--no-compare", action="store_true", help="skip the plain FP32 GPU comparison run")
     return p.parse_args()
 
 
@@ -333,7 +334,8 @@ def run_ours(args, rank, world):
 
     # ---- the plain FP32 GPU method on the same matrix, for comparison ----
     plain = None
-    if prec in (binding.LRS_PREC_SPLIT_BF16, binding.LRS_PREC_BF16X3) and w.dtype != "f64":
+    if (prec in (binding.LRS_PREC_SPLIT_BF16, binding.LRS_PREC_BF16X3) and w.dtype != "f64"
+            and not args.no_compare):
         pb = path.Buffers(w.m, w.n, w.grid.l, w.k, A_d.device, False)
 
         def pstep():

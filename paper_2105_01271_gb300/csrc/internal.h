@@ -99,6 +99,18 @@ lrs_status launch_form_q(lrs_ctx* ctx, const double* V, int64_t p, int64_t r,
 lrs_status launch_id_coeffs(lrs_ctx* ctx, const double* R, int64_t k, int64_t m,
                             const int32_t* perm, int32_t* J, double* P, int64_t ldp);
 
+// orth_gram.cu ------------------------------------------------------------------
+// Orthonormal basis of a tall-skinny M (p x c row-major, p >= 4c, c <= 128)
+// by pivoted Cholesky of the FP64 Gram (CPQR's pivots and stop rule) and one
+// Cholesky-QR refinement.  Only for rtol >= kOrthGramRtolMin (the Gram squares
+// the condition number).  Returns LRS_ERANK (nothing reported) when the
+// refinement breaks down; the caller then runs Householder CPQR.  Synchronises.
+constexpr double kOrthGramRtolMin = 1e-6;
+bool orth_gram_eligible(int64_t p, int64_t c, double rtol);
+size_t orth_gram_ws(int64_t p, int64_t c, int num_sms);
+lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldm, double rtol,
+                            double* Q, int64_t ldq, int64_t* r_out);
+
 // svd_small.cu ------------------------------------------------------------------
 // R factor (r x r, row-major) of B^T where B is r x n row-major in FP32 or FP64.
 lrs_status launch_tsqr(lrs_ctx* ctx, const void* B, int b_f64, int64_t r, int64_t n,

@@ -79,16 +79,20 @@ static size_t cpqr_ws(int64_t p, int64_t c, int64_t kmax) {
   return b + 4096;
 }
 
-// bytes of workspace one orthonormalisation of a p x c matrix needs
-static size_t orth_ws(int64_t p, int64_t c) {
+// bytes of workspace one orthonormalisation of a p x c matrix needs (either
+// route: the Gram route's buffers are released before a CPQR fallback)
+static size_t orth_ws(int64_t p, int64_t c, int num_sms) {
   const int64_t kmax = p < c ? p : c;
+  // the Gram route only runs for c <= 128 (c here may be an upper bound)
+  const size_t g = orth_gram_ws(p, c < 128 ? c : 128, num_sms);
   size_t b = 0;
   b += align256(8 * (size_t)(p * c));            // column-major copy
   b += align256(4 * (size_t)c);                  // perm
   b += align256(8 * (size_t)(kmax * c));         // R
   b += align256(8 * (size_t)(p * kmax));         // V
   b += 2 * 256;                                  // scalars
-  return b + cpqr_ws(p, c, kmax);
+  b += cpqr_ws(p, c, kmax);
+  return b > g ? b : g;
 }
 
 // Orthonormal basis of the numerical range of Min (p x c, row-major ldi):
@@ -96,6 +100,13 @@ static size_t orth_ws(int64_t p, int64_t c) {
 static lrs_status orth(lrs_ctx* ctx, const double* Min, int64_t p, int64_t c, int64_t ldi,
                        double rtol, double* Q, int64_t ldq, int64_t* r_out) {
   const int64_t kmax = p < c ? p : c;
+  if (orth_gram_eligible(p, c, rtol)) {
+    // tall-skinny: pivoted Cholesky of the Gram (same pivots and stop rule)
+    const size_t mark = ctx->ws_top;
+    lrs_status gs = launch_orth_gram(ctx, Min, p, c, ldi, rtol, Q, ldq, r_out);
+    ctx->ws_top = mark;
+    if (gs != LRS_ERANK) return gs;
+  }
   double* Mc = (double*)ws_alloc(ctx, 8 * (size_t)(p * c));
   CpqrOut o{};
   o.perm = (int32_t*)ws_alloc(ctx, 4 * (size_t)c);
@@ -195,7 +206,7 @@ lrs_status lrs_range_find(lrs_ctx* ctx, const double* G, int64_t m, int64_t l, i
   if (ldg < l || ldq < (m < l ? m : l)) return lrs_fail(ctx, LRS_EINVAL, "range_find: ldg/ldq too small");
   if (!(rtol >= 0.0) || rtol >= 1.0) return lrs_fail(ctx, LRS_EINVAL, "range_find: rtol=%g not in [0,1)", rtol);
   LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-  lrs_status st = ws_reserve(ctx, orth_ws(m, l));
+  lrs_status st = ws_reserve(ctx, orth_ws(m, l, ctx->num_sms));
   if (st) return st;
   return orth(ctx, G, m, l, ldg, rtol, Q, ldq, r_out);
 }
@@ -233,7 +244,7 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
     need += align256(8 * (size_t)(nI * wmax)) + 2 * align256(8 * (size_t)(m * wmax));
     need += align256(8 * (size_t)(nI * wmax));                        // orthonormal T
     if (tc) need += align256(4 * (size_t)(nI * wmax)) + align256(4 * (size_t)(m * wmax));  // FP32 operands
-    const size_t o1 = orth_ws(m, l), o2 = orth_ws(nI, wmax);
+    const size_t o1 = orth_ws(m, l, ctx->num_sms), o2 = orth_ws(nI, wmax, ctx->num_sms);
     size_t inner = o1 > o2 ? o1 : o2;
     if (tc) {
       const size_t t1 = gemm_tc_workspace(nI, m, prec) + gemm_tc_splitk_workspace(nI, wmax, m, ctx->num_sms);

@@ -1,0 +1,339 @@
+// Orthonormal basis of a TALL-SKINNY p x c matrix M (p >= 4c, c <= 128) with
+// the rank-revealing truncation of the paper's QR(.) (Algs. 2/3/7), without a
+// p-row Householder sweep per pivot:
+//
+//   1. G = M^T M in FP64 (split over row blocks, fixed-order sum).
+//   2. Pivoted Cholesky of G: G(piv, piv) = R^T R.  Column pivoting of M by
+//      largest remaining 2-norm depends on M only through G (the remaining
+//      norm^2 of a column is the diagonal of the Schur complement), so the
+//      pivots, the stop step r (|R_jj| <= rtol |R_00|) and |R_jj| are those of
+//      Householder CPQR in exact arithmetic; ties go to the lowest current
+//      position with the same swap rule as cpqr.cu.
+//   3. Q_1 = M(:, piv[0:r]) R_11^{-1}   (row-wise triangular solve).
+//   4. One refinement (Cholesky-QR2): G_2 = Q_1^T Q_1 = R_2^T R_2,
+//      Q = Q_1 R_2^{-1}.  Q spans M(:, piv[0:r]); its R factor
+//      (R_2 R_11) has a positive diagonal.
+//
+// Forming G squares the condition number, so this route is only taken when
+// rtol^2 stays far above the FP64 rounding of G (rtol >= 1e-6); otherwise the
+// Householder CPQR in cpqr.cu runs.
+#include "common.cuh"
+#include "internal.h"
+
+namespace lrs {
+
+namespace {
+
+constexpr int kGramRows = 32;           // rows of M staged per pass
+constexpr int kMaxC = 128;
+
+// packed upper-triangle index e -> (i, j), row i holding entries (i, i..c-1)
+__device__ __forceinline__ void tri_ij(int e, int c, int& i, int& j) {
+  int ii = 0, base = 0;
+  while (base + (c - ii) <= e) { base += c - ii; ++ii; }
+  i = ii;
+  j = ii + (e - base);
+}
+
+// This block's rows' contribution to the upper triangle of M^T M.  Entries
+// are dealt round-robin to the 256 threads (KPER per thread, fully unrolled,
+// so every lane of every warp keeps the FP64 pipes busy); packed layout
+// part[blockIdx.x * ntri + e].
+template <int KPER>
+__global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__ M, int64_t p, int c,
+                                                      int64_t ldm, int64_t rows_b, double* __restrict__ part) {
+  extern __shared__ double tile[];                 // kGramRows x c
+  const int ntri = c * (c + 1) / 2;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_b;
+  const int64_t r1 = min(p, r0 + rows_b);
+  double acc[KPER];
+  int ii[KPER], jj[KPER];
+#pragma unroll
+  for (int q = 0; q < KPER; ++q) {
+    const int e = threadIdx.x + q * 256;
+    acc[q] = 0.0;
+    if (e < ntri) tri_ij(e, c, ii[q], jj[q]);
+    else { ii[q] = 0; jj[q] = 0; }
+  }
+  for (int64_t a0 = r0; a0 < r1; a0 += kGramRows) {
+    const int nr = (int)min((int64_t)kGramRows, r1 - a0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * c; e += blockDim.x) {
+      const int rr = e / c, cc = e - rr * c;
+      tile[rr * c + cc] = M[(a0 + rr) * ldm + cc];
+    }
+    __syncthreads();
+    for (int rr = 0; rr < nr; ++rr) {
+      const double* row = tile + rr * c;
+#pragma unroll
+      for (int q = 0; q < KPER; ++q) acc[q] = fma(row[ii[q]], row[jj[q]], acc[q]);
+    }
+  }
+  double* out = part + (int64_t)blockIdx.x * ntri;
+#pragma unroll
+  for (int q = 0; q < KPER; ++q) {
+    const int e = threadIdx.x + q * 256;
+    if (e < ntri) out[e] = acc[q];
+  }
+}
+
+// G (c x c, full symmetric, row-major) = sum over blocks, in block order
+__global__ void k_gram_reduce(const double* __restrict__ part, int nb, int c, double* __restrict__ G) {
+  const int ntri = c * (c + 1) / 2;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ntri; e += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * ntri + e];
+    int i, j;
+    tri_ij(e, c, i, j);
+    G[i * c + j] = s;
+    G[j * c + i] = s;
+  }
+}
+
+__device__ __forceinline__ bool better(double a, int pa, double b, int pb) {
+  return (a > b) || (a == b && pa < pb);
+}
+
+// Pivoted (pivot = 1) or plain Cholesky of the c x c PSD G, one block, in
+// POSITION order: the pivot moves to position j by the symmetric swap of
+// positions j and piv (the transposition cpqr.cu applies), so the remaining
+// block is always [j+1, c)^2 and row j of the working matrix becomes row j of
+// R (rows < j keep R, and their columns j and piv are swapped with the rest).
+// Per step: argmax of the remaining diagonal (the remaining column norm^2,
+// lowest position on ties) | one thread: sqrt, reciprocal, stop test | swap
+// and scale row j (disjoint element pairs, one phase) | Schur update of the
+// remaining block, a warp per row.  Four block barriers per step.
+// Outputs: perm[pos] = physical column, R (rows 0..rank-1, row-major ldr,
+// pivoted order, zero below the diagonal), *rank.
+__global__ void __launch_bounds__(256) k_pchol(const double* __restrict__ Gin, int c, int kmax, double rtol,
+                                               int pivot, int32_t* __restrict__ perm, double* __restrict__ R,
+                                               int64_t ldr, int32_t* __restrict__ rank) {
+  extern __shared__ double sm[];
+  const int ld = c + 1;
+  double* G = sm;                                   // c x ld, by position
+  int* phys_at = reinterpret_cast<int*>(G + c * ld);
+  __shared__ double sv[8];
+  __shared__ int sp[8];
+  __shared__ int s_piv, s_stop;
+  __shared__ double s_ljj, s_inv, s_top;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int a = wid; a < c; a += nw)
+    for (int b = lane; b < c; b += 32) G[a * ld + b] = Gin[a * c + b];
+  for (int q = threadIdx.x; q < c; q += blockDim.x) phys_at[q] = q;
+  __syncthreads();
+  int j = 0;
+  for (;; ++j) {
+    double bv = -1.0;
+    int bp = 0x7fffffff;
+    if (pivot) {
+      for (int q = j + threadIdx.x; q < c; q += blockDim.x) {
+        const double d = G[q * ld + q];
+        if (d > bv) { bv = d; bp = q; }
+      }
+    } else if (threadIdx.x == 0 && j < c) {
+      bv = G[j * ld + j]; bp = j;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+      if (better(ov, op, bv, bp)) { bv = ov; bp = op; }
+    }
+    if (lane == 0) { sv[wid] = bv; sp[wid] = bp; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < nw; ++w)
+        if (better(sv[w], sp[w], bv, bp)) { bv = sv[w]; bp = sp[w]; }
+      const double nrm = sqrt(fmax(bv, 0.0));
+      if (j == 0) s_top = nrm;
+      const bool stop = (j >= kmax) || j >= c || !(bv > 0.0) || (j > 0 && nrm <= rtol * s_top);
+      s_stop = stop ? 1 : 0;
+      if (!stop) {
+        if (bp != j) { const int t = phys_at[j]; phys_at[j] = phys_at[bp]; phys_at[bp] = t; }
+        s_piv = bp; s_ljj = nrm; s_inv = 1.0 / nrm;
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int pv = s_piv;
+    const double inv = s_inv;
+    // swap positions j and pv (rows and columns) and scale row j beyond the
+    // diagonal; each thread owns index a and touches only (a, j), (a, pv),
+    // (j, a), (pv, a), so the phase needs no inner barrier
+    for (int a = threadIdx.x; a < c; a += blockDim.x) {
+      if (a == j) {
+        if (pv != j) {
+          G[pv * ld + pv] = G[j * ld + j];
+          G[j * ld + pv] *= inv;                    // (j, pv) = old (pv, j): symmetric, stays; scaled
+        }
+        G[j * ld + j] = s_ljj;
+      } else if (a != pv) {
+        if (pv != j) {
+          const double cj = G[a * ld + j], cp = G[a * ld + pv];
+          G[a * ld + j] = cp;
+          G[a * ld + pv] = cj;
+          const double rj = G[j * ld + a], rp = G[pv * ld + a];
+          G[j * ld + a] = (a > j) ? rp * inv : rp;
+          G[pv * ld + a] = rj;
+        } else if (a > j) {
+          G[j * ld + a] *= inv;
+        }
+      }
+    }
+    __syncthreads();
+    // Schur complement of the remaining block: S_ab -= R_ja R_jb
+    for (int a = j + 1 + wid; a < c; a += nw) {
+      const double ra = G[j * ld + a];
+      for (int b = j + 1 + lane; b < c; b += 32) G[a * ld + b] = fma(-ra, G[j * ld + b], G[a * ld + b]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *rank = j;
+  for (int q = threadIdx.x; q < c; q += blockDim.x) perm[q] = phys_at[q];
+  for (int a = wid; a < j; a += nw)
+    for (int b = lane; b < c; b += 32) R[(int64_t)a * ldr + b] = (b < a) ? 0.0 : G[a * ld + b];
+}
+
+// Q (p x r, row-major ldq) = M(:, perm[0:r]) R^{-1}, R upper triangular
+// (r x r leading block of the ldr-strided R).  One thread per row; the block's
+// rows of Q live in shared memory during the substitution.  perm may be NULL
+// (identity).
+constexpr int kTrsmRows = 128;
+__global__ void __launch_bounds__(kTrsmRows) k_trsm_rows(const double* __restrict__ M, int64_t p, int64_t ldm,
+                                                         const int32_t* __restrict__ perm,
+                                                         const double* __restrict__ R, int64_t ldr, int r,
+                                                         double* __restrict__ Q, int64_t ldq) {
+  extern __shared__ double sm[];
+  double* Rs = sm;                                  // r x r
+  double* qs = Rs + r * r;                          // kTrsmRows x (r + 1)
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) Rs[e] = R[(int64_t)(e / r) * ldr + (e % r)];
+  const int64_t i0 = (int64_t)blockIdx.x * kTrsmRows;
+  const int ld = r + 1;
+  // stage the rows of M(:, perm) (coalesced over the block's rows)
+  for (int e = threadIdx.x; e < kTrsmRows * r; e += blockDim.x) {
+    const int rr = e / r, t = e - rr * r;
+    const int64_t i = i0 + rr;
+    const int col = perm ? perm[t] : t;
+    qs[rr * ld + t] = (i < p) ? M[i * ldm + col] : 0.0;
+  }
+  __syncthreads();
+  double* q = qs + threadIdx.x * ld;
+  for (int jx = 0; jx < r; ++jx) {
+    // two independent FMA chains (even / odd t) halve the dependent latency
+    double a0 = q[jx], a1 = 0.0;
+    int t = 0;
+    for (; t + 1 < jx; t += 2) {
+      a0 = fma(-q[t], Rs[t * r + jx], a0);
+      a1 = fma(-q[t + 1], Rs[(t + 1) * r + jx], a1);
+    }
+    if (t < jx) a0 = fma(-q[t], Rs[t * r + jx], a0);
+    q[jx] = (a0 + a1) / Rs[jx * r + jx];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kTrsmRows * r; e += blockDim.x) {
+    const int rr = e / r, t = e - rr * r;
+    const int64_t i = i0 + rr;
+    if (i < p) Q[i * ldq + t] = qs[rr * ld + t];
+  }
+}
+
+lrs_status gram(lrs_ctx* ctx, const double* M, int64_t p, int c, int64_t ldm, double* G) {
+  int64_t nb = ctx->num_sms;
+  int64_t rows_b = (p + nb - 1) / nb;
+  if (rows_b < kGramRows) rows_b = kGramRows;
+  nb = (p + rows_b - 1) / rows_b;
+  const int ntri = c * (c + 1) / 2;
+  double* part = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(nb * ntri));
+  if (!part) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (gram)");
+  const size_t dyn = sizeof(double) * (size_t)(kGramRows * c);
+  const int per = (ntri + 255) / 256;
+  if (per <= 8) k_gram_partial<8><<<(unsigned)nb, 256, dyn, ctx->stream>>>(M, p, c, ldm, rows_b, part);
+  else if (per <= 16) k_gram_partial<16><<<(unsigned)nb, 256, dyn, ctx->stream>>>(M, p, c, ldm, rows_b, part);
+  else if (per <= 24) k_gram_partial<24><<<(unsigned)nb, 256, dyn, ctx->stream>>>(M, p, c, ldm, rows_b, part);
+  else k_gram_partial<33><<<(unsigned)nb, 256, dyn, ctx->stream>>>(M, p, c, ldm, rows_b, part);
+  ctx->launches++;
+  k_gram_reduce<<<(ntri + 255) / 256, 256, 0, ctx->stream>>>(part, (int)nb, c, G);
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
+
+size_t pchol_smem(int c) { return sizeof(double) * (size_t)(c * (c + 1)) + sizeof(int) * (size_t)c; }
+
+lrs_status pchol(lrs_ctx* ctx, const double* G, int c, int kmax, double rtol, int pivot, int32_t* perm,
+                 double* R, int64_t ldr, int32_t* rank) {
+  const size_t dyn = pchol_smem(c);
+  if (dyn > 48 * 1024)
+    LRS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_pchol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  k_pchol<<<1, 256, dyn, ctx->stream>>>(G, c, kmax, rtol, pivot, perm, R, ldr, rank);
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
+
+lrs_status trsm_rows(lrs_ctx* ctx, const double* M, int64_t p, int64_t ldm, const int32_t* perm, const double* R,
+                     int64_t ldr, int r, double* Q, int64_t ldq) {
+  const size_t dyn = sizeof(double) * (size_t)(r * r + kTrsmRows * (r + 1));
+  if (dyn > 48 * 1024)
+    LRS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  const unsigned nb = (unsigned)((p + kTrsmRows - 1) / kTrsmRows);
+  k_trsm_rows<<<nb, kTrsmRows, dyn, ctx->stream>>>(M, p, ldm, perm, R, ldr, r, Q, ldq);
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
+
+}  // namespace
+
+bool orth_gram_eligible(int64_t p, int64_t c, double rtol) {
+  return c >= 1 && c <= kMaxC && p >= 4 * c && rtol >= kOrthGramRtolMin;
+}
+
+size_t orth_gram_ws(int64_t p, int64_t c, int num_sms) {
+  auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+  size_t b = 0;
+  b += a256(sizeof(double) * (size_t)num_sms * (size_t)(c * (c + 1) / 2));   // Gram partials (one pass at a time)
+  b += 2 * a256(sizeof(double) * (size_t)(c * c));       // G, R
+  b += a256(4 * (size_t)c) + a256(8);                    // perm, rank
+  b += a256(sizeof(double) * (size_t)(p * c));           // Q_1
+  return b + 1024;
+}
+
+lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldm, double rtol,
+                            double* Q, int64_t ldq, int64_t* r_out) {
+  const int ci = (int)c;
+  double* G = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(c * c));
+  double* R = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(c * c));
+  int32_t* perm = (int32_t*)ws_alloc(ctx, 4 * (size_t)c);
+  int32_t* rank = (int32_t*)ws_alloc(ctx, 8);
+  double* Q1 = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(p * c));
+  if (!G || !R || !perm || !rank || !Q1) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (orth_gram)");
+  const size_t mark = ctx->ws_top;
+  lrs_status st = gram(ctx, M, p, ci, ldm, G);
+  if (st) return st;
+  ctx->ws_top = mark;
+  st = pchol(ctx, G, ci, ci, rtol, 1, perm, R, c, rank);
+  if (st) return st;
+  int32_t* h = (int32_t*)ctx->host_scratch;
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 40, rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  const int r = h[40];
+  *r_out = r;
+  if (r == 0) return LRS_OK;
+  st = trsm_rows(ctx, M, p, ldm, perm, R, c, r, Q1, r);
+  if (st) return st;
+  // refinement: G_2 = Q_1^T Q_1 = R_2^T R_2 (plain Cholesky), Q = Q_1 R_2^{-1}
+  st = gram(ctx, Q1, p, r, r, G);
+  if (st) return st;
+  ctx->ws_top = mark;
+  st = pchol(ctx, G, r, r, 0.0, 0, perm, R, r, rank);
+  if (st) return st;
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 41, rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  // Q_1 has full column rank r by construction; a breakdown here means the
+  // first pass lost it to rounding: the caller falls back to Householder CPQR
+  if (h[41] != r) return LRS_ERANK;
+  return trsm_rows(ctx, Q1, p, r, nullptr, R, r, r, Q, ldq);
+}
+
+}  // namespace lrs

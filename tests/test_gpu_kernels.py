@@ -118,6 +118,27 @@ def test_range_find_full_rank_parity(lrs, m, l):
     np.testing.assert_allclose(_np(Q), Qo, atol=1e-11)
 
 
+@pytest.mark.parametrize("p,c", [(16384, 72), (2000, 72), (400, 100), (1000, 128)])
+def test_range_find_tall_skinny_gram_route(lrs, p, c):
+    """Tall-skinny inputs at rtol = 1e-6 take the pivoted-Cholesky-of-the-Gram
+    route: same rank as the oracle's Householder CPQR on a spectrum that
+    crosses rtol, the same range (projector distance), orthonormal columns."""
+    torch = _torch()
+    rng = np.random.default_rng(p + c)
+    U, _ = np.linalg.qr(rng.standard_normal((p, c)))
+    V, _ = np.linalg.qr(rng.standard_normal((c, c)))
+    M = (U * np.logspace(0, -9, c)) @ V.T
+    Qo, ro = oracle.range_find(M, 1e-6)
+    Q = torch.zeros((p, c), dtype=torch.float64, device="cuda")
+    r = lrs.range_find(_dev(M), p, c, c, 1e-6, Q, c)
+    assert r == ro
+    Qg = _np(Q)[:, :r]
+    np.testing.assert_allclose(Qg.T @ Qg, np.eye(r), atol=1e-13)
+    # Q_g spans the oracle's range: distances ~ u kappa(M_r) with kappa <= 1/rtol
+    assert np.linalg.norm(Qg @ (Qg.T @ Qo) - Qo) <= 1e-7
+    assert np.all(np.isfinite(_np(Q)))
+
+
 @pytest.mark.parametrize("shape", [(600, 1024), (600, 200)])
 def test_range_find_blob_sketch(lrs, shape):
     """Wide / tall smooth sketches with a fast-decaying spectrum (truncated)."""
