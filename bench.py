@@ -70,6 +70,25 @@ def cfg_dict(w, rtol, prec_name):
 
 
 # ---------------------------------------------------------------------------
+# multi-rank bookkeeping (one process per GPU; independent matrices per rank)
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """The largest x over all ranks: the job takes as long as its slowest rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, ms_per_step_max: float) -> float:
+    """Whole-job decompositions per second: each rank finishes one matrix per
+    step, the step lasts as long as the slowest rank (weak scaling)."""
+    return world * 1e3 / ms_per_step_max
+
+
+# ---------------------------------------------------------------------------
 def clocks_start(dev):
     f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
     q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -185,7 +204,7 @@ def run_ours(args, rank, world):
     prec_name = args.prec if args.prec != "auto" else ("fp64" if w.dtype == "f64" else "split_bf16")
     prec = prec_map[prec_name]
 
-    A_np = synth.make_workload(w)
+    A_np = synth.make_workload(w, seed_offset=rank)     # an independent matrix per rank
     tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.int16}[w.dtype]
     A_h = torch.from_numpy(A_np.view(np.int16) if w.dtype == "bf16" else A_np).pin_memory()
     del A_np
@@ -226,12 +245,8 @@ def run_ours(args, rank, world):
     barrier()
     clocks = clocks_stop(clk)
     launches = (ctx.launches - l0) // max(args.steps, 1)
-    ms = ev0.elapsed_time(ev1) / args.steps
-    t = torch.tensor([ms], device=f"cuda:{dev}")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
-    value = world * 1e3 / ms
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, f"cuda:{dev}")
+    value = job_throughput(world, ms)
 
     # ---- per-call breakdown (one extra step, events around each ABI call) ----
     phases = {}
@@ -326,11 +341,7 @@ def run_ours(args, rank, world):
         f1.record(stream)
     stream.synchronize()
     barrier()
-    e2e_ms = f0.elapsed_time(f1) / e2e_steps
-    te = torch.tensor([e2e_ms], device=f"cuda:{dev}")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_ms = float(te.item())
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1) / e2e_steps, world, f"cuda:{dev}")
 
     # ---- the plain FP32 GPU method on the same matrix, for comparison ----
     plain = None
@@ -367,7 +378,7 @@ def run_ours(args, rank, world):
            "vs_baseline": None, "dtype": w.dtype if prec != binding.LRS_PREC_FP64 else "f64",
            "data": "synthetic", "config": cfg_dict(w, rtol, prec_name),
            "roofline": roof, "clocks": clocks, "gpu_launches": int(launches),
-           "e2e": {"value": world * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+           "e2e": {"value": job_throughput(world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h)},
            "result": {"err_est_svd": s.err_est, "r": s.r, "err_est_id": d.err_est},
            "phases_ms": phases}

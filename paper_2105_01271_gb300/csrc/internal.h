@@ -108,8 +108,10 @@ lrs_status launch_id_coeffs(lrs_ctx* ctx, const double* R, int64_t k, int64_t m,
 constexpr double kOrthGramRtolMin = 1e-6;
 bool orth_gram_eligible(int64_t p, int64_t c, double rtol);
 size_t orth_gram_ws(int64_t p, int64_t c, int num_sms);
+// refine = false: skip the Cholesky-QR2 pass (well-conditioned basis of the
+// same range, orthonormal only to ~u cond^2; for intermediate C-PWR iterates)
 lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldm, double rtol,
-                            double* Q, int64_t ldq, int64_t* r_out);
+                            double* Q, int64_t ldq, int64_t* r_out, bool refine = true);
 
 // svd_small.cu ------------------------------------------------------------------
 // R factor (r x r, row-major) of B^T where B is r x n row-major in FP32 or FP64.

@@ -97,13 +97,16 @@ static size_t orth_ws(int64_t p, int64_t c, int num_sms) {
 
 // Orthonormal basis of the numerical range of Min (p x c, row-major ldi):
 // Q (p x r, row-major ldq), r returned through *r_out.  Synchronises.
+// intermediate = true: the basis only feeds a product that is orthonormalised
+// again (the W^T G step of C-PWR), so a well-conditioned basis of the same
+// range suffices (the Gram route then skips its refinement pass).
 static lrs_status orth(lrs_ctx* ctx, const double* Min, int64_t p, int64_t c, int64_t ldi,
-                       double rtol, double* Q, int64_t ldq, int64_t* r_out) {
+                       double rtol, double* Q, int64_t ldq, int64_t* r_out, bool intermediate = false) {
   const int64_t kmax = p < c ? p : c;
   if (orth_gram_eligible(p, c, rtol)) {
     // tall-skinny: pivoted Cholesky of the Gram (same pivots and stop rule)
     const size_t mark = ctx->ws_top;
-    lrs_status gs = launch_orth_gram(ctx, Min, p, c, ldi, rtol, Q, ldq, r_out);
+    lrs_status gs = launch_orth_gram(ctx, Min, p, c, ldi, rtol, Q, ldq, r_out, !intermediate);
     ctx->ws_top = mark;
     if (gs != LRS_ERANK) return gs;
   }
@@ -312,7 +315,7 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
     const void* Tcur = tc ? (const void*)T32 : (const void*)Tm;
     int32_t tdt = tc ? LRS_F32 : LRS_F64;
     if (reorth) {
-      st = orth(ctx, Tm, nI, gc, gc, rtol, To, gc, &tc_cols);
+      st = orth(ctx, Tm, nI, gc, gc, rtol, To, gc, &tc_cols, /*intermediate=*/true);
       if (st) return st;
       ctx->ws_top = mark;
       if (tc) {
@@ -330,7 +333,8 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
     ctx->ws_top = mark;
     if (reorth) {
       double* Go = (Gn == Ga) ? Gb : Ga;
-      st = orth(ctx, Gn, m, tc_cols, wmax, rtol, Go, wmax, &gc);
+      // only the last iterate is returned as the orthonormal basis G_q
+      st = orth(ctx, Gn, m, tc_cols, wmax, rtol, Go, wmax, &gc, /*intermediate=*/it + 1 < q);
       if (st) return st;
       ctx->ws_top = mark;
       Gcur = Go;

@@ -13,6 +13,9 @@
 //   4. One refinement (Cholesky-QR2): G_2 = Q_1^T Q_1 = R_2^T R_2,
 //      Q = Q_1 R_2^{-1}.  Q spans M(:, piv[0:r]); its R factor
 //      (R_2 R_11) has a positive diagonal.
+//   Q_1 alone spans the same range with |Q_1^T Q_1 - I| ~ u cond(M_r)^2
+//   (<= ~1e-4 at rtol = 1e-6): callers whose basis only feeds a product that
+//   is orthonormalised again skip step 4 (refine = false).
 //
 // Forming G squares the condition number, so this route is only taken when
 // rtol^2 stays far above the FP64 rounding of G (rtol >= 1e-6); otherwise the
@@ -195,11 +198,10 @@ __global__ void __launch_bounds__(256) k_pchol(const double* __restrict__ Gin, i
 }
 
 // Q (p x r, row-major ldq) = M(:, perm[0:r]) R^{-1}, R upper triangular
-// (r x r leading block of the ldr-strided R).  One thread per row; the block's
-// rows of Q live in shared memory during the substitution.  perm may be NULL
-// (identity).
-constexpr int kTrsmRows = 128;
-__global__ void __launch_bounds__(kTrsmRows) k_trsm_rows(const double* __restrict__ M, int64_t p, int64_t ldm,
+// (r x r leading block of the ldr-strided R).  One thread per row (blockDim
+// rows per block); the block's rows of Q live in shared memory during the
+// substitution.  perm may be NULL (identity).
+__global__ void __launch_bounds__(128) k_trsm_rows(const double* __restrict__ M, int64_t p, int64_t ldm,
                                                          const int32_t* __restrict__ perm,
                                                          const double* __restrict__ R, int64_t ldr, int r,
                                                          double* __restrict__ Q, int64_t ldq) {
@@ -207,10 +209,11 @@ __global__ void __launch_bounds__(kTrsmRows) k_trsm_rows(const double* __restric
   double* Rs = sm;                                  // r x r
   double* qs = Rs + r * r;                          // kTrsmRows x (r + 1)
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) Rs[e] = R[(int64_t)(e / r) * ldr + (e % r)];
-  const int64_t i0 = (int64_t)blockIdx.x * kTrsmRows;
+  const int rows = blockDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * rows;
   const int ld = r + 1;
   // stage the rows of M(:, perm) (coalesced over the block's rows)
-  for (int e = threadIdx.x; e < kTrsmRows * r; e += blockDim.x) {
+  for (int e = threadIdx.x; e < rows * r; e += blockDim.x) {
     const int rr = e / r, t = e - rr * r;
     const int64_t i = i0 + rr;
     const int col = perm ? perm[t] : t;
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(kTrsmRows) k_trsm_rows(const double* __restric
     q[jx] = (a0 + a1) / Rs[jx * r + jx];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < kTrsmRows * r; e += blockDim.x) {
+  for (int e = threadIdx.x; e < rows * r; e += blockDim.x) {
     const int rr = e / r, t = e - rr * r;
     const int64_t i = i0 + rr;
     if (i < p) Q[i * ldq + t] = qs[rr * ld + t];
@@ -273,11 +276,14 @@ lrs_status pchol(lrs_ctx* ctx, const double* G, int c, int kmax, double rtol, in
 
 lrs_status trsm_rows(lrs_ctx* ctx, const double* M, int64_t p, int64_t ldm, const int32_t* perm, const double* R,
                      int64_t ldr, int r, double* Q, int64_t ldq) {
-  const size_t dyn = sizeof(double) * (size_t)(r * r + kTrsmRows * (r + 1));
+  // rows per block: 128, fewer (down to 32) while that leaves SMs idle
+  int rows = 128;
+  while (rows > 32 && (p + rows - 1) / rows < 2 * (int64_t)ctx->num_sms) rows >>= 1;
+  const size_t dyn = sizeof(double) * (size_t)(r * r + rows * (r + 1));
   if (dyn > 48 * 1024)
     LRS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-  const unsigned nb = (unsigned)((p + kTrsmRows - 1) / kTrsmRows);
-  k_trsm_rows<<<nb, kTrsmRows, dyn, ctx->stream>>>(M, p, ldm, perm, R, ldr, r, Q, ldq);
+  const unsigned nb = (unsigned)((p + rows - 1) / rows);
+  k_trsm_rows<<<nb, rows, dyn, ctx->stream>>>(M, p, ldm, perm, R, ldr, r, Q, ldq);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
   return LRS_OK;
@@ -300,7 +306,7 @@ size_t orth_gram_ws(int64_t p, int64_t c, int num_sms) {
 }
 
 lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldm, double rtol,
-                            double* Q, int64_t ldq, int64_t* r_out) {
+                            double* Q, int64_t ldq, int64_t* r_out, bool refine) {
   const int ci = (int)c;
   double* G = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(c * c));
   double* R = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(c * c));
@@ -320,6 +326,7 @@ lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c,
   const int r = h[40];
   *r_out = r;
   if (r == 0) return LRS_OK;
+  if (!refine) return trsm_rows(ctx, M, p, ldm, perm, R, c, r, Q, ldq);
   st = trsm_rows(ctx, M, p, ldm, perm, R, c, r, Q1, r);
   if (st) return st;
   // refinement: G_2 = Q_1^T Q_1 = R_2^T R_2 (plain Cholesky), Q = Q_1 R_2^{-1}

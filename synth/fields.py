@@ -257,12 +257,14 @@ WORKLOADS = {
 }
 
 
-def make_workload(w: Workload, rows: slice | None = None) -> np.ndarray:
-    """Materialise (rows of) a workload's A in its storage dtype."""
+def make_workload(w: Workload, rows: slice | None = None, seed_offset: int = 0) -> np.ndarray:
+    """Materialise (rows of) a workload's A in its storage dtype.  seed_offset
+    gives independent matrices of the same recipe (one per rank)."""
     p = w.params
+    seed = p["seed"] + seed_offset
     if w.field == "heat":
-        return heat_field(w.m, w.N, w.d, p["K"], p["seed"], w.dtype, rows=rows)
+        return heat_field(w.m, w.N, w.d, p["K"], seed, w.dtype, rows=rows)
     if w.field == "blob":
-        return blob_field(w.m, w.N, p["nblobs"], p["seed"], p.get("kappa", 1e-5), w.dtype,
+        return blob_field(w.m, w.N, p["nblobs"], seed, p.get("kappa", 1e-5), w.dtype,
                           rows=rows)
     raise ValueError(w.field)

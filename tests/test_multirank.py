@@ -1,0 +1,84 @@
+"""Host logic of the N > 1 bench path on CPU: world-size-2 gloo ranks.
+
+The path shards by independent problems (one matrix per rank, no data-path
+collective); the only cross-rank steps are the barrier and the max-over-ranks
+step time, which these tests run over gloo.
+"""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        local_ms = 10.0 + 5.0 * rank            # rank 1 is the slow one
+        ms = bench.max_over_ranks(local_ms, world, "cpu")
+        value = bench.job_throughput(world, ms)
+        dist.barrier()
+        with open(os.path.join(out_dir, f"r{rank}.json"), "w") as f:
+            json.dump({"ms": ms, "value": value}, f)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_job_throughput_gloo(tmp_path):
+    import torch.multiprocessing as mp
+    world = 2
+    mp.start_processes(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world,
+                       start_method="spawn", join=True)
+    res = [json.load(open(tmp_path / f"r{r}.json")) for r in range(world)]
+    for r in res:
+        assert r["ms"] == 15.0                   # the slowest rank's step time, on every rank
+        assert r["value"] == pytest.approx(world * 1e3 / 15.0)
+
+
+def test_single_rank_helpers_need_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.5, 1) == 3.5
+    assert bench.job_throughput(1, 4.0) == 250.0
+
+
+def test_each_rank_gets_an_independent_matrix():
+    import synth
+    w = synth.WORKLOADS["heat2d_m200_64x64_f64"]
+    a0 = synth.make_workload(w, rows=slice(0, 8))
+    a0b = synth.make_workload(w, rows=slice(0, 8), seed_offset=0)
+    a1 = synth.make_workload(w, rows=slice(0, 8), seed_offset=1)
+    assert np.array_equal(a0, a0b)               # rank 0 keeps the canonical matrix
+    assert not np.allclose(a0, a1)
+
+
+def test_reference_arm_under_torchrun_prints_one_line():
+    """torchrun with 2 ranks: rank 0 alone times the oracle and prints one
+    JSON line; the other rank exits 0 without work."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
+           os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "heat2d_m200_64x64_f64",
+           "--gpus", "2", "--steps", "1", "--warmup", "1"]
+    p = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
