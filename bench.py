@@ -35,6 +35,13 @@ sys.path.insert(0, ROOT)
 METRIC = "A-pass HBM GB/s (% of peak); rank-k SVD/ID per sec at stated rel. error"
 UNIT = "decomps/s"
 
+# DRAM bytes (read + write) of one A-pass launch from an ncu capture of the
+# current kernel (profiles/k_apass_<workload>.md); set to None when the kernel
+# changes until it is captured again.
+APASS_TRAFFIC = {("blob2d_m2000_512x512_f32", "split_bf16"): 2.108051e9 + 72.391424e6}
+# FP64 nominal of the part: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
 
 def parse():
     p = argparse.ArgumentParser()
@@ -319,9 +326,30 @@ def run_ours(args, rank, world):
     else:
         roof = {"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfl / alu_peak,
                 "peak_source": f"{nsm} SMs x {'128 FP32' if bsz == 4 else '2 FP64'} FMA/clk x 2 x {sm_max:.0f} MHz"}
-    roof.update({"kernel": "A-pass B = Q^T A_f (lrs_gemm_tn)", "traffic": None,
+    roof.update({"kernel": "A-pass B = Q^T A_f (lrs_gemm_tn)",
+                 "traffic": APASS_TRAFFIC.get((w.name, prec_name)),
                  "algorithmic_bytes": alg_bytes, "algorithmic_flops": alg_flops, "ms": apass_ms,
+                 "ms_covers": "the whole lrs_gemm_tn call (X split, kernel, status read-back)",
                  "r": r, "hbm_gbs_achieved": gbs, "hbm_frac": gbs / hbm_peak})
+
+    # ---- the step's largest kernel by time: the FP64 pivoted QR (row ID call) ----
+    with torch.cuda.stream(stream):
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for _ in range(reps):
+            ctx.id_k(bufs.Gid, w.m, w.grid.l, w.grid.l, w.k, bufs.J, bufs.P, w.k)
+        h1.record(stream)
+    stream.synchronize()
+    id_ms = h0.elapsed_time(h1) / reps
+    # CPQR of the l x m transpose, k steps: update + norm + dot = 3 FMA per remaining element
+    pq, cq = w.grid.l, w.m
+    cpqr_flops = sum(6.0 * (pq - j) * (cq - j) for j in range(min(w.k, pq, cq)))
+    roof_qr = {"bound": "alu", "kernel": "pivoted QR of the sketch (k_cpqr via lrs_id_k)",
+               "achieved": cpqr_flops / (id_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+               "unit": "TFLOP/s (FP64)", "ms": id_ms, "algorithmic_flops": cpqr_flops,
+               "peak_source": "nominal FP64 from unit counts: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
+               "traffic": None}
+    roof_qr["frac"] = roof_qr["achieved"] / roof_qr["peak"]
 
     # ---- end to end through the public API, host buffers in and out ----
     h2d = A_h.numel() * A_h.element_size()
@@ -377,7 +405,8 @@ def run_ours(args, rank, world):
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": w.dtype if prec != binding.LRS_PREC_FP64 else "f64",
            "data": "synthetic", "config": cfg_dict(w, rtol, prec_name),
-           "roofline": roof, "clocks": clocks, "gpu_launches": int(launches),
+           "roofline": roof, "roofline_pivoted_qr": roof_qr, "clocks": clocks,
+           "gpu_launches": int(launches),
            "e2e": {"value": job_throughput(world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h)},
            "result": {"err_est_svd": s.err_est, "r": s.r, "err_est_id": d.err_est},
