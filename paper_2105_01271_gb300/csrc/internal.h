@@ -113,6 +113,13 @@ size_t orth_gram_ws(int64_t p, int64_t c, int num_sms);
 lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldm, double rtol,
                             double* Q, int64_t ldq, int64_t* r_out, bool refine = true);
 
+// R (r x r upper, row-major, positive diagonal) with R^T R = B B^T for a wide
+// FP32 B (r x n, r <= 128): double-float Gram on the FP32 pipe + FP64
+// Cholesky.  LRS_ERANK (nothing reported) when the Cholesky breaks down; the
+// caller then runs TSQR.  Synchronises.
+size_t r_of_bt_gram_ws(int64_t r, int num_sms);
+lrs_status launch_r_of_bt_gram(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, int64_t ldb, double* R);
+
 // svd_small.cu ------------------------------------------------------------------
 // R factor (r x r, row-major) of B^T where B is r x n row-major in FP32 or FP64.
 lrs_status launch_tsqr(lrs_ctx* ctx, const void* B, int b_f64, int64_t r, int64_t n,

@@ -365,7 +365,7 @@ lrs_status lrs_svd_k(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int6
   const int f64 = prec == LRS_PREC_FP64;
   const size_t bsz = f64 ? 8 : 4;
   size_t need = align256(bsz * (size_t)(r * n));            // B
-  need += tsqr_ws(r, n, bsz);
+  need += tsqr_ws(r, n, bsz) + r_of_bt_gram_ws(r, ctx->num_sms);
   need += 4 * align256(8 * (size_t)(r * r)) + align256(8 * (size_t)(m * r)) + 65536;
   if (prec >= LRS_PREC_SPLIT_BF16)
     need += gemm_tc_workspace(r, m, prec) + gemm_tc_splitk_workspace(r, n, m, ctx->num_sms) + 4096;
@@ -381,9 +381,9 @@ lrs_status lrs_svd_k(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int6
   double* sgn = (double*)ws_alloc(ctx, 8 * (size_t)kk);
   if (!B || !fro2 || !Rm || !Vr || !sv || !Wk || !QT || !sgn) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd_k)");
   // (a4) B = Q^T A_f -- the one full read of A_f (||A_f||_F^2 fused on the tensor-core path)
-  if (prec >= LRS_PREC_SPLIT_BF16 && r <= 128) {
-    GemmArgs g{r, n, m, Q, LRS_F64, ldq, A, dtype, lda, B, f64, 0, n, 1.0};
-    st = launch_gemm_tc(ctx, g, prec, fro2);
+  GemmArgs ga{r, n, m, Q, LRS_F64, ldq, A, dtype, lda, B, f64, 0, n, 1.0};
+  if (prec >= LRS_PREC_SPLIT_BF16 && (r <= 128 || apass_eligible(ga, prec))) {
+    st = launch_gemm_tc(ctx, ga, prec, fro2);
     if (st) return st;
   } else {
     st = gemm(ctx, prec, r, n, m, Q, LRS_F64, ldq, A, dtype, lda, B, f64, 0, n);
@@ -391,8 +391,17 @@ lrs_status lrs_svd_k(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int6
     st = launch_fro2(ctx, A, dtype, m, n, lda, fro2);
     if (st) return st;
   }
-  // (a5) SVD(B): R of B^T, Jacobi on R -> U_B = Vr, s
-  st = launch_tsqr(ctx, B, f64, r, n, n, Rm);
+  // (a5) SVD(B): R of B^T, Jacobi on R -> U_B = Vr, s.  FP32 B: R from the
+  // double-float Gram and an FP64 Cholesky (TSQR if that breaks down); FP64 B:
+  // Householder TSQR.
+  st = LRS_ERANK;
+  if (!f64 && r <= 128) {
+    const size_t mark = ctx->ws_top;
+    st = launch_r_of_bt_gram(ctx, (const float*)B, r, n, n, Rm);
+    ctx->ws_top = mark;
+    if (st != LRS_OK && st != LRS_ERANK) return st;
+  }
+  if (st == LRS_ERANK) st = launch_tsqr(ctx, B, f64, r, n, n, Rm);
   if (st) return st;
   st = launch_jacobi(ctx, Rm, r, Vr, sv, f64);
   if (st) return st;

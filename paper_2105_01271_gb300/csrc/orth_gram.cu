@@ -93,6 +93,21 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int nb, int c, do
   }
 }
 
+// 1/sqrt(x) for x > 0 by Newton-Raphson on f(y) = y^-2 - x, i.e.
+// y <- y (3 - x y^2) / 2, from an FP32 seed (~23 correct bits; each step
+// doubles them, two steps reach FP64 precision within an ulp or two).  Keeps
+// the pivot step off the FP64 square-root and divide sequences, which are long
+// dependent chains on this part's narrow FP64 pipe.  Outside the FP32 range of
+// the seed it falls back to 1 / sqrt(x).
+__device__ __forceinline__ double rsqrt_newton(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+  double y = (double)rsqrtf((float)x);
+  const double hx = 0.5 * x;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) y = y * fma(-hx * y, y, 1.5);
+  return y;
+}
+
 __device__ __forceinline__ bool better(double a, int pa, double b, int pb) {
   return (a > b) || (a == b && pa < pb);
 }
@@ -147,13 +162,15 @@ __global__ void __launch_bounds__(256) k_pchol(const double* __restrict__ Gin, i
     if (threadIdx.x == 0) {
       for (int w = 1; w < nw; ++w)
         if (better(sv[w], sp[w], bv, bp)) { bv = sv[w]; bp = sp[w]; }
-      const double nrm = sqrt(fmax(bv, 0.0));
-      if (j == 0) s_top = nrm;
-      const bool stop = (j >= kmax) || j >= c || !(bv > 0.0) || (j > 0 && nrm <= rtol * s_top);
+      // R_jj = sqrt(d), 1 / R_jj = rsqrt(d); the stop test |R_jj| <= rtol |R_00|
+      // is taken on the squares, d <= rtol^2 d_0
+      const double y = bv > 0.0 ? rsqrt_newton(bv) : 0.0;
+      if (j == 0) s_top = bv;
+      const bool stop = (j >= kmax) || j >= c || !(bv > 0.0) || (j > 0 && bv <= rtol * rtol * s_top);
       s_stop = stop ? 1 : 0;
       if (!stop) {
         if (bp != j) { const int t = phys_at[j]; phys_at[j] = phys_at[bp]; phys_at[bp] = t; }
-        s_piv = bp; s_ljj = nrm; s_inv = 1.0 / nrm;
+        s_piv = bp; s_ljj = bv * y; s_inv = y;
       }
     }
     __syncthreads();
@@ -198,21 +215,24 @@ __global__ void __launch_bounds__(256) k_pchol(const double* __restrict__ Gin, i
 }
 
 // Q (p x r, row-major ldq) = M(:, perm[0:r]) R^{-1}, R upper triangular
-// (r x r leading block of the ldr-strided R).  One thread per row (blockDim
-// rows per block); the block's rows of Q live in shared memory during the
-// substitution.  perm may be NULL (identity).
-__global__ void __launch_bounds__(128) k_trsm_rows(const double* __restrict__ M, int64_t p, int64_t ldm,
-                                                         const int32_t* __restrict__ perm,
-                                                         const double* __restrict__ R, int64_t ldr, int r,
-                                                         double* __restrict__ Q, int64_t ldq) {
+// (r x r leading block of the ldr-strided R).  A team of T threads (T = 1..32,
+// a power of two) solves one row: for each unknown j the team splits the dot
+// q[0:j] . R[0:j, j] by t mod T and reduces it with shuffles, so p * T threads
+// keep every SM's FP64 units busy even when p is small.  The block's rows of
+// Q live in shared memory during the substitution.  perm may be NULL.
+__global__ void __launch_bounds__(256) k_trsm_rows(const double* __restrict__ M, int64_t p, int64_t ldm,
+                                                   const int32_t* __restrict__ perm,
+                                                   const double* __restrict__ R, int64_t ldr, int r, int T,
+                                                   double* __restrict__ Q, int64_t ldq) {
   extern __shared__ double sm[];
   double* Rs = sm;                                  // r x r
-  double* qs = Rs + r * r;                          // kTrsmRows x (r + 1)
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) Rs[e] = R[(int64_t)(e / r) * ldr + (e % r)];
-  const int rows = blockDim.x;
-  const int64_t i0 = (int64_t)blockIdx.x * rows;
+  double* dinv = Rs + r * r;                        // r: 1 / R_jj
+  double* qs = dinv + r;                            // rows x (r + 1)
+  const int rows = blockDim.x / T;
   const int ld = r + 1;
-  // stage the rows of M(:, perm) (coalesced over the block's rows)
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) Rs[e] = R[(int64_t)(e / r) * ldr + (e % r)];
+  for (int j = threadIdx.x; j < r; j += blockDim.x) dinv[j] = 1.0 / R[(int64_t)j * ldr + j];
+  const int64_t i0 = (int64_t)blockIdx.x * rows;
   for (int e = threadIdx.x; e < rows * r; e += blockDim.x) {
     const int rr = e / r, t = e - rr * r;
     const int64_t i = i0 + rr;
@@ -220,17 +240,16 @@ __global__ void __launch_bounds__(128) k_trsm_rows(const double* __restrict__ M,
     qs[rr * ld + t] = (i < p) ? M[i * ldm + col] : 0.0;
   }
   __syncthreads();
-  double* q = qs + threadIdx.x * ld;
+  const int lane = threadIdx.x & 31;
+  const int tm = threadIdx.x & (T - 1);
+  const unsigned tmask = (T == 32 ? 0xffffffffu : ((1u << T) - 1u)) << (lane & ~(T - 1));
+  double* q = qs + (threadIdx.x / T) * ld;
   for (int jx = 0; jx < r; ++jx) {
-    // two independent FMA chains (even / odd t) halve the dependent latency
-    double a0 = q[jx], a1 = 0.0;
-    int t = 0;
-    for (; t + 1 < jx; t += 2) {
-      a0 = fma(-q[t], Rs[t * r + jx], a0);
-      a1 = fma(-q[t + 1], Rs[(t + 1) * r + jx], a1);
-    }
-    if (t < jx) a0 = fma(-q[t], Rs[t * r + jx], a0);
-    q[jx] = (a0 + a1) / Rs[jx * r + jx];
+    double a = 0.0;
+    for (int t = tm; t < jx; t += T) a = fma(q[t], Rs[t * r + jx], a);
+    for (int o = 1; o < T; o <<= 1) a += __shfl_xor_sync(tmask, a, o);
+    if (tm == 0) q[jx] = (q[jx] - a) * dinv[jx];
+    __syncwarp(tmask);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < rows * r; e += blockDim.x) {
@@ -276,17 +295,95 @@ lrs_status pchol(lrs_ctx* ctx, const double* G, int c, int kmax, double rtol, in
 
 lrs_status trsm_rows(lrs_ctx* ctx, const double* M, int64_t p, int64_t ldm, const int32_t* perm, const double* R,
                      int64_t ldr, int r, double* Q, int64_t ldq) {
-  // rows per block: 128, fewer (down to 32) while that leaves SMs idle
-  int rows = 128;
-  while (rows > 32 && (p + rows - 1) / rows < 2 * (int64_t)ctx->num_sms) rows >>= 1;
-  const size_t dyn = sizeof(double) * (size_t)(r * r + rows * (r + 1));
+  // team size: enough threads (p * T) for ~8 FP64-busy warps per SM
+  const int64_t want = (int64_t)ctx->num_sms * 8 * 32;
+  int T = 1;
+  while (T < 32 && p * T < want) T <<= 1;
+  const int rows = 256 / T;
+  const size_t dyn = sizeof(double) * (size_t)(r * r + r + rows * (r + 1));
   if (dyn > 48 * 1024)
     LRS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   const unsigned nb = (unsigned)((p + rows - 1) / rows);
-  k_trsm_rows<<<nb, rows, dyn, ctx->stream>>>(M, p, ldm, perm, R, ldr, r, Q, ldq);
+  k_trsm_rows<<<nb, 256, dyn, ctx->stream>>>(M, p, ldm, perm, R, ldr, r, T, Q, ldq);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
   return LRS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// G = B B^T for a wide FP32 B (r x n row-major, r <= 128), accurate to ~2^-44
+// relative per entry on the FP32 pipe: each product a b is made exact as
+// p + e by Dekker's two-product (p = a b rounded, e = fma(a, b, -p)), and each
+// entry keeps a double-float sum (Knuth's two-sum carries the rounding error
+// of every addition into the low word).  Blocks take column ranges; per-block
+// (hi, lo) partials of the packed upper triangle are combined in FP64 in
+// block order.
+constexpr int kDfCols = 65;             // columns staged per pass (odd: row reads hit distinct banks)
+
+template <int KPER>
+__global__ void __launch_bounds__(256) k_gram_df(const float* __restrict__ B, int r, int64_t n, int64_t ldb,
+                                                int64_t cols_b, float* __restrict__ part_hi,
+                                                float* __restrict__ part_lo) {
+  extern __shared__ float tf[];                    // r x kDfCols
+  const int ntri = r * (r + 1) / 2;
+  const int64_t c0 = (int64_t)blockIdx.x * cols_b;
+  const int64_t c1 = min(n, c0 + cols_b);
+  float sh[KPER], sl[KPER];
+  int ij[KPER];                                    // i | j << 8
+#pragma unroll
+  for (int q = 0; q < KPER; ++q) {
+    const int e = threadIdx.x + q * 256;
+    int i = 0, j = 0;
+    if (e < ntri) tri_ij(e, r, i, j);
+    ij[q] = i | (j << 8);
+    sh[q] = 0.f;
+    sl[q] = 0.f;
+  }
+  for (int64_t a0 = c0; a0 < c1; a0 += kDfCols) {
+    const int nc = (int)min((int64_t)kDfCols, c1 - a0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < r * kDfCols; e += blockDim.x) {
+      const int i = e / kDfCols, t = e - i * kDfCols;
+      tf[e] = (t < nc) ? B[(int64_t)i * ldb + a0 + t] : 0.f;
+    }
+    __syncthreads();
+    for (int t = 0; t < nc; ++t) {
+#pragma unroll
+      for (int q = 0; q < KPER; ++q) {
+        const float a = tf[(ij[q] & 255) * kDfCols + t];
+        const float b = tf[(ij[q] >> 8) * kDfCols + t];
+        // _rn intrinsics: the compiler must not fuse these into FMAs, or the
+        // error-free transformations stop being exact
+        const float p = __fmul_rn(a, b);
+        const float pe = fmaf(a, b, -p);          // a b = p + pe exactly
+        const float s2 = __fadd_rn(sh[q], p);     // two-sum: sh + p = s2 + err exactly
+        const float bb = __fsub_rn(s2, sh[q]);
+        const float err = __fadd_rn(__fsub_rn(sh[q], __fsub_rn(s2, bb)), __fsub_rn(p, bb));
+        sh[q] = s2;
+        sl[q] = __fadd_rn(sl[q], __fadd_rn(err, pe));
+      }
+    }
+  }
+  float* oh = part_hi + (int64_t)blockIdx.x * ntri;
+  float* ol = part_lo + (int64_t)blockIdx.x * ntri;
+#pragma unroll
+  for (int q = 0; q < KPER; ++q) {
+    const int e = threadIdx.x + q * 256;
+    if (e < ntri) { oh[e] = sh[q]; ol[e] = sl[q]; }
+  }
+}
+
+__global__ void k_gram_df_reduce(const float* __restrict__ hi, const float* __restrict__ lo, int nb, int r,
+                                 double* __restrict__ G) {
+  const int ntri = r * (r + 1) / 2;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ntri; e += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += (double)hi[(int64_t)b * ntri + e] + (double)lo[(int64_t)b * ntri + e];
+    int i, j;
+    tri_ij(e, r, i, j);
+    G[i * r + j] = s;
+    G[j * r + i] = s;
+  }
 }
 
 }  // namespace
@@ -341,6 +438,49 @@ lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c,
   // first pass lost it to rounding: the caller falls back to Householder CPQR
   if (h[41] != r) return LRS_ERANK;
   return trsm_rows(ctx, Q1, p, r, nullptr, R, r, r, Q, ldq);
+}
+
+}  // namespace lrs
+
+namespace lrs {
+
+size_t r_of_bt_gram_ws(int64_t r, int num_sms) {
+  auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t ntri = (size_t)(r * (r + 1) / 2);
+  return 2 * a256(sizeof(float) * (size_t)num_sms * ntri) + a256(sizeof(double) * (size_t)(r * r)) +
+         a256(4 * (size_t)r) + a256(8) + 1024;
+}
+
+lrs_status launch_r_of_bt_gram(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, int64_t ldb, double* R) {
+  if (r < 1 || r > kMaxC) return lrs_fail(ctx, LRS_EINVAL, "svd: r=%lld out of range for the Gram route", (long long)r);
+  const int ri = (int)r;
+  const int ntri = ri * (ri + 1) / 2;
+  int64_t nb = ctx->num_sms;
+  int64_t cols_b = (n + nb - 1) / nb;
+  if (cols_b < kDfCols) cols_b = kDfCols;
+  nb = (n + cols_b - 1) / cols_b;
+  float* hi = (float*)ws_alloc(ctx, sizeof(float) * (size_t)(nb * ntri));
+  float* lo = (float*)ws_alloc(ctx, sizeof(float) * (size_t)(nb * ntri));
+  double* G = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(r * r));
+  int32_t* perm = (int32_t*)ws_alloc(ctx, 4 * (size_t)r);
+  int32_t* rank = (int32_t*)ws_alloc(ctx, 8);
+  if (!hi || !lo || !G || !perm || !rank) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd gram)");
+  const size_t dyn = sizeof(float) * (size_t)(ri * kDfCols);
+  const int per = (ntri + 255) / 256;
+  if (per <= 8) k_gram_df<8><<<(unsigned)nb, 256, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
+  else if (per <= 16) k_gram_df<16><<<(unsigned)nb, 256, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
+  else if (per <= 24) k_gram_df<24><<<(unsigned)nb, 256, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
+  else k_gram_df<33><<<(unsigned)nb, 256, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
+  ctx->launches++;
+  k_gram_df_reduce<<<(ntri + 255) / 256, 256, 0, ctx->stream>>>(hi, lo, (int)nb, ri, G);
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  lrs_status st = pchol(ctx, G, ri, ri, 0.0, 0, perm, R, r, rank);
+  if (st) return st;
+  int32_t* h = (int32_t*)ctx->host_scratch;
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 42, rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return h[42] == ri ? LRS_OK : LRS_ERANK;
 }
 
 }  // namespace lrs
