@@ -23,6 +23,37 @@ __device__ __forceinline__ size_t dtype_size(int32_t dt) {
 }
 
 // ---------------------------------------------------------------------------
+// pivot comparisons and reciprocal square roots off the FP64 pipe
+//
+// Pivoting compares non-negative squared norms.  Non-negative doubles order
+// exactly as their bit patterns read as integers, so the comparison runs on
+// the integer pipe (anything with the sign bit set, and +0, map to key 0).
+__device__ __forceinline__ long long norm_key(double a) {
+  const long long k = __double_as_longlong(a);
+  return k > 0 ? k : 0;
+}
+// (a, position pa) beats (b, pb): larger value, lower position on ties
+__device__ __forceinline__ bool pivot_better(double a, int pa, double b, int pb) {
+  const long long ka = norm_key(a), kb = norm_key(b);
+  return (ka > kb) || (ka == kb && pa < pb);
+}
+
+// 1/sqrt(x) for x > 0 by Newton-Raphson on f(y) = y^-2 - x, i.e.
+// y <- y (3 - x y^2) / 2, from an FP32 seed (~23 correct bits; each step
+// doubles them, two steps reach FP64 precision within an ulp or two).  Keeps
+// serial pivot steps off the FP64 square-root and divide sequences, long
+// dependent chains on this part's narrow FP64 pipe.  Outside the FP32 range
+// of the seed it falls back to 1 / sqrt(x).
+__device__ __forceinline__ double rsqrt_newton(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+  double y = (double)rsqrtf((float)x);
+  const double hx = 0.5 * x;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) y = y * fma(-hx * y, y, 1.5);
+  return y;
+}
+
+// ---------------------------------------------------------------------------
 // warp / block reductions
 // ---------------------------------------------------------------------------
 template <typename T>

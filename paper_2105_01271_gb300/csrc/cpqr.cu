@@ -54,9 +54,7 @@ struct CpqrState {
   int team;             // threads per column in the update and dot phases (1..8, power of 2)
 };
 
-__device__ __forceinline__ bool better(double a, int pa, double b, int pb) {
-  return (a > b) || (a == b && pa < pb);
-}
+__device__ __forceinline__ bool better(double a, int pa, double b, int pb) { return pivot_better(a, pa, b, pb); }
 
 // block-wide argmax over (val, pos, phys); thread 0 ends with the winner
 __device__ void block_best(double& val, int& pos, int& phys, double* sv, int* sp, int* sf) {
@@ -247,7 +245,7 @@ __global__ void __launch_bounds__(kCpqrThreads, 1) k_cpqr(CpqrState s) {
       }
       // thread 0 holds the global winner
       if (threadIdx.x == 0) {
-        const double nrm = sqrt(fmax(bv, 0.0));
+        const double nrm = bv > 0.0 ? bv * rsqrt_newton(bv) : 0.0;
         if (j == 0) top = nrm;
         const bool stop = (j >= s.kmax) || bf < 0 || bv <= 0.0 || (j > 0 && nrm <= s.rtol * top);
         s_stop = stop ? 1 : 0;
@@ -257,7 +255,7 @@ __global__ void __launch_bounds__(kCpqrThreads, 1) k_cpqr(CpqrState s) {
           const double sgn = x0 >= 0.0 ? 1.0 : -1.0;
           const double vn2 = 2.0 * nrm * (nrm + fabs(x0));     // ||x + sgn ||x|| e_j||^2
           s_alpha = nrm; s_sgn = sgn; s_x0 = x0;
-          s_inv = vn2 > 0.0 ? 1.0 / sqrt(vn2) : 0.0;
+          s_inv = vn2 > 0.0 ? rsqrt_newton(vn2) : 0.0;
         }
       }
       __syncthreads();

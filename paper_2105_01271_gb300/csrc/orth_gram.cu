@@ -93,24 +93,7 @@ __global__ void k_gram_reduce(const double* __restrict__ part, int nb, int c, do
   }
 }
 
-// 1/sqrt(x) for x > 0 by Newton-Raphson on f(y) = y^-2 - x, i.e.
-// y <- y (3 - x y^2) / 2, from an FP32 seed (~23 correct bits; each step
-// doubles them, two steps reach FP64 precision within an ulp or two).  Keeps
-// the pivot step off the FP64 square-root and divide sequences, which are long
-// dependent chains on this part's narrow FP64 pipe.  Outside the FP32 range of
-// the seed it falls back to 1 / sqrt(x).
-__device__ __forceinline__ double rsqrt_newton(double x) {
-  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
-  double y = (double)rsqrtf((float)x);
-  const double hx = 0.5 * x;
-#pragma unroll
-  for (int it = 0; it < 2; ++it) y = y * fma(-hx * y, y, 1.5);
-  return y;
-}
-
-__device__ __forceinline__ bool better(double a, int pa, double b, int pb) {
-  return (a > b) || (a == b && pa < pb);
-}
+__device__ __forceinline__ bool better(double a, int pa, double b, int pb) { return pivot_better(a, pa, b, pb); }
 
 // Pivoted (pivot = 1) or plain Cholesky of the c x c PSD G, one block, in
 // POSITION order: the pivot moves to position j by the symmetric swap of
@@ -146,7 +129,7 @@ __global__ void __launch_bounds__(256) k_pchol(const double* __restrict__ Gin, i
     if (pivot) {
       for (int q = j + threadIdx.x; q < c; q += blockDim.x) {
         const double d = G[q * ld + q];
-        if (d > bv) { bv = d; bp = q; }
+        if (norm_key(d) > norm_key(bv)) { bv = d; bp = q; }
       }
     } else if (threadIdx.x == 0 && j < c) {
       bv = G[j * ld + j]; bp = j;
