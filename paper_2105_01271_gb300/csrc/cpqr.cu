@@ -84,6 +84,7 @@ __device__ void block_best(double& val, int& pos, int& phys, double* sv, int* sp
 }
 
 constexpr int kCpqrThreads = 512;
+constexpr int kCpqrMaxBlocks = 160;
 
 // One warp sums part[b * c + cc] over the nb blocks (lane-strided, fixed
 // shuffle tree: the same order in every block and every run).
@@ -133,6 +134,22 @@ __device__ __forceinline__ double sum4_blocks(const double* part, int64_t c, int
   a += __shfl_xor_sync(0xffffffffu, a, 1);
   a += __shfl_xor_sync(0xffffffffu, a, 2);
   return a;
+}
+
+// Sum of part[bb * c + cc] over the nb (<= 160) blocks by one warp: every
+// lane issues its (at most 5) loads before the first add, so the L2 latency is
+// paid once; then a fixed shuffle tree (the same order in every block and
+// run).  Used in owner mode, where a block owns only a few columns.
+__device__ __forceinline__ double warp_sum_blocks_wide(const double* part, int64_t c, int64_t cc, int nb,
+                                                       int lane) {
+  double v[5];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int bb = lane + 32 * k;
+    v[k] = bb < nb ? __ldcg(part + (int64_t)bb * c + cc) : 0.0;
+  }
+  double a = ((v[0] + v[1]) + (v[2] + v[3])) + v[4];
+  return warp_sum(a);
 }
 
 __global__ void __launch_bounds__(kCpqrThreads, 1) k_cpqr(CpqrState s) {
@@ -218,18 +235,30 @@ __global__ void __launch_bounds__(kCpqrThreads, 1) k_cpqr(CpqrState s) {
     // ---- (N) norms^2 and the best candidate -------------------------------
     {
       double bv = -1.0; int bp = 0x7fffffff, bf = -1;
-      const int q4 = lane & 3, slot = lane >> 2;
-      for (int64_t base = c_lo + wid * 8; base < c_hi; base += (int64_t)nw * 8) {
-        const int64_t cc = base + slot;
-        const double a = sum4_blocks(s.part_n, s.c, cc, cc < c_hi, nb, q4);
-        if (cc < c_hi && !done[cc]) {
-          if (q4 == 0) {
-            if (s.redundant) sums[cc] = a;
-            else s.colsum[cc] = a;
+      if (s.redundant) {
+        // every block reduces every column: 4 lanes per column keep the FP64 adds few
+        const int q4 = lane & 3, slot = lane >> 2;
+        for (int64_t base = c_lo + wid * 8; base < c_hi; base += (int64_t)nw * 8) {
+          const int64_t cc = base + slot;
+          const double a = sum4_blocks(s.part_n, s.c, cc, cc < c_hi, nb, q4);
+          if (cc < c_hi && !done[cc]) {
+            if (q4 == 0) sums[cc] = a;
+            const int pc = pos_of[cc];
+            if (better(a, pc, bv, bp)) { bv = a; bp = pc; bf = (int)cc; }
           }
-          const int pc = pos_of[cc];
-          if (better(a, pc, bv, bp)) { bv = a; bp = pc; bf = (int)cc; }
         }
+      } else {
+        // a block owns a few columns: a whole warp per column
+        for (int64_t cc = c_lo + wid; cc < c_hi; cc += nw) {
+          if (done[cc]) continue;
+          const double a = warp_sum_blocks_wide(s.part_n, s.c, cc, nb, lane);
+          if (lane == 0) {
+            s.colsum[cc] = a;
+            const int pc = pos_of[cc];
+            if (better(a, pc, bv, bp)) { bv = a; bp = pc; bf = (int)cc; }
+          }
+        }
+
       }
       block_best(bv, bp, bf, sv, sp, sf);
       if (!s.redundant) {
@@ -299,13 +328,18 @@ __global__ void __launch_bounds__(kCpqrThreads, 1) k_cpqr(CpqrState s) {
 
     // ---- (D) dots ------------------------------------------------------------
     {
-      const int q4 = lane & 3, slot = lane >> 2;
-      for (int64_t base = c_lo + wid * 8; base < c_hi; base += (int64_t)nw * 8) {
-        const int64_t cc = base + slot;
-        const double a = sum4_blocks(s.part_d, s.c, cc, cc < c_hi, nb, q4);
-        if (cc < c_hi && q4 == 0) {
-          if (s.redundant) sums[cc] = a;
-          else s.colsum[cc] = a;
+      if (s.redundant) {
+        const int q4 = lane & 3, slot = lane >> 2;
+        for (int64_t base = c_lo + wid * 8; base < c_hi; base += (int64_t)nw * 8) {
+          const int64_t cc = base + slot;
+          const double a = sum4_blocks(s.part_d, s.c, cc, cc < c_hi, nb, q4);
+          if (cc < c_hi && q4 == 0) sums[cc] = a;
+        }
+      } else {
+        for (int64_t cc = c_lo + wid; cc < c_hi; cc += nw) {
+          if (done[cc]) continue;
+          const double a = warp_sum_blocks_wide(s.part_d, s.c, cc, nb, lane);
+          if (lane == 0) s.colsum[cc] = a;
         }
       }
     }
@@ -339,6 +373,7 @@ size_t cpqr_scratch_bytes(int64_t p, int64_t c, int64_t kmax, int num_sms) {
   auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
   int64_t nb = (p * c + 2047) / 2048;
   if (nb > num_sms) nb = num_sms;
+  if (nb > kCpqrMaxBlocks) nb = kCpqrMaxBlocks;
   if (nb > (p + 3) / 4) nb = (p + 3) / 4;
   if (nb < 1) nb = 1;
   const int64_t rows_b = (p + nb - 1) / nb;
@@ -365,6 +400,7 @@ lrs_status launch_cpqr(lrs_ctx* ctx, double* M, int64_t p, int64_t c, int64_t ld
   // block), at most one per SM, at least 4 rows each
   int64_t nb = (p * c + 2047) / 2048;
   if (nb > ctx->num_sms) nb = ctx->num_sms;
+  if (nb > kCpqrMaxBlocks) nb = kCpqrMaxBlocks;   // the owner sums load <= 5 partials per lane
   if (nb > (p + 3) / 4) nb = (p + 3) / 4;
   if (nb < 1) nb = 1;
   s.rows_b = (p + nb - 1) / nb;
