@@ -61,7 +61,11 @@ def parse():
 def workload_params(name):
     import synth
     w = synth.WORKLOADS[name]
-    rtol = {"f64": 1e-14, "f32": 1e-6, "bf16": 1e-12}[w.dtype]
+    # rank-revealing tolerance of QR(.): FP64 data 1e-14; FP32 data 1e-6 (FP32-level
+    # products resolve ~1e-7); BF16-stored data 2^-11, a quarter of BF16's unit
+    # roundoff (below it the pivoted QR of the sketch walks the rounding-noise
+    # floor; at 2^-11 the 3-D heat sketch keeps r = 114 >= k = 64)
+    rtol = {"f64": 1e-14, "f32": 1e-6, "bf16": 2.0 ** -11}[w.dtype]
     return w, rtol
 
 
@@ -139,6 +143,12 @@ def clocks_stop(h):
 
 
 # ---------------------------------------------------------------------------
+def sample_rows(w) -> int:
+    """Snapshots in the oracle's timed sample: 200, fewer for very wide rows so
+    the FP64 sample stays near 2 GB (14 for the 16.7M-dof field)."""
+    return max(4, min(w.m, 200, int(2e9 // (8 * w.n))))
+
+
 def run_reference(args, rank, world):
     """FP64 CPU oracle on a bounded sample: the first m_s snapshots."""
     if rank != 0:
@@ -146,13 +156,15 @@ def run_reference(args, rank, world):
     import oracle
     import synth
     w, rtol = workload_params(args.workload)
-    ms = min(w.m, 200)
+    ms = sample_rows(w)
     A = synth.make_workload(w, rows=slice(0, ms))
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
 
+    ks = min(w.k, ms)                 # a sample of ms snapshots has rank <= ms
+
     def one():
-        oracle.svd_path(A, w.grid, w.k, q=w.q, gram_grid=w.gram, rtol=rtol)
-        oracle.id_path(A, w.grid, w.k, q=w.q, gram_grid=w.gram, rtol=rtol)
+        oracle.svd_path(A, w.grid, ks, q=w.q, gram_grid=w.gram, rtol=rtol)
+        oracle.id_path(A, w.grid, ks, q=w.q, gram_grid=w.gram, rtol=rtol)
 
     for _ in range(args.warmup):
         one()
@@ -161,7 +173,7 @@ def run_reference(args, rank, world):
         one()
     dt = (time.perf_counter() - t0) / args.steps
     value = (ms / w.m) / dt
-    sample = f"first {ms} of {w.m} snapshots per step, value scaled by {ms}/{w.m}"
+    sample = (f"first {ms} of {w.m} snapshots per step (k = {ks}), value scaled by {ms}/{w.m}")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -175,20 +187,21 @@ def run_reference(args, rank, world):
 def cpu_baseline(w, rtol, budget_s=25.0):
     import oracle
     import synth
-    ms = min(w.m, 200)
+    ms = sample_rows(w)
     A = synth.make_workload(w, rows=slice(0, ms))
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    ks = min(w.k, ms)                 # a sample of ms snapshots has rank <= ms
     t0 = time.perf_counter()
     reps = 0
     while True:
-        oracle.svd_path(A, w.grid, w.k, q=w.q, gram_grid=w.gram, rtol=rtol)
-        oracle.id_path(A, w.grid, w.k, q=w.q, gram_grid=w.gram, rtol=rtol)
+        oracle.svd_path(A, w.grid, ks, q=w.q, gram_grid=w.gram, rtol=rtol)
+        oracle.id_path(A, w.grid, ks, q=w.q, gram_grid=w.gram, rtol=rtol)
         reps += 1
         if time.perf_counter() - t0 > budget_s / 3 or reps >= 3:
             break
     dt = (time.perf_counter() - t0) / reps
     return {"value": (ms / w.m) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{reps} run(s) on the first {ms} of {w.m} snapshots, scaled by {ms}/{w.m}"}
+            "sample": f"{reps} run(s) on the first {ms} of {w.m} snapshots (k = {ks}), scaled by {ms}/{w.m}"}
 
 
 # ---------------------------------------------------------------------------

@@ -26,7 +26,11 @@ __global__ void __launch_bounds__(256) k_gemm_tn(GemmArgs a) {
   __shared__ T Xs[BK][BM];
   __shared__ T As[BK][BN];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+  // one flat grid over the (M tile, N tile) pairs, M tiles fastest: either
+  // dimension can be a dof count
+  const int64_t gm = (a.M + BM - 1) / BM;
+  const int64_t bid = blockIdx.x;
+  const int64_t m0 = (bid % gm) * BM, n0 = (bid / gm) * BN;
   T acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
@@ -84,9 +88,10 @@ __global__ void __launch_bounds__(256) k_gemm_tn(GemmArgs a) {
 
 lrs_status launch_gemm_simt(lrs_ctx* ctx, const GemmArgs& a, int fp64) {
   if (a.M <= 0 || a.N <= 0) return LRS_OK;
-  const int64_t gy = (a.M + BM - 1) / BM, gx = (a.N + BN - 1) / BN;
-  if (gy > 65535) return lrs_fail(ctx, LRS_EINVAL, "gemm: M=%lld too large for the SIMT path", (long long)a.M);
-  dim3 grid((unsigned)gx, (unsigned)gy);
+  const int64_t gm = (a.M + BM - 1) / BM, gn = (a.N + BN - 1) / BN;
+  if (gm * gn > 0x7fffffffLL)
+    return lrs_fail(ctx, LRS_EINVAL, "gemm: M=%lld N=%lld too large for the SIMT path", (long long)a.M, (long long)a.N);
+  dim3 grid((unsigned)(gm * gn));
   if (fp64) k_gemm_tn<double><<<grid, 256, 0, ctx->stream>>>(a);
   else k_gemm_tn<float><<<grid, 256, 0, ctx->stream>>>(a);
   ctx->launches++;

@@ -116,14 +116,32 @@ def heat_field(m: int, N: int, d: int, K: int, seed: int, dtype: str = "f64",
         tmp = np.einsum("tij,jy->tiy", C, S)
         A = np.einsum("tiy,ix->tyx", tmp, S).reshape(mt, N * N)
     elif d == 3:
+        # separable: three matrix products per chunk of snapshots (BLAS), rounded
+        # to the storage type chunk by chunk (the float64 field is never whole);
+        # chunks run on a thread pool (numpy and BLAS release the GIL)
         C = coef.reshape(mt, K, K, K)                            # [t, i(x), j(y), l(z)]
-        A = np.empty((mt, N * N * N), dtype=np.float64)
-        for r0 in range(0, mt, 8):
-            Cb = C[r0:r0 + 8]
-            t1 = np.einsum("tijl,lz->tijz", Cb, S)
-            t2 = np.einsum("tijz,jy->tizy", t1, S)
-            t3 = np.einsum("tizy,ix->tzyx", t2, S)
-            A[r0:r0 + len(Cb)] = t3.reshape(len(Cb), -1)
+        probe = _store(np.zeros((1, 1)), dtype)
+        out = np.empty((mt, N * N * N), dtype=probe.dtype)
+
+        def chunk(r0):
+            Cb = C[r0:r0 + 4]
+            b = len(Cb)
+            t1 = (Cb.reshape(b * K * K, K) @ S).reshape(b, K, K, N)                  # [t,i,j,z]
+            t2 = np.ascontiguousarray(t1.transpose(0, 1, 3, 2)).reshape(b * K * N, K) @ S
+            t2 = t2.reshape(b, K, N, N)                                            # [t,i,z,y]
+            t3 = np.ascontiguousarray(t2.transpose(0, 2, 3, 1)).reshape(b * N * N, K) @ S
+            out[r0:r0 + b] = _store(t3.reshape(b, N * N * N), dtype)               # [t,(z,y,x)]
+
+        starts = list(range(0, mt, 4))
+        if len(starts) > 1 and N ** 3 >= (1 << 18):
+            import concurrent.futures as cf
+            import os
+            with cf.ThreadPoolExecutor(max_workers=min(len(starts), os.cpu_count() or 1)) as ex:
+                list(ex.map(chunk, starts))
+        else:
+            for r0 in starts:
+                chunk(r0)
+        return out
     else:
         raise ValueError("heat_field supports d = 2 or 3")
     return _store(A, dtype)

@@ -173,3 +173,62 @@ def test_blob_id_path(lrs, blob, prec):
     e_g = oracle.id_rel_error(A, J, P)
     e_o = oracle.id_rel_error(A, d["J"], d["P"])
     assert e_g <= e_o * (1 + 1e-3), (e_g, e_o)
+
+
+# ---------------------------------------------------------------------------
+# precision form on BF16 storage: the 3-D heat field (the 16.7M-dof workload's
+# recipe at 64^3), 8x injection onto 8^3 (l = 512), k = 64, rtol = 2^-11
+HEAT3 = dict(m=500, N=64, grid=GridSpec((64, 64, 64), (8, 8, 8), "inject"), k=64, rtol=2.0 ** -11)
+
+
+@pytest.fixture(scope="module")
+def heat3():
+    c = HEAT3
+    A = synth.heat_field(c["m"], c["N"], 3, 12, 2, "bf16")
+    Ae = synth.fields.bf16_bits_to_f64(A)
+    o = oracle.svd_path(Ae, c["grid"], c["k"], q=0, rtol=c["rtol"])
+    d = oracle.id_path(Ae, c["grid"], c["k"], q=0, rtol=c["rtol"])
+    return A, Ae, o, d
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+def test_heat3d_bf16_svd_path(lrs, heat3, prec):
+    """B = Q^T A with BF16 data (one exact piece) and Q in 2 or 3 pieces.  The
+    BF16 rounding floor makes eps ~1e-3 here, so eps is held to the product
+    error bound: E = B_gpu - B, ||E||_F <= (c_p + (m+2) u32) || |Q|^T |A| ||_F,
+    |eps_g^2 - eps_o^2| <= (2 ||E|| eps_o ||A|| + ||E||^2) / ||A||^2."""
+    from paper_2105_01271_gb300 import path
+    A, Ae, o, _ = heat3
+    c = HEAT3
+    res = path.svd_path(lrs, _dev(A), "bf16", c["grid"], c["k"], q=0, rtol=c["rtol"], prec=prec)
+    assert res.r == o["r"] and c["k"] <= o["r"] <= 128
+    U, S, V = _np(res.U), _np(res.S), _np(res.V).astype(np.float64)
+    eps_g = oracle.rel_fro_error(Ae, U, S, V)
+    eps_o = oracle.rel_fro_error(Ae, o["U"], o["S"], o["V"])
+    nA = np.linalg.norm(Ae)
+    cp = PIECE_ERR[prec] + (c["m"] + 2) * U32
+    e_bound = cp * np.linalg.norm(np.abs(o["Q"]).T @ np.abs(Ae))
+    assert abs(eps_g ** 2 - eps_o ** 2) <= (2 * e_bound * eps_o * nA + e_bound ** 2) / nA ** 2
+    assert np.all(np.abs(S - o["S"]) <= e_bound + 64 * U32 * o["S"][0])
+    # U = Q V_B, V_B from FP32 Jacobi rotations: ~u32 per rotation through a
+    # column, ~10 sweeps x r rotations -> below 1e-4
+    np.testing.assert_allclose(U.T @ U, np.eye(U.shape[1]), atol=1e-4)
+
+
+def test_heat3d_bf16_id_path(lrs, heat3):
+    """q = 0 and injection: the sketch is an exact copy, so the FP64 CPQR sees
+    the oracle's input and every one of the k pivots must match."""
+    from paper_2105_01271_gb300 import path
+    A, Ae, _, d = heat3
+    c = HEAT3
+    gaps = []
+    oracle.row_id(d["G"], c["k"], gaps)
+    assert _prefix(gaps, 1e-10) == c["k"]
+    res = path.id_path(lrs, _dev(A), "bf16", c["grid"], c["k"], q=0, rtol=c["rtol"], prec=2)
+    J, P = _np(res.J), _np(res.P)
+    assert np.array_equal(J, d["J"])
+    assert np.array_equal(P[J], np.eye(c["k"]))
+    _, R, _, _, _ = oracle.cpqr(d["G"].T, kmax=c["k"])
+    kappa = np.linalg.cond(R[:, :c["k"]])
+    assert np.all(np.abs(P - d["P"]) <= 64 * 2.0 ** -53 * kappa * np.maximum(1.0, np.abs(d["P"])))
+    assert abs(res.err_est - d["err_est"]) <= 1e-9 * d["err_est"]
