@@ -303,69 +303,90 @@ lrs_status trsm_rows(lrs_ctx* ctx, const double* M, int64_t p, int64_t ldm, cons
 // block order.
 constexpr int kDfCols = 65;             // columns staged per pass (odd: row reads hit distinct banks)
 
-template <int KPER>
+// Thread layout: the upper triangle of G in 4 x 4 tiles (tile (ti, tj),
+// ti <= tj), dealt round-robin, TPT tiles per thread.  Per staged column a
+// tile loads 8 values and updates 16 double-float sums.  The output is a full
+// r x r partial per block; only entries (i, j) with i/4 <= j/4 are written.
+template <int TPT>
 __global__ void __launch_bounds__(256) k_gram_df(const float* __restrict__ B, int r, int64_t n, int64_t ldb,
                                                 int64_t cols_b, float* __restrict__ part_hi,
                                                 float* __restrict__ part_lo) {
-  extern __shared__ float tf[];                    // r x kDfCols
-  const int ntri = r * (r + 1) / 2;
+  extern __shared__ float tf[];                    // rp x kDfCols, rp = r rounded up to 4 (zero rows)
+  const int nt = (r + 3) / 4, ntiles = nt * (nt + 1) / 2, rp = nt * 4;
   const int64_t c0 = (int64_t)blockIdx.x * cols_b;
   const int64_t c1 = min(n, c0 + cols_b);
-  float sh[KPER], sl[KPER];
-  int ij[KPER];                                    // i | j << 8
+  float sh[TPT][16], sl[TPT][16];
+  int ti[TPT], tj[TPT];
 #pragma unroll
-  for (int q = 0; q < KPER; ++q) {
+  for (int q = 0; q < TPT; ++q) {
     const int e = threadIdx.x + q * 256;
-    int i = 0, j = 0;
-    if (e < ntri) tri_ij(e, r, i, j);
-    ij[q] = i | (j << 8);
-    sh[q] = 0.f;
-    sl[q] = 0.f;
+    int a = 0, b = 0;
+    if (e < ntiles) tri_ij(e, nt, a, b);
+    ti[q] = e < ntiles ? a : -1;
+    tj[q] = b;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) { sh[q][u] = 0.f; sl[q][u] = 0.f; }
   }
   for (int64_t a0 = c0; a0 < c1; a0 += kDfCols) {
     const int nc = (int)min((int64_t)kDfCols, c1 - a0);
     __syncthreads();
-    for (int e = threadIdx.x; e < r * kDfCols; e += blockDim.x) {
+    for (int e = threadIdx.x; e < rp * kDfCols; e += blockDim.x) {
       const int i = e / kDfCols, t = e - i * kDfCols;
-      tf[e] = (t < nc) ? B[(int64_t)i * ldb + a0 + t] : 0.f;
+      tf[e] = (t < nc && i < r) ? B[(int64_t)i * ldb + a0 + t] : 0.f;
     }
     __syncthreads();
-    for (int t = 0; t < nc; ++t) {
 #pragma unroll
-      for (int q = 0; q < KPER; ++q) {
-        const float a = tf[(ij[q] & 255) * kDfCols + t];
-        const float b = tf[(ij[q] >> 8) * kDfCols + t];
-        // _rn intrinsics: the compiler must not fuse these into FMAs, or the
-        // error-free transformations stop being exact
-        const float p = __fmul_rn(a, b);
-        const float pe = fmaf(a, b, -p);          // a b = p + pe exactly
-        const float s2 = __fadd_rn(sh[q], p);     // two-sum: sh + p = s2 + err exactly
-        const float bb = __fsub_rn(s2, sh[q]);
-        const float err = __fadd_rn(__fsub_rn(sh[q], __fsub_rn(s2, bb)), __fsub_rn(p, bb));
-        sh[q] = s2;
-        sl[q] = __fadd_rn(sl[q], __fadd_rn(err, pe));
+    for (int q = 0; q < TPT; ++q) {
+      if (ti[q] < 0) continue;
+      const float* xi = tf + (ti[q] * 4) * kDfCols;
+      const float* xj = tf + (tj[q] * 4) * kDfCols;
+      for (int t = 0; t < nc; ++t) {
+        float va[4], vb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { va[u] = xi[u * kDfCols + t]; vb[u] = xj[u * kDfCols + t]; }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            // _rn intrinsics: the compiler must not fuse these into FMAs, or
+            // the error-free transformations stop being exact
+            const float p = __fmul_rn(va[u], vb[v]);
+            const float pe = fmaf(va[u], vb[v], -p);      // a b = p + pe exactly
+            float& h = sh[q][u * 4 + v];
+            const float s2 = __fadd_rn(h, p);            // two-sum: h + p = s2 + err exactly
+            const float bb = __fsub_rn(s2, h);
+            const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s2, bb)), __fsub_rn(p, bb));
+            h = s2;
+            sl[q][u * 4 + v] = __fadd_rn(sl[q][u * 4 + v], __fadd_rn(err, pe));
+          }
       }
     }
   }
-  float* oh = part_hi + (int64_t)blockIdx.x * ntri;
-  float* ol = part_lo + (int64_t)blockIdx.x * ntri;
+  float* oh = part_hi + (int64_t)blockIdx.x * r * r;
+  float* ol = part_lo + (int64_t)blockIdx.x * r * r;
 #pragma unroll
-  for (int q = 0; q < KPER; ++q) {
-    const int e = threadIdx.x + q * 256;
-    if (e < ntri) { oh[e] = sh[q]; ol[e] = sl[q]; }
+  for (int q = 0; q < TPT; ++q) {
+    if (ti[q] < 0) continue;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const int i = ti[q] * 4 + u, j = tj[q] * 4 + v;
+        if (i < r && j < r) { oh[i * r + j] = sh[q][u * 4 + v]; ol[i * r + j] = sl[q][u * 4 + v]; }
+      }
   }
 }
 
+// G (r x r, FP64) = sum over blocks in block order; entry (i, j) is read from
+// the upper tile that holds it
 __global__ void k_gram_df_reduce(const float* __restrict__ hi, const float* __restrict__ lo, int nb, int r,
                                  double* __restrict__ G) {
-  const int ntri = r * (r + 1) / 2;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ntri; e += gridDim.x * blockDim.x) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
+    const int i = e / r, j = e - i * r;
+    const int src = (i / 4 <= j / 4) ? e : j * r + i;
     double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += (double)hi[(int64_t)b * ntri + e] + (double)lo[(int64_t)b * ntri + e];
-    int i, j;
-    tri_ij(e, r, i, j);
-    G[i * r + j] = s;
-    G[j * r + i] = s;
+    for (int b = 0; b < nb; ++b) s += (double)hi[(int64_t)b * r * r + src] + (double)lo[(int64_t)b * r * r + src];
+    G[e] = s;
   }
 }
 
@@ -429,33 +450,31 @@ namespace lrs {
 
 size_t r_of_bt_gram_ws(int64_t r, int num_sms) {
   auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
-  const size_t ntri = (size_t)(r * (r + 1) / 2);
-  return 2 * a256(sizeof(float) * (size_t)num_sms * ntri) + a256(sizeof(double) * (size_t)(r * r)) +
+  return 2 * a256(sizeof(float) * 2 * (size_t)num_sms * (size_t)(r * r)) + a256(sizeof(double) * (size_t)(r * r)) +
          a256(4 * (size_t)r) + a256(8) + 1024;
 }
 
 lrs_status launch_r_of_bt_gram(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, int64_t ldb, double* R) {
   if (r < 1 || r > kMaxC) return lrs_fail(ctx, LRS_EINVAL, "svd: r=%lld out of range for the Gram route", (long long)r);
   const int ri = (int)r;
-  const int ntri = ri * (ri + 1) / 2;
-  int64_t nb = ctx->num_sms;
+  const int nt = (ri + 3) / 4, ntiles = nt * (nt + 1) / 2;
+  int64_t nb = 2 * (int64_t)ctx->num_sms;         // two blocks per SM: few tiles leave warps idle
   int64_t cols_b = (n + nb - 1) / nb;
   if (cols_b < kDfCols) cols_b = kDfCols;
   nb = (n + cols_b - 1) / cols_b;
-  float* hi = (float*)ws_alloc(ctx, sizeof(float) * (size_t)(nb * ntri));
-  float* lo = (float*)ws_alloc(ctx, sizeof(float) * (size_t)(nb * ntri));
+  float* hi = (float*)ws_alloc(ctx, sizeof(float) * (size_t)(nb * r * r));
+  float* lo = (float*)ws_alloc(ctx, sizeof(float) * (size_t)(nb * r * r));
   double* G = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(r * r));
   int32_t* perm = (int32_t*)ws_alloc(ctx, 4 * (size_t)r);
   int32_t* rank = (int32_t*)ws_alloc(ctx, 8);
   if (!hi || !lo || !G || !perm || !rank) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd gram)");
-  const size_t dyn = sizeof(float) * (size_t)(ri * kDfCols);
-  const int per = (ntri + 255) / 256;
-  if (per <= 8) k_gram_df<8><<<(unsigned)nb, 256, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
-  else if (per <= 16) k_gram_df<16><<<(unsigned)nb, 256, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
-  else if (per <= 24) k_gram_df<24><<<(unsigned)nb, 256, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
-  else k_gram_df<33><<<(unsigned)nb, 256, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
+  const size_t dyn = sizeof(float) * (size_t)(nt * 4 * kDfCols);
+  const int tpt = (ntiles + 255) / 256;
+  if (tpt <= 1) k_gram_df<1><<<(unsigned)nb, 256, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
+  else if (tpt <= 2) k_gram_df<2><<<(unsigned)nb, 256, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
+  else k_gram_df<3><<<(unsigned)nb, 256, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
   ctx->launches++;
-  k_gram_df_reduce<<<(ntri + 255) / 256, 256, 0, ctx->stream>>>(hi, lo, (int)nb, ri, G);
+  k_gram_df_reduce<<<(ri * ri + 255) / 256, 256, 0, ctx->stream>>>(hi, lo, (int)nb, ri, G);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
   lrs_status st = pchol(ctx, G, ri, ri, 0.0, 0, perm, R, r, rank);
