@@ -10,7 +10,8 @@
 //
 // Roles (480 threads):
 //   warps 0-3   epilogue: drain a finished accumulator from TMEM and store
-//               C (for a fixed r, a warp writes 32 consecutive dofs).
+//               C (for a fixed r, a warp writes 32 consecutive dofs; or, for
+//               C stored n-major, each thread 16 consecutive r-values).
 //   warps 4-11  converters: read a raw 64 x 128 slab from shared memory, split
 //               it into BF16 pieces (x = x_0 + x_1 [+ x_2]) and write them in
 //               the K-major 128-byte-swizzled UMMA layout; fused ||A||_F^2.
@@ -68,7 +69,7 @@ struct ApParams {
   uint32_t tmem_cols;         // allocated TMEM columns
   int nacc;                   // accumulator buffers (1 or 2)
   int stacked;                // 1: X pieces stacked along UMMA N (one MMA per data piece)
-  void* C; int c_f64; int64_t ldc; double alpha;
+  void* C; int c_f64; int c_trans; int vec_ok; int64_t ldc; double alpha;
   int* err;
   double* fro2_part;          // per-CTA partial ||A||_F^2 or nullptr
 };
@@ -179,7 +180,30 @@ __global__ void __launch_bounds__(kThreads, 1) k_apass(const __grid_constant__ C
           }
         }
         if (n < P.N) {
-          if (P.c_f64) {
+          if (P.c_trans) {
+            // C stored n-major: this thread's 16 consecutive entries of row n
+            const int lim = (int)min((int64_t)16, P.M - c0);
+            if (P.c_f64) {
+              double* dst = reinterpret_cast<double*>(P.C) + n * P.ldc + c0;
+#pragma unroll
+              for (int e = 0; e < 16; ++e)
+                if (e < lim) dst[e] = P.alpha * (double)__uint_as_float(v[e]);
+            } else {
+              float* dst = reinterpret_cast<float*>(P.C) + n * P.ldc + c0;
+              const float fa = (float)P.alpha;
+              if (lim == 16 && P.vec_ok) {
+#pragma unroll
+                for (int e = 0; e < 16; e += 4)
+                  *reinterpret_cast<float4*>(dst + e) =
+                      make_float4(fa * __uint_as_float(v[e]), fa * __uint_as_float(v[e + 1]),
+                                  fa * __uint_as_float(v[e + 2]), fa * __uint_as_float(v[e + 3]));
+              } else {
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                  if (e < lim) dst[e] = fa * __uint_as_float(v[e]);
+              }
+            }
+          } else if (P.c_f64) {
 #pragma unroll
             for (int e = 0; e < 16; ++e)
               if (c0 + e < P.M)
@@ -464,7 +488,8 @@ lrs_status run_apass(lrs_ctx* ctx, const GemmArgs& a, double* fro2_out) {
   P.rN = cfg.rN; P.RS = cfg.RS; P.PS = cfg.PS;
   P.raw_bytes = cfg.raw_bytes; P.stage_bytes = cfg.stage_bytes;
   P.acc_cols = cfg.acc_cols; P.tmem_cols = cfg.tmem_cols; P.nacc = cfg.nacc; P.stacked = cfg.stacked;
-  P.C = a.C; P.c_f64 = a.c_f64; P.ldc = a.ldc; P.alpha = a.alpha;
+  P.C = a.C; P.c_f64 = a.c_f64; P.c_trans = a.c_trans; P.ldc = a.ldc; P.alpha = a.alpha;
+  P.vec_ok = ((reinterpret_cast<uintptr_t>(a.C) & 15u) == 0 && (a.ldc & 3) == 0) ? 1 : 0;
 
   const size_t xbytes = (size_t)P.Kt * SX * cfg.rN * 128;
   uint8_t* Xp = (uint8_t*)ws_alloc(ctx, xbytes);
@@ -509,7 +534,7 @@ lrs_status run_apass(lrs_ctx* ctx, const GemmArgs& a, double* fro2_out) {
 bool apass_eligible(const GemmArgs& a, int prec) {
   if (prec != LRS_PREC_SPLIT_BF16 && prec != LRS_PREC_BF16X3) return false;
   if (a.adt != LRS_F32 && a.adt != LRS_BF16) return false;
-  if (a.c_trans || a.M < 1 || a.M > kMaxR || a.N < TN || a.K < 1) return false;
+  if (a.M < 1 || a.M > kMaxR || a.N < TN || a.K < 1) return false;
   if (a.N >= (int64_t)1 << 31 || a.K >= (int64_t)1 << 31) return false;
   const int esize = a.adt == LRS_F32 ? 4 : 2;
   if ((reinterpret_cast<uintptr_t>(a.A) & 15u) != 0 || ((a.lda * esize) & 15) != 0) return false;

@@ -368,7 +368,8 @@ lrs_status lrs_svd_k(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int6
   need += tsqr_ws(r, n, bsz) + r_of_bt_gram_ws(r, ctx->num_sms);
   need += 4 * align256(8 * (size_t)(r * r)) + align256(8 * (size_t)(m * r)) + 65536;
   if (prec >= LRS_PREC_SPLIT_BF16)
-    need += gemm_tc_workspace(r, m, prec) + gemm_tc_splitk_workspace(r, n, m, ctx->num_sms) + 4096;
+    need += gemm_tc_workspace(r, m, prec) + gemm_tc_splitk_workspace(r, n, m, ctx->num_sms) + 4096 +
+            gemm_tc_workspace(kk, r, LRS_PREC_BF16X3) + 4096;
   lrs_status st = ws_reserve(ctx, need);
   if (st) return st;
   void* B = ws_alloc(ctx, bsz * (size_t)(r * n));
@@ -415,8 +416,18 @@ lrs_status lrs_svd_k(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int6
   if (st) return st;
   st = launch_scale_cols(ctx, Vr, r, r, sv, sgn, kk, Wk, kk);
   if (st) return st;
-  st = gemm(ctx, f64 ? LRS_PREC_FP64 : LRS_PREC_FP32, n, kk, r, B, f64 ? LRS_F64 : LRS_F32, n, Wk,
-            LRS_F64, kk, V, f64, 0, ldv);
+  if (prec >= LRS_PREC_SPLIT_BF16 && !f64) {
+    // V^T (kk x n) = Wk^T B on the tensor cores (B streamed once, V stored
+    // n-major), three BF16 pieces per operand: V carries the reconstruction,
+    // so it keeps FP32-level accuracy whatever the A-pass precision
+    GemmArgs gv{kk, n, r, Wk, LRS_F64, kk, B, LRS_F32, n, V, 0, 1, ldv, 1.0};
+    st = apass_eligible(gv, LRS_PREC_BF16X3) ? launch_gemm_tc(ctx, gv, LRS_PREC_BF16X3)
+                                             : gemm(ctx, LRS_PREC_FP32, n, kk, r, B, LRS_F32, n, Wk, LRS_F64, kk,
+                                                    V, 0, 0, ldv);
+  } else {
+    st = gemm(ctx, f64 ? LRS_PREC_FP64 : LRS_PREC_FP32, n, kk, r, B, f64 ? LRS_F64 : LRS_F32, n, Wk,
+              LRS_F64, kk, V, f64, 0, ldv);
+  }
   if (st) return st;
   LRS_CUDA_TRY(ctx, cudaMemcpyAsync(S, sv, 8 * (size_t)kk, cudaMemcpyDeviceToDevice, ctx->stream));
   if (err_est) {
