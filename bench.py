@@ -59,6 +59,9 @@ def parse():
     return p.parse_args()
 
 
+BATCH_WORKLOAD = "batch256_mixed_f32"
+
+
 def workload_params(name):
     import synth
     w = synth.WORKLOADS[name]
@@ -206,6 +209,108 @@ def cpu_baseline(w, rtol, budget_s=25.0):
 
 
 # ---------------------------------------------------------------------------
+def run_batch_bench(args, rank, world):
+    """Batching form: 256 independent FP32 matrices (grids 32^2..256^2, m 50..2000,
+    heat or blob, full weighting with factors 2/4/8, k 5..60) decomposed (SVD + ID)
+    by lrs_batch_run on an autotuned number of streams; one step = the whole batch.
+    The per-matrix loop (one stream, items one after another) is timed beside it."""
+    import concurrent.futures as cf
+    import torch
+    import synth
+    from paper_2105_01271_gb300 import binding
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    specs = synth.batch_specs(256, seed=3 + rank)          # an independent batch per rank
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        mats = list(ex.map(synth.make_batch_matrix, specs))
+    host = [torch.from_numpy(a).pin_memory() for a in mats]
+    del mats
+    Ad = [torch.empty(h.shape, dtype=torch.float32, device=f"cuda:{dev}") for h in host]
+    for a, h in zip(Ad, host):
+        a.copy_(h)
+    items = (binding.lrs_batch_item * len(specs))()
+    outs = []
+    for it, sp, A in zip(items, specs, Ad):
+        k = sp.k
+        U = torch.empty((sp.m, k), dtype=torch.float64, device=A.device)
+        S = torch.empty((k,), dtype=torch.float64, device=A.device)
+        V = torch.empty((sp.n, k), dtype=torch.float32, device=A.device)
+        J = torch.empty((k,), dtype=torch.int32, device=A.device)
+        P = torch.empty((sp.m, k), dtype=torch.float64, device=A.device)
+        it.A, it.dtype, it.m, it.lda = A.data_ptr(), binding.LRS_F32, sp.m, sp.n
+        it.sketch = binding.make_grid((sp.N, sp.N), (sp.s, sp.s), "fullweight")
+        it.q, it.k, it.prec, it.rtol = 0, k, binding.LRS_PREC_SPLIT_BF16, 1e-6
+        it.do_svd, it.do_id = 1, 1
+        it.U, it.ldu, it.S, it.V, it.ldv = U.data_ptr(), k, S.data_ptr(), V.data_ptr(), k
+        it.J, it.P, it.ldp = J.data_ptr(), P.data_ptr(), k
+        outs.append((U, S, V, J, P))
+    torch.cuda.synchronize(dev)
+    best, ms_item = binding.autotune_batch(items, dev, candidates=(1, 2, 4, 8, 16))
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed(nstreams, steps):
+        for _ in range(args.warmup):
+            binding.run_batch(items, dev, nstreams)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            binding.run_batch(items, dev, nstreams)
+        barrier()
+        return (time.perf_counter() - t0) * 1e3 / steps
+
+    clk = clocks_start(dev)
+    ms = max_over_ranks(timed(best, args.steps), world, f"cuda:{dev}")
+    clocks = clocks_stop(clk)
+    launches = sum(int(it.launches) for it in items)
+    statuses = [int(it.status) for it in items]
+    loop_ms = max_over_ranks(timed(1, max(1, min(args.steps, 3))), world, f"cuda:{dev}")
+
+    # end to end: every matrix copied in from pinned host memory, every output read back
+    h2d = sum(h.numel() * h.element_size() for h in host)
+    hout = [[torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in o] for o in outs]
+    d2h = sum(t.numel() * t.element_size() for o in outs for t in o)
+    barrier()
+    t0 = time.perf_counter()
+    for a, h in zip(Ad, host):
+        a.copy_(h, non_blocking=True)
+    torch.cuda.synchronize(dev)
+    binding.run_batch(items, dev, best)
+    for ho, o in zip(hout, outs):
+        for x, y in zip(ho, o):
+            x.copy_(y, non_blocking=True)
+    barrier()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, world, f"cuda:{dev}")
+    if rank != 0:
+        return
+    total_a = sum(sp.m * sp.n * 4 for sp in specs)
+    out = {"metric": METRIC, "value": job_throughput(world, ms) * len(specs), "unit": UNIT,
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": BATCH_WORKLOAD, "matrices": len(specs), "prec": "split_bf16",
+                      "streams": best, "timing": "host wall clock around the blocking lrs_batch_run",
+                      "total_A_bytes": total_a, "l2": "inputs larger than L2, no flush"},
+           "roofline": {"bound": "hbm", "achieved": total_a / (ms * 1e-3) / 1e9,
+                        "peak": 6795.8, "unit": "GB/s", "frac": total_a / (ms * 1e-3) / 1e9 / 6795.8,
+                        "kernel": "whole batch: bytes of every A_f read once / step time (latency-bound path)",
+                        "traffic": None},
+           "clocks": clocks, "gpu_launches": launches,
+           "e2e": {"value": job_throughput(world, e2e_ms) * len(specs), "unit": UNIT,
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+           "per_matrix_loop": {"value": job_throughput(world, loop_ms) * len(specs), "ms_per_step": loop_ms,
+                               "speedup_of_batch": loop_ms / ms},
+           "autotune": {"candidates": [1, 2, 4, 8, 16], "best": best, "ms_per_sampled_item": ms_item},
+           "items": {"ok": statuses.count(0), "rank_short": statuses.count(4), "failed": len(statuses) -
+                     statuses.count(0) - statuses.count(4)}}
+    print(json.dumps(out), flush=True)
+
+
 def run_ours(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -441,6 +546,8 @@ def main():
         dist.init_process_group("nccl")
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == BATCH_WORKLOAD:
+        run_batch_bench(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1 and args.impl == "ours":

@@ -208,6 +208,70 @@ lrs_status lrs_id_k_static(lrs_ctx* ctx, const double* Ysk, int64_t m, int64_t l
 /* Number of kernel launches this context has issued (for launch accounting). */
 int64_t lrs_launch_count(const lrs_ctx* ctx);
 
+/* ------------------------------------------------------------------------
+ * Batching form: many independent decompositions of different sizes.
+ *
+ * The paper treats one snapshot matrix at a time; this runs a list of them
+ * (each its own A_f, grid, k, q, precision) through the same path as
+ * lrs_power_pass + lrs_range_find + lrs_svd_k (SVD, Algs. 7 and 2) and
+ * lrs_power_pass + lrs_id_k (row ID, Alg. 4), with re-orthonormalisation on
+ * for the SVD and off for the ID, exactly as the single-matrix calls.
+ *
+ * Item (all pointers device pointers on `device`, caller-owned; U/S/V may be
+ * NULL when do_svd = 0, J/P when do_id = 0):
+ *   A, dtype, m, lda      the m x n matrix, n = sketch.N product
+ *   sketch, gram          the sketch grid; the C-PWR subsample grid (q > 0)
+ *   q, k, prec, rtol      as in lrs_power_pass / lrs_svd_k
+ *   U (m x k, ldu), S (k), V (n x k, ldv; FP64 for LRS_PREC_FP64 else FP32)
+ *   J (k), P (m x k, ldp)
+ * Written by the call: r (SVD basis rank), err_svd, err_id, status (an
+ * lrs_status; LRS_ERANK means fewer than k directions, outputs at rank r),
+ * launches (kernels launched for this item).
+ *
+ * lrs_batch_run: n_streams worker threads, each with its own context and
+ * CUDA stream, take items largest-first from a shared queue, so the
+ * latency-bound steps of different matrices overlap on the GPU.  Results are
+ * bit-identical to running the items one by one.  Returns LRS_OK when every
+ * item ended LRS_OK or LRS_ERANK, else the first other status (the items'
+ * own statuses tell which).  Blocks until all items are done.
+ *
+ * lrs_batch_autotune: times lrs_batch_run on a sample of the items (every
+ * 4th when there are 32 or more) for each candidate stream count and returns the fastest
+ * in *best (its time per sampled item in *ms_per_item).
+ *
+ * The worker contexts, streams and buffers are kept per device across calls
+ * (the first runs size them; later runs allocate nothing); calls for one
+ * device are serialised.  lrs_batch_release frees them.
+ * ---------------------------------------------------------------------- */
+typedef struct lrs_batch_item {
+  const void* A;
+  int32_t dtype;
+  int64_t m, lda;
+  lrs_grid sketch;
+  lrs_grid gram;
+  int32_t q, k, prec;
+  double rtol;
+  int32_t do_svd, do_id;
+  double* U;
+  int64_t ldu;
+  double* S;
+  void* V;
+  int64_t ldv;
+  int32_t* J;
+  double* P;
+  int64_t ldp;
+  int64_t r;
+  double err_svd, err_id;
+  int32_t status;
+  int64_t launches;   /* kernels this item launched */
+  char error[120];    /* lrs_last_error text when status is not OK/ERANK */
+} lrs_batch_item;
+
+lrs_status lrs_batch_run(int device, lrs_batch_item* items, int64_t n_items, int32_t n_streams);
+lrs_status lrs_batch_autotune(int device, lrs_batch_item* items, int64_t n_items, const int32_t* candidates,
+                              int32_t n_candidates, int32_t* best, double* ms_per_item);
+lrs_status lrs_batch_release(int device);
+
 #ifdef __cplusplus
 }
 #endif

@@ -36,6 +36,18 @@ class lrs_grid(C.Structure):
     _fields_ = [("ndim", C.c_int32), ("kind", C.c_int32), ("N", C.c_int64 * 3), ("s", C.c_int32 * 3)]
 
 
+class lrs_batch_item(C.Structure):
+    """Mirror of include/lrs.h's lrs_batch_item (one decomposition of a batch)."""
+    _fields_ = [("A", C.c_void_p), ("dtype", C.c_int32), ("m", C.c_int64), ("lda", C.c_int64),
+                ("sketch", lrs_grid), ("gram", lrs_grid),
+                ("q", C.c_int32), ("k", C.c_int32), ("prec", C.c_int32), ("rtol", C.c_double),
+                ("do_svd", C.c_int32), ("do_id", C.c_int32),
+                ("U", C.c_void_p), ("ldu", C.c_int64), ("S", C.c_void_p), ("V", C.c_void_p),
+                ("ldv", C.c_int64), ("J", C.c_void_p), ("P", C.c_void_p), ("ldp", C.c_int64),
+                ("r", C.c_int64), ("err_svd", C.c_double), ("err_id", C.c_double), ("status", C.c_int32),
+                ("launches", C.c_int64), ("error", C.c_char * 120)]
+
+
 def make_grid(N, s, kind) -> lrs_grid:
     """lrs_grid from per-axis sizes (x first), factors and stencil name/code."""
     g = lrs_grid()
@@ -76,6 +88,10 @@ _SIG = {
     "lrs_gemm_tn": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_void_p, C.c_int32,
                               C.c_int64, C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_int32,
                               C.c_int32, C.c_int64, C.c_int32]),
+    "lrs_batch_run": (C.c_int, [C.c_int, C.c_void_p, C.c_int64, C.c_int32]),
+    "lrs_batch_autotune": (C.c_int, [C.c_int, C.c_void_p, C.c_int64, C.POINTER(C.c_int32), C.c_int32,
+                                     C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
+    "lrs_batch_release": (C.c_int, [C.c_int]),
 }
 
 EXPORTS = tuple(_SIG)
@@ -192,3 +208,29 @@ class Context:
 
 def load(device: int = 0, stream=None) -> Context:
     return Context(device, stream)
+
+
+def run_batch(items, device: int = 0, n_streams: int = 4) -> int:
+    """lrs_batch_run over a ctypes array of lrs_batch_item (status per item in
+    items[i].status); raises LrsError unless every item ended OK or ERANK."""
+    lib = load_library()
+    st = lib.lrs_batch_run(int(device), C.cast(items, C.c_void_p), len(items), int(n_streams))
+    if st != LRS_OK:
+        bad = [(i, it.status, it.error.decode(errors="replace")) for i, it in enumerate(items)
+               if it.status not in (LRS_OK, LRS_ERANK)]
+        raise LrsError(st, f"batch: {len(bad)} item(s) failed, first {bad[:3]}")
+    return st
+
+
+def autotune_batch(items, device: int = 0, candidates=(1, 2, 4, 8)):
+    """lrs_batch_autotune: (best stream count, ms per sampled item)."""
+    lib = load_library()
+    cand = (C.c_int32 * len(candidates))(*candidates)
+    best, ms = C.c_int32(0), C.c_double(0.0)
+    st = lib.lrs_batch_autotune(int(device), C.cast(items, C.c_void_p), len(items), cand, len(candidates),
+                                C.byref(best), C.byref(ms))
+    if st != LRS_OK:
+        bad = [(i, it.status, it.error.decode(errors="replace")) for i, it in enumerate(items)
+               if it.status not in (LRS_OK, LRS_ERANK)]
+        raise LrsError(st, f"batch autotune: {len(bad)} item(s) failed, first {bad[:3]}")
+    return best.value, ms.value

@@ -514,7 +514,7 @@ lrs_status run_apass(lrs_ctx* ctx, const GemmArgs& a, double* fro2_out) {
   }
   P.fro2_part = part;
   auto kern = k_apass<RAW, SA, SX>;
-  LRS_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem));
+  { const lrs_status _s = raise_dyn_smem(ctx, (const void*)kern, (size_t)(cfg.smem)); if (_s) return _s; }
   kern<<<grid, kThreads, cfg.smem, ctx->stream>>>(map, P);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());

@@ -414,7 +414,7 @@ lrs_status launch_cpqr(lrs_ctx* ctx, double* M, int64_t p, int64_t c, int64_t ld
   s.slab_in_smem = slab_bytes <= 200 * 1024 ? 1 : 0;
   const size_t dyn = s.slab_in_smem ? slab_bytes : 0;
   if (dyn > 48 * 1024)
-    LRS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_cpqr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    { const lrs_status _s = raise_dyn_smem(ctx, (const void*)k_cpqr, (size_t)(dyn)); if (_s) return _s; }
   int per_sm = 0;
   LRS_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cpqr, kCpqrThreads, dyn));
   if (per_sm < 1) return lrs_fail(ctx, LRS_ECUDA, "cpqr: kernel does not fit on an SM");
@@ -488,7 +488,7 @@ lrs_status launch_form_q(lrs_ctx* ctx, const double* V, int64_t p, int64_t r, do
   const size_t dyn = sizeof(double) * (size_t)p;
   if (dyn > 200 * 1024) return lrs_fail(ctx, LRS_EINVAL, "form_q: p=%lld too large", (long long)p);
   if (dyn > 48 * 1024)
-    LRS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_form_q, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    { const lrs_status _s = raise_dyn_smem(ctx, (const void*)k_form_q, (size_t)(dyn)); if (_s) return _s; }
   k_form_q<<<(unsigned)r, 512, dyn, ctx->stream>>>(V, p, r, Q, ldq);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
@@ -531,7 +531,7 @@ lrs_status launch_id_coeffs(lrs_ctx* ctx, const double* R, int64_t k, int64_t m,
   const size_t dyn = sizeof(double) * (size_t)(k * k);
   if (dyn > 200 * 1024) return lrs_fail(ctx, LRS_EINVAL, "id: k=%lld too large", (long long)k);
   if (dyn > 48 * 1024)
-    LRS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_id_coeffs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    { const lrs_status _s = raise_dyn_smem(ctx, (const void*)k_id_coeffs, (size_t)(dyn)); if (_s) return _s; }
   const int64_t cols = m - k;
   const unsigned nb = (unsigned)((cols + 127) / 128 > 0 ? (cols + 127) / 128 : 1);
   k_id_coeffs<<<nb, 128, dyn, ctx->stream>>>(R, k, m, perm, J, P, ldp);

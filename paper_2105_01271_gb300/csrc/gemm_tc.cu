@@ -456,7 +456,7 @@ static lrs_status run_tc(lrs_ctx* ctx, const GemmArgs& a, double* fro2_out) {
   }
   P.fro2_part = part;
   auto kern = k_gemm_tc<ADT, SA, SX, NS>;
-  LRS_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem));
+  { const lrs_status _s = raise_dyn_smem(ctx, (const void*)kern, (size_t)(Cfg::kSmem)); if (_s) return _s; }
   const int64_t ntiles = P.Mt * P.Nt * P.splits;
   const unsigned grid = (unsigned)(ntiles < ctx->num_sms ? ntiles : ctx->num_sms);
   kern<<<grid, kThreads, Cfg::kSmem, ctx->stream>>>(P);

@@ -26,6 +26,12 @@ lrs_status lrs_fail(lrs_ctx* ctx, lrs_status st, const char* fmt, ...);
 
 namespace lrs {
 
+// kernel attributes ---------------------------------------------------------
+// Raise (never lower) func's dynamic shared-memory limit on ctx's device; safe
+// across threads.  Every launch with more than 48 KB of dynamic shared memory
+// goes through it.
+lrs_status raise_dyn_smem(lrs_ctx* ctx, const void* func, size_t bytes);
+
 // workspace ---------------------------------------------------------------
 lrs_status ws_reserve(lrs_ctx* ctx, size_t bytes);           // grow (only between calls)
 void* ws_alloc(lrs_ctx* ctx, size_t bytes);                   // 256-B aligned, nullptr if full

@@ -3,6 +3,10 @@
 #include "common.cuh"
 #include "internal.h"
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -129,6 +133,23 @@ static lrs_status orth(lrs_ctx* ctx, const double* Min, int64_t p, int64_t c, in
   st = launch_form_q(ctx, o.V, p, r, Q, ldq);
   if (st) return st;
   *r_out = r;
+  return LRS_OK;
+}
+
+// Raise (never lower) a kernel's dynamic shared-memory limit.  The limit is
+// process-wide state of the function (per device), so contexts running on
+// other threads -- the batch executor's workers -- must never shrink it
+// between another thread's occupancy check and its (cooperative) launch.
+lrs_status raise_dyn_smem(lrs_ctx* ctx, const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> cur;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& c = cur[{func, ctx->device}];
+  if (bytes <= c) return LRS_OK;
+  const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess)
+    return lrs_fail(ctx, LRS_ECUDA, "cudaFuncSetAttribute(%zu B): %s", bytes, cudaGetErrorString(e));
+  c = bytes;
   return LRS_OK;
 }
 

@@ -269,7 +269,7 @@ lrs_status pchol(lrs_ctx* ctx, const double* G, int c, int kmax, double rtol, in
                  double* R, int64_t ldr, int32_t* rank) {
   const size_t dyn = pchol_smem(c);
   if (dyn > 48 * 1024)
-    LRS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_pchol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    { const lrs_status _s = raise_dyn_smem(ctx, (const void*)k_pchol, (size_t)(dyn)); if (_s) return _s; }
   k_pchol<<<1, 256, dyn, ctx->stream>>>(G, c, kmax, rtol, pivot, perm, R, ldr, rank);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
@@ -285,7 +285,7 @@ lrs_status trsm_rows(lrs_ctx* ctx, const double* M, int64_t p, int64_t ldm, cons
   const int rows = 256 / T;
   const size_t dyn = sizeof(double) * (size_t)(r * r + r + rows * (r + 1));
   if (dyn > 48 * 1024)
-    LRS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_trsm_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    { const lrs_status _s = raise_dyn_smem(ctx, (const void*)k_trsm_rows, (size_t)(dyn)); if (_s) return _s; }
   const unsigned nb = (unsigned)((p + rows - 1) / rows);
   k_trsm_rows<<<nb, 256, dyn, ctx->stream>>>(M, p, ldm, perm, R, ldr, r, T, Q, ldq);
   ctx->launches++;

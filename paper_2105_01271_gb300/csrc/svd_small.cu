@@ -101,7 +101,7 @@ static lrs_status tsqr_impl(lrs_ctx* ctx, const void* B, int b_f64, int64_t r, i
   if (C < r) return lrs_fail(ctx, LRS_EINVAL, "svd: rank r=%lld too large for the TSQR tile", (long long)r);
   const size_t dyn = sizeof(T) * (size_t)(r * C);
   auto kern = k_tsqr_leaf<T>;
-  LRS_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  { const lrs_status _s = raise_dyn_smem(ctx, (const void*)kern, (size_t)(dyn)); if (_s) return _s; }
   const void* src = B;
   int src_f64 = b_f64;
   int64_t cur_n = n, cur_ld = ldb;
@@ -229,10 +229,10 @@ lrs_status launch_jacobi(lrs_ctx* ctx, double* R, int64_t r, double* V, double* 
   if (dyn > kSmemCap || r > 1024)
     return lrs_fail(ctx, LRS_EINVAL, "svd: rank r=%lld too large for the Jacobi tile", (long long)r);
   if (fp64) {
-    LRS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_jacobi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    { const lrs_status _s = raise_dyn_smem(ctx, (const void*)k_jacobi<double>, (size_t)(dyn)); if (_s) return _s; }
     k_jacobi<double><<<1, 1024, dyn, ctx->stream>>>(R, r, V, s, 40);
   } else {
-    LRS_CUDA_TRY(ctx, cudaFuncSetAttribute(k_jacobi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    { const lrs_status _s = raise_dyn_smem(ctx, (const void*)k_jacobi<float>, (size_t)(dyn)); if (_s) return _s; }
     k_jacobi<float><<<1, 1024, dyn, ctx->stream>>>(R, r, V, s, 40);
   }
   ctx->launches++;

@@ -286,3 +286,48 @@ def make_workload(w: Workload, rows: slice | None = None, seed_offset: int = 0) 
         return blob_field(w.m, w.N, p["nblobs"], seed, p.get("kappa", 1e-5), w.dtype,
                           rows=rows)
     raise ValueError(w.field)
+
+
+# ----------------------------------------------------------------------------
+# batching form: many matrices of mixed size
+# ----------------------------------------------------------------------------
+@dataclass
+class BatchSpec:
+    field: str          # "heat" or "blob"
+    m: int
+    N: int              # 2-D grid N x N
+    s: int              # full-weighting factor per axis (divides N)
+    k: int
+    seed: int
+
+    @property
+    def n(self) -> int:
+        return self.N * self.N
+
+    @property
+    def l(self) -> int:
+        return (self.N // self.s) ** 2
+
+
+def batch_specs(count: int = 256, seed: int = 3, grids=(32, 64, 128, 256), m_range=(50, 2000),
+                k_range=(5, 60), factors=(2, 4, 8)) -> list:
+    """Seeded list of independent 2-D FP32 problems: grid N^2 from `grids`,
+    m ~ U[m_range], field heat or blob, full-weighting factor from `factors`
+    (powers of two, so they divide N), k ~ U[k_range] capped at min(m, l)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        N = int(rng.choice(grids))
+        m = int(rng.integers(m_range[0], m_range[1] + 1))
+        field = "heat" if rng.integers(0, 2) == 0 else "blob"
+        sf = int(rng.choice(factors))
+        k = int(rng.integers(k_range[0], k_range[1] + 1))
+        l = (N // sf) ** 2
+        out.append(BatchSpec(field, m, N, sf, min(k, m, l), 1000 + i))
+    return out
+
+
+def make_batch_matrix(b: BatchSpec, dtype: str = "f32") -> np.ndarray:
+    if b.field == "heat":
+        return heat_field(b.m, b.N, 2, 16, b.seed, dtype)
+    return blob_field(b.m, b.N, 8, b.seed, 1e-5, dtype)

@@ -12,6 +12,7 @@ import pytest
 import scipy.ndimage as ndi
 
 import oracle
+import synth
 from synth import GridSpec
 
 
@@ -115,3 +116,15 @@ def test_subsample_index_matches_injection():
     A = _rand(3, 128, seed=4)
     np.testing.assert_array_equal(A[:, I], oracle.sketch(A, g))
     np.testing.assert_array_equal(oracle.subsample(A, g), A[:, I])
+
+
+def test_batch_recipe_is_seeded_and_valid():
+    """The batching workload's recipe: deterministic per seed, every factor
+    divides its grid, k <= min(m, l), both field types present."""
+    a = synth.batch_specs(count=256, seed=3)
+    b = synth.batch_specs(count=256, seed=3)
+    assert a == b
+    assert len(a) == 256 and {x.field for x in a} == {"heat", "blob"}
+    for x in a:
+        assert x.N in (32, 64, 128, 256) and x.N % x.s == 0 and 50 <= x.m <= 2000
+        assert 1 <= x.k <= min(x.m, x.l)
