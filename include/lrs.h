@@ -272,6 +272,60 @@ lrs_status lrs_batch_autotune(int device, lrs_batch_item* items, int64_t n_items
                               int32_t n_candidates, int32_t* best, double* ms_per_item);
 lrs_status lrs_batch_release(int device);
 
+/* ------------------------------------------------------------------------
+ * Range error: how much of A_f a basis Q captures.
+ *   *err = ||A_f - Q Q^T A_f||_F / ||A_f||_F = sqrt(1 - ||Q^T A_f||_F^2 / ||A_f||_F^2)
+ * for Q (m x r, row-major ldq) with orthonormal columns.  The products run in
+ * FP64 (the difference of two squared norms must resolve tolerances near
+ * 1e-3, i.e. 1e-6 in the squares).  err is a host pointer.  Synchronises.
+ * ---------------------------------------------------------------------- */
+lrs_status lrs_range_error(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                           const double* Q, int64_t ldq, int64_t r, double* err);
+
+/* ------------------------------------------------------------------------
+ * Learned sketch proposal (an addition to the paper's method): a 3-layer MLP
+ * that maps the top LRS_MLP_NSIGMA singular values of the cheapest
+ * configuration's sketch (the first thing the adaptive enlargement computes)
+ * plus the sizes to one of LRS_MLP_OUT sketch configurations (coarsening
+ * factor, C-PWR passes).
+ * Width LRS_MLP_HID, ReLU, softmax cross-entropy; BF16 weights, FP32
+ * accumulation; trained by Adam in these kernels.
+ *
+ * Parameters: one FP32 buffer of lrs_mlp_param_count() values, laid out
+ *   W1 [HID x IN] | b1 [HID] | W2 [HID x HID] | b2 [HID] | W3 [OUT x HID] | b3 [OUT]
+ * (row-major), the master copy; wbf16 (uint16, same layout) holds the BF16
+ * rounding (RNE) of the weight slots, which the products read.  All device
+ * pointers.
+ *   lrs_mlp_init_bf16  wbf16 <- round(params) on the weight slots
+ *   lrs_mlp_features   x (IN floats) of one matrix from the singular values
+ *                      sigma (device, descending, ns of them) of Q^T Y, where
+ *                      Y (m x l) is the cheapest configuration's sketch and Q
+ *                      its range-finder basis of rank r (rtol 1e-6), grid N:
+ *                      clip(log10(sigma_i / sigma_1), -6, 0) / 6 (missing -1),
+ *                      log2(N) / 8, log2(m) / 11, r / min(m, l)
+ *   lrs_mlp_forward    logits (B x OUT) for X (B x IN)
+ *   lrs_mlp_loss_grad  mean cross-entropy over labels y (B, int32) into *loss
+ *                      (device) and its gradient w.r.t. the BF16 weights and
+ *                      the biases into grad (param layout)
+ *   lrs_mlp_adam       one Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected
+ *                      by `step` >= 1) on params, refreshing wbf16
+ * ---------------------------------------------------------------------- */
+#define LRS_MLP_NSIGMA 64
+#define LRS_MLP_IN 67
+#define LRS_MLP_HID 128
+#define LRS_MLP_OUT 6
+int64_t lrs_mlp_param_count(void);
+lrs_status lrs_mlp_init_bf16(lrs_ctx* ctx, const float* params, uint16_t* wbf16);
+lrs_status lrs_mlp_features(lrs_ctx* ctx, const double* sigma, int64_t ns, int64_t r, int64_t l, int64_t N, int64_t m,
+                            float* x);
+lrs_status lrs_mlp_forward(lrs_ctx* ctx, const float* params, const uint16_t* wbf16, const float* X, int64_t B,
+                           float* logits);
+lrs_status lrs_mlp_loss_grad(lrs_ctx* ctx, const float* params, const uint16_t* wbf16, const float* X,
+                             const int32_t* y, int64_t B, float* grad, float* loss);
+lrs_status lrs_mlp_adam(lrs_ctx* ctx, float* params, uint16_t* wbf16, const float* grad, float* m1, float* m2,
+                        int64_t step, float lr);
+
+
 #ifdef __cplusplus
 }
 #endif

@@ -92,6 +92,17 @@ _SIG = {
     "lrs_batch_autotune": (C.c_int, [C.c_int, C.c_void_p, C.c_int64, C.POINTER(C.c_int32), C.c_int32,
                                      C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "lrs_batch_release": (C.c_int, [C.c_int]),
+    "lrs_range_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_int64,
+                                  C.c_void_p, C.c_int64, C.c_int64, C.POINTER(C.c_double)]),
+    "lrs_mlp_param_count": (C.c_int64, []),
+    "lrs_mlp_init_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lrs_mlp_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
+                                   C.c_void_p]),
+    "lrs_mlp_forward": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
+    "lrs_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                    C.c_void_p, C.c_void_p]),
+    "lrs_mlp_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.c_int64, C.c_float]),
 }
 
 EXPORTS = tuple(_SIG)
@@ -200,6 +211,28 @@ class Context:
         st = self._check(self.lib.lrs_id_k_static(self.h, _ptr(Ysk), m, l, ldy, k, _ptr(J), _ptr(P), ldp,
                                                   C.byref(err)), allow_rank=True)
         return err.value, st
+
+    def range_error(self, A, dtype, m, n, lda, Q, ldq, r) -> float:
+        err = C.c_double(0.0)
+        self._check(self.lib.lrs_range_error(self.h, _ptr(A), dtype, m, n, lda, _ptr(Q), ldq, r, C.byref(err)))
+        return err.value
+
+    def mlp_init_bf16(self, params, wbf16):
+        return self._check(self.lib.lrs_mlp_init_bf16(self.h, _ptr(params), _ptr(wbf16)))
+
+    def mlp_features(self, sigma, ns, r, l, N, m, x):
+        return self._check(self.lib.lrs_mlp_features(self.h, _ptr(sigma), ns, r, l, N, m, _ptr(x)))
+
+    def mlp_forward(self, params, wbf16, X, B, logits):
+        return self._check(self.lib.lrs_mlp_forward(self.h, _ptr(params), _ptr(wbf16), _ptr(X), B, _ptr(logits)))
+
+    def mlp_loss_grad(self, params, wbf16, X, y, B, grad, loss):
+        return self._check(self.lib.lrs_mlp_loss_grad(self.h, _ptr(params), _ptr(wbf16), _ptr(X), _ptr(y), B,
+                                                      _ptr(grad), _ptr(loss)))
+
+    def mlp_adam(self, params, wbf16, grad, m1, m2, step, lr):
+        return self._check(self.lib.lrs_mlp_adam(self.h, _ptr(params), _ptr(wbf16), _ptr(grad), _ptr(m1), _ptr(m2),
+                                                 step, lr))
 
     def gemm_tn(self, M, N, K, X, x_dtype, ldx, A, a_dtype, lda, Cm, c_f64, c_trans, ldc, prec):
         return self._check(self.lib.lrs_gemm_tn(self.h, M, N, K, _ptr(X), x_dtype, ldx, _ptr(A),

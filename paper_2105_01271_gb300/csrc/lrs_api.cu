@@ -509,6 +509,37 @@ lrs_status lrs_id_k(lrs_ctx* ctx, const double* Ysk, int64_t m, int64_t l, int64
   return LRS_OK;
 }
 
+lrs_status lrs_range_error(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                           const double* Q, int64_t ldq, int64_t r, double* err) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  if (!A || !Q || !err) return lrs_fail(ctx, LRS_EINVAL, "range_error: NULL pointer");
+  if (!dtype_ok(dtype) || m < 1 || n < 1 || r < 0 || r > m || lda < n || ldq < r)
+    return lrs_fail(ctx, LRS_EINVAL, "range_error: bad sizes");
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  lrs_status st = ws_reserve(ctx, align256(8 * (size_t)(r * n)) + 4096);
+  if (st) return st;
+  double* B = r > 0 ? (double*)ws_alloc(ctx, 8 * (size_t)(r * n)) : nullptr;
+  double* sq = (double*)ws_alloc(ctx, 16);
+  if ((r > 0 && !B) || !sq) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (range_error)");
+  st = launch_fro2(ctx, A, dtype, m, n, lda, sq);
+  if (st) return st;
+  if (r > 0) {
+    st = gemm(ctx, LRS_PREC_FP64, r, n, m, Q, LRS_F64, ldq, A, dtype, lda, B, 1, 0, n);
+    if (st) return st;
+    st = launch_fro2(ctx, B, LRS_F64, r, n, n, sq + 1);
+    if (st) return st;
+  } else {
+    LRS_CUDA_TRY(ctx, cudaMemsetAsync(sq + 1, 0, 8, ctx->stream));
+  }
+  double* h = (double*)ctx->host_scratch;
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 8, sq, 16, cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  const double a2 = h[8], b2 = h[9];
+  *err = a2 > 0.0 ? sqrt(fmax(0.0, 1.0 - b2 / a2)) : 0.0;
+  return LRS_OK;
+}
+
 lrs_status lrs_gemm_tn(lrs_ctx* ctx, int64_t M, int64_t N, int64_t K, const void* X, int32_t x_dtype,
                        int64_t ldx, const void* A, int32_t a_dtype, int64_t lda, void* C, int32_t c_f64,
                        int32_t c_trans, int64_t ldc, int32_t prec) {
