@@ -18,9 +18,6 @@ import os
 import sys
 import time
 
-for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-    os.environ.setdefault(_v, "1")       # one BLAS thread per worker process
-
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -74,6 +71,8 @@ def build(count, seed, procs):
 
 
 def main():
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(v, "1")       # one BLAS thread per worker (inherited by the spawned pool)
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=1200)
     ap.add_argument("--test", type=int, default=300)
