@@ -12,11 +12,13 @@ a relative Frobenius tolerance:
       ||A - Q Q^T A||_F / ||A||_F <= tol        (tol = 1e-3)
   label = index of the cheapest passing configuration (the last one if none).
 
-Features come from the cheapest configuration's own basis, which the
-adaptive enlargement computes first anyway: Y = A D (full weighting, s = 8),
-Q = range_find(Y, 1e-6) of rank r, and the top 64 singular values of Q^T Y
-as log10(sigma_i / sigma_1) clipped to [-6, 0] and divided by 6 (missing
-values -1); then log2(N) / 8, log2(m) / 11 and r / min(m, l): 67 numbers.
+Features come from the cheapest configuration's range finder, which the
+adaptive enlargement runs first anyway: Y = A D (full weighting, s = 8), its
+pivoted QR Y P = Q R stopped at rtol 1e-6 after r steps, and the leading 64
+diagonal entries d_i = |R_ii| (non-increasing; the rank-revealing part of
+the factorization) as log10(d_i / d_0) clipped to [-6, 0] and divided by 6
+(missing values -1); then log2(N) / 8, log2(m) / 11 and r / min(m, l): 67
+numbers.
 
 The MLP (3 layers, width 128, ReLU, softmax cross-entropy over the 6
 configurations) is restated in float64 with its weights rounded to BF16 as
@@ -28,6 +30,7 @@ from __future__ import annotations
 import numpy as np
 
 from .sketch import as_f64, sketch, subsample
+from .cpqr import cpqr
 from .rangefinder import range_find
 from .cpwr import cpwr
 
@@ -67,12 +70,12 @@ def features(A, N: int) -> np.ndarray:
     A = as_f64(A)
     g, _ = grids_for(N, CONFIGS[0][0], 0)
     Y = sketch(A, g)
-    Q, r = range_find(Y, FEATURE_RTOL)
+    _, R, _, r, _ = cpqr(Y, rtol=FEATURE_RTOL)
     f = -np.ones(N_IN)
-    s = np.linalg.svd(Q.T @ Y, compute_uv=False)[:N_SIGMA] if r > 0 else np.zeros(0)
-    if s.size and s[0] > 0:
-        v = np.log10(np.maximum(s / s[0], 1e-300))
-        f[: s.size] = np.clip(v, -6.0, 0.0) / 6.0
+    d = np.abs(np.diag(R)[: min(r, N_SIGMA)])
+    if d.size and d[0] > 0:
+        v = np.log10(np.maximum(d / d[0], 1e-300))
+        f[: d.size] = np.clip(v, -6.0, 0.0) / 6.0
     m, l = A.shape[0], Y.shape[1]
     f[N_SIGMA] = np.log2(N) / 8.0
     f[N_SIGMA + 1] = np.log2(m) / 11.0

@@ -64,6 +64,7 @@ def test_range_basis_and_label_on_an_exact_rank_field():
     # features: three singular values, the rest missing; rank 3 of min(m, l) = min(40, 16)
     f = L.features(A, N)
     assert np.all(f[:3] > -1.0) and f[0] == 0.0 and np.all(f[3:L.N_SIGMA] == -1.0)
+    assert np.all(np.diff(f[:3]) <= 0.0)              # a pivoted R's diagonal does not increase
     assert f[L.N_SIGMA + 2] == 3 / 16 and f[L.N_SIGMA] == 5 / 8
 
 
