@@ -134,6 +134,12 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
  */
 lrs_status lrs_range_find(lrs_ctx* ctx, const double* G, int64_t m, int64_t l, int64_t ldg,
                           double rtol, double* Q, int64_t ldq, int64_t* r_out);
+/* lrs_range_find that also writes |R_ii| (i < r, non-increasing: the pivoted
+ * factor's diagonal, which reveals the numerical rank) into rdiag (device,
+ * min(m,l) doubles; entries from r on are left as they were).  rdiag NULL is
+ * lrs_range_find. */
+lrs_status lrs_range_find_diag(lrs_ctx* ctx, const double* G, int64_t m, int64_t l, int64_t ldg,
+                               double rtol, double* Q, int64_t ldq, int64_t* r_out, double* rdiag);
 
 /*
  * lrs_svd_k -- TPC-SVD from a range basis (Sec. 3.1, Alg. 2):
@@ -284,10 +290,10 @@ lrs_status lrs_range_error(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m
 
 /* ------------------------------------------------------------------------
  * Learned sketch proposal (an addition to the paper's method): a 3-layer MLP
- * that maps the top LRS_MLP_NSIGMA singular values of the cheapest
- * configuration's sketch (the first thing the adaptive enlargement computes)
- * plus the sizes to one of LRS_MLP_OUT sketch configurations (coarsening
- * factor, C-PWR passes).
+ * that maps the leading LRS_MLP_NSIGMA diagonal entries of the pivoted R of
+ * the cheapest configuration's sketch (the first thing the adaptive
+ * enlargement computes) plus the sizes to one of LRS_MLP_OUT sketch
+ * configurations (coarsening factor, C-PWR passes).
  * Width LRS_MLP_HID, ReLU, softmax cross-entropy; BF16 weights, FP32
  * accumulation; trained by Adam in these kernels.
  *
@@ -297,11 +303,11 @@ lrs_status lrs_range_error(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m
  * rounding (RNE) of the weight slots, which the products read.  All device
  * pointers.
  *   lrs_mlp_init_bf16  wbf16 <- round(params) on the weight slots
- *   lrs_mlp_features   x (IN floats) of one matrix from the singular values
- *                      sigma (device, descending, ns of them) of Q^T Y, where
- *                      Y (m x l) is the cheapest configuration's sketch and Q
- *                      its range-finder basis of rank r (rtol 1e-6), grid N:
- *                      clip(log10(sigma_i / sigma_1), -6, 0) / 6 (missing -1),
+ *   lrs_mlp_features   x (IN floats) of one matrix from d = |R_ii| (device,
+ *                      non-increasing, ns of them) written by
+ *                      lrs_range_find_diag for the cheapest configuration's
+ *                      sketch Y (m x l) at rtol 1e-6, rank r, grid N:
+ *                      clip(log10(d_i / d_0), -6, 0) / 6 (missing -1),
  *                      log2(N) / 8, log2(m) / 11, r / min(m, l)
  *   lrs_mlp_forward    logits (B x OUT) for X (B x IN)
  *   lrs_mlp_loss_grad  mean cross-entropy over labels y (B, int32) into *loss
@@ -316,7 +322,7 @@ lrs_status lrs_range_error(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m
 #define LRS_MLP_OUT 6
 int64_t lrs_mlp_param_count(void);
 lrs_status lrs_mlp_init_bf16(lrs_ctx* ctx, const float* params, uint16_t* wbf16);
-lrs_status lrs_mlp_features(lrs_ctx* ctx, const double* sigma, int64_t ns, int64_t r, int64_t l, int64_t N, int64_t m,
+lrs_status lrs_mlp_features(lrs_ctx* ctx, const double* rdiag, int64_t ns, int64_t r, int64_t l, int64_t N, int64_t m,
                             float* x);
 lrs_status lrs_mlp_forward(lrs_ctx* ctx, const float* params, const uint16_t* wbf16, const float* X, int64_t B,
                            float* logits);

@@ -78,6 +78,8 @@ _SIG = {
                                  C.c_int64, C.POINTER(C.c_int64)]),
     "lrs_range_find": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64,
                                  C.c_double, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
+    "lrs_range_find_diag": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64,
+                                      C.c_double, C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.c_void_p]),
     "lrs_svd_k": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_int64,
                             C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_void_p,
                             C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
@@ -193,6 +195,12 @@ class Context:
                                             C.byref(r)))
         return r.value
 
+    def range_find_diag(self, G, m, l, ldg, rtol, Q, ldq, rdiag) -> int:
+        r = C.c_int64(0)
+        self._check(self.lib.lrs_range_find_diag(self.h, _ptr(G), m, l, ldg, rtol, _ptr(Q), ldq,
+                                                 C.byref(r), _ptr(rdiag)))
+        return r.value
+
     def svd_k(self, A, dtype, m, n, lda, Q, ldq, r, k, prec, U, ldu, S, V, ldv):
         err = C.c_double(0.0)
         st = self._check(self.lib.lrs_svd_k(self.h, _ptr(A), dtype, m, n, lda, _ptr(Q), ldq, r, k,
@@ -220,8 +228,8 @@ class Context:
     def mlp_init_bf16(self, params, wbf16):
         return self._check(self.lib.lrs_mlp_init_bf16(self.h, _ptr(params), _ptr(wbf16)))
 
-    def mlp_features(self, sigma, ns, r, l, N, m, x):
-        return self._check(self.lib.lrs_mlp_features(self.h, _ptr(sigma), ns, r, l, N, m, _ptr(x)))
+    def mlp_features(self, rdiag, ns, r, l, N, m, x):
+        return self._check(self.lib.lrs_mlp_features(self.h, _ptr(rdiag), ns, r, l, N, m, _ptr(x)))
 
     def mlp_forward(self, params, wbf16, X, B, logits):
         return self._check(self.lib.lrs_mlp_forward(self.h, _ptr(params), _ptr(wbf16), _ptr(X), B, _ptr(logits)))

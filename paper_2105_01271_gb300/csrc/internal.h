@@ -116,8 +116,11 @@ bool orth_gram_eligible(int64_t p, int64_t c, double rtol);
 size_t orth_gram_ws(int64_t p, int64_t c, int num_sms);
 // refine = false: skip the Cholesky-QR2 pass (well-conditioned basis of the
 // same range, orthonormal only to ~u cond^2; for intermediate C-PWR iterates)
+// rdiag (optional, device): |R_ii| of the pivoted factor, i < r
 lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldm, double rtol,
-                            double* Q, int64_t ldq, int64_t* r_out, bool refine = true);
+                            double* Q, int64_t ldq, int64_t* r_out, bool refine = true, double* rdiag = nullptr);
+// out[i] = |R[i * ld + i]|, i < r (device pointers)
+lrs_status launch_abs_diag(lrs_ctx* ctx, const double* R, int64_t ld, int64_t r, double* out);
 
 // R (r x r upper, row-major, positive diagonal) with R^T R = B B^T for a wide
 // FP32 B (r x n, r <= 128): double-float Gram on the FP32 pipe + FP64

@@ -104,13 +104,27 @@ static size_t orth_ws(int64_t p, int64_t c, int num_sms) {
 // intermediate = true: the basis only feeds a product that is orthonormalised
 // again (the W^T G step of C-PWR), so a well-conditioned basis of the same
 // range suffices (the Gram route then skips its refinement pass).
+__global__ void k_abs_diag(const double* __restrict__ R, int64_t ld, int64_t r, double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < r) out[i] = fabs(R[i * ld + i]);
+}
+
+lrs_status launch_abs_diag(lrs_ctx* ctx, const double* R, int64_t ld, int64_t r, double* out) {
+  if (r < 1) return LRS_OK;
+  k_abs_diag<<<(unsigned)((r + 255) / 256), 256, 0, ctx->stream>>>(R, ld, r, out);
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
+
 static lrs_status orth(lrs_ctx* ctx, const double* Min, int64_t p, int64_t c, int64_t ldi,
-                       double rtol, double* Q, int64_t ldq, int64_t* r_out, bool intermediate = false) {
+                       double rtol, double* Q, int64_t ldq, int64_t* r_out, bool intermediate = false,
+                       double* rdiag = nullptr) {
   const int64_t kmax = p < c ? p : c;
   if (orth_gram_eligible(p, c, rtol)) {
     // tall-skinny: pivoted Cholesky of the Gram (same pivots and stop rule)
     const size_t mark = ctx->ws_top;
-    lrs_status gs = launch_orth_gram(ctx, Min, p, c, ldi, rtol, Q, ldq, r_out, !intermediate);
+    lrs_status gs = launch_orth_gram(ctx, Min, p, c, ldi, rtol, Q, ldq, r_out, !intermediate, rdiag);
     ctx->ws_top = mark;
     if (gs != LRS_ERANK) return gs;
   }
@@ -130,6 +144,10 @@ static lrs_status orth(lrs_ctx* ctx, const double* Min, int64_t p, int64_t c, in
   int32_t r = 0;
   LRS_CUDA_TRY(ctx, cudaMemcpyAsync(&r, o.rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
   LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (rdiag && r > 0) {
+    st = launch_abs_diag(ctx, o.R, c, r, rdiag);
+    if (st) return st;
+  }
   st = launch_form_q(ctx, o.V, p, r, Q, ldq);
   if (st) return st;
   *r_out = r;
@@ -223,6 +241,11 @@ lrs_status lrs_sketch(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int
 
 lrs_status lrs_range_find(lrs_ctx* ctx, const double* G, int64_t m, int64_t l, int64_t ldg,
                           double rtol, double* Q, int64_t ldq, int64_t* r_out) {
+  return lrs_range_find_diag(ctx, G, m, l, ldg, rtol, Q, ldq, r_out, nullptr);
+}
+
+lrs_status lrs_range_find_diag(lrs_ctx* ctx, const double* G, int64_t m, int64_t l, int64_t ldg,
+                               double rtol, double* Q, int64_t ldq, int64_t* r_out, double* rdiag) {
   if (!ctx) return LRS_EINVAL;
   ctx->err[0] = 0;
   if (!G || !Q || !r_out) return lrs_fail(ctx, LRS_EINVAL, "range_find: NULL pointer");
@@ -232,7 +255,7 @@ lrs_status lrs_range_find(lrs_ctx* ctx, const double* G, int64_t m, int64_t l, i
   LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   lrs_status st = ws_reserve(ctx, orth_ws(m, l, ctx->num_sms));
   if (st) return st;
-  return orth(ctx, G, m, l, ldg, rtol, Q, ldq, r_out);
+  return orth(ctx, G, m, l, ldg, rtol, Q, ldq, r_out, false, rdiag);
 }
 
 lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t lda,

@@ -112,8 +112,8 @@ __global__ void k_round_weights(const float* __restrict__ p, uint16_t* __restric
   if (i < kParams) w[i] = is_weight_slot(i) ? __bfloat16_as_ushort(__float2bfloat16_rn(p[i])) : (uint16_t)0;
 }
 
-// features of one matrix from the singular values (descending) of Q^T Y for
-// the cheapest configuration's sketch Y and basis Q (rank r, l columns)
+// features of one matrix from |R_ii| (non-increasing) of the range finder's
+// pivoted factor of the cheapest configuration's sketch (rank r, l columns)
 __global__ void k_features(const double* __restrict__ s, int64_t ns, double r, double l, double N, double m,
                            float* __restrict__ x) {
   for (int i = threadIdx.x; i < kIn; i += blockDim.x) {
@@ -180,14 +180,14 @@ lrs_status lrs_mlp_init_bf16(lrs_ctx* ctx, const float* params, uint16_t* wbf16)
   return LRS_OK;
 }
 
-lrs_status lrs_mlp_features(lrs_ctx* ctx, const double* sigma, int64_t ns, int64_t r, int64_t l, int64_t N, int64_t m,
+lrs_status lrs_mlp_features(lrs_ctx* ctx, const double* rdiag, int64_t ns, int64_t r, int64_t l, int64_t N, int64_t m,
                             float* x) {
   if (!ctx) return LRS_EINVAL;
   ctx->err[0] = 0;
-  if ((!sigma && ns > 0) || !x || ns < 0 || r < 0 || l < 1 || N < 1 || m < 1)
+  if ((!rdiag && ns > 0) || !x || ns < 0 || r < 0 || l < 1 || N < 1 || m < 1)
     return lrs_fail(ctx, LRS_EINVAL, "mlp_features: bad arguments");
   LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-  k_features<<<1, 128, 0, ctx->stream>>>(sigma, ns, (double)r, (double)l, (double)N, (double)m, x);
+  k_features<<<1, 128, 0, ctx->stream>>>(rdiag, ns, (double)r, (double)l, (double)N, (double)m, x);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
   return LRS_OK;

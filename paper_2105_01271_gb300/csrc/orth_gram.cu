@@ -407,7 +407,7 @@ size_t orth_gram_ws(int64_t p, int64_t c, int num_sms) {
 }
 
 lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldm, double rtol,
-                            double* Q, int64_t ldq, int64_t* r_out, bool refine) {
+                            double* Q, int64_t ldq, int64_t* r_out, bool refine, double* rdiag) {
   const int ci = (int)c;
   double* G = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(c * c));
   double* R = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(c * c));
@@ -427,6 +427,10 @@ lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c,
   const int r = h[40];
   *r_out = r;
   if (r == 0) return LRS_OK;
+  if (rdiag) {
+    st = launch_abs_diag(ctx, R, c, r, rdiag);
+    if (st) return st;
+  }
   if (!refine) return trsm_rows(ctx, M, p, ldm, perm, R, c, r, Q, ldq);
   st = trsm_rows(ctx, M, p, ldm, perm, R, c, r, Q1, r);
   if (st) return st;

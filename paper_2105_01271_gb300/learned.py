@@ -8,9 +8,9 @@ the configurations
     CONFIGS = (s, q): (8, 0), (8, 1), (4, 0), (4, 1), (2, 0), (2, 1)   (cheapest first)
 
 in order until the range error of the method's basis meets the tolerance.
-The proposal reads the top 64 singular values of the first configuration's
-sketch (computed by either variant anyway), runs the MLP of include/lrs.h on
-them, and jumps to the predicted configuration, enlarging from there if it
+The proposal reads the leading 64 diagonal entries of the pivoted R that the
+range finder computes for the first configuration's sketch (which either
+variant computes anyway), runs the MLP of include/lrs.h on them, and jumps to the predicted configuration, enlarging from there if it
 still misses.  `decompose_to_tolerance` runs either variant and reports the
 configurations it tried.
 """
@@ -22,7 +22,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from .binding import DTYPE, LRS_PREC_FP64, LRS_PREC_SPLIT_BF16, Context, load_library, make_grid
+from .binding import DTYPE, LRS_PREC_SPLIT_BF16, Context, load_library, make_grid
 
 CONFIGS = [(8, 0), (8, 1), (4, 0), (4, 1), (2, 0), (2, 1)]
 N_SIGMA, N_IN, N_HID, N_OUT = 64, 67, 128, 6
@@ -96,25 +96,22 @@ class Buffers:
     Y: torch.Tensor
     G: torch.Tensor
     Q: torch.Tensor
-    sU: torch.Tensor
-    sS: torch.Tensor
-    sV: torch.Tensor
+    d: torch.Tensor
     x: torch.Tensor
 
 
 def buffers(m: int, N: int, device) -> Buffers:
     l = (N // 2) ** 2                      # the finest configuration's coarse size
     w = max(l, m)
-    l0 = (N // CONFIGS[0][0]) ** 2
     f64 = torch.float64
     e = lambda *shape: torch.empty(shape, dtype=f64, device=device)
-    return Buffers(e(m, w), e(m, w), e(m, w), e(m, N_SIGMA), e(N_SIGMA), e(max(l0, 1), N_SIGMA),
-                   torch.empty((1, N_IN), dtype=torch.float32, device=device))
+    return Buffers(e(m, w), e(m, w), e(m, w), e(w), torch.empty((1, N_IN), dtype=torch.float32, device=device))
 
 
-def basis(ctx: Context, A: torch.Tensor, m: int, N: int, cfg: int, bufs: Buffers, rtol: float = 1e-6):
+def basis(ctx: Context, A: torch.Tensor, m: int, N: int, cfg: int, bufs: Buffers, rtol: float = 1e-6,
+          diag: bool = False):
     """The method's orthonormal basis for configuration `cfg`: (Q, ldq, r, l).
-    For q = 0 the sketch stays in bufs.G (m x l)."""
+    With diag (q = 0 only) the range finder also leaves |R_ii| in bufs.d."""
     s, q = CONFIGS[cfg]
     g = make_grid((N, N), (s, s), "fullweight")
     gram = make_grid((N, N), (2, 2), "inject") if q > 0 else None
@@ -123,18 +120,17 @@ def basis(ctx: Context, A: torch.Tensor, m: int, N: int, cfg: int, bufs: Buffers
     if q > 0:
         return bufs.G, l, gc, l
     ldq = min(m, l)
-    r = ctx.range_find(bufs.G, m, gc, l, rtol, bufs.Q, ldq)
+    if diag:
+        r = ctx.range_find_diag(bufs.G, m, gc, l, rtol, bufs.Q, ldq, bufs.d)
+    else:
+        r = ctx.range_find(bufs.G, m, gc, l, rtol, bufs.Q, ldq)
     return bufs.Q, ldq, r, l
 
 
-def basis_features(ctx: Context, m: int, N: int, bufs: Buffers, r: int, ldq: int, l: int) -> torch.Tensor:
-    """Features of one matrix from the first configuration's sketch (bufs.G)
-    and basis (bufs.Q, rank r): singular values of Q^T Y in FP64, then the
-    feature map of lrs_mlp_features."""
-    k = min(N_SIGMA, r)
-    if k > 0:
-        ctx.svd_k(bufs.G, DTYPE["f64"], m, l, l, bufs.Q, ldq, r, k, LRS_PREC_FP64, bufs.sU, k, bufs.sS, bufs.sV, k)
-    ctx.mlp_features(bufs.sS, k, r, l, N, m, bufs.x)
+def basis_features(ctx: Context, m: int, N: int, bufs: Buffers, r: int, l: int) -> torch.Tensor:
+    """Features of one matrix from the first configuration's range finder
+    (|R_ii| in bufs.d, rank r): the feature map of lrs_mlp_features."""
+    ctx.mlp_features(bufs.d, min(N_SIGMA, r), r, l, N, m, bufs.x)
     return bufs.x
 
 
@@ -159,9 +155,9 @@ def decompose_to_tolerance(ctx: Context, A: torch.Tensor, m: int, N: int, tol: f
     cfg = 0 if start is None else int(start)
     have = False
     if model is not None:
-        Q, ldq, r, l = basis(ctx, A, m, N, 0, bufs)
+        Q, ldq, r, l = basis(ctx, A, m, N, 0, bufs, diag=True)
         have = True
-        x = basis_features(ctx, m, N, bufs, r, ldq, l)
+        x = basis_features(ctx, m, N, bufs, r, l)
         cfg = run.predicted = int(model.logits(x).argmax(dim=1).item())
     while True:
         if not (have and cfg == 0):

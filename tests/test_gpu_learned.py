@@ -120,14 +120,14 @@ def test_basis_features_match_oracle(lrs, spec):
     m, N = A.shape[0], spec["N"]
     Ad = torch.from_numpy(A).cuda()
     bufs = learned.buffers(m, N, Ad.device)
-    Q, ldq, r, l = learned.basis(lrs, Ad, m, N, 0, bufs)
-    x = learned.basis_features(lrs, m, N, bufs, r, ldq, l).cpu().numpy().ravel().astype(np.float64)
+    Q, ldq, r, l = learned.basis(lrs, Ad, m, N, 0, bufs, diag=True)
+    x = learned.basis_features(lrs, m, N, bufs, r, l).cpu().numpy().ravel().astype(np.float64)
     xo = L.features(A, N)
     # the sizes are exact; the rank may differ by one at the stop threshold
     assert np.allclose(x[L.N_SIGMA:L.N_SIGMA + 2], xo[L.N_SIGMA:L.N_SIGMA + 2], atol=1e-6)
     ro = int(round(xo[-1] * min(m, l)))
     assert abs(r - ro) <= 1
-    # log singular values: close where they are clear of the clip at 1e-6
+    # log |R_ii|: close where they are clear of the clip at 1e-6
     clear = xo[:L.N_SIGMA] > -0.9
     assert np.max(np.abs(x[:L.N_SIGMA][clear] - xo[:L.N_SIGMA][clear]), initial=0.0) <= 1e-4
     assert np.all(x[:L.N_SIGMA][~clear] <= -0.85)
