@@ -38,7 +38,7 @@ UNIT = "decomps/s"
 # DRAM bytes (read + write) of one A-pass launch from an ncu capture of the
 # current kernel (profiles/k_apass_<workload>.md); set to None when the kernel
 # changes until it is captured again.
-APASS_TRAFFIC = {("blob2d_m2000_512x512_f32", "split_bf16"): None,
+APASS_TRAFFIC = {("blob2d_m2000_512x512_f32", "split_bf16"): 2.107053e9 + 72.585728e6,
                  ("heat3d_m500_256c_bf16", "split_bf16"): 16.779508e9 + 7.618061e9}
 # FP64 nominal of the part: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
@@ -114,10 +114,27 @@ def clocks_start(dev):
                                "-lms", "200", "-i", str(dev)], stdout=f, stderr=subprocess.DEVNULL)
     except Exception:
         pr = None
+    # wait for the first sample: the query tool's start-up (seconds on a fresh
+    # machine, during which it can hold up this process's launches) must end
+    # before the warm-up, so it never falls inside the timed region
+    t0 = time.time()
+    while pr is not None and pr.poll() is None and time.time() - t0 < 20.0:
+        if os.path.getsize(f.name) > 0:
+            break
+        time.sleep(0.05)
     return pr, f
 
 
-def clocks_stop(h):
+def clocks_mark(h) -> int:
+    """Samples written so far (those before the timed region are dropped)."""
+    pr, f = h
+    if pr is None:
+        return 0
+    with open(f.name) as g:
+        return len(g.read().splitlines())
+
+
+def clocks_stop(h, skip: int = 0):
     pr, f = h
     if pr is None:
         return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -129,7 +146,7 @@ def clocks_stop(h):
     f.seek(0)
     sm, mx, reasons = [], [], set()
     names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-    for line in f.read().splitlines():
+    for line in f.read().splitlines()[skip:]:
         parts = [x.strip() for x in line.split(",")]
         if len(parts) < 7:
             continue
@@ -254,10 +271,12 @@ def run_batch_bench(args, rank, world):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def timed(nstreams, steps):
+    def timed(nstreams, steps, clk=None):
         for _ in range(args.warmup):
             binding.run_batch(items, dev, nstreams)
         barrier()
+        if clk is not None:
+            timed.mark = clocks_mark(clk)
         t0 = time.perf_counter()
         for _ in range(steps):
             binding.run_batch(items, dev, nstreams)
@@ -265,8 +284,8 @@ def run_batch_bench(args, rank, world):
         return (time.perf_counter() - t0) * 1e3 / steps
 
     clk = clocks_start(dev)
-    ms = max_over_ranks(timed(best, args.steps), world, f"cuda:{dev}")
-    clocks = clocks_stop(clk)
+    ms = max_over_ranks(timed(best, args.steps, clk), world, f"cuda:{dev}")
+    clocks = clocks_stop(clk, timed.mark)
     launches = sum(int(it.launches) for it in items)
     statuses = [int(it.status) for it in items]
     loop_ms = max_over_ranks(timed(1, max(1, min(args.steps, 3))), world, f"cuda:{dev}")
@@ -347,6 +366,7 @@ def run_ours(args, rank, world):
         d = path.id_path(ctx, A_d, w.dtype, w.grid, w.k, q=w.q, gram=w.gram, rtol=rtol, prec=prec, bufs=bufs)
         return s, d
 
+    clk = clocks_start(dev)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             s, d = step()
@@ -359,8 +379,8 @@ def run_ours(args, rank, world):
 
     # ---- timed region (device time, CUDA events on the library's stream) ----
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clk = clocks_start(dev)
     barrier()
+    mark = clocks_mark(clk)
     l0 = ctx.launches
     with torch.cuda.stream(stream):
         ev0.record(stream)
@@ -369,7 +389,7 @@ def run_ours(args, rank, world):
         ev1.record(stream)
     stream.synchronize()
     barrier()
-    clocks = clocks_stop(clk)
+    clocks = clocks_stop(clk, mark)
     launches = (ctx.launches - l0) // max(args.steps, 1)
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, f"cuda:{dev}")
     value = job_throughput(world, ms)
