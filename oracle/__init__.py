@@ -19,6 +19,11 @@ numpy/scipy (LAPACK) as the only library steps:
   cpwr.py         Sec. 5, Alg. 7: coarse-grid power iteration.
   svd.py          Sec. 3.1, Alg. 2: TPC-SVD projection B = Q^T A_f and SVD(B).
   interp.py       Sec. 4, Alg. 4: TPC-ID (row ID of the sketch by CPQR of A_c^T).
+  spc.py          Sec. 4, Algs. 5/6: SPC-ID lifting operator T_r, the
+                  single-pass error estimate eps_hat(tau) and the SPC-ID
+                  error bound.
+  learned.py      the learned sketch proposal (not in the paper): features,
+                  labels, the MLP and Adam in float64.
   metrics.py      Sec. 6: relative Frobenius error, Eckart-Young, MREO.
 
 Pins (tests/test_oracle_*.py) tie each routine to something other than itself:
