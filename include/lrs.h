@@ -178,6 +178,42 @@ lrs_status lrs_id_k(lrs_ctx* ctx, const double* Ysk, int64_t m, int64_t l, int64
                     int32_t* J, double* P, int64_t ldp, double* err_est);
 
 /*
+ * lrs_spc_lift -- the lifted row skeleton of SPC-ID (Sec. 4, Alg. 5):
+ *   S_f = A_c(J,:) T_r  (k x n),   T_r = A_c^+ U_r U_r^T A_f,
+ * so that A_f ~ P S_f with (J, P) the rank-k row ID of the sketch A_c = Y
+ * (lrs_id_k).  T_r is Alg. 5's lifting operator after its H^T = A_c^T A_f is
+ * substituted.  U_r (m x r), S_r (r), V_r (l x r) are the leading r singular
+ * triplets of Y, as lrs_svd_k returns them for A = Y (FP64) and Q a range
+ * basis of Y; k <= r <= min(m, l) and s_r > 0.  Computed as
+ *   X = U_r S_r^-1 V_r^T Y(J,:)^T (m x k, FP64),  S_f = X^T A_f,
+ * the second product being one read of A_f by the A-pass kernel in `prec`.
+ *   A   m x n in dtype (row stride lda).   Y  m x l FP64 (row stride ldy).
+ *   U   row stride ldu >= r;  V  row stride ldv >= r;  S, J device.
+ *   Sf  k x n (row stride ldsf >= n): FP64 when prec == LRS_PREC_FP64, else FP32.
+ * EINVAL: sizes or strides out of range, s_r <= 0 (read back: synchronises once).
+ */
+lrs_status lrs_spc_lift(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                        const double* Y, int64_t l, int64_t ldy, const double* U, int64_t ldu, const double* S,
+                        const double* V, int64_t ldv, int64_t r, const int32_t* J, int32_t k, int32_t prec,
+                        void* Sf, int64_t ldsf);
+
+/*
+ * lrs_spc_err -- SPC-ID-ERR (Sec. 4, Alg. 6): with every c-th snapshot kept,
+ * B_f = A_f(J,:) and B_c = Y(J,:) for the 0-based rows J = c-1, 2c-1, ...
+ * (m_c = floor(m / c) of them, 1 <= m_c <= 128),
+ *   eps_hat[i] = c * lambda_max(B_f B_f^T - taus[i] B_c B_c^T),  i < ntau,
+ * the estimate of eps(tau) in the SPC-ID error bound, for each tau >= 0 of the
+ * caller's grid (the bound minimises over tau together with its other terms).
+ * Grams in FP64 (FP32 data: double-float accumulation), lambda_max by cyclic
+ * Jacobi (one block per tau, at most 40 sweeps).
+ *   A  m x n in dtype (row stride lda).   Y  m x l FP64 (row stride ldy).
+ *   taus, eps_hat: HOST arrays of ntau doubles.  Synchronises.
+ */
+lrs_status lrs_spc_err(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                       const double* Y, int64_t l, int64_t ldy, int32_t c, const double* taus, int32_t ntau,
+                       double* eps_hat);
+
+/*
  * lrs_gemm_tn -- the dense contraction every A-pass uses:
  *   C (M x N) = X^T A,   X: K x M,  A: K x N  (both row-major, K rows).
  * Exposed for tests and benchmarks of the A-pass kernel alone.

@@ -96,6 +96,13 @@ _SIG = {
     "lrs_batch_release": (C.c_int, [C.c_int]),
     "lrs_range_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_int64,
                                   C.c_void_p, C.c_int64, C.c_int64, C.POINTER(C.c_double)]),
+    "lrs_spc_lift": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_int64,
+                               C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                               C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int32, C.c_int32,
+                               C.c_void_p, C.c_int64]),
+    "lrs_spc_err": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_int64,
+                              C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.POINTER(C.c_double), C.c_int32,
+                              C.POINTER(C.c_double)]),
     "lrs_mlp_param_count": (C.c_int64, []),
     "lrs_mlp_init_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "lrs_mlp_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
@@ -224,6 +231,17 @@ class Context:
         err = C.c_double(0.0)
         self._check(self.lib.lrs_range_error(self.h, _ptr(A), dtype, m, n, lda, _ptr(Q), ldq, r, C.byref(err)))
         return err.value
+
+    def spc_lift(self, A, dtype, m, n, lda, Y, l, ldy, U, ldu, S, V, ldv, r, J, k, prec, Sf, ldsf):
+        return self._check(self.lib.lrs_spc_lift(self.h, _ptr(A), dtype, m, n, lda, _ptr(Y), l, ldy, _ptr(U), ldu,
+                                                 _ptr(S), _ptr(V), ldv, r, _ptr(J), k, prec, _ptr(Sf), ldsf))
+
+    def spc_err(self, A, dtype, m, n, lda, Y, l, ldy, c, taus) -> list:
+        nt = len(taus)
+        t = (C.c_double * nt)(*[float(x) for x in taus])
+        out = (C.c_double * nt)()
+        self._check(self.lib.lrs_spc_err(self.h, _ptr(A), dtype, m, n, lda, _ptr(Y), l, ldy, c, t, nt, out))
+        return list(out)
 
     def mlp_init_bf16(self, params, wbf16):
         return self._check(self.lib.lrs_mlp_init_bf16(self.h, _ptr(params), _ptr(wbf16)))

@@ -127,6 +127,10 @@ lrs_status launch_abs_diag(lrs_ctx* ctx, const double* R, int64_t ld, int64_t r,
 // Cholesky.  LRS_ERANK (nothing reported) when the Cholesky breaks down; the
 // caller then runs TSQR.  Synchronises.
 size_t r_of_bt_gram_ws(int64_t r, int num_sms);
+// G (r x r FP64, both triangles) = B B^T for B r x n FP32 (row stride ldb),
+// double-float accumulation (r <= 128); workspace gram_df_ws(r, num_sms)
+size_t gram_df_ws(int64_t r, int num_sms);
+lrs_status launch_gram_df(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, int64_t ldb, double* G);
 lrs_status launch_r_of_bt_gram(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, int64_t ldb, double* R);
 
 // svd_small.cu ------------------------------------------------------------------

@@ -452,14 +452,18 @@ lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c,
 
 namespace lrs {
 
-size_t r_of_bt_gram_ws(int64_t r, int num_sms) {
+size_t gram_df_ws(int64_t r, int num_sms) {
   auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
-  return 2 * a256(sizeof(float) * 2 * (size_t)num_sms * (size_t)(r * r)) + a256(sizeof(double) * (size_t)(r * r)) +
-         a256(4 * (size_t)r) + a256(8) + 1024;
+  return 2 * a256(sizeof(float) * 2 * (size_t)num_sms * (size_t)(r * r)) + 512;
 }
 
-lrs_status launch_r_of_bt_gram(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, int64_t ldb, double* R) {
-  if (r < 1 || r > kMaxC) return lrs_fail(ctx, LRS_EINVAL, "svd: r=%lld out of range for the Gram route", (long long)r);
+size_t r_of_bt_gram_ws(int64_t r, int num_sms) {
+  auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+  return gram_df_ws(r, num_sms) + a256(sizeof(double) * (size_t)(r * r)) + a256(4 * (size_t)r) + a256(8) + 512;
+}
+
+lrs_status launch_gram_df(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, int64_t ldb, double* G) {
+  if (r < 1 || r > kMaxC || n < 1) return lrs_fail(ctx, LRS_EINVAL, "gram: r=%lld n=%lld out of range", (long long)r, (long long)n);
   const int ri = (int)r;
   const int nt = (ri + 3) / 4, ntiles = nt * (nt + 1) / 2;
   int64_t nb = 2 * (int64_t)ctx->num_sms;         // two blocks per SM: few tiles leave warps idle
@@ -468,10 +472,7 @@ lrs_status launch_r_of_bt_gram(lrs_ctx* ctx, const float* B, int64_t r, int64_t 
   nb = (n + cols_b - 1) / cols_b;
   float* hi = (float*)ws_alloc(ctx, sizeof(float) * (size_t)(nb * r * r));
   float* lo = (float*)ws_alloc(ctx, sizeof(float) * (size_t)(nb * r * r));
-  double* G = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(r * r));
-  int32_t* perm = (int32_t*)ws_alloc(ctx, 4 * (size_t)r);
-  int32_t* rank = (int32_t*)ws_alloc(ctx, 8);
-  if (!hi || !lo || !G || !perm || !rank) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd gram)");
+  if (!hi || !lo) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (double-float gram)");
   const size_t dyn = sizeof(float) * (size_t)(nt * 4 * kDfCols);
   const int tpt = (ntiles + 255) / 256;
   if (tpt <= 1) k_gram_df<1><<<(unsigned)nb, 256, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
@@ -481,6 +482,18 @@ lrs_status launch_r_of_bt_gram(lrs_ctx* ctx, const float* B, int64_t r, int64_t 
   k_gram_df_reduce<<<(ri * ri + 255) / 256, 256, 0, ctx->stream>>>(hi, lo, (int)nb, ri, G);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
+
+lrs_status launch_r_of_bt_gram(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, int64_t ldb, double* R) {
+  if (r < 1 || r > kMaxC) return lrs_fail(ctx, LRS_EINVAL, "svd: r=%lld out of range for the Gram route", (long long)r);
+  const int ri = (int)r;
+  double* G = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(r * r));
+  int32_t* perm = (int32_t*)ws_alloc(ctx, 4 * (size_t)r);
+  int32_t* rank = (int32_t*)ws_alloc(ctx, 8);
+  if (!G || !perm || !rank) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd gram)");
+  lrs_status gs = launch_gram_df(ctx, B, r, n, ldb, G);
+  if (gs) return gs;
   lrs_status st = pchol(ctx, G, ri, ri, 0.0, 0, perm, R, r, rank);
   if (st) return st;
   int32_t* h = (int32_t*)ctx->host_scratch;

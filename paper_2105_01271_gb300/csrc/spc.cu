@@ -1,0 +1,347 @@
+// SPC-ID lifting (Sec. 4, Alg. 5) and its single-pass error estimate
+// SPC-ID-ERR (Alg. 6), declared in include/lrs.h.
+//
+// Lifting.  With the SVD of the sketch A_c = Y (U_r, S_r, V_r: its leading r
+// triplets) and the row ID's skeleton rows J, the lifted skeleton is
+//     S_f = A_c(J,:) T_r = A_c(J,:) V_r S_r^-1 U_r^T A_f = X^T A_f,
+//     X   = U_r S_r^-1 V_r^T A_c(J,:)^T                       (m x k)
+// (T_r = A_c^+ U_r U_r^T A_f, the form Alg. 5's operator takes once
+// H^T = A_c^T A_f is substituted).  A_f is resident in HBM here, so the
+// sketch is known before the one full read, and that read contracts A_f
+// with the k columns of X instead of accumulating H (n x l) and forming
+// T_r (l x n): S_r^-1 is applied once, not twice.
+//
+// Error estimate.  Every c-th snapshot, B_f = A_f(J,:), B_c = A_c(J,:):
+//     eps_hat(tau) = c lambda_max(B_f B_f^T - tau B_c B_c^T)
+// for each tau of a caller-given grid.  The m_c x m_c Grams are FP64 (FP32
+// data: the double-float Gram of the SVD path), and lambda_max comes from a
+// one-block cyclic Jacobi eigenvalue iteration per tau (parallel round-robin
+// ordering, rotations from Golub & Van Loan's symmetric 2x2 Schur step).
+#include "common.cuh"
+#include "internal.h"
+
+#include <math.h>
+
+namespace lrs {
+namespace {
+
+constexpr int kEigMax = 128;    // largest m_c (the matrix lives in shared memory)
+constexpr int kEigSweeps = 40;  // Jacobi sweeps at most (quadratic convergence: ~10 needed)
+
+// C[i][j] = (sum_t a(i,t) b(t,j)) / div[i] (div may be NULL), FP64,
+//   a(i,t) = A[i*a_si + t*a_st],  b(t,j) = B[t*b_st + col(j)*b_sj],  col(j) = cols ? cols[j] : j.
+// 16 x 16 output tile per block, K staged through shared memory 16 at a time.
+__global__ void k_small_gemm(int64_t M, int64_t N, int64_t K, const double* __restrict__ A, int64_t a_si,
+                             int64_t a_st, const double* __restrict__ B, int64_t b_st, int64_t b_sj,
+                             const int32_t* __restrict__ cols, const double* __restrict__ div,
+                             double* __restrict__ C, int64_t ldc) {
+  __shared__ double As[16][17], Bs[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t i0 = (int64_t)blockIdx.y * 16, j0 = (int64_t)blockIdx.x * 16;
+  const int64_t bj = j0 + tx;
+  const int64_t bcol = bj < N ? (cols ? (int64_t)cols[bj] : bj) : 0;
+  double acc = 0.0;
+  for (int64_t t0 = 0; t0 < K; t0 += 16) {
+    const int64_t ai = i0 + ty, at = t0 + tx, bt = t0 + ty;
+    As[ty][tx] = (ai < M && at < K) ? A[ai * a_si + at * a_st] : 0.0;
+    Bs[ty][tx] = (bt < K && bj < N) ? B[bt * b_st + bcol * b_sj] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 16; ++u) acc = fma(As[ty][u], Bs[u][tx], acc);
+    __syncthreads();
+  }
+  const int64_t i = i0 + ty;
+  if (i < M && bj < N) C[i * ldc + bj] = div ? acc / div[i] : acc;
+}
+
+lrs_status small_gemm(lrs_ctx* ctx, int64_t M, int64_t N, int64_t K, const double* A, int64_t a_si, int64_t a_st,
+                      const double* B, int64_t b_st, int64_t b_sj, const int32_t* cols, const double* div,
+                      double* C, int64_t ldc) {
+  if (M < 1 || N < 1) return LRS_OK;
+  const dim3 grid((unsigned)((N + 15) / 16), (unsigned)((M + 15) / 16));
+  if (grid.y > 65535u) return lrs_fail(ctx, LRS_EINVAL, "spc: %lld rows exceed the small-product grid", (long long)M);
+  k_small_gemm<<<grid, 256, 0, ctx->stream>>>(M, N, K, A, a_si, a_st, B, b_st, b_sj, cols, div, C, ldc);
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
+
+// Row Gram, partial over a column slab: part[b][e] = sum_{t in slab b} B(i,t) B(j,t)
+// for the packed upper-triangle entry e = (i, j), i <= j < r.  B(i, t) =
+// B[i * ldb + t] in storage type dt.  32 columns are staged in shared memory
+// (FP64) at a time; thread x owns the entries x, x + 256, ...
+constexpr int kRgCols = 32;
+constexpr int kRgPer = 33;      // ceil(128 * 129 / 2 / 256)
+
+__global__ void __launch_bounds__(256) k_row_gram(const void* __restrict__ B, int32_t dt, int r, int64_t n,
+                                                  int64_t ldb, int64_t cols_b, double* __restrict__ part) {
+  extern __shared__ double rg[];                   // r x (kRgCols + 1)
+  const int T = r * (r + 1) / 2;
+  const int64_t c0 = (int64_t)blockIdx.x * cols_b;
+  const int64_t c1 = min(n, c0 + cols_b);
+  int ei[kRgPer], ej[kRgPer];
+  double acc[kRgPer];
+#pragma unroll
+  for (int u = 0; u < kRgPer; ++u) {
+    const int e = threadIdx.x + 256 * u;
+    int i = 0, rem = e;
+    while (i < r && rem >= r - i) { rem -= r - i; ++i; }       // row i holds r - i entries (i..r-1)
+    ei[u] = i;
+    ej[u] = i + rem;
+    acc[u] = 0.0;
+  }
+  for (int64_t a0 = c0; a0 < c1; a0 += kRgCols) {
+    const int nc = (int)min((int64_t)kRgCols, c1 - a0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < r * kRgCols; e += blockDim.x) {
+      const int i = e / kRgCols, t = e - i * kRgCols;
+      rg[i * (kRgCols + 1) + t] = t < nc ? ld_f64(B, dt, (int64_t)i * ldb + a0 + t) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kRgPer; ++u) {
+      if (threadIdx.x + 256 * u < T) {
+        const double* xi = rg + ei[u] * (kRgCols + 1);
+        const double* xj = rg + ej[u] * (kRgCols + 1);
+        double s = acc[u];
+        for (int t = 0; t < kRgCols; ++t) s = fma(xi[t], xj[t], s);
+        acc[u] = s;
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kRgPer; ++u) {
+    const int e = threadIdx.x + 256 * u;
+    if (e < T) part[(int64_t)blockIdx.x * T + e] = acc[u];
+  }
+}
+
+// G (r x r, both triangles) = sum over blocks of the packed partials, in block order
+__global__ void k_row_gram_reduce(const double* __restrict__ part, int nb, int r, double* __restrict__ G) {
+  const int T = r * (r + 1) / 2;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < T; e += gridDim.x * blockDim.x) {
+    int i = 0, rem = e;
+    while (rem >= r - i) { rem -= r - i; ++i; }
+    const int j = i + rem;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * T + e];
+    G[i * r + j] = s;
+    G[j * r + i] = s;
+  }
+}
+
+size_t row_gram_ws(int64_t r, int num_sms) {
+  return sizeof(double) * (size_t)(2 * num_sms) * (size_t)(r * (r + 1) / 2) + 512;
+}
+
+lrs_status row_gram(lrs_ctx* ctx, const void* B, int32_t dt, int64_t r, int64_t n, int64_t ldb, double* G) {
+  int64_t nb = 2 * (int64_t)ctx->num_sms;
+  int64_t cols_b = (n + nb - 1) / nb;
+  cols_b = ((cols_b + kRgCols - 1) / kRgCols) * kRgCols;
+  nb = (n + cols_b - 1) / cols_b;
+  const int64_t T = r * (r + 1) / 2;
+  double* part = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(nb * T));
+  if (!part) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (row gram)");
+  const size_t dyn = sizeof(double) * (size_t)(r * (kRgCols + 1));
+  k_row_gram<<<(unsigned)nb, 256, dyn, ctx->stream>>>(B, dt, (int)r, n, ldb, cols_b, part);
+  k_row_gram_reduce<<<(unsigned)((T + 255) / 256), 256, 0, ctx->stream>>>(part, (int)nb, (int)r, G);
+  ctx->launches += 2;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
+
+// out[b] = c * lambda_max(Gf - taus[b] Gc) (n x n symmetric, n <= kEigMax), one
+// block per tau: cyclic Jacobi with the round-robin ordering of the indices
+// (a dummy index n pads an odd n; its pairs are skipped), at most kEigSweeps
+// sweeps, stopping once the off-diagonal squares fall below 1e-30 of the
+// diagonal's.  sweeps[b] = sweeps taken (kEigSweeps + 1 if not converged).
+__global__ void __launch_bounds__(256) k_eig_max(const double* __restrict__ Gf, const double* __restrict__ Gc,
+                                                 int n, const double* __restrict__ taus, double c,
+                                                 double* __restrict__ out, int* __restrict__ sweeps) {
+  extern __shared__ double em[];
+  const int ld = n + 1;
+  double* M = em;
+  double* cs = M + n * ld;
+  double* sn = cs + kEigMax / 2;
+  int* pp = reinterpret_cast<int*>(sn + kEigMax / 2);
+  int* qq = pp + kEigMax / 2;
+  __shared__ double red[32];
+  __shared__ int done;
+  const double tau = taus[blockIdx.x];
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e - i * n;
+    M[i * ld + j] = Gf[e] - tau * Gc[e];
+  }
+  __syncthreads();
+  const int np = n + (n & 1), half = np / 2;
+  int sw = 0;
+  for (; sw <= kEigSweeps; ++sw) {
+    double off = 0.0, dia = 0.0;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int i = e / n, j = e - i * n;
+      const double v = M[i * ld + j];
+      if (i == j) dia += v * v; else off += v * v;
+    }
+    off = block_sum(off, red);
+    dia = block_sum(dia, red);
+    if (threadIdx.x == 0) done = (off <= 1e-30 * dia) || sw == kEigSweeps;
+    __syncthreads();
+    if (done) break;
+    for (int t = 0; t < np - 1; ++t) {
+      for (int pi = threadIdx.x; pi < half; pi += blockDim.x) {
+        int a, b;
+        if (pi == 0) { a = t; b = np - 1; }
+        else { a = (t + pi) % (np - 1); b = (t - pi + (np - 1)) % (np - 1); }
+        const int p = min(a, b), q = max(a, b);
+        double cc = 1.0, ss = 0.0;
+        if (q < n) {
+          const double apq = M[p * ld + q];
+          if (apq != 0.0) {
+            const double theta = (M[q * ld + q] - M[p * ld + p]) / (2.0 * apq);
+            const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
+            cc = 1.0 / sqrt(1.0 + tt * tt);
+            ss = tt * cc;
+          }
+        }
+        pp[pi] = p;
+        qq[pi] = q < n ? q : -1;
+        cs[pi] = cc;
+        sn[pi] = ss;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < half * n; e += blockDim.x) {      // rows p, q <- J^T M
+        const int pi = e / n, j = e - pi * n;
+        const int q = qq[pi];
+        if (q < 0) continue;
+        const int p = pp[pi];
+        const double x = M[p * ld + j], y = M[q * ld + j];
+        M[p * ld + j] = cs[pi] * x - sn[pi] * y;
+        M[q * ld + j] = sn[pi] * x + cs[pi] * y;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < half * n; e += blockDim.x) {      // columns p, q <- M J
+        const int pi = e / n, j = e - pi * n;
+        const int q = qq[pi];
+        if (q < 0) continue;
+        const int p = pp[pi];
+        const double x = M[j * ld + p], y = M[j * ld + q];
+        M[j * ld + p] = cs[pi] * x - sn[pi] * y;
+        M[j * ld + q] = sn[pi] * x + cs[pi] * y;
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) {
+    double mx = M[0];
+    for (int i = 1; i < n; ++i) mx = fmax(mx, M[i * ld + i]);
+    out[blockIdx.x] = c * mx;
+    sweeps[blockIdx.x] = sw;
+  }
+}
+
+size_t eig_smem(int n) {
+  return sizeof(double) * (size_t)(n * (n + 1)) + (2 * sizeof(double) + 2 * sizeof(int)) * (kEigMax / 2);
+}
+
+bool spc_dtype_ok(int32_t dt) { return dt == LRS_F64 || dt == LRS_F32 || dt == LRS_BF16; }
+
+}  // namespace
+}  // namespace lrs
+
+using namespace lrs;
+
+extern "C" {
+
+lrs_status lrs_spc_lift(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                        const double* Y, int64_t l, int64_t ldy, const double* U, int64_t ldu, const double* S,
+                        const double* V, int64_t ldv, int64_t r, const int32_t* J, int32_t k, int32_t prec,
+                        void* Sf, int64_t ldsf) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  if (!A || !Y || !U || !S || !V || !J || !Sf) return lrs_fail(ctx, LRS_EINVAL, "spc_lift: NULL pointer");
+  if (!spc_dtype_ok(dtype) || prec < LRS_PREC_FP64 || prec > LRS_PREC_BF16X3)
+    return lrs_fail(ctx, LRS_EINVAL, "spc_lift: bad dtype/prec");
+  if (m < 1 || n < 1 || l < 1 || k < 1 || r < k || r > (m < l ? m : l))
+    return lrs_fail(ctx, LRS_EINVAL, "spc_lift: need 1 <= k <= r <= min(m, l) (m=%lld l=%lld r=%lld k=%d)",
+                    (long long)m, (long long)l, (long long)r, k);
+  if (lda < n || ldy < l || ldu < r || ldv < r || ldsf < n)
+    return lrs_fail(ctx, LRS_EINVAL, "spc_lift: strides too small");
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  // the r-th singular value must be nonzero: S_r^-1 enters the operator
+  double* h = (double*)ctx->host_scratch;
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 12, S + (r - 1), sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (!(h[12] > 0.0)) return lrs_fail(ctx, LRS_EINVAL, "spc_lift: s_r = %g is not positive", h[12]);
+  const bool tc = prec >= LRS_PREC_SPLIT_BF16;
+  const size_t need = 8 * (size_t)(r * k) + 8 * (size_t)(m * k) + 4096 +
+                      (tc ? gemm_tc_workspace(k, m, prec) + gemm_tc_splitk_workspace(k, n, m, ctx->num_sms) : 0);
+  lrs_status st = ws_reserve(ctx, need);
+  if (st) return st;
+  double* Mk = (double*)ws_alloc(ctx, 8 * (size_t)(r * k));      // S_r^-1 V_r^T A_c(J,:)^T  (r x k)
+  double* X = (double*)ws_alloc(ctx, 8 * (size_t)(m * k));       // U_r Mk                   (m x k)
+  if (!Mk || !X) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (spc_lift)");
+  // Mk(q, j) = (1 / S_q) sum_t V(t, q) Y(J_j, t)
+  st = small_gemm(ctx, r, k, l, V, 1, ldv, Y, 1, ldy, J, S, Mk, k);
+  if (st) return st;
+  // X(i, j) = sum_q U(i, q) Mk(q, j)
+  st = small_gemm(ctx, m, k, r, U, ldu, 1, Mk, k, 1, nullptr, nullptr, X, k);
+  if (st) return st;
+  // S_f = X^T A_f: the one full read of A_f
+  GemmArgs g{k, n, m, X, LRS_F64, k, A, dtype, lda, Sf, prec == LRS_PREC_FP64 ? 1 : 0, 0, ldsf, 1.0};
+  if (prec == LRS_PREC_FP64) return launch_gemm_simt(ctx, g, 1);
+  if (prec == LRS_PREC_FP32) return launch_gemm_simt(ctx, g, 0);
+  return launch_gemm_tc(ctx, g, prec);
+}
+
+lrs_status lrs_spc_err(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                       const double* Y, int64_t l, int64_t ldy, int32_t c, const double* taus, int32_t ntau,
+                       double* eps_hat) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  if (!A || !Y || !taus || !eps_hat) return lrs_fail(ctx, LRS_EINVAL, "spc_err: NULL pointer");
+  if (!spc_dtype_ok(dtype)) return lrs_fail(ctx, LRS_EINVAL, "spc_err: bad dtype");
+  if (m < 1 || n < 1 || l < 1 || c < 1 || ntau < 1 || ntau > 65535)
+    return lrs_fail(ctx, LRS_EINVAL, "spc_err: bad sizes");
+  const int64_t mc = m / c;
+  if (mc < 1 || mc > kEigMax)
+    return lrs_fail(ctx, LRS_EINVAL, "spc_err: m_c = m / c = %lld outside [1, %d]", (long long)mc, kEigMax);
+  if (lda < n || ldy < l) return lrs_fail(ctx, LRS_EINVAL, "spc_err: strides too small");
+  for (int32_t i = 0; i < ntau; ++i)
+    if (!(taus[i] >= 0.0) || !isfinite(taus[i])) return lrs_fail(ctx, LRS_EINVAL, "spc_err: tau[%d] = %g", i, taus[i]);
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const size_t gram_ws = dtype == LRS_F32 ? gram_df_ws(mc, ctx->num_sms) : row_gram_ws(mc, ctx->num_sms);
+  const size_t need = 2 * 8 * (size_t)(mc * mc) + 16 * (size_t)ntau + 4 * (size_t)ntau + gram_ws +
+                      row_gram_ws(mc, ctx->num_sms) + 8192;
+  lrs_status st = ws_reserve(ctx, need);
+  if (st) return st;
+  double* Gf = (double*)ws_alloc(ctx, 8 * (size_t)(mc * mc));
+  double* Gc = (double*)ws_alloc(ctx, 8 * (size_t)(mc * mc));
+  double* dtau = (double*)ws_alloc(ctx, 8 * (size_t)ntau);
+  double* dout = (double*)ws_alloc(ctx, 8 * (size_t)ntau);
+  int* dsw = (int*)ws_alloc(ctx, 4 * (size_t)ntau);
+  if (!Gf || !Gc || !dtau || !dout || !dsw) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (spc_err)");
+  // B_f = A_f(J,:), J = c-1, 2c-1, ...: rows at stride c * lda from row c - 1
+  const size_t esz = dtype == LRS_F64 ? 8 : (dtype == LRS_F32 ? 4 : 2);
+  const char* Bf = (const char*)A + (size_t)(c - 1) * (size_t)lda * esz;
+  const size_t mark = ctx->ws_top;
+  if (dtype == LRS_F32) st = launch_gram_df(ctx, (const float*)Bf, mc, n, (int64_t)c * lda, Gf);
+  else st = row_gram(ctx, Bf, dtype, mc, n, (int64_t)c * lda, Gf);
+  if (st) return st;
+  ctx->ws_top = mark;
+  st = row_gram(ctx, Y + (size_t)(c - 1) * (size_t)ldy, LRS_F64, mc, l, (int64_t)c * ldy, Gc);
+  if (st) return st;
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(dtau, taus, 8 * (size_t)ntau, cudaMemcpyHostToDevice, ctx->stream));
+  const size_t smem = eig_smem((int)mc);
+  if (smem > 48 * 1024) {
+    st = raise_dyn_smem(ctx, (const void*)k_eig_max, smem);
+    if (st) return st;
+  }
+  k_eig_max<<<(unsigned)ntau, 256, smem, ctx->stream>>>(Gf, Gc, (int)mc, dtau, (double)c, dout, dsw);
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(eps_hat, dout, 8 * (size_t)ntau, cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return LRS_OK;
+}
+
+}  // extern "C"

@@ -3,7 +3,9 @@
 ``svd_path`` = lrs_power_pass (sketch + C-PWR with re-orthonormalisation) ->
 lrs_range_find -> lrs_svd_k  (paper Algs. 7 and 2);
 ``id_path``  = lrs_power_pass (C-PWR without re-orthonormalisation, as in the
-paper's ID experiments) -> lrs_id_k  (Alg. 4).
+paper's ID experiments) -> lrs_id_k  (Alg. 4);
+``spc_id_path`` = lrs_sketch -> lrs_range_find + lrs_svd_k of the sketch ->
+lrs_id_k -> lrs_spc_lift  (SPC-ID, Alg. 5); ``spc_err`` = lrs_spc_err (Alg. 6).
 Device buffers come from torch; every arithmetic step runs in liblrs.so.
 """
 from __future__ import annotations
@@ -12,7 +14,7 @@ from dataclasses import dataclass
 
 import torch
 
-from .binding import (DTYPE, LRS_PREC_FP32, LRS_PREC_FP64, Context, grid_of)
+from .binding import (DTYPE, LRS_F64, LRS_PREC_FP32, LRS_PREC_FP64, Context, grid_of)
 
 
 @dataclass
@@ -91,3 +93,51 @@ def id_path(ctx: Context, A: torch.Tensor, dtype: str, grid, k: int, q: int = 0,
     ctx.power_pass(A, dt, m, n, g, gg, q, 0, rtol, prec, b.Yid, l, b.Gid, l)
     err, st = ctx.id_k(b.Gid, m, l, l, k, b.J, b.P, k)
     return IdResult(b.J, b.P, err, st)
+
+
+@dataclass
+class SpcResult:
+    J: torch.Tensor
+    P: torch.Tensor
+    Sf: torch.Tensor       # lifted skeleton A_c(J,:) T_r (k x n): A_f ~ P Sf
+    Y: torch.Tensor        # the sketch A_c
+    r: int                 # lifting rank used
+    rank_c: int            # numerical rank of the sketch
+    err_est: float         # coarse ID error (lrs_id_k)
+    status: int
+
+
+def spc_id_path(ctx: Context, A: torch.Tensor, dtype: str, grid, k: int, r_lift: int, rtol: float = 1e-12,
+                prec: int | None = None) -> SpcResult:
+    """SPC-ID (Alg. 5): the sketch, its SVD (range basis at rtol, then the
+    leading r = min(r_lift, rank) triplets), the row ID of the sketch, and the
+    lifted skeleton from one read of A_f."""
+    m, n = A.shape
+    dt = DTYPE[dtype]
+    prec = default_prec(dtype) if prec is None else prec
+    l = int(grid.l)
+    dev = A.device
+    f64 = torch.float64
+    Y = torch.empty((m, l), dtype=f64, device=dev)
+    ctx.sketch(A, dt, m, n, grid_of(grid), Y, l)
+    ldq = min(m, l)
+    Q = torch.empty((m, ldq), dtype=f64, device=dev)
+    rank_c = ctx.range_find(Y, m, l, l, rtol, Q, ldq)
+    r = min(int(r_lift), rank_c)
+    U = torch.empty((m, r), dtype=f64, device=dev)
+    S = torch.empty((r,), dtype=f64, device=dev)
+    V = torch.empty((l, r), dtype=f64, device=dev)
+    ctx.svd_k(Y, LRS_F64, m, l, l, Q, ldq, rank_c, r, LRS_PREC_FP64, U, r, S, V, r)
+    J = torch.empty((k,), dtype=torch.int32, device=dev)
+    P = torch.empty((m, k), dtype=f64, device=dev)
+    err, st = ctx.id_k(Y, m, l, l, k, J, P, k)
+    Sf = torch.empty((k, n), dtype=f64 if prec == LRS_PREC_FP64 else torch.float32, device=dev)
+    ctx.spc_lift(A, dt, m, n, n, Y, l, l, U, r, S, V, r, r, J, k, prec, Sf, n)
+    return SpcResult(J, P, Sf, Y, r, rank_c, err, st)
+
+
+def spc_err(ctx: Context, A: torch.Tensor, dtype: str, Y: torch.Tensor, c: int, taus) -> list:
+    """SPC-ID-ERR (Alg. 6): eps_hat(tau) for each tau, every c-th snapshot."""
+    m, n = A.shape
+    l = Y.shape[1]
+    return ctx.spc_err(A, DTYPE[dtype], m, n, n, Y, l, l, c, taus)
