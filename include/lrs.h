@@ -178,13 +178,30 @@ lrs_status lrs_id_k(lrs_ctx* ctx, const double* Ysk, int64_t m, int64_t l, int64
                     int32_t* J, double* P, int64_t ldp, double* err_est);
 
 /*
+ * lrs_sketch_svd -- the leading r singular triplets of a sketch Y = A_c
+ * (m x l FP64), the SVD step of SPC-ID (Alg. 5: U_c, S_c, V_c of A_c).
+ *   The range finder of lrs_range_find (tolerance rtol) gives Q and the
+ *   numerical rank (*rank_out).  Up to 112 directions (the FP64 Jacobi tile
+ *   of lrs_svd_k) the result is lrs_svd_k(Y, Q, rank, r).  Beyond, Q keeps its
+ *   leading 112 directions, refined by two steps of subspace iteration
+ *   Q <- orth(Y Y^T Q), and the SVD of Q^T Y (Rayleigh-Ritz) gives the
+ *   triplets; their error shrinks as (s_113 / s_r)^4.
+ *   Q   caller scratch, m x min(m,l) FP64 (row stride ldq); on return it holds
+ *       the basis used.
+ *   U   m x r, S r, V l x r (FP64; row strides ldu, ldv >= r); 1 <= r <= 112.
+ * ERANK (nothing written) when the numerical rank is below r.
+ */
+lrs_status lrs_sketch_svd(lrs_ctx* ctx, const double* Y, int64_t m, int64_t l, int64_t ldy, double rtol, double* Q,
+                          int64_t ldq, int32_t r, double* U, int64_t ldu, double* S, double* V, int64_t ldv,
+                          int64_t* rank_out);
+
+/*
  * lrs_spc_lift -- the lifted row skeleton of SPC-ID (Sec. 4, Alg. 5):
  *   S_f = A_c(J,:) T_r  (k x n),   T_r = A_c^+ U_r U_r^T A_f,
  * so that A_f ~ P S_f with (J, P) the rank-k row ID of the sketch A_c = Y
  * (lrs_id_k).  T_r is Alg. 5's lifting operator after its H^T = A_c^T A_f is
  * substituted.  U_r (m x r), S_r (r), V_r (l x r) are the leading r singular
- * triplets of Y, as lrs_svd_k returns them for A = Y (FP64) and Q a range
- * basis of Y; k <= r <= min(m, l) and s_r > 0.  Computed as
+ * triplets of Y (lrs_sketch_svd); k <= r <= min(m, l) and s_r > 0.  Computed as
  *   X = U_r S_r^-1 V_r^T Y(J,:)^T (m x k, FP64),  S_f = X^T A_f,
  * the second product being one read of A_f by the A-pass kernel in `prec`.
  *   A   m x n in dtype (row stride lda).   Y  m x l FP64 (row stride ldy).

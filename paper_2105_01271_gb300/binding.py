@@ -96,6 +96,9 @@ _SIG = {
     "lrs_batch_release": (C.c_int, [C.c_int]),
     "lrs_range_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_int64,
                                   C.c_void_p, C.c_int64, C.c_int64, C.POINTER(C.c_double)]),
+    "lrs_sketch_svd": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_double,
+                                 C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p,
+                                 C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "lrs_spc_lift": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_int64,
                                C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
                                C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int32, C.c_int32,
@@ -231,6 +234,12 @@ class Context:
         err = C.c_double(0.0)
         self._check(self.lib.lrs_range_error(self.h, _ptr(A), dtype, m, n, lda, _ptr(Q), ldq, r, C.byref(err)))
         return err.value
+
+    def sketch_svd(self, Y, m, l, ldy, rtol, Q, ldq, r, U, ldu, S, V, ldv) -> int:
+        rank = C.c_int64(0)
+        self._check(self.lib.lrs_sketch_svd(self.h, _ptr(Y), m, l, ldy, rtol, _ptr(Q), ldq, r, _ptr(U), ldu,
+                                            _ptr(S), _ptr(V), ldv, C.byref(rank)))
+        return rank.value
 
     def spc_lift(self, A, dtype, m, n, lda, Y, l, ldy, U, ldu, S, V, ldv, r, J, k, prec, Sf, ldsf):
         return self._check(self.lib.lrs_spc_lift(self.h, _ptr(A), dtype, m, n, lda, _ptr(Y), l, ldy, _ptr(U), ldu,

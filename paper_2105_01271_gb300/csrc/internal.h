@@ -116,6 +116,11 @@ bool orth_gram_eligible(int64_t p, int64_t c, double rtol);
 size_t orth_gram_ws(int64_t p, int64_t c, int num_sms);
 // refine = false: skip the Cholesky-QR2 pass (well-conditioned basis of the
 // same range, orthonormal only to ~u cond^2; for intermediate C-PWR iterates)
+// the range finder of lrs_range_find on M (p x c, row stride ldi) into Q
+// (p x r, row stride ldq), with its workspace bound; callers reserve first
+size_t orth_ws_of(int64_t p, int64_t c, int num_sms);
+lrs_status orth_basis(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldi, double rtol, double* Q,
+                      int64_t ldq, int64_t* r_out);
 // rdiag (optional, device): |R_ii| of the pivoted factor, i < r
 lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldm, double rtol,
                             double* Q, int64_t ldq, int64_t* r_out, bool refine = true, double* rdiag = nullptr);

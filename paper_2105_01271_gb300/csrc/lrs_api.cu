@@ -171,6 +171,13 @@ lrs_status raise_dyn_smem(lrs_ctx* ctx, const void* func, size_t bytes) {
   return LRS_OK;
 }
 
+size_t orth_ws_of(int64_t p, int64_t c, int num_sms) { return orth_ws(p, c, num_sms); }
+
+lrs_status orth_basis(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldi, double rtol, double* Q,
+                      int64_t ldq, int64_t* r_out) {
+  return orth(ctx, M, p, c, ldi, rtol, Q, ldq, r_out);
+}
+
 static lrs_status gemm(lrs_ctx* ctx, int prec, int64_t M, int64_t N, int64_t K, const void* X,
                        int32_t xdt, int64_t ldx, const void* A, int32_t adt, int64_t lda, void* C,
                        int c_f64, int c_trans, int64_t ldc, double alpha = 1.0) {

@@ -245,6 +245,8 @@ size_t eig_smem(int n) {
 
 bool spc_dtype_ok(int32_t dt) { return dt == LRS_F64 || dt == LRS_F32 || dt == LRS_BF16; }
 
+constexpr int64_t kSketchSvdDirs = 112;   // the FP64 Jacobi tile of lrs_svd_k holds r <= 112
+
 }  // namespace
 }  // namespace lrs
 
@@ -291,6 +293,63 @@ lrs_status lrs_spc_lift(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, i
   if (prec == LRS_PREC_FP64) return launch_gemm_simt(ctx, g, 1);
   if (prec == LRS_PREC_FP32) return launch_gemm_simt(ctx, g, 0);
   return launch_gemm_tc(ctx, g, prec);
+}
+
+lrs_status lrs_sketch_svd(lrs_ctx* ctx, const double* Y, int64_t m, int64_t l, int64_t ldy, double rtol, double* Q,
+                          int64_t ldq, int32_t r, double* U, int64_t ldu, double* S, double* V, int64_t ldv,
+                          int64_t* rank_out) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  if (!Y || !Q || !U || !S || !V || !rank_out) return lrs_fail(ctx, LRS_EINVAL, "sketch_svd: NULL pointer");
+  const int64_t mn = m < l ? m : l;
+  if (m < 1 || l < 1 || r < 1 || r > kSketchSvdDirs || r > mn)
+    return lrs_fail(ctx, LRS_EINVAL, "sketch_svd: need 1 <= r <= min(m, l, %lld) (r=%d)", (long long)kSketchSvdDirs, r);
+  if (ldy < l || ldq < mn || ldu < r || ldv < r) return lrs_fail(ctx, LRS_EINVAL, "sketch_svd: strides too small");
+  if (!(rtol >= 0.0) || rtol >= 1.0) return lrs_fail(ctx, LRS_EINVAL, "sketch_svd: rtol=%g not in [0,1)", rtol);
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const int64_t pmax = mn < kSketchSvdDirs ? mn : kSketchSvdDirs;
+  const size_t iter_ws = 8 * (size_t)(l * m) + 8 * (size_t)(l * pmax) + 8 * (size_t)(m * pmax) + 1024 +
+                         orth_ws_of(m, pmax, ctx->num_sms);
+  const size_t ow = orth_ws_of(m, l, ctx->num_sms);
+  lrs_status st = ws_reserve(ctx, ow > iter_ws ? ow : iter_ws);
+  if (st) return st;
+  int64_t rank = 0;
+  st = orth_basis(ctx, Y, m, l, ldy, rtol, Q, ldq, &rank);
+  if (st) return st;
+  *rank_out = rank;
+  if (rank < r) return lrs_fail(ctx, LRS_ERANK, "sketch_svd: numerical rank %lld < r = %d", (long long)rank, r);
+  const int64_t p = rank < pmax ? rank : pmax;
+  if (rank > p) {
+    // More directions than the Jacobi tile holds: keep the pivoted QR's
+    // leading p and refine them by two steps of subspace iteration,
+    // Q_p <- orth(Y Y^T Q_p), which shrinks their angle to the dominant
+    // p-dimensional singular subspace by (s_{p+1} / s_p)^2 per step; the
+    // SVD below is then the Rayleigh-Ritz step on that subspace.
+    ctx->ws_top = 0;                                    // Q is the caller's; nothing else is live
+    double* Yt = (double*)ws_alloc(ctx, 8 * (size_t)(l * m));
+    double* T = (double*)ws_alloc(ctx, 8 * (size_t)(l * p));
+    double* Z = (double*)ws_alloc(ctx, 8 * (size_t)(m * p));
+    if (!Yt || !T || !Z) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (sketch_svd)");
+    st = launch_transpose(ctx, Y, m, l, ldy, Yt, m);   // Yt = Y^T (l x m, row-major)
+    if (st) return st;
+    const size_t mark = ctx->ws_top;
+    for (int it = 0; it < 2; ++it) {
+      GemmArgs g1{l, p, m, Y, LRS_F64, ldy, Q, LRS_F64, ldq, T, 1, 0, p, 1.0};      // T = Y^T Q_p
+      st = launch_gemm_simt(ctx, g1, 1);
+      if (st) return st;
+      GemmArgs g2{m, p, l, Yt, LRS_F64, m, T, LRS_F64, p, Z, 1, 0, p, 1.0};         // Z = Y T
+      st = launch_gemm_simt(ctx, g2, 1);
+      if (st) return st;
+      int64_t rz = 0;
+      ctx->ws_top = mark;
+      st = orth_basis(ctx, Z, m, p, p, 0.0, Q, ldq, &rz);
+      if (st) return st;
+      if (rz != p) return lrs_fail(ctx, LRS_ERANK, "sketch_svd: subspace iteration lost rank (%lld of %lld)",
+                                   (long long)rz, (long long)p);
+    }
+  }
+  st = lrs_svd_k(ctx, Y, LRS_F64, m, l, ldy, Q, ldq, p, r, LRS_PREC_FP64, U, ldu, S, V, ldv, nullptr);
+  return st == LRS_ERANK ? LRS_OK : st;
 }
 
 lrs_status lrs_spc_err(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,

@@ -4,8 +4,8 @@
 lrs_range_find -> lrs_svd_k  (paper Algs. 7 and 2);
 ``id_path``  = lrs_power_pass (C-PWR without re-orthonormalisation, as in the
 paper's ID experiments) -> lrs_id_k  (Alg. 4);
-``spc_id_path`` = lrs_sketch -> lrs_range_find + lrs_svd_k of the sketch ->
-lrs_id_k -> lrs_spc_lift  (SPC-ID, Alg. 5); ``spc_err`` = lrs_spc_err (Alg. 6).
+``spc_id_path`` = lrs_sketch -> lrs_sketch_svd -> lrs_id_k -> lrs_spc_lift
+(SPC-ID, Alg. 5); ``spc_err`` = lrs_spc_err (Alg. 6).
 Device buffers come from torch; every arithmetic step runs in liblrs.so.
 """
 from __future__ import annotations
@@ -14,7 +14,7 @@ from dataclasses import dataclass
 
 import torch
 
-from .binding import (DTYPE, LRS_F64, LRS_PREC_FP32, LRS_PREC_FP64, Context, grid_of)
+from .binding import (DTYPE, LRS_PREC_FP32, LRS_PREC_FP64, Context, grid_of)
 
 
 @dataclass
@@ -109,9 +109,9 @@ class SpcResult:
 
 def spc_id_path(ctx: Context, A: torch.Tensor, dtype: str, grid, k: int, r_lift: int, rtol: float = 1e-12,
                 prec: int | None = None) -> SpcResult:
-    """SPC-ID (Alg. 5): the sketch, its SVD (range basis at rtol, then the
-    leading r = min(r_lift, rank) triplets), the row ID of the sketch, and the
-    lifted skeleton from one read of A_f."""
+    """SPC-ID (Alg. 5): the sketch, its leading r triplets (r = r_lift, at
+    most the sketch's numerical rank at rtol), the row ID of the sketch, and
+    the lifted skeleton from one read of A_f."""
     m, n = A.shape
     dt = DTYPE[dtype]
     prec = default_prec(dtype) if prec is None else prec
@@ -122,12 +122,11 @@ def spc_id_path(ctx: Context, A: torch.Tensor, dtype: str, grid, k: int, r_lift:
     ctx.sketch(A, dt, m, n, grid_of(grid), Y, l)
     ldq = min(m, l)
     Q = torch.empty((m, ldq), dtype=f64, device=dev)
-    rank_c = ctx.range_find(Y, m, l, l, rtol, Q, ldq)
-    r = min(int(r_lift), rank_c)
+    r = int(r_lift)
     U = torch.empty((m, r), dtype=f64, device=dev)
     S = torch.empty((r,), dtype=f64, device=dev)
     V = torch.empty((l, r), dtype=f64, device=dev)
-    ctx.svd_k(Y, LRS_F64, m, l, l, Q, ldq, rank_c, r, LRS_PREC_FP64, U, r, S, V, r)
+    rank_c = ctx.sketch_svd(Y, m, l, l, rtol, Q, ldq, r, U, r, S, V, r)
     J = torch.empty((k,), dtype=torch.int32, device=dev)
     P = torch.empty((m, k), dtype=f64, device=dev)
     err, st = ctx.id_k(Y, m, l, l, k, J, P, k)
