@@ -60,6 +60,7 @@ def parse():
 
 
 BATCH_WORKLOAD = "batch256_mixed_f32"
+SPC_WORKLOAD = "spc_blob2d_m2000_512x512_f32"
 
 
 def workload_params(name):
@@ -330,6 +331,147 @@ def run_batch_bench(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def run_spc_bench(args, rank, world):
+    """SPC-ID (Alg. 5) with its single-pass error estimate (Alg. 6) on the
+    2000 x 512^2 FP32 blob field: full weighting s = 16 (l = 1024), k = 50,
+    lifting rank r = 60, split-BF16 products; eps_hat on every 16th snapshot
+    (m_c = 125) for 16 values of tau from 0.1 to 1e4 (the Grams' natural
+    ratio is n / l = 256).  One step = lrs_sketch -> lrs_sketch_svd
+    -> lrs_id_k -> lrs_spc_lift -> lrs_spc_err.  The dominant kernel is the
+    lifting read S_f = X^T A_f (timed alone with CUDA events)."""
+    import torch
+    import synth
+    from paper_2105_01271_gb300 import binding, path
+
+    w = synth.WORKLOADS["blob2d_m2000_512x512_f32"]
+    k, r_lift, c = 50, 60, 16
+    taus = [float(t) for t in np.geomspace(1e-1, 1e4, 16)]        # around n / l = 256
+    prec = binding.LRS_PREC_SPLIT_BF16
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    A_h = torch.from_numpy(synth.make_workload(w, seed_offset=rank)).pin_memory()
+    stream = torch.cuda.Stream(dev)
+    ctx = binding.Context(dev, stream)
+    A_d = torch.empty(A_h.shape, dtype=torch.float32, device=f"cuda:{dev}")
+    with torch.cuda.stream(stream):
+        A_d.copy_(A_h, non_blocking=True)
+    stream.synchronize()
+
+    def step():
+        res = path.spc_id_path(ctx, A_d, "f32", w.grid, k, r_lift, prec=prec)
+        eps = path.spc_err(ctx, A_d, "f32", res.Y, c, taus)
+        return res, eps
+
+    clk = clocks_start(dev)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            res, eps = step()
+    stream.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    mark = clocks_mark(clk)
+    l0 = ctx.launches
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            res, eps = step()
+        ev1.record(stream)
+    stream.synchronize()
+    barrier()
+    clocks = clocks_stop(clk, mark)
+    launches = (ctx.launches - l0) // max(args.steps, 1)
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, f"cuda:{dev}")
+
+    # the lifting call alone: small products + the read of A_f (S_r read-back included)
+    m, n, l = w.m, w.n, w.grid.l
+    reps = max(args.steps, 5)
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        lift = lambda: ctx.spc_lift(A_d, binding.LRS_F32, m, n, n, res.Y, l, l, res.U, res.r, res.S, res.V, res.r,
+                                    res.r, res.J, k, prec, res.Sf, n)
+        lift()
+        e0.record(stream)
+        for _ in range(reps):
+            lift()
+        e1.record(stream)
+    stream.synchronize()
+    lift_ms = e0.elapsed_time(e1) / reps
+    alg_bytes = 4 * m * n + 8 * m * k + 4 * k * n
+    gbs = alg_bytes / (lift_ms * 1e-3) / 1e9
+    hbm_peak, peak_src = 6795.8, "measured (MEASURED_PEAKS.json hbm_gbs)"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm_peak = float(json.load(f)["hbm_gbs"])
+    except Exception:
+        peak_src = "fallback 6795.8 GB/s"
+
+    # end to end: A_f in from pinned host memory, S_f, P, J and eps_hat back
+    Sf_h = torch.empty(res.Sf.shape, dtype=res.Sf.dtype, pin_memory=True)
+    P_h = torch.empty(res.P.shape, dtype=res.P.dtype, pin_memory=True)
+    J_h = torch.empty(res.J.shape, dtype=res.J.dtype, pin_memory=True)
+    barrier()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, min(args.steps, 3))):
+            A_d.copy_(A_h, non_blocking=True)
+            r2, _ = step()
+            Sf_h.copy_(r2.Sf, non_blocking=True)
+            P_h.copy_(r2.P, non_blocking=True)
+            J_h.copy_(r2.J, non_blocking=True)
+    stream.synchronize()
+    barrier()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / max(1, min(args.steps, 3)), world, f"cuda:{dev}")
+    if rank != 0:
+        return
+    out = {"metric": METRIC, "value": job_throughput(world, ms), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": SPC_WORKLOAD, "m": m, "n": n, "grid": "512x512",
+                      "sketch": f"fullweight s=16 (l={l})", "k": k, "r_lift": r_lift, "rank_c": res.rank_c,
+                      "err_c": c, "m_c": m // c, "taus": len(taus), "prec": "split_bf16", "storage": "f32",
+                      "l2": "inputs larger than L2, no flush"},
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                        "peak_source": peak_src, "kernel": "SPC lifting read S_f = X^T A_f (lrs_spc_lift)",
+                        "traffic": None, "algorithmic_bytes": alg_bytes, "ms": lift_ms,
+                        "ms_covers": "the whole lrs_spc_lift call (s_r read-back, two small FP64 products, "
+                                     "the A-pass kernel)"},
+           "clocks": clocks, "gpu_launches": launches,
+           "e2e": {"value": job_throughput(world, e2e_ms), "unit": UNIT,
+                   "h2d_bytes_per_step": int(A_h.numel() * 4),
+                   "d2h_bytes_per_step": int(Sf_h.numel() * Sf_h.element_size() + P_h.numel() * 8 + J_h.numel() * 4)},
+           "result": {"rank_c": res.rank_c, "err_id_coarse": res.err_est,
+                      "eps_hat_min": min(eps), "eps_hat_tau0": eps[0]}}
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = spc_cpu_baseline(w, k, r_lift, c, taus)
+    print(json.dumps(out), flush=True)
+
+
+def spc_cpu_baseline(w, k, r_lift, c, taus):
+    import oracle
+    import oracle.spc as spc
+    import synth
+    ms = sample_rows(w)
+    A = synth.make_workload(w, rows=slice(0, ms)).astype(np.float64)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    t0 = time.perf_counter()
+    Ac = oracle.sketch(A, w.grid)
+    s = np.linalg.svd(Ac, compute_uv=False)
+    rank = int(np.sum(s > 1e-12 * s[0]))
+    ks = min(k, rank)
+    spc.spc_id(A, Ac, ks, max(ks, min(r_lift, rank)))
+    spc.eps_hat(A, Ac, c, taus)
+    dt = time.perf_counter() - t0
+    return {"value": (ms / w.m) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one run on the first {ms} of {w.m} snapshots (k = {ks}), scaled by {ms}/{w.m}"}
+
+
 def run_ours(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -568,6 +710,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == BATCH_WORKLOAD:
         run_batch_bench(args, rank, world)
+    elif args.workload == SPC_WORKLOAD:
+        run_spc_bench(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1 and args.impl == "ours":

@@ -180,12 +180,12 @@ lrs_status lrs_id_k(lrs_ctx* ctx, const double* Ysk, int64_t m, int64_t l, int64
 /*
  * lrs_sketch_svd -- the leading r singular triplets of a sketch Y = A_c
  * (m x l FP64), the SVD step of SPC-ID (Alg. 5: U_c, S_c, V_c of A_c).
- *   The range finder of lrs_range_find (tolerance rtol) gives Q and the
- *   numerical rank (*rank_out).  Up to 112 directions (the FP64 Jacobi tile
- *   of lrs_svd_k) the result is lrs_svd_k(Y, Q, rank, r).  Beyond, Q keeps its
- *   leading 112 directions, refined by two steps of subspace iteration
- *   Q <- orth(Y Y^T Q), and the SVD of Q^T Y (Rayleigh-Ritz) gives the
- *   triplets; their error shrinks as (s_113 / s_r)^4.
+ *   The pivoted QR of lrs_range_find (tolerance rtol), stopped after at most
+ *   112 steps (the FP64 Jacobi tile of lrs_svd_k), gives Q and *rank_out =
+ *   min(numerical rank, 112).  When it stops at 112 with directions left, Q
+ *   is refined by two steps of subspace iteration Q <- orth(Y Y^T Q); the SVD
+ *   of Q^T Y (Rayleigh-Ritz) gives the triplets, whose error then shrinks as
+ *   (s_113 / s_r)^4.
  *   Q   caller scratch, m x min(m,l) FP64 (row stride ldq); on return it holds
  *       the basis used.
  *   U   m x r, S r, V l x r (FP64; row strides ldu, ldv >= r); 1 <= r <= 112.
@@ -221,8 +221,8 @@ lrs_status lrs_spc_lift(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, i
  *   eps_hat[i] = c * lambda_max(B_f B_f^T - taus[i] B_c B_c^T),  i < ntau,
  * the estimate of eps(tau) in the SPC-ID error bound, for each tau >= 0 of the
  * caller's grid (the bound minimises over tau together with its other terms).
- * Grams in FP64 (FP32 data: double-float accumulation), lambda_max by cyclic
- * Jacobi (one block per tau, at most 40 sweeps).
+ * Grams in FP64 (FP32 data: double-float accumulation); lambda_max by
+ * Householder tridiagonalisation and Sturm-count bisection (one block per tau).
  *   A  m x n in dtype (row stride lda).   Y  m x l FP64 (row stride ldy).
  *   taus, eps_hat: HOST arrays of ntau doubles.  Synchronises.
  */

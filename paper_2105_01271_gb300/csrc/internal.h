@@ -117,10 +117,11 @@ size_t orth_gram_ws(int64_t p, int64_t c, int num_sms);
 // refine = false: skip the Cholesky-QR2 pass (well-conditioned basis of the
 // same range, orthonormal only to ~u cond^2; for intermediate C-PWR iterates)
 // the range finder of lrs_range_find on M (p x c, row stride ldi) into Q
-// (p x r, row stride ldq), with its workspace bound; callers reserve first
+// (p x r, row stride ldq), with its workspace bound; callers reserve first.
+// kcap > 0: at most kcap pivoted Householder steps (r <= kcap)
 size_t orth_ws_of(int64_t p, int64_t c, int num_sms);
 lrs_status orth_basis(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldi, double rtol, double* Q,
-                      int64_t ldq, int64_t* r_out);
+                      int64_t ldq, int64_t* r_out, int64_t kcap = 0);
 // rdiag (optional, device): |R_ii| of the pivoted factor, i < r
 lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldm, double rtol,
                             double* Q, int64_t ldq, int64_t* r_out, bool refine = true, double* rdiag = nullptr);

@@ -119,9 +119,10 @@ lrs_status launch_abs_diag(lrs_ctx* ctx, const double* R, int64_t ld, int64_t r,
 
 static lrs_status orth(lrs_ctx* ctx, const double* Min, int64_t p, int64_t c, int64_t ldi,
                        double rtol, double* Q, int64_t ldq, int64_t* r_out, bool intermediate = false,
-                       double* rdiag = nullptr) {
-  const int64_t kmax = p < c ? p : c;
-  if (orth_gram_eligible(p, c, rtol)) {
+                       double* rdiag = nullptr, int64_t kcap = 0) {
+  int64_t kmax = p < c ? p : c;
+  if (kcap > 0 && kcap < kmax) kmax = kcap;           // at most kcap pivoted steps (Householder route)
+  if (kcap <= 0 && orth_gram_eligible(p, c, rtol)) {
     // tall-skinny: pivoted Cholesky of the Gram (same pivots and stop rule)
     const size_t mark = ctx->ws_top;
     lrs_status gs = launch_orth_gram(ctx, Min, p, c, ldi, rtol, Q, ldq, r_out, !intermediate, rdiag);
@@ -174,8 +175,8 @@ lrs_status raise_dyn_smem(lrs_ctx* ctx, const void* func, size_t bytes) {
 size_t orth_ws_of(int64_t p, int64_t c, int num_sms) { return orth_ws(p, c, num_sms); }
 
 lrs_status orth_basis(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldi, double rtol, double* Q,
-                      int64_t ldq, int64_t* r_out) {
-  return orth(ctx, M, p, c, ldi, rtol, Q, ldq, r_out);
+                      int64_t ldq, int64_t* r_out, int64_t kcap) {
+  return orth(ctx, M, p, c, ldi, rtol, Q, ldq, r_out, false, nullptr, kcap);
 }
 
 static lrs_status gemm(lrs_ctx* ctx, int prec, int64_t M, int64_t N, int64_t K, const void* X,

@@ -14,9 +14,9 @@
 // Error estimate.  Every c-th snapshot, B_f = A_f(J,:), B_c = A_c(J,:):
 //     eps_hat(tau) = c lambda_max(B_f B_f^T - tau B_c B_c^T)
 // for each tau of a caller-given grid.  The m_c x m_c Grams are FP64 (FP32
-// data: the double-float Gram of the SVD path), and lambda_max comes from a
-// one-block cyclic Jacobi eigenvalue iteration per tau (parallel round-robin
-// ordering, rotations from Golub & Van Loan's symmetric 2x2 Schur step).
+// data: the double-float Gram of the SVD path), and lambda_max comes from one
+// block per tau: Householder tridiagonalisation in shared memory, then
+// bisection on Sturm counts.
 #include "common.cuh"
 #include "internal.h"
 
@@ -26,7 +26,6 @@ namespace lrs {
 namespace {
 
 constexpr int kEigMax = 128;    // largest m_c (the matrix lives in shared memory)
-constexpr int kEigSweeps = 40;  // Jacobi sweeps at most (quadratic convergence: ~10 needed)
 
 // C[i][j] = (sum_t a(i,t) b(t,j)) / div[i] (div may be NULL), FP64,
 //   a(i,t) = A[i*a_si + t*a_st],  b(t,j) = B[t*b_st + col(j)*b_sj],  col(j) = cols ? cols[j] : j.
@@ -150,98 +149,131 @@ lrs_status row_gram(lrs_ctx* ctx, const void* B, int32_t dt, int64_t r, int64_t 
   return LRS_OK;
 }
 
-// out[b] = c * lambda_max(Gf - taus[b] Gc) (n x n symmetric, n <= kEigMax), one
-// block per tau: cyclic Jacobi with the round-robin ordering of the indices
-// (a dummy index n pads an odd n; its pairs are skipped), at most kEigSweeps
-// sweeps, stopping once the off-diagonal squares fall below 1e-30 of the
-// diagonal's.  sweeps[b] = sweeps taken (kEigSweeps + 1 if not converged).
-__global__ void __launch_bounds__(256) k_eig_max(const double* __restrict__ Gf, const double* __restrict__ Gc,
-                                                 int n, const double* __restrict__ taus, double c,
-                                                 double* __restrict__ out, int* __restrict__ sweeps) {
-  extern __shared__ double em[];
-  const int ld = n + 1;
-  double* M = em;
-  double* cs = M + n * ld;
-  double* sn = cs + kEigMax / 2;
-  int* pp = reinterpret_cast<int*>(sn + kEigMax / 2);
-  int* qq = pp + kEigMax / 2;
-  __shared__ double red[32];
-  __shared__ int done;
-  const double tau = taus[blockIdx.x];
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e / n, j = e - i * n;
-    M[i * ld + j] = Gf[e] - tau * Gc[e];
+// Sturm count of the symmetric tridiagonal (d, e): the number of its
+// eigenvalues below x, from the signs of the LDL^T pivots of T - x I.
+__device__ int sturm_count(const double* d, const double* e, int n, double x, double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  cnt += q < 0.0;
+  for (int i = 1; i < n; ++i) {
+    q = (d[i] - x) - e[i - 1] * e[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += q < 0.0;
   }
-  __syncthreads();
-  const int np = n + (n & 1), half = np / 2;
-  int sw = 0;
-  for (; sw <= kEigSweeps; ++sw) {
-    double off = 0.0, dia = 0.0;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-      const int i = e / n, j = e - i * n;
-      const double v = M[i * ld + j];
-      if (i == j) dia += v * v; else off += v * v;
-    }
-    off = block_sum(off, red);
-    dia = block_sum(dia, red);
-    if (threadIdx.x == 0) done = (off <= 1e-30 * dia) || sw == kEigSweeps;
-    __syncthreads();
-    if (done) break;
-    for (int t = 0; t < np - 1; ++t) {
-      for (int pi = threadIdx.x; pi < half; pi += blockDim.x) {
-        int a, b;
-        if (pi == 0) { a = t; b = np - 1; }
-        else { a = (t + pi) % (np - 1); b = (t - pi + (np - 1)) % (np - 1); }
-        const int p = min(a, b), q = max(a, b);
-        double cc = 1.0, ss = 0.0;
-        if (q < n) {
-          const double apq = M[p * ld + q];
-          if (apq != 0.0) {
-            const double theta = (M[q * ld + q] - M[p * ld + p]) / (2.0 * apq);
-            const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
-            cc = 1.0 / sqrt(1.0 + tt * tt);
-            ss = tt * cc;
-          }
-        }
-        pp[pi] = p;
-        qq[pi] = q < n ? q : -1;
-        cs[pi] = cc;
-        sn[pi] = ss;
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < half * n; e += blockDim.x) {      // rows p, q <- J^T M
-        const int pi = e / n, j = e - pi * n;
-        const int q = qq[pi];
-        if (q < 0) continue;
-        const int p = pp[pi];
-        const double x = M[p * ld + j], y = M[q * ld + j];
-        M[p * ld + j] = cs[pi] * x - sn[pi] * y;
-        M[q * ld + j] = sn[pi] * x + cs[pi] * y;
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < half * n; e += blockDim.x) {      // columns p, q <- M J
-        const int pi = e / n, j = e - pi * n;
-        const int q = qq[pi];
-        if (q < 0) continue;
-        const int p = pp[pi];
-        const double x = M[j * ld + p], y = M[j * ld + q];
-        M[j * ld + p] = cs[pi] * x - sn[pi] * y;
-        M[j * ld + q] = sn[pi] * x + cs[pi] * y;
-      }
-      __syncthreads();
-    }
-  }
-  if (threadIdx.x == 0) {
-    double mx = M[0];
-    for (int i = 1; i < n; ++i) mx = fmax(mx, M[i * ld + i]);
-    out[blockIdx.x] = c * mx;
-    sweeps[blockIdx.x] = sw;
-  }
+  return cnt;
 }
 
-size_t eig_smem(int n) {
-  return sizeof(double) * (size_t)(n * (n + 1)) + (2 * sizeof(double) + 2 * sizeof(int)) * (kEigMax / 2);
+// out[b] = c * lambda_max(Gf - taus[b] Gc) (n x n symmetric, n <= kEigMax), one
+// block per tau: Householder reduction of the matrix to tridiagonal form in
+// shared memory (Golub & Van Loan, Sec. 8.3.1), then bisection on the Sturm
+// count (Sec. 8.4.1) with kEigPts points per pass, so each pass narrows the
+// bracket of lambda_max by kEigPts + 1; 10 passes reach the rounding level.
+constexpr int kEigPts = 64;
+constexpr int kEigPasses = 10;
+
+__global__ void __launch_bounds__(256) k_eig_max(const double* __restrict__ Gf, const double* __restrict__ Gc,
+                                                 int n, const double* __restrict__ taus, double c,
+                                                 double* __restrict__ out) {
+  extern __shared__ double em[];
+  const int ld = n + 1;
+  double* M = em;                 // n x ld
+  double* v = M + n * ld;         // Householder vector
+  double* w = v + n;              // p, then w = p - K v
+  double* d = w + n;              // tridiagonal: diagonal
+  double* e = d + n;              //              sub-diagonal, e[i] couples i and i + 1
+  __shared__ double red[32];
+  __shared__ double s_lo, s_hi;
+  __shared__ int s_cnt[kEigPts];
+  const double tau = taus[blockIdx.x];
+  for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
+    const int i = q / n, j = q - i * n;
+    M[i * ld + j] = Gf[q] - tau * Gc[q];
+  }
+  __syncthreads();
+  for (int k = 0; k + 2 < n; ++k) {
+    const int len = n - k - 1;                                   // column k below the diagonal
+    double xs = 0.0;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+      const double x = M[(k + 1 + i) * ld + k];
+      xs += x * x;
+    }
+    xs = block_sum(xs, red);
+    const double x0 = M[(k + 1) * ld + k];
+    if (threadIdx.x == 0) d[k] = M[k * ld + k];
+    if (xs == 0.0) {                                             // already reduced (block-uniform)
+      if (threadIdx.x == 0) e[k] = 0.0;
+      __syncthreads();
+      continue;
+    }
+    const double nx = sqrt(xs);
+    const double alpha = x0 >= 0.0 ? -nx : nx;                   // H x = alpha e_1
+    const double beta = 1.0 / (xs - alpha * x0);                 // 2 / (v^T v), v = x - alpha e_1
+    for (int i = threadIdx.x; i < len; i += blockDim.x) v[i] = i == 0 ? x0 - alpha : M[(k + 1 + i) * ld + k];
+    if (threadIdx.x == 0) e[k] = alpha;
+    __syncthreads();
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {       // p = beta A22 v
+      const double* row = M + (k + 1 + i) * ld + (k + 1);
+      double acc = 0.0;
+      for (int j = 0; j < len; ++j) acc = fma(row[j], v[j], acc);
+      w[i] = beta * acc;
+    }
+    __syncthreads();
+    double pv = 0.0;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) pv += w[i] * v[i];
+    pv = block_sum(pv, red);
+    const double K = 0.5 * beta * pv;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) w[i] -= K * v[i];
+    __syncthreads();
+    for (int q = threadIdx.x; q < len * len; q += blockDim.x) {  // A22 -= v w^T + w v^T
+      const int i = q / len, j = q - i * len;
+      M[(k + 1 + i) * ld + (k + 1 + j)] -= v[i] * w[j] + w[i] * v[j];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (n >= 2) {
+      d[n - 2] = M[(n - 2) * ld + (n - 2)];
+      e[n - 2] = M[(n - 1) * ld + (n - 2)];
+    }
+    d[n - 1] = M[(n - 1) * ld + (n - 1)];
+    // Gershgorin bracket of the spectrum
+    double lo = d[0], hi = d[0], emax = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
+      lo = fmin(lo, d[i] - r);
+      hi = fmax(hi, d[i] + r);
+      if (i + 1 < n) emax = fmax(emax, fabs(e[i]));
+    }
+    const double pad = 1e-15 * fmax(fabs(lo), fabs(hi)) + 1e-300;
+    s_lo = lo - pad;
+    s_hi = hi + pad;
+    red[0] = 1e-290 * fmax(1.0, emax * emax);                    // smallest pivot magnitude
+  }
+  __syncthreads();
+  const double pivmin = red[0];
+  __syncthreads();
+  for (int pass = 0; pass < kEigPasses; ++pass) {
+    const double lo = s_lo, hi = s_hi;
+    if (threadIdx.x < kEigPts) {
+      const double x = lo + (hi - lo) * (double)(threadIdx.x + 1) / (double)(kEigPts + 1);
+      s_cnt[threadIdx.x] = sturm_count(d, e, n, x, pivmin);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // count(x) = n exactly when lambda_max < x: keep the last point below it
+      int t = -1;
+      while (t + 1 < kEigPts && s_cnt[t + 1] < n) ++t;
+      const double step = (hi - lo) / (double)(kEigPts + 1);
+      s_lo = t < 0 ? lo : lo + step * (double)(t + 1);
+      s_hi = t + 1 < kEigPts ? lo + step * (double)(t + 2) : hi;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = c * 0.5 * (s_lo + s_hi);
 }
+
+size_t eig_smem(int n) { return sizeof(double) * ((size_t)n * (size_t)(n + 1) + 4 * (size_t)n); }
 
 bool spc_dtype_ok(int32_t dt) { return dt == LRS_F64 || dt == LRS_F32 || dt == LRS_BF16; }
 
@@ -313,18 +345,20 @@ lrs_status lrs_sketch_svd(lrs_ctx* ctx, const double* Y, int64_t m, int64_t l, i
   const size_t ow = orth_ws_of(m, l, ctx->num_sms);
   lrs_status st = ws_reserve(ctx, ow > iter_ws ? ow : iter_ws);
   if (st) return st;
+  // the pivoted QR, stopped at rtol or after pmax steps (only the leading
+  // directions enter the SVD)
   int64_t rank = 0;
-  st = orth_basis(ctx, Y, m, l, ldy, rtol, Q, ldq, &rank);
+  st = orth_basis(ctx, Y, m, l, ldy, rtol, Q, ldq, &rank, pmax);
   if (st) return st;
   *rank_out = rank;
   if (rank < r) return lrs_fail(ctx, LRS_ERANK, "sketch_svd: numerical rank %lld < r = %d", (long long)rank, r);
-  const int64_t p = rank < pmax ? rank : pmax;
-  if (rank > p) {
-    // More directions than the Jacobi tile holds: keep the pivoted QR's
-    // leading p and refine them by two steps of subspace iteration,
-    // Q_p <- orth(Y Y^T Q_p), which shrinks their angle to the dominant
-    // p-dimensional singular subspace by (s_{p+1} / s_p)^2 per step; the
-    // SVD below is then the Rayleigh-Ritz step on that subspace.
+  const int64_t p = rank;
+  if (p == pmax && pmax < mn) {
+    // The sketch may have more directions than the Jacobi tile holds: refine
+    // the leading p by two steps of subspace iteration, Q_p <- orth(Y Y^T Q_p),
+    // which shrinks their angle to the dominant p-dimensional singular
+    // subspace by (s_{p+1} / s_p)^2 per step; the SVD below is then the
+    // Rayleigh-Ritz step on that subspace.
     ctx->ws_top = 0;                                    // Q is the caller's; nothing else is live
     double* Yt = (double*)ws_alloc(ctx, 8 * (size_t)(l * m));
     double* T = (double*)ws_alloc(ctx, 8 * (size_t)(l * p));
@@ -334,15 +368,13 @@ lrs_status lrs_sketch_svd(lrs_ctx* ctx, const double* Y, int64_t m, int64_t l, i
     if (st) return st;
     const size_t mark = ctx->ws_top;
     for (int it = 0; it < 2; ++it) {
-      GemmArgs g1{l, p, m, Y, LRS_F64, ldy, Q, LRS_F64, ldq, T, 1, 0, p, 1.0};      // T = Y^T Q_p
-      st = launch_gemm_simt(ctx, g1, 1);
+      st = small_gemm(ctx, l, p, m, Yt, m, 1, Q, ldq, 1, nullptr, nullptr, T, p);   // T = Y^T Q_p
       if (st) return st;
-      GemmArgs g2{m, p, l, Yt, LRS_F64, m, T, LRS_F64, p, Z, 1, 0, p, 1.0};         // Z = Y T
-      st = launch_gemm_simt(ctx, g2, 1);
+      st = small_gemm(ctx, m, p, l, Y, ldy, 1, T, p, 1, nullptr, nullptr, Z, p);    // Z = Y T
       if (st) return st;
       int64_t rz = 0;
       ctx->ws_top = mark;
-      st = orth_basis(ctx, Z, m, p, p, 0.0, Q, ldq, &rz);
+      st = orth_basis(ctx, Z, m, p, p, 0.0, Q, ldq, &rz, p);
       if (st) return st;
       if (rz != p) return lrs_fail(ctx, LRS_ERANK, "sketch_svd: subspace iteration lost rank (%lld of %lld)",
                                    (long long)rz, (long long)p);
@@ -377,8 +409,7 @@ lrs_status lrs_spc_err(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, in
   double* Gc = (double*)ws_alloc(ctx, 8 * (size_t)(mc * mc));
   double* dtau = (double*)ws_alloc(ctx, 8 * (size_t)ntau);
   double* dout = (double*)ws_alloc(ctx, 8 * (size_t)ntau);
-  int* dsw = (int*)ws_alloc(ctx, 4 * (size_t)ntau);
-  if (!Gf || !Gc || !dtau || !dout || !dsw) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (spc_err)");
+  if (!Gf || !Gc || !dtau || !dout) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (spc_err)");
   // B_f = A_f(J,:), J = c-1, 2c-1, ...: rows at stride c * lda from row c - 1
   const size_t esz = dtype == LRS_F64 ? 8 : (dtype == LRS_F32 ? 4 : 2);
   const char* Bf = (const char*)A + (size_t)(c - 1) * (size_t)lda * esz;
@@ -395,7 +426,7 @@ lrs_status lrs_spc_err(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, in
     st = raise_dyn_smem(ctx, (const void*)k_eig_max, smem);
     if (st) return st;
   }
-  k_eig_max<<<(unsigned)ntau, 256, smem, ctx->stream>>>(Gf, Gc, (int)mc, dtau, (double)c, dout, dsw);
+  k_eig_max<<<(unsigned)ntau, 256, smem, ctx->stream>>>(Gf, Gc, (int)mc, dtau, (double)c, dout);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
   LRS_CUDA_TRY(ctx, cudaMemcpyAsync(eps_hat, dout, 8 * (size_t)ntau, cudaMemcpyDeviceToHost, ctx->stream));

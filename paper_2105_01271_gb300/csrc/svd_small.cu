@@ -156,7 +156,12 @@ k_jacobi(const double* __restrict__ R, int64_t r, double* __restrict__ Vout, dou
   for (int64_t c = threadIdx.x; c < rp; c += blockDim.x) order[c] = (int)c;
   __syncthreads();
   const T eps = sizeof(T) == 8 ? T(1.1102230246251565e-16) : T(5.9604645e-08);
-  const T tol = eps * sqrt((T)r);
+  // a pair counts as orthogonal once |w_p . w_q| <= tol ||w_p|| ||w_q||.  The
+  // computed dot product itself carries ~sqrt(r) eps of rounding, so a
+  // threshold at that level keeps re-rotating converged pairs until the sweep
+  // cap; eps * max(r, 16) (the column length, as in LAPACK's one-sided
+  // Jacobi) sits safely above it.
+  const T tol = eps * (T)(r > 16 ? r : 16);
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();

@@ -101,6 +101,9 @@ class SpcResult:
     P: torch.Tensor
     Sf: torch.Tensor       # lifted skeleton A_c(J,:) T_r (k x n): A_f ~ P Sf
     Y: torch.Tensor        # the sketch A_c
+    U: torch.Tensor        # leading r singular triplets of A_c
+    S: torch.Tensor
+    V: torch.Tensor
     r: int                 # lifting rank used
     rank_c: int            # numerical rank of the sketch
     err_est: float         # coarse ID error (lrs_id_k)
@@ -132,7 +135,7 @@ def spc_id_path(ctx: Context, A: torch.Tensor, dtype: str, grid, k: int, r_lift:
     err, st = ctx.id_k(Y, m, l, l, k, J, P, k)
     Sf = torch.empty((k, n), dtype=f64 if prec == LRS_PREC_FP64 else torch.float32, device=dev)
     ctx.spc_lift(A, dt, m, n, n, Y, l, l, U, r, S, V, r, r, J, k, prec, Sf, n)
-    return SpcResult(J, P, Sf, Y, r, rank_c, err, st)
+    return SpcResult(J, P, Sf, Y, U, S, V, r, rank_c, err, st)
 
 
 def spc_err(ctx: Context, A: torch.Tensor, dtype: str, Y: torch.Tensor, c: int, taus) -> list:
