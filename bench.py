@@ -112,7 +112,7 @@ def clocks_start(dev):
          "clocks_event_reasons.sw_power_cap")
     try:
         pr = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                               "-lms", "200", "-i", str(dev)], stdout=f, stderr=subprocess.DEVNULL)
+                               "-lms", "50", "-i", str(dev)], stdout=f, stderr=subprocess.DEVNULL)
     except Exception:
         pr = None
     # wait for the first sample: the query tool's start-up (seconds on a fresh
@@ -136,6 +136,9 @@ def clocks_mark(h) -> int:
 
 
 def clocks_stop(h, skip: int = 0):
+    """Median SM clock and throttle reasons of the samples taken after `skip`
+    (the timed region).  A region shorter than two sampling periods also
+    keeps the sample just before it, taken under the same warm-up load."""
     pr, f = h
     if pr is None:
         return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -147,7 +150,10 @@ def clocks_stop(h, skip: int = 0):
     f.seek(0)
     sm, mx, reasons = [], [], set()
     names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-    for line in f.read().splitlines()[skip:]:
+    lines = f.read().splitlines()
+    if len(lines) - skip < 2 and skip > 0:
+        skip -= 1
+    for line in lines[skip:]:
         parts = [x.strip() for x in line.split(",")]
         if len(parts) < 7:
             continue

@@ -19,6 +19,10 @@ struct lrs_ctx {
   size_t ws_top = 0;
   // small pinned host buffer for scalar read-back
   void* host_scratch = nullptr;
+  // side buffer for split-K partial sums of the CUDA-core GEMM (independent of
+  // the workspace arena, which callers lay out before the GEMM runs)
+  void* aux = nullptr;
+  size_t aux_cap = 0;
   int64_t launches = 0;
 };
 
@@ -34,6 +38,7 @@ lrs_status raise_dyn_smem(lrs_ctx* ctx, const void* func, size_t bytes);
 
 // workspace ---------------------------------------------------------------
 lrs_status ws_reserve(lrs_ctx* ctx, size_t bytes);           // grow (only between calls)
+lrs_status aux_reserve(lrs_ctx* ctx, size_t bytes);          // grow ctx->aux (synchronises when it grows)
 void* ws_alloc(lrs_ctx* ctx, size_t bytes);                   // 256-B aligned, nullptr if full
 
 // sketch.cu ----------------------------------------------------------------

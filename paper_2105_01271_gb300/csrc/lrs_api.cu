@@ -45,6 +45,23 @@ lrs_status ws_reserve(lrs_ctx* ctx, size_t bytes) {
   return LRS_OK;
 }
 
+lrs_status aux_reserve(lrs_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->aux_cap) return LRS_OK;
+  if (ctx->aux) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->aux);
+    ctx->aux = nullptr;
+    ctx->aux_cap = 0;
+  }
+  const size_t cap = bytes + (bytes >> 2);
+  if (cudaMalloc(&ctx->aux, cap) != cudaSuccess) {
+    cudaGetLastError();
+    return lrs_fail(ctx, LRS_ENOMEM, "cannot allocate a %zu-byte split-K buffer", cap);
+  }
+  ctx->aux_cap = cap;
+  return LRS_OK;
+}
+
 void* ws_alloc(lrs_ctx* ctx, size_t bytes) {
   const size_t b = align256(bytes);
   if (ctx->ws_top + b > ctx->ws_cap) return nullptr;
@@ -219,6 +236,7 @@ lrs_status lrs_create(lrs_ctx** out, int device, void* cuda_stream) {
 void lrs_destroy(lrs_ctx* ctx) {
   if (!ctx) return;
   if (ctx->ws) { cudaStreamSynchronize(ctx->stream); cudaFree(ctx->ws); }
+  if (ctx->aux) { cudaStreamSynchronize(ctx->stream); cudaFree(ctx->aux); }
   if (ctx->host_scratch) cudaFreeHost(ctx->host_scratch);
   delete ctx;
 }
