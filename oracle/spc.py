@@ -1,4 +1,14 @@
-"""SPC-ID and its single-pass error estimate (oracle; test infrastructure).
+"""SPC-SVD, SPC-ID and the single-pass error estimate (oracle; test infrastructure).
+
+Paper, Sec. 3.2, Alg. 3 (SPC-SVD).  The same single read forms A_c = A_f D and
+H = A_f^T A_c; then QR(A_c) = Q_c R_c, H R_c^-1 = A_f^T Q_c, and the SVD of
+(H R_c^-1)^T = Q_c^T A_f = U~ S V^T gives U = Q_c U~, S, V (rank k: the
+leading k).  Reading: R_c^-1 exists only on the numerical range of A_c (the
+sketch of FP32 or smooth data is numerically rank deficient), so Q_c is taken
+as the leading r left singular vectors U_r of A_c, where R_c^-1 becomes
+V_r S_r^-1 (A_c V_r S_r^-1 = U_r):  B = S_r^-1 V_r^T H^T = U_r^T A_f.  With r =
+rank A_c = l (full column rank) this is Alg. 3 as printed (range(U_r) =
+range(Q_c)); the pins check that case against the literal QR route.
 
 Paper, Sec. 4, Alg. 5 (SPC-ID).  One read of A_f, row by row, forms
 
@@ -93,6 +103,34 @@ def spc_id(Af, Ac: np.ndarray, k: int, r: int):
     T = lifting_operator(Af, Ac, r)
     J, P, _ = row_id(Ac, k)
     return J, P, Ac[J] @ T, T
+
+
+def spc_svd(Af, Ac: np.ndarray, k: int, r: int, col_block: int = 1 << 15):
+    """Alg. 3 with Q_c = U_r: returns (U_k, S_k, V_k) of B = S_r^-1 V_r^T H^T."""
+    Af = as_f64(Af)
+    n = Af.shape[1]
+    U, s, V, rank = _thin_svd(Ac)
+    if not 1 <= r <= rank:
+        raise ValueError(f"r = {r} outside [1, rank A_c = {rank}]")
+    left = V[:, :r] / s[:r]                         # R_c^-1 restricted: V_r S_r^-1 (l x r)
+    B = np.empty((r, n))
+    for c0 in range(0, n, col_block):
+        Hb = Af[:, c0:c0 + col_block].T @ Ac        # rows c0.. of H = A_f^T A_c
+        B[:, c0:c0 + col_block] = (Hb @ left).T     # (H R_c^-1)^T
+    Ub, sb, Vbt = np.linalg.svd(B, full_matrices=False)
+    kk = min(k, r)
+    return U[:, :r] @ Ub[:, :kk], sb[:kk], Vbt[:kk].T
+
+
+def spc_svd_qr(Af, Ac: np.ndarray, k: int):
+    """Alg. 3 as printed, for a sketch of full column rank: QR(A_c), H R_c^-1,
+    SVD of its transpose."""
+    Af = as_f64(Af)
+    Qc, Rc = np.linalg.qr(Ac)
+    H = Af.T @ Ac
+    HR = np.linalg.solve(Rc.T, H.T).T               # H R_c^-1
+    Ub, sb, Vbt = np.linalg.svd(HR.T, full_matrices=False)
+    return Qc @ Ub[:, :k], sb[:k], Vbt[:k].T
 
 
 def subsample_rows(m: int, c: int) -> np.ndarray:

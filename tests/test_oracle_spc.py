@@ -104,3 +104,31 @@ def test_theorem_bound_holds(k):
             assert err <= b * (1 + 1e-9), (r, t)
     bound, _, _ = spc.spc_bound(Ac, J, P, taus, eps, k)
     assert np.isfinite(bound)
+
+
+def test_spc_svd_full_rank_sketch_matches_alg3_as_printed():
+    """A sketch of full column rank (r = l): the U_r form of Alg. 3 and the
+    literal QR(A_c), H R_c^-1 route give the same rank-k factors."""
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((40, 64)) @ np.diag(0.8 ** np.arange(64)) @ rng.standard_normal((64, 256))
+    Ac = oracle.sketch(A, GridSpec((16, 16), (4, 4), "blockavg"))     # l = 16, full column rank
+    assert np.linalg.matrix_rank(Ac) == 16
+    U1, s1, V1 = spc.spc_svd(A, Ac, 6, 16)
+    U2, s2, V2 = spc.spc_svd_qr(A, Ac, 6)
+    assert np.allclose(s1, s2, rtol=1e-10)
+    assert np.allclose(U1 @ U1.T, U2 @ U2.T, atol=1e-9) and np.allclose(V1 @ V1.T, V2 @ V2.T, atol=1e-9)
+
+
+def test_spc_svd_recovers_exact_rank_k_data():
+    """rank A_f = k = rank A_c: range(U_k) = range(A_f) and U S V^T = A_f."""
+    m, N, k = 30, 16, 4
+    rng = np.random.default_rng(9)
+    x = (np.arange(N) + 0.5) / N
+    modes = [np.outer(np.sin((a + 1) * np.pi * x), np.cos(b * np.pi * x)).ravel()
+             for a, b in [(0, 0), (1, 0), (0, 1), (2, 1)]]
+    A = rng.standard_normal((m, k)) @ np.stack(modes)
+    Ac = oracle.sketch(A, GridSpec((N, N), (4, 4), "fullweight"))
+    U, s, V = spc.spc_svd(A, Ac, k, k)
+    assert np.linalg.norm(A - (U * s) @ V.T) <= 1e-11 * np.linalg.norm(A)
+    # the singular values are A_f's own
+    assert np.allclose(s, np.linalg.svd(A, compute_uv=False)[:k], rtol=1e-10)
