@@ -231,6 +231,50 @@ lrs_status lrs_spc_err(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, in
                        double* eps_hat);
 
 /*
+ * Single-read SPC over streamed snapshots (Sec. 3.2, Alg. 3; Sec. 4, Algs. 5
+ * and 6).  The rows of A_f arrive in blocks, from host memory or from device
+ * memory, and each block is read once:
+ *   A_c(rows,:) = a_f D,   H^T += A_c(rows,:)^T a_f   (l x n on the device,
+ *   FP32, FP64 when prec == LRS_PREC_FP64),   ||A_f||_F^2 += ||a_f||_F^2,
+ * and, with err_c > 0, the rows c-1, 2c-1, ... are kept for SPC-ID-ERR.
+ * Host blocks are copied on the stream's own copy stream into two staging
+ * buffers, each guarded by a "copied" and a "free" event, so the copy of one
+ * block overlaps the work on the previous one.
+ *
+ *   lrs_spc_stream_create  ctx (borrowed; must outlive the stream), storage
+ *       dtype, m rows in all, sketch grid, block_rows (staging size),
+ *       err_c (0: keep no rows; else 1 <= m / err_c <= 128), prec of the
+ *       H^T products.  Allocates A_c (8 m l bytes), H^T (4 or 8 l n bytes),
+ *       2 staging blocks and the kept rows.
+ *   lrs_spc_stream_push    nrows rows of A_f (row stride ld >= n), host
+ *       (on_device = 0; pinned memory overlaps best) or device (1; read in
+ *       place); returns once the work is queued on ctx's stream.  The rows
+ *       must total m before a finisher runs.
+ *   lrs_spc_stream_svd     SPC-SVD (Alg. 3) with Q_c = the leading r left
+ *       singular vectors of A_c (lrs_sketch_svd, tolerance rtol; r <= 112):
+ *       B = S_r^-1 V_r^T H^T = U_r^T A_f, then as lrs_svd_k: U (m x k FP64),
+ *       S (k), V (n x k; FP64 for FP64 prec, else FP32); err_est (host, may
+ *       be NULL) as lrs_svd_k's.
+ *   lrs_spc_stream_id      SPC-ID (Alg. 5): (J, P) = lrs_id_k of A_c, and the
+ *       lifted skeleton S_f = A_c(J,:) T_r (k x n; FP64 for FP64 prec, else
+ *       FP32) with T_r = V_r S_r^-2 V_r^T H^T, the operator as printed.
+ *   lrs_spc_stream_err     SPC-ID-ERR (Alg. 6) on the kept rows: as
+ *       lrs_spc_err with c = err_c (host taus / eps_hat).
+ *   lrs_spc_stream_sketch  A_c (device, m x l FP64, row stride l).
+ */
+typedef struct lrs_spc_stream lrs_spc_stream;
+lrs_status lrs_spc_stream_create(lrs_ctx* ctx, int32_t dtype, int64_t m, const lrs_grid* sketch, int64_t block_rows,
+                                 int32_t err_c, int32_t prec, lrs_spc_stream** out);
+lrs_status lrs_spc_stream_push(lrs_spc_stream* s, const void* rows, int64_t nrows, int64_t ld, int32_t on_device);
+lrs_status lrs_spc_stream_svd(lrs_spc_stream* s, double rtol, int32_t r, int32_t k, double* U, int64_t ldu, double* S,
+                              void* V, int64_t ldv, double* err_est);
+lrs_status lrs_spc_stream_id(lrs_spc_stream* s, double rtol, int32_t r, int32_t k, int32_t* J, double* P, int64_t ldp,
+                             void* Sf, int64_t ldsf, double* err_est);
+lrs_status lrs_spc_stream_err(lrs_spc_stream* s, const double* taus, int32_t ntau, double* eps_hat);
+const double* lrs_spc_stream_sketch(const lrs_spc_stream* s);
+void lrs_spc_stream_destroy(lrs_spc_stream* s);
+
+/*
  * lrs_gemm_tn -- the dense contraction every A-pass uses:
  *   C (M x N) = X^T A,   X: K x M,  A: K x N  (both row-major, K rows).
  * Exposed for tests and benchmarks of the A-pass kernel alone.

@@ -106,6 +106,16 @@ _SIG = {
     "lrs_spc_err": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_int64,
                               C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.POINTER(C.c_double), C.c_int32,
                               C.POINTER(C.c_double)]),
+    "lrs_spc_stream_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_int64, C.c_int32,
+                                        C.c_int32, C.POINTER(C.c_void_p)]),
+    "lrs_spc_stream_push": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32]),
+    "lrs_spc_stream_svd": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_int32, C.c_void_p, C.c_int64,
+                                     C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
+    "lrs_spc_stream_id": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                    C.c_int64, C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
+    "lrs_spc_stream_err": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_double)]),
+    "lrs_spc_stream_sketch": (C.c_void_p, [C.c_void_p]),
+    "lrs_spc_stream_destroy": (None, [C.c_void_p]),
     "lrs_mlp_param_count": (C.c_int64, []),
     "lrs_mlp_init_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "lrs_mlp_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
@@ -150,7 +160,9 @@ def _ptr(x) -> int:
         return 0
     if isinstance(x, int):
         return x
-    return int(x.data_ptr())
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    return int(x.ctypes.data)              # a numpy array in host memory
 
 
 class Context:
@@ -272,6 +284,56 @@ class Context:
     def gemm_tn(self, M, N, K, X, x_dtype, ldx, A, a_dtype, lda, Cm, c_f64, c_trans, ldc, prec):
         return self._check(self.lib.lrs_gemm_tn(self.h, M, N, K, _ptr(X), x_dtype, ldx, _ptr(A),
                                                 a_dtype, lda, _ptr(Cm), c_f64, c_trans, ldc, prec))
+
+
+class SpcStream:
+    """lrs_spc_stream: the single read of streamed snapshots (Algs. 3, 5, 6).
+    Keep the Context alive while the stream exists."""
+
+    def __init__(self, ctx: Context, dtype: int, m: int, sketch: lrs_grid, block_rows: int, err_c: int = 0,
+                 prec: int = LRS_PREC_SPLIT_BF16):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        h = C.c_void_p()
+        ctx._check(self.lib.lrs_spc_stream_create(ctx.h, dtype, m, C.byref(sketch), block_rows, err_c, prec,
+                                                  C.byref(h)))
+        self.h = h
+
+    def push(self, rows, nrows: int, ld: int, on_device: bool):
+        return self.ctx._check(self.lib.lrs_spc_stream_push(self.h, _ptr(rows), nrows, ld, 1 if on_device else 0))
+
+    def svd(self, rtol, r, k, U, ldu, S, V, ldv) -> float:
+        err = C.c_double(0.0)
+        self.ctx._check(self.lib.lrs_spc_stream_svd(self.h, rtol, r, k, _ptr(U), ldu, _ptr(S), _ptr(V), ldv,
+                                                    C.byref(err)))
+        return err.value
+
+    def id(self, rtol, r, k, J, P, ldp, Sf, ldsf) -> float:
+        err = C.c_double(0.0)
+        self.ctx._check(self.lib.lrs_spc_stream_id(self.h, rtol, r, k, _ptr(J), _ptr(P), ldp, _ptr(Sf), ldsf,
+                                                   C.byref(err)))
+        return err.value
+
+    def err(self, taus) -> list:
+        nt = len(taus)
+        t = (C.c_double * nt)(*[float(x) for x in taus])
+        out = (C.c_double * nt)()
+        self.ctx._check(self.lib.lrs_spc_stream_err(self.h, t, nt, out))
+        return list(out)
+
+    def sketch_ptr(self) -> int:
+        return int(self.lib.lrs_spc_stream_sketch(self.h) or 0)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lrs_spc_stream_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def load(device: int = 0, stream=None) -> Context:

@@ -533,6 +533,7 @@ lrs_status run_apass(lrs_ctx* ctx, const GemmArgs& a, double* fro2_out) {
 
 bool apass_eligible(const GemmArgs& a, int prec) {
   if (prec != LRS_PREC_SPLIT_BF16 && prec != LRS_PREC_BF16X3) return false;
+  if (a.accum) return false;                       // the epilogue overwrites C
   if (a.adt != LRS_F32 && a.adt != LRS_BF16) return false;
   if (a.M < 1 || a.M > kMaxR || a.N < TN || a.K < 1) return false;
   if (a.N >= (int64_t)1 << 31 || a.K >= (int64_t)1 << 31) return false;

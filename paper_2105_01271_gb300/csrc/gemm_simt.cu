@@ -89,8 +89,13 @@ __global__ void __launch_bounds__(256) k_gemm_tn(GemmArgs a, int64_t kc, T* __re
       }
       const T v = alpha * acc[i][j];
       const int64_t off = a.c_trans ? gn * a.ldc + gm : gm * a.ldc + gn;
-      if (a.c_f64) reinterpret_cast<double*>(a.C)[off] = (double)v;
-      else reinterpret_cast<float*>(a.C)[off] = (float)v;
+      if (a.c_f64) {
+        double* c = reinterpret_cast<double*>(a.C) + off;
+        *c = a.accum ? *c + (double)v : (double)v;
+      } else {
+        float* c = reinterpret_cast<float*>(a.C) + off;
+        *c = a.accum ? *c + (float)v : (float)v;
+      }
     }
   }
 }
@@ -104,8 +109,13 @@ __global__ void k_gemm_sum(const T* __restrict__ part, int64_t splits, GemmArgs 
     const int64_t gm = e / a.N, gn = e - gm * a.N;
     const T v = (T)a.alpha * s;
     const int64_t off = a.c_trans ? gn * a.ldc + gm : gm * a.ldc + gn;
-    if (a.c_f64) reinterpret_cast<double*>(a.C)[off] = (double)v;
-    else reinterpret_cast<float*>(a.C)[off] = (float)v;
+    if (a.c_f64) {
+      double* c = reinterpret_cast<double*>(a.C) + off;
+      *c = a.accum ? *c + (double)v : (double)v;
+    } else {
+      float* c = reinterpret_cast<float*>(a.C) + off;
+      *c = a.accum ? *c + (float)v : (float)v;
+    }
   }
 }
 

@@ -82,6 +82,7 @@ struct TcParams {
   const void* A; int32_t adt; int64_t lda;
   void* C; int c_f64; int c_trans; int64_t ldc;
   double alpha;
+  int accum;
   int64_t Mt, Nt, Kt;
   int64_t splits, KS;       // split-K: K-tile chunks of KS tiles; splits > 1 -> FP32 partials
   float* partial;           // splits x M x N (row-major) when splits > 1
@@ -288,8 +289,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcParams P) {
               if (nn >= P.N) break;
               const double val = P.alpha * (double)__uint_as_float(v[e]);
               const int64_t off = P.c_trans ? nn * P.ldc + m : m * P.ldc + nn;
-              if (P.c_f64) reinterpret_cast<double*>(P.C)[off] = val;
-              else reinterpret_cast<float*>(P.C)[off] = (float)val;
+              if (P.c_f64) {
+                double* c = reinterpret_cast<double*>(P.C) + off;
+                *c = P.accum ? *c + val : val;
+              } else {
+                float* c = reinterpret_cast<float*>(P.C) + off;
+                *c = P.accum ? (float)((double)*c + val) : (float)val;
+              }
             }
           }
         }
@@ -391,7 +397,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcParams P) {
 // ---------------------------------------------------------------------------
 // C = alpha * sum_s partial[s] in a fixed order (deterministic split-K)
 __global__ void k_splitk_reduce(const float* __restrict__ part, int64_t splits, int64_t M, int64_t N,
-                                double alpha, void* __restrict__ C, int c_f64, int c_trans, int64_t ldc) {
+                                double alpha, void* __restrict__ C, int c_f64, int c_trans, int64_t ldc, int accum) {
   const int64_t total = M * N;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -399,8 +405,13 @@ __global__ void k_splitk_reduce(const float* __restrict__ part, int64_t splits, 
     for (int64_t s = 0; s < splits; ++s) acc += (double)part[s * total + e];
     const int64_t m = e / N, nn = e - m * N;
     const int64_t off = c_trans ? nn * ldc + m : m * ldc + nn;
-    if (c_f64) reinterpret_cast<double*>(C)[off] = alpha * acc;
-    else reinterpret_cast<float*>(C)[off] = (float)(alpha * acc);
+    if (c_f64) {
+      double* c = reinterpret_cast<double*>(C) + off;
+      *c = accum ? *c + alpha * acc : alpha * acc;
+    } else {
+      float* c = reinterpret_cast<float*>(C) + off;
+      *c = accum ? (float)((double)*c + alpha * acc) : (float)(alpha * acc);
+    }
   }
 }
 
@@ -425,7 +436,7 @@ static lrs_status run_tc(lrs_ctx* ctx, const GemmArgs& a, double* fro2_out) {
   TcParams P{};
   P.M = a.M; P.N = a.N; P.K = a.K;
   P.A = a.A; P.adt = a.adt; P.lda = a.lda;
-  P.C = a.C; P.c_f64 = a.c_f64; P.c_trans = a.c_trans; P.ldc = a.ldc; P.alpha = a.alpha;
+  P.C = a.C; P.c_f64 = a.c_f64; P.c_trans = a.c_trans; P.ldc = a.ldc; P.alpha = a.alpha; P.accum = a.accum;
   P.Mt = (a.M + TBM - 1) / TBM; P.Nt = (a.N + TBN - 1) / TBN; P.Kt = (a.K + TBK - 1) / TBK;
   P.splits = fro2_out ? 1 : choose_splits(P.Mt * P.Nt, P.Kt, ctx->num_sms);
   P.KS = (P.Kt + P.splits - 1) / P.splits;
@@ -467,7 +478,7 @@ static lrs_status run_tc(lrs_ctx* ctx, const GemmArgs& a, double* fro2_out) {
     int64_t nb = (tot + 255) / 256;
     if (nb > (int64_t)ctx->num_sms * 8) nb = (int64_t)ctx->num_sms * 8;
     k_splitk_reduce<<<(unsigned)nb, 256, 0, ctx->stream>>>(P.partial, P.splits, a.M, a.N, a.alpha, a.C,
-                                                            a.c_f64, a.c_trans, a.ldc);
+                                                            a.c_f64, a.c_trans, a.ldc, a.accum);
     ctx->launches++;
     LRS_CUDA_TRY(ctx, cudaGetLastError());
   }

@@ -73,8 +73,18 @@ struct GemmArgs {
   const void* A; int32_t adt; int64_t lda;
   void* C; int c_f64; int c_trans; int64_t ldc;
   double alpha;            // C = alpha * X^T A
+  int accum = 0;           // 1: C += alpha * X^T A (CUDA-core and k_gemm_tc paths; never the TMA A-pass)
 };
 lrs_status launch_gemm_simt(lrs_ctx* ctx, const GemmArgs& a, int fp64);
+// lrs_api.cu: the precision dispatch of every product (FP64 / FP32 CUDA cores, tensor-core forms)
+lrs_status gemm_prec(lrs_ctx* ctx, int prec, int64_t M, int64_t N, int64_t K, const void* X, int32_t xdt, int64_t ldx,
+                     const void* A, int32_t adt, int64_t lda, void* C, int c_f64, int c_trans, int64_t ldc);
+// the SVD of a given B (r x n, row stride n; FP64 when prec is FP64, else FP32)
+// with rows in the basis Q (m x r): U = Q U_B, S, V = B^T U_B S^-1, as lrs_svd_k
+size_t svd_from_b_ws(int64_t r, int64_t n, int64_t m, int64_t kk, int32_t prec, int num_sms);
+lrs_status svd_from_b(lrs_ctx* ctx, const void* B, int64_t r, int64_t n, const double* Q, int64_t ldq, int64_t m,
+                      int32_t k, int32_t prec, double* U, int64_t ldu, double* S, void* V, int64_t ldv,
+                      const double* fro2, double* err_est);
 // fro2_out (device, may be NULL): also ||A||_F^2 of the operand A, fused (M <= 128 only)
 lrs_status launch_gemm_tc(lrs_ctx* ctx, const GemmArgs& a, int prec, double* fro2_out = nullptr);
 // apass_tc.cu: the same product for a narrow X (M <= 256) and a wide FP32/BF16
@@ -127,6 +137,17 @@ size_t orth_gram_ws(int64_t p, int64_t c, int num_sms);
 size_t orth_ws_of(int64_t p, int64_t c, int num_sms);
 lrs_status orth_basis(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldi, double rtol, double* Q,
                       int64_t ldq, int64_t* r_out, int64_t kcap = 0);
+// spc.cu: C[i][j] = (sum_t a(i,t) b(t,j)) / div[i] (div may be NULL), FP64, with
+// a(i,t) = A[i*a_si + t*a_st], b(t,j) = B[t*b_st + col(j)*b_sj], col(j) = cols ? cols[j] : j
+lrs_status spc_small_gemm(lrs_ctx* ctx, int64_t M, int64_t N, int64_t K, const double* A, int64_t a_si, int64_t a_st,
+                          const double* B, int64_t b_st, int64_t b_sj, const int32_t* cols, const double* div,
+                          double* C, int64_t ldc);
+// spc.cu: eps_hat[i] = cf lambda_max(B_f B_f^T - taus[i] B_c B_c^T) from kept rows
+// B_f (mc x n, storage dtype, row stride ldb) and B_c (mc x l FP64, row stride ldc);
+// taus / eps_hat host arrays; synchronises
+lrs_status spc_err_from_rows(lrs_ctx* ctx, const void* Bf, int32_t dtype, int64_t mc, int64_t n, int64_t ldb,
+                             const double* Bc, int64_t l, int64_t ldc, double cf, const double* taus, int32_t ntau,
+                             double* eps_hat);
 // rdiag (optional, device): |R_ii| of the pivoted factor, i < r
 lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldm, double rtol,
                             double* Q, int64_t ldq, int64_t* r_out, bool refine = true, double* rdiag = nullptr);

@@ -420,52 +420,37 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
   return LRS_OK;
 }
 
-lrs_status lrs_svd_k(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
-                     const double* Q, int64_t ldq, int64_t r, int32_t k, int32_t prec, double* U,
-                     int64_t ldu, double* S, void* V, int64_t ldv, double* err_est) {
-  if (!ctx) return LRS_EINVAL;
-  ctx->err[0] = 0;
-  if (!A || !Q || !U || !S || !V) return lrs_fail(ctx, LRS_EINVAL, "svd_k: NULL pointer");
-  if (!dtype_ok(dtype) || !prec_ok(prec)) return lrs_fail(ctx, LRS_EINVAL, "svd_k: bad dtype/prec");
-  if (m < 1 || n < 1 || r < 1 || k < 1) return lrs_fail(ctx, LRS_EINVAL, "svd_k: m=%lld n=%lld r=%lld k=%d", (long long)m, (long long)n, (long long)r, k);
-  if (r > m) return lrs_fail(ctx, LRS_EINVAL, "svd_k: r=%lld > m=%lld", (long long)r, (long long)m);
-  const int64_t kk = k < r ? k : r;
-  if (lda < n || ldq < r || ldu < kk || ldv < kk) return lrs_fail(ctx, LRS_EINVAL, "svd_k: strides too small");
-  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-  const int f64 = prec == LRS_PREC_FP64;
-  const size_t bsz = f64 ? 8 : 4;
-  size_t need = align256(bsz * (size_t)(r * n));            // B
-  need += tsqr_ws(r, n, bsz) + r_of_bt_gram_ws(r, ctx->num_sms);
+}  // extern "C"
+
+namespace lrs {
+
+size_t svd_from_b_ws(int64_t r, int64_t n, int64_t m, int64_t kk, int32_t prec, int num_sms) {
+  const size_t bsz = prec == LRS_PREC_FP64 ? 8 : 4;
+  size_t need = tsqr_ws(r, n, bsz) + r_of_bt_gram_ws(r, num_sms);
   need += 4 * align256(8 * (size_t)(r * r)) + align256(8 * (size_t)(m * r)) + 65536;
-  if (prec >= LRS_PREC_SPLIT_BF16)
-    need += gemm_tc_workspace(r, m, prec) + gemm_tc_splitk_workspace(r, n, m, ctx->num_sms) + 4096 +
-            gemm_tc_workspace(kk, r, LRS_PREC_BF16X3) + 4096;
-  lrs_status st = ws_reserve(ctx, need);
-  if (st) return st;
-  void* B = ws_alloc(ctx, bsz * (size_t)(r * n));
-  double* fro2 = (double*)ws_alloc(ctx, 8);
+  if (prec >= LRS_PREC_SPLIT_BF16) need += gemm_tc_workspace(kk, r, LRS_PREC_BF16X3) + 4096;
+  return need;
+}
+
+// (a5) SVD of a given B (r x n, FP64 when prec is FP64, else FP32; row stride
+// n) whose rows live in the range basis Q (m x r): U = Q U_B(:, :kk), S, V =
+// B^T U_B S^-1.  fro2 (device, may be NULL) holds ||A_f||_F^2 for err_est.
+lrs_status svd_from_b(lrs_ctx* ctx, const void* B, int64_t r, int64_t n, const double* Q, int64_t ldq, int64_t m,
+                      int32_t k, int32_t prec, double* U, int64_t ldu, double* S, void* V, int64_t ldv,
+                      const double* fro2, double* err_est) {
+  const int f64 = prec == LRS_PREC_FP64;
+  const int64_t kk = k < r ? k : r;
   double* Rm = (double*)ws_alloc(ctx, 8 * (size_t)(r * r));
   double* Vr = (double*)ws_alloc(ctx, 8 * (size_t)(r * r));
   double* sv = (double*)ws_alloc(ctx, 8 * (size_t)r);
   double* Wk = (double*)ws_alloc(ctx, 8 * (size_t)(r * kk));
   double* QT = (double*)ws_alloc(ctx, 8 * (size_t)(m * r));
   double* sgn = (double*)ws_alloc(ctx, 8 * (size_t)kk);
-  if (!B || !fro2 || !Rm || !Vr || !sv || !Wk || !QT || !sgn) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd_k)");
-  // (a4) B = Q^T A_f -- the one full read of A_f (||A_f||_F^2 fused on the tensor-core path)
-  GemmArgs ga{r, n, m, Q, LRS_F64, ldq, A, dtype, lda, B, f64, 0, n, 1.0};
-  if (prec >= LRS_PREC_SPLIT_BF16 && (r <= 128 || apass_eligible(ga, prec))) {
-    st = launch_gemm_tc(ctx, ga, prec, fro2);
-    if (st) return st;
-  } else {
-    st = gemm(ctx, prec, r, n, m, Q, LRS_F64, ldq, A, dtype, lda, B, f64, 0, n);
-    if (st) return st;
-    st = launch_fro2(ctx, A, dtype, m, n, lda, fro2);
-    if (st) return st;
-  }
-  // (a5) SVD(B): R of B^T, Jacobi on R -> U_B = Vr, s.  FP32 B: R from the
+  if (!Rm || !Vr || !sv || !Wk || !QT || !sgn) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd)");
+  // SVD(B): R of B^T, Jacobi on R -> U_B = Vr, s.  FP32 B: R from the
   // double-float Gram and an FP64 Cholesky (TSQR if that breaks down); FP64 B:
   // Householder TSQR.
-  st = LRS_ERANK;
+  lrs_status st = LRS_ERANK;
   if (!f64 && r <= 128) {
     const size_t mark = ctx->ws_top;
     st = launch_r_of_bt_gram(ctx, (const float*)B, r, n, n, Rm);
@@ -502,16 +487,65 @@ lrs_status lrs_svd_k(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int6
   LRS_CUDA_TRY(ctx, cudaMemcpyAsync(S, sv, 8 * (size_t)kk, cudaMemcpyDeviceToDevice, ctx->stream));
   if (err_est) {
     double* h = (double*)ctx->host_scratch;
-    LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h, fro2, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    if (fro2) LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h, fro2, 8, cudaMemcpyDeviceToHost, ctx->stream));
     std::vector<double> s_h((size_t)r);
     LRS_CUDA_TRY(ctx, cudaMemcpyAsync(s_h.data(), sv, 8 * (size_t)r, cudaMemcpyDeviceToHost, ctx->stream));
     LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     // energy of B beyond rank k, summed smallest first
     double tail = 0.0;
     for (int64_t i = r - 1; i >= kk; --i) tail += s_h[(size_t)i] * s_h[(size_t)i];
-    const double f = h[0];
+    const double f = fro2 ? h[0] : 0.0;
     *err_est = f > 0.0 ? sqrt(tail / f) : 0.0;
   }
+  return LRS_OK;
+}
+
+lrs_status gemm_prec(lrs_ctx* ctx, int prec, int64_t M, int64_t N, int64_t K, const void* X, int32_t xdt, int64_t ldx,
+                     const void* A, int32_t adt, int64_t lda, void* C, int c_f64, int c_trans, int64_t ldc) {
+  return gemm(ctx, prec, M, N, K, X, xdt, ldx, A, adt, lda, C, c_f64, c_trans, ldc);
+}
+
+}  // namespace lrs
+
+extern "C" {
+
+lrs_status lrs_svd_k(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                     const double* Q, int64_t ldq, int64_t r, int32_t k, int32_t prec, double* U,
+                     int64_t ldu, double* S, void* V, int64_t ldv, double* err_est) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  if (!A || !Q || !U || !S || !V) return lrs_fail(ctx, LRS_EINVAL, "svd_k: NULL pointer");
+  if (!dtype_ok(dtype) || !prec_ok(prec)) return lrs_fail(ctx, LRS_EINVAL, "svd_k: bad dtype/prec");
+  if (m < 1 || n < 1 || r < 1 || k < 1) return lrs_fail(ctx, LRS_EINVAL, "svd_k: m=%lld n=%lld r=%lld k=%d", (long long)m, (long long)n, (long long)r, k);
+  if (r > m) return lrs_fail(ctx, LRS_EINVAL, "svd_k: r=%lld > m=%lld", (long long)r, (long long)m);
+  const int64_t kk = k < r ? k : r;
+  if (lda < n || ldq < r || ldu < kk || ldv < kk) return lrs_fail(ctx, LRS_EINVAL, "svd_k: strides too small");
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const int f64 = prec == LRS_PREC_FP64;
+  const size_t bsz = f64 ? 8 : 4;
+  size_t need = align256(bsz * (size_t)(r * n)) + 256 + svd_from_b_ws(r, n, m, kk, prec, ctx->num_sms);
+  if (prec >= LRS_PREC_SPLIT_BF16)
+    need += gemm_tc_workspace(r, m, prec) + gemm_tc_splitk_workspace(r, n, m, ctx->num_sms) + 4096;
+  lrs_status st = ws_reserve(ctx, need);
+  if (st) return st;
+  void* B = ws_alloc(ctx, bsz * (size_t)(r * n));
+  double* fro2 = (double*)ws_alloc(ctx, 8);
+  if (!B || !fro2) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd_k)");
+  // (a4) B = Q^T A_f -- the one full read of A_f (||A_f||_F^2 fused on the tensor-core path)
+  GemmArgs ga{r, n, m, Q, LRS_F64, ldq, A, dtype, lda, B, f64, 0, n, 1.0};
+  const size_t mark = ctx->ws_top;
+  if (prec >= LRS_PREC_SPLIT_BF16 && (r <= 128 || apass_eligible(ga, prec))) {
+    st = launch_gemm_tc(ctx, ga, prec, fro2);
+    if (st) return st;
+  } else {
+    st = gemm(ctx, prec, r, n, m, Q, LRS_F64, ldq, A, dtype, lda, B, f64, 0, n);
+    if (st) return st;
+    st = launch_fro2(ctx, A, dtype, m, n, lda, fro2);
+    if (st) return st;
+  }
+  ctx->ws_top = mark;
+  st = svd_from_b(ctx, B, r, n, Q, ldq, m, k, prec, U, ldu, S, V, ldv, fro2, err_est);
+  if (st) return st;
   return r < k ? lrs_fail(ctx, LRS_ERANK, "svd_k: rank r=%lld < k=%d", (long long)r, k) : LRS_OK;
 }
 

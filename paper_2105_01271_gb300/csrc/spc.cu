@@ -277,9 +277,63 @@ size_t eig_smem(int n) { return sizeof(double) * ((size_t)n * (size_t)(n + 1) + 
 
 bool spc_dtype_ok(int32_t dt) { return dt == LRS_F64 || dt == LRS_F32 || dt == LRS_BF16; }
 
+// eps_hat[i] = cf * lambda_max(B_f B_f^T - taus[i] B_c B_c^T) for kept rows
+// B_f (mc x n, storage dt, row stride ldb) and B_c (mc x l FP64, row stride ldc)
+lrs_status spc_err_rows(lrs_ctx* ctx, const void* Bf, int32_t dtype, int64_t mc, int64_t n, int64_t ldb,
+                        const double* Bc, int64_t l, int64_t ldc, double cf, const double* taus, int32_t ntau,
+                        double* eps_hat) {
+  if (ntau < 1 || ntau > 65535) return lrs_fail(ctx, LRS_EINVAL, "spc_err: %d taus", ntau);
+  if (mc < 1 || mc > kEigMax)
+    return lrs_fail(ctx, LRS_EINVAL, "spc_err: m_c = %lld kept rows outside [1, %d]", (long long)mc, kEigMax);
+  for (int32_t i = 0; i < ntau; ++i)
+    if (!(taus[i] >= 0.0) || !isfinite(taus[i])) return lrs_fail(ctx, LRS_EINVAL, "spc_err: tau[%d] = %g", i, taus[i]);
+  const size_t gram_ws = dtype == LRS_F32 ? gram_df_ws(mc, ctx->num_sms) : row_gram_ws(mc, ctx->num_sms);
+  const size_t need = 2 * 8 * (size_t)(mc * mc) + 16 * (size_t)ntau + 4 * (size_t)ntau + gram_ws +
+                      row_gram_ws(mc, ctx->num_sms) + 8192;
+  lrs_status st = ws_reserve(ctx, need);
+  if (st) return st;
+  double* Gf = (double*)ws_alloc(ctx, 8 * (size_t)(mc * mc));
+  double* Gc = (double*)ws_alloc(ctx, 8 * (size_t)(mc * mc));
+  double* dtau = (double*)ws_alloc(ctx, 8 * (size_t)ntau);
+  double* dout = (double*)ws_alloc(ctx, 8 * (size_t)ntau);
+  if (!Gf || !Gc || !dtau || !dout) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (spc_err)");
+  const size_t mark = ctx->ws_top;
+  if (dtype == LRS_F32) st = launch_gram_df(ctx, (const float*)Bf, mc, n, ldb, Gf);
+  else st = row_gram(ctx, Bf, dtype, mc, n, ldb, Gf);
+  if (st) return st;
+  ctx->ws_top = mark;
+  st = row_gram(ctx, Bc, LRS_F64, mc, l, ldc, Gc);
+  if (st) return st;
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(dtau, taus, 8 * (size_t)ntau, cudaMemcpyHostToDevice, ctx->stream));
+  const size_t smem = eig_smem((int)mc);
+  if (smem > 48 * 1024) {
+    st = raise_dyn_smem(ctx, (const void*)k_eig_max, smem);
+    if (st) return st;
+  }
+  k_eig_max<<<(unsigned)ntau, 256, smem, ctx->stream>>>(Gf, Gc, (int)mc, dtau, cf, dout);
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(eps_hat, dout, 8 * (size_t)ntau, cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return LRS_OK;
+}
+
 constexpr int64_t kSketchSvdDirs = 112;   // the FP64 Jacobi tile of lrs_svd_k holds r <= 112
 
 }  // namespace
+
+lrs_status spc_small_gemm(lrs_ctx* ctx, int64_t M, int64_t N, int64_t K, const double* A, int64_t a_si, int64_t a_st,
+                          const double* B, int64_t b_st, int64_t b_sj, const int32_t* cols, const double* div,
+                          double* C, int64_t ldc) {
+  return small_gemm(ctx, M, N, K, A, a_si, a_st, B, b_st, b_sj, cols, div, C, ldc);
+}
+
+lrs_status spc_err_from_rows(lrs_ctx* ctx, const void* Bf, int32_t dtype, int64_t mc, int64_t n, int64_t ldb,
+                             const double* Bc, int64_t l, int64_t ldc, double cf, const double* taus, int32_t ntau,
+                             double* eps_hat) {
+  return spc_err_rows(ctx, Bf, dtype, mc, n, ldb, Bc, l, ldc, cf, taus, ntau, eps_hat);
+}
+
 }  // namespace lrs
 
 using namespace lrs;
@@ -391,47 +445,14 @@ lrs_status lrs_spc_err(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, in
   ctx->err[0] = 0;
   if (!A || !Y || !taus || !eps_hat) return lrs_fail(ctx, LRS_EINVAL, "spc_err: NULL pointer");
   if (!spc_dtype_ok(dtype)) return lrs_fail(ctx, LRS_EINVAL, "spc_err: bad dtype");
-  if (m < 1 || n < 1 || l < 1 || c < 1 || ntau < 1 || ntau > 65535)
-    return lrs_fail(ctx, LRS_EINVAL, "spc_err: bad sizes");
-  const int64_t mc = m / c;
-  if (mc < 1 || mc > kEigMax)
-    return lrs_fail(ctx, LRS_EINVAL, "spc_err: m_c = m / c = %lld outside [1, %d]", (long long)mc, kEigMax);
+  if (m < 1 || n < 1 || l < 1 || c < 1) return lrs_fail(ctx, LRS_EINVAL, "spc_err: bad sizes");
   if (lda < n || ldy < l) return lrs_fail(ctx, LRS_EINVAL, "spc_err: strides too small");
-  for (int32_t i = 0; i < ntau; ++i)
-    if (!(taus[i] >= 0.0) || !isfinite(taus[i])) return lrs_fail(ctx, LRS_EINVAL, "spc_err: tau[%d] = %g", i, taus[i]);
   LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-  const size_t gram_ws = dtype == LRS_F32 ? gram_df_ws(mc, ctx->num_sms) : row_gram_ws(mc, ctx->num_sms);
-  const size_t need = 2 * 8 * (size_t)(mc * mc) + 16 * (size_t)ntau + 4 * (size_t)ntau + gram_ws +
-                      row_gram_ws(mc, ctx->num_sms) + 8192;
-  lrs_status st = ws_reserve(ctx, need);
-  if (st) return st;
-  double* Gf = (double*)ws_alloc(ctx, 8 * (size_t)(mc * mc));
-  double* Gc = (double*)ws_alloc(ctx, 8 * (size_t)(mc * mc));
-  double* dtau = (double*)ws_alloc(ctx, 8 * (size_t)ntau);
-  double* dout = (double*)ws_alloc(ctx, 8 * (size_t)ntau);
-  if (!Gf || !Gc || !dtau || !dout) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (spc_err)");
   // B_f = A_f(J,:), J = c-1, 2c-1, ...: rows at stride c * lda from row c - 1
   const size_t esz = dtype == LRS_F64 ? 8 : (dtype == LRS_F32 ? 4 : 2);
   const char* Bf = (const char*)A + (size_t)(c - 1) * (size_t)lda * esz;
-  const size_t mark = ctx->ws_top;
-  if (dtype == LRS_F32) st = launch_gram_df(ctx, (const float*)Bf, mc, n, (int64_t)c * lda, Gf);
-  else st = row_gram(ctx, Bf, dtype, mc, n, (int64_t)c * lda, Gf);
-  if (st) return st;
-  ctx->ws_top = mark;
-  st = row_gram(ctx, Y + (size_t)(c - 1) * (size_t)ldy, LRS_F64, mc, l, (int64_t)c * ldy, Gc);
-  if (st) return st;
-  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(dtau, taus, 8 * (size_t)ntau, cudaMemcpyHostToDevice, ctx->stream));
-  const size_t smem = eig_smem((int)mc);
-  if (smem > 48 * 1024) {
-    st = raise_dyn_smem(ctx, (const void*)k_eig_max, smem);
-    if (st) return st;
-  }
-  k_eig_max<<<(unsigned)ntau, 256, smem, ctx->stream>>>(Gf, Gc, (int)mc, dtau, (double)c, dout);
-  ctx->launches++;
-  LRS_CUDA_TRY(ctx, cudaGetLastError());
-  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(eps_hat, dout, 8 * (size_t)ntau, cudaMemcpyDeviceToHost, ctx->stream));
-  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-  return LRS_OK;
+  return spc_err_rows(ctx, Bf, dtype, m / c, n, (int64_t)c * lda, Y + (size_t)(c - 1) * (size_t)ldy, l,
+                      (int64_t)c * ldy, (double)c, taus, ntau, eps_hat);
 }
 
 }  // extern "C"
