@@ -116,7 +116,7 @@ class _DeviceArray:
     """A view of raw device memory for torch (the CUDA array interface)."""
 
     def __init__(self, ptr, shape):
-        self.__cuda_array_interface__ = {"shape": shape, "typestr": "<f8", "data": (int(ptr), True),
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": "<f8", "data": (int(ptr), False),
                                          "version": 3, "strides": None}
 
 
