@@ -61,6 +61,7 @@ def parse():
 
 BATCH_WORKLOAD = "batch256_mixed_f32"
 SPC_WORKLOAD = "spc_blob2d_m2000_512x512_f32"
+STREAM_WORKLOAD = "spcstream_blob2d_m2000_512x512_f32"
 
 
 def workload_params(name):
@@ -459,6 +460,129 @@ def run_spc_bench(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def run_stream_bench(args, rank, world):
+    """Single-read SPC over streamed snapshots on the 2000 x 512^2 FP32 blob
+    field: row blocks of 250 snapshots pushed through lrs_spc_stream (sketch
+    rows + H^T += A_c^T a_f, split-BF16 products, every 16th row kept), then
+    SPC-SVD (Alg. 3; r = 60, k = 50), SPC-ID (Alg. 5) and SPC-ID-ERR (Alg. 6;
+    16 taus).  value: the rows pushed from device memory (resident input);
+    e2e: the same rows pushed from pinned host memory (copies overlapped with
+    the H^T products by the stream's staging slots)."""
+    import torch
+    import synth
+    from paper_2105_01271_gb300 import binding
+
+    w = synth.WORKLOADS["blob2d_m2000_512x512_f32"]
+    k, r, c, block = 50, 60, 16, 250
+    taus = [float(t) for t in np.geomspace(1e-1, 1e4, 16)]
+    prec = binding.LRS_PREC_SPLIT_BF16
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    A_h = torch.from_numpy(synth.make_workload(w, seed_offset=rank)).pin_memory()
+    m, n, l = w.m, w.n, w.grid.l
+    stream = torch.cuda.Stream(dev)
+    ctx = binding.Context(dev, stream)
+    A_d = torch.empty(A_h.shape, dtype=torch.float32, device=f"cuda:{dev}")
+    A_d.copy_(A_h)
+    torch.cuda.synchronize(dev)
+    st = binding.SpcStream(ctx, binding.LRS_F32, m, binding.grid_of(w.grid), block, c, prec)
+    U = torch.empty((m, k), dtype=torch.float64, device=A_d.device)
+    S = torch.empty((k,), dtype=torch.float64, device=A_d.device)
+    V = torch.empty((n, k), dtype=torch.float32, device=A_d.device)
+    J = torch.empty((k,), dtype=torch.int32, device=A_d.device)
+    P = torch.empty((m, k), dtype=torch.float64, device=A_d.device)
+    Sf = torch.empty((k, n), dtype=torch.float32, device=A_d.device)
+
+    def step(src, on_device):
+        st.reset()
+        for r0 in range(0, m, block):
+            b = min(block, m - r0)
+            st.push(src.data_ptr() + r0 * n * 4, b, n, on_device)
+        e1 = st.svd(1e-12, r, k, U, k, S, V, k)
+        st.id(1e-12, r, k, J, P, k, Sf, n)
+        eps = st.err(taus)
+        return e1, eps
+
+    clk = clocks_start(dev)
+    for _ in range(args.warmup):
+        step(A_d, True)
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    barrier()
+    mark = clocks_mark(clk)
+    l0 = ctx.launches
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        err_svd, eps = step(A_d, True)
+    ev1.record(stream)
+    barrier()
+    clocks = clocks_stop(clk, mark)
+    launches = (ctx.launches - l0) // max(args.steps, 1)
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, f"cuda:{dev}")
+
+    # the pushes alone (the one read of A_f: sketch rows + H^T products)
+    st.reset()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for r0 in range(0, m, block):
+        st.push(A_d.data_ptr() + r0 * n * 4, min(block, m - r0), n, True)
+    p1.record(stream)
+    torch.cuda.synchronize(dev)
+    push_ms = p0.elapsed_time(p1)
+    st.svd(1e-12, r, k, U, k, S, V, k)
+
+    # end to end from pinned host memory
+    for _ in range(1):
+        step(A_h, False)
+    barrier()
+    t0 = time.perf_counter()
+    reps = max(1, min(args.steps, 3))
+    for _ in range(reps):
+        step(A_h, False)
+        Sf_h = Sf.cpu()
+    barrier()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / reps, world, f"cuda:{dev}")
+    if rank != 0:
+        return
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    bf16_peak = peaks.get("bf16_tflops_sustained", 1697.6)
+    # H^T products: 2 l n m flops per BF16 piece product, 3 piece products (split-BF16: hi*hi, hi*lo, lo*hi)
+    flops = 2.0 * l * n * m * 3
+    tfl = flops / (push_ms * 1e-3) / 1e12
+    out = {"metric": METRIC, "value": job_throughput(world, ms), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": STREAM_WORKLOAD, "m": m, "n": n, "grid": "512x512",
+                      "sketch": f"fullweight s=16 (l={l})", "block_rows": block, "k": k, "r": r, "err_c": c,
+                      "taus": len(taus), "prec": "split_bf16", "storage": "f32",
+                      "l2": "inputs larger than L2, no flush"},
+           "roofline": {"bound": "tensor", "achieved": tfl, "peak": bf16_peak, "unit": "TFLOP/s",
+                        "frac": tfl / bf16_peak,
+                        "peak_source": "measured sustained bf16 (MEASURED_PEAKS.json bf16_tflops_sustained)"
+                        if "bf16_tflops_sustained" in peaks else "fallback 1697.6 (sustained)",
+                        "kernel": "the pushes: sketch rows + H^T += A_c^T a_f (k_gemm_tc, accumulate epilogue)",
+                        "traffic": None, "algorithmic_flops": flops, "ms": push_ms,
+                        "ms_covers": "all pushes of one matrix from device memory (8 blocks of 250 rows)"},
+           "clocks": clocks, "gpu_launches": launches,
+           "e2e": {"value": job_throughput(world, e2e_ms), "unit": UNIT,
+                   "h2d_bytes_per_step": int(A_h.numel() * 4), "d2h_bytes_per_step": int(Sf.numel() * 4)},
+           "result": {"err_est_svd": err_svd, "eps_hat_min": min(eps)}}
+    print(json.dumps(out), flush=True)
+    st.close()
+
+
 def spc_cpu_baseline(w, k, r_lift, c, taus):
     import oracle
     import oracle.spc as spc
@@ -718,6 +842,8 @@ def main():
         run_batch_bench(args, rank, world)
     elif args.workload == SPC_WORKLOAD:
         run_spc_bench(args, rank, world)
+    elif args.workload == STREAM_WORKLOAD:
+        run_stream_bench(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1 and args.impl == "ours":

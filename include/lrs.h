@@ -261,6 +261,8 @@ lrs_status lrs_spc_err(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, in
  *   lrs_spc_stream_err     SPC-ID-ERR (Alg. 6) on the kept rows: as
  *       lrs_spc_err with c = err_c (host taus / eps_hat).
  *   lrs_spc_stream_sketch  A_c (device, m x l FP64, row stride l).
+ *   lrs_spc_stream_reset   start a new matrix of the same shape in the same
+ *       buffers (waits for the stream's queued work).
  */
 typedef struct lrs_spc_stream lrs_spc_stream;
 lrs_status lrs_spc_stream_create(lrs_ctx* ctx, int32_t dtype, int64_t m, const lrs_grid* sketch, int64_t block_rows,
@@ -272,6 +274,7 @@ lrs_status lrs_spc_stream_id(lrs_spc_stream* s, double rtol, int32_t r, int32_t 
                              void* Sf, int64_t ldsf, double* err_est);
 lrs_status lrs_spc_stream_err(lrs_spc_stream* s, const double* taus, int32_t ntau, double* eps_hat);
 const double* lrs_spc_stream_sketch(const lrs_spc_stream* s);
+lrs_status lrs_spc_stream_reset(lrs_spc_stream* s);
 void lrs_spc_stream_destroy(lrs_spc_stream* s);
 
 /*

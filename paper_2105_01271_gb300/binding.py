@@ -116,6 +116,7 @@ _SIG = {
     "lrs_spc_stream_err": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_double)]),
     "lrs_spc_stream_sketch": (C.c_void_p, [C.c_void_p]),
     "lrs_spc_stream_destroy": (None, [C.c_void_p]),
+    "lrs_spc_stream_reset": (C.c_int, [C.c_void_p]),
     "lrs_mlp_param_count": (C.c_int64, []),
     "lrs_mlp_init_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "lrs_mlp_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
@@ -323,6 +324,9 @@ class SpcStream:
 
     def sketch_ptr(self) -> int:
         return int(self.lib.lrs_spc_stream_sketch(self.h) or 0)
+
+    def reset(self):
+        return self.ctx._check(self.lib.lrs_spc_stream_reset(self.h))
 
     def close(self):
         if getattr(self, "h", None):

@@ -156,6 +156,18 @@ lrs_status lrs_spc_stream_create(lrs_ctx* ctx, int32_t dtype, int64_t m, const l
 
 void lrs_spc_stream_destroy(lrs_spc_stream* s) { destroy(s); }
 
+lrs_status lrs_spc_stream_reset(lrs_spc_stream* s) {
+  if (!s) return LRS_EINVAL;
+  // queued work on the old rows may still read the staging buffers: wait for it
+  LRS_CUDA_TRY(s->ctx, cudaStreamSynchronize(s->ctx->stream));
+  LRS_CUDA_TRY(s->ctx, cudaStreamSynchronize(s->copy));
+  s->pushed = 0;
+  s->blocks = 0;
+  s->svd_r = 0;
+  s->slot = 0;
+  return LRS_OK;
+}
+
 const double* lrs_spc_stream_sketch(const lrs_spc_stream* s) { return s ? s->Ac : nullptr; }
 
 lrs_status lrs_spc_stream_push(lrs_spc_stream* s, const void* rows, int64_t nrows, int64_t ld, int32_t on_device) {
