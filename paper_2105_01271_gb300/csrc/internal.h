@@ -172,6 +172,8 @@ lrs_status launch_tsqr(lrs_ctx* ctx, const void* B, int b_f64, int64_t r, int64_
 // one-sided Jacobi on the columns of R (r x r): R V = U_R diag(s); returns
 // V (r x r, row-major) and s (r), sorted descending.
 lrs_status launch_jacobi(lrs_ctx* ctx, double* R, int64_t r, double* V, double* s, int fp64);
+// workspace of launch_jacobi's multi-SM FP64 form (it falls back to one block without it)
+size_t jacobi_ws(int64_t r);
 
 // misc.cu -------------------------------------------------------------------------
 // transposed copy of a row-major FP64 matrix: dst (cols x rows) = src^T

@@ -427,7 +427,7 @@ namespace lrs {
 size_t svd_from_b_ws(int64_t r, int64_t n, int64_t m, int64_t kk, int32_t prec, int num_sms) {
   const size_t bsz = prec == LRS_PREC_FP64 ? 8 : 4;
   size_t need = tsqr_ws(r, n, bsz) + r_of_bt_gram_ws(r, num_sms);
-  need += 4 * align256(8 * (size_t)(r * r)) + align256(8 * (size_t)(m * r)) + 65536;
+  need += 4 * align256(8 * (size_t)(r * r)) + align256(8 * (size_t)(m * r)) + jacobi_ws(r) + 65536;
   if (prec >= LRS_PREC_SPLIT_BF16) need += gemm_tc_workspace(kk, r, LRS_PREC_BF16X3) + 4096;
   return need;
 }

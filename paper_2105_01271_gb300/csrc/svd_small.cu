@@ -227,8 +227,145 @@ k_jacobi(const double* __restrict__ R, int64_t r, double* __restrict__ Vout, dou
   for (int64_t k = threadIdx.x; k < r; k += blockDim.x) s_out[k] = s_norm[order[k]];
 }
 
+// ---------------------------------------------------------------------------
+// FP64 one-sided Jacobi across the GPU: the pairs of one round-robin round
+// are spread over up to one block (one warp) per SM, with a grid barrier
+// between rounds.  On GB300 the FP64 pipe of one SM retires one warp-wide
+// DFMA every 16 cycles, so the one-block kernel above spends ~50 us per round
+// at r = 112; here each SM works on one pair per round.  The columns live in
+// global memory (L2-resident: 2 r^2 doubles) and are read with ld.global.cg,
+// since another SM may have rotated them in the previous round.
+// ---------------------------------------------------------------------------
+struct JacobiCoop {
+  double* W;       // rp columns of length r (column c at c * r)
+  double* Vc;      // rp columns of length r, starts as I
+  const double* R; // r x r row-major input
+  int64_t r, rp;
+  int max_sweeps;
+  int* rot;        // rotations per sweep (max_sweeps counters, zeroed)
+  int* sweeps;     // sweeps taken
+  GridBarrier bar;
+};
+
+__global__ void __launch_bounds__(32) k_jacobi_coop(JacobiCoop J) {
+  const int lane = threadIdx.x;
+  const int64_t r = J.r, rp = J.rp;
+  for (int64_t e = (int64_t)blockIdx.x * 32 + lane; e < rp * r; e += (int64_t)gridDim.x * 32) {
+    const int64_t c = e / r, i = e - c * r;
+    J.W[e] = c < r ? J.R[i * r + c] : 0.0;
+    J.Vc[e] = (c == i && c < r) ? 1.0 : 0.0;
+  }
+  if (!grid_sync(J.bar)) return;
+  const double eps = 1.1102230246251565e-16;
+  const double tol = eps * (double)(r > 16 ? r : 16);        // as the one-block kernel
+  const double tol2 = tol * tol;
+  int sweep = 0;
+  for (; sweep < J.max_sweeps; ++sweep) {
+    for (int64_t round = 0; round < rp - 1; ++round) {
+      for (int64_t pr = blockIdx.x; pr < rp / 2; pr += gridDim.x) {
+        const int64_t sa = pr, sb = rp - 1 - pr;
+        int64_t p = sa == 0 ? 0 : 1 + ((sa - 1 + round) % (rp - 1));
+        int64_t q = 1 + ((sb - 1 + round) % (rp - 1));
+        if (p > q) { const int64_t t = p; p = q; q = t; }
+        if (q >= r) continue;                                  // the zero pad column
+        double* wp = J.W + p * r;
+        double* wq = J.W + q * r;
+        double a = 0.0, b = 0.0, g = 0.0;
+        for (int64_t i = lane; i < r; i += 32) {
+          const double x = __ldcg(wp + i), y = __ldcg(wq + i);
+          a = fma(x, x, a); b = fma(y, y, b); g = fma(x, y, g);
+        }
+        a = warp_sum(a); b = warp_sum(b); g = warp_sum(g);
+        if (g == 0.0 || g * g <= tol2 * (a * b)) continue;
+        const double zeta = (b - a) / (2.0 * g);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / sqrt(1.0 + t * t);
+        const double sn = cs * t;
+        double* vp = J.Vc + p * r;
+        double* vq = J.Vc + q * r;
+        for (int64_t i = lane; i < r; i += 32) {
+          const double x = __ldcg(wp + i), y = __ldcg(wq + i);
+          wp[i] = cs * x - sn * y;
+          wq[i] = sn * x + cs * y;
+          const double u = __ldcg(vp + i), w = __ldcg(vq + i);
+          vp[i] = cs * u - sn * w;
+          vq[i] = sn * u + cs * w;
+        }
+        if (lane == 0) atomicAdd(J.rot + sweep, 1);
+      }
+      if (!grid_sync(J.bar)) return;
+    }
+    // the barrier above orders every count of this sweep before this read
+    if (ld_volatile_s32(J.rot + sweep) == 0) break;
+  }
+  if (blockIdx.x == 0 && lane == 0) *J.sweeps = sweep;
+}
+
+// singular values (column norms of W), descending with ties by index, and V
+__global__ void __launch_bounds__(1024) k_jacobi_finish(const double* __restrict__ W, const double* __restrict__ Vc,
+                                                        int64_t r, double* __restrict__ Vout,
+                                                        double* __restrict__ s_out) {
+  __shared__ double s_norm[1024];
+  __shared__ int order[1024];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t c = wid; c < r; c += nw) {
+    double a = 0.0;
+    for (int64_t i = lane; i < r; i += 32) a = fma(W[c * r + i], W[c * r + i], a);
+    a = warp_sum(a);
+    if (lane == 0) s_norm[c] = sqrt(a);
+  }
+  __syncthreads();
+  for (int64_t c = threadIdx.x; c < r; c += blockDim.x) {
+    int64_t rank = 0;
+    const double v = s_norm[c];
+    for (int64_t d = 0; d < r; ++d) {
+      const double u = s_norm[d];
+      if (u > v || (u == v && d < c)) ++rank;
+    }
+    order[rank] = (int)c;
+  }
+  __syncthreads();
+  for (int64_t e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const int64_t i = e / r, k = e - i * r;
+    Vout[i * r + k] = Vc[(int64_t)order[k] * r + i];
+  }
+  for (int64_t k = threadIdx.x; k < r; k += blockDim.x) s_out[k] = s_norm[order[k]];
+}
+
+size_t jacobi_ws(int64_t r) {
+  const int64_t rp = (r + 1) & ~int64_t(1);
+  return 2 * ((sizeof(double) * (size_t)(rp * r) + 255) & ~size_t(255)) + 1024;
+}
+
 lrs_status launch_jacobi(lrs_ctx* ctx, double* R, int64_t r, double* V, double* s, int fp64) {
   const int64_t rp = (r + 1) & ~int64_t(1);
+  if (fp64 && ctx->coop_ok && r >= 24 && r <= 1024) {
+    JacobiCoop J{};
+    J.r = r; J.rp = rp; J.R = R; J.max_sweeps = 40;
+    J.W = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(rp * r));
+    J.Vc = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(rp * r));
+    unsigned* scratch = (unsigned*)ws_alloc(ctx, 512);
+    if (J.W && J.Vc && scratch) {
+      LRS_CUDA_TRY(ctx, cudaMemsetAsync(scratch, 0, 512, ctx->stream));
+      J.bar.count = scratch; J.bar.gen = scratch + 1; J.bar.err = (int*)(scratch + 2);
+      J.sweeps = (int*)(scratch + 3);
+      J.rot = (int*)(scratch + 4);                       // 40 counters
+      int64_t nb = rp / 2;
+      if (nb > ctx->num_sms) nb = ctx->num_sms;
+      void* args[] = {&J};
+      LRS_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)k_jacobi_coop, dim3((unsigned)nb), dim3(32), args, 0,
+                                                    ctx->stream));
+      k_jacobi_finish<<<1, 1024, 0, ctx->stream>>>(J.W, J.Vc, r, V, s);
+      ctx->launches += 2;
+      LRS_CUDA_TRY(ctx, cudaGetLastError());
+      int* h = (int*)ctx->host_scratch;
+      LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 48, J.bar.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+      LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+      if (h[48] != 0) return lrs_fail(ctx, LRS_ETIMEOUT, "svd: Jacobi grid barrier wait gave up");
+      return LRS_OK;
+    }
+    // no room in the workspace: the one-block kernel below
+  }
   const size_t tsz = fp64 ? 8 : 4;
   const size_t dyn = tsz * 2 * (size_t)(rp * r) + sizeof(int) * (size_t)rp + 64;
   if (dyn > kSmemCap || r > 1024)
