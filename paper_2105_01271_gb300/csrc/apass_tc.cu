@@ -70,6 +70,7 @@ struct ApParams {
   int nacc;                   // accumulator buffers (1 or 2)
   int stacked;                // 1: X pieces stacked along UMMA N (one MMA per data piece)
   void* C; int c_f64; int c_trans; int vec_ok; int64_t ldc; double alpha;
+  int accum;                // C += alpha X^T A instead of C = alpha X^T A
   int* err;
   double* fro2_part;          // per-CTA partial ||A||_F^2 or nullptr
 };
@@ -187,33 +188,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_apass(const __grid_constant__ C
               double* dst = reinterpret_cast<double*>(P.C) + n * P.ldc + c0;
 #pragma unroll
               for (int e = 0; e < 16; ++e)
-                if (e < lim) dst[e] = P.alpha * (double)__uint_as_float(v[e]);
+                if (e < lim) dst[e] = (P.accum ? dst[e] : 0.0) + P.alpha * (double)__uint_as_float(v[e]);
             } else {
               float* dst = reinterpret_cast<float*>(P.C) + n * P.ldc + c0;
               const float fa = (float)P.alpha;
               if (lim == 16 && P.vec_ok) {
 #pragma unroll
-                for (int e = 0; e < 16; e += 4)
-                  *reinterpret_cast<float4*>(dst + e) =
-                      make_float4(fa * __uint_as_float(v[e]), fa * __uint_as_float(v[e + 1]),
-                                  fa * __uint_as_float(v[e + 2]), fa * __uint_as_float(v[e + 3]));
+                for (int e = 0; e < 16; e += 4) {
+                  float4 o = P.accum ? *reinterpret_cast<const float4*>(dst + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+                  o.x += fa * __uint_as_float(v[e]);
+                  o.y += fa * __uint_as_float(v[e + 1]);
+                  o.z += fa * __uint_as_float(v[e + 2]);
+                  o.w += fa * __uint_as_float(v[e + 3]);
+                  *reinterpret_cast<float4*>(dst + e) = o;
+                }
               } else {
 #pragma unroll
                 for (int e = 0; e < 16; ++e)
-                  if (e < lim) dst[e] = fa * __uint_as_float(v[e]);
+                  if (e < lim) dst[e] = (P.accum ? dst[e] : 0.f) + fa * __uint_as_float(v[e]);
               }
             }
           } else if (P.c_f64) {
 #pragma unroll
             for (int e = 0; e < 16; ++e)
-              if (c0 + e < P.M)
-                reinterpret_cast<double*>(P.C)[(c0 + e) * P.ldc + n] = P.alpha * (double)__uint_as_float(v[e]);
+              if (c0 + e < P.M) {
+                double* c = reinterpret_cast<double*>(P.C) + (c0 + e) * P.ldc + n;
+                *c = (P.accum ? *c : 0.0) + P.alpha * (double)__uint_as_float(v[e]);
+              }
           } else {
             // FP32 output: no FP64 arithmetic (the FP64 pipe is narrow)
             const float fa = (float)P.alpha;
 #pragma unroll
             for (int e = 0; e < 16; ++e)
-              if (c0 + e < P.M) reinterpret_cast<float*>(P.C)[(c0 + e) * P.ldc + n] = fa * __uint_as_float(v[e]);
+              if (c0 + e < P.M) {
+                float* c = reinterpret_cast<float*>(P.C) + (c0 + e) * P.ldc + n;
+                *c = (P.accum ? *c : 0.f) + fa * __uint_as_float(v[e]);
+              }
           }
         }
       }
@@ -488,7 +498,7 @@ lrs_status run_apass(lrs_ctx* ctx, const GemmArgs& a, double* fro2_out) {
   P.rN = cfg.rN; P.RS = cfg.RS; P.PS = cfg.PS;
   P.raw_bytes = cfg.raw_bytes; P.stage_bytes = cfg.stage_bytes;
   P.acc_cols = cfg.acc_cols; P.tmem_cols = cfg.tmem_cols; P.nacc = cfg.nacc; P.stacked = cfg.stacked;
-  P.C = a.C; P.c_f64 = a.c_f64; P.c_trans = a.c_trans; P.ldc = a.ldc; P.alpha = a.alpha;
+  P.C = a.C; P.c_f64 = a.c_f64; P.c_trans = a.c_trans; P.ldc = a.ldc; P.alpha = a.alpha; P.accum = a.accum;
   P.vec_ok = ((reinterpret_cast<uintptr_t>(a.C) & 15u) == 0 && (a.ldc & 3) == 0) ? 1 : 0;
 
   const size_t xbytes = (size_t)P.Kt * SX * cfg.rN * 128;
@@ -533,7 +543,6 @@ lrs_status run_apass(lrs_ctx* ctx, const GemmArgs& a, double* fro2_out) {
 
 bool apass_eligible(const GemmArgs& a, int prec) {
   if (prec != LRS_PREC_SPLIT_BF16 && prec != LRS_PREC_BF16X3) return false;
-  if (a.accum) return false;                       // the epilogue overwrites C
   if (a.adt != LRS_F32 && a.adt != LRS_BF16) return false;
   if (a.M < 1 || a.M > kMaxR || a.N < TN || a.K < 1) return false;
   if (a.N >= (int64_t)1 << 31 || a.K >= (int64_t)1 << 31) return false;

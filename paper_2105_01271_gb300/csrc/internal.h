@@ -73,7 +73,7 @@ struct GemmArgs {
   const void* A; int32_t adt; int64_t lda;
   void* C; int c_f64; int c_trans; int64_t ldc;
   double alpha;            // C = alpha * X^T A
-  int accum = 0;           // 1: C += alpha * X^T A (CUDA-core and k_gemm_tc paths; never the TMA A-pass)
+  int accum = 0;           // 1: C += alpha * X^T A
 };
 lrs_status launch_gemm_simt(lrs_ctx* ctx, const GemmArgs& a, int fp64);
 // lrs_api.cu: the precision dispatch of every product (FP64 / FP32 CUDA cores, tensor-core forms)

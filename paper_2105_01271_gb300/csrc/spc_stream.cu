@@ -46,6 +46,7 @@ namespace lrs {
 namespace {
 
 constexpr int32_t kStreamMaxR = 112;
+constexpr int64_t kHtSlab = 256;        // rows of H^T per tensor-core product (the TMA A-pass holds <= 256)
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -181,8 +182,9 @@ lrs_status lrs_spc_stream_push(lrs_spc_stream* s, const void* rows, int64_t nrow
   LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   const bool tc = s->prec >= LRS_PREC_SPLIT_BF16;
   const int hf64 = s->prec == LRS_PREC_FP64;
-  const size_t need = (tc ? gemm_tc_workspace(s->l, s->block_rows, s->prec) +
-                                gemm_tc_splitk_workspace(s->l, s->n, s->block_rows, ctx->num_sms)
+  const int64_t ml = s->l < kHtSlab ? s->l : kHtSlab;
+  const size_t need = (tc ? gemm_tc_workspace(ml, s->block_rows, s->prec) +
+                                gemm_tc_splitk_workspace(ml, s->n, s->block_rows, ctx->num_sms)
                           : 0) + 65536;
   lrs_status st = ws_reserve(ctx, need);
   if (st) return st;
@@ -211,14 +213,25 @@ lrs_status lrs_spc_stream_push(lrs_spc_stream* s, const void* rows, int64_t nrow
     // the sketch rows, then H^T += A_c(rows,:)^T a_f, then ||a_f||^2
     st = launch_sketch(ctx, blk, s->dtype, b, ldb, s->grid, s->Ac + (size_t)r0 * (size_t)s->l, s->l);
     if (st) return st;
-    GemmArgs ga{s->l, s->n, b, s->Ac + (size_t)r0 * (size_t)s->l, LRS_F64, s->l, blk, s->dtype, ldb,
-                s->Ht, hf64, 0, s->n, 1.0, r0 > 0 ? 1 : 0};
     const size_t mark = ctx->ws_top;
-    if (s->prec == LRS_PREC_FP64) st = launch_gemm_simt(ctx, ga, 1);
-    else if (s->prec == LRS_PREC_FP32) st = launch_gemm_simt(ctx, ga, 0);
-    else st = launch_gemm_tc(ctx, ga, s->prec);
+    if (!tc) {
+      GemmArgs ga{s->l, s->n, b, s->Ac + (size_t)r0 * (size_t)s->l, LRS_F64, s->l, blk, s->dtype, ldb,
+                  s->Ht, hf64, 0, s->n, 1.0, r0 > 0 ? 1 : 0};
+      st = launch_gemm_simt(ctx, ga, hf64);
+      if (st) return st;
+    } else {
+      // row slabs of H^T of at most kHtSlab rows: each is one TMA A-pass over the block
+      // (the block is re-read per slab, 4 b n bytes, against 8 l n bytes of H^T traffic)
+      for (int64_t j0 = 0; j0 < s->l; j0 += kHtSlab) {
+        const int64_t mj = (s->l - j0) < kHtSlab ? (s->l - j0) : kHtSlab;
+        GemmArgs ga{mj, s->n, b, s->Ac + (size_t)r0 * (size_t)s->l + j0, LRS_F64, s->l, blk, s->dtype, ldb,
+                    (float*)s->Ht + (size_t)j0 * (size_t)s->n, 0, 0, s->n, 1.0, r0 > 0 ? 1 : 0};
+        st = launch_gemm_tc(ctx, ga, s->prec);
+        ctx->ws_top = mark;
+        if (st) return st;
+      }
+    }
     ctx->ws_top = mark;
-    if (st) return st;
     st = launch_fro2(ctx, blk, s->dtype, b, s->n, ldb, s->fro2_parts + s->blocks);
     if (st) return st;
     // rows i (global) with (i + 1) % c == 0 are kept for SPC-ID-ERR
