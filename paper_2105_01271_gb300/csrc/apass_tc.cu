@@ -186,44 +186,72 @@ __global__ void __launch_bounds__(kThreads, 1) k_apass(const __grid_constant__ C
             const int lim = (int)min((int64_t)16, P.M - c0);
             if (P.c_f64) {
               double* dst = reinterpret_cast<double*>(P.C) + n * P.ldc + c0;
+              if (P.accum) {
+                double old[16];
 #pragma unroll
-              for (int e = 0; e < 16; ++e)
-                if (e < lim) dst[e] = (P.accum ? dst[e] : 0.0) + P.alpha * (double)__uint_as_float(v[e]);
-            } else {
-              float* dst = reinterpret_cast<float*>(P.C) + n * P.ldc + c0;
-              const float fa = (float)P.alpha;
-              if (lim == 16 && P.vec_ok) {
+                for (int e = 0; e < 16; ++e) old[e] = e < lim ? dst[e] : 0.0;
 #pragma unroll
-                for (int e = 0; e < 16; e += 4) {
-                  float4 o = P.accum ? *reinterpret_cast<const float4*>(dst + e) : make_float4(0.f, 0.f, 0.f, 0.f);
-                  o.x += fa * __uint_as_float(v[e]);
-                  o.y += fa * __uint_as_float(v[e + 1]);
-                  o.z += fa * __uint_as_float(v[e + 2]);
-                  o.w += fa * __uint_as_float(v[e + 3]);
-                  *reinterpret_cast<float4*>(dst + e) = o;
-                }
+                for (int e = 0; e < 16; ++e)
+                  if (e < lim) dst[e] = old[e] + P.alpha * (double)__uint_as_float(v[e]);
               } else {
 #pragma unroll
                 for (int e = 0; e < 16; ++e)
-                  if (e < lim) dst[e] = (P.accum ? dst[e] : 0.f) + fa * __uint_as_float(v[e]);
+                  if (e < lim) dst[e] = P.alpha * (double)__uint_as_float(v[e]);
+              }
+            } else {
+              float* dst = reinterpret_cast<float*>(P.C) + n * P.ldc + c0;
+              const float fa = (float)P.alpha;
+              if (P.accum) {
+                // all old values in flight before any store (a store may alias a later load)
+                float old[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) old[e] = e < lim ? dst[e] : 0.f;
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                  if (e < lim) dst[e] = old[e] + fa * __uint_as_float(v[e]);
+              } else if (lim == 16 && P.vec_ok) {
+#pragma unroll
+                for (int e = 0; e < 16; e += 4)
+                  *reinterpret_cast<float4*>(dst + e) =
+                      make_float4(fa * __uint_as_float(v[e]), fa * __uint_as_float(v[e + 1]),
+                                  fa * __uint_as_float(v[e + 2]), fa * __uint_as_float(v[e + 3]));
+              } else {
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                  if (e < lim) dst[e] = fa * __uint_as_float(v[e]);
               }
             }
           } else if (P.c_f64) {
+            double* col = reinterpret_cast<double*>(P.C) + n;
+            if (P.accum) {
+              double old[16];
 #pragma unroll
-            for (int e = 0; e < 16; ++e)
-              if (c0 + e < P.M) {
-                double* c = reinterpret_cast<double*>(P.C) + (c0 + e) * P.ldc + n;
-                *c = (P.accum ? *c : 0.0) + P.alpha * (double)__uint_as_float(v[e]);
-              }
+              for (int e = 0; e < 16; ++e) old[e] = c0 + e < P.M ? col[(c0 + e) * P.ldc] : 0.0;
+#pragma unroll
+              for (int e = 0; e < 16; ++e)
+                if (c0 + e < P.M) col[(c0 + e) * P.ldc] = old[e] + P.alpha * (double)__uint_as_float(v[e]);
+            } else {
+#pragma unroll
+              for (int e = 0; e < 16; ++e)
+                if (c0 + e < P.M) col[(c0 + e) * P.ldc] = P.alpha * (double)__uint_as_float(v[e]);
+            }
           } else {
             // FP32 output: no FP64 arithmetic (the FP64 pipe is narrow)
             const float fa = (float)P.alpha;
+            float* col = reinterpret_cast<float*>(P.C) + n;
+            if (P.accum) {
+              // all 16 old values in flight before any store (a store may alias a later load)
+              float old[16];
 #pragma unroll
-            for (int e = 0; e < 16; ++e)
-              if (c0 + e < P.M) {
-                float* c = reinterpret_cast<float*>(P.C) + (c0 + e) * P.ldc + n;
-                *c = (P.accum ? *c : 0.f) + fa * __uint_as_float(v[e]);
-              }
+              for (int e = 0; e < 16; ++e) old[e] = c0 + e < P.M ? col[(c0 + e) * P.ldc] : 0.f;
+#pragma unroll
+              for (int e = 0; e < 16; ++e)
+                if (c0 + e < P.M) col[(c0 + e) * P.ldc] = old[e] + fa * __uint_as_float(v[e]);
+            } else {
+#pragma unroll
+              for (int e = 0; e < 16; ++e)
+                if (c0 + e < P.M) col[(c0 + e) * P.ldc] = fa * __uint_as_float(v[e]);
+            }
           }
         }
       }
