@@ -424,10 +424,12 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
 
 namespace lrs {
 
+constexpr int64_t kJacobiWideMaxN = 8192;   // B^T columns longer than this take the TSQR route
+
 size_t svd_from_b_ws(int64_t r, int64_t n, int64_t m, int64_t kk, int32_t prec, int num_sms) {
   const size_t bsz = prec == LRS_PREC_FP64 ? 8 : 4;
   size_t need = tsqr_ws(r, n, bsz) + r_of_bt_gram_ws(r, num_sms);
-  need += 4 * align256(8 * (size_t)(r * r)) + align256(8 * (size_t)(m * r)) + jacobi_ws(r) + 65536;
+  need += 4 * align256(8 * (size_t)(r * r)) + align256(8 * (size_t)(m * r)) + jacobi_ws(r, n > r && n <= kJacobiWideMaxN ? n : r) + 65536;
   if (prec >= LRS_PREC_SPLIT_BF16) need += gemm_tc_workspace(kk, r, LRS_PREC_BF16X3) + 4096;
   return need;
 }
@@ -451,16 +453,29 @@ lrs_status svd_from_b(lrs_ctx* ctx, const void* B, int64_t r, int64_t n, const d
   // double-float Gram and an FP64 Cholesky (TSQR if that breaks down); FP64 B:
   // Householder TSQR.
   lrs_status st = LRS_ERANK;
-  if (!f64 && r <= 128) {
+  bool direct = false;
+  if (f64 && r >= 24 && n <= kJacobiWideMaxN) {
+    // FP64 B of moderate width: one-sided Jacobi on B^T itself across the SMs
+    // (no TSQR); the rotations are U_B
     const size_t mark = ctx->ws_top;
-    st = launch_r_of_bt_gram(ctx, (const float*)B, r, n, n, Rm);
+    st = launch_jacobi_wide(ctx, (const double*)B, r, n, n, Vr, sv);
     ctx->ws_top = mark;
     if (st != LRS_OK && st != LRS_ERANK) return st;
+    direct = st == LRS_OK;
   }
-  if (st == LRS_ERANK) st = launch_tsqr(ctx, B, f64, r, n, n, Rm);
-  if (st) return st;
-  st = launch_jacobi(ctx, Rm, r, Vr, sv, f64);
-  if (st) return st;
+  if (!direct) {
+    st = LRS_ERANK;
+    if (!f64 && r <= 128) {
+      const size_t mark = ctx->ws_top;
+      st = launch_r_of_bt_gram(ctx, (const float*)B, r, n, n, Rm);
+      ctx->ws_top = mark;
+      if (st != LRS_OK && st != LRS_ERANK) return st;
+    }
+    if (st == LRS_ERANK) st = launch_tsqr(ctx, B, f64, r, n, n, Rm);
+    if (st) return st;
+    st = launch_jacobi(ctx, Rm, r, Vr, sv, f64);
+    if (st) return st;
+  }
   // U = Q Vr(:, :kk):  U^T = Vr_k^T Q^T
   st = launch_transpose(ctx, Q, m, r, ldq, QT, m);
   if (st) return st;

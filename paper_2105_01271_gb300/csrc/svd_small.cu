@@ -237,10 +237,11 @@ k_jacobi(const double* __restrict__ R, int64_t r, double* __restrict__ Vout, dou
 // since another SM may have rotated them in the previous round.
 // ---------------------------------------------------------------------------
 struct JacobiCoop {
-  double* W;       // rp columns of length r (column c at c * r)
+  double* W;       // rp columns of length len (column c at c * len)
   double* Vc;      // rp columns of length r, starts as I
-  const double* R; // r x r row-major input
-  int64_t r, rp;
+  const double* R; // the input: r x r row-major (by_rows = 0), or r x len row-major (by_rows = 1)
+  int64_t r, rp, len, ldr;
+  int by_rows;     // 1: column c of the Jacobi matrix is row c of R (B^T of a wide B)
   int max_sweeps;
   int* rot;        // rotations per sweep (max_sweeps counters, zeroed)
   int* sweeps;     // sweeps taken
@@ -249,10 +250,13 @@ struct JacobiCoop {
 
 __global__ void __launch_bounds__(32) k_jacobi_coop(JacobiCoop J) {
   const int lane = threadIdx.x;
-  const int64_t r = J.r, rp = J.rp;
+  const int64_t r = J.r, rp = J.rp, len = J.len;
+  for (int64_t e = (int64_t)blockIdx.x * 32 + lane; e < rp * len; e += (int64_t)gridDim.x * 32) {
+    const int64_t c = e / len, i = e - c * len;
+    J.W[e] = c < r ? (J.by_rows ? J.R[c * J.ldr + i] : J.R[i * J.ldr + c]) : 0.0;
+  }
   for (int64_t e = (int64_t)blockIdx.x * 32 + lane; e < rp * r; e += (int64_t)gridDim.x * 32) {
     const int64_t c = e / r, i = e - c * r;
-    J.W[e] = c < r ? J.R[i * r + c] : 0.0;
     J.Vc[e] = (c == i && c < r) ? 1.0 : 0.0;
   }
   if (!grid_sync(J.bar)) return;
@@ -268,10 +272,10 @@ __global__ void __launch_bounds__(32) k_jacobi_coop(JacobiCoop J) {
         int64_t q = 1 + ((sb - 1 + round) % (rp - 1));
         if (p > q) { const int64_t t = p; p = q; q = t; }
         if (q >= r) continue;                                  // the zero pad column
-        double* wp = J.W + p * r;
-        double* wq = J.W + q * r;
+        double* wp = J.W + p * len;
+        double* wq = J.W + q * len;
         double a = 0.0, b = 0.0, g = 0.0;
-        for (int64_t i = lane; i < r; i += 32) {
+        for (int64_t i = lane; i < len; i += 32) {
           const double x = __ldcg(wp + i), y = __ldcg(wq + i);
           a = fma(x, x, a); b = fma(y, y, b); g = fma(x, y, g);
         }
@@ -283,10 +287,12 @@ __global__ void __launch_bounds__(32) k_jacobi_coop(JacobiCoop J) {
         const double sn = cs * t;
         double* vp = J.Vc + p * r;
         double* vq = J.Vc + q * r;
-        for (int64_t i = lane; i < r; i += 32) {
+        for (int64_t i = lane; i < len; i += 32) {
           const double x = __ldcg(wp + i), y = __ldcg(wq + i);
           wp[i] = cs * x - sn * y;
           wq[i] = sn * x + cs * y;
+        }
+        for (int64_t i = lane; i < r; i += 32) {
           const double u = __ldcg(vp + i), w = __ldcg(vq + i);
           vp[i] = cs * u - sn * w;
           vq[i] = sn * u + cs * w;
@@ -303,14 +309,14 @@ __global__ void __launch_bounds__(32) k_jacobi_coop(JacobiCoop J) {
 
 // singular values (column norms of W), descending with ties by index, and V
 __global__ void __launch_bounds__(1024) k_jacobi_finish(const double* __restrict__ W, const double* __restrict__ Vc,
-                                                        int64_t r, double* __restrict__ Vout,
+                                                        int64_t r, int64_t len, double* __restrict__ Vout,
                                                         double* __restrict__ s_out) {
   __shared__ double s_norm[1024];
   __shared__ int order[1024];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int64_t c = wid; c < r; c += nw) {
     double a = 0.0;
-    for (int64_t i = lane; i < r; i += 32) a = fma(W[c * r + i], W[c * r + i], a);
+    for (int64_t i = lane; i < len; i += 32) a = fma(W[c * len + i], W[c * len + i], a);
     a = warp_sum(a);
     if (lane == 0) s_norm[c] = sqrt(a);
   }
@@ -332,38 +338,59 @@ __global__ void __launch_bounds__(1024) k_jacobi_finish(const double* __restrict
   for (int64_t k = threadIdx.x; k < r; k += blockDim.x) s_out[k] = s_norm[order[k]];
 }
 
-size_t jacobi_ws(int64_t r) {
+size_t jacobi_ws(int64_t r, int64_t len) {
   const int64_t rp = (r + 1) & ~int64_t(1);
-  return 2 * ((sizeof(double) * (size_t)(rp * r) + 255) & ~size_t(255)) + 1024;
+  return ((sizeof(double) * (size_t)(rp * len) + 255) & ~size_t(255)) +
+         ((sizeof(double) * (size_t)(rp * r) + 255) & ~size_t(255)) + 1024;
+}
+
+// the cooperative FP64 Jacobi on the columns of R (r x r, by_rows = 0) or of
+// B^T (B r x len row-major, stride ldr, by_rows = 1); false: no workspace
+static bool jacobi_coop(lrs_ctx* ctx, const double* R, int64_t r, int64_t len, int64_t ldr, int by_rows, double* V,
+                        double* s, lrs_status* st_out) {
+  const int64_t rp = (r + 1) & ~int64_t(1);
+  JacobiCoop J{};
+  J.r = r; J.rp = rp; J.len = len; J.ldr = ldr; J.by_rows = by_rows; J.R = R; J.max_sweeps = 40;
+  J.W = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(rp * len));
+  J.Vc = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(rp * r));
+  unsigned* scratch = (unsigned*)ws_alloc(ctx, 512);
+  if (!J.W || !J.Vc || !scratch) return false;
+  *st_out = LRS_OK;
+  lrs_status& st = *st_out;
+  cudaError_t e = cudaMemsetAsync(scratch, 0, 512, ctx->stream);
+  if (e != cudaSuccess) { st = lrs_fail(ctx, LRS_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e)); return true; }
+  J.bar.count = scratch; J.bar.gen = scratch + 1; J.bar.err = (int*)(scratch + 2);
+  J.sweeps = (int*)(scratch + 3);
+  J.rot = (int*)(scratch + 4);                           // 40 counters
+  int64_t nb = rp / 2;
+  if (nb > ctx->num_sms) nb = ctx->num_sms;
+  void* args[] = {&J};
+  e = cudaLaunchCooperativeKernel((const void*)k_jacobi_coop, dim3((unsigned)nb), dim3(32), args, 0, ctx->stream);
+  if (e != cudaSuccess) { st = lrs_fail(ctx, LRS_ECUDA, "jacobi launch: %s", cudaGetErrorString(e)); return true; }
+  k_jacobi_finish<<<1, 1024, 0, ctx->stream>>>(J.W, J.Vc, r, len, V, s);
+  ctx->launches += 2;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) { st = lrs_fail(ctx, LRS_ECUDA, "jacobi: %s", cudaGetErrorString(e)); return true; }
+  int* h = (int*)ctx->host_scratch;
+  e = cudaMemcpyAsync(h + 48, J.bar.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) { st = lrs_fail(ctx, LRS_ECUDA, "jacobi: %s", cudaGetErrorString(e)); return true; }
+  if (h[48] != 0) st = lrs_fail(ctx, LRS_ETIMEOUT, "svd: Jacobi grid barrier wait gave up");
+  return true;
+}
+
+lrs_status launch_jacobi_wide(lrs_ctx* ctx, const double* B, int64_t r, int64_t n, int64_t ldb, double* V, double* s) {
+  if (!ctx->coop_ok || r < 1 || r > 1024) return LRS_ERANK;
+  lrs_status st = LRS_OK;
+  if (!jacobi_coop(ctx, B, r, n, ldb, 1, V, s, &st)) return LRS_ERANK;
+  return st;
 }
 
 lrs_status launch_jacobi(lrs_ctx* ctx, double* R, int64_t r, double* V, double* s, int fp64) {
   const int64_t rp = (r + 1) & ~int64_t(1);
   if (fp64 && ctx->coop_ok && r >= 24 && r <= 1024) {
-    JacobiCoop J{};
-    J.r = r; J.rp = rp; J.R = R; J.max_sweeps = 40;
-    J.W = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(rp * r));
-    J.Vc = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(rp * r));
-    unsigned* scratch = (unsigned*)ws_alloc(ctx, 512);
-    if (J.W && J.Vc && scratch) {
-      LRS_CUDA_TRY(ctx, cudaMemsetAsync(scratch, 0, 512, ctx->stream));
-      J.bar.count = scratch; J.bar.gen = scratch + 1; J.bar.err = (int*)(scratch + 2);
-      J.sweeps = (int*)(scratch + 3);
-      J.rot = (int*)(scratch + 4);                       // 40 counters
-      int64_t nb = rp / 2;
-      if (nb > ctx->num_sms) nb = ctx->num_sms;
-      void* args[] = {&J};
-      LRS_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)k_jacobi_coop, dim3((unsigned)nb), dim3(32), args, 0,
-                                                    ctx->stream));
-      k_jacobi_finish<<<1, 1024, 0, ctx->stream>>>(J.W, J.Vc, r, V, s);
-      ctx->launches += 2;
-      LRS_CUDA_TRY(ctx, cudaGetLastError());
-      int* h = (int*)ctx->host_scratch;
-      LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 48, J.bar.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-      LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-      if (h[48] != 0) return lrs_fail(ctx, LRS_ETIMEOUT, "svd: Jacobi grid barrier wait gave up");
-      return LRS_OK;
-    }
+    lrs_status st = LRS_OK;
+    if (jacobi_coop(ctx, R, r, r, r, 0, V, s, &st)) return st;
     // no room in the workspace: the one-block kernel below
   }
   const size_t tsz = fp64 ? 8 : 4;
