@@ -175,11 +175,6 @@ lrs_status launch_jacobi(lrs_ctx* ctx, double* R, int64_t r, double* V, double* 
 // workspace of the multi-SM FP64 Jacobi on r columns of length len (launch_jacobi
 // falls back to one block without it)
 size_t jacobi_ws(int64_t r, int64_t len);
-// FP64 one-sided Jacobi straight on the columns of B^T (B r x n row-major, n
-// moderate): V (r x r) = the accumulated rotations (B's left singular
-// vectors, descending), s = B's singular values.  LRS_ERANK: not available
-// (no cooperative launch or no workspace); the caller takes the R route.
-lrs_status launch_jacobi_wide(lrs_ctx* ctx, const double* B, int64_t r, int64_t n, int64_t ldb, double* V, double* s);
 
 // misc.cu -------------------------------------------------------------------------
 // transposed copy of a row-major FP64 matrix: dst (cols x rows) = src^T

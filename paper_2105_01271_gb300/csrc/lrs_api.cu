@@ -424,12 +424,45 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
 
 namespace lrs {
 
-constexpr int64_t kJacobiWideMaxN = 8192;   // B^T columns longer than this take the TSQR route
+__global__ void k_unpermute_r(const double* __restrict__ R, const int32_t* __restrict__ perm, int64_t rank, int64_t r,
+                              double* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= r * r) return;
+  const int64_t i = e / r, j = e - i * r;                 // out(i, perm[j]) = R(i, j)
+  out[i * r + perm[j]] = i < rank ? R[i * r + j] : 0.0;
+}
+
+// R (r x r, row-major) with B^T = Q R for B (r x n FP64 row-major): the
+// cooperative pivoted QR of B^T (column-major B^T is B's row-major storage)
+// run to r steps, its columns returned to their original order
+static lrs_status r_of_bt_cpqr(lrs_ctx* ctx, const double* B, int64_t r, int64_t n, double* Rout) {
+  if (n < r) return LRS_ERANK;
+  double* Mc = (double*)ws_alloc(ctx, 8 * (size_t)(n * r));
+  CpqrOut o{};
+  o.perm = (int32_t*)ws_alloc(ctx, 4 * (size_t)r);
+  o.R = (double*)ws_alloc(ctx, 8 * (size_t)(r * r));
+  o.V = (double*)ws_alloc(ctx, 8 * (size_t)(n * r));
+  o.tail2 = (double*)ws_alloc(ctx, 8);
+  o.rank = (int32_t*)ws_alloc(ctx, 8);
+  if (!Mc || !o.perm || !o.R || !o.V || !o.tail2 || !o.rank) return LRS_ERANK;
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(Mc, B, 8 * (size_t)(n * r), cudaMemcpyDeviceToDevice, ctx->stream));
+  lrs_status st = launch_cpqr(ctx, Mc, n, r, n, r, 0.0, o);
+  if (st) return st;
+  int32_t rank = 0;
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(&rank, o.rank, 4, cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  k_unpermute_r<<<(unsigned)((r * r + 255) / 256), 256, 0, ctx->stream>>>(o.R, o.perm, rank, r, Rout);
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
 
 size_t svd_from_b_ws(int64_t r, int64_t n, int64_t m, int64_t kk, int32_t prec, int num_sms) {
   const size_t bsz = prec == LRS_PREC_FP64 ? 8 : 4;
   size_t need = tsqr_ws(r, n, bsz) + r_of_bt_gram_ws(r, num_sms);
-  need += 4 * align256(8 * (size_t)(r * r)) + align256(8 * (size_t)(m * r)) + jacobi_ws(r, n > r && n <= kJacobiWideMaxN ? n : r) + 65536;
+  need += 4 * align256(8 * (size_t)(r * r)) + align256(8 * (size_t)(m * r)) + jacobi_ws(r, r) + 65536;
+  if (prec == LRS_PREC_FP64)                     // R of B^T by the pivoted QR
+    need += 2 * align256(8 * (size_t)(n * r)) + align256(8 * (size_t)(r * r)) + cpqr_ws(n, r, r) + 1024;
   if (prec >= LRS_PREC_SPLIT_BF16) need += gemm_tc_workspace(kk, r, LRS_PREC_BF16X3) + 4096;
   return need;
 }
@@ -453,29 +486,25 @@ lrs_status svd_from_b(lrs_ctx* ctx, const void* B, int64_t r, int64_t n, const d
   // double-float Gram and an FP64 Cholesky (TSQR if that breaks down); FP64 B:
   // Householder TSQR.
   lrs_status st = LRS_ERANK;
-  bool direct = false;
-  if (f64 && r >= 24 && n <= kJacobiWideMaxN) {
-    // FP64 B of moderate width: one-sided Jacobi on B^T itself across the SMs
-    // (no TSQR); the rotations are U_B
+  if (f64 && r >= 24 && ctx->coop_ok) {
+    // FP64 B: R of B^T by the cooperative pivoted QR (many SMs, no pivot
+    // tolerance), columns put back in order: B^T = Q (R P^T); the Jacobi on
+    // R P^T then gives U_B.  Replaces the one-block-per-leaf Householder TSQR.
     const size_t mark = ctx->ws_top;
-    st = launch_jacobi_wide(ctx, (const double*)B, r, n, n, Vr, sv);
+    st = r_of_bt_cpqr(ctx, (const double*)B, r, n, Rm);
     ctx->ws_top = mark;
     if (st != LRS_OK && st != LRS_ERANK) return st;
-    direct = st == LRS_OK;
   }
-  if (!direct) {
-    st = LRS_ERANK;
-    if (!f64 && r <= 128) {
-      const size_t mark = ctx->ws_top;
-      st = launch_r_of_bt_gram(ctx, (const float*)B, r, n, n, Rm);
-      ctx->ws_top = mark;
-      if (st != LRS_OK && st != LRS_ERANK) return st;
-    }
-    if (st == LRS_ERANK) st = launch_tsqr(ctx, B, f64, r, n, n, Rm);
-    if (st) return st;
-    st = launch_jacobi(ctx, Rm, r, Vr, sv, f64);
-    if (st) return st;
+  if (st == LRS_ERANK && !f64 && r <= 128) {
+    const size_t mark = ctx->ws_top;
+    st = launch_r_of_bt_gram(ctx, (const float*)B, r, n, n, Rm);
+    ctx->ws_top = mark;
+    if (st != LRS_OK && st != LRS_ERANK) return st;
   }
+  if (st == LRS_ERANK) st = launch_tsqr(ctx, B, f64, r, n, n, Rm);
+  if (st) return st;
+  st = launch_jacobi(ctx, Rm, r, Vr, sv, f64);
+  if (st) return st;
   // U = Q Vr(:, :kk):  U^T = Vr_k^T Q^T
   st = launch_transpose(ctx, Q, m, r, ldq, QT, m);
   if (st) return st;

@@ -379,12 +379,6 @@ static bool jacobi_coop(lrs_ctx* ctx, const double* R, int64_t r, int64_t len, i
   return true;
 }
 
-lrs_status launch_jacobi_wide(lrs_ctx* ctx, const double* B, int64_t r, int64_t n, int64_t ldb, double* V, double* s) {
-  if (!ctx->coop_ok || r < 1 || r > 1024) return LRS_ERANK;
-  lrs_status st = LRS_OK;
-  if (!jacobi_coop(ctx, B, r, n, ldb, 1, V, s, &st)) return LRS_ERANK;
-  return st;
-}
 
 lrs_status launch_jacobi(lrs_ctx* ctx, double* R, int64_t r, double* V, double* s, int fp64) {
   const int64_t rp = (r + 1) & ~int64_t(1);
