@@ -331,3 +331,38 @@ def make_batch_matrix(b: BatchSpec, dtype: str = "f32") -> np.ndarray:
     if b.field == "heat":
         return heat_field(b.m, b.N, 2, 16, b.seed, dtype)
     return blob_field(b.m, b.N, 8, b.seed, 1e-5, dtype)
+
+
+# ----------------------------------------------------------------------------
+# the mixed 2-D set of the learned sketch proposal
+# ----------------------------------------------------------------------------
+LEARNED_FIELDS = ("heat", "blob", "tanh")
+
+
+def learned_specs(count: int, seed: int) -> list:
+    """Seeded draws of the learned proposal's matrices: 2-D fields on N x N
+    grids, N in {32, 64, 128}, m ~ U[64, 512] snapshots, FP32 storage; heat
+    (16 modes, 20%), advected blobs (2-16 blobs, 40%), travelling tanh fronts
+    (1-4 fronts, sharpness 10-200, 40%)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        out.append(dict(field=LEARNED_FIELDS[int(rng.choice(3, p=[0.2, 0.4, 0.4]))],
+                        N=int(rng.choice([32, 64, 128])), m=int(rng.integers(64, 513)),
+                        nfronts=int(rng.integers(1, 5)), nblobs=int(rng.integers(2, 17)),
+                        seed=int(seed * 100000 + i)))
+    return out
+
+
+def learned_matrix(sp: dict) -> np.ndarray:
+    if sp["field"] == "heat":
+        return heat_field(sp["m"], sp["N"], 2, 16, sp["seed"], "f32")
+    if sp["field"] == "blob":
+        return blob_field(sp["m"], sp["N"], sp["nblobs"], sp["seed"], 1e-5, "f32")
+    return tanh_front_field(sp["m"], sp["N"], sp["nfronts"], sp["seed"], "f32")
+
+
+def learned_spec_from_meta(row) -> dict:
+    """The spec of one stored meta row (field, N, m, fronts, blobs, seed)."""
+    f, N, m, nf, nb, seed = (int(v) for v in row)
+    return dict(field=LEARNED_FIELDS[f], N=N, m=m, nfronts=nf, nblobs=nb, seed=seed)

@@ -2,7 +2,7 @@
 sketch proposal for seeded synthetic matrices, computed by the FP64 oracle
 only (oracle.learned) from synth's generators.
 
-    python tests/golden/make_learned_set.py [--train 1200] [--test 300] [--procs N]
+    python tests/golden/make_learned_set.py [--train 1600] [--test 400] [--procs N]
 
 Matrices: 2-D fields on N x N grids, N in {32, 64, 128}, m in [64, 512]
 snapshots, FP32 storage: the heat field (16 modes; 20%), advected blobs (2-16
@@ -24,26 +24,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
-FIELDS = ("heat", "blob", "tanh")
+import synth  # noqa: E402
 
-
-def specs(count: int, seed: int):
-    rng = np.random.default_rng(seed)
-    out = []
-    for i in range(count):
-        out.append(dict(field=FIELDS[int(rng.choice(3, p=[0.2, 0.4, 0.4]))], N=int(rng.choice([32, 64, 128])),
-                        m=int(rng.integers(64, 513)), nfronts=int(rng.integers(1, 5)),
-                        nblobs=int(rng.integers(2, 17)), seed=int(seed * 100000 + i)))
-    return out
-
-
-def matrix(sp):
-    import synth
-    if sp["field"] == "heat":
-        return synth.heat_field(sp["m"], sp["N"], 2, 16, sp["seed"], "f32")
-    if sp["field"] == "blob":
-        return synth.blob_field(sp["m"], sp["N"], sp["nblobs"], sp["seed"], 1e-5, "f32")
-    return synth.tanh_front_field(sp["m"], sp["N"], sp["nfronts"], sp["seed"], "f32")
+FIELDS = synth.LEARNED_FIELDS
+specs = synth.learned_specs
+matrix = synth.learned_matrix
 
 
 def one(sp):
