@@ -573,6 +573,8 @@ bool apass_eligible(const GemmArgs& a, int prec) {
   if (prec != LRS_PREC_SPLIT_BF16 && prec != LRS_PREC_BF16X3) return false;
   if (a.adt != LRS_F32 && a.adt != LRS_BF16) return false;
   if (a.M < 1 || a.M > kMaxR || a.N < TN || a.K < 1) return false;
+  // few column tiles over a long K: the split-K tensor-core kernel fills the SMs, this one cannot
+  if (a.N < 64 * TN && a.K >= 8192) return false;
   if (a.N >= (int64_t)1 << 31 || a.K >= (int64_t)1 << 31) return false;
   const int esize = a.adt == LRS_F32 ? 4 : 2;
   if ((reinterpret_cast<uintptr_t>(a.A) & 15u) != 0 || ((a.lda * esize) & 15) != 0) return false;

@@ -320,8 +320,10 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
     const size_t o1 = orth_ws(m, l, ctx->num_sms), o2 = orth_ws(nI, wmax, ctx->num_sms);
     size_t inner = o1 > o2 ? o1 : o2;
     if (tc) {
-      const size_t t1 = gemm_tc_workspace(wmax, m, prec) + gemm_tc_splitk_workspace(wmax, nI, m, ctx->num_sms);
-      const size_t t2 = gemm_tc_workspace(wmax, nI, prec) + gemm_tc_splitk_workspace(wmax, m, nI, ctx->num_sms);
+      // either operand may be the prepared one (the narrow one when it is <= 256 wide)
+      const size_t t1 = gemm_tc_workspace(nI > wmax ? nI : wmax, m, prec) +
+                        gemm_tc_splitk_workspace(nI > wmax ? nI : wmax, nI > wmax ? nI : wmax, m, ctx->num_sms);
+      const size_t t2 = gemm_tc_workspace(wmax, nI, prec) + gemm_tc_splitk_workspace(wmax, wmax, nI, ctx->num_sms);
       const size_t t = (t1 > t2 ? t1 : t2) + 4096;
       if (t > inner) inner = t;
     }
@@ -376,8 +378,12 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
       // the orthonormalisation reads FP64; the next product reads FP32.  T^T =
       // G^T W: the narrow G is the prepared operand and the wide W streams
       // through the TMA A-pass once; T is stored transposed (n-major) directly
-      if (reorth) st = gemm(ctx, prec, gc, nI, m, G32, LRS_F32, gc, W, wdt, nI, Tm, 1, 1, gc);
-      else st = gemm(ctx, prec, gc, nI, m, G32, LRS_F32, gc, W, wdt, nI, T32, 0, 1, gc);
+      // (for a wide G, gc > 256, the older kernel with W prepared tiles better)
+      const bool narrow = gc <= 256;
+      if (reorth && narrow) st = gemm(ctx, prec, gc, nI, m, G32, LRS_F32, gc, W, wdt, nI, Tm, 1, 1, gc);
+      else if (narrow) st = gemm(ctx, prec, gc, nI, m, G32, LRS_F32, gc, W, wdt, nI, T32, 0, 1, gc);
+      else if (reorth) st = gemm(ctx, prec, nI, gc, m, W, wdt, nI, G32, LRS_F32, gc, Tm, 1, 0, gc);
+      else st = gemm(ctx, prec, nI, gc, m, W, wdt, nI, G32, LRS_F32, gc, T32, 0, 0, gc);
     } else {
       st = gemm(ctx, prec, nI, gc, m, W, wdt, nI, Gcur, LRS_F64, ldcur, Tm, 1, 0, gc);
     }
@@ -401,7 +407,7 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
     // G = W T   (m x tc_cols)  computed as (W^T)^T T; tensor-core modes form
     // G^T = T^T W^T with the narrow T prepared and W^T streamed, stored transposed
     double* Gn = (Gcur == Ga) ? Gb : Ga;
-    if (tc) st = gemm(ctx, prec, tc_cols, m, nI, Tcur, tdt, gc, WT, wdt, m, Gn, 1, 1, wmax);
+    if (tc && tc_cols <= 256) st = gemm(ctx, prec, tc_cols, m, nI, Tcur, tdt, gc, WT, wdt, m, Gn, 1, 1, wmax);
     else st = gemm(ctx, prec, m, tc_cols, nI, WT, wdt, m, Tcur, tdt, gc, Gn, 1, 0, wmax);
     if (st) return st;
     ctx->ws_top = mark;
