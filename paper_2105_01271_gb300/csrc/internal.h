@@ -151,6 +151,15 @@ lrs_status spc_err_from_rows(lrs_ctx* ctx, const void* Bf, int32_t dtype, int64_
 // rdiag (optional, device): |R_ii| of the pivoted factor, i < r
 lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldm, double rtol,
                             double* Q, int64_t ldq, int64_t* r_out, bool refine = true, double* rdiag = nullptr);
+// the same for a WIDE (or square) M (c > 128 columns): left-looking pivoted
+// Cholesky that forms only the pivots' Gram columns (one cooperative launch),
+// then the tall-skinny tail (Q_1 = M(:, piv) R_11^{-1}, one Cholesky-QR
+// refinement).  LRS_ERANK (nothing reported) when the rank exceeds 128 or the
+// refinement breaks down: the caller then runs Householder CPQR.
+bool orth_wide_eligible(int64_t p, int64_t c, double rtol, int num_sms);
+size_t orth_wide_ws(int64_t p, int64_t c, int num_sms);
+lrs_status launch_orth_wide(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldm, double rtol,
+                            double* Q, int64_t ldq, int64_t* r_out, bool refine, double* rdiag);
 // out[i] = |R[i * ld + i]|, i < r (device pointers)
 lrs_status launch_abs_diag(lrs_ctx* ctx, const double* R, int64_t ld, int64_t r, double* out);
 

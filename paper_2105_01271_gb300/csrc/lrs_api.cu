@@ -113,7 +113,12 @@ static size_t orth_ws(int64_t p, int64_t c, int num_sms) {
   b += align256(8 * (size_t)(p * kmax));         // V
   b += 2 * 256;                                  // scalars
   b += cpqr_ws(p, c, kmax);
-  return b > g ? b : g;
+  if (b < g) b = g;
+  if (c > 128) {
+    const size_t w = orth_wide_ws(p, c, num_sms);
+    if (b < w) b = w;
+  }
+  return b;
 }
 
 // Orthonormal basis of the numerical range of Min (p x c, row-major ldi):
@@ -139,6 +144,13 @@ static lrs_status orth(lrs_ctx* ctx, const double* Min, int64_t p, int64_t c, in
                        double* rdiag = nullptr, int64_t kcap = 0) {
   int64_t kmax = p < c ? p : c;
   if (kcap > 0 && kcap < kmax) kmax = kcap;           // at most kcap pivoted steps (Householder route)
+  if (kcap <= 0 && orth_wide_eligible(p, c, rtol, ctx->num_sms)) {
+    // wide: left-looking pivoted Cholesky (same pivots and stop rule)
+    const size_t mark = ctx->ws_top;
+    lrs_status ws = launch_orth_wide(ctx, Min, p, c, ldi, rtol, Q, ldq, r_out, !intermediate, rdiag);
+    ctx->ws_top = mark;
+    if (ws != LRS_ERANK) return ws;
+  }
   if (kcap <= 0 && orth_gram_eligible(p, c, rtol)) {
     // tall-skinny: pivoted Cholesky of the Gram (same pivots and stop rule)
     const size_t mark = ctx->ws_top;

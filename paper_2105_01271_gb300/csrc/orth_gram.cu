@@ -503,3 +503,307 @@ lrs_status launch_r_of_bt_gram(lrs_ctx* ctx, const float* B, int64_t r, int64_t 
 }
 
 }  // namespace lrs
+
+namespace lrs {
+
+// ---------------------------------------------------------------------------
+// WIDE (or square) M, c > 128 columns: left-looking pivoted Cholesky of
+// G = M^T M without forming G.  Step j needs only the pivot's column of the
+// Schur complement,
+//     S(:, piv) = M^T m_piv - L(:, 0:j) L(piv, 0:j)^T,
+// one FP64 matrix-vector product over the ORIGINAL columns (p c FMAs, against
+// 3 (p-j)(c-j) for a Householder step), then L(:, j) = S(:, piv) / sqrt(d_piv)
+// and the remaining norms^2 are down-dated, d_i -= L(i, j)^2.  The pivot and
+// tie rules and the stop test are those of k_pchol (and so of cpqr.cu).
+//
+// One persistent cooperative launch.  Block b owns a contiguous range of
+// physical columns (all p rows, in shared memory) and their d_i; L lives in
+// global memory by physical column, L[i * kmax + t].  One grid barrier per
+// step: each block publishes its best remaining candidate (double-buffered by
+// step parity, so a block still reading step j's candidates never sees step
+// j+1's), and every block reduces the candidates itself in block order, so
+// all blocks take the same decision and apply the same position swap to their
+// own copy of the permutation.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kLpThreads = 512;
+constexpr int kLpMaxCpb = 16;           // owned columns per block
+
+struct LpcholState {
+  const double* Mc; int64_t p, c, ldm;  // column-major copy of M (column i at Mc + i * ldm)
+  int64_t kmax; double rtol;
+  int64_t cpb;                          // columns owned per block
+  double* L;                            // c x kmax, by physical column
+  int32_t* perm; double* R; int64_t ldr; int32_t* rank;
+  double* best_val; int32_t* best_pos; int32_t* best_phys;   // 2 x nb each
+  GridBarrier bar;
+};
+
+__global__ void __launch_bounds__(kLpThreads, 1) k_lpchol(LpcholState s) {
+  extern __shared__ double lsm[];
+  const int nb = gridDim.x, b = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t o_lo = min(s.c, (int64_t)b * s.cpb), o_hi = min(s.c, o_lo + s.cpb);
+  const int nown = (int)(o_hi - o_lo);
+  const int64_t p = s.p;
+  double* slab = lsm;                               // nown x p: owned columns
+  double* xpiv = slab + s.cpb * p;                  // p: the pivot column
+  double* lpiv = xpiv + p;                          // kmax: L(piv, 0:j)
+  double* red = lpiv + s.kmax;                      // nw x kLpMaxCpb partial dots
+  double* d = red + nw * kLpMaxCpb;                 // nown: remaining norms^2
+  int32_t* pos_of = reinterpret_cast<int32_t*>(d + kLpMaxCpb);
+  int32_t* phys_at = pos_of + s.c;
+  __shared__ double sv[32];
+  __shared__ int sp[32], sf[32];
+  __shared__ int s_piv, s_stop;
+  __shared__ double s_dpiv, s_top;
+  __shared__ unsigned char s_done[kLpMaxCpb];
+
+  for (int64_t e = threadIdx.x; e < (int64_t)nown * p; e += blockDim.x) {
+    const int64_t cc = e / p, i = e - cc * p;
+    slab[cc * p + i] = s.Mc[(o_lo + cc) * s.ldm + i];
+  }
+  for (int64_t q = threadIdx.x; q < s.c; q += blockDim.x) { pos_of[q] = (int)q; phys_at[q] = (int)q; }
+  if (threadIdx.x < kLpMaxCpb) s_done[threadIdx.x] = 0;
+  __syncthreads();
+  // d_i = ||m_i||^2, a warp per owned column (fixed order)
+  for (int cc = wid; cc < nown; cc += nw) {
+    double a = 0.0;
+    for (int64_t i = lane; i < p; i += 32) a = fma(slab[cc * p + i], slab[cc * p + i], a);
+    a = warp_sum(a);
+    if (lane == 0) d[cc] = a;
+  }
+  __syncthreads();
+
+  // publish this block's best remaining candidate into buffer `buf`
+  auto publish = [&](int buf) {
+    double bv = -1.0; int bp = 0x7fffffff, bf = -1;
+    if (threadIdx.x < 32) {
+      for (int cc = lane; cc < nown; cc += 32) {
+        if (s_done[cc]) continue;
+        const int ph = (int)(o_lo + cc);
+        if (pivot_better(d[cc], pos_of[ph], bv, bp)) { bv = d[cc]; bp = pos_of[ph]; bf = ph; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+        const int of = __shfl_xor_sync(0xffffffffu, bf, o);
+        if (pivot_better(ov, op, bv, bp)) { bv = ov; bp = op; bf = of; }
+      }
+      if (lane == 0) {
+        s.best_val[buf * nb + b] = bv; s.best_pos[buf * nb + b] = bp; s.best_phys[buf * nb + b] = bf;
+      }
+    }
+  };
+  // every block: the winner of buffer `buf` (block order, same result everywhere)
+  auto decide = [&](int buf, int64_t j) {
+    double bv = -1.0; int bp = 0x7fffffff, bf = -1;
+    for (int bb = threadIdx.x; bb < nb; bb += blockDim.x) {
+      const double v = __ldcg(s.best_val + buf * nb + bb);
+      const int pp = __ldcg(s.best_pos + buf * nb + bb);
+      if (pivot_better(v, pp, bv, bp)) { bv = v; bp = pp; bf = __ldcg(s.best_phys + buf * nb + bb); }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+      const int of = __shfl_xor_sync(0xffffffffu, bf, o);
+      if (pivot_better(ov, op, bv, bp)) { bv = ov; bp = op; bf = of; }
+    }
+    if (lane == 0) { sv[wid] = bv; sp[wid] = bp; sf[wid] = bf; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < nw; ++w)
+        if (pivot_better(sv[w], sp[w], bv, bp)) { bv = sv[w]; bp = sp[w]; bf = sf[w]; }
+      if (j == 0) s_top = bv;
+      const bool stop = (j >= s.kmax) || bf < 0 || !(bv > 0.0) || (j > 0 && bv <= s.rtol * s.rtol * s_top);
+      s_stop = stop ? 1 : 0;
+      if (!stop) {
+        // move the pivot to position j (the transposition of cpqr.cu)
+        const int pj = phys_at[j];
+        phys_at[j] = bf; phys_at[bp] = pj;
+        pos_of[bf] = (int)j; pos_of[pj] = bp;
+        s_piv = bf; s_dpiv = bv;
+        if (bf >= o_lo && bf < o_hi) s_done[bf - o_lo] = 1;
+      }
+    }
+    __syncthreads();
+  };
+
+  publish(0);
+  if (!grid_sync(s.bar)) return;
+  int64_t j = 0;
+  for (;; ++j) {
+    decide((int)(j & 1), j);
+    if (s_stop) break;
+    const int piv = s_piv;
+    const double ljj = s_dpiv * rsqrt_newton(s_dpiv), inv = rsqrt_newton(s_dpiv);
+    // the pivot column and L(piv, 0:j)
+    for (int64_t i = threadIdx.x; i < p; i += blockDim.x) xpiv[i] = __ldcg(s.Mc + (int64_t)piv * s.ldm + i);
+    for (int64_t t = threadIdx.x; t < j; t += blockDim.x) lpiv[t] = __ldcg(s.L + (int64_t)piv * s.kmax + t);
+    __syncthreads();
+    // raw dots m_i . m_piv for the owned columns: rows split over the block
+    double acc[kLpMaxCpb];
+#pragma unroll
+    for (int cc = 0; cc < kLpMaxCpb; ++cc) acc[cc] = 0.0;
+    for (int64_t i = threadIdx.x; i < p; i += blockDim.x) {
+      const double x = xpiv[i];
+#pragma unroll
+      for (int cc = 0; cc < kLpMaxCpb; ++cc)
+        if (cc < nown) acc[cc] = fma(x, slab[cc * p + i], acc[cc]);
+    }
+#pragma unroll
+    for (int cc = 0; cc < kLpMaxCpb; ++cc) {
+      if (cc < nown) {
+        const double a = warp_sum(acc[cc]);
+        if (lane == 0) red[wid * kLpMaxCpb + cc] = a;
+      }
+    }
+    __syncthreads();
+    // a warp per owned column: block sum of the dots, minus L(i, 0:j) L(piv, 0:j)
+    for (int cc = wid; cc < nown; cc += nw) {
+      const int64_t ph = o_lo + cc;
+      double corr = 0.0;
+      if (!s_done[cc] || ph == piv)
+        for (int64_t t = lane; t < j; t += 32) corr = fma(__ldcg(s.L + ph * s.kmax + t), lpiv[t], corr);
+      corr = warp_sum(corr);
+      if (lane == 0) {
+        double g = 0.0;
+        for (int w = 0; w < nw; ++w) g += red[w * kLpMaxCpb + cc];
+        double lij;
+        if (ph == piv) lij = ljj;
+        else if (s_done[cc]) lij = 0.0;
+        else {
+          lij = (g - corr) * inv;
+          d[cc] = fma(-lij, lij, d[cc]);
+        }
+        s.L[ph * s.kmax + j] = lij;
+      }
+    }
+    __syncthreads();
+    publish((int)((j + 1) & 1));
+    if (!grid_sync(s.bar)) return;
+  }
+
+  // epilogue: rank, permutation, the leading r x r block of R (pivoted order)
+  const int64_t r = j;
+  if (b == 0) {
+    if (threadIdx.x == 0) *s.rank = (int32_t)r;
+    for (int64_t q = threadIdx.x; q < s.c; q += blockDim.x) s.perm[q] = phys_at[q];
+  }
+  for (int64_t e = (int64_t)b * blockDim.x + threadIdx.x; e < r * r; e += (int64_t)nb * blockDim.x) {
+    const int64_t i = e / r, q = e - i * r;
+    s.R[i * s.ldr + q] = (q < i) ? 0.0 : __ldcg(s.L + (int64_t)phys_at[q] * s.kmax + i);
+  }
+}
+
+struct LpGeom { int64_t nb, cpb; size_t smem; };
+
+LpGeom lp_geom(int64_t p, int64_t c, int64_t kmax, int num_sms) {
+  LpGeom g{};
+  g.cpb = (c + num_sms - 1) / num_sms;
+  if (g.cpb < 1) g.cpb = 1;
+  g.nb = (c + g.cpb - 1) / g.cpb;
+  g.smem = sizeof(double) * (size_t)(g.cpb * p + p + kmax + (kLpThreads / 32) * kLpMaxCpb + kLpMaxCpb) +
+           sizeof(int32_t) * (size_t)(2 * c);
+  return g;
+}
+
+constexpr int64_t kLpMaxRank = 128;     // the refinement's Gram kernels take up to 128 columns
+
+}  // namespace
+
+bool orth_wide_eligible(int64_t p, int64_t c, double rtol, int num_sms) {
+  if (c <= kMaxC || p < 1 || !(rtol >= kOrthGramRtolMin)) return false;
+  const int64_t kmax = min(min(p, c), kLpMaxRank + 1);
+  const LpGeom g = lp_geom(p, c, kmax, num_sms);
+  return g.cpb <= kLpMaxCpb && g.smem <= 200 * 1024;
+}
+
+size_t orth_wide_ws(int64_t p, int64_t c, int num_sms) {
+  auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const int64_t kmax = min(min(p, c), kLpMaxRank + 1);
+  const LpGeom g = lp_geom(p, c, kmax, num_sms);
+  size_t b = 0;
+  b += a256(sizeof(double) * (size_t)(p * c));           // column-major copy
+  b += a256(sizeof(double) * (size_t)(c * kmax));        // L
+  b += a256(sizeof(double) * (size_t)(kmax * kmax));     // R
+  b += a256(4 * (size_t)c) + a256(8);                    // perm, rank
+  b += 2 * a256(sizeof(double) * (size_t)(2 * g.nb)) + a256(4 * (size_t)(2 * g.nb)) + 256;   // candidates, barrier
+  // then the tall-skinny tail (Q_1 and the refinement's Gram) on p x r, r <= 128
+  b += orth_gram_ws(p, kLpMaxRank, num_sms);
+  return b + 1024;
+}
+
+lrs_status launch_orth_wide(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldm, double rtol,
+                            double* Q, int64_t ldq, int64_t* r_out, bool refine, double* rdiag) {
+  if (!ctx->coop_ok) return LRS_ERANK;               // the caller's Householder route reports it
+  const int64_t kmax_full = min(p, c);
+  const int64_t kmax = min(kmax_full, kLpMaxRank + 1);
+  const LpGeom g = lp_geom(p, c, kmax, ctx->num_sms);
+  double* Mc = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(p * c));
+  double* L = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(c * kmax));
+  double* R = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(kmax * kmax));
+  int32_t* perm = (int32_t*)ws_alloc(ctx, 4 * (size_t)c);
+  int32_t* rank = (int32_t*)ws_alloc(ctx, 8);
+  double* bv = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(2 * g.nb));
+  int32_t* bp = (int32_t*)ws_alloc(ctx, sizeof(double) * (size_t)(2 * g.nb));
+  int32_t* bf = (int32_t*)ws_alloc(ctx, 4 * (size_t)(2 * g.nb));
+  unsigned* bar = (unsigned*)ws_alloc(ctx, 256);
+  if (!Mc || !L || !R || !perm || !rank || !bv || !bp || !bf || !bar)
+    return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (orth_wide)");
+  lrs_status st = launch_transpose(ctx, M, p, c, ldm, Mc, p);
+  if (st) return st;
+  LpcholState s{};
+  s.Mc = Mc; s.p = p; s.c = c; s.ldm = p; s.kmax = kmax; s.rtol = rtol; s.cpb = g.cpb;
+  s.L = L; s.perm = perm; s.R = R; s.ldr = kmax; s.rank = rank;
+  s.best_val = bv; s.best_pos = bp; s.best_phys = bf;
+  LRS_CUDA_TRY(ctx, cudaMemsetAsync(bar, 0, 256, ctx->stream));
+  s.bar.count = bar; s.bar.gen = bar + 1; s.bar.err = (int*)(bar + 2);
+  if (g.smem > 48 * 1024)
+    { const lrs_status _s = raise_dyn_smem(ctx, (const void*)k_lpchol, g.smem); if (_s) return _s; }
+  int per_sm = 0;
+  LRS_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lpchol, kLpThreads, g.smem));
+  if (per_sm < 1 || g.nb > (int64_t)per_sm * ctx->num_sms) return LRS_ERANK;
+  void* args[] = {&s};
+  LRS_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)k_lpchol, dim3((unsigned)g.nb), dim3(kLpThreads),
+                                                args, g.smem, ctx->stream));
+  ctx->launches++;
+  int32_t* h = (int32_t*)ctx->host_scratch;
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 43, rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 44, bar + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (h[44] != 0) return lrs_fail(ctx, LRS_ETIMEOUT, "orth_wide: grid barrier wait gave up");
+  const int r = h[43];
+  // more than 128 directions: the refinement kernels cannot take it; the
+  // caller's Householder route runs instead
+  if (r > kLpMaxRank) return LRS_ERANK;
+  *r_out = r;
+  if (r == 0) return LRS_OK;
+  if (rdiag) {
+    st = launch_abs_diag(ctx, R, kmax, r, rdiag);
+    if (st) return st;
+  }
+  if (!refine) return trsm_rows(ctx, M, p, ldm, perm, R, kmax, r, Q, ldq);
+  double* Q1 = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(p * r));
+  double* G2 = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(r * r));
+  double* R2 = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(r * r));
+  if (!Q1 || !G2 || !R2) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (orth_wide refine)");
+  st = trsm_rows(ctx, M, p, ldm, perm, R, kmax, r, Q1, r);
+  if (st) return st;
+  // refinement: G_2 = Q_1^T Q_1 = R_2^T R_2 (plain Cholesky), Q = Q_1 R_2^{-1}
+  const size_t mark = ctx->ws_top;
+  st = gram(ctx, Q1, p, r, r, G2);
+  if (st) return st;
+  ctx->ws_top = mark;
+  st = pchol(ctx, G2, r, r, 0.0, 0, perm, R2, r, rank);
+  if (st) return st;
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 45, rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (h[45] != r) return LRS_ERANK;
+  return trsm_rows(ctx, Q1, p, r, nullptr, R2, r, r, Q, ldq);
+}
+
+}  // namespace lrs

@@ -154,7 +154,44 @@ def test_range_find_blob_sketch(lrs, shape):
         assert r == ro
         Qg = _np(Q)[:, :r]
         np.testing.assert_allclose(Qg.T @ Qg, np.eye(r), atol=1e-13)
-        np.testing.assert_allclose(Qg, Qo, atol=1e-9)
+        # both sides are the QR of the same pivot columns, unique up to the
+        # sign of each column (the wide route's R has a positive diagonal,
+        # Householder's R_jj = -sign(x_0) ||x||)
+        np.testing.assert_allclose(Qg * _col_signs(Qg, Qo), Qo, atol=1e-9)
+
+
+def _col_signs(Qg, Qo):
+    return np.where(np.sum(Qg * Qo, axis=0) < 0.0, -1.0, 1.0)
+
+
+def _spectrum_matrix(p, c, n, seed):
+    """p x c matrix of rank n with singular values logspace(0, -9, n)."""
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.standard_normal((p, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((c, n)))
+    return (U * np.logspace(0, -9, n)) @ V.T
+
+
+@pytest.mark.parametrize("p,c,n", [(2000, 1024, 150), (600, 1024, 120), (129, 1000, 129),
+                                   (256, 2400, 160), (1000, 131, 131), (300, 700, 300)])
+def test_range_find_wide_gram_route(lrs, p, c, n):
+    """Wide inputs (c > 128) at rtol = 1e-6 take the left-looking pivoted
+    Cholesky route (ragged column ownership: c not a multiple of the columns
+    per block; p < c and p > c); ranks above 128 (the last case, rank ~200)
+    fall back to Householder CPQR.  Same rank as the oracle, orthonormal Q,
+    the oracle's range up to u kappa(M_r) with kappa <= 1/rtol."""
+    torch = _torch()
+    M = _spectrum_matrix(p, c, n, seed=p + c)
+    Qo, ro = oracle.range_find(M, 1e-6)
+    kq = min(p, c)
+    for _ in range(2):                                   # deterministic across calls
+        Q = torch.zeros((p, kq), dtype=torch.float64, device="cuda")
+        r = lrs.range_find(_dev(M), p, c, c, 1e-6, Q, kq)
+        assert r == ro
+        Qg = _np(Q)[:, :r]
+        np.testing.assert_allclose(Qg.T @ Qg, np.eye(r), atol=1e-13)
+        assert np.linalg.norm(Qg @ (Qg.T @ Qo) - Qo) <= 1e-7
+        np.testing.assert_allclose(Qg * _col_signs(Qg, Qo), Qo, atol=1e-7)
 
 
 # ---------------------------------------------------------------------------
