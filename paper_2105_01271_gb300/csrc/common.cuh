@@ -53,6 +53,21 @@ __device__ __forceinline__ double rsqrt_newton(double x) {
   return y;
 }
 
+// A pivot candidate (norm^2, position, physical column) in one 16-byte record,
+// written and read with single 16-byte accesses through L2 (ld/st .cg), so a
+// block reads another block's candidate in one round trip.
+struct __align__(16) PivotCand { double val; int pos; int phys; };
+
+__device__ __forceinline__ void cand_store(PivotCand* p, double v, int pos, int phys) {
+  int4 x;
+  x.x = __double2loint(v); x.y = __double2hiint(v); x.z = pos; x.w = phys;
+  __stcg(reinterpret_cast<int4*>(p), x);
+}
+__device__ __forceinline__ void cand_load(const PivotCand* p, double& v, int& pos, int& phys) {
+  const int4 x = __ldcg(reinterpret_cast<const int4*>(p));
+  v = __hiloint2double(x.y, x.x); pos = x.z; phys = x.w;
+}
+
 // ---------------------------------------------------------------------------
 // warp / block reductions
 // ---------------------------------------------------------------------------

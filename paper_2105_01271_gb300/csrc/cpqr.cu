@@ -367,9 +367,281 @@ __global__ void __launch_bounds__(kCpqrThreads, 1) k_cpqr(CpqrState s) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Column-owner form of the same factorisation, for c >= 128 columns whose
+// owned slabs fit in shared memory.  Block b owns a contiguous range of
+// physical columns with all their rows, so the Householder dot products and
+// the norms are block-local and a step needs ONE grid barrier:
+//   every block: v_j from the pivot column (read from the winner's slot),
+//     H_j applied to its live columns (dot, update, row j of R), norms^2 over
+//     rows > j, its best candidate published with a copy of that column
+//                                                          -- grid barrier --
+//   every block: the winner among the candidates (block order, so the same
+//     decision everywhere), stop test, the position swap in its own copy of
+//     the permutation.
+// Candidates and candidate columns are double-buffered by step parity: a
+// block still reading step j's slots never sees step j+1's writes.  Pivot,
+// tie, reflector and stop rules are those of k_cpqr.
+// ---------------------------------------------------------------------------
+struct CpqrColsState {
+  const double* M; int64_t p, c, ldm;    // column-major input, read once
+  int64_t kmax; double rtol; int64_t cpb;
+  int32_t* perm; double* R; double* V; double* tail2; int32_t* rank;
+  double* Rphys;                         // kmax x c by physical column
+  PivotCand* cand;                       // 2 x nb
+  double* cand_col;                      // 2 x nb x p
+  double* tail_part;                     // nb
+  GridBarrier bar;
+};
+
+constexpr int kColsThreads = 512;
+
+__global__ void __launch_bounds__(kColsThreads, 1) k_cpqr_cols(CpqrColsState s) {
+  extern __shared__ double csm[];
+  const int nb = gridDim.x, b = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t p = s.p;
+  const int64_t o_lo = min(s.c, (int64_t)b * s.cpb), o_hi = min(s.c, o_lo + s.cpb);
+  const int nown = (int)(o_hi - o_lo);
+  double* slab = csm;                         // nown x p (column cc at slab + cc * p)
+  double* vv = slab + s.cpb * p;              // p: the reflector (rows >= j), first the pivot column
+  double* nrm2 = vv + p;                      // cpb: remaining norms^2 of the owned columns
+  int32_t* pos_of = reinterpret_cast<int32_t*>(nrm2 + s.cpb);
+  int32_t* phys_at = pos_of + s.c;
+  uint8_t* done = reinterpret_cast<uint8_t*>(phys_at + s.c);   // cpb
+  __shared__ double sv[32];
+  __shared__ int sp[32], sf[32];
+  __shared__ int s_piv, s_stop;
+  __shared__ double s_alpha, s_sgn, s_inv, s_top;
+
+  for (int64_t e = threadIdx.x; e < (int64_t)nown * p; e += blockDim.x) {
+    const int64_t cc = e / p, i = e - cc * p;
+    slab[cc * p + i] = s.M[(o_lo + cc) * s.ldm + i];
+  }
+  for (int64_t q = threadIdx.x; q < s.c; q += blockDim.x) { pos_of[q] = (int)q; phys_at[q] = (int)q; }
+  for (int64_t cc = threadIdx.x; cc < s.cpb; cc += blockDim.x) done[cc] = 0;
+  __syncthreads();
+
+  // norms^2 over rows >= r0 of the owned live columns (a warp per column)
+  auto norms = [&](int64_t r0) {
+    for (int cc = wid; cc < nown; cc += nw) {
+      double a = 0.0;
+      if (!done[cc]) {
+        const double* col = slab + (int64_t)cc * p;
+        for (int64_t i = r0 + lane; i < p; i += 32) a = fma(col[i], col[i], a);
+      }
+      a = warp_sum(a);
+      if (lane == 0) nrm2[cc] = a;
+    }
+  };
+  // best owned candidate -> buffer `buf`, with a copy of its column
+  auto publish = [&](int buf) {
+    __syncthreads();
+    if (wid == 0) {
+      double bv = -1.0; int bp = 0x7fffffff, bf = -1;
+      for (int cc = lane; cc < nown; cc += 32) {
+        if (done[cc]) continue;
+        const int ph = (int)(o_lo + cc);
+        if (pivot_better(nrm2[cc], pos_of[ph], bv, bp)) { bv = nrm2[cc]; bp = pos_of[ph]; bf = ph; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+        const int of = __shfl_xor_sync(0xffffffffu, bf, o);
+        if (pivot_better(ov, op, bv, bp)) { bv = ov; bp = op; bf = of; }
+      }
+      if (lane == 0) {
+        cand_store(s.cand + buf * nb + b, bv, bp, bf);
+        sf[0] = bf;
+      }
+    }
+    __syncthreads();
+    const int bf = sf[0];
+    if (bf >= 0) {
+      const double* col = slab + (bf - o_lo) * p;
+      double* dst = s.cand_col + ((int64_t)buf * nb + b) * p;
+      for (int64_t i = threadIdx.x; i < p; i += blockDim.x) dst[i] = col[i];
+    }
+  };
+
+  norms(0);
+  publish(0);
+  if (!grid_sync(s.bar)) return;
+  int64_t j = 0;
+  for (;; ++j) {
+    const int buf = (int)(j & 1);
+    // ---- decide: the winner of buffer buf (every block, block order) -------
+    {
+      double bv = -1.0; int bp = 0x7fffffff, bf = -1;
+      for (int bb = threadIdx.x; bb < nb; bb += blockDim.x) {
+        double v; int pp, pf;
+        cand_load(s.cand + buf * nb + bb, v, pp, pf);
+        if (pivot_better(v, pp, bv, bp)) { bv = v; bp = pp; bf = pf; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+        const int of = __shfl_xor_sync(0xffffffffu, bf, o);
+        if (pivot_better(ov, op, bv, bp)) { bv = ov; bp = op; bf = of; }
+      }
+      __syncthreads();
+      if (lane == 0) { sv[wid] = bv; sp[wid] = bp; sf[wid] = bf; }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w)
+          if (pivot_better(sv[w], sp[w], bv, bp)) { bv = sv[w]; bp = sp[w]; bf = sf[w]; }
+        const double nrm = bv > 0.0 ? bv * rsqrt_newton(bv) : 0.0;
+        if (j == 0) s_top = nrm;
+        const bool stop = (j >= s.kmax) || bf < 0 || !(bv > 0.0) || (j > 0 && nrm <= s.rtol * s_top);
+        s_stop = stop ? 1 : 0;
+        if (!stop) {
+          const int pj = phys_at[j];
+          phys_at[j] = bf; phys_at[bp] = pj;
+          pos_of[bf] = (int)j; pos_of[pj] = bp;
+          if (bf >= o_lo && bf < o_hi) done[bf - o_lo] = 1;
+          s_piv = bf; s_alpha = nrm;
+        }
+      }
+      __syncthreads();
+    }
+    if (s_stop) break;
+    const int piv = s_piv;
+    // ---- the reflector from the winner's column (rows >= j) -----------------
+    {
+      const int64_t owner = piv / s.cpb;
+      const double* src = s.cand_col + ((int64_t)buf * nb + owner) * p;
+      for (int64_t i = j + threadIdx.x; i < p; i += blockDim.x) vv[i] = __ldcg(src + i);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const double x0 = vv[j], nrm = s_alpha;
+        const double sgn = x0 >= 0.0 ? 1.0 : -1.0;
+        const double vn2 = 2.0 * nrm * (nrm + fabs(x0));
+        s_sgn = sgn;
+        s_inv = vn2 > 0.0 ? rsqrt_newton(vn2) : 0.0;
+      }
+      __syncthreads();
+      const double inv = s_inv;
+      for (int64_t i = j + threadIdx.x; i < p; i += blockDim.x)
+        vv[i] = (i == j) ? (vv[i] + s_sgn * s_alpha) * inv : vv[i] * inv;
+      __syncthreads();
+      if (b == 0) {
+        for (int64_t i = threadIdx.x; i < p; i += blockDim.x) s.V[j * p + i] = i < j ? 0.0 : vv[i];
+        if (threadIdx.x == 0) s.Rphys[j * s.c + piv] = -s_sgn * s_alpha;
+      }
+    }
+    // ---- H_j on the owned live columns, row j of R, norms over rows > j -----
+    for (int cc = wid; cc < nown; cc += nw) {
+      double a = 0.0;
+      if (!done[cc]) {
+        double* col = slab + (int64_t)cc * p;
+        double d = 0.0;
+        for (int64_t i = j + lane; i < p; i += 32) d = fma(vv[i], col[i], d);
+        d = warp_sum(d);
+        const double tw = 2.0 * d;
+        for (int64_t i = j + lane; i < p; i += 32) {
+          const double x = fma(-tw, vv[i], col[i]);
+          col[i] = x;
+          if (i > j) a = fma(x, x, a);
+          else s.Rphys[j * s.c + o_lo + cc] = x;
+        }
+      }
+      a = warp_sum(a);
+      if (lane == 0) nrm2[cc] = a;
+    }
+    publish((int)((j + 1) & 1));
+    if (!grid_sync(s.bar)) return;
+  }
+
+  // ---- epilogue: rank, permutation, R in pivoted order, trailing norm --------
+  const int64_t r = j;
+  {
+    double t = 0.0;
+    for (int cc = threadIdx.x; cc < nown; cc += blockDim.x)
+      if (!done[cc]) t += nrm2[cc];
+    t = block_sum(t, sv);
+    if (threadIdx.x == 0) s.tail_part[b] = t;
+  }
+  if (!grid_sync(s.bar)) return;
+  if (b == 0) {
+    if (threadIdx.x == 0) *s.rank = (int32_t)r;
+    double t = 0.0;
+    if (threadIdx.x == 0)
+      for (int bb = 0; bb < nb; ++bb) t += __ldcg(s.tail_part + bb);
+    if (threadIdx.x == 0) *s.tail2 = (r < min(s.p, s.c)) ? t : 0.0;
+    for (int64_t q = threadIdx.x; q < s.c; q += blockDim.x) s.perm[q] = phys_at[q];
+  }
+  for (int64_t e = (int64_t)b * blockDim.x + threadIdx.x; e < r * s.c; e += (int64_t)nb * blockDim.x) {
+    const int64_t i = e / s.c, q = e - i * s.c;
+    s.R[i * s.c + q] = (q < i) ? 0.0 : __ldcg(s.Rphys + i * s.c + phys_at[q]);
+  }
+}
+
+struct ColsGeom { int64_t nb, cpb; size_t smem; };
+
+ColsGeom cols_geom(int64_t p, int64_t c, int num_sms) {
+  ColsGeom g{};
+  g.cpb = (c + num_sms - 1) / num_sms;
+  if (g.cpb < 1) g.cpb = 1;
+  g.nb = (c + g.cpb - 1) / g.cpb;
+  g.smem = sizeof(double) * (size_t)(g.cpb * p + p + g.cpb) + sizeof(int32_t) * (size_t)(2 * c) + (size_t)g.cpb + 16;
+  return g;
+}
+
+bool cpqr_cols_eligible(int64_t p, int64_t c, int num_sms) {
+  if (c < 128 || p < 1) return false;
+  return cols_geom(p, c, num_sms).smem <= 200 * 1024;
+}
+
+size_t cpqr_cols_scratch_bytes(int64_t p, int64_t c, int64_t kmax, int num_sms) {
+  auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const ColsGeom g = cols_geom(p, c, num_sms);
+  size_t b = 0;
+  b += a256(sizeof(double) * (size_t)(kmax > 0 ? kmax : 1) * c);
+  b += a256(sizeof(PivotCand) * (size_t)(2 * g.nb));
+  b += a256(sizeof(double) * (size_t)(2 * g.nb * p));
+  b += a256(sizeof(double) * (size_t)g.nb);
+  b += 256;
+  return b;
+}
+
+lrs_status launch_cpqr_cols(lrs_ctx* ctx, double* M, int64_t p, int64_t c, int64_t ldm,
+                            int64_t kmax, double rtol, const CpqrOut& o) {
+  const ColsGeom g = cols_geom(p, c, ctx->num_sms);
+  CpqrColsState s{};
+  s.M = M; s.p = p; s.c = c; s.ldm = ldm; s.kmax = kmax; s.rtol = rtol; s.cpb = g.cpb;
+  s.perm = o.perm; s.R = o.R; s.V = o.V; s.tail2 = o.tail2; s.rank = o.rank;
+  s.Rphys = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(kmax > 0 ? kmax : 1) * c);
+  s.cand = (PivotCand*)ws_alloc(ctx, sizeof(PivotCand) * (size_t)(2 * g.nb));
+  s.cand_col = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(2 * g.nb * p));
+  s.tail_part = (double*)ws_alloc(ctx, sizeof(double) * (size_t)g.nb);
+  unsigned* bar = (unsigned*)ws_alloc(ctx, 256);
+  if (!s.Rphys || !s.cand || !s.cand_col || !s.tail_part || !bar)
+    return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (cpqr_cols)");
+  if (g.smem > 48 * 1024)
+    { const lrs_status _s = raise_dyn_smem(ctx, (const void*)k_cpqr_cols, g.smem); if (_s) return _s; }
+  int per_sm = 0;
+  LRS_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cpqr_cols, kColsThreads, g.smem));
+  if (per_sm < 1 || g.nb > (int64_t)per_sm * ctx->num_sms)
+    return lrs_fail(ctx, LRS_ECUDA, "cpqr_cols: %lld blocks do not fit", (long long)g.nb);
+  LRS_CUDA_TRY(ctx, cudaMemsetAsync(bar, 0, 256, ctx->stream));
+  s.bar.count = bar; s.bar.gen = bar + 1; s.bar.err = (int*)(bar + 2);
+  void* args[] = {&s};
+  LRS_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)k_cpqr_cols, dim3((unsigned)g.nb),
+                                                dim3(kColsThreads), args, g.smem, ctx->stream));
+  ctx->launches++;
+  int* h = (int*)ctx->host_scratch;
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 33, bar + 2, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (h[33] != 0) return lrs_fail(ctx, LRS_ETIMEOUT, "cpqr_cols: grid barrier wait gave up");
+  return LRS_OK;
+}
+
 // Bytes launch_cpqr takes from the workspace for these sizes (the same block
 // count, slab placement and 256-byte rounding as the launch below).
 size_t cpqr_scratch_bytes(int64_t p, int64_t c, int64_t kmax, int num_sms) {
+  if (cpqr_cols_eligible(p, c, num_sms)) return cpqr_cols_scratch_bytes(p, c, kmax, num_sms);
   auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
   int64_t nb = (p * c + 2047) / 2048;
   if (nb > num_sms) nb = num_sms;
@@ -393,6 +665,7 @@ size_t cpqr_scratch_bytes(int64_t p, int64_t c, int64_t kmax, int num_sms) {
 lrs_status launch_cpqr(lrs_ctx* ctx, double* M, int64_t p, int64_t c, int64_t ldm,
                        int64_t kmax, double rtol, const CpqrOut& o) {
   if (!ctx->coop_ok) return lrs_fail(ctx, LRS_ECUDA, "device lacks cooperative launch");
+  if (cpqr_cols_eligible(p, c, ctx->num_sms)) return launch_cpqr_cols(ctx, M, p, c, ldm, kmax, rtol, o);
   CpqrState s{};
   s.M = M; s.p = p; s.c = c; s.ldm = ldm; s.kmax = kmax; s.rtol = rtol;
   s.perm = o.perm; s.R = o.R; s.V = o.V; s.tail2 = o.tail2; s.rank = o.rank;
@@ -498,16 +771,20 @@ lrs_status launch_form_q(lrs_ctx* ctx, const double* V, int64_t p, int64_t r, do
 // ---------------------------------------------------------------------------
 // ID coefficients.  R is k x m (pivoted order, row stride m).  Column q >= k
 // of R_2 gives C[:, q-k] = R_1^{-1} R[:, q] by back substitution; then
-// P[perm[i], :] = e_i (i < k) and P[perm[q], :] = C[:, q-k]^T.
+// P[perm[i], :] = e_i (i < k) and P[perm[q], :] = C[:, q-k]^T.  A team of T
+// threads (a power of two dividing 32) solves one column: for each unknown i
+// the team splits R_1[i, i+1:] . c[i+1:] by index mod T and reduces it with
+// shuffles, then one lane applies 1 / R_ii (precomputed per block).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_id_coeffs(const double* __restrict__ R, int64_t k, int64_t m,
+__global__ void __launch_bounds__(256) k_id_coeffs(const double* __restrict__ R, int64_t k, int64_t m,
                                                    const int32_t* __restrict__ perm,
                                                    int32_t* __restrict__ J, double* __restrict__ P,
-                                                   int64_t ldp) {
-  extern __shared__ double R1[];   // k x k
+                                                   int64_t ldp, int T) {
+  extern __shared__ double R1[];   // k x k, then 1 / R_ii (k), then one solution vector per team
+  double* dinv = R1 + k * k;
+  double* cs = dinv + k;
   for (int64_t e = threadIdx.x; e < k * k; e += blockDim.x) R1[e] = R[(e / k) * m + (e % k)];
-  __syncthreads();
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t i = threadIdx.x; i < k; i += blockDim.x) dinv[i] = 1.0 / R[i * m + i];
   if (blockIdx.x == 0) {
     for (int64_t i = threadIdx.x; i < k; i += blockDim.x) {
       J[i] = perm[i];
@@ -515,26 +792,44 @@ __global__ void __launch_bounds__(128) k_id_coeffs(const double* __restrict__ R,
       for (int64_t t = 0; t < k; ++t) prow[t] = (t == i) ? 1.0 : 0.0;
     }
   }
-  if (q >= m - k) return;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int tm = threadIdx.x & (T - 1);
+  const int team = threadIdx.x / T, nteams = blockDim.x / T;
+  const unsigned tmask = (T == 32 ? 0xffffffffu : ((1u << T) - 1u)) << (lane & ~(T - 1));
+  const int64_t q = (int64_t)blockIdx.x * nteams + team;
+  if (q >= m - k) return;                          // whole teams leave together
   const int64_t col = k + q;
-  double* prow = P + (int64_t)perm[col] * ldp;
-  // back substitution, writing the solution straight into P's row
+  double* c = cs + (int64_t)team * k;
+  for (int64_t i = tm; i < k; i += T) c[i] = R[i * m + col];
+  __syncwarp(tmask);
   for (int64_t i = k - 1; i >= 0; --i) {
-    double acc = R[i * m + col];
-    for (int64_t t = i + 1; t < k; ++t) acc = fma(-R1[i * k + t], prow[t], acc);
-    prow[i] = acc / R1[i * k + i];
+    double a = 0.0;
+    for (int64_t t = i + 1 + tm; t < k; t += T) a = fma(R1[i * k + t], c[t], a);
+    for (int o = 1; o < T; o <<= 1) a += __shfl_xor_sync(tmask, a, o);
+    if (tm == 0) c[i] = (c[i] - a) * dinv[i];
+    __syncwarp(tmask);
   }
+  double* prow = P + (int64_t)perm[col] * ldp;
+  for (int64_t t = tm; t < k; t += T) prow[t] = c[t];
 }
 
 lrs_status launch_id_coeffs(lrs_ctx* ctx, const double* R, int64_t k, int64_t m,
                             const int32_t* perm, int32_t* J, double* P, int64_t ldp) {
-  const size_t dyn = sizeof(double) * (size_t)(k * k);
+  const int64_t cols = m - k;
+  // team size: about 8 warps' worth of threads per SM, at most half a warp
+  const int64_t want = (int64_t)ctx->num_sms * 8 * 32;
+  int T = 1;
+  while (T < 16 && cols * T < want) T <<= 1;
+  // larger teams (fewer solution vectors) when k x k leaves little shared memory
+  while (T < 32 && sizeof(double) * (size_t)(k * k + k + (256 / T) * k) > 200 * 1024) T <<= 1;
+  const int nteams = 256 / T;
+  const size_t dyn = sizeof(double) * (size_t)(k * k + k + nteams * k);
   if (dyn > 200 * 1024) return lrs_fail(ctx, LRS_EINVAL, "id: k=%lld too large", (long long)k);
   if (dyn > 48 * 1024)
     { const lrs_status _s = raise_dyn_smem(ctx, (const void*)k_id_coeffs, (size_t)(dyn)); if (_s) return _s; }
-  const int64_t cols = m - k;
-  const unsigned nb = (unsigned)((cols + 127) / 128 > 0 ? (cols + 127) / 128 : 1);
-  k_id_coeffs<<<nb, 128, dyn, ctx->stream>>>(R, k, m, perm, J, P, ldp);
+  const unsigned nb = (unsigned)((cols + nteams - 1) / nteams > 0 ? (cols + nteams - 1) / nteams : 1);
+  k_id_coeffs<<<nb, 256, dyn, ctx->stream>>>(R, k, m, perm, J, P, ldp, T);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
   return LRS_OK;

@@ -97,6 +97,8 @@ static size_t cpqr_ws(int64_t p, int64_t c, int64_t kmax) {
   b += 4 * align256(8 * nbmax) + 256;             // per-block best, barrier
   // slab storage when a block's rows do not fit in shared memory
   b += align256(8 * (size_t)(p * c + 3 * nbmax * c + 2 * nbmax + p));
+  // column-owner form: two candidate columns per block (at most min(c, 1024) blocks)
+  b += align256(8 * (size_t)(2 * (c < (int64_t)nbmax ? c : (int64_t)nbmax) * p));
   return b + 4096;
 }
 
@@ -377,7 +379,9 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
   const double* Gcur = Y;
   int64_t ldcur = ldy;
   if (reorth) {
-    st = orth(ctx, Y, m, l, ldy, rtol, Ga, wmax, &gc);
+    // Q_np only feeds W^T Q_np, which is orthonormalised again: a
+    // well-conditioned basis of the same range suffices (no refinement pass)
+    st = orth(ctx, Y, m, l, ldy, rtol, Ga, wmax, &gc, /*intermediate=*/q > 0);
     if (st) return st;
     ctx->ws_top = mark;
     Gcur = Ga; ldcur = wmax;
@@ -527,10 +531,9 @@ lrs_status svd_from_b(lrs_ctx* ctx, const void* B, int64_t r, int64_t n, const d
   if (st) return st;
   st = launch_jacobi(ctx, Rm, r, Vr, sv, f64);
   if (st) return st;
-  // U = Q Vr(:, :kk):  U^T = Vr_k^T Q^T
-  st = launch_transpose(ctx, Q, m, r, ldq, QT, m);
-  if (st) return st;
-  st = gemm(ctx, LRS_PREC_FP64, kk, m, r, Vr, LRS_F64, r, QT, LRS_F64, m, U, 1, 1, ldu);
+  // U = Q Vr(:, :kk): m x kk x r in FP64, 16 x 16 output tiles over the SMs
+  (void)QT;
+  st = spc_small_gemm(ctx, m, kk, r, Q, ldq, 1, Vr, r, 1, nullptr, nullptr, U, ldu);
   if (st) return st;
   // sign convention on U, then V = B^T Vr_k diag(sign) S_k^{-1} carries the same signs
   st = launch_sign_fix(ctx, U, m, kk, ldu, sgn);

@@ -99,11 +99,14 @@ __device__ __forceinline__ bool better(double a, int pa, double b, int pb) { ret
 // POSITION order: the pivot moves to position j by the symmetric swap of
 // positions j and piv (the transposition cpqr.cu applies), so the remaining
 // block is always [j+1, c)^2 and row j of the working matrix becomes row j of
-// R (rows < j keep R, and their columns j and piv are swapped with the rest).
-// Per step: argmax of the remaining diagonal (the remaining column norm^2,
-// lowest position on ties) | one thread: sqrt, reciprocal, stop test | swap
-// and scale row j (disjoint element pairs, one phase) | Schur update of the
-// remaining block, a warp per row.  Four block barriers per step.
+// R (rows < j hold R, and their columns j and piv are swapped with the rest).
+// Only the upper triangle is stored and updated (sym(a, b) = G[min][max]).
+// Per step: every warp finds the argmax of the remaining diagonal itself (the
+// remaining column norm^2, lowest position on ties; the same answer in every
+// warp, no barrier) and one lane takes the square root and the stop test |
+// swap and scale row j (each thread owns one index a and the two cells of a)
+// | Schur update of the remaining upper triangle, a warp per row.  Three
+// block barriers per step.
 // Outputs: perm[pos] = physical column, R (rows 0..rank-1, row-major ldr,
 // pivoted order, zero below the diagonal), *rank.
 __global__ void __launch_bounds__(256) k_pchol(const double* __restrict__ Gin, int c, int kmax, double rtol,
@@ -111,40 +114,35 @@ __global__ void __launch_bounds__(256) k_pchol(const double* __restrict__ Gin, i
                                                int64_t ldr, int32_t* __restrict__ rank) {
   extern __shared__ double sm[];
   const int ld = c + 1;
-  double* G = sm;                                   // c x ld, by position
+  double* G = sm;                                   // c x ld, upper triangle by position
   int* phys_at = reinterpret_cast<int*>(G + c * ld);
-  __shared__ double sv[8];
-  __shared__ int sp[8];
   __shared__ int s_piv, s_stop;
   __shared__ double s_ljj, s_inv, s_top;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int a = wid; a < c; a += nw)
-    for (int b = lane; b < c; b += 32) G[a * ld + b] = Gin[a * c + b];
+    for (int b2 = lane; b2 < c; b2 += 32) G[a * ld + b2] = Gin[a * c + b2];
   for (int q = threadIdx.x; q < c; q += blockDim.x) phys_at[q] = q;
   __syncthreads();
   int j = 0;
   for (;; ++j) {
+    // ---- pivot: every warp reduces the remaining diagonal itself -------------
     double bv = -1.0;
     int bp = 0x7fffffff;
     if (pivot) {
-      for (int q = j + threadIdx.x; q < c; q += blockDim.x) {
+      for (int q = j + lane; q < c; q += 32) {
         const double d = G[q * ld + q];
         if (norm_key(d) > norm_key(bv)) { bv = d; bp = q; }
       }
-    } else if (threadIdx.x == 0 && j < c) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+        if (better(ov, op, bv, bp)) { bv = ov; bp = op; }
+      }
+    } else if (j < c) {
       bv = G[j * ld + j]; bp = j;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      const int op = __shfl_xor_sync(0xffffffffu, bp, o);
-      if (better(ov, op, bv, bp)) { bv = ov; bp = op; }
-    }
-    if (lane == 0) { sv[wid] = bv; sp[wid] = bp; }
-    __syncthreads();
     if (threadIdx.x == 0) {
-      for (int w = 1; w < nw; ++w)
-        if (better(sv[w], sp[w], bv, bp)) { bv = sv[w]; bp = sp[w]; }
       // R_jj = sqrt(d), 1 / R_jj = rsqrt(d); the stop test |R_jj| <= rtol |R_00|
       // is taken on the squares, d <= rtol^2 d_0
       const double y = bv > 0.0 ? rsqrt_newton(bv) : 0.0;
@@ -160,41 +158,45 @@ __global__ void __launch_bounds__(256) k_pchol(const double* __restrict__ Gin, i
     if (s_stop) break;
     const int pv = s_piv;
     const double inv = s_inv;
-    // swap positions j and pv (rows and columns) and scale row j beyond the
-    // diagonal; each thread owns index a and touches only (a, j), (a, pv),
-    // (j, a), (pv, a), so the phase needs no inner barrier
+    // ---- swap positions j and pv, scale row j beyond the diagonal -------------
+    // thread a exchanges sym(a, j) and sym(a, pv); for a > j the new sym(j, a)
+    // is row j of R and is stored scaled.
     for (int a = threadIdx.x; a < c; a += blockDim.x) {
       if (a == j) {
-        if (pv != j) {
-          G[pv * ld + pv] = G[j * ld + j];
-          G[j * ld + pv] *= inv;                    // (j, pv) = old (pv, j): symmetric, stays; scaled
-        }
+        if (pv != j) G[pv * ld + pv] = G[j * ld + j];
         G[j * ld + j] = s_ljj;
-      } else if (a != pv) {
+      } else if (a == pv) {
+        G[j * ld + pv] *= inv;                      // sym(j, pv) is unchanged by the swap
+      } else if (a < j) {
+        if (pv != j) {                              // finished rows: swap columns j and pv
+          const double t = G[a * ld + j];
+          G[a * ld + j] = G[a * ld + pv];
+          G[a * ld + pv] = t;
+        }
+      } else {
+        // a > j, a != pv: new sym(j, a) = old sym(pv, a); new sym(pv, a) = old sym(j, a)
         if (pv != j) {
-          const double cj = G[a * ld + j], cp = G[a * ld + pv];
-          G[a * ld + j] = cp;
-          G[a * ld + pv] = cj;
-          const double rj = G[j * ld + a], rp = G[pv * ld + a];
-          G[j * ld + a] = (a > j) ? rp * inv : rp;
-          G[pv * ld + a] = rj;
-        } else if (a > j) {
+          double* cpa = (a < pv) ? &G[a * ld + pv] : &G[pv * ld + a];
+          const double old_j = G[j * ld + a], old_p = *cpa;
+          G[j * ld + a] = old_p * inv;
+          *cpa = old_j;
+        } else {
           G[j * ld + a] *= inv;
         }
       }
     }
     __syncthreads();
-    // Schur complement of the remaining block: S_ab -= R_ja R_jb
+    // ---- Schur complement, upper triangle: S_ab -= R_ja R_jb (j < a <= b) -----
     for (int a = j + 1 + wid; a < c; a += nw) {
       const double ra = G[j * ld + a];
-      for (int b = j + 1 + lane; b < c; b += 32) G[a * ld + b] = fma(-ra, G[j * ld + b], G[a * ld + b]);
+      for (int b2 = a + lane; b2 < c; b2 += 32) G[a * ld + b2] = fma(-ra, G[j * ld + b2], G[a * ld + b2]);
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) *rank = j;
   for (int q = threadIdx.x; q < c; q += blockDim.x) perm[q] = phys_at[q];
   for (int a = wid; a < j; a += nw)
-    for (int b = lane; b < c; b += 32) R[(int64_t)a * ldr + b] = (b < a) ? 0.0 : G[a * ld + b];
+    for (int b2 = lane; b2 < c; b2 += 32) R[(int64_t)a * ldr + b2] = (b2 < a) ? 0.0 : G[a * ld + b2];
 }
 
 // Q (p x r, row-major ldq) = M(:, perm[0:r]) R^{-1}, R upper triangular
@@ -536,7 +538,7 @@ struct LpcholState {
   int64_t cpb;                          // columns owned per block
   double* L;                            // c x kmax, by physical column
   int32_t* perm; double* R; int64_t ldr; int32_t* rank;
-  double* best_val; int32_t* best_pos; int32_t* best_phys;   // 2 x nb each
+  PivotCand* cand;                      // 2 x nb
   GridBarrier bar;
 };
 
@@ -550,14 +552,14 @@ __global__ void __launch_bounds__(kLpThreads, 1) k_lpchol(LpcholState s) {
   double* slab = lsm;                               // nown x p: owned columns
   double* xpiv = slab + s.cpb * p;                  // p: the pivot column
   double* lpiv = xpiv + p;                          // kmax: L(piv, 0:j)
-  double* red = lpiv + s.kmax;                      // nw x kLpMaxCpb partial dots
-  double* d = red + nw * kLpMaxCpb;                 // nown: remaining norms^2
-  int32_t* pos_of = reinterpret_cast<int32_t*>(d + kLpMaxCpb);
+  double* d = lpiv + s.kmax;                        // nown: remaining norms^2
+  double* lown = d + kLpMaxCpb;                     // cpb x kmax: L rows of the owned columns
+  int32_t* pos_of = reinterpret_cast<int32_t*>(lown + s.cpb * s.kmax);
   int32_t* phys_at = pos_of + s.c;
   __shared__ double sv[32];
   __shared__ int sp[32], sf[32];
   __shared__ int s_piv, s_stop;
-  __shared__ double s_dpiv, s_top;
+  __shared__ double s_ljj, s_inv, s_top;
   __shared__ unsigned char s_done[kLpMaxCpb];
 
   for (int64_t e = threadIdx.x; e < (int64_t)nown * p; e += blockDim.x) {
@@ -592,18 +594,16 @@ __global__ void __launch_bounds__(kLpThreads, 1) k_lpchol(LpcholState s) {
         const int of = __shfl_xor_sync(0xffffffffu, bf, o);
         if (pivot_better(ov, op, bv, bp)) { bv = ov; bp = op; bf = of; }
       }
-      if (lane == 0) {
-        s.best_val[buf * nb + b] = bv; s.best_pos[buf * nb + b] = bp; s.best_phys[buf * nb + b] = bf;
-      }
+      if (lane == 0) cand_store(s.cand + buf * nb + b, bv, bp, bf);
     }
   };
   // every block: the winner of buffer `buf` (block order, same result everywhere)
   auto decide = [&](int buf, int64_t j) {
     double bv = -1.0; int bp = 0x7fffffff, bf = -1;
     for (int bb = threadIdx.x; bb < nb; bb += blockDim.x) {
-      const double v = __ldcg(s.best_val + buf * nb + bb);
-      const int pp = __ldcg(s.best_pos + buf * nb + bb);
-      if (pivot_better(v, pp, bv, bp)) { bv = v; bp = pp; bf = __ldcg(s.best_phys + buf * nb + bb); }
+      double v; int pp, pf;
+      cand_load(s.cand + buf * nb + bb, v, pp, pf);
+      if (pivot_better(v, pp, bv, bp)) { bv = v; bp = pp; bf = pf; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -625,7 +625,9 @@ __global__ void __launch_bounds__(kLpThreads, 1) k_lpchol(LpcholState s) {
         const int pj = phys_at[j];
         phys_at[j] = bf; phys_at[bp] = pj;
         pos_of[bf] = (int)j; pos_of[pj] = bp;
-        s_piv = bf; s_dpiv = bv;
+        // L(piv, j) = sqrt(d_piv) and its reciprocal, once per step
+        const double y = rsqrt_newton(bv);
+        s_piv = bf; s_ljj = bv * y; s_inv = y;
         if (bf >= o_lo && bf < o_hi) s_done[bf - o_lo] = 1;
       }
     }
@@ -639,47 +641,41 @@ __global__ void __launch_bounds__(kLpThreads, 1) k_lpchol(LpcholState s) {
     decide((int)(j & 1), j);
     if (s_stop) break;
     const int piv = s_piv;
-    const double ljj = s_dpiv * rsqrt_newton(s_dpiv), inv = rsqrt_newton(s_dpiv);
+    const double ljj = s_ljj, inv = s_inv;
     // the pivot column and L(piv, 0:j)
     for (int64_t i = threadIdx.x; i < p; i += blockDim.x) xpiv[i] = __ldcg(s.Mc + (int64_t)piv * s.ldm + i);
     for (int64_t t = threadIdx.x; t < j; t += blockDim.x) lpiv[t] = __ldcg(s.L + (int64_t)piv * s.kmax + t);
     __syncthreads();
-    // raw dots m_i . m_piv for the owned columns: rows split over the block
-    double acc[kLpMaxCpb];
-#pragma unroll
-    for (int cc = 0; cc < kLpMaxCpb; ++cc) acc[cc] = 0.0;
-    for (int64_t i = threadIdx.x; i < p; i += blockDim.x) {
-      const double x = xpiv[i];
-#pragma unroll
-      for (int cc = 0; cc < kLpMaxCpb; ++cc)
-        if (cc < nown) acc[cc] = fma(x, slab[cc * p + i], acc[cc]);
-    }
-#pragma unroll
-    for (int cc = 0; cc < kLpMaxCpb; ++cc) {
-      if (cc < nown) {
-        const double a = warp_sum(acc[cc]);
-        if (lane == 0) red[wid * kLpMaxCpb + cc] = a;
-      }
-    }
-    __syncthreads();
-    // a warp per owned column: block sum of the dots, minus L(i, 0:j) L(piv, 0:j)
+    // a warp per owned column: m_i . m_piv - L(i, 0:j) L(piv, 0:j), fixed
+    // order (four interleaved partial sums per lane, then the shuffle tree)
     for (int cc = wid; cc < nown; cc += nw) {
       const int64_t ph = o_lo + cc;
-      double corr = 0.0;
-      if (!s_done[cc] || ph == piv)
-        for (int64_t t = lane; t < j; t += 32) corr = fma(__ldcg(s.L + ph * s.kmax + t), lpiv[t], corr);
+      const bool live = !s_done[cc];
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, corr = 0.0;
+      if (live) {
+        const double* col = slab + (int64_t)cc * p;
+        int64_t i = lane;
+        for (; i + 96 < p; i += 128) {
+          a0 = fma(xpiv[i], col[i], a0);
+          a1 = fma(xpiv[i + 32], col[i + 32], a1);
+          a2 = fma(xpiv[i + 64], col[i + 64], a2);
+          a3 = fma(xpiv[i + 96], col[i + 96], a3);
+        }
+        for (; i < p; i += 32) a0 = fma(xpiv[i], col[i], a0);
+        for (int64_t t = lane; t < j; t += 32) corr = fma(lown[cc * s.kmax + t], lpiv[t], corr);
+      }
+      const double g = warp_sum((a0 + a1) + (a2 + a3));
       corr = warp_sum(corr);
       if (lane == 0) {
-        double g = 0.0;
-        for (int w = 0; w < nw; ++w) g += red[w * kLpMaxCpb + cc];
         double lij;
         if (ph == piv) lij = ljj;
-        else if (s_done[cc]) lij = 0.0;
+        else if (!live) lij = 0.0;
         else {
           lij = (g - corr) * inv;
           d[cc] = fma(-lij, lij, d[cc]);
         }
         s.L[ph * s.kmax + j] = lij;
+        lown[cc * s.kmax + j] = lij;
       }
     }
     __syncthreads();
@@ -706,7 +702,7 @@ LpGeom lp_geom(int64_t p, int64_t c, int64_t kmax, int num_sms) {
   g.cpb = (c + num_sms - 1) / num_sms;
   if (g.cpb < 1) g.cpb = 1;
   g.nb = (c + g.cpb - 1) / g.cpb;
-  g.smem = sizeof(double) * (size_t)(g.cpb * p + p + kmax + (kLpThreads / 32) * kLpMaxCpb + kLpMaxCpb) +
+  g.smem = sizeof(double) * (size_t)(g.cpb * p + p + kmax + kLpMaxCpb + g.cpb * kmax) +
            sizeof(int32_t) * (size_t)(2 * c);
   return g;
 }
@@ -731,7 +727,7 @@ size_t orth_wide_ws(int64_t p, int64_t c, int num_sms) {
   b += a256(sizeof(double) * (size_t)(c * kmax));        // L
   b += a256(sizeof(double) * (size_t)(kmax * kmax));     // R
   b += a256(4 * (size_t)c) + a256(8);                    // perm, rank
-  b += 2 * a256(sizeof(double) * (size_t)(2 * g.nb)) + a256(4 * (size_t)(2 * g.nb)) + 256;   // candidates, barrier
+  b += a256(sizeof(PivotCand) * (size_t)(2 * g.nb)) + 256;   // candidates, barrier
   // then the tall-skinny tail (Q_1 and the refinement's Gram) on p x r, r <= 128
   b += orth_gram_ws(p, kLpMaxRank, num_sms);
   return b + 1024;
@@ -748,18 +744,16 @@ lrs_status launch_orth_wide(lrs_ctx* ctx, const double* M, int64_t p, int64_t c,
   double* R = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(kmax * kmax));
   int32_t* perm = (int32_t*)ws_alloc(ctx, 4 * (size_t)c);
   int32_t* rank = (int32_t*)ws_alloc(ctx, 8);
-  double* bv = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(2 * g.nb));
-  int32_t* bp = (int32_t*)ws_alloc(ctx, sizeof(double) * (size_t)(2 * g.nb));
-  int32_t* bf = (int32_t*)ws_alloc(ctx, 4 * (size_t)(2 * g.nb));
+  PivotCand* cand = (PivotCand*)ws_alloc(ctx, sizeof(PivotCand) * (size_t)(2 * g.nb));
   unsigned* bar = (unsigned*)ws_alloc(ctx, 256);
-  if (!Mc || !L || !R || !perm || !rank || !bv || !bp || !bf || !bar)
+  if (!Mc || !L || !R || !perm || !rank || !cand || !bar)
     return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (orth_wide)");
   lrs_status st = launch_transpose(ctx, M, p, c, ldm, Mc, p);
   if (st) return st;
   LpcholState s{};
   s.Mc = Mc; s.p = p; s.c = c; s.ldm = p; s.kmax = kmax; s.rtol = rtol; s.cpb = g.cpb;
   s.L = L; s.perm = perm; s.R = R; s.ldr = kmax; s.rank = rank;
-  s.best_val = bv; s.best_pos = bp; s.best_phys = bf;
+  s.cand = cand;
   LRS_CUDA_TRY(ctx, cudaMemsetAsync(bar, 0, 256, ctx->stream));
   s.bar.count = bar; s.bar.gen = bar + 1; s.bar.err = (int*)(bar + 2);
   if (g.smem > 48 * 1024)

@@ -37,73 +37,108 @@ bool grid_from_abi(const lrs_grid* g, GridDev* o, char* why, size_t nwhy) {
   return true;
 }
 
+// One thread per coarse point j and group of kSkRows snapshots: the stencil
+// offsets (32-bit: a row holds < 2^31 elements, checked on the host) are
+// computed once and reused for every snapshot of the group, whose loads are
+// independent and in flight together.  The accumulation order per value is
+// fixed (z, then y, then x), the same for every snapshot and launch shape.
+constexpr int kSkRows = 4;
+
 template <int KIND, typename OutT>
 __global__ void __launch_bounds__(256) k_sketch(const void* __restrict__ A, int32_t dt, int64_t m,
                                                 int64_t lda, GridDev g, OutT* __restrict__ Y,
                                                 int64_t ldy) {
-  const int64_t total = m * g.l;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t t = idx / g.l, j = idx - t * g.l;
-    const int64_t xc = j % g.Nc[0];
-    const int64_t yc = (j / g.Nc[0]) % g.Nc[1];
-    const int64_t zc = j / (g.Nc[0] * g.Nc[1]);
-    const int64_t cx = g.s[0] * xc + g.s[0] / 2;
-    const int64_t cy = g.s[1] * yc + g.s[1] / 2;
-    const int64_t cz = g.s[2] * zc + g.s[2] / 2;
-    const int64_t row = t * lda;
-    double acc = 0.0;
-    if (KIND == LRS_INJECT) {
-      acc = ld_f64(A, dt, row + (cz * g.N[1] + cy) * g.N[0] + cx);
-    } else if (KIND == LRS_FULLWEIGHT) {
-      const int rz = g.ndim >= 3 ? 1 : 0, ry = g.ndim >= 2 ? 1 : 0;
-      for (int dz = -rz; dz <= rz; ++dz) {
-        const int64_t z = cz + dz;
-        if (z < 0 || z >= g.N[2]) continue;
-        const double wz = g.ndim >= 3 ? (dz == 0 ? 0.5 : 0.25) : 1.0;
-        for (int dy = -ry; dy <= ry; ++dy) {
-          const int64_t y = cy + dy;
-          if (y < 0 || y >= g.N[1]) continue;
-          const double wy = g.ndim >= 2 ? (dy == 0 ? 0.5 : 0.25) : 1.0;
-          const int64_t base = row + (z * g.N[1] + y) * g.N[0];
-          for (int dx = -1; dx <= 1; ++dx) {
-            const int64_t x = cx + dx;
-            if (x < 0 || x >= g.N[0]) continue;
-            const double wx = dx == 0 ? 0.5 : 0.25;
-            acc += (wz * (wy * wx)) * ld_f64(A, dt, base + x);
+  const uint32_t l = (uint32_t)g.l, Ncx = (uint32_t)g.Nc[0], Ncy = (uint32_t)g.Nc[1];
+  const uint32_t Nx = (uint32_t)g.N[0], Ny = (uint32_t)g.N[1], Nz = (uint32_t)g.N[2];
+  const uint32_t sx = (uint32_t)g.s[0], sy = (uint32_t)g.s[1], sz = (uint32_t)g.s[2];
+  for (int64_t t0 = (int64_t)blockIdx.y * kSkRows; t0 < m; t0 += (int64_t)gridDim.y * kSkRows) {
+    const int nt = (int)min((int64_t)kSkRows, m - t0);
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < l; j += gridDim.x * blockDim.x) {
+      const uint32_t xc = j % Ncx, rest = j / Ncx;
+      const uint32_t yc = rest % Ncy, zc = rest / Ncy;
+      const uint32_t cx = sx * xc + sx / 2, cy = sy * yc + sy / 2, cz = sz * zc + sz / 2;
+      double acc[kSkRows];
+#pragma unroll
+      for (int u = 0; u < kSkRows; ++u) acc[u] = 0.0;
+      if (KIND == LRS_INJECT) {
+        const uint32_t off = (cz * Ny + cy) * Nx + cx;
+#pragma unroll
+        for (int u = 0; u < kSkRows; ++u)
+          if (u < nt) acc[u] = ld_f64(A, dt, (t0 + u) * lda + off);
+      } else if (KIND == LRS_FULLWEIGHT) {
+        const int rz = g.ndim >= 3 ? 1 : 0, ry = g.ndim >= 2 ? 1 : 0;
+        for (int dz = -rz; dz <= rz; ++dz) {
+          const int64_t z = (int64_t)cz + dz;
+          if (z < 0 || z >= Nz) continue;
+          const double wz = g.ndim >= 3 ? (dz == 0 ? 0.5 : 0.25) : 1.0;
+          for (int dy = -ry; dy <= ry; ++dy) {
+            const int64_t y = (int64_t)cy + dy;
+            if (y < 0 || y >= Ny) continue;
+            const double wy = g.ndim >= 2 ? (dy == 0 ? 0.5 : 0.25) : 1.0;
+            const uint32_t base = ((uint32_t)z * Ny + (uint32_t)y) * Nx;
+            for (int dx = -1; dx <= 1; ++dx) {
+              const int64_t x = (int64_t)cx + dx;
+              if (x < 0 || x >= Nx) continue;
+              const double w = wz * (wy * (dx == 0 ? 0.5 : 0.25));
+              const uint32_t off = base + (uint32_t)x;
+              double v[kSkRows];
+#pragma unroll
+              for (int u = 0; u < kSkRows; ++u) v[u] = u < nt ? ld_f64(A, dt, (t0 + u) * lda + off) : 0.0;
+#pragma unroll
+              for (int u = 0; u < kSkRows; ++u) acc[u] += w * v[u];
+            }
           }
         }
+      } else {  // block average
+        const double wx = 1.0 / sx, wy = g.ndim >= 2 ? 1.0 / sy : 1.0, wz = g.ndim >= 3 ? 1.0 / sz : 1.0;
+        const double w = wz * (wy * wx);
+        for (uint32_t z = sz * zc; z < sz * (zc + 1); ++z)
+          for (uint32_t y = sy * yc; y < sy * (yc + 1); ++y) {
+            const uint32_t base = (z * Ny + y) * Nx;
+            for (uint32_t x = sx * xc; x < sx * (xc + 1); ++x) {
+#pragma unroll
+              for (int u = 0; u < kSkRows; ++u)
+                if (u < nt) acc[u] += w * ld_f64(A, dt, (t0 + u) * lda + base + x);
+            }
+          }
       }
-    } else {  // block average
-      const double wx = 1.0 / g.s[0], wy = g.ndim >= 2 ? 1.0 / g.s[1] : 1.0,
-                   wz = g.ndim >= 3 ? 1.0 / g.s[2] : 1.0;
-      const double w = wz * (wy * wx);
-      for (int64_t z = g.s[2] * zc; z < g.s[2] * (zc + 1); ++z)
-        for (int64_t y = g.s[1] * yc; y < g.s[1] * (yc + 1); ++y) {
-          const int64_t base = row + (z * g.N[1] + y) * g.N[0];
-          for (int64_t x = g.s[0] * xc; x < g.s[0] * (xc + 1); ++x) acc += w * ld_f64(A, dt, base + x);
-        }
+#pragma unroll
+      for (int u = 0; u < kSkRows; ++u)
+        if (u < nt) Y[(t0 + u) * ldy + j] = (OutT)acc[u];
     }
-    Y[t * ldy + j] = (OutT)acc;
   }
 }
 
-static int grid_blocks(lrs_ctx* ctx, int64_t work, int threads) {
-  int64_t b = (work + threads - 1) / threads;
-  const int64_t cap = (int64_t)ctx->num_sms * 16;
-  if (b > cap) b = cap;
-  if (b < 1) b = 1;
-  return (int)b;
+// grid: x over coarse points (256 per block), y over groups of kSkRows
+// snapshots, about 16 blocks per SM in total
+static dim3 sketch_grid(lrs_ctx* ctx, int64_t m, int64_t l) {
+  int64_t bx = (l + 255) / 256;
+  if (bx > 4096) bx = 4096;
+  if (bx < 1) bx = 1;
+  int64_t by = ((int64_t)ctx->num_sms * 16 + bx - 1) / bx;
+  const int64_t groups = (m + kSkRows - 1) / kSkRows;
+  if (by > groups) by = groups;
+  if (by > 65535) by = 65535;
+  if (by < 1) by = 1;
+  return dim3((unsigned)bx, (unsigned)by);
+}
+
+static bool sketch_sizes_ok(lrs_ctx* ctx, const GridDev& g) {
+  if (g.n >= (int64_t)1 << 31 || g.l >= (int64_t)1 << 31) {
+    lrs_fail(ctx, LRS_EINVAL, "sketch: a snapshot of %lld points exceeds 2^31", (long long)g.n);
+    return false;
+  }
+  return true;
 }
 
 lrs_status launch_sketch(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int64_t lda,
                          const GridDev& g, double* Y, int64_t ldy) {
-  const int th = 256;
-  const int nb = grid_blocks(ctx, m * g.l, th);
+  if (!sketch_sizes_ok(ctx, g)) return LRS_EINVAL;
+  const dim3 grid = sketch_grid(ctx, m, g.l);
   switch (g.kind) {
-    case LRS_INJECT: k_sketch<LRS_INJECT, double><<<nb, th, 0, ctx->stream>>>(A, dt, m, lda, g, Y, ldy); break;
-    case LRS_FULLWEIGHT: k_sketch<LRS_FULLWEIGHT, double><<<nb, th, 0, ctx->stream>>>(A, dt, m, lda, g, Y, ldy); break;
-    default: k_sketch<LRS_BLOCKAVG, double><<<nb, th, 0, ctx->stream>>>(A, dt, m, lda, g, Y, ldy); break;
+    case LRS_INJECT: k_sketch<LRS_INJECT, double><<<grid, 256, 0, ctx->stream>>>(A, dt, m, lda, g, Y, ldy); break;
+    case LRS_FULLWEIGHT: k_sketch<LRS_FULLWEIGHT, double><<<grid, 256, 0, ctx->stream>>>(A, dt, m, lda, g, Y, ldy); break;
+    default: k_sketch<LRS_BLOCKAVG, double><<<grid, 256, 0, ctx->stream>>>(A, dt, m, lda, g, Y, ldy); break;
   }
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
@@ -121,8 +156,9 @@ lrs_status launch_gather32(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, i
                            const GridDev& g, float* W, int64_t ldw) {
   GridDev gi = g;
   gi.kind = LRS_INJECT;
-  const int nb = grid_blocks(ctx, m * gi.l, 256);
-  k_sketch<LRS_INJECT, float><<<nb, 256, 0, ctx->stream>>>(A, dt, m, lda, gi, W, ldw);
+  if (!sketch_sizes_ok(ctx, gi)) return LRS_EINVAL;
+  const dim3 grid = sketch_grid(ctx, m, gi.l);
+  k_sketch<LRS_INJECT, float><<<grid, 256, 0, ctx->stream>>>(A, dt, m, lda, gi, W, ldw);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
   return LRS_OK;

@@ -137,6 +137,8 @@ lrs_status launch_tsqr(lrs_ctx* ctx, const void* B, int b_f64, int64_t r, int64_
 // One-sided Jacobi, one block, round-robin pairing (r' = r rounded up to even
 // columns; the pad column is zero and never rotates).
 // ---------------------------------------------------------------------------
+constexpr int kJacLanes = 16;
+
 template <typename T>
 __global__ void __launch_bounds__(1024, 1)
 k_jacobi(const double* __restrict__ R, int64_t r, double* __restrict__ Vout, double* __restrict__ s_out,
@@ -162,12 +164,16 @@ k_jacobi(const double* __restrict__ R, int64_t r, double* __restrict__ Vout, dou
   // cap; eps * max(r, 16) (the column length, as in LAPACK's one-sided
   // Jacobi) sits safely above it.
   const T tol = eps * (T)(r > 16 ? r : 16);
+  // a team of kJacLanes lanes (half a warp) per pair: all pairs of a round at
+  // r <= 128 run in one pass of the block, with a 4-level shuffle tree
+  const int lg = threadIdx.x % kJacLanes, grp = threadIdx.x / kJacLanes, ngrp = blockDim.x / kJacLanes;
+  const unsigned gmask = ((1u << kJacLanes) - 1u) << (lane & (32 - kJacLanes));
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
     for (int64_t round = 0; round < rp - 1; ++round) {
       // round-robin: slot 0 fixed, others rotate; pairs (slot a, slot rp-1-a)
-      for (int64_t pr = wid; pr < rp / 2; pr += nw) {
+      for (int64_t pr = grp; pr < rp / 2; pr += ngrp) {
         const int64_t sa = pr, sb = rp - 1 - pr;
         auto slot = [&](int64_t sidx) -> int64_t {
           if (sidx == 0) return 0;
@@ -178,23 +184,26 @@ k_jacobi(const double* __restrict__ R, int64_t r, double* __restrict__ Vout, dou
         if (q >= r) continue;                        // the zero pad column
         T* wp = Wc + p * r; T* wq = Wc + q * r;
         T a = T(0), b = T(0), g = T(0);
-        for (int64_t i = lane; i < r; i += 32) {
+        for (int64_t i = lg; i < r; i += kJacLanes) {
           a = fma(wp[i], wp[i], a); b = fma(wq[i], wq[i], b); g = fma(wp[i], wq[i], g);
         }
-        a = warp_sum(a); b = warp_sum(b); g = warp_sum(g);
+#pragma unroll
+        for (int o = kJacLanes / 2; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(gmask, a, o); b += __shfl_xor_sync(gmask, b, o); g += __shfl_xor_sync(gmask, g, o);
+        }
         if (fabs(g) <= tol * (sqrt(a) * sqrt(b)) || g == T(0)) continue;
         const T zeta = (b - a) / (T(2) * g);
         const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
         const T cs = T(1) / sqrt(T(1) + t * t);
         const T sn = cs * t;
-        for (int64_t i = lane; i < r; i += 32) {
+        for (int64_t i = lg; i < r; i += kJacLanes) {
           const T x = wp[i], y = wq[i];
           wp[i] = cs * x - sn * y; wq[i] = sn * x + cs * y;
           T* vp = Vc + p * r; T* vq = Vc + q * r;
           const T u = vp[i], w = vq[i];
           vp[i] = cs * u - sn * w; vq[i] = sn * u + cs * w;
         }
-        if (lane == 0) atomicAdd(&s_rot, 1);
+        if (lg == 0) atomicAdd(&s_rot, 1);
       }
       __syncthreads();
     }
