@@ -18,6 +18,31 @@ __device__ __forceinline__ double ld_f64(const void* p, int32_t dt, int64_t i) {
   return (double)__uint_as_float(((unsigned)b) << 16);
 }
 
+// FP32 -> FP64 widening on the integer pipe: for a normal number the double
+// has the same sign, the exponent rebiased by 1023 - 127 = 896 and the 23
+// mantissa bits shifted up by 29 -- exact, the value the conversion
+// instruction gives.  +-0 is built the same way; subnormals, infinities and
+// NaN take the conversion instruction.  Keeps stencil loads off this part's
+// narrow FP64 pipe, which the conversion instruction would otherwise share
+// with the accumulation.
+__device__ __forceinline__ double widen_f32(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+  if (e - 1u < 254u)
+    return __longlong_as_double((long long)(sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(u & 0x7fffffu) << 29)));
+  if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)sign);
+  return (double)f;
+}
+
+// element i of A_f widened to double, conversions on the integer pipe
+__device__ __forceinline__ double ld_wide(const void* p, int32_t dt, int64_t i) {
+  if (dt == LRS_F64) return __ldg(reinterpret_cast<const double*>(p) + i);
+  if (dt == LRS_F32) return widen_f32(__ldg(reinterpret_cast<const float*>(p) + i));
+  const unsigned short b = __ldg(reinterpret_cast<const unsigned short*>(p) + i);
+  return widen_f32(__uint_as_float(((unsigned)b) << 16));
+}
+
 __device__ __forceinline__ size_t dtype_size(int32_t dt) {
   return dt == LRS_F64 ? 8 : (dt == LRS_F32 ? 4 : 2);
 }
@@ -101,16 +126,20 @@ __device__ __forceinline__ T block_sum(T v, T* red) {
 // Grid barrier with a bounded wait.
 //
 // Used only by kernels launched with cudaLaunchCooperativeKernel, which
-// guarantees that all blocks are co-resident.  Thread 0 of each block reads
-// the generation, fences, counts itself in; the last arrival resets the count
-// and bumps the generation, the others poll the generation.  Each wait gives
-// up after kSpinLimit polls (about a second), records LRS_ETIMEOUT in *err
-// and returns false; every block then leaves the kernel at its next barrier,
-// so a lost arrival never hangs the GPU.
+// guarantees that all blocks are co-resident.  *count only grows (zeroed
+// before the launch): thread 0 of each block arrives with one release-add,
+// whose old value tells it which barrier this is (old / gridDim.x), and then
+// polls with acquire loads until the count reaches the end of that barrier.
+// The release orders every write the block made before the barrier (the
+// block barrier before it gathers them to thread 0); the acquire and the
+// block barrier after it order every read that follows.  Each wait gives up
+// after kSpinLimit polls (about a second), records LRS_ETIMEOUT in *err and
+// returns false; every block then leaves the kernel at its next barrier, so a
+// lost arrival never hangs the GPU.
 // ---------------------------------------------------------------------------
 struct GridBarrier {
-  unsigned int* count;   // arrivals in the current generation
-  unsigned int* gen;     // generation counter
+  unsigned int* count;   // arrivals so far (all barriers of the launch)
+  unsigned int* gen;     // unused (kept for the buffer layout)
   int* err;              // 0 = ok, else an lrs_status
 };
 
@@ -121,6 +150,11 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ unsigned atom_add_release_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
 __device__ __forceinline__ int ld_volatile_s32(const int* p) {
   return *reinterpret_cast<const volatile int*>(p);
 }
@@ -128,22 +162,14 @@ __device__ __forceinline__ int ld_volatile_s32(const int* p) {
 __device__ __forceinline__ bool grid_sync(const GridBarrier& b) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned g = ld_acquire_u32(b.gen);
-    __threadfence();
-    const unsigned arrived = atomicAdd(b.count, 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(b.count, 0u);
-      __threadfence();
-      atomicAdd(b.gen, 1u);
-    } else {
-      long long it = 0;
-      while (ld_acquire_u32(b.gen) == g) {
-        if (((++it) & 63) == 0 && ld_volatile_s32(b.err) != 0) break;
-        if (it > kSpinLimit) { atomicCAS(b.err, 0, (int)LRS_ETIMEOUT); break; }
-        if (it > 256) __nanosleep(20);
-      }
+    const unsigned old = atom_add_release_u32(b.count, 1u);
+    const unsigned target = (old / gridDim.x + 1u) * gridDim.x;
+    long long it = 0;
+    while ((int)(ld_acquire_u32(b.count) - target) < 0) {
+      if (((++it) & 63) == 0 && ld_volatile_s32(b.err) != 0) break;
+      if (it > kSpinLimit) { atomicCAS(b.err, 0, (int)LRS_ETIMEOUT); break; }
+      if (it > 256) __nanosleep(20);
     }
-    __threadfence();
   }
   __syncthreads();
   return ld_volatile_s32(b.err) == 0;

@@ -201,10 +201,12 @@ __global__ void __launch_bounds__(256) k_pchol(const double* __restrict__ Gin, i
 
 // Q (p x r, row-major ldq) = M(:, perm[0:r]) R^{-1}, R upper triangular
 // (r x r leading block of the ldr-strided R).  A team of T threads (T = 1..32,
-// a power of two) solves one row: for each unknown j the team splits the dot
-// q[0:j] . R[0:j, j] by t mod T and reduces it with shuffles, so p * T threads
-// keep every SM's FP64 units busy even when p is small.  The block's rows of
-// Q live in shared memory during the substitution.  perm may be NULL.
+// a power of two) solves one row q R = m right-looking: lane t mod T owns
+// unknowns t; at step j the owner of j finishes q_j = m_j / R_jj and hands it
+// to the team with one shuffle, and every lane subtracts q_j R_jt from its own
+// unknowns t > j.  No FP64 reduction across lanes, so p * T threads keep every
+// SM's FP64 units on useful work even when p is small.  The block's rows live
+// in shared memory during the substitution.  perm may be NULL.
 __global__ void __launch_bounds__(256) k_trsm_rows(const double* __restrict__ M, int64_t p, int64_t ldm,
                                                    const int32_t* __restrict__ perm,
                                                    const double* __restrict__ R, int64_t ldr, int r, int T,
@@ -228,13 +230,18 @@ __global__ void __launch_bounds__(256) k_trsm_rows(const double* __restrict__ M,
   const int lane = threadIdx.x & 31;
   const int tm = threadIdx.x & (T - 1);
   const unsigned tmask = (T == 32 ? 0xffffffffu : ((1u << T) - 1u)) << (lane & ~(T - 1));
+  const int base = lane & ~(T - 1);
   double* q = qs + (threadIdx.x / T) * ld;
   for (int jx = 0; jx < r; ++jx) {
-    double a = 0.0;
-    for (int t = tm; t < jx; t += T) a = fma(q[t], Rs[t * r + jx], a);
-    for (int o = 1; o < T; o <<= 1) a += __shfl_xor_sync(tmask, a, o);
-    if (tm == 0) q[jx] = (q[jx] - a) * dinv[jx];
-    __syncwarp(tmask);
+    const int owner = jx & (T - 1);
+    double qj = 0.0;
+    if (tm == owner) { qj = q[jx] * dinv[jx]; q[jx] = qj; }
+    qj = __shfl_sync(tmask, qj, base + owner);
+    const double* Rrow = Rs + jx * r;
+    // unknowns t > jx owned by this lane: t = tm, tm + T, ...
+    int t = tm + ((jx + 1 - tm + T - 1) / T) * T;
+    if (jx + 1 <= tm) t = tm;
+    for (; t < r; t += T) q[t] = fma(-qj, Rrow[t], q[t]);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < rows * r; e += blockDim.x) {

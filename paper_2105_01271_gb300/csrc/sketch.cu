@@ -64,7 +64,12 @@ __global__ void __launch_bounds__(256) k_sketch(const void* __restrict__ A, int3
         const uint32_t off = (cz * Ny + cy) * Nx + cx;
 #pragma unroll
         for (int u = 0; u < kSkRows; ++u)
-          if (u < nt) acc[u] = ld_f64(A, dt, (t0 + u) * lda + off);
+          if (u < nt) {
+            // an FP32 output takes the value straight through (the compiler
+            // folds the widening away); an FP64 one widens on the integer pipe
+            if (sizeof(OutT) == 4) acc[u] = ld_f64(A, dt, (t0 + u) * lda + off);
+            else acc[u] = ld_wide(A, dt, (t0 + u) * lda + off);
+          }
       } else if (KIND == LRS_FULLWEIGHT) {
         const int rz = g.ndim >= 3 ? 1 : 0, ry = g.ndim >= 2 ? 1 : 0;
         for (int dz = -rz; dz <= rz; ++dz) {
@@ -83,7 +88,7 @@ __global__ void __launch_bounds__(256) k_sketch(const void* __restrict__ A, int3
               const uint32_t off = base + (uint32_t)x;
               double v[kSkRows];
 #pragma unroll
-              for (int u = 0; u < kSkRows; ++u) v[u] = u < nt ? ld_f64(A, dt, (t0 + u) * lda + off) : 0.0;
+              for (int u = 0; u < kSkRows; ++u) v[u] = u < nt ? ld_wide(A, dt, (t0 + u) * lda + off) : 0.0;
 #pragma unroll
               for (int u = 0; u < kSkRows; ++u) acc[u] += w * v[u];
             }
@@ -98,7 +103,7 @@ __global__ void __launch_bounds__(256) k_sketch(const void* __restrict__ A, int3
             for (uint32_t x = sx * xc; x < sx * (xc + 1); ++x) {
 #pragma unroll
               for (int u = 0; u < kSkRows; ++u)
-                if (u < nt) acc[u] += w * ld_f64(A, dt, (t0 + u) * lda + base + x);
+                if (u < nt) acc[u] += w * ld_wide(A, dt, (t0 + u) * lda + base + x);
             }
           }
       }

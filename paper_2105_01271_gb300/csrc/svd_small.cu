@@ -167,24 +167,27 @@ k_jacobi(const double* __restrict__ R, int64_t r, double* __restrict__ Vout, dou
   // a team of kJacLanes lanes (half a warp) per pair: all pairs of a round at
   // r <= 128 run in one pass of the block, with a 4-level shuffle tree
   const int lg = threadIdx.x % kJacLanes, grp = threadIdx.x / kJacLanes, ngrp = blockDim.x / kJacLanes;
+  const int ri = (int)r, rpi = (int)rp;
   const unsigned gmask = ((1u << kJacLanes) - 1u) << (lane & (32 - kJacLanes));
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
-    for (int64_t round = 0; round < rp - 1; ++round) {
+    for (int round = 0; round < rpi - 1; ++round) {
       // round-robin: slot 0 fixed, others rotate; pairs (slot a, slot rp-1-a)
-      for (int64_t pr = grp; pr < rp / 2; pr += ngrp) {
-        const int64_t sa = pr, sb = rp - 1 - pr;
-        auto slot = [&](int64_t sidx) -> int64_t {
+      for (int pr = grp; pr < rpi / 2; pr += ngrp) {
+        const int sa = pr, sb = rpi - 1 - pr;
+        auto slot = [&](int sidx) -> int {
           if (sidx == 0) return 0;
-          return 1 + ((sidx - 1 + round) % (rp - 1));
+          int v = sidx - 1 + round;                  // < 2 (rp - 1): one conditional subtract
+          if (v >= rpi - 1) v -= rpi - 1;
+          return 1 + v;
         };
-        int64_t p = slot(sa), q = slot(sb);
-        if (p > q) { const int64_t tmp = p; p = q; q = tmp; }
-        if (q >= r) continue;                        // the zero pad column
-        T* wp = Wc + p * r; T* wq = Wc + q * r;
+        int p = slot(sa), q = slot(sb);
+        if (p > q) { const int tmp = p; p = q; q = tmp; }
+        if (q >= ri) continue;                       // the zero pad column
+        T* wp = Wc + p * ri; T* wq = Wc + q * ri;
         T a = T(0), b = T(0), g = T(0);
-        for (int64_t i = lg; i < r; i += kJacLanes) {
+        for (int i = lg; i < ri; i += kJacLanes) {
           a = fma(wp[i], wp[i], a); b = fma(wq[i], wq[i], b); g = fma(wp[i], wq[i], g);
         }
 #pragma unroll
@@ -196,10 +199,10 @@ k_jacobi(const double* __restrict__ R, int64_t r, double* __restrict__ Vout, dou
         const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
         const T cs = T(1) / sqrt(T(1) + t * t);
         const T sn = cs * t;
-        for (int64_t i = lg; i < r; i += kJacLanes) {
+        for (int i = lg; i < ri; i += kJacLanes) {
           const T x = wp[i], y = wq[i];
           wp[i] = cs * x - sn * y; wq[i] = sn * x + cs * y;
-          T* vp = Vc + p * r; T* vq = Vc + q * r;
+          T* vp = Vc + p * ri; T* vq = Vc + q * ri;
           const T u = vp[i], w = vq[i];
           vp[i] = cs * u - sn * w; vq[i] = sn * u + cs * w;
         }
