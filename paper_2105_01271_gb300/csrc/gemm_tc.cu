@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(256) k_prep_x(const void* __restrict__ X, int3
 struct TcParams {
   int64_t M, N, K;
   const uint8_t* Xp;        // pre-split X pieces
+  const uint8_t* Ap;        // pre-split A pieces (same image layout, by (nt, kt)); NULL: split in the CTA
   const void* A; int32_t adt; int64_t lda;
   void* C; int c_f64; int c_trans; int64_t ldc;
   double alpha;
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcParams P) {
       const int64_t n = nt * TBN + nl;
       int64_t kt_lo, kt_hi;
       kt_range(tile, kt_lo, kt_hi);
-      if (!have_cur) {
+      if (!have_cur && !P.Ap) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int64_t k0 = kt_lo * TBK + (int64_t)(ch + 2 * i) * 8;
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcParams P) {
           else load_a8<ADT>(P.A, P.lda, k0, P.K, n, P.N, cur[i]);
         }
       }
-      for (int64_t kt = kt_lo; kt < kt_hi; ++kt, ++it) {
+      for (int64_t kt = kt_lo; kt < kt_hi && !P.Ap; ++kt, ++it) {
         // prefetch the next slab (next k-tile of this tile, or the first of the next tile)
         VT nxt[4][8];
         const bool last = (kt + 1 == kt_hi);
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcParams P) {
         for (int64_t kt = kt_lo; kt < kt_hi; ++kt, ++it) {
           const int s = (int)(it % NS);
           const uint32_t ph = (uint32_t)((it / NS) & 1);
-          if (!mbar_wait(&full_x[s], ph, P.err) || !mbar_wait(&full_a[s], ph, P.err)) { ok = false; break; }
+          if (!mbar_wait(&full_x[s], ph, P.err) || (!P.Ap && !mbar_wait(&full_a[s], ph, P.err))) { ok = false; break; }
           tc_fence_after();
           const uint32_t a0 = smem_u32(smem + (size_t)s * Cfg::kStageBytes);   // A-data pieces (UMMA B)
           const uint32_t x0 = a0 + SA * kPieceBytes;                           // X pieces (UMMA A)
@@ -361,7 +362,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcParams P) {
     if (lane == 0) {
       int64_t it = 0;
       for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t mt = (tile / P.Nt) % P.Mt;
+        const int64_t mt = (tile / P.Nt) % P.Mt, nt = tile % P.Nt;
         int64_t kt_lo, kt_hi;
         kt_range(tile, kt_lo, kt_hi);
         bool ok = true;
@@ -371,7 +372,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcParams P) {
           if (!mbar_wait(&empty[s], ph ^ 1u, P.err)) { ok = false; break; }
           uint8_t* xdst = smem + (size_t)s * Cfg::kStageBytes + SA * kPieceBytes;
           const uint8_t* xsrc = P.Xp + ((mt * P.Kt + kt) * SX) * (int64_t)kPieceBytes;
-          mbar_arrive_expect_tx(&full_x[s], SX * kPieceBytes);
+          if (P.Ap) {
+            // both operands pre-split: one barrier completes on both copies
+            uint8_t* adst = smem + (size_t)s * Cfg::kStageBytes;
+            const uint8_t* asrc = P.Ap + ((nt * P.Kt + kt) * SA) * (int64_t)kPieceBytes;
+            mbar_arrive_expect_tx(&full_x[s], (SX + SA) * kPieceBytes);
+            bulk_g2s(adst, asrc, SA * kPieceBytes, &full_x[s]);
+          } else {
+            mbar_arrive_expect_tx(&full_x[s], SX * kPieceBytes);
+          }
           bulk_g2s(xdst, xsrc, SX * kPieceBytes, &full_x[s]);
         }
         if (!ok) {
@@ -433,6 +442,9 @@ template <int ADT, int SA, int SX>
 static lrs_status run_tc(lrs_ctx* ctx, const GemmArgs& a, double* fro2_out) {
   constexpr int NS = (SA + SX) <= 4 ? 3 : 2;
   using Cfg = TcCfg<ADT, SA, SX, NS>;
+  // everything taken from the workspace below is dead once the launches are
+  // queued (one stream): give it back on return
+  const size_t ws_mark = ctx->ws_top;
   TcParams P{};
   P.M = a.M; P.N = a.N; P.K = a.K;
   P.A = a.A; P.adt = a.adt; P.lda = a.lda;
@@ -459,6 +471,21 @@ static lrs_status run_tc(lrs_ctx* ctx, const GemmArgs& a, double* fro2_out) {
   }
   P.Xp = Xp;
   P.err = err;
+  // with two or more row tiles every CTA row would split the same A slabs
+  // again: split A once into the same image (when the workspace has room)
+  P.Ap = nullptr;
+  if (P.Mt >= 2 && !fro2_out) {
+    const size_t abytes = (size_t)(P.Nt * P.Kt * SA) * kPieceBytes;
+    uint8_t* Ap = (uint8_t*)ws_alloc(ctx, abytes);
+    if (Ap) {
+      const int64_t total = P.Nt * P.Kt * TBM * 8;
+      int64_t nb = (total + 255) / 256;
+      if (nb > (int64_t)ctx->num_sms * 32) nb = (int64_t)ctx->num_sms * 32;
+      k_prep_x<SA><<<(unsigned)nb, 256, 0, ctx->stream>>>(a.A, a.adt, a.lda, a.K, a.N, P.Nt, P.Kt, Ap);
+      ctx->launches++;
+      P.Ap = Ap;
+    }
+  }
   double* part = nullptr;
   if (fro2_out) {
     if (P.Mt != 1) return lrs_fail(ctx, LRS_EINVAL, "gemm: fused ||A||^2 needs M <= %d", TBM);
@@ -490,7 +517,14 @@ static lrs_status run_tc(lrs_ctx* ctx, const GemmArgs& a, double* fro2_out) {
   LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 16, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   if (h[16] != 0) return lrs_fail(ctx, LRS_ETIMEOUT, "tensor-core gemm: a pipeline wait gave up");
+  ctx->ws_top = ws_mark;
   return LRS_OK;
+}
+
+size_t gemm_tc_a_workspace(int64_t N, int64_t K, int prec) {
+  const int64_t Nt = (N + TBN - 1) / TBN, Kt = (K + TBK - 1) / TBK;
+  const int sa = prec == LRS_PREC_BF16X3 ? 3 : 2;
+  return (size_t)(Nt * Kt * sa) * kPieceBytes + 512;
 }
 
 size_t gemm_tc_workspace(int64_t M, int64_t K, int prec) {

@@ -95,6 +95,9 @@ size_t apass_workspace(int64_t M, int64_t K, int prec);
 lrs_status launch_apass(lrs_ctx* ctx, const GemmArgs& a, int prec, double* fro2_out);
 // workspace bytes the tensor-core path needs for an M x K operand X (0 for SIMT modes)
 size_t gemm_tc_workspace(int64_t M, int64_t K, int prec);
+// extra workspace that lets the generic tensor-core product split its K x N
+// operand A once instead of once per row tile (used when available)
+size_t gemm_tc_a_workspace(int64_t N, int64_t K, int prec);
 // extra workspace of the split-K partial sums for an M x N x K product (0 when not split)
 size_t gemm_tc_splitk_workspace(int64_t M, int64_t N, int64_t K, int num_sms);
 

@@ -336,8 +336,10 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
     if (tc) {
       // either operand may be the prepared one (the narrow one when it is <= 256 wide)
       const size_t t1 = gemm_tc_workspace(nI > wmax ? nI : wmax, m, prec) +
-                        gemm_tc_splitk_workspace(nI > wmax ? nI : wmax, nI > wmax ? nI : wmax, m, ctx->num_sms);
-      const size_t t2 = gemm_tc_workspace(wmax, nI, prec) + gemm_tc_splitk_workspace(wmax, wmax, nI, ctx->num_sms);
+                        gemm_tc_splitk_workspace(nI > wmax ? nI : wmax, nI > wmax ? nI : wmax, m, ctx->num_sms) +
+                        gemm_tc_a_workspace(nI > wmax ? nI : wmax, m, prec);
+      const size_t t2 = gemm_tc_workspace(wmax, nI, prec) + gemm_tc_splitk_workspace(wmax, wmax, nI, ctx->num_sms) +
+                        gemm_tc_a_workspace(wmax, nI, prec);
       const size_t t = (t1 > t2 ? t1 : t2) + 4096;
       if (t > inner) inner = t;
     }
