@@ -845,7 +845,8 @@ def run_ours(args, rank, world):
                  "ms_covers": "the whole lrs_gemm_tn call (X split, kernel, status read-back)",
                  "r": r, "hbm_gbs_achieved": gbs, "hbm_frac": gbs / hbm_peak})
 
-    # ---- the step's largest kernel by time: the FP64 pivoted QR (row ID call) ----
+    # ---- the step's largest kernel by time: the FP64 pivoted QR (row ID call; the
+    # ms covers the whole lrs_id_k call: transpose, CPQR, coefficients) ----
     with torch.cuda.stream(stream):
         h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         h0.record(stream)
@@ -857,7 +858,7 @@ def run_ours(args, rank, world):
     # CPQR of the l x m transpose, k steps: update + norm + dot = 3 FMA per remaining element
     pq, cq = w.grid.l, w.m
     cpqr_flops = sum(6.0 * (pq - j) * (cq - j) for j in range(min(w.k, pq, cq)))
-    roof_qr = {"bound": "alu", "kernel": "pivoted QR of the sketch (k_cpqr via lrs_id_k)",
+    roof_qr = {"bound": "alu", "kernel": "pivoted QR of the sketch (k_cpqr_cols via lrs_id_k)",
                "achieved": cpqr_flops / (id_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                "unit": "TFLOP/s (FP64)", "ms": id_ms, "algorithmic_flops": cpqr_flops,
                "peak_source": "nominal FP64 from unit counts: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
