@@ -536,16 +536,36 @@ __global__ void __launch_bounds__(kColsThreads, 1) k_cpqr_cols(CpqrColsState s) 
       double a = 0.0;
       if (!done[cc]) {
         double* col = slab + (int64_t)cc * p;
-        double d = 0.0;
-        for (int64_t i = j + lane; i < p; i += 32) d = fma(vv[i], col[i], d);
-        d = warp_sum(d);
-        const double tw = 2.0 * d;
-        for (int64_t i = j + lane; i < p; i += 32) {
+        // four interleaved partial sums per lane (the FP64 latency chains)
+        double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+        int64_t i = j + lane;
+        for (; i + 96 < p; i += 128) {
+          d0 = fma(vv[i], col[i], d0);
+          d1 = fma(vv[i + 32], col[i + 32], d1);
+          d2 = fma(vv[i + 64], col[i + 64], d2);
+          d3 = fma(vv[i + 96], col[i + 96], d3);
+        }
+        for (; i < p; i += 32) d0 = fma(vv[i], col[i], d0);
+        const double tw = 2.0 * warp_sum((d0 + d1) + (d2 + d3));
+        if (lane == 0) {                              // row j of R
+          const double x = fma(-tw, vv[j], col[j]);
+          col[j] = x;
+          s.Rphys[j * s.c + o_lo + cc] = x;
+        }
+        double n0 = 0.0, n1 = 0.0, n2 = 0.0, n3 = 0.0;
+        i = j + 1 + lane;
+        for (; i + 96 < p; i += 128) {
+          const double x0 = fma(-tw, vv[i], col[i]), x1 = fma(-tw, vv[i + 32], col[i + 32]);
+          const double x2 = fma(-tw, vv[i + 64], col[i + 64]), x3 = fma(-tw, vv[i + 96], col[i + 96]);
+          col[i] = x0; col[i + 32] = x1; col[i + 64] = x2; col[i + 96] = x3;
+          n0 = fma(x0, x0, n0); n1 = fma(x1, x1, n1); n2 = fma(x2, x2, n2); n3 = fma(x3, x3, n3);
+        }
+        for (; i < p; i += 32) {
           const double x = fma(-tw, vv[i], col[i]);
           col[i] = x;
-          if (i > j) a = fma(x, x, a);
-          else s.Rphys[j * s.c + o_lo + cc] = x;
+          n0 = fma(x, x, n0);
         }
+        a = (n0 + n1) + (n2 + n3);
       }
       a = warp_sum(a);
       if (lane == 0) nrm2[cc] = a;

@@ -58,9 +58,9 @@ lrs_status launch_gather(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int
                          const GridDev& g, double* W, int64_t ldw);
 // *out = sum of part[0..np) (device, one block, fixed order)
 lrs_status launch_sum(lrs_ctx* ctx, const double* part, int np, double* out);
-// W32[m x |I|] (FP32) = A(:, I): the same subsample stored in FP32 (tensor-core operands)
-lrs_status launch_gather32(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int64_t lda,
-                           const GridDev& g, float* W, int64_t ldw);
+// W (m x |I|) and W^T (|I| x m), FP32, from one pass over A
+lrs_status launch_gather32_both(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int64_t lda,
+                                const GridDev& g, float* W, int64_t ldw, float* WT, int64_t ldwt);
 // sum of squares of A (m x n), FP64, into *out (device)
 lrs_status launch_fro2(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int64_t n,
                        int64_t lda, double* out);

@@ -367,9 +367,7 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
   const size_t mark = ctx->ws_top;
   const int32_t wdt = tc ? LRS_F32 : LRS_F64;
   if (tc) {
-    st = launch_gather32(ctx, A, dtype, m, lda, gg, (float*)W, nI);
-    if (st) return st;
-    st = launch_transpose32(ctx, (const float*)W, m, nI, nI, (float*)WT, m);
+    st = launch_gather32_both(ctx, A, dtype, m, lda, gg, (float*)W, nI, (float*)WT, m);
   } else {
     st = launch_gather(ctx, A, dtype, m, lda, gg, (double*)W, nI);
     if (st) return st;

@@ -80,16 +80,30 @@ __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__
   }
 }
 
-// G (c x c, full symmetric, row-major) = sum over blocks, in block order
+// G (c x c, full symmetric, row-major) = sum over the nb block partials: a
+// warp per packed entry, lanes over blocks (four loads in flight each), then a
+// fixed shuffle tree -- the same order in every run.
 __global__ void k_gram_reduce(const double* __restrict__ part, int nb, int c, double* __restrict__ G) {
   const int ntri = c * (c + 1) / 2;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ntri; e += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * ntri + e];
-    int i, j;
-    tri_ij(e, c, i, j);
-    G[i * c + j] = s;
-    G[j * c + i] = s;
+  const int lane = threadIdx.x & 31;
+  const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwt = (gridDim.x * blockDim.x) >> 5;
+  for (int e = w0; e < ntri; e += nwt) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int b = lane;
+    for (; b + 96 < nb; b += 128) {
+      a0 += part[(int64_t)b * ntri + e];
+      a1 += part[(int64_t)(b + 32) * ntri + e];
+      a2 += part[(int64_t)(b + 64) * ntri + e];
+      a3 += part[(int64_t)(b + 96) * ntri + e];
+    }
+    for (; b < nb; b += 32) a0 += part[(int64_t)b * ntri + e];
+    const double sum = warp_sum((a0 + a1) + (a2 + a3));
+    if (lane == 0) {
+      int i, j;
+      tri_ij(e, c, i, j);
+      G[i * c + j] = sum;
+      G[j * c + i] = sum;
+    }
   }
 }
 
@@ -266,7 +280,7 @@ lrs_status gram(lrs_ctx* ctx, const double* M, int64_t p, int c, int64_t ldm, do
   else if (per <= 24) k_gram_partial<24><<<(unsigned)nb, 256, dyn, ctx->stream>>>(M, p, c, ldm, rows_b, part);
   else k_gram_partial<33><<<(unsigned)nb, 256, dyn, ctx->stream>>>(M, p, c, ldm, rows_b, part);
   ctx->launches++;
-  k_gram_reduce<<<(ntri + 255) / 256, 256, 0, ctx->stream>>>(part, (int)nb, c, G);
+  k_gram_reduce<<<(ntri + 7) / 8, 256, 0, ctx->stream>>>(part, (int)nb, c, G);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
   return LRS_OK;
@@ -386,16 +400,25 @@ __global__ void __launch_bounds__(256) k_gram_df(const float* __restrict__ B, in
   }
 }
 
-// G (r x r, FP64) = sum over blocks in block order; entry (i, j) is read from
-// the upper tile that holds it
+// G (r x r, FP64) = sum over the block partials; entry (i, j) is read from
+// the upper tile that holds it.  A warp per entry, lanes over blocks, fixed
+// shuffle tree (deterministic).
 __global__ void k_gram_df_reduce(const float* __restrict__ hi, const float* __restrict__ lo, int nb, int r,
                                  double* __restrict__ G) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwt = (gridDim.x * blockDim.x) >> 5;
+  for (int e = w0; e < r * r; e += nwt) {
     const int i = e / r, j = e - i * r;
     const int src = (i / 4 <= j / 4) ? e : j * r + i;
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += (double)hi[(int64_t)b * r * r + src] + (double)lo[(int64_t)b * r * r + src];
-    G[e] = s;
+    double a0 = 0.0, a1 = 0.0;
+    int b = lane;
+    for (; b + 32 < nb; b += 64) {
+      a0 += (double)hi[(int64_t)b * r * r + src] + (double)lo[(int64_t)b * r * r + src];
+      a1 += (double)hi[(int64_t)(b + 32) * r * r + src] + (double)lo[(int64_t)(b + 32) * r * r + src];
+    }
+    for (; b < nb; b += 32) a0 += (double)hi[(int64_t)b * r * r + src] + (double)lo[(int64_t)b * r * r + src];
+    const double sum = warp_sum(a0 + a1);
+    if (lane == 0) G[e] = sum;
   }
 }
 
@@ -488,7 +511,7 @@ lrs_status launch_gram_df(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, in
   else if (tpt <= 2) k_gram_df<2><<<(unsigned)nb, 256, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
   else k_gram_df<3><<<(unsigned)nb, 256, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
   ctx->launches++;
-  k_gram_df_reduce<<<(ri * ri + 255) / 256, 256, 0, ctx->stream>>>(hi, lo, (int)nb, ri, G);
+  k_gram_df_reduce<<<(ri * ri + 7) / 8, 256, 0, ctx->stream>>>(hi, lo, (int)nb, ri, G);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
   return LRS_OK;

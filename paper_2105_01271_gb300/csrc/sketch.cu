@@ -150,6 +150,63 @@ lrs_status launch_sketch(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int
   return LRS_OK;
 }
 
+// W = A_f(:, I) and its transpose W^T in one pass (FP32 outputs): a thread
+// takes one subsample point j and 8 consecutive snapshots, writes W[t, j]
+// (coalesced over j) and the 8 values W^T[j, t0..t0+7] as 32 contiguous
+// bytes (two 16-byte stores when the row stride and base allow).
+constexpr int kGtRows = 8;
+
+__global__ void __launch_bounds__(256) k_gather_both(const void* __restrict__ A, int32_t dt, int64_t m,
+                                                     int64_t lda, GridDev g, float* __restrict__ W, int64_t ldw,
+                                                     float* __restrict__ WT, int64_t ldwt, int vec) {
+  const uint32_t l = (uint32_t)g.l, Ncx = (uint32_t)g.Nc[0], Ncy = (uint32_t)g.Nc[1];
+  const uint32_t Nx = (uint32_t)g.N[0], Ny = (uint32_t)g.N[1];
+  const uint32_t sx = (uint32_t)g.s[0], sy = (uint32_t)g.s[1], sz = (uint32_t)g.s[2];
+  for (int64_t t0 = (int64_t)blockIdx.y * kGtRows; t0 < m; t0 += (int64_t)gridDim.y * kGtRows) {
+    const int nt = (int)min((int64_t)kGtRows, m - t0);
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < l; j += gridDim.x * blockDim.x) {
+      const uint32_t xc = j % Ncx, rest = j / Ncx;
+      const uint32_t yc = rest % Ncy, zc = rest / Ncy;
+      const uint32_t off = ((sz * zc + sz / 2) * Ny + (sy * yc + sy / 2)) * Nx + (sx * xc + sx / 2);
+      float v[kGtRows];
+#pragma unroll
+      for (int u = 0; u < kGtRows; ++u) v[u] = u < nt ? (float)ld_f64(A, dt, (t0 + u) * lda + off) : 0.f;
+#pragma unroll
+      for (int u = 0; u < kGtRows; ++u)
+        if (u < nt) W[(t0 + u) * ldw + j] = v[u];
+      float* dst = WT + (int64_t)j * ldwt + t0;
+      if (vec && nt == kGtRows) {
+        reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+        reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < kGtRows; ++u)
+          if (u < nt) dst[u] = v[u];
+      }
+    }
+  }
+}
+
+lrs_status launch_gather32_both(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int64_t lda,
+                                const GridDev& g, float* W, int64_t ldw, float* WT, int64_t ldwt) {
+  GridDev gi = g;
+  gi.kind = LRS_INJECT;
+  if (!sketch_sizes_ok(ctx, gi)) return LRS_EINVAL;
+  int64_t bx = (gi.l + 255) / 256;
+  if (bx > 4096) bx = 4096;
+  if (bx < 1) bx = 1;
+  int64_t by = ((int64_t)ctx->num_sms * 16 + bx - 1) / bx;
+  const int64_t groups = (m + kGtRows - 1) / kGtRows;
+  if (by > groups) by = groups;
+  if (by > 65535) by = 65535;
+  if (by < 1) by = 1;
+  const int vec = (ldwt % 4 == 0) && ((reinterpret_cast<uintptr_t>(WT) & 15) == 0) ? 1 : 0;
+  k_gather_both<<<dim3((unsigned)bx, (unsigned)by), 256, 0, ctx->stream>>>(A, dt, m, lda, gi, W, ldw, WT, ldwt, vec);
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
+
 lrs_status launch_gather(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int64_t lda,
                          const GridDev& g, double* W, int64_t ldw) {
   GridDev gi = g;
@@ -157,17 +214,6 @@ lrs_status launch_gather(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int
   return launch_sketch(ctx, A, dt, m, lda, gi, W, ldw);
 }
 
-lrs_status launch_gather32(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int64_t lda,
-                           const GridDev& g, float* W, int64_t ldw) {
-  GridDev gi = g;
-  gi.kind = LRS_INJECT;
-  if (!sketch_sizes_ok(ctx, gi)) return LRS_EINVAL;
-  const dim3 grid = sketch_grid(ctx, m, gi.l);
-  k_sketch<LRS_INJECT, float><<<grid, 256, 0, ctx->stream>>>(A, dt, m, lda, gi, W, ldw);
-  ctx->launches++;
-  LRS_CUDA_TRY(ctx, cudaGetLastError());
-  return LRS_OK;
-}
 
 // ---------------------------------------------------------------------------
 // ||A||_F^2: per-block FP64 partials in a fixed order, then one block sums
