@@ -324,17 +324,21 @@ lrs_status trsm_rows(lrs_ctx* ctx, const double* M, int64_t p, int64_t ldm, cons
 // of every addition into the low word).  Blocks take column ranges; per-block
 // (hi, lo) partials of the packed upper triangle are combined in FP64 in
 // block order.
-constexpr int kDfCols = 65;             // columns staged per pass (odd: row reads hit distinct banks)
+constexpr int kDfCols = 64;             // columns staged per pass
 
 // Thread layout: the upper triangle of G in 4 x 4 tiles (tile (ti, tj),
-// ti <= tj), dealt round-robin, TPT tiles per thread.  Per staged column a
-// tile loads 8 values and updates 16 double-float sums.  The output is a full
-// r x r partial per block; only entries (i, j) with i/4 <= j/4 are written.
+// ti <= tj), dealt round-robin, TPT tiles per thread.  The staged columns are
+// stored transposed (row index fastest), so per staged column a tile loads
+// its two 4-row groups as two 16-byte words (conflict-free: a warp's tiles
+// share ti and take consecutive tj) and updates 16 double-float sums.  The
+// output is a full r x r partial per block; only entries (i, j) with
+// i/4 <= j/4 are written.
 template <int TPT>
 __global__ void __launch_bounds__(256) k_gram_df(const float* __restrict__ B, int r, int64_t n, int64_t ldb,
                                                 int64_t cols_b, float* __restrict__ part_hi,
                                                 float* __restrict__ part_lo) {
-  extern __shared__ float tf[];                    // rp x kDfCols, rp = r rounded up to 4 (zero rows)
+  extern __shared__ float4 tf4[];                  // kDfCols x rp floats (column t at t * rp), rp = r rounded up to 4
+  float* tf = reinterpret_cast<float*>(tf4);
   const int nt = (r + 3) / 4, ntiles = nt * (nt + 1) / 2, rp = nt * 4;
   const int64_t c0 = (int64_t)blockIdx.x * cols_b;
   const int64_t c1 = min(n, c0 + cols_b);
@@ -354,19 +358,16 @@ __global__ void __launch_bounds__(256) k_gram_df(const float* __restrict__ B, in
     const int nc = (int)min((int64_t)kDfCols, c1 - a0);
     __syncthreads();
     for (int e = threadIdx.x; e < rp * kDfCols; e += blockDim.x) {
-      const int i = e / kDfCols, t = e - i * kDfCols;
-      tf[e] = (t < nc && i < r) ? B[(int64_t)i * ldb + a0 + t] : 0.f;
+      const int i = e / kDfCols, t = e - i * kDfCols;     // a row's 64 columns: coalesced reads
+      tf[t * rp + i] = (t < nc && i < r) ? B[(int64_t)i * ldb + a0 + t] : 0.f;
     }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < TPT; ++q) {
       if (ti[q] < 0) continue;
-      const float* xi = tf + (ti[q] * 4) * kDfCols;
-      const float* xj = tf + (tj[q] * 4) * kDfCols;
       for (int t = 0; t < nc; ++t) {
-        float va[4], vb[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) { va[u] = xi[u * kDfCols + t]; vb[u] = xj[u * kDfCols + t]; }
+        const float4 a4 = tf4[(t * rp) / 4 + ti[q]], b4 = tf4[(t * rp) / 4 + tj[q]];
+        const float va[4] = {a4.x, a4.y, a4.z, a4.w}, vb[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
