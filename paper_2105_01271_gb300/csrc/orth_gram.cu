@@ -327,26 +327,30 @@ lrs_status trsm_rows(lrs_ctx* ctx, const double* M, int64_t p, int64_t ldm, cons
 constexpr int kDfCols = 64;             // columns staged per pass
 
 // Thread layout: the upper triangle of G in 4 x 4 tiles (tile (ti, tj),
-// ti <= tj), dealt round-robin, TPT tiles per thread.  The staged columns are
-// stored transposed (row index fastest), so per staged column a tile loads
-// its two 4-row groups as two 16-byte words (conflict-free: a warp's tiles
-// share ti and take consecutive tj) and updates 16 double-float sums.  The
-// output is a full r x r partial per block; only entries (i, j) with
-// i/4 <= j/4 are written.
+// ti <= tj), dealt round-robin, TPT tiles per thread; the block has just
+// enough whole warps for its tiles (the launch sizes it), so few threads idle.
+// The staged columns are stored transposed (row index fastest): per staged
+// column a tile loads its two 4-row groups as two 16-byte words
+// (conflict-free: a warp's tiles share ti and take consecutive tj) and
+// updates 16 double-float sums.  The output is a full r x r partial per
+// block; only entries (i, j) with i/4 <= j/4 are written.
+constexpr int kDfMaxThreads = 256;
+
 template <int TPT>
-__global__ void __launch_bounds__(256) k_gram_df(const float* __restrict__ B, int r, int64_t n, int64_t ldb,
-                                                int64_t cols_b, float* __restrict__ part_hi,
-                                                float* __restrict__ part_lo) {
+__global__ void __launch_bounds__(kDfMaxThreads) k_gram_df(const float* __restrict__ B, int r, int64_t n,
+                                                           int64_t ldb, int64_t cols_b, float* __restrict__ part_hi,
+                                                           float* __restrict__ part_lo) {
   extern __shared__ float4 tf4[];                  // kDfCols x rp floats (column t at t * rp), rp = r rounded up to 4
   float* tf = reinterpret_cast<float*>(tf4);
   const int nt = (r + 3) / 4, ntiles = nt * (nt + 1) / 2, rp = nt * 4;
+  const int nth = blockDim.x;
   const int64_t c0 = (int64_t)blockIdx.x * cols_b;
   const int64_t c1 = min(n, c0 + cols_b);
   float sh[TPT][16], sl[TPT][16];
   int ti[TPT], tj[TPT];
 #pragma unroll
   for (int q = 0; q < TPT; ++q) {
-    const int e = threadIdx.x + q * 256;
+    const int e = threadIdx.x + q * nth;
     int a = 0, b = 0;
     if (e < ntiles) tri_ij(e, nt, a, b);
     ti[q] = e < ntiles ? a : -1;
@@ -357,7 +361,7 @@ __global__ void __launch_bounds__(256) k_gram_df(const float* __restrict__ B, in
   for (int64_t a0 = c0; a0 < c1; a0 += kDfCols) {
     const int nc = (int)min((int64_t)kDfCols, c1 - a0);
     __syncthreads();
-    for (int e = threadIdx.x; e < rp * kDfCols; e += blockDim.x) {
+    for (int e = threadIdx.x; e < rp * kDfCols; e += nth) {
       const int i = e / kDfCols, t = e - i * kDfCols;     // a row's 64 columns: coalesced reads
       tf[t * rp + i] = (t < nc && i < r) ? B[(int64_t)i * ldb + a0 + t] : 0.f;
     }
@@ -507,10 +511,14 @@ lrs_status launch_gram_df(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, in
   float* lo = (float*)ws_alloc(ctx, sizeof(float) * (size_t)(nb * r * r));
   if (!hi || !lo) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (double-float gram)");
   const size_t dyn = sizeof(float) * (size_t)(nt * 4 * kDfCols);
-  const int tpt = (ntiles + 255) / 256;
-  if (tpt <= 1) k_gram_df<1><<<(unsigned)nb, 256, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
-  else if (tpt <= 2) k_gram_df<2><<<(unsigned)nb, 256, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
-  else k_gram_df<3><<<(unsigned)nb, 256, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
+  // tiles per thread and just enough whole warps for them
+  int tpt = 1;
+  while (tpt < 3 && (ntiles + tpt - 1) / tpt > kDfMaxThreads) ++tpt;
+  int th = ((ntiles + tpt - 1) / tpt + 31) / 32 * 32;
+  if (th > kDfMaxThreads) th = kDfMaxThreads;
+  if (tpt == 1) k_gram_df<1><<<(unsigned)nb, th, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
+  else if (tpt == 2) k_gram_df<2><<<(unsigned)nb, th, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
+  else k_gram_df<3><<<(unsigned)nb, th, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
   ctx->launches++;
   k_gram_df_reduce<<<(ri * ri + 7) / 8, 256, 0, ctx->stream>>>(hi, lo, (int)nb, ri, G);
   ctx->launches++;
