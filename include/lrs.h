@@ -314,6 +314,18 @@ lrs_status lrs_id_k_static(lrs_ctx* ctx, const double* Ysk, int64_t m, int64_t l
 /* Number of kernel launches this context has issued (for launch accounting). */
 int64_t lrs_launch_count(const lrs_ctx* ctx);
 
+/* Kernel timing (measurement support; the paper has no counterpart).
+ * lrs_set_kernel_timing(ctx, 1) makes every later call that runs the
+ * tensor-core A-pass kernel (the one full read of A_f inside lrs_svd_k and
+ * lrs_gemm_tn, and the SPC lifting read) bracket that kernel alone with two
+ * CUDA events on ctx's stream; lrs_last_kernel_ms then returns its duration
+ * in milliseconds for the most recent such call, or -1 when none was timed.
+ * The events are created on the first call with on = 1 (LRS_ECUDA if that
+ * fails) and released by lrs_destroy.  Timing costs one event record on
+ * each side of the kernel; the calls synchronise ctx's stream anyway. */
+lrs_status lrs_set_kernel_timing(lrs_ctx* ctx, int32_t on);
+double lrs_last_kernel_ms(const lrs_ctx* ctx);
+
 /* ------------------------------------------------------------------------
  * Batching form: many independent decompositions of different sizes.
  *

@@ -70,6 +70,8 @@ _SIG = {
     "lrs_last_error": (C.c_char_p, [C.c_void_p]),
     "lrs_version": (C.c_char_p, []),
     "lrs_launch_count": (C.c_int64, [C.c_void_p]),
+    "lrs_set_kernel_timing": (C.c_int, [C.c_void_p, C.c_int32]),
+    "lrs_last_kernel_ms": (C.c_double, [C.c_void_p]),
     "lrs_sketch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64,
                              C.POINTER(lrs_grid), C.c_void_p, C.c_int64]),
     "lrs_power_pass": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64,
@@ -197,6 +199,12 @@ class Context:
     @property
     def launches(self) -> int:
         return int(self.lib.lrs_launch_count(self.h))
+
+    def set_kernel_timing(self, on: bool):
+        return self._check(self.lib.lrs_set_kernel_timing(self.h, 1 if on else 0))
+
+    def last_kernel_ms(self) -> float:
+        return float(self.lib.lrs_last_kernel_ms(self.h))
 
     # --- the C ABI, one wrapper per entry point -----------------------------
     def sketch(self, A, dtype, m, lda, grid: lrs_grid, Y, ldy):

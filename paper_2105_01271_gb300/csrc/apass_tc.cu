@@ -553,9 +553,12 @@ lrs_status run_apass(lrs_ctx* ctx, const GemmArgs& a, double* fro2_out) {
   P.fro2_part = part;
   auto kern = k_apass<RAW, SA, SX>;
   { const lrs_status _s = raise_dyn_smem(ctx, (const void*)kern, (size_t)(cfg.smem)); if (_s) return _s; }
+  const bool timing = ctx->time_kernels && ctx->kev0 && ctx->kev1;
+  if (timing) LRS_CUDA_TRY(ctx, cudaEventRecord(ctx->kev0, ctx->stream));
   kern<<<grid, kThreads, cfg.smem, ctx->stream>>>(map, P);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
+  if (timing) LRS_CUDA_TRY(ctx, cudaEventRecord(ctx->kev1, ctx->stream));
   if (fro2_out) {
     lrs_status st = launch_sum(ctx, part, (int)grid, fro2_out);
     if (st) return st;
@@ -564,6 +567,11 @@ lrs_status run_apass(lrs_ctx* ctx, const GemmArgs& a, double* fro2_out) {
   LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 20, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   if (h[20] != 0) return lrs_fail(ctx, LRS_ETIMEOUT, "a-pass: a pipeline wait gave up");
+  if (timing) {
+    float ms = 0.f;
+    LRS_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->kev0, ctx->kev1));
+    ctx->last_kernel_ms = ms;
+  }
   return LRS_OK;
 }
 

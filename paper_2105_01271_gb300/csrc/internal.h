@@ -24,6 +24,10 @@ struct lrs_ctx {
   void* aux = nullptr;
   size_t aux_cap = 0;
   int64_t launches = 0;
+  // optional timing of the A-pass kernel (lrs_set_kernel_timing)
+  int time_kernels = 0;
+  cudaEvent_t kev0 = nullptr, kev1 = nullptr;
+  double last_kernel_ms = -1.0;
 };
 
 lrs_status lrs_fail(lrs_ctx* ctx, lrs_status st, const char* fmt, ...);

@@ -249,6 +249,8 @@ lrs_status lrs_create(lrs_ctx** out, int device, void* cuda_stream) {
 
 void lrs_destroy(lrs_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->kev0) cudaEventDestroy(ctx->kev0);
+  if (ctx->kev1) cudaEventDestroy(ctx->kev1);
   if (ctx->ws) { cudaStreamSynchronize(ctx->stream); cudaFree(ctx->ws); }
   if (ctx->aux) { cudaStreamSynchronize(ctx->stream); cudaFree(ctx->aux); }
   if (ctx->host_scratch) cudaFreeHost(ctx->host_scratch);
@@ -258,6 +260,21 @@ void lrs_destroy(lrs_ctx* ctx) {
 const char* lrs_last_error(const lrs_ctx* ctx) { return ctx ? ctx->err : "NULL context"; }
 
 int64_t lrs_launch_count(const lrs_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+lrs_status lrs_set_kernel_timing(lrs_ctx* ctx, int32_t on) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  if (on && !ctx->kev0) {
+    LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    LRS_CUDA_TRY(ctx, cudaEventCreate(&ctx->kev0));
+    LRS_CUDA_TRY(ctx, cudaEventCreate(&ctx->kev1));
+  }
+  ctx->time_kernels = on ? 1 : 0;
+  ctx->last_kernel_ms = -1.0;
+  return LRS_OK;
+}
+
+double lrs_last_kernel_ms(const lrs_ctx* ctx) { return ctx ? ctx->last_kernel_ms : -1.0; }
 
 static bool dtype_ok(int32_t dt) { return dt == LRS_F64 || dt == LRS_F32 || dt == LRS_BF16; }
 static bool prec_ok(int32_t p) { return p >= LRS_PREC_FP64 && p <= LRS_PREC_BF16X3; }

@@ -196,7 +196,8 @@ def test_range_find_wide_gram_route(lrs, p, c, n):
 
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("seed", [0, 1, 2, 3])
-@pytest.mark.parametrize("m,l,k", [(120, 80, 20), (45, 200, 30), (300, 64, 64), (200, 600, 60)])
+@pytest.mark.parametrize("m,l,k", [(120, 80, 20), (45, 200, 30), (300, 64, 64), (200, 600, 60),
+                                   (1000, 96, 40), (130, 1500, 50)])
 def test_id_k_pivot_gap(lrs, seed, m, l, k):
     torch = _torch()
     Y = synth.pivot_gap_matrix(m, l, seed=seed)
@@ -280,3 +281,23 @@ def test_gemm_tc_deterministic(lrs):
         lrs.gemm_tn(90, 3000, 700, _dev(X), 0, 90, _dev(A), 1, 3000, Cd, 0, 0, 3000, 2)
         outs.append(_np(Cd))
     assert all(np.array_equal(outs[0], o) for o in outs)
+
+
+def test_kernel_timing(lrs):
+    """lrs_set_kernel_timing / lrs_last_kernel_ms: -1 until a timed A-pass
+    call, a positive duration after one, and the product is unchanged."""
+    torch = _torch()
+    rng = np.random.default_rng(6)
+    X = rng.standard_normal((700, 90))
+    A = rng.standard_normal((700, 3000)).astype(np.float32)
+    ref = torch.empty((90, 3000), dtype=torch.float32, device="cuda")
+    lrs.gemm_tn(90, 3000, 700, _dev(X), 0, 90, _dev(A), 1, 3000, ref, 0, 0, 3000, 2)
+    lrs.set_kernel_timing(True)
+    assert lrs.last_kernel_ms() == -1.0
+    Cd = torch.empty((90, 3000), dtype=torch.float32, device="cuda")
+    lrs.gemm_tn(90, 3000, 700, _dev(X), 0, 90, _dev(A), 1, 3000, Cd, 0, 0, 3000, 2)
+    t = lrs.last_kernel_ms()
+    lrs.set_kernel_timing(False)
+    assert 0.0 < t < 1000.0
+    assert lrs.last_kernel_ms() == -1.0
+    assert np.array_equal(_np(Cd), _np(ref))
