@@ -196,8 +196,6 @@ size_t jacobi_ws(int64_t r, int64_t len);
 // transposed copy of a row-major FP64 matrix: dst (cols x rows) = src^T
 lrs_status launch_transpose(lrs_ctx* ctx, const double* src, int64_t rows, int64_t cols,
                             int64_t lds, double* dst, int64_t ldd);
-lrs_status launch_transpose32(lrs_ctx* ctx, const float* src, int64_t rows, int64_t cols,
-                              int64_t lds, float* dst, int64_t ldd);
 // FP64 -> FP32 copy (round to nearest)
 lrs_status launch_to_f32(lrs_ctx* ctx, const double* src, int64_t rows, int64_t cols, int64_t lds,
                          float* dst, int64_t ldd);

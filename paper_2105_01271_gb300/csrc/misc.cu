@@ -31,16 +31,6 @@ lrs_status launch_transpose(lrs_ctx* ctx, const double* src, int64_t rows, int64
   return LRS_OK;
 }
 
-lrs_status launch_transpose32(lrs_ctx* ctx, const float* src, int64_t rows, int64_t cols, int64_t lds,
-                              float* dst, int64_t ldd) {
-  if (rows <= 0 || cols <= 0) return LRS_OK;
-  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
-  k_transpose<float, float><<<grid, dim3(32, 8), 0, ctx->stream>>>(src, rows, cols, lds, dst, ldd);
-  ctx->launches++;
-  LRS_CUDA_TRY(ctx, cudaGetLastError());
-  return LRS_OK;
-}
-
 // dst (rows x cols, FP32, row stride ldd) = src (FP64, row stride lds), rounded to nearest
 __global__ void k_to_f32(const double* __restrict__ src, int64_t rows, int64_t cols, int64_t lds,
                          float* __restrict__ dst, int64_t ldd) {
