@@ -5,6 +5,9 @@ One step = one rank-k decomposition of one snapshot matrix through the C ABI:
        -> lrs_svd_k            (paper Algs. 7 and 2)
   ID : lrs_power_pass (C-PWR without re-orthonormalisation) -> lrs_id_k
                                (paper Alg. 4)
+The SVD and the ID run concurrently (the ID on a second context and stream);
+the same step with the two one after the other is reported as
+serial_ms_per_step.
 The default workload is the 2000-snapshot blob field on a 512^2 grid (FP32,
 full weighting onto 32^2, l = 1024, k = 50, q = 1).  The matrix (2.1 GB) is
 larger than L2 (129 MB), so no flush is needed between steps.
@@ -748,15 +751,40 @@ def run_ours(args, rank, world):
         bufs = path.Buffers(w.m, w.n, w.grid.l, w.k, A_d.device, prec == binding.LRS_PREC_FP64)
     stream.synchronize()
 
+    # The SVD and the ID of a step are independent decompositions of the same
+    # matrix (disjoint output buffers): they run concurrently, the ID on a
+    # second context with its own stream, driven from a worker thread (the
+    # ABI calls release the GIL).  Their one-block and barrier-bound kernels
+    # then overlap with the other path's work.
+    stream2 = torch.cuda.Stream(device=dev)
+    ctx2 = binding.load(dev, stream2)
+    from concurrent.futures import ThreadPoolExecutor
+    pool = ThreadPoolExecutor(max_workers=1)
+
+    def step_on(Ad):
+        fut = pool.submit(path.id_path, ctx2, Ad, w.dtype, w.grid, w.k, w.q, w.gram, rtol, prec, bufs)
+        s_ = path.svd_path(ctx, Ad, w.dtype, w.grid, w.k, q=w.q, gram=w.gram, rtol=rtol, prec=prec, bufs=bufs)
+        return s_, fut.result()
+
+    def join_streams():
+        # stream waits for everything queued on stream2 so far
+        e = torch.cuda.Event()
+        e.record(stream2)
+        stream.wait_event(e)
+
     def step():
-        s = path.svd_path(ctx, A_d, w.dtype, w.grid, w.k, q=w.q, gram=w.gram, rtol=rtol, prec=prec, bufs=bufs)
-        d = path.id_path(ctx, A_d, w.dtype, w.grid, w.k, q=w.q, gram=w.gram, rtol=rtol, prec=prec, bufs=bufs)
-        return s, d
+        return step_on(A_d)
+
+    def serial_step():
+        s_ = path.svd_path(ctx, A_d, w.dtype, w.grid, w.k, q=w.q, gram=w.gram, rtol=rtol, prec=prec, bufs=bufs)
+        d_ = path.id_path(ctx, A_d, w.dtype, w.grid, w.k, q=w.q, gram=w.gram, rtol=rtol, prec=prec, bufs=bufs)
+        return s_, d_
 
     clk = clocks_start(dev)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             s, d = step()
+        join_streams()
     stream.synchronize()
 
     def barrier():
@@ -765,21 +793,44 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize(dev)
 
     # ---- timed region (device time, CUDA events on the library's stream) ----
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # Each step is bracketed by its own pair of events; an input smaller than
+    # L2 (129 MB) has L2 flushed before every step (a 256 MB buffer is
+    # overwritten outside the events), a larger one needs no flush.
+    a_bytes = w.m * w.n * {"f64": 8, "f32": 4, "bf16": 2}[w.dtype]
+    flush_buf = (torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{dev}")
+                 if a_bytes <= 129e6 else None)
+
+    def timed_steps(fn, nsteps, concurrent):
+        pairs = []
+        with torch.cuda.stream(stream):
+            for _ in range(nsteps):
+                if flush_buf is not None:
+                    flush_buf.zero_()
+                e_s, e_e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e_s.record(stream)
+                if concurrent:
+                    stream2.wait_event(e_s)
+                out = fn()
+                if concurrent:
+                    join_streams()
+                e_e.record(stream)
+                pairs.append((e_s, e_e))
+        stream.synchronize()
+        return sum(a.elapsed_time(b) for a, b in pairs) / nsteps, out
+
     barrier()
     mark = clocks_mark(clk)
-    l0 = ctx.launches
-    with torch.cuda.stream(stream):
-        ev0.record(stream)
-        for _ in range(args.steps):
-            s, d = step()
-        ev1.record(stream)
-    stream.synchronize()
+    l0 = ctx.launches + ctx2.launches
+    ms_local, (s, d) = timed_steps(step, args.steps, True)
     barrier()
     clocks = clocks_stop(clk, mark)
-    launches = (ctx.launches - l0) // max(args.steps, 1)
-    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, f"cuda:{dev}")
+    launches = (ctx.launches + ctx2.launches - l0) // max(args.steps, 1)
+    ms = max_over_ranks(ms_local, world, f"cuda:{dev}")
     value = job_throughput(world, ms)
+
+    # the same steps with the SVD and the ID one after the other on one stream
+    serial_local, _ = timed_steps(serial_step, args.steps, False)
+    serial_ms = max_over_ranks(serial_local, world, f"cuda:{dev}")
 
     # ---- per-call breakdown (one extra step, events around each ABI call) ----
     phases = {}
@@ -908,10 +959,6 @@ def run_ours(args, rank, world):
     copied = [torch.cuda.Event(), torch.cuda.Event()]
     released = [torch.cuda.Event(), torch.cuda.Event()]
 
-    def step_on(Ad):
-        path.svd_path(ctx, Ad, w.dtype, w.grid, w.k, q=w.q, gram=w.gram, rtol=rtol, prec=prec, bufs=bufs)
-        path.id_path(ctx, Ad, w.dtype, w.grid, w.k, q=w.q, gram=w.gram, rtol=rtol, prec=prec, bufs=bufs)
-
     def copy_in(i):
         b = i % 2
         with torch.cuda.stream(cstream):
@@ -930,7 +977,9 @@ def run_ours(args, rank, world):
             copy_in(i + 1)
         with torch.cuda.stream(stream):
             stream.wait_event(copied[i % 2])
+            stream2.wait_event(copied[i % 2])
             step_on(dbuf[i % 2])
+            join_streams()
             released[i % 2].record(stream)
             for ho, o in zip(host_outs, outs):
                 ho.copy_(o, non_blocking=True)
@@ -947,21 +996,18 @@ def run_ours(args, rank, world):
         pb = path.Buffers(w.m, w.n, w.grid.l, w.k, A_d.device, False)
 
         def pstep():
+            # the same concurrent arrangement as the headline step
+            fut = pool.submit(path.id_path, ctx2, A_d, w.dtype, w.grid, w.k, w.q, w.gram, rtol,
+                              binding.LRS_PREC_FP32, pb)
             a = path.svd_path(ctx, A_d, w.dtype, w.grid, w.k, q=w.q, gram=w.gram, rtol=rtol,
                               prec=binding.LRS_PREC_FP32, bufs=pb)
-            b = path.id_path(ctx, A_d, w.dtype, w.grid, w.k, q=w.q, gram=w.gram, rtol=rtol,
-                             prec=binding.LRS_PREC_FP32, bufs=pb)
-            return a, b
+            return a, fut.result()
         with torch.cuda.stream(stream):
             pstep()
-            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            g0.record(stream)
-            nps = 3
-            for _ in range(nps):
-                ps_, pd_ = pstep()
-            g1.record(stream)
+            join_streams()
         stream.synchronize()
-        pms = g0.elapsed_time(g1) / nps
+        nps = 3
+        pms, (ps_, pd_) = timed_steps(pstep, nps, True)
         plain = {"prec": "fp32", "value": 1e3 / pms, "ms_per_step": pms, "steps": nps,
                  "err_est_svd": ps_.err_est, "err_est_id": pd_.err_est, "r": ps_.r,
                  "speedup_of_headline": (1e3 / ms) / (1e3 / pms),
@@ -980,7 +1026,9 @@ def run_ours(args, rank, world):
                    "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms, "steps": e2e_steps,
                    "overlap": "H2D of step i+1 on a copy stream during step i (two device buffers)"},
            "result": {"err_est_svd": s.err_est, "r": s.r, "err_est_id": d.err_est},
-           "phases_ms": phases}
+           "phases_ms": phases,
+           "serial_ms_per_step": serial_ms}
+    out["config"]["svd_and_id"] = "concurrent: the ID on a second context and stream"
     if plain is not None:
         out["plain_fp32_gpu"] = plain
     if not args.no_cpu_baseline and world == 1:
