@@ -326,6 +326,39 @@ lrs_status trsm_rows(lrs_ctx* ctx, const double* M, int64_t p, int64_t ldm, cons
 // block order.
 constexpr int kDfCols = 64;             // columns staged per pass
 
+// Packed FP32 pairs (sm_100+ .f32x2 instructions): each lane of the pair is
+// rounded to nearest exactly like the scalar _rn operation, so the packed
+// error-free transformations below give bit-for-bit the scalar results with
+// half the instructions.  Low half = first operand of the pack.
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
 // Thread layout: the upper triangle of G in 4 x 4 tiles (tile (ti, tj),
 // ti <= tj), dealt round-robin, TPT tiles per thread; the block has just
 // enough whole warps for its tiles (the launch sizes it), so few threads idle.
@@ -346,7 +379,8 @@ __global__ void __launch_bounds__(kDfMaxThreads) k_gram_df(const float* __restri
   const int nth = blockDim.x;
   const int64_t c0 = (int64_t)blockIdx.x * cols_b;
   const int64_t c1 = min(n, c0 + cols_b);
-  float sh[TPT][16], sl[TPT][16];
+  // entry (u, v) of a tile lives in pair u * 2 + v / 2, half v % 2
+  uint64_t sh[TPT][8], sl[TPT][8];
   int ti[TPT], tj[TPT];
 #pragma unroll
   for (int q = 0; q < TPT; ++q) {
@@ -356,7 +390,7 @@ __global__ void __launch_bounds__(kDfMaxThreads) k_gram_df(const float* __restri
     ti[q] = e < ntiles ? a : -1;
     tj[q] = b;
 #pragma unroll
-    for (int u = 0; u < 16; ++u) { sh[q][u] = 0.f; sl[q][u] = 0.f; }
+    for (int u = 0; u < 8; ++u) { sh[q][u] = 0ull; sl[q][u] = 0ull; }
   }
   for (int64_t a0 = c0; a0 < c1; a0 += kDfCols) {
     const int nc = (int)min((int64_t)kDfCols, c1 - a0);
@@ -371,22 +405,26 @@ __global__ void __launch_bounds__(kDfMaxThreads) k_gram_df(const float* __restri
       if (ti[q] < 0) continue;
       for (int t = 0; t < nc; ++t) {
         const float4 a4 = tf4[(t * rp) / 4 + ti[q]], b4 = tf4[(t * rp) / 4 + tj[q]];
-        const float va[4] = {a4.x, a4.y, a4.z, a4.w}, vb[4] = {b4.x, b4.y, b4.z, b4.w};
+        const float va[4] = {a4.x, a4.y, a4.z, a4.w};
+        const uint64_t bp[2] = {f2_pack(b4.x, b4.y), f2_pack(b4.z, b4.w)};
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 4; ++u) {
+          const uint64_t A = f2_pack(va[u], va[u]), nA = f2_pack(-va[u], -va[u]);
 #pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            // _rn intrinsics: the compiler must not fuse these into FMAs, or
-            // the error-free transformations stop being exact
-            const float p = __fmul_rn(va[u], vb[v]);
-            const float pe = fmaf(va[u], vb[v], -p);      // a b = p + pe exactly
-            float& h = sh[q][u * 4 + v];
-            const float s2 = __fadd_rn(h, p);            // two-sum: h + p = s2 + err exactly
-            const float bb = __fsub_rn(s2, h);
-            const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s2, bb)), __fsub_rn(p, bb));
+          for (int vp = 0; vp < 2; ++vp) {
+            // per lane: p = RN(a b); -pe = p - a b exactly (one FMA); two-sum of
+            // h + p; the low word collects err + pe.  Inline PTX: nothing is
+            // contracted, so the error-free transformations stay exact.
+            const uint64_t p = f2_mul(A, bp[vp]);
+            const uint64_t npe = f2_fma(nA, bp[vp], p);
+            uint64_t& h = sh[q][u * 2 + vp];
+            const uint64_t s2 = f2_add(h, p);
+            const uint64_t bb = f2_sub(s2, h);
+            const uint64_t err = f2_add(f2_sub(h, f2_sub(s2, bb)), f2_sub(p, bb));
             h = s2;
-            sl[q][u * 4 + v] = __fadd_rn(sl[q][u * 4 + v], __fadd_rn(err, pe));
+            sl[q][u * 2 + vp] = f2_add(sl[q][u * 2 + vp], f2_sub(err, npe));
           }
+        }
       }
     }
   }
@@ -398,9 +436,13 @@ __global__ void __launch_bounds__(kDfMaxThreads) k_gram_df(const float* __restri
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const int i = ti[q] * 4 + u, j = tj[q] * 4 + v;
-        if (i < r && j < r) { oh[i * r + j] = sh[q][u * 4 + v]; ol[i * r + j] = sl[q][u * 4 + v]; }
+      for (int vp = 0; vp < 2; ++vp) {
+        float h0, h1, l0, l1;
+        f2_unpack(sh[q][u * 2 + vp], h0, h1);
+        f2_unpack(sl[q][u * 2 + vp], l0, l1);
+        const int i = ti[q] * 4 + u, j = tj[q] * 4 + vp * 2;
+        if (i < r && j < r) { oh[i * r + j] = h0; ol[i * r + j] = l0; }
+        if (i < r && j + 1 < r) { oh[i * r + j + 1] = h1; ol[i * r + j + 1] = l1; }
       }
   }
 }
