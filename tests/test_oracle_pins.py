@@ -36,7 +36,7 @@ def test_omega_identity_gives_eckart_young():
         ey = np.sqrt(np.sum(s_ref[k:] ** 2) / np.sum(s_ref ** 2))
         assert abs(err - ey) <= 1e-12 + 1e-9 * ey
         np.testing.assert_allclose(o["S"], s_ref[:k], rtol=1e-12)
-        # spectral-norm error = sigma_{k+1} (Eckart-Young)
+        # spectral-norm error = sigma_{k+1} (the Eckart-Young optimum of Sec. 1)
         Ah = (o["U"] * o["S"]) @ o["V"].T
         assert abs(np.linalg.norm(A - Ah, 2) - s_ref[k]) <= 1e-10 * s_ref[0]
 
