@@ -326,6 +326,18 @@ int64_t lrs_launch_count(const lrs_ctx* ctx);
 lrs_status lrs_set_kernel_timing(lrs_ctx* ctx, int32_t on);
 double lrs_last_kernel_ms(const lrs_ctx* ctx);
 
+/* Failure injection for tests (the paper has no counterpart).
+ * lrs_set_workspace_limit caps the device workspace later calls on ctx may
+ * reserve at `bytes` (0 removes the cap): a call that needs more returns
+ * LRS_ENOMEM before any launch, and ctx stays usable.
+ * lrs_selftest_barrier_timeout launches, on ctx's stream, a two-block
+ * cooperative kernel in which one block never arrives at the grid barrier that
+ * the library's cooperative kernels use; the other block gives up after
+ * spin_limit polls (1 .. the library's own limit) and the call returns
+ * LRS_ETIMEOUT.  Nothing faults or hangs; ctx stays usable.  Synchronises. */
+lrs_status lrs_set_workspace_limit(lrs_ctx* ctx, size_t bytes);
+lrs_status lrs_selftest_barrier_timeout(lrs_ctx* ctx, int64_t spin_limit);
+
 /* ------------------------------------------------------------------------
  * Batching form: many independent decompositions of different sizes.
  *

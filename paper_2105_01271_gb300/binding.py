@@ -72,6 +72,8 @@ _SIG = {
     "lrs_launch_count": (C.c_int64, [C.c_void_p]),
     "lrs_set_kernel_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "lrs_last_kernel_ms": (C.c_double, [C.c_void_p]),
+    "lrs_set_workspace_limit": (C.c_int, [C.c_void_p, C.c_size_t]),
+    "lrs_selftest_barrier_timeout": (C.c_int, [C.c_void_p, C.c_int64]),
     "lrs_sketch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64,
                              C.POINTER(lrs_grid), C.c_void_p, C.c_int64]),
     "lrs_power_pass": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64,
@@ -205,6 +207,13 @@ class Context:
 
     def last_kernel_ms(self) -> float:
         return float(self.lib.lrs_last_kernel_ms(self.h))
+
+    def set_workspace_limit(self, nbytes: int):
+        return self._check(self.lib.lrs_set_workspace_limit(self.h, int(nbytes)))
+
+    def selftest_barrier_timeout(self, spin_limit: int) -> int:
+        """Status of the forced barrier timeout (LRS_ETIMEOUT expected); does not raise."""
+        return int(self.lib.lrs_selftest_barrier_timeout(self.h, int(spin_limit)))
 
     # --- the C ABI, one wrapper per entry point -----------------------------
     def sketch(self, A, dtype, m, lda, grid: lrs_grid, Y, ldy):

@@ -192,7 +192,7 @@ __device__ __forceinline__ int ld_volatile_s32(const int* p) {
   return *reinterpret_cast<const volatile int*>(p);
 }
 
-__device__ __forceinline__ bool grid_sync(const GridBarrier& b) {
+__device__ __forceinline__ bool grid_sync(const GridBarrier& b, long long spin_limit = kSpinLimit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned old = atom_add_release_u32(b.count, 1u);
@@ -200,7 +200,7 @@ __device__ __forceinline__ bool grid_sync(const GridBarrier& b) {
     long long it = 0;
     while ((int)(ld_acquire_u32(b.count) - target) < 0) {
       if (((++it) & 63) == 0 && ld_volatile_s32(b.err) != 0) break;
-      if (it > kSpinLimit) { atomicCAS(b.err, 0, (int)LRS_ETIMEOUT); break; }
+      if (it > spin_limit) { atomicCAS(b.err, 0, (int)LRS_ETIMEOUT); break; }
       if (it > 256) __nanosleep(20);
     }
   }

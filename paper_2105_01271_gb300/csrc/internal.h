@@ -17,6 +17,7 @@ struct lrs_ctx {
   char* ws = nullptr;
   size_t ws_cap = 0;
   size_t ws_top = 0;
+  size_t ws_limit = 0;      // lrs_set_workspace_limit (0: none)
   // small pinned host buffer for scalar read-back
   void* host_scratch = nullptr;
   // side buffer for split-K partial sums of the CUDA-core GEMM (independent of
@@ -196,6 +197,8 @@ size_t jacobi_ws(int64_t r, int64_t len);
 // transposed copy of a row-major FP64 matrix: dst (cols x rows) = src^T
 lrs_status launch_transpose(lrs_ctx* ctx, const double* src, int64_t rows, int64_t cols,
                             int64_t lds, double* dst, int64_t ldd);
+// two-block cooperative launch whose barrier wait runs out (lrs_selftest_barrier_timeout)
+lrs_status launch_barrier_selftest(lrs_ctx* ctx, int64_t spin_limit);
 // FP64 -> FP32 copy (round to nearest)
 lrs_status launch_to_f32(lrs_ctx* ctx, const double* src, int64_t rows, int64_t cols, int64_t lds,
                          float* dst, int64_t ldd);

@@ -29,6 +29,8 @@ static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 lrs_status ws_reserve(lrs_ctx* ctx, size_t bytes) {
   ctx->ws_top = 0;
+  if (ctx->ws_limit && bytes > ctx->ws_limit)
+    return lrs_fail(ctx, LRS_ENOMEM, "workspace limit: %zu bytes needed, %zu allowed", bytes, ctx->ws_limit);
   if (bytes <= ctx->ws_cap) return LRS_OK;
   if (ctx->ws) {
     cudaStreamSynchronize(ctx->stream);
@@ -275,6 +277,26 @@ lrs_status lrs_set_kernel_timing(lrs_ctx* ctx, int32_t on) {
 }
 
 double lrs_last_kernel_ms(const lrs_ctx* ctx) { return ctx ? ctx->last_kernel_ms : -1.0; }
+
+lrs_status lrs_set_workspace_limit(lrs_ctx* ctx, size_t bytes) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  ctx->ws_limit = bytes;
+  return LRS_OK;
+}
+
+lrs_status lrs_selftest_barrier_timeout(lrs_ctx* ctx, int64_t spin_limit) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  if (spin_limit < 1 || spin_limit > kSpinLimit)
+    return lrs_fail(ctx, LRS_EINVAL, "selftest: spin_limit %lld not in [1, %lld]", (long long)spin_limit,
+                    (long long)kSpinLimit);
+  if (!ctx->coop_ok) return lrs_fail(ctx, LRS_ECUDA, "device lacks cooperative launch");
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  lrs_status st = ws_reserve(ctx, 256);
+  if (st) return st;
+  return launch_barrier_selftest(ctx, spin_limit);
+}
 
 static bool dtype_ok(int32_t dt) { return dt == LRS_F64 || dt == LRS_F32 || dt == LRS_BF16; }
 static bool prec_ok(int32_t p) { return p >= LRS_PREC_FP64 && p <= LRS_PREC_BF16X3; }

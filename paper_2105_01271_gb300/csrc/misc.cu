@@ -116,4 +116,32 @@ lrs_status launch_scale_cols(lrs_ctx* ctx, const double* V, int64_t r, int64_t l
   return LRS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Self-test of the bounded grid barrier: a two-block cooperative launch in
+// which block 1 leaves without arriving, so block 0's wait runs out after
+// spin_limit polls, records LRS_ETIMEOUT and returns.  The host reads the
+// flag; nothing faults, traps or hangs.
+__global__ void k_barrier_selftest(GridBarrier bar, long long spin_limit) {
+  if (blockIdx.x != 0) return;
+  grid_sync(bar, spin_limit);
+}
+
+lrs_status launch_barrier_selftest(lrs_ctx* ctx, int64_t spin_limit) {
+  unsigned* bar = (unsigned*)ws_alloc(ctx, 256);
+  if (!bar) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (selftest)");
+  LRS_CUDA_TRY(ctx, cudaMemsetAsync(bar, 0, 256, ctx->stream));
+  GridBarrier b{};
+  b.count = bar; b.gen = bar + 1; b.err = (int*)(bar + 2);
+  long long lim = spin_limit;
+  void* args[] = {&b, &lim};
+  LRS_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)k_barrier_selftest, dim3(2), dim3(32), args, 0,
+                                                ctx->stream));
+  ctx->launches++;
+  int* h = (int*)ctx->host_scratch;
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 36, bar + 2, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (h[36] != 0) return lrs_fail(ctx, (lrs_status)h[36], "selftest: the grid barrier wait gave up");
+  return LRS_OK;
+}
+
 }  // namespace lrs
