@@ -144,7 +144,8 @@ lrs_status lrs_range_find_diag(lrs_ctx* ctx, const double* G, int64_t m, int64_t
 /*
  * lrs_svd_k -- TPC-SVD from a range basis (Sec. 3.1, Alg. 2):
  *   B = Q^T A_f (r x n; the one full read of A_f; ||A_f||_F^2 fused),
- *   SVD(B) via the R factor of B^T (Householder TSQR) and one-sided Jacobi,
+ *   SVD(B) via the R factor of B^T (FP32 B: a double-float Gram B B^T and an
+ *   FP64 Cholesky; FP64 B: the pivoted QR of B^T) and one-sided Jacobi,
  *   U_k = Q U_B(:,1:k), S_k, V_k = B^T U_B(:,1:k) S_k^{-1}.
  *   A   m x n in dtype, row stride lda.    Q  m x r FP64, row stride ldq.
  *   U   m x k FP64 (row stride ldu).       S  k FP64.
@@ -290,22 +291,29 @@ lrs_status lrs_gemm_tn(lrs_ctx* ctx, int64_t M, int64_t N, int64_t K,
                        void* C, int32_t c_f64, int32_t c_trans, int64_t ldc, int32_t prec);
 
 /*
- * lrs_id_k_static -- lrs_id_k for callers that cannot allocate device memory
- * at call time (code inside a CUDA-graph capture or a real-time loop where
- * cudaMalloc would stall or is not allowed, or a host framework that owns
- * every allocation).  The paper has no counterpart: it is a deployment
+ * lrs_id_k_static -- lrs_id_k for callers that must not allocate device
+ * memory while they run: a real-time loop whose time budget has no room for
+ * cudaMalloc (it can synchronise the whole device and take milliseconds), or
+ * a host framework that owns every device allocation and does not let a
+ * library make its own.  The paper has no counterpart: it is a deployment
  * variant of the same row ID.
  *   Same arguments, results and statuses as lrs_id_k.  All scratch lives in
  *   one file-scope device array of LRS_ID_STATIC_SCRATCH_BYTES (32 MiB) that
  *   every GPU loading the library keeps until the process exits; the call
  *   makes no cudaMalloc/cudaFree and calls no allocating library routine.
- *   Scratch needed: about 8*m*l + 16*S*m + 16*k*m + 8*k*l bytes (S = SM
- *   count); a request above the array's size is rejected with LRS_EINVAL
- *   before any launch.
+ *   Scratch needed: about 8*m*l + 16*S*l + 16*k*m + 8*k*l bytes (S = SM
+ *   count) when m >= 128 (the column-owner pivoted QR); for m < 128 the
+ *   row-slab pivoted QR needs less unless a block's slab overflows shared
+ *   memory.  A request above the array's size is rejected with LRS_EINVAL
+ *   before any launch, and lrs_last_error then states the exact byte count.
  *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress); make that first call before any stream capture.
- *   Every call shares the array: calls whose GPU work overlaps (two streams
- *   or two contexts at once) race.  The call synchronises ctx's stream.
+ *   (cudaGetSymbolAddress); make that first call before any stream capture
+ *   begins on that device.
+ *   Every call shares the array and finds in it what the last call left:
+ *   calls whose GPU work overlaps (two streams or two contexts at once) race.
+ *   The call synchronises ctx's stream (it reads the rank and the error
+ *   terms back), also when it fails after queueing work, so no work of a
+ *   returned call is still using the array.
  */
 #define LRS_ID_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
 lrs_status lrs_id_k_static(lrs_ctx* ctx, const double* Ysk, int64_t m, int64_t l, int64_t ldy, int32_t k,

@@ -1,10 +1,10 @@
 // lrs_id_k_static: the row ID of lrs_id_k with all of its scratch in one
 // file-scope device array instead of the context's cudaMalloc'ed workspace.
 //
-// For callers that cannot allocate device memory at call time: code running
-// inside a CUDA-graph capture or a real-time loop where cudaMalloc would
-// stall or be illegal, or a host framework that owns every allocation and
-// forbids libraries from making their own.
+// For callers that must not allocate device memory while they run: a
+// real-time loop whose time budget has no room for cudaMalloc (it can
+// synchronise the whole device), or a host framework that owns every device
+// allocation and does not let a library make its own.
 //
 // The array (LRS_ID_STATIC_SCRATCH_BYTES) is part of the library's device
 // image: every GPU that loads the library holds it until the process exits.
@@ -109,6 +109,10 @@ extern "C" lrs_status lrs_id_k_static(lrs_ctx* ctx, const double* Ysk, int64_t m
     return LRS_OK;
   };
   st = run();
+  // A call that failed after queueing work (e.g. an occupancy check after the
+  // norm kernels) waits for that work, so nothing of it still writes the
+  // shared array when the next call, maybe on another stream, begins.
+  if (st != LRS_OK) cudaStreamSynchronize(ctx->stream);
   ctx->ws = save_ws;
   ctx->ws_cap = save_cap;
   ctx->ws_top = save_top;

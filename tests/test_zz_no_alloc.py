@@ -1,6 +1,6 @@
-"""lrs_id_k_static: the row ID for callers that cannot allocate device memory
-while they run (inside a CUDA-graph capture, a real-time loop, or a host
-framework that owns every allocation).  Its scratch is one device array of the
+"""lrs_id_k_static: the row ID for callers that must not allocate device memory
+while they run (a real-time loop with no time for cudaMalloc, or a host
+framework that owns every device allocation).  Its scratch is one device array of the
 library, so it must give the same skeleton and coefficients as lrs_id_k, call
 after call, whatever the previous call left in that array.
 
@@ -50,6 +50,22 @@ def test_static_matches_allocating_entry_point_twice(lrs):
         # and both agree with the oracle's skeleton on these gap inputs
         Jo, Po, eo = oracle.row_id(Y, k)
         assert np.array_equal(Js, Jo)
+
+
+def test_static_row_slab_route(lrs):
+    """Fewer than 128 snapshots: the row ID takes the row-slab pivoted QR (not
+    the column-owner one), whose scratch the static array must hold as well."""
+    Y = synth.pivot_gap_matrix(100, 64, seed=13)
+    k = 20
+    for _ in range(2):
+        Js, Ps, es = _run(lrs, Y, k, static=True)
+        Ja, Pa, ea = _run(lrs, Y, k, static=False)
+        assert np.array_equal(Js, Ja)
+        assert np.array_equal(Ps[Js], np.eye(k))
+        np.testing.assert_allclose(Ps, Pa, rtol=1e-9, atol=1e-11)
+        assert abs(es - ea) <= 1e-10 * max(ea, 1e-16) + 1e-14
+    Jo, Po, eo = oracle.row_id(Y, k)
+    assert np.array_equal(Js, Jo)
 
 
 def test_static_blob_sketch_size(lrs):
