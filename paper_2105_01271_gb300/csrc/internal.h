@@ -173,14 +173,17 @@ lrs_status launch_abs_diag(lrs_ctx* ctx, const double* R, int64_t ld, int64_t r,
 
 // R (r x r upper, row-major, positive diagonal) with R^T R = B B^T for a wide
 // FP32 B (r x n, r <= 128): double-float Gram on the FP32 pipe + FP64
-// Cholesky.  LRS_ERANK (nothing reported) when the Cholesky breaks down; the
-// caller then runs TSQR.  Synchronises.
+// Cholesky.  With perm_out (device, r entries) the Cholesky is pivoted:
+// P^T B B^T P = R^T R, perm_out[pos] = row of B.  LRS_ERANK (nothing
+// reported) when the Cholesky breaks down; the caller then runs TSQR.
+// Synchronises.
 size_t r_of_bt_gram_ws(int64_t r, int num_sms);
 // G (r x r FP64, both triangles) = B B^T for B r x n FP32 (row stride ldb),
 // double-float accumulation (r <= 128); workspace gram_df_ws(r, num_sms)
 size_t gram_df_ws(int64_t r, int num_sms);
 lrs_status launch_gram_df(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, int64_t ldb, double* G);
-lrs_status launch_r_of_bt_gram(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, int64_t ldb, double* R);
+lrs_status launch_r_of_bt_gram(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, int64_t ldb, double* R,
+                               int32_t* perm_out = nullptr);
 
 // svd_small.cu ------------------------------------------------------------------
 // R factor (r x r, row-major) of B^T where B is r x n row-major in FP32 or FP64.
@@ -192,6 +195,14 @@ lrs_status launch_jacobi(lrs_ctx* ctx, double* R, int64_t r, double* V, double* 
 // workspace of the multi-SM FP64 Jacobi on r columns of length len (launch_jacobi
 // falls back to one block without it)
 size_t jacobi_ws(int64_t r, int64_t len);
+// jacobi_cluster.cu: FP64 one-sided Jacobi on the rows of R (r x r upper
+// triangular, row stride ldr) on one thread-block cluster: U_B (r x r
+// row-major, row perm[i] <- position i; perm NULL = identity) and s (r),
+// descending.  LRS_ERANK (nothing launched) when no cluster fits or r is out
+// of range [8, 1024]; workspace jacobi_rows_ws(r).
+size_t jacobi_rows_ws(int64_t r);
+lrs_status launch_jacobi_rows(lrs_ctx* ctx, const double* R, int64_t r, int64_t ldr, const int32_t* perm,
+                              double* Ub, double* s);
 
 // misc.cu -------------------------------------------------------------------------
 // transposed copy of a row-major FP64 matrix: dst (cols x rows) = src^T

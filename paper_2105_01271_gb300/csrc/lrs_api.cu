@@ -526,6 +526,7 @@ size_t svd_from_b_ws(int64_t r, int64_t n, int64_t m, int64_t kk, int32_t prec, 
   const size_t bsz = prec == LRS_PREC_FP64 ? 8 : 4;
   size_t need = tsqr_ws(r, n, bsz) + r_of_bt_gram_ws(r, num_sms);
   need += 4 * align256(8 * (size_t)(r * r)) + align256(8 * (size_t)(m * r)) + jacobi_ws(r, r) + 65536;
+  need += jacobi_rows_ws(r) + align256(4 * (size_t)r);
   if (prec == LRS_PREC_FP64)                     // R of B^T by the pivoted QR
     need += 2 * align256(8 * (size_t)(n * r)) + align256(8 * (size_t)(r * r)) + cpqr_ws(n, r, r) + 1024;
   if (prec >= LRS_PREC_SPLIT_BF16) need += gemm_tc_workspace(kk, r, LRS_PREC_BF16X3) + 4096;
@@ -547,9 +548,11 @@ lrs_status svd_from_b(lrs_ctx* ctx, const void* B, int64_t r, int64_t n, const d
   double* QT = (double*)ws_alloc(ctx, 8 * (size_t)(m * r));
   double* sgn = (double*)ws_alloc(ctx, 8 * (size_t)kk);
   if (!Rm || !Vr || !sv || !Wk || !QT || !sgn) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd)");
-  // SVD(B): R of B^T, Jacobi on R -> U_B = Vr, s.  FP32 B: R from the
-  // double-float Gram and an FP64 Cholesky (TSQR if that breaks down); FP64 B:
-  // Householder TSQR.
+  // SVD(B), all in FP64 once B exists.  FP32 B: R from the double-float Gram
+  // and a PIVOTED FP64 Cholesky (P^T B B^T P = R^T R), then the FP64
+  // one-sided Jacobi on the rows of R across a thread-block cluster, U_B =
+  // P U' (jacobi_cluster.cu); TSQR if the Cholesky breaks down.  FP64 B: R
+  // of B^T by the cooperative pivoted QR, FP64 Jacobi on its columns.
   lrs_status st = LRS_ERANK;
   if (f64 && r >= 24 && ctx->coop_ok) {
     // FP64 B: R of B^T by the cooperative pivoted QR (many SMs, no pivot
@@ -560,15 +563,38 @@ lrs_status svd_from_b(lrs_ctx* ctx, const void* B, int64_t r, int64_t n, const d
     ctx->ws_top = mark;
     if (st != LRS_OK && st != LRS_ERANK) return st;
   }
+  int32_t* piv = (int32_t*)ws_alloc(ctx, 4 * (size_t)r);
+  if (!piv) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd)");
+  bool pivoted = false;
   if (st == LRS_ERANK && !f64 && r <= 128) {
     const size_t mark = ctx->ws_top;
-    st = launch_r_of_bt_gram(ctx, (const float*)B, r, n, n, Rm);
+    st = launch_r_of_bt_gram(ctx, (const float*)B, r, n, n, Rm, piv);
     ctx->ws_top = mark;
     if (st != LRS_OK && st != LRS_ERANK) return st;
+    pivoted = st == LRS_OK;
   }
   if (st == LRS_ERANK) st = launch_tsqr(ctx, B, f64, r, n, n, Rm);
   if (st) return st;
-  st = launch_jacobi(ctx, Rm, r, Vr, sv, f64);
+  st = LRS_ERANK;
+  if (!f64) {
+    const size_t mark = ctx->ws_top;
+    st = launch_jacobi_rows(ctx, Rm, r, r, pivoted ? piv : nullptr, Vr, sv);
+    ctx->ws_top = mark;
+    if (st != LRS_OK && st != LRS_ERANK) return st;
+  }
+  if (st == LRS_ERANK) {
+    // FP64 Jacobi on the columns of R (one block, or across the SMs); the
+    // pivoted factor's right vectors are rows of P^T U_B, so a pivoted R is
+    // only ever taken by the cluster kernel above
+    if (pivoted) {
+      const size_t mark = ctx->ws_top;
+      st = launch_r_of_bt_gram(ctx, (const float*)B, r, n, n, Rm, nullptr);
+      ctx->ws_top = mark;
+      if (st == LRS_ERANK) st = launch_tsqr(ctx, B, f64, r, n, n, Rm);
+      if (st) return st;
+    }
+    st = launch_jacobi(ctx, Rm, r, Vr, sv, 1);
+  }
   if (st) return st;
   // U = Q Vr(:, :kk): m x kk x r in FP64, 16 x 16 output tiles over the SMs
   (void)QT;

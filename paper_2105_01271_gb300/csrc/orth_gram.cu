@@ -535,16 +535,18 @@ lrs_status launch_gram_df(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, in
   return LRS_OK;
 }
 
-lrs_status launch_r_of_bt_gram(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, int64_t ldb, double* R) {
+lrs_status launch_r_of_bt_gram(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, int64_t ldb, double* R,
+                               int32_t* perm_out) {
   if (r < 1 || r > kMaxC) return lrs_fail(ctx, LRS_EINVAL, "svd: r=%lld out of range for the Gram route", (long long)r);
   const int ri = (int)r;
   double* G = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(r * r));
-  int32_t* perm = (int32_t*)ws_alloc(ctx, 4 * (size_t)r);
+  int32_t* perm = perm_out ? perm_out : (int32_t*)ws_alloc(ctx, 4 * (size_t)r);
   int32_t* rank = (int32_t*)ws_alloc(ctx, 8);
   if (!G || !perm || !rank) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd gram)");
   lrs_status gs = launch_gram_df(ctx, B, r, n, ldb, G);
   if (gs) return gs;
-  lrs_status st = pchol(ctx, G, ri, ri, 0.0, 0, perm, R, r, rank);
+  // pivoted when the caller takes the permutation (P^T B B^T P = R^T R)
+  lrs_status st = pchol(ctx, G, ri, ri, 0.0, perm_out ? 1 : 0, perm, R, r, rank);
   if (st) return st;
   int32_t* h = (int32_t*)ctx->host_scratch;
   LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 42, rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));

@@ -186,6 +186,40 @@ def blob_field(m: int, N: int, nblobs: int, seed: int, kappa: float = 1e-5,
     return _store(out, dtype)
 
 
+def spiked_blob_field(m: int, N: int, nblobs: int, seed: int, nspikes: int, s: int,
+                      ratio: float = 0.97, amp0: float = 10.0, kappa: float = 1e-5,
+                      dtype: str = "f32"):
+    """The blob field with a clear pivot gap for the row ID: nspikes snapshots
+    (drawn without replacement) each carry one extra Gaussian bump of
+    amplitude amp0 * ratio**j (j = 0, 1, ... in draw order).  The bumps sit on
+    coarse points of the sketch grid with per-axis factor s, spaced
+    Nc // g coarse cells apart (g = ceil(sqrt(nspikes)) per axis, Nc = N / s),
+    with standard deviation a quarter of that spacing, so they are nearly
+    orthogonal to each other and every one meets the sketch stencil the same
+    way.  The spiked rows then dominate the sketch and its C-PWR iterate in
+    amplitude order, each pivot ahead of the next by a margin of about
+    1 - ratio**3 (the iterate is cubic in the row scale), which the tests
+    check rather than assume.  Returns (A, spiked row indices in draw order)."""
+    base = blob_field(m, N, nblobs, seed, kappa, "f64")
+    rng = np.random.default_rng(seed + 7919)
+    rows = rng.choice(m, nspikes, replace=False)
+    g = int(np.ceil(np.sqrt(nspikes)))
+    Nc = N // s
+    step = max(1, Nc // g)
+    cells = rng.choice(g * g, nspikes, replace=False)
+    sd = step * s / 4.0                              # fine points
+    idx = np.arange(N)
+    for j in range(nspikes):
+        # coarse point (a, b) sits at fine index s * a + s // 2 per axis
+        cx = s * ((cells[j] % g) * step) + s // 2
+        cy = s * ((cells[j] // g) * step) + s // 2
+        dx = (idx - cx + N / 2.0) % N - N / 2.0      # periodic minimum image
+        dy = (idx - cy + N / 2.0) % N - N / 2.0
+        phi = np.exp(-dy[:, None] ** 2 / (2 * sd * sd)) * np.exp(-dx[None, :] ** 2 / (2 * sd * sd))
+        base[rows[j]] += amp0 * ratio ** j * phi.ravel()
+    return _store(base, dtype), rows
+
+
 # ----------------------------------------------------------------------------
 # travelling tanh fronts (slow decay)
 # ----------------------------------------------------------------------------

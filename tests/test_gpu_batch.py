@@ -107,8 +107,16 @@ def test_batch_items_against_the_oracle(batch):
         U, S, V = h[i][0][:, :kk], h[i][1][:kk], h[i][2][:, :kk].astype(np.float64)
         eps_g = oracle.rel_fro_error(A, U, S, V)
         eps_o = oracle.rel_fro_error(A, o["U"], o["S"], o["V"])
-        # FP32 data, split-BF16 A-pass: same tolerance as the single-matrix blob test
-        assert abs(eps_g - eps_o) <= 1e-5 * eps_o + 64 * 2.0 ** -24
+        # FP32 data, split-BF16 A-pass.  eps is ~5e-5 for these heat items, below
+        # the 1e-4 where the 1e-5 relative tolerance applies; it is held to the
+        # product error bound instead: E = B_gpu - B, ||E||_F <= c || |Q|^T |A| ||_F
+        # (c = 3 * 2^-16 + (m + 2) u32), |eps_g^2 - eps_o^2| <= (2 ||E|| eps_o ||A|| + ||E||^2) / ||A||^2
+        nA = np.linalg.norm(A)
+        c = 3 * 2.0 ** -16 + (sp.m + 2) * 2.0 ** -24
+        e_b = c * np.linalg.norm(np.abs(o["Q"]).T @ np.abs(A))
+        if eps_o >= 1e-4:
+            assert abs(eps_g / eps_o - 1.0) <= 1e-5, (eps_g, eps_o)
+        assert abs(eps_g ** 2 - eps_o ** 2) <= (2 * e_b * eps_o * nA + e_b ** 2) / nA ** 2, (eps_g, eps_o)
         d = oracle.id_path(A, g, sp.k, q=0, rtol=1e-6)
         gaps = []
         oracle.row_id(d["G"], sp.k, gaps)
@@ -117,7 +125,55 @@ def test_batch_items_against_the_oracle(batch):
             if gp <= 1e-10:
                 break
             npre += 1
-        assert np.array_equal(h[i][3][:npre], d["J"][:npre])
+        # q = 0: the ID runs the FP64 CPQR on the FP64 sketch, and every
+        # margin of these items is far above its rounding: all k pivots match
+        assert npre == sp.k, (i, npre, min(gaps))
+        assert np.array_equal(h[i][3], d["J"])
+
+
+def test_batch_cpwr_items_against_the_oracle():
+    """Batch items with one C-PWR pass (q = 1, 2x injection subsample,
+    split-BF16 products) on spiked blob fields, whose every ID pivot has a
+    clear margin: J is the oracle's and eps within 1e-5 relative."""
+    torch = _torch()
+    from paper_2105_01271_gb300 import binding as b
+    cases = [(300, 64, 4, 12), (420, 64, 8, 10), (250, 128, 8, 16)]
+    items = (b.lrs_batch_item * len(cases))()
+    outs, mats = [], []
+    for it, (m, N, s, k) in zip(items, cases):
+        A, _ = synth.spiked_blob_field(m, N, 6, 40 + N, k, s, ratio=0.97, amp0=300.0)
+        Ad = torch.from_numpy(A).cuda()
+        mats.append((A, Ad))
+        U = torch.empty((m, k), dtype=torch.float64, device="cuda")
+        S = torch.empty((k,), dtype=torch.float64, device="cuda")
+        V = torch.empty((N * N, k), dtype=torch.float32, device="cuda")
+        J = torch.full((k,), -1, dtype=torch.int32, device="cuda")
+        P = torch.empty((m, k), dtype=torch.float64, device="cuda")
+        it.A, it.dtype, it.m, it.lda = Ad.data_ptr(), b.LRS_F32, m, N * N
+        it.sketch = b.make_grid((N, N), (s, s), "fullweight")
+        it.gram = b.make_grid((N, N), (2, 2), "inject")
+        it.q, it.k, it.prec, it.rtol = 1, k, b.LRS_PREC_SPLIT_BF16, 1e-6
+        it.do_svd, it.do_id = 1, 1
+        it.U, it.ldu, it.S, it.V, it.ldv = U.data_ptr(), k, S.data_ptr(), V.data_ptr(), k
+        it.J, it.P, it.ldp = J.data_ptr(), P.data_ptr(), k
+        outs.append((U, S, V, J, P))
+    b.run_batch(items, n_streams=2)
+    for i, (m, N, s, k) in enumerate(cases):
+        assert items[i].status == b.LRS_OK, items[i].error
+        A = mats[i][0].astype(np.float64)
+        g = GridSpec((N, N), (s, s), "fullweight")
+        gi = GridSpec((N, N), (2, 2), "inject")
+        o = oracle.svd_path(A, g, k, q=1, gram_grid=gi, rtol=1e-6)
+        d = oracle.id_path(A, g, k, q=1, gram_grid=gi, rtol=1e-6)
+        U, S, V, J, P = (t.cpu().numpy() for t in outs[i])
+        eps_g = oracle.rel_fro_error(A, U, S, V.astype(np.float64))
+        eps_o = oracle.rel_fro_error(A, o["U"], o["S"], o["V"])
+        assert eps_o >= 1e-4 and abs(eps_g / eps_o - 1.0) <= 1e-5, (i, eps_g, eps_o)
+        gaps = []
+        oracle.row_id(d["G"], k, gaps)
+        assert min(gaps) > 1e-2, (i, min(gaps))
+        assert np.array_equal(J, d["J"]), i
+        assert np.array_equal(P[J], np.eye(k))
 
 
 def test_autotune_picks_a_candidate(batch):
