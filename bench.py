@@ -1,13 +1,13 @@
 """Benchmark of the deterministic-sketch low-rank path on GB300.
 
 One step = one rank-k decomposition of one snapshot matrix through the C ABI:
-  SVD: lrs_power_pass (sketch + C-PWR, re-orthonormalised) -> lrs_range_find
-       -> lrs_svd_k            (paper Algs. 7 and 2)
-  ID : lrs_power_pass (C-PWR without re-orthonormalisation) -> lrs_id_k
-                               (paper Alg. 4)
-The SVD and the ID run concurrently (the ID on a second context and stream);
-the same step with the two one after the other is reported as
-serial_ms_per_step.
+  lrs_power_pass2: one touch of A_f (sketch + C-PWR subsample), both C-PWR
+       iterates (re-orthonormalised for the SVD, plain for the ID; Alg. 7)
+  SVD: [lrs_range_find] -> lrs_svd_k (paper Alg. 2)
+  ID : lrs_id_k (paper Alg. 4)
+After the shared pass the SVD and the ID run concurrently (the ID on a second
+context and stream); the same step with the two one after the other is
+reported as serial_ms_per_step.
 The default workload is the 2000-snapshot blob field on a 512^2 grid (FP32,
 full weighting onto 32^2, l = 1024, k = 50, q = 1).  The matrix (2.1 GB) is
 larger than L2 (129 MB), so no flush is needed between steps.
@@ -751,20 +751,27 @@ def run_ours(args, rank, world):
         bufs = path.Buffers(w.m, w.n, w.grid.l, w.k, A_d.device, prec == binding.LRS_PREC_FP64)
     stream.synchronize()
 
-    # The SVD and the ID of a step are independent decompositions of the same
-    # matrix (disjoint output buffers): they run concurrently, the ID on a
-    # second context with its own stream, driven from a worker thread (the
-    # ABI calls release the GIL).  Their one-block and barrier-bound kernels
-    # then overlap with the other path's work.
+    # One touch of A_f serves both paths (lrs_power_pass2: the sketch and the
+    # C-PWR subsample are read once, both iterates formed); then the SVD and
+    # the ID continue concurrently, the ID on a second context with its own
+    # stream, driven from a worker thread (the ABI calls release the GIL), so
+    # their one-block and barrier-bound kernels overlap with the other's.
     stream2 = torch.cuda.Stream(device=dev)
     ctx2 = binding.load(dev, stream2)
     from concurrent.futures import ThreadPoolExecutor
     pool = ThreadPoolExecutor(max_workers=1)
 
-    def step_on(Ad):
-        fut = pool.submit(path.id_path, ctx2, Ad, w.dtype, w.grid, w.k, w.q, w.gram, rtol, prec, bufs)
-        s_ = path.svd_path(ctx, Ad, w.dtype, w.grid, w.k, q=w.q, gram=w.gram, rtol=rtol, prec=prec, bufs=bufs)
+    def step_with(Ad, pr, b):
+        gc = path.power_pass2(ctx, Ad, w.dtype, w.grid, w.q, w.gram, rtol, pr, b)
+        e = torch.cuda.Event()
+        e.record(stream)
+        stream2.wait_event(e)
+        fut = pool.submit(path.id_from_pass, ctx2, w.m, w.grid, w.k, b)
+        s_ = path.svd_from_pass(ctx, Ad, w.dtype, w.grid, w.k, w.q, gc, rtol, pr, b)
         return s_, fut.result()
+
+    def step_on(Ad):
+        return step_with(Ad, prec, bufs)
 
     def join_streams():
         # stream waits for everything queued on stream2 so far
@@ -776,8 +783,9 @@ def run_ours(args, rank, world):
         return step_on(A_d)
 
     def serial_step():
-        s_ = path.svd_path(ctx, A_d, w.dtype, w.grid, w.k, q=w.q, gram=w.gram, rtol=rtol, prec=prec, bufs=bufs)
-        d_ = path.id_path(ctx, A_d, w.dtype, w.grid, w.k, q=w.q, gram=w.gram, rtol=rtol, prec=prec, bufs=bufs)
+        gc = path.power_pass2(ctx, A_d, w.dtype, w.grid, w.q, w.gram, rtol, prec, bufs)
+        s_ = path.svd_from_pass(ctx, A_d, w.dtype, w.grid, w.k, w.q, gc, rtol, prec, bufs)
+        d_ = path.id_from_pass(ctx, w.m, w.grid, w.k, bufs)
         return s_, d_
 
     clk = clocks_start(dev)
@@ -835,11 +843,11 @@ def run_ours(args, rank, world):
     # ---- per-call breakdown (one extra step, events around each ABI call) ----
     phases = {}
     with torch.cuda.stream(stream):
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         gg = binding.grid_of(w.gram) if w.gram is not None and w.q > 0 else None
         evs[0].record(stream)
-        gc = ctx.power_pass(A_d, binding.DTYPE[w.dtype], w.m, w.n, binding.grid_of(w.grid), gg, w.q, 1,
-                            rtol, prec, bufs.Y, w.grid.l, bufs.G, w.grid.l)
+        gc = ctx.power_pass2(A_d, binding.DTYPE[w.dtype], w.m, w.n, binding.grid_of(w.grid), gg, w.q, rtol, prec,
+                             bufs.Y, w.grid.l, bufs.Gid, w.grid.l, bufs.G, w.grid.l)
         evs[1].record(stream)
         if w.q > 0:
             Qb, ldq, r = bufs.G, w.grid.l, gc
@@ -851,13 +859,10 @@ def run_ours(args, rank, world):
         ctx.svd_k(A_d, binding.DTYPE[w.dtype], w.m, w.n, w.n, Qb, ldq, r, w.k, prec, bufs.U, w.k,
                   bufs.S, bufs.V, w.k)
         evs[3].record(stream)
-        ctx.power_pass(A_d, binding.DTYPE[w.dtype], w.m, w.n, binding.grid_of(w.grid), gg, w.q, 0,
-                       rtol, prec, bufs.Yid, w.grid.l, bufs.Gid, w.grid.l)
-        evs[4].record(stream)
         ctx.id_k(bufs.Gid, w.m, w.grid.l, w.grid.l, w.k, bufs.J, bufs.P, w.k)
-        evs[5].record(stream)
+        evs[4].record(stream)
     stream.synchronize()
-    names = ["power_pass(svd)", "range_find", "svd_k", "power_pass(id)", "id_k"]
+    names = ["power_pass2", "range_find", "svd_k", "id_k"]
     for i, nm in enumerate(names):
         phases[nm] = evs[i].elapsed_time(evs[i + 1])
 
@@ -996,12 +1001,8 @@ def run_ours(args, rank, world):
         pb = path.Buffers(w.m, w.n, w.grid.l, w.k, A_d.device, False)
 
         def pstep():
-            # the same concurrent arrangement as the headline step
-            fut = pool.submit(path.id_path, ctx2, A_d, w.dtype, w.grid, w.k, w.q, w.gram, rtol,
-                              binding.LRS_PREC_FP32, pb)
-            a = path.svd_path(ctx, A_d, w.dtype, w.grid, w.k, q=w.q, gram=w.gram, rtol=rtol,
-                              prec=binding.LRS_PREC_FP32, bufs=pb)
-            return a, fut.result()
+            # the same arrangement as the headline step, FP32 FMA products
+            return step_with(A_d, binding.LRS_PREC_FP32, pb)
         with torch.cuda.stream(stream):
             pstep()
             join_streams()

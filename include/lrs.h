@@ -124,6 +124,25 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
                           double* Y, int64_t ldy, double* G, int64_t ldg, int64_t* g_cols);
 
 /*
+ * lrs_power_pass2 -- both C-PWR iterates of one matrix from one touch of A_f
+ * (Sec. 5, Alg. 7): the sketch points and the Gram subsample W are read once,
+ * then the q iterations run twice on them, first without the optional
+ * re-orthonormalisations (G0: the iterate the row ID takes, as the paper's
+ * ID experiments run C-PWR) and then with them (G: the orthonormal basis the
+ * SVD takes).  Equal to lrs_power_pass(reorth = 0) -> G0 and
+ * lrs_power_pass(reorth = 1) -> G on the same arguments, bit for bit, with
+ * one sketch launch and one subsample gather instead of two of each.
+ *   Y   m x l FP64 (row stride ldy): the sketch A_f D.
+ *   G0  m x l FP64 (row stride ldg0): G_q without re-orthonormalisation.
+ *   G   m x l FP64 (row stride ldg): the re-orthonormalised G_q in its first
+ *       *g_cols columns.  q = 0 returns G0 = G = Y (*g_cols = l).
+ */
+lrs_status lrs_power_pass2(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t lda,
+                           const lrs_grid* sketch, const lrs_grid* gram, int32_t q, double rtol, int32_t prec,
+                           double* Y, int64_t ldy, double* G0, int64_t ldg0, double* G, int64_t ldg,
+                           int64_t* g_cols);
+
+/*
  * lrs_range_find -- orthonormal basis of the numerical range of G (the
  * "QR(A_c)" of Algs. 2/3 and "QR(G_q)" of Alg. 7), by Householder QR with
  * column pivoting in FP64, stopped before the first step whose largest

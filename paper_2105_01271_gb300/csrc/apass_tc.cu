@@ -23,6 +23,17 @@
 // The accumulator is double-buffered in TMEM, so the epilogue of tile t runs
 // under the MMAs of tile t+1.  Every wait is bounded (LRS_ETIMEOUT).
 //
+// Accumulation in K chunks.  The tensor core adds each MMA's products into
+// its FP32 accumulator with truncation, so a sum over the whole K sweep (K/16
+// MMAs per piece) drifts toward zero by about half an FP32 ulp per MMA: ~4e-6
+// relative at K = 2000, a systematic shrink of B that moves the relative
+// reconstruction error of a decomposition with eps ~ 2e-4 by ~3e-4.  So the
+// MMAs accumulate one chunk of kc slabs at a time (the double buffer now
+// alternates per chunk), and the epilogue adds each chunk to a running FP32
+// sum kept in a third TMEM region, with round-to-nearest: the drift per
+// chunk is then ~4 kc MMAs' worth, unbiased across chunks.  Configurations
+// whose TMEM cannot hold the running sum keep the whole-K accumulation.
+//
 // Shared-memory bandwidth, not HBM, is what limits this loop: per slab the
 // raw tile is written (TMA) and read (converters), the pieces are written and
 // then read by the MMAs.  To keep the MMA operand reads down, the X pieces sit
@@ -55,6 +66,7 @@ constexpr int kMmaWarp = 12, kRawWarp = 13, kXWarp = 14;
 constexpr int kThreads = 15 * 32;
 constexpr int kMaxRS = 8, kMaxPS = 4;
 constexpr int kMaxR = 256;              // UMMA N limit
+constexpr int kChunkSlabs = 2;          // K slabs (of TK snapshots) per accumulation chunk
 constexpr size_t kSmemBudget = 227 * 1024 - 2048;   // dynamic bytes (static barriers + slack kept aside)
 
 struct ApParams {
@@ -69,6 +81,8 @@ struct ApParams {
   uint32_t tmem_cols;         // allocated TMEM columns
   int nacc;                   // accumulator buffers (1 or 2)
   int stacked;                // 1: X pieces stacked along UMMA N (one MMA per data piece)
+  int kc;                     // K slabs per accumulation chunk (>= Kt: the whole K at once)
+  uint32_t sum_col;           // TMEM column of the running sum (kc < Kt)
   void* C; int c_f64; int c_trans; int vec_ok; int64_t ldc; double alpha;
   int accum;                // C += alpha X^T A instead of C = alpha X^T A
   int* err;
@@ -159,12 +173,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_apass(const __grid_constant__ C
   if (warp < kEpiWarps) {
     // ---------------- epilogue: TMEM -> C ----------------
     Ring ar(P.nacc);
-    for (int64_t tile = blockIdx.x; tile < P.Nt; tile += gridDim.x, ar.next()) {
+    bool eok = true;
+    for (int64_t tile = blockIdx.x; tile < P.Nt && eok; tile += gridDim.x) {
+     for (int64_t k0 = 0; k0 < P.Kt; k0 += P.kc, ar.next()) {
+      const bool first = k0 == 0, last = k0 + P.kc >= P.Kt;
       const int acc = ar.idx;
-      if (!warp_wait(&acc_full[acc], ar.phase, P.err, lane)) break;
+      if (!warp_wait(&acc_full[acc], ar.phase, P.err, lane)) { eok = false; break; }
       tc_fence_after();
       const int64_t n = tile * TN + warp * 32 + lane;
-      const uint32_t tbase = tmem + (uint32_t)acc * P.acc_cols + ((uint32_t)(warp * 32) << 16);
+      const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+      const uint32_t tbase = tmem + (uint32_t)acc * P.acc_cols + lanes;
+      const uint32_t sbase = tmem + P.sum_col + lanes;
       for (int c0 = 0; c0 < P.rN; c0 += 16) {
         uint32_t v[16];
         tmem_ld16(tbase + (uint32_t)c0, v);
@@ -179,6 +198,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_apass(const __grid_constant__ C
 #pragma unroll
             for (int e = 0; e < 16; ++e) v[e] = __float_as_uint(__uint_as_float(v[e]) + __uint_as_float(u[e]));
           }
+        }
+        if (!first) {
+          // running sum of the earlier chunks, added with round-to-nearest
+          uint32_t u[16];
+          tmem_ld16(sbase + (uint32_t)c0, u);
+          tmem_ld_wait();
+#pragma unroll
+          for (int e = 0; e < 16; ++e) v[e] = __float_as_uint(__uint_as_float(u[e]) + __uint_as_float(v[e]));
+        }
+        if (!last) {
+          tmem_st16(sbase + (uint32_t)c0, v);
+          continue;
         }
         if (n < P.N) {
           if (P.c_trans) {
@@ -255,9 +286,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_apass(const __grid_constant__ C
           }
         }
       }
+      if (!last) tmem_st_wait();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[acc]);
+     }
     }
   } else if (warp < kEpiWarps + kConvWarps) {
     // ---------------- converters ----------------
@@ -339,12 +372,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_apass(const __grid_constant__ C
       const uint32_t xpiece = (uint32_t)P.rN * 128u;
       Ring pr(P.PS), ar(P.nacc);
       bool ok = true;
-      for (int64_t tile = blockIdx.x; tile < P.Nt && ok; tile += gridDim.x, ar.next()) {
+      for (int64_t tile = blockIdx.x; tile < P.Nt && ok; tile += gridDim.x) {
+       for (int64_t k0 = 0; k0 < P.Kt && ok; k0 += P.kc, ar.next()) {
         const int acc = ar.idx;
-        if (!mbar_wait(&acc_empty[acc], ar.phase ^ 1u, P.err)) break;
+        if (!mbar_wait(&acc_empty[acc], ar.phase ^ 1u, P.err)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)acc * P.acc_cols;
-        for (int64_t kt = 0; kt < P.Kt; ++kt, pr.next()) {
+        const int64_t k1 = k0 + P.kc < P.Kt ? k0 + P.kc : P.Kt;
+        for (int64_t kt = k0; kt < k1; ++kt, pr.next()) {
           const int ps = pr.idx;
           const uint32_t ph = pr.phase;
           if (!mbar_wait(&x_full[ps], ph, P.err) || !mbar_wait(&a_full[ps], ph, P.err)) { ok = false; break; }
@@ -361,7 +396,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_apass(const __grid_constant__ C
                 const int nj = (SX < kP - i) ? SX : kP - i;
                 const uint64_t ad = sdesc_kmajor_sw128(a0 + i * kPieceA + kk * 32);
                 const uint64_t bd = sdesc_kmajor_sw128(x0 + kk * 32);
-                const uint32_t accum = (kt == 0 && kk == 0 && i == 0) ? 0u : 1u;
+                const uint32_t accum = (kt == k0 && kk == 0 && i == 0) ? 0u : 1u;
                 umma_bf16(d, ad, bd, idesc_bf16_f32(TN, nj * P.rN), accum);
               }
             }
@@ -375,7 +410,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_apass(const __grid_constant__ C
                   if (i + j >= kP) continue;
                   const uint64_t ad = sdesc_kmajor_sw128(a0 + i * kPieceA + kk * 32);
                   const uint64_t bd = sdesc_kmajor_sw128(x0 + j * xpiece + kk * 32);
-                  const uint32_t accum = (kt == 0 && kk == 0 && i == 0 && j == 0) ? 0u : 1u;
+                  const uint32_t accum = (kt == k0 && kk == 0 && i == 0 && j == 0) ? 0u : 1u;
                   umma_bf16(d, ad, bd, idesc, accum);
                 }
             }
@@ -384,6 +419,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_apass(const __grid_constant__ C
         }
         if (!ok) break;
         umma_commit(&acc_full[acc]);
+       }
       }
       // every MMA this thread issued has finished before TMEM is released
       umma_commit(&mma_done);
@@ -466,6 +502,8 @@ struct ApCfg {
   int rN, RS, PS, stacked;
   uint32_t raw_bytes, stage_bytes, acc_cols, tmem_cols;
   int nacc;
+  int kc;             // slabs per accumulation chunk, 0: whole K
+  uint32_t sum_col;
   size_t smem;
 };
 
@@ -484,22 +522,38 @@ bool plan(int64_t M, int esize, int SA, int SX, ApCfg* c) {
   }
   if (c->RS < 2) return false;
   c->smem = 1024 + (size_t)c->RS * c->raw_bytes + (size_t)c->PS * c->stage_bytes;
-  // stacking needs the widest MMA, max(SA, SX) pieces of rN, within UMMA N <= 256
+  // stacking needs the widest MMA, max(SA, SX) pieces of rN, within UMMA N <= 256.
+  // Preference: K-chunked accumulation (accuracy) over stacking (fewer operand
+  // reads): stacked + chunked, unstacked + chunked, then the whole-K forms.
   const int kp = SA > SX ? SA : SX;
-  c->stacked = (LRS_APASS_STACK && kp * c->rN <= kMaxR) ? 1 : 0;
-  const int width = c->stacked ? SX * c->rN : c->rN;
-  c->acc_cols = (uint32_t)((width + 63) / 64 * 64);
-  uint32_t cols = 32;
-  while (cols < 2 * c->acc_cols) cols <<= 1;
-  if (cols <= 512) {
-    c->nacc = 2;
-  } else {
-    c->nacc = 1;
-    cols = 32;
-    while (cols < c->acc_cols) cols <<= 1;
+  const bool can_stack = LRS_APASS_STACK && kp * c->rN <= kMaxR;
+  auto pow2 = [](uint32_t need) { uint32_t cols = 32; while (cols < need) cols <<= 1; return cols; };
+  const uint32_t sum_cols = (uint32_t)c->rN;
+  for (int form = 0; form < 4; ++form) {
+    const int stacked = (form == 0 || form == 2) ? 1 : 0;
+    const bool chunked = form < 2;
+    if (stacked && !can_stack) continue;
+    const int width = stacked ? SX * c->rN : c->rN;
+    const uint32_t acc_cols = (uint32_t)((width + 63) / 64 * 64);
+    if (chunked) {
+      const uint32_t cols = pow2(2 * acc_cols + sum_cols);
+      if (cols > 512) continue;
+      c->stacked = stacked; c->acc_cols = acc_cols; c->nacc = 2; c->tmem_cols = cols;
+      c->sum_col = 2 * acc_cols; c->kc = kChunkSlabs;
+      return true;
+    }
+    c->stacked = stacked; c->acc_cols = acc_cols; c->sum_col = 0; c->kc = 0;
+    uint32_t cols = pow2(2 * acc_cols);
+    if (cols <= 512) {
+      c->nacc = 2;
+    } else {
+      c->nacc = 1;
+      cols = pow2(acc_cols);
+    }
+    c->tmem_cols = cols;
+    return true;
   }
-  c->tmem_cols = cols;
-  return true;
+  return false;
 }
 
 template <int RAW, int SA, int SX>
@@ -526,6 +580,8 @@ lrs_status run_apass(lrs_ctx* ctx, const GemmArgs& a, double* fro2_out) {
   P.rN = cfg.rN; P.RS = cfg.RS; P.PS = cfg.PS;
   P.raw_bytes = cfg.raw_bytes; P.stage_bytes = cfg.stage_bytes;
   P.acc_cols = cfg.acc_cols; P.tmem_cols = cfg.tmem_cols; P.nacc = cfg.nacc; P.stacked = cfg.stacked;
+  P.kc = cfg.kc > 0 ? cfg.kc : (int)P.Kt;
+  P.sum_col = cfg.sum_col;
   P.C = a.C; P.c_f64 = a.c_f64; P.c_trans = a.c_trans; P.ldc = a.ldc; P.alpha = a.alpha; P.accum = a.accum;
   P.vec_ok = ((reinterpret_cast<uintptr_t>(a.C) & 15u) == 0 && (a.ldc & 3) == 0) ? 1 : 0;
 

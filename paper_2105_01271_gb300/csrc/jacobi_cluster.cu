@@ -20,9 +20,9 @@
 // (2 NC - 1 rounds, every block pair meets once; the blocks' internal pairs
 // are taken in the first round of the sweep): CTA i holds the blocks at
 // tournament positions i and 2 NC - 1 - i in its shared memory, rotates the
-// b x b cross pairs in b conflict-free sub-rounds (a team of kTeam lanes per
-// pair, FP64 throughout), then sends each block it gives up straight into
-// the shared memory of the CTA that takes it next (distributed shared memory),
+// b x b cross pairs in b conflict-free sub-rounds (a warp per pair, FP64
+// data throughout), then sends each block it gives up straight into the
+// shared memory of the CTA that takes it next (distributed shared memory),
 // double-buffered by round parity, with one cluster barrier per round.
 // On GB300 an SM retires 2 FP64 FMAs per clock, so spreading the sweep over
 // up to 16 SMs with a hardware barrier is what makes FP64 affordable here.
@@ -39,7 +39,6 @@ namespace lrs {
 
 namespace {
 
-constexpr int kTeam = 8;             // lanes per column pair
 constexpr int kMaxSweeps = 40;
 
 struct JacRowsArgs {
@@ -51,8 +50,20 @@ struct JacRowsArgs {
   int* sweeps;          // out: sweeps taken (for tests and tuning)
 };
 
-// shared layout per CTA: buf[parity][slot] = b columns of rs doubles, then
-// ids[parity][slot][b] (global column index, -1 for pad), counters
+// One warp per column pair.  The FP64 pipe of a GB300 SM retires 2 FMAs per
+// clock, shared by its four schedulers, so a CTA keeps b >= 4 warps (one pair
+// each) busy per sub-round.  Per pair: the dot product g = x.y (one FMA per
+// element), the rotation (four FP64 operations per element) and the column
+// norms tracked through the rotation (a' = c^2 (a - 2 t g + t^2 b), b' = c^2
+// (b + 2 t g + t^2 a), recomputed from the columns at the start of every
+// sweep).  The angle t = tan(theta) is solved in FP32 from the FP64 a, b, g;
+// c = (1 + t^2)^-1/2 and s = c t are formed in FP64 from that t, so the
+// rotation is orthogonal to FP64 rounding whatever the accuracy of t (a
+// less accurate angle only leaves a smaller off-diagonal for the next sweep).
+//
+// shared layout per CTA: buf[parity][slot] = b columns of rs doubles,
+// nrm[parity][slot][b] (tracked squared norms), ids[parity][slot][b]
+// (global column index, -1 for pad), per-sweep rotation counters
 __global__ void __launch_bounds__(256, 1) k_jacobi_rows_cl(JacRowsArgs a) {
   extern __shared__ double jsm[];
   cg::cluster_group cl = cg::this_cluster();
@@ -61,13 +72,12 @@ __global__ void __launch_bounds__(256, 1) k_jacobi_rows_cl(JacRowsArgs a) {
   const int b = a.b, rs = a.rs, r = a.r;
   const int blk = b * rs;                               // doubles per block
   double* buf = jsm;                                    // [2][2][blk]
-  int* ids = reinterpret_cast<int*>(buf + 4 * blk);     // [2][2][b]
+  double* nrm = buf + 4 * blk;                          // [2][2][b]
+  int* ids = reinterpret_cast<int*>(nrm + 4 * b);       // [2][2][b]
   int* rotc = ids + 4 * b;                              // [kMaxSweeps] (CTA 0's copy is the sum)
   __shared__ int s_rot;
   const int tid = threadIdx.x, nth = blockDim.x;
-  const int lg = tid % kTeam, team = tid / kTeam, nteam = nth / kTeam;
-  const int lane = tid & 31;
-  const unsigned gmask = ((1u << kTeam) - 1u) << (lane & (32 - kTeam));
+  const int lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
   const int nb2 = 2 * NC;
 
   // ---- round 0: CTA i holds block i (slot 0) and block 2 NC - 1 - i (slot 1)
@@ -91,48 +101,65 @@ __global__ void __launch_bounds__(256, 1) k_jacobi_rows_cl(JacRowsArgs a) {
   const double tol = eps * (double)(r > 16 ? r : 16);   // |x.y| <= tol ||x|| ||y||: orthogonal
   const double tol2 = tol * tol;
 
-  // rotate the pair (x, y) of columns in place (a team of kTeam lanes)
-  auto rotate = [&](double* x, double* y) -> int {
-    double aa = 0.0, bb = 0.0, gg = 0.0;
-    for (int i = lg; i < rs; i += kTeam) {
-      const double u = x[i], v = y[i];
-      aa = fma(u, u, aa); bb = fma(v, v, bb); gg = fma(u, v, gg);
-    }
-#pragma unroll
-    for (int o = kTeam / 2; o > 0; o >>= 1) {
-      aa += __shfl_xor_sync(gmask, aa, o);
-      bb += __shfl_xor_sync(gmask, bb, o);
-      gg += __shfl_xor_sync(gmask, gg, o);
-    }
+  // rotate the pair (x, y) with tracked squared norms (na, nb) in place (one warp)
+  auto rotate = [&](double* x, double* y, double* na, double* nb) -> int {
+    double gg = 0.0;
+    for (int i = lane; i < rs; i += 32) gg = fma(x[i], y[i], gg);
+    gg = warp_sum(gg);
+    const double aa = *na, bb = *nb;
     if (gg == 0.0 || gg * gg <= tol2 * (aa * bb)) return 0;
-    const double zeta = (bb - aa) / (2.0 * gg);
-    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-    const double cs = 1.0 / sqrt(1.0 + t * t);
+    // tan(theta) in FP32: zeta = (b - a) / (2 g), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2))
+    const float zf = (float)(bb - aa) / (float)(2.0 * gg);
+    const float tf = copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)));
+    if (!(tf != 0.0f)) return 0;
+    const double t = (double)tf;
+    const double cs = rsqrt_newton(fma(t, t, 1.0));
     const double sn = cs * t;
-    for (int i = lg; i < rs; i += kTeam) {
+    for (int i = lane; i < rs; i += 32) {
       const double u = x[i], v = y[i];
-      x[i] = cs * u - sn * v;
-      y[i] = sn * u + cs * v;
+      x[i] = fma(-sn, v, cs * u);
+      y[i] = fma(sn, u, cs * v);
     }
+    __syncwarp();
+    if (lane == 0) {
+      const double c2 = cs * cs, tg = 2.0 * t * gg, t2 = t * t;
+      *na = c2 * (fma(t2, bb, aa) - tg);
+      *nb = c2 * (fma(t2, aa, bb) + tg);
+    }
+    __syncwarp();
     return 1;
+  };
+  // squared norms of the columns this CTA holds (start of every sweep)
+  auto renorm = [&](int p) {
+    for (int q = wid; q < 2 * b; q += nw) {
+      const int slot = q / b, j = q - slot * b;
+      const double* x = buf + (p * 2 + slot) * blk + j * rs;
+      double t = 0.0;
+      for (int i = lane; i < rs; i += 32) t = fma(x[i], x[i], t);
+      t = warp_sum(t);
+      if (lane == 0) nrm[(p * 2 + slot) * b + j] = t;
+    }
   };
 
   int par = 0, sweep = 0;
   for (; sweep < kMaxSweeps; ++sweep) {
     if (tid == 0) s_rot = 0;
+    renorm(par);
     __syncthreads();
+    int nrot = 0;                                       // lane 0 of each warp counts
     for (int round = 0; round < nb2 - 1; ++round) {
       double* A0 = buf + (par * 2 + 0) * blk;
       double* B0 = buf + (par * 2 + 1) * blk;
+      double* nA = nrm + (par * 2 + 0) * b;
+      double* nB = nrm + (par * 2 + 1) * b;
       const int* idA = ids + (par * 2 + 0) * b;
       const int* idB = ids + (par * 2 + 1) * b;
-      int nrot = 0;
       if (round == 0) {
         // internal pairs of both blocks: round-robin within a block, b' = b
         // rounded up to even, pairs (u, b' - 1 - u) with slot 0 fixed
         const int bp = (b + 1) & ~1;
         for (int sr = 0; sr < bp - 1; ++sr) {
-          for (int pr = team; pr < bp; pr += nteam) {      // bp / 2 pairs per block, 2 blocks
+          for (int pr = wid; pr < bp; pr += nw) {        // bp / 2 pairs per block, 2 blocks
             const int which = pr / (bp / 2), u = pr % (bp / 2);
             auto slotpos = [&](int sidx) -> int {
               if (sidx == 0) return 0;
@@ -146,24 +173,22 @@ __global__ void __launch_bounds__(256, 1) k_jacobi_rows_cl(JacRowsArgs a) {
             const int* id = which == 0 ? idA : idB;
             if (id[p] < 0 || id[q] < 0) continue;
             double* base = which == 0 ? A0 : B0;
-            const int did = rotate(base + p * rs, base + q * rs);
-            if (lg == 0) nrot += did;
+            double* nn = which == 0 ? nA : nB;
+            nrot += rotate(base + p * rs, base + q * rs, nn + p, nn + q);
           }
           __syncthreads();
         }
       }
       // cross pairs: sub-round u pairs column j of A with column (j + u) mod b of B
       for (int u = 0; u < b; ++u) {
-        for (int j = team; j < b; j += nteam) {
+        for (int j = wid; j < b; j += nw) {
           int q = j + u;
           if (q >= b) q -= b;
           if (idA[j] < 0 || idB[q] < 0) continue;
-          const int did = rotate(A0 + j * rs, B0 + q * rs);
-          if (lg == 0) nrot += did;
+          nrot += rotate(A0 + j * rs, B0 + q * rs, nA + j, nB + q);
         }
         __syncthreads();
       }
-      if (lg == 0 && nrot) atomicAdd(&s_rot, nrot);
       // ---- hand the blocks on (tournament rotation of positions 1 .. 2NC-1) ----
       // slot 0 of CTA i is position i, slot 1 is position 2NC-1-i.  Position p
       // moves to p + 1 (2NC-1 wraps to 1); position 0 stays.
@@ -174,13 +199,16 @@ __global__ void __launch_bounds__(256, 1) k_jacobi_rows_cl(JacRowsArgs a) {
         const int dcta = dpos < NC ? dpos : nb2 - 1 - dpos;
         const int dslot = dpos < NC ? 0 : 1;
         double* dst = cl.map_shared_rank(buf + (npar * 2 + dslot) * blk, dcta);
+        double* dnr = cl.map_shared_rank(nrm + (npar * 2 + dslot) * b, dcta);
         int* did = cl.map_shared_rank(ids + (npar * 2 + dslot) * b, dcta);
         const double* src = buf + (par * 2 + slot) * blk;
         for (int e = tid; e < blk; e += nth) dst[e] = src[e];
+        const double* snr = nrm + (par * 2 + slot) * b;
         const int* sid = ids + (par * 2 + slot) * b;
-        for (int e = tid; e < b; e += nth) did[e] = sid[e];
+        for (int e = tid; e < b; e += nth) { dnr[e] = snr[e]; did[e] = sid[e]; }
       }
       if (round == nb2 - 2) {
+        if (lane == 0 && nrot) atomicAdd(&s_rot, nrot);
         __syncthreads();                                 // s_rot complete
         if (tid == 0 && s_rot) atomicAdd(cl.map_shared_rank(rotc + sweep, 0), s_rot);
       }
@@ -246,49 +274,50 @@ struct ClusterPlan {
 };
 
 size_t rows_smem(int b, int rs) {
-  return sizeof(double) * (size_t)(4 * b * rs) + sizeof(int) * (size_t)(4 * b + kMaxSweeps) + 64;
+  return sizeof(double) * (size_t)(4 * b * rs + 4 * b) + sizeof(int) * (size_t)(4 * b + kMaxSweeps) + 64;
 }
 
-// cluster size: the padded column count 2 NC b should stay close to r (pad
-// columns cost pairs) while NC is as large as the hardware schedules
-// (per-SM FP64 throughput is the bound); estimate the sweep cost as the
-// per-CTA pair work plus a barrier term per round
-ClusterPlan plan_for(lrs_ctx* ctx, int r) {
-  ClusterPlan best;
-  double best_cost = 1e300;
+bool cluster_fits(int nc, int threads, size_t smem) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nc);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)nc;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  const cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, (const void*)k_jacobi_rows_cl, &cfg);
+  if (e != cudaSuccess) { cudaGetLastError(); return false; }
+  return nclusters >= 1;
+}
+
+// Blocks of 4 columns give each CTA four pairs per sub-round (a warp each, one
+// per scheduler), and as many CTAs as that leaves (r / 8, at most 16): the
+// per-SM FP64 throughput is the bound, so the sweep is spread as widely as
+// the pair count allows while every CTA still fills its four schedulers.
+ClusterPlan plan_for(int r) {
+  ClusterPlan pl;
   const int rs = (r + 1) & ~1;
-  for (int nc = 16; nc >= 2; --nc) {
-    const int b = (r + 2 * nc - 1) / (2 * nc);
-    if (b < 1) continue;
-    const int cols = 2 * nc * b;
-    const double pairs_per_cta = (double)cols * (cols - 1) / 2.0 / nc;
-    const double cost = pairs_per_cta * (double)rs / kTeam + 120.0 * (2 * nc - 1);
-    if (cost < best_cost) {
-      // can the device schedule a cluster of this size with this shared memory?
-      int threads = ((b * kTeam + 31) / 32) * 32;
-      if (threads < 64) threads = 64;
-      if (threads > 256) threads = 256;
-      const size_t smem = rows_smem(b, rs);
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3((unsigned)nc);
-      cfg.blockDim = dim3((unsigned)threads);
-      cfg.dynamicSmemBytes = smem;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = (unsigned)nc;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      int nclusters = 0;
-      const cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, (const void*)k_jacobi_rows_cl, &cfg);
-      if (e != cudaSuccess) { cudaGetLastError(); continue; }
-      if (nclusters < 1) continue;
-      best_cost = cost;
-      best.nc = nc; best.b = b; best.threads = threads; best.smem = smem;
+  int b = 4;
+  int nc = (r + 2 * b - 1) / (2 * b);
+  if (nc > 16) { nc = 16; b = (r + 31) / 32; }
+  if (nc < 2) { nc = 2; b = (r + 3) / 4; }
+  for (; nc >= 2; --nc) {
+    const int bb = (r + 2 * nc - 1) / (2 * nc);
+    if (bb > 8) break;                                   // 8 warps per CTA at most
+    const int bp = (bb + 1) & ~1;
+    const int threads = 32 * (bp > 2 ? bp : 2);
+    const size_t smem = rows_smem(bb, rs);
+    if (cluster_fits(nc, threads, smem)) {
+      pl.nc = nc; pl.b = bb; pl.threads = threads; pl.smem = smem;
+      return pl;
     }
   }
-  return best;
+  return pl;
 }
 
 }  // namespace
@@ -310,7 +339,7 @@ lrs_status launch_jacobi_rows(lrs_ctx* ctx, const double* R, int64_t r, int64_t 
     attr_set[ctx->device] = 1;
   }
   const int ri = (int)r;
-  ClusterPlan pl = plan_for(ctx, ri);
+  ClusterPlan pl = plan_for(ri);
   if (pl.nc < 2) return LRS_ERANK;
   if (pl.smem > 48 * 1024) {
     const lrs_status st = raise_dyn_smem(ctx, (const void*)k_jacobi_rows_cl, pl.smem);

@@ -337,82 +337,55 @@ lrs_status lrs_range_find_diag(lrs_ctx* ctx, const double* G, int64_t m, int64_t
   return orth(ctx, G, m, l, ldg, rtol, Q, ldq, r_out, false, rdiag);
 }
 
-lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t lda,
-                          const lrs_grid* sketch, const lrs_grid* gram, int32_t q, int32_t reorth,
-                          double rtol, int32_t prec, double* Y, int64_t ldy, double* G, int64_t ldg,
-                          int64_t* g_cols) {
-  if (!ctx) return LRS_EINVAL;
-  ctx->err[0] = 0;
-  GridDev gs, gg;
-  char why[256];
-  if (!grid_from_abi(sketch, &gs, why, sizeof why)) return lrs_fail(ctx, LRS_EINVAL, "power_pass: sketch grid: %s", why);
-  if (!A || !Y || !G || !g_cols) return lrs_fail(ctx, LRS_EINVAL, "power_pass: NULL pointer");
-  if (!dtype_ok(dtype) || !prec_ok(prec)) return lrs_fail(ctx, LRS_EINVAL, "power_pass: bad dtype/prec");
-  if (m < 1 || q < 0 || q > 16) return lrs_fail(ctx, LRS_EINVAL, "power_pass: m=%lld q=%d", (long long)m, q);
-  if (lda < gs.n || ldy < gs.l || ldg < gs.l) return lrs_fail(ctx, LRS_EINVAL, "power_pass: strides too small");
-  if (!(rtol >= 0.0) || rtol >= 1.0) return lrs_fail(ctx, LRS_EINVAL, "power_pass: rtol=%g not in [0,1)", rtol);
-  if (q > 0) {
-    if (!grid_from_abi(gram, &gg, why, sizeof why)) return lrs_fail(ctx, LRS_EINVAL, "power_pass: gram grid: %s", why);
-    if (gg.n != gs.n) return lrs_fail(ctx, LRS_EINVAL, "power_pass: gram grid has n=%lld, sketch n=%lld", (long long)gg.n, (long long)gs.n);
-  }
-  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-  const int64_t l = gs.l;
-  const int64_t nI = q > 0 ? gg.l : 0;
+}  // extern "C"
+
+namespace lrs {
+
+// workspace of one C-PWR pass (W, W^T and the loop buffers)
+static size_t cpwr_ws(lrs_ctx* ctx, int64_t m, int64_t l, int64_t nI, int32_t prec) {
   const int64_t wmax = l > m ? l : m;
-  // Tensor-core modes split every operand into BF16 pieces (<= 24 bits), so
-  // their operands are kept in FP32 (exact for FP32/BF16 data); the CUDA-core
-  // modes read FP64 operands directly.
   const bool tc = prec >= LRS_PREC_SPLIT_BF16;
   const size_t wsz = tc ? 4 : 8;
   size_t need = 0;
-  if (q > 0) {
-    need += 2 * align256(wsz * (size_t)(m * nI));                     // W, W^T
-    need += align256(8 * (size_t)(nI * wmax)) + 2 * align256(8 * (size_t)(m * wmax));
-    need += align256(8 * (size_t)(nI * wmax));                        // orthonormal T
-    if (tc) need += align256(4 * (size_t)(nI * wmax)) + align256(4 * (size_t)(m * wmax));  // FP32 operands
-    const size_t o1 = orth_ws(m, l, ctx->num_sms), o2 = orth_ws(nI, wmax, ctx->num_sms);
-    size_t inner = o1 > o2 ? o1 : o2;
-    if (tc) {
-      // either operand may be the prepared one (the narrow one when it is <= 256 wide)
-      const size_t t1 = gemm_tc_workspace(nI > wmax ? nI : wmax, m, prec) +
-                        gemm_tc_splitk_workspace(nI > wmax ? nI : wmax, nI > wmax ? nI : wmax, m, ctx->num_sms) +
-                        gemm_tc_a_workspace(nI > wmax ? nI : wmax, m, prec);
-      const size_t t2 = gemm_tc_workspace(wmax, nI, prec) + gemm_tc_splitk_workspace(wmax, wmax, nI, ctx->num_sms) +
-                        gemm_tc_a_workspace(wmax, nI, prec);
-      const size_t t = (t1 > t2 ? t1 : t2) + 4096;
-      if (t > inner) inner = t;
-    }
-    need += inner;
+  need += 2 * align256(wsz * (size_t)(m * nI));                     // W, W^T
+  need += align256(8 * (size_t)(nI * wmax)) + 2 * align256(8 * (size_t)(m * wmax));
+  need += align256(8 * (size_t)(nI * wmax));                        // orthonormal T
+  if (tc) need += align256(4 * (size_t)(nI * wmax)) + align256(4 * (size_t)(m * wmax));  // FP32 operands
+  const size_t o1 = orth_ws(m, l, ctx->num_sms), o2 = orth_ws(nI, wmax, ctx->num_sms);
+  size_t inner = o1 > o2 ? o1 : o2;
+  if (tc) {
+    // either operand may be the prepared one (the narrow one when it is <= 256 wide)
+    const size_t t1 = gemm_tc_workspace(nI > wmax ? nI : wmax, m, prec) +
+                      gemm_tc_splitk_workspace(nI > wmax ? nI : wmax, nI > wmax ? nI : wmax, m, ctx->num_sms) +
+                      gemm_tc_a_workspace(nI > wmax ? nI : wmax, m, prec);
+    const size_t t2 = gemm_tc_workspace(wmax, nI, prec) + gemm_tc_splitk_workspace(wmax, wmax, nI, ctx->num_sms) +
+                      gemm_tc_a_workspace(wmax, nI, prec);
+    const size_t t = (t1 > t2 ? t1 : t2) + 4096;
+    if (t > inner) inner = t;
   }
-  lrs_status st = ws_reserve(ctx, need);
-  if (st) return st;
-  st = launch_sketch(ctx, A, dtype, m, lda, gs, Y, ldy);
-  if (st) return st;
-  if (q == 0) {
-    LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(G, ldg * 8, Y, ldy * 8, l * 8, m, cudaMemcpyDeviceToDevice, ctx->stream));
-    *g_cols = l;
-    return LRS_OK;
-  }
-  void* W = ws_alloc(ctx, wsz * (size_t)(m * nI));
-  void* WT = ws_alloc(ctx, wsz * (size_t)(m * nI));
+  return need + inner;
+}
+
+// The C-PWR loop of Alg. 7 from a given sketch Y (m x l, ldy) and the
+// gathered subsample W (m x nI) and W^T (nI x m), both in wdt: q iterations
+// G <- W^T G; [QR]; G <- W G; [QR].  Loop buffers come from the workspace
+// above the caller's mark; the result is copied to G (ldg), *g_cols columns.
+static lrs_status cpwr_loop(lrs_ctx* ctx, const void* W, const void* WT, int64_t m, int64_t l, int64_t nI,
+                            const double* Y, int64_t ldy, int32_t q, int32_t reorth, double rtol, int32_t prec,
+                            double* G, int64_t ldg, int64_t* g_cols) {
+  const int64_t wmax = l > m ? l : m;
+  const bool tc = prec >= LRS_PREC_SPLIT_BF16;
+  const int32_t wdt = tc ? LRS_F32 : LRS_F64;
   double* Tm = (double*)ws_alloc(ctx, 8 * (size_t)(nI * wmax));
   double* To = (double*)ws_alloc(ctx, 8 * (size_t)(nI * wmax));
   double* Ga = (double*)ws_alloc(ctx, 8 * (size_t)(m * wmax));
   double* Gb = (double*)ws_alloc(ctx, 8 * (size_t)(m * wmax));
   float* T32 = tc ? (float*)ws_alloc(ctx, 4 * (size_t)(nI * wmax)) : nullptr;
   float* G32 = tc ? (float*)ws_alloc(ctx, 4 * (size_t)(m * wmax)) : nullptr;
-  if (!W || !WT || !Tm || !To || !Ga || !Gb || (tc && (!T32 || !G32)))
+  if (!Tm || !To || !Ga || !Gb || (tc && (!T32 || !G32)))
     return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (power_pass)");
   const size_t mark = ctx->ws_top;
-  const int32_t wdt = tc ? LRS_F32 : LRS_F64;
-  if (tc) {
-    st = launch_gather32_both(ctx, A, dtype, m, lda, gg, (float*)W, nI, (float*)WT, m);
-  } else {
-    st = launch_gather(ctx, A, dtype, m, lda, gg, (double*)W, nI);
-    if (st) return st;
-    st = launch_transpose(ctx, (const double*)W, m, nI, nI, (double*)WT, m);
-  }
-  if (st) return st;
+  lrs_status st = LRS_OK;
   // starting block: Q_np = QR(A_f D) with re-orthonormalisation, else A_f D
   int64_t gc = l;
   const double* Gcur = Y;
@@ -481,6 +454,113 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
   }
   LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(G, ldg * 8, Gcur, ldcur * 8, gc * 8, m, cudaMemcpyDeviceToDevice, ctx->stream));
   *g_cols = gc;
+  return LRS_OK;
+}
+
+// validation shared by lrs_power_pass and lrs_power_pass2
+static lrs_status power_pass_check(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t lda,
+                                   const lrs_grid* sketch, const lrs_grid* gram, int32_t q, double rtol,
+                                   int32_t prec, GridDev* gs, GridDev* gg) {
+  char why[256];
+  if (!grid_from_abi(sketch, gs, why, sizeof why)) return lrs_fail(ctx, LRS_EINVAL, "power_pass: sketch grid: %s", why);
+  if (!A) return lrs_fail(ctx, LRS_EINVAL, "power_pass: NULL pointer");
+  if (!dtype_ok(dtype) || !prec_ok(prec)) return lrs_fail(ctx, LRS_EINVAL, "power_pass: bad dtype/prec");
+  if (m < 1 || q < 0 || q > 16) return lrs_fail(ctx, LRS_EINVAL, "power_pass: m=%lld q=%d", (long long)m, q);
+  if (lda < gs->n) return lrs_fail(ctx, LRS_EINVAL, "power_pass: lda too small");
+  if (!(rtol >= 0.0) || rtol >= 1.0) return lrs_fail(ctx, LRS_EINVAL, "power_pass: rtol=%g not in [0,1)", rtol);
+  if (q > 0) {
+    if (!grid_from_abi(gram, gg, why, sizeof why)) return lrs_fail(ctx, LRS_EINVAL, "power_pass: gram grid: %s", why);
+    if (gg->n != gs->n) return lrs_fail(ctx, LRS_EINVAL, "power_pass: gram grid has n=%lld, sketch n=%lld", (long long)gg->n, (long long)gs->n);
+  }
+  return LRS_OK;
+}
+
+// the one touch of A_f: the sketch Y, and with q > 0 the subsample W and
+// W^T (FP32 for the tensor-core modes, else FP64) in the workspace
+static lrs_status touch(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t lda, const GridDev& gs,
+                        const GridDev& gg, int32_t q, int32_t prec, double* Y, int64_t ldy, void** W, void** WT) {
+  lrs_status st = launch_sketch(ctx, A, dtype, m, lda, gs, Y, ldy);
+  if (st || q == 0) return st;
+  const int64_t nI = gg.l;
+  const bool tc = prec >= LRS_PREC_SPLIT_BF16;
+  const size_t wsz = tc ? 4 : 8;
+  *W = ws_alloc(ctx, wsz * (size_t)(m * nI));
+  *WT = ws_alloc(ctx, wsz * (size_t)(m * nI));
+  if (!*W || !*WT) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (power_pass)");
+  if (tc) return launch_gather32_both(ctx, A, dtype, m, lda, gg, (float*)*W, nI, (float*)*WT, m);
+  st = launch_gather(ctx, A, dtype, m, lda, gg, (double*)*W, nI);
+  if (st) return st;
+  return launch_transpose(ctx, (const double*)*W, m, nI, nI, (double*)*WT, m);
+}
+
+}  // namespace lrs
+
+extern "C" {
+
+lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t lda,
+                          const lrs_grid* sketch, const lrs_grid* gram, int32_t q, int32_t reorth,
+                          double rtol, int32_t prec, double* Y, int64_t ldy, double* G, int64_t ldg,
+                          int64_t* g_cols) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  GridDev gs, gg;
+  lrs_status st = power_pass_check(ctx, A, dtype, m, lda, sketch, gram, q, rtol, prec, &gs, &gg);
+  if (st) return st;
+  if (!Y || !G || !g_cols) return lrs_fail(ctx, LRS_EINVAL, "power_pass: NULL pointer");
+  if (ldy < gs.l || ldg < gs.l) return lrs_fail(ctx, LRS_EINVAL, "power_pass: strides too small");
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const int64_t l = gs.l;
+  const int64_t nI = q > 0 ? gg.l : 0;
+  st = ws_reserve(ctx, q > 0 ? cpwr_ws(ctx, m, l, nI, prec) : 0);
+  if (st) return st;
+  void *W = nullptr, *WT = nullptr;
+  st = touch(ctx, A, dtype, m, lda, gs, gg, q, prec, Y, ldy, &W, &WT);
+  if (st) return st;
+  if (q == 0) {
+    LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(G, ldg * 8, Y, ldy * 8, l * 8, m, cudaMemcpyDeviceToDevice, ctx->stream));
+    *g_cols = l;
+    return LRS_OK;
+  }
+  st = cpwr_loop(ctx, W, WT, m, l, nI, Y, ldy, q, reorth, rtol, prec, G, ldg, g_cols);
+  if (st) return st;
+  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return LRS_OK;
+}
+
+lrs_status lrs_power_pass2(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t lda,
+                           const lrs_grid* sketch, const lrs_grid* gram, int32_t q, double rtol, int32_t prec,
+                           double* Y, int64_t ldy, double* G0, int64_t ldg0, double* G, int64_t ldg,
+                           int64_t* g_cols) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  GridDev gs, gg;
+  lrs_status st = power_pass_check(ctx, A, dtype, m, lda, sketch, gram, q, rtol, prec, &gs, &gg);
+  if (st) return st;
+  if (!Y || !G || !G0 || !g_cols) return lrs_fail(ctx, LRS_EINVAL, "power_pass2: NULL pointer");
+  if (ldy < gs.l || ldg < gs.l || ldg0 < gs.l) return lrs_fail(ctx, LRS_EINVAL, "power_pass2: strides too small");
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const int64_t l = gs.l;
+  const int64_t nI = q > 0 ? gg.l : 0;
+  st = ws_reserve(ctx, q > 0 ? cpwr_ws(ctx, m, l, nI, prec) : 0);
+  if (st) return st;
+  void *W = nullptr, *WT = nullptr;
+  st = touch(ctx, A, dtype, m, lda, gs, gg, q, prec, Y, ldy, &W, &WT);
+  if (st) return st;
+  if (q == 0) {
+    LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(G0, ldg0 * 8, Y, ldy * 8, l * 8, m, cudaMemcpyDeviceToDevice, ctx->stream));
+    LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(G, ldg * 8, Y, ldy * 8, l * 8, m, cudaMemcpyDeviceToDevice, ctx->stream));
+    *g_cols = l;
+    return LRS_OK;
+  }
+  // the ID's iterate first (no re-orthonormalisation), then the SVD's; the
+  // loop buffers are reused, W and W^T stay below the mark
+  const size_t mark = ctx->ws_top;
+  int64_t g0 = 0;
+  st = cpwr_loop(ctx, W, WT, m, l, nI, Y, ldy, q, 0, rtol, prec, G0, ldg0, &g0);
+  if (st) return st;
+  ctx->ws_top = mark;
+  st = cpwr_loop(ctx, W, WT, m, l, nI, Y, ldy, q, 1, rtol, prec, G, ldg, g_cols);
+  if (st) return st;
   LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   return LRS_OK;
 }

@@ -4,6 +4,9 @@
 lrs_range_find -> lrs_svd_k  (paper Algs. 7 and 2);
 ``id_path``  = lrs_power_pass (C-PWR without re-orthonormalisation, as in the
 paper's ID experiments) -> lrs_id_k  (Alg. 4);
+``power_pass2`` + ``svd_from_pass`` / ``id_from_pass`` = both paths of one
+matrix from one touch of A_f (lrs_power_pass2: the sketch and the subsample
+read once, both C-PWR iterates);
 ``spc_id_path`` = lrs_sketch -> lrs_sketch_svd -> lrs_id_k -> lrs_spc_lift
 (SPC-ID, Alg. 5); ``spc_err`` = lrs_spc_err (Alg. 6).
 Device buffers come from torch; every arithmetic step runs in liblrs.so.
@@ -93,6 +96,42 @@ def id_path(ctx: Context, A: torch.Tensor, dtype: str, grid, k: int, q: int = 0,
     ctx.power_pass(A, dt, m, n, g, gg, q, 0, rtol, prec, b.Yid, l, b.Gid, l)
     err, st = ctx.id_k(b.Gid, m, l, l, k, b.J, b.P, k)
     return IdResult(b.J, b.P, err, st)
+
+
+def power_pass2(ctx: Context, A: torch.Tensor, dtype: str, grid, q: int = 0, gram=None, rtol: float = 1e-12,
+                prec: int | None = None, bufs: Buffers | None = None) -> int:
+    """One touch of A_f for both paths: the sketch into bufs.Y, the ID's C-PWR
+    iterate into bufs.Gid, the SVD's orthonormal one into bufs.G; returns the
+    SVD basis width."""
+    m, n = A.shape
+    prec = default_prec(dtype) if prec is None else prec
+    l = int(grid.l)
+    gg = grid_of(gram) if (gram is not None and q > 0) else None
+    return ctx.power_pass2(A, DTYPE[dtype], m, n, grid_of(grid), gg, q, rtol, prec, bufs.Y, l, bufs.Gid, l,
+                           bufs.G, l)
+
+
+def svd_from_pass(ctx: Context, A: torch.Tensor, dtype: str, grid, k: int, q: int, gc: int, rtol: float,
+                  prec: int, bufs: Buffers) -> SvdResult:
+    """The SVD path after power_pass2 (the basis of bufs.G, gc columns)."""
+    m, n = A.shape
+    l = int(grid.l)
+    if q > 0:
+        Qb, ldq, r = bufs.G, l, gc
+    else:
+        ldq = bufs.Q.shape[1]
+        r = ctx.range_find(bufs.G, m, gc, l, rtol, bufs.Q, ldq)
+        Qb = bufs.Q
+    err, st = ctx.svd_k(A, DTYPE[dtype], m, n, n, Qb, ldq, r, k, prec, bufs.U, k, bufs.S, bufs.V, k)
+    kk = min(k, r)
+    return SvdResult(bufs.U[:, :kk], bufs.S[:kk], bufs.V[:, :kk], err, r, gc, st)
+
+
+def id_from_pass(ctx: Context, m: int, grid, k: int, bufs: Buffers) -> IdResult:
+    """The row ID after power_pass2 (the iterate in bufs.Gid)."""
+    l = int(grid.l)
+    err, st = ctx.id_k(bufs.Gid, m, l, l, k, bufs.J, bufs.P, k)
+    return IdResult(bufs.J, bufs.P, err, st)
 
 
 @dataclass

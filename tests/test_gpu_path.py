@@ -331,3 +331,28 @@ def test_heat3d_bf16_id_path(lrs, heat3):
     kappa = np.linalg.cond(R[:, :c["k"]])
     assert np.all(np.abs(P - d["P"]) <= 64 * 2.0 ** -53 * kappa * np.maximum(1.0, np.abs(d["P"])))
     assert abs(res.err_est - d["err_est"]) <= 1e-9 * d["err_est"]
+
+
+@pytest.mark.parametrize("prec,q", [(1, 1), (2, 1), (3, 1), (2, 0)])
+def test_power_pass2_equals_two_passes(lrs, blob, prec, q):
+    """lrs_power_pass2 (one touch of A_f, both C-PWR iterates) gives exactly
+    what lrs_power_pass gives without and with re-orthonormalisation."""
+    torch = _torch()
+    from paper_2105_01271_gb300 import binding as b
+    A, _, _ = blob
+    c = BLOB_SMALL
+    m, n, l = A.shape[0], A.shape[1], c["grid"].l
+    Ad = _dev(A)
+    g = b.grid_of(c["grid"])
+    gg = b.grid_of(c["gram"]) if q > 0 else None
+    f64 = dict(dtype=torch.float64, device="cuda")
+    Y1, G1, Y2, G2 = (torch.full((m, l), np.nan, **f64) for _ in range(4))
+    Y, G0, G = (torch.full((m, l), np.nan, **f64) for _ in range(3))
+    lrs.power_pass(Ad, b.LRS_F32, m, n, g, gg, q, 0, c["rtol"], prec, Y1, l, G1, l)
+    gc2 = lrs.power_pass(Ad, b.LRS_F32, m, n, g, gg, q, 1, c["rtol"], prec, Y2, l, G2, l)
+    gc = lrs.power_pass2(Ad, b.LRS_F32, m, n, g, gg, q, c["rtol"], prec, Y, l, G0, l, G, l)
+    torch.cuda.synchronize()
+    assert gc == gc2
+    assert torch.equal(Y, Y1) and torch.equal(Y, Y2)
+    assert torch.equal(G0, G1)
+    assert torch.equal(G[:, :gc], G2[:, :gc])
