@@ -112,6 +112,15 @@ lrs_status lrs_sketch(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int
  *   rank-revealing range finder of lrs_range_find with tolerance rtol.  With
  *   reorth the loop starts from QR(A_f D) (Alg. 7's Q_np), which has the same
  *   range as A_f D up to the truncated directions.
+ *   Without reorth (the iterate (W W^T)^q A_f D, which the row ID takes) and
+ *   prec other than LRS_PREC_FP64, the iterate is formed from the factors of
+ *   the re-orthonormalised loop: each QR(.) there gives (input) = Q Rt, so
+ *   (W W^T)^q Y = Q_q (Rt_g,q Rt_t,q ... Rt_t,1 Rt_np), evaluated in FP64.
+ *   Equal in exact arithmetic up to the directions the rank truncation drops;
+ *   it keeps every retained direction to the accuracy of the products
+ *   relative to that direction's own scale, where the direct product scales
+ *   direction j by s_j^(2q+1) and loses all below the products' rounding of
+ *   the top one.  Iterates of more than 128 directions use the direct form.
  *   Y   m x l FP64 (row stride ldy): the sketch A_f D.
  *   G   m x l FP64 (row stride ldg): G_q in its first *g_cols columns (the
  *       rank after truncation when reorth != 0, else l).

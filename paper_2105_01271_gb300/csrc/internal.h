@@ -157,8 +157,14 @@ lrs_status spc_err_from_rows(lrs_ctx* ctx, const void* Bf, int32_t dtype, int64_
                              const double* Bc, int64_t l, int64_t ldc, double cf, const double* taus, int32_t ntau,
                              double* eps_hat);
 // rdiag (optional, device): |R_ii| of the pivoted factor, i < r
+// Rt (optional, device, r x c row-major): the factor in original column
+// order, M ~= Q Rt (with the refinement folded in)
 lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldm, double rtol,
-                            double* Q, int64_t ldq, int64_t* r_out, bool refine = true, double* rdiag = nullptr);
+                            double* Q, int64_t ldq, int64_t* r_out, bool refine = true, double* rdiag = nullptr,
+                            double* Rt = nullptr);
+// Rt(t, perm[j]) = R(t, j) for the pivoted factor R (rows 0..r-1, row stride ldr)
+lrs_status launch_rt_scatter(lrs_ctx* ctx, const double* R, int64_t ldr, const int32_t* perm, int64_t r, int64_t c,
+                             double* Rt);
 // the same for a WIDE (or square) M (c > 128 columns): left-looking pivoted
 // Cholesky that forms only the pivots' Gram columns (one cooperative launch),
 // then the tall-skinny tail (Q_1 = M(:, piv) R_11^{-1}, one Cholesky-QR
@@ -167,7 +173,7 @@ lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c,
 bool orth_wide_eligible(int64_t p, int64_t c, double rtol, int num_sms);
 size_t orth_wide_ws(int64_t p, int64_t c, int num_sms);
 lrs_status launch_orth_wide(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldm, double rtol,
-                            double* Q, int64_t ldq, int64_t* r_out, bool refine, double* rdiag);
+                            double* Q, int64_t ldq, int64_t* r_out, bool refine, double* rdiag, double* Rt = nullptr);
 // out[i] = |R[i * ld + i]|, i < r (device pointers)
 lrs_status launch_abs_diag(lrs_ctx* ctx, const double* R, int64_t ld, int64_t r, double* out);
 

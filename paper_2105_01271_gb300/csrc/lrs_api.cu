@@ -143,22 +143,26 @@ lrs_status launch_abs_diag(lrs_ctx* ctx, const double* R, int64_t ld, int64_t r,
   return LRS_OK;
 }
 
+// Rt (optional, device, r x c row-major, room for 128 rows): the factor with
+// Min ~= Q Rt, columns in their original order (every route: the triangular
+// factor of its pivoted QR scattered back, the refinement folded in); not
+// written when r > 128.
 static lrs_status orth(lrs_ctx* ctx, const double* Min, int64_t p, int64_t c, int64_t ldi,
                        double rtol, double* Q, int64_t ldq, int64_t* r_out, bool intermediate = false,
-                       double* rdiag = nullptr, int64_t kcap = 0) {
+                       double* rdiag = nullptr, int64_t kcap = 0, double* Rt = nullptr) {
   int64_t kmax = p < c ? p : c;
   if (kcap > 0 && kcap < kmax) kmax = kcap;           // at most kcap pivoted steps (Householder route)
   if (kcap <= 0 && orth_wide_eligible(p, c, rtol, ctx->num_sms)) {
     // wide: left-looking pivoted Cholesky (same pivots and stop rule)
     const size_t mark = ctx->ws_top;
-    lrs_status ws = launch_orth_wide(ctx, Min, p, c, ldi, rtol, Q, ldq, r_out, !intermediate, rdiag);
+    lrs_status ws = launch_orth_wide(ctx, Min, p, c, ldi, rtol, Q, ldq, r_out, !intermediate, rdiag, Rt);
     ctx->ws_top = mark;
     if (ws != LRS_ERANK) return ws;
   }
   if (kcap <= 0 && orth_gram_eligible(p, c, rtol)) {
     // tall-skinny: pivoted Cholesky of the Gram (same pivots and stop rule)
     const size_t mark = ctx->ws_top;
-    lrs_status gs = launch_orth_gram(ctx, Min, p, c, ldi, rtol, Q, ldq, r_out, !intermediate, rdiag);
+    lrs_status gs = launch_orth_gram(ctx, Min, p, c, ldi, rtol, Q, ldq, r_out, !intermediate, rdiag, Rt);
     ctx->ws_top = mark;
     if (gs != LRS_ERANK) return gs;
   }
@@ -180,6 +184,10 @@ static lrs_status orth(lrs_ctx* ctx, const double* Min, int64_t p, int64_t c, in
   LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   if (rdiag && r > 0) {
     st = launch_abs_diag(ctx, o.R, c, r, rdiag);
+    if (st) return st;
+  }
+  if (Rt && r > 0 && r <= 128) {       // callers size Rt for 128 rows (wider: no factor written)
+    st = launch_rt_scatter(ctx, o.R, c, o.perm, r, c, Rt);
     if (st) return st;
   }
   st = launch_form_q(ctx, o.V, p, r, Q, ldq);
@@ -351,6 +359,10 @@ static size_t cpwr_ws(lrs_ctx* ctx, int64_t m, int64_t l, int64_t nI, int32_t pr
   need += align256(8 * (size_t)(nI * wmax)) + 2 * align256(8 * (size_t)(m * wmax));
   need += align256(8 * (size_t)(nI * wmax));                        // orthonormal T
   if (tc) need += align256(4 * (size_t)(nI * wmax)) + align256(4 * (size_t)(m * wmax));  // FP32 operands
+  // the factor chain of the iterate without re-orthonormalisation: two
+  // products of at most 128 x l and one factor of at most 128 x max(l, 128)
+  const int64_t lc = l > 128 ? l : 128;
+  need += 3 * align256(8 * (size_t)(128 * lc));
   const size_t o1 = orth_ws(m, l, ctx->num_sms), o2 = orth_ws(nI, wmax, ctx->num_sms);
   size_t inner = o1 > o2 ? o1 : o2;
   if (tc) {
@@ -370,12 +382,42 @@ static size_t cpwr_ws(lrs_ctx* ctx, int64_t m, int64_t l, int64_t nI, int32_t pr
 // gathered subsample W (m x nI) and W^T (nI x m), both in wdt: q iterations
 // G <- W^T G; [QR]; G <- W G; [QR].  Loop buffers come from the workspace
 // above the caller's mark; the result is copied to G (ldg), *g_cols columns.
+//
+// Gid (optional, with reorth, q > 0): the iterate WITHOUT re-orthonormalisation,
+// (W W^T)^q Y, formed from the factors of this re-orthonormalised loop.  Every
+// QR(.) returns its factor with (input) = Q Rt, so
+//   (W W^T)^q Y = Q_q (Rt_g,q Rt_t,q ... Rt_g,1 Rt_t,1 Rt_np)
+// up to the directions the rank truncation drops; the product of the small
+// factors and the final Q_q times it run in FP64.  Products W^T G and W T in
+// FP32-level arithmetic resolve each direction of an ORTHONORMAL iterate to
+// FP32 accuracy relative to that direction's own scale, whereas the direct
+// (W W^T)^q Y scales direction j by s_j^(2q+1) and buries every direction
+// below ~1e-7 of the top under the products' rounding.
+// *gid_done tells whether Gid was written (the chain holds at most 128
+// directions; wider iterates leave it to the caller).
 static lrs_status cpwr_loop(lrs_ctx* ctx, const void* W, const void* WT, int64_t m, int64_t l, int64_t nI,
                             const double* Y, int64_t ldy, int32_t q, int32_t reorth, double rtol, int32_t prec,
-                            double* G, int64_t ldg, int64_t* g_cols) {
+                            double* G, int64_t ldg, int64_t* g_cols, double* Gid = nullptr, int64_t ldgid = 0,
+                            bool* gid_done = nullptr) {
   const int64_t wmax = l > m ? l : m;
   const bool tc = prec >= LRS_PREC_SPLIT_BF16;
   const int32_t wdt = tc ? LRS_F32 : LRS_F64;
+  bool chain = Gid && reorth && q > 0;
+  if (gid_done) *gid_done = false;
+  const int64_t lc = l > 128 ? l : 128;
+  double* Nc = chain ? (double*)ws_alloc(ctx, 8 * (size_t)(128 * lc)) : nullptr;   // the product so far
+  double* Nn = chain ? (double*)ws_alloc(ctx, 8 * (size_t)(128 * lc)) : nullptr;
+  double* Rf = chain ? (double*)ws_alloc(ctx, 8 * (size_t)(128 * lc)) : nullptr;   // one factor
+  if (chain && (!Nc || !Nn || !Rf)) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (power_pass chain)");
+  int64_t nrows = 0;                   // rows of the product so far (its columns: l)
+  // Nn <- Rf (rr x nrows) * Nc (nrows x l); swap
+  auto chain_mul = [&](int64_t rr) -> lrs_status {
+    lrs_status s2 = spc_small_gemm(ctx, rr, l, nrows, Rf, nrows, 1, Nc, l, 1, nullptr, nullptr, Nn, l);
+    if (s2) return s2;
+    double* t = Nc; Nc = Nn; Nn = t;
+    nrows = rr;
+    return LRS_OK;
+  };
   double* Tm = (double*)ws_alloc(ctx, 8 * (size_t)(nI * wmax));
   double* To = (double*)ws_alloc(ctx, 8 * (size_t)(nI * wmax));
   double* Ga = (double*)ws_alloc(ctx, 8 * (size_t)(m * wmax));
@@ -393,10 +435,12 @@ static lrs_status cpwr_loop(lrs_ctx* ctx, const void* W, const void* WT, int64_t
   if (reorth) {
     // Q_np only feeds W^T Q_np, which is orthonormalised again: a
     // well-conditioned basis of the same range suffices (no refinement pass)
-    st = orth(ctx, Y, m, l, ldy, rtol, Ga, wmax, &gc, /*intermediate=*/q > 0);
+    st = orth(ctx, Y, m, l, ldy, rtol, Ga, wmax, &gc, /*intermediate=*/q > 0, nullptr, 0, chain ? Nc : nullptr);
     if (st) return st;
     ctx->ws_top = mark;
     Gcur = Ga; ldcur = wmax;
+    nrows = gc;                        // Y = Q_np Rt_np
+    if (gc > 128) chain = false;       // no factor chain beyond 128 directions
   }
   for (int it = 0; it < q; ++it) {
     // T = W^T G   (nI x gc)
@@ -421,9 +465,10 @@ static lrs_status cpwr_loop(lrs_ctx* ctx, const void* W, const void* WT, int64_t
     const void* Tcur = tc ? (const void*)T32 : (const void*)Tm;
     int32_t tdt = tc ? LRS_F32 : LRS_F64;
     if (reorth) {
-      st = orth(ctx, Tm, nI, gc, gc, rtol, To, gc, &tc_cols, /*intermediate=*/true);
+      st = orth(ctx, Tm, nI, gc, gc, rtol, To, gc, &tc_cols, /*intermediate=*/true, nullptr, 0, chain ? Rf : nullptr);
       if (st) return st;
       ctx->ws_top = mark;
+      if (chain) { st = chain_mul(tc_cols); if (st) return st; }
       if (tc) {
         st = launch_to_f32(ctx, To, nI, tc_cols, gc, T32, gc);
         if (st) return st;
@@ -442,9 +487,11 @@ static lrs_status cpwr_loop(lrs_ctx* ctx, const void* W, const void* WT, int64_t
     if (reorth) {
       double* Go = (Gn == Ga) ? Gb : Ga;
       // only the last iterate is returned as the orthonormal basis G_q
-      st = orth(ctx, Gn, m, tc_cols, wmax, rtol, Go, wmax, &gc, /*intermediate=*/it + 1 < q);
+      st = orth(ctx, Gn, m, tc_cols, wmax, rtol, Go, wmax, &gc, /*intermediate=*/it + 1 < q, nullptr, 0,
+                chain ? Rf : nullptr);
       if (st) return st;
       ctx->ws_top = mark;
+      if (chain) { st = chain_mul(gc); if (st) return st; }
       Gcur = Go;
     } else {
       gc = tc_cols;
@@ -454,6 +501,12 @@ static lrs_status cpwr_loop(lrs_ctx* ctx, const void* W, const void* WT, int64_t
   }
   LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(G, ldg * 8, Gcur, ldcur * 8, gc * 8, m, cudaMemcpyDeviceToDevice, ctx->stream));
   *g_cols = gc;
+  if (chain) {
+    // (W W^T)^q Y = Q_q N, N = the factor product (gc x l), in FP64
+    st = spc_small_gemm(ctx, m, l, gc, Gcur, ldcur, 1, Nc, l, 1, nullptr, nullptr, Gid, ldgid);
+    if (st) return st;
+    if (gid_done) *gid_done = true;
+  }
   return LRS_OK;
 }
 
@@ -511,7 +564,7 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
   LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   const int64_t l = gs.l;
   const int64_t nI = q > 0 ? gg.l : 0;
-  st = ws_reserve(ctx, q > 0 ? cpwr_ws(ctx, m, l, nI, prec) : 0);
+  st = ws_reserve(ctx, q > 0 ? cpwr_ws(ctx, m, l, nI, prec) + align256(8 * (size_t)(m * l)) : 0);
   if (st) return st;
   void *W = nullptr, *WT = nullptr;
   st = touch(ctx, A, dtype, m, lda, gs, gg, q, prec, Y, ldy, &W, &WT);
@@ -520,6 +573,23 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
     LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(G, ldg * 8, Y, ldy * 8, l * 8, m, cudaMemcpyDeviceToDevice, ctx->stream));
     *g_cols = l;
     return LRS_OK;
+  }
+  if (!reorth && prec != LRS_PREC_FP64) {
+    // the iterate without re-orthonormalisation from the factors of the
+    // re-orthonormalised loop (cpwr_loop); its basis goes to scratch
+    double* Gs = (double*)ws_alloc(ctx, 8 * (size_t)(m * l));
+    if (!Gs) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (power_pass)");
+    const size_t mark = ctx->ws_top;
+    int64_t gq = 0;
+    bool done = false;
+    st = cpwr_loop(ctx, W, WT, m, l, nI, Y, ldy, q, 1, rtol, prec, Gs, l, &gq, G, ldg, &done);
+    if (st) return st;
+    ctx->ws_top = mark;
+    if (done) {
+      *g_cols = l;
+      LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+      return LRS_OK;
+    }
   }
   st = cpwr_loop(ctx, W, WT, m, l, nI, Y, ldy, q, reorth, rtol, prec, G, ldg, g_cols);
   if (st) return st;
@@ -552,15 +622,21 @@ lrs_status lrs_power_pass2(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m
     *g_cols = l;
     return LRS_OK;
   }
-  // the ID's iterate first (no re-orthonormalisation), then the SVD's; the
-  // loop buffers are reused, W and W^T stay below the mark
+  // The SVD's re-orthonormalised loop; its factors also give the ID's
+  // iterate (the same result as lrs_power_pass with reorth = 0).  FP64
+  // products, or a chain wider than 128 directions: the ID's loop runs on its
+  // own.  The loop buffers are reused, W and W^T stay below the mark.
   const size_t mark = ctx->ws_top;
-  int64_t g0 = 0;
-  st = cpwr_loop(ctx, W, WT, m, l, nI, Y, ldy, q, 0, rtol, prec, G0, ldg0, &g0);
+  bool done = false;
+  st = cpwr_loop(ctx, W, WT, m, l, nI, Y, ldy, q, 1, rtol, prec, G, ldg, g_cols,
+                 prec != LRS_PREC_FP64 ? G0 : nullptr, ldg0, &done);
   if (st) return st;
   ctx->ws_top = mark;
-  st = cpwr_loop(ctx, W, WT, m, l, nI, Y, ldy, q, 1, rtol, prec, G, ldg, g_cols);
-  if (st) return st;
+  if (!done) {
+    int64_t g0 = 0;
+    st = cpwr_loop(ctx, W, WT, m, l, nI, Y, ldy, q, 0, rtol, prec, G0, ldg0, &g0);
+    if (st) return st;
+  }
   LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   return LRS_OK;
 }

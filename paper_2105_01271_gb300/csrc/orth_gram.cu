@@ -438,6 +438,55 @@ __global__ void k_gram_df_reduce(const float* __restrict__ hi, const float* __re
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// R factors in the original column order, for callers that chain them:
+// Rt (r x c, row-major) with M ~= Q Rt.
+// From a pivoted factor R (rows 0..r-1, pivoted column order, row stride
+// ldr) and perm[pos] = original column: Rt(t, perm[j]) = R(t, j) (j >= t).
+__global__ void k_rt_scatter(const double* __restrict__ R, int64_t ldr, const int32_t* __restrict__ perm, int64_t r,
+                             int64_t c, double* __restrict__ Rt) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= r * c) return;
+  const int64_t t = e / c, j = e - t * c;
+  Rt[t * c + perm[j]] = j >= t ? R[t * ldr + j] : 0.0;
+}
+// From the left-looking factor L (by original column, L[i * kmax + t]):
+// Rt(t, i) = L(i, t).
+__global__ void k_rt_from_l(const double* __restrict__ L, int64_t kmax, int64_t r, int64_t c, double* __restrict__ Rt) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= r * c) return;
+  const int64_t t = e / c, i = e - t * c;
+  Rt[t * c + i] = L[i * kmax + t];
+}
+// out = U X for U (r x r upper triangular, row stride r) and X (r x c):
+// out(t, i) = sum_{s >= t} U(t, s) X(s, i), FP64, fixed order
+__global__ void k_trmm_upper(const double* __restrict__ U, int64_t r, const double* __restrict__ X, int64_t c,
+                             double* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= r * c) return;
+  const int64_t t = e / c, i = e - t * c;
+  double acc = 0.0;
+  for (int64_t s = t; s < r; ++s) acc = fma(U[t * r + s], X[s * c + i], acc);
+  out[t * c + i] = acc;
+}
+
+lrs_status launch_rt_scatter(lrs_ctx* ctx, const double* R, int64_t ldr, const int32_t* perm, int64_t r, int64_t c,
+                             double* Rt) {
+  if (r < 1 || c < 1) return LRS_OK;
+  k_rt_scatter<<<(unsigned)((r * c + 255) / 256), 256, 0, ctx->stream>>>(R, ldr, perm, r, c, Rt);
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
+
+static lrs_status launch_trmm_upper(lrs_ctx* ctx, const double* U, int64_t r, const double* X, int64_t c,
+                                    double* out) {
+  k_trmm_upper<<<(unsigned)((r * c + 255) / 256), 256, 0, ctx->stream>>>(U, r, X, c, out);
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
+
 bool orth_gram_eligible(int64_t p, int64_t c, double rtol) {
   return c >= 1 && c <= kMaxC && p >= 4 * c && rtol >= kOrthGramRtolMin;
 }
@@ -449,18 +498,22 @@ size_t orth_gram_ws(int64_t p, int64_t c, int num_sms) {
   b += 2 * a256(sizeof(double) * (size_t)(c * c));       // G, R
   b += a256(4 * (size_t)c) + a256(8);                    // perm, rank
   b += a256(sizeof(double) * (size_t)(p * c));           // Q_1
+  b += a256(sizeof(double) * (size_t)(c * c));           // the first factor (original column order)
   return b + 1024;
 }
 
 lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldm, double rtol,
-                            double* Q, int64_t ldq, int64_t* r_out, bool refine, double* rdiag) {
+                            double* Q, int64_t ldq, int64_t* r_out, bool refine, double* rdiag, double* Rt) {
   const int ci = (int)c;
   double* G = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(c * c));
   double* R = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(c * c));
   int32_t* perm = (int32_t*)ws_alloc(ctx, 4 * (size_t)c);
   int32_t* rank = (int32_t*)ws_alloc(ctx, 8);
   double* Q1 = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(p * c));
-  if (!G || !R || !perm || !rank || !Q1) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (orth_gram)");
+  // the first factor in original column order when it is refined afterwards
+  double* R1t = (Rt && refine) ? (double*)ws_alloc(ctx, sizeof(double) * (size_t)(c * c)) : Rt;
+  if (!G || !R || !perm || !rank || !Q1 || (Rt && !R1t))
+    return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (orth_gram)");
   const size_t mark = ctx->ws_top;
   lrs_status st = gram(ctx, M, p, ci, ldm, G);
   if (st) return st;
@@ -477,6 +530,12 @@ lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c,
     st = launch_abs_diag(ctx, R, c, r, rdiag);
     if (st) return st;
   }
+  // M(:, perm) = Q_1 R: the factor in original column order, before the
+  // refinement reuses R and perm (then Rt <- R_2 Rt)
+  if (Rt) {
+    st = launch_rt_scatter(ctx, R, c, perm, r, c, R1t);
+    if (st) return st;
+  }
   if (!refine) return trsm_rows(ctx, M, p, ldm, perm, R, c, r, Q, ldq);
   st = trsm_rows(ctx, M, p, ldm, perm, R, c, r, Q1, r);
   if (st) return st;
@@ -491,6 +550,10 @@ lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c,
   // Q_1 has full column rank r by construction; a breakdown here means the
   // first pass lost it to rounding: the caller falls back to Householder CPQR
   if (h[41] != r) return LRS_ERANK;
+  if (Rt) {
+    st = launch_trmm_upper(ctx, R, r, R1t, c, Rt);
+    if (st) return st;
+  }
   return trsm_rows(ctx, Q1, p, r, nullptr, R, r, r, Q, ldq);
 }
 
@@ -780,11 +843,12 @@ size_t orth_wide_ws(int64_t p, int64_t c, int num_sms) {
   b += a256(sizeof(PivotCand) * (size_t)(2 * g.nb)) + 256;   // candidates, barrier
   // then the tall-skinny tail (Q_1 and the refinement's Gram) on p x r, r <= 128
   b += orth_gram_ws(p, kLpMaxRank, num_sms);
+  b += a256(sizeof(double) * (size_t)(kmax * c));        // the factor in original column order
   return b + 1024;
 }
 
 lrs_status launch_orth_wide(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldm, double rtol,
-                            double* Q, int64_t ldq, int64_t* r_out, bool refine, double* rdiag) {
+                            double* Q, int64_t ldq, int64_t* r_out, bool refine, double* rdiag, double* Rt) {
   if (!ctx->coop_ok) return LRS_ERANK;               // the caller's Householder route reports it
   const int64_t kmax_full = min(p, c);
   const int64_t kmax = min(kmax_full, kLpMaxRank + 1);
@@ -830,6 +894,14 @@ lrs_status launch_orth_wide(lrs_ctx* ctx, const double* M, int64_t p, int64_t c,
     st = launch_abs_diag(ctx, R, kmax, r, rdiag);
     if (st) return st;
   }
+  // M = Q_1 L^T in original column order (L is kept by original column)
+  double* R1t = (Rt && refine) ? (double*)ws_alloc(ctx, sizeof(double) * (size_t)(r * c)) : Rt;
+  if (Rt) {
+    if (!R1t) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (orth_wide factor)");
+    k_rt_from_l<<<(unsigned)((r * c + 255) / 256), 256, 0, ctx->stream>>>(L, kmax, r, c, R1t);
+    ctx->launches++;
+    LRS_CUDA_TRY(ctx, cudaGetLastError());
+  }
   if (!refine) return trsm_rows(ctx, M, p, ldm, perm, R, kmax, r, Q, ldq);
   double* Q1 = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(p * r));
   double* G2 = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(r * r));
@@ -847,6 +919,10 @@ lrs_status launch_orth_wide(lrs_ctx* ctx, const double* M, int64_t p, int64_t c,
   LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 45, rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
   LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   if (h[45] != r) return LRS_ERANK;
+  if (Rt) {
+    st = launch_trmm_upper(ctx, R2, r, R1t, c, Rt);
+    if (st) return st;
+  }
   return trsm_rows(ctx, Q1, p, r, nullptr, R2, r, r, Q, ldq);
 }
 

@@ -14,8 +14,10 @@ Tolerances (derived from the arithmetic, stated here):
     standard deviation at most c (|Q|^T |A_f|)_jk, c = c_p + (sqrt(m) + 1) u32
     (c_p the per-term error of the product form: u32, 2^-16, 2^-23), and a
     first-order change u_i^T E v_i of s_i has at most that deviation, so
-    |ds_i| <= 6 c max(|Q|^T |A_f|) (six standard deviations); the double-float
-    Gram adds 2^-44 s_1^2 / s_i and the FP64 Cholesky and Jacobi 64 u64 s_1.
+    |ds_i| <= 6 c max(|Q|^T |A_f|) (six standard deviations); the tensor
+    cores' truncated accumulation shrinks B by at most C_TRUNC relative (one
+    FP32 ulp per MMA of an accumulation chunk), the double-float Gram adds
+    2^-44 s_1^2 / s_i and the FP64 Cholesky and Jacobi 64 u64 s_1.
   * Skeleton J: identical to the oracle's wherever every pivot margin
     (best - runner-up)/best exceeds the perturbation the path's arithmetic can
     cause (FP64 sketch and CPQR: 1e-10; C-PWR products in FP32 or BF16 pieces:
@@ -64,6 +66,11 @@ def _prefix(gaps, margin):
 # per-term error of a product form: FP32 FMA (Q rounded to FP32), two and
 # three BF16 pieces
 C_PIECE = {1: U32, 2: 2.0 ** -16, 3: 2.0 ** -23}
+# systematic shrink of the tensor-core A-pass: each MMA's accumulation is
+# truncated (less than one FP32 ulp of the running partial), and the A-pass
+# accumulates 2 slabs of 64 snapshots per chunk before a round-to-nearest add:
+# 16 MMAs per chunk with two pieces (stacked), 48 with three (unstacked)
+C_TRUNC = {1: 0.0, 2: 16 * U32, 3: 48 * U32}
 
 
 def s_tol(o, A, m, prec, values=None):
@@ -73,7 +80,7 @@ def s_tol(o, A, m, prec, values=None):
     c = C_PIECE[prec] + (np.sqrt(m) + 1.0) * U32
     s1 = o["sB"][0]
     sv = o["S"] if values is None else np.asarray(values)
-    return 6.0 * c * QA.max() + 2.0 ** -44 * s1 ** 2 / sv + 64 * 2.0 ** -53 * s1
+    return 6.0 * c * QA.max() + C_TRUNC[prec] * sv + 2.0 ** -44 * s1 ** 2 / sv + 64 * 2.0 ** -53 * s1
 
 
 def err_est_bound2(o, A, m, prec, k):

@@ -44,11 +44,13 @@ def golden():
 
 def s_tol(g, m, values):
     """Per-value bound on |s_gpu - s_oracle| for split-BF16 products (see
-    tests/test_gpu_path.py): 6 c max(|Q|^T |A_f|) + 2^-44 s_1^2 / s_i + 64 u64 s_1."""
+    tests/test_gpu_path.py): 6 c max(|Q|^T |A_f|) + 16 u32 s_i + 2^-44 s_1^2 / s_i
+    + 64 u64 s_1."""
     c = 2.0 ** -16 + (np.sqrt(m) + 1.0) * U32
     s1 = g["sB"][0]
     v = np.asarray(values)
-    return 6.0 * c * g["absQA_max"] + 2.0 ** -44 * s1 ** 2 / v + 64 * U64 * s1
+    # + the truncated tensor-core accumulation: 16 MMAs per chunk, < 1 ulp each
+    return 6.0 * c * g["absQA_max"] + 16 * U32 * v + 2.0 ** -44 * s1 ** 2 / v + 64 * U64 * s1
 
 
 def check_svd_against_golden(g, res, A, m, k):
