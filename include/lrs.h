@@ -115,15 +115,21 @@ lrs_status lrs_sketch(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int
  *   Without reorth (the iterate (W W^T)^q A_f D, which the row ID takes) and
  *   prec other than LRS_PREC_FP64, the iterate is formed from the factors of
  *   the re-orthonormalised loop: each QR(.) there gives (input) = Q Rt, so
- *   (W W^T)^q Y = Q_q (Rt_g,q Rt_t,q ... Rt_t,1 Rt_np), evaluated in FP64.
- *   Equal in exact arithmetic up to the directions the rank truncation drops;
- *   it keeps every retained direction to the accuracy of the products
- *   relative to that direction's own scale, where the direct product scales
- *   direction j by s_j^(2q+1) and loses all below the products' rounding of
- *   the top one.  Iterates of more than 128 directions use the direct form.
+ *   (W W^T)^q Y = Q_q M Rt_np with M = Rt_g,q Rt_t,q ... Rt_g,1 Rt_t,1, in
+ *   exact arithmetic up to the directions the rank truncation drops.  Since
+ *   the row ID (lrs_id_k) depends only on the inner products of the rows,
+ *   G then holds the m x r matrix H = Q_q M Ra^T (Ra^T Ra = Rt_np Rt_np^T,
+ *   r = the rank of QR(A_f D), *g_cols = r <= 128), whose rows have the
+ *   iterate's inner products: lrs_id_k(H) is the iterate's row ID, its
+ *   pivoted QR taking r rows instead of l.  All of it runs in FP64 on r x r
+ *   factors, so every retained direction keeps the products' accuracy
+ *   relative to its own scale, where the direct product scales direction j
+ *   by s_j^(2q+1) and loses all below the products' rounding of the top one.
+ *   Wider iterates (and LRS_PREC_FP64) take the direct form, *g_cols = l.
  *   Y   m x l FP64 (row stride ldy): the sketch A_f D.
  *   G   m x l FP64 (row stride ldg): G_q in its first *g_cols columns (the
- *       rank after truncation when reorth != 0, else l).
+ *       rank after truncation when reorth != 0; without reorth l, or r for
+ *       the row-Gram form below).
  *   q = 0 returns G = Y.  `gram` may be NULL when q = 0.
  *   prec: arithmetic of the W^T G and W G products (lrs_prec).
  */
@@ -142,14 +148,17 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
  * lrs_power_pass(reorth = 1) -> G on the same arguments, bit for bit, with
  * one sketch launch and one subsample gather instead of two of each.
  *   Y   m x l FP64 (row stride ldy): the sketch A_f D.
- *   G0  m x l FP64 (row stride ldg0): G_q without re-orthonormalisation.
+ *   G0  m x l FP64 (row stride ldg0): G_q without re-orthonormalisation in
+ *       its first *g0_cols columns, in the form lrs_power_pass gives it
+ *       (the row-Gram form H of r columns, or the iterate itself).
  *   G   m x l FP64 (row stride ldg): the re-orthonormalised G_q in its first
- *       *g_cols columns.  q = 0 returns G0 = G = Y (*g_cols = l).
+ *       *g_cols columns.  q = 0 returns G0 = G = Y (*g_cols = *g0_cols = l).
+ * The re-orthonormalised loop runs once: its factors give G0.
  */
 lrs_status lrs_power_pass2(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t lda,
                            const lrs_grid* sketch, const lrs_grid* gram, int32_t q, double rtol, int32_t prec,
-                           double* Y, int64_t ldy, double* G0, int64_t ldg0, double* G, int64_t ldg,
-                           int64_t* g_cols);
+                           double* Y, int64_t ldy, double* G0, int64_t ldg0, int64_t* g0_cols, double* G,
+                           int64_t ldg, int64_t* g_cols);
 
 /*
  * lrs_range_find -- orthonormal basis of the numerical range of G (the
@@ -201,7 +210,8 @@ lrs_status lrs_svd_k(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int6
  *   P   m x k FP64 (row stride ldp) with P(J,:) = I exactly.
  *   err_est (host, may be NULL): ||R_22||_F / ||Ysk||_F, the relative error of
  *       the coarse ID.  Lift: A_f ~ P A_f(J, :) (Alg. 4).
- * Returns LRS_ERANK if the sketch has a zero column norm before step k.
+ * Returns LRS_ERANK if the sketch has a zero column norm before step k, or
+ * fewer than k columns (l < k; nothing written).
  */
 lrs_status lrs_id_k(lrs_ctx* ctx, const double* Ysk, int64_t m, int64_t l, int64_t ldy, int32_t k,
                     int32_t* J, double* P, int64_t ldp, double* err_est);

@@ -82,8 +82,8 @@ _SIG = {
                                  C.c_int64, C.POINTER(C.c_int64)]),
     "lrs_power_pass2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64,
                                   C.POINTER(lrs_grid), C.POINTER(lrs_grid), C.c_int32, C.c_double,
-                                  C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
-                                  C.c_int64, C.POINTER(C.c_int64)]),
+                                  C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                  C.POINTER(C.c_int64), C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "lrs_range_find": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64,
                                  C.c_double, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "lrs_range_find_diag": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64,
@@ -234,13 +234,15 @@ class Context:
         return gc.value
 
     def power_pass2(self, A, dtype, m, lda, sketch: lrs_grid, gram, q, rtol, prec,
-                    Y, ldy, G0, ldg0, G, ldg) -> int:
+                    Y, ldy, G0, ldg0, G, ldg):
+        """Returns (columns of G0, columns of G)."""
         gc = C.c_int64(0)
+        g0 = C.c_int64(0)
         gp = C.byref(gram) if gram is not None else None
         self._check(self.lib.lrs_power_pass2(self.h, _ptr(A), dtype, m, lda, C.byref(sketch), gp,
-                                             q, rtol, prec, _ptr(Y), ldy, _ptr(G0), ldg0, _ptr(G), ldg,
-                                             C.byref(gc)))
-        return gc.value
+                                             q, rtol, prec, _ptr(Y), ldy, _ptr(G0), ldg0, C.byref(g0),
+                                             _ptr(G), ldg, C.byref(gc)))
+        return g0.value, gc.value
 
     def range_find(self, G, m, l, ldg, rtol, Q, ldq) -> int:
         r = C.c_int64(0)

@@ -96,7 +96,8 @@ lrs_status run_item(lrs_ctx* ctx, Scratch& sc, lrs_batch_item& it) {
     lrs_status st = lrs_power_pass(ctx, it.A, it.dtype, m, it.lda, &it.sketch, gram, it.q, 0, it.rtol, it.prec,
                                    sc.Y, l, sc.G, l, &gc);
     if (st) return st;
-    st = lrs_id_k(ctx, sc.G, m, l, l, it.k, it.J, it.P, it.ldp, &it.err_id);
+    // gc: the columns of the iterate's form (l, or r for the row-Gram form)
+    st = lrs_id_k(ctx, sc.G, m, gc, l, it.k, it.J, it.P, it.ldp, &it.err_id);
     if (st != LRS_OK && st != LRS_ERANK) return st;
     if (st == LRS_ERANK) worst = st;
   }

@@ -35,6 +35,68 @@ __device__ __forceinline__ double widen_f32(float f) {
   return (double)f;
 }
 
+// FP64 -> FP32 pair on the integer pipe: hi = x truncated to 24 significant
+// bits (exact FP32), lo = the next bits of x rounded to FP32, so hi + lo
+// carries x to ~2^-47 relative.  For 2^-74 <= |x| < 2^127 (both parts normal
+// FP32); outside it (and for 0, denormals, inf, NaN) the conversion
+// instructions.  Keeps the narrow FP64
+// pipe (64-cycle issue per warp instruction on this part) for the arithmetic.
+__device__ __forceinline__ void split_f64_f2(double x, float& hi, float& lo) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((u >> 52) & 0x7ffu) - 1023;           // unbiased exponent
+  if (e >= -74 && e < 127) {                                // hi and lo both normal FP32
+    const unsigned sign = (unsigned)(u >> 32) & 0x80000000u;
+    const unsigned long long m = u & 0xfffffffffffffull;     // 52 fraction bits
+    hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29));
+    const unsigned rest = (unsigned)(m & 0x1fffffffu);        // the low 29 bits
+    // rest * 2^(e - 52): an integer-to-float conversion (rounds 29 to 24
+    // bits), then the power of two from its exponent bits
+    const float rf = __uint2float_rn(rest);
+    lo = rest ? __uint_as_float(sign | __float_as_uint(rf) - ((unsigned)(52 - e) << 23)) : 0.0f;
+    return;
+  }
+  hi = __double2float_rz(x);
+  lo = __double2float_rn(x - (double)hi);
+}
+
+// Double-float arithmetic on (hi, lo) pairs of FP32 (Knuth's two-sum, the
+// FMA two-product): about 2^-46 relative, on the FP32 pipe.  The _rn
+// intrinsics keep the compiler from contracting the error-free steps.
+struct df32 {
+  float hi, lo;
+};
+__device__ __forceinline__ df32 df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, err};
+}
+__device__ __forceinline__ df32 df_norm(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ df32 df_add(df32 a, df32 b) {
+  const df32 s = df_two_sum(a.hi, b.hi);
+  return df_norm(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df32 df_neg(df32 a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df32 df_mul(df32 a, df32 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float e = __fmaf_rn(a.hi, b.hi, -p);
+  return df_norm(p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e)));
+}
+__device__ __forceinline__ df32 df_mul_f(df32 a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  const float e = __fmaf_rn(a.hi, b, -p);
+  return df_norm(p, __fmaf_rn(a.lo, b, e));
+}
+__device__ __forceinline__ df32 df_from_f(float a) { return {a, 0.0f}; }
+__device__ __forceinline__ df32 df_from_f64(double x) {
+  df32 r;
+  split_f64_f2(x, r.hi, r.lo);
+  return r;
+}
+
 // element i of A_f widened to double, conversions on the integer pipe
 __device__ __forceinline__ double ld_wide(const void* p, int32_t dt, int64_t i) {
   if (dt == LRS_F64) return __ldg(reinterpret_cast<const double*>(p) + i);

@@ -162,6 +162,10 @@ lrs_status spc_err_from_rows(lrs_ctx* ctx, const void* Bf, int32_t dtype, int64_
 lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c, int64_t ldm, double rtol,
                             double* Q, int64_t ldq, int64_t* r_out, bool refine = true, double* rdiag = nullptr,
                             double* Rt = nullptr);
+// one-block Cholesky of a c x c PSD G (pivot = 1: pivoted, CPQR's rules),
+// R (rows 0..rank-1, row stride ldr, pivoted order, zeros below the diagonal)
+lrs_status launch_pchol(lrs_ctx* ctx, const double* G, int c, int kmax, double rtol, int pivot, int32_t* perm,
+                        double* R, int64_t ldr, int32_t* rank);
 // Rt(t, perm[j]) = R(t, j) for the pivoted factor R (rows 0..r-1, row stride ldr)
 lrs_status launch_rt_scatter(lrs_ctx* ctx, const double* R, int64_t ldr, const int32_t* perm, int64_t r, int64_t c,
                              double* Rt);

@@ -51,19 +51,26 @@ struct JacRowsArgs {
 };
 
 // One warp per column pair.  The FP64 pipe of a GB300 SM retires 2 FMAs per
-// clock, shared by its four schedulers, so a CTA keeps b >= 4 warps (one pair
-// each) busy per sub-round.  Per pair: the dot product g = x.y (one FMA per
-// element), the rotation (four FP64 operations per element) and the column
-// norms tracked through the rotation (a' = c^2 (a - 2 t g + t^2 b), b' = c^2
-// (b + 2 t g + t^2 a), recomputed from the columns at the start of every
-// sweep).  The angle t = tan(theta) is solved in FP32 from the FP64 a, b, g;
-// c = (1 + t^2)^-1/2 and s = c t are formed in FP64 from that t, so the
-// rotation is orthogonal to FP64 rounding whatever the accuracy of t (a
-// less accurate angle only leaves a smaller off-diagonal for the next sweep).
+// clock, shared by its four schedulers (a warp instruction holds a
+// scheduler's share for ~64 cycles, also the latency of a dependent one), so
+// a CTA keeps b = 4 warps (one pair each) busy per sub-round and each pair
+// step issues as few FP64 instructions as possible: the dot product g = x.y
+// (one FMA per element and a shuffle tree) and the rotation (four per
+// element) run in FP64; the control arithmetic runs on the FP32 pipe.
+//   * The squared column norms a, b are tracked through the rotations in
+//     double-float (a' = (a - 2 t g + t^2 b) / (1 + t^2)), recomputed from the
+//     columns in FP64 at the start of every sweep.
+//   * The angle t = tan(theta) is solved in FP32 from them and g.
+//   * c and s are built in FP64 from the FP32 c~ = (1 + t^2)^-1/2: with
+//     kappa = c~^2 (1 + t^2) (FP64; c~^2 and c~ t are exact products),
+//     c = c~ rho, s = c~ t rho, rho = kappa^-1/2 = 1 - d/2 + 3 d^2 / 8 for
+//     d = kappa - 1 ~ 1e-7, so c^2 + s^2 = 1 to FP64 rounding: the rotation
+//     is orthogonal whatever the accuracy of t (a less accurate angle only
+//     leaves a smaller off-diagonal for the next sweep).
 //
 // shared layout per CTA: buf[parity][slot] = b columns of rs doubles,
-// nrm[parity][slot][b] (tracked squared norms), ids[parity][slot][b]
-// (global column index, -1 for pad), per-sweep rotation counters
+// nrm[parity][slot][b] (tracked squared norms, double-float), ids[parity]
+// [slot][b] (global column index, -1 for pad), per-sweep rotation counters
 __global__ void __launch_bounds__(256, 1) k_jacobi_rows_cl(JacRowsArgs a) {
   extern __shared__ double jsm[];
   cg::cluster_group cl = cg::this_cluster();
@@ -72,7 +79,7 @@ __global__ void __launch_bounds__(256, 1) k_jacobi_rows_cl(JacRowsArgs a) {
   const int b = a.b, rs = a.rs, r = a.r;
   const int blk = b * rs;                               // doubles per block
   double* buf = jsm;                                    // [2][2][blk]
-  double* nrm = buf + 4 * blk;                          // [2][2][b]
+  float2* nrm = reinterpret_cast<float2*>(buf + 4 * blk);   // [2][2][b] (hi, lo)
   int* ids = reinterpret_cast<int*>(nrm + 4 * b);       // [2][2][b]
   int* rotc = ids + 4 * b;                              // [kMaxSweeps] (CTA 0's copy is the sum)
   __shared__ int s_rot;
@@ -97,39 +104,58 @@ __global__ void __launch_bounds__(256, 1) k_jacobi_rows_cl(JacRowsArgs a) {
   for (int e = tid; e < kMaxSweeps; e += nth) rotc[e] = 0;
   cl.sync();                                            // every CTA started; DSMEM usable
 
-  const double eps = 1.1102230246251565e-16;
-  const double tol = eps * (double)(r > 16 ? r : 16);   // |x.y| <= tol ||x|| ||y||: orthogonal
-  const double tol2 = tol * tol;
+  // a pair is orthogonal once |x.y| <= tol ||x|| ||y||
+  const float tolf = 1.1102230246251565e-16f * (float)(r > 16 ? r : 16);
 
   // rotate the pair (x, y) with tracked squared norms (na, nb) in place (one warp)
-  auto rotate = [&](double* x, double* y, double* na, double* nb) -> int {
+  auto rotate = [&](double* x, double* y, float2* na, float2* nb) -> int {
     double gg = 0.0;
     for (int i = lane; i < rs; i += 32) gg = fma(x[i], y[i], gg);
     gg = warp_sum(gg);
-    const double aa = *na, bb = *nb;
-    if (gg == 0.0 || gg * gg <= tol2 * (aa * bb)) return 0;
-    // tan(theta) in FP32: zeta = (b - a) / (2 g), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2))
-    const float zf = (float)(bb - aa) / (float)(2.0 * gg);
+    const df32 g = df_from_f64(gg);
+    const float2 av = *na, bv = *nb;
+    const df32 aa{av.x, av.y}, bb{bv.x, bv.y};
+    if (g.hi == 0.0f || fabsf(g.hi) <= tolf * (sqrtf(aa.hi) * sqrtf(bb.hi))) return 0;
+    // zeta = (b - a) / (2 g) with the difference in double-float, then
+    // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), all FP32
+    const df32 dd = df_add(bb, df_neg(aa));
+    const float zf = __fdiv_rn(dd.hi + dd.lo, 2.0f * g.hi);
     const float tf = copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)));
     if (!(tf != 0.0f)) return 0;
-    const double t = (double)tf;
-    const double cs = rsqrt_newton(fma(t, t, 1.0));
-    const double sn = cs * t;
+    const float cf = rsqrtf(fmaf(tf, tf, 1.0f));
+    const double td = widen_f32(tf), cd = widen_f32(cf);
+    const double sd = cd * td;                           // exact (24 x 24 bits)
+    const double kap = (cd * cd) * fma(td, td, 1.0);     // c~^2 exact, one rounding each after
+    const double dlt = kap - 1.0;                        // exact (kappa ~ 1)
+    const double rho = fma(dlt, fma(dlt, 0.375, -0.5), 1.0);
+    const double cs = cd * rho, sn = sd * rho;
     for (int i = lane; i < rs; i += 32) {
       const double u = x[i], v = y[i];
       x[i] = fma(-sn, v, cs * u);
       y[i] = fma(sn, u, cs * v);
     }
-    __syncwarp();
     if (lane == 0) {
-      const double c2 = cs * cs, tg = 2.0 * t * gg, t2 = t * t;
-      *na = c2 * (fma(t2, bb, aa) - tg);
-      *nb = c2 * (fma(t2, aa, bb) + tg);
+      // a' = (a - 2 t g + t^2 b) / (1 + t^2), b' = (b + 2 t g + t^2 a) / (1 + t^2)
+      const df32 tg2 = df_mul_f(g, 2.0f * tf);
+      const float t2 = __fmul_rn(tf, tf);
+      const df32 t2df{t2, __fmaf_rn(tf, tf, -t2)};
+      const df32 na2 = df_add(df_add(aa, df_neg(tg2)), df_mul(t2df, bb));
+      const df32 nb2v = df_add(df_add(bb, tg2), df_mul(t2df, aa));
+      const float c2 = __fmul_rn(cf, cf);
+      const df32 q0{c2, __fmaf_rn(cf, cf, -c2)};         // c~^2 = 1 / kappa(1 + t^2) ... times rho^2 below
+      // 1 / (1 + t^2) = c~^2 rho^2, rho^2 = 1 - d + d^2 (d = kappa - 1, from the FP64 value)
+      float dh, dl;
+      split_f64_f2(dlt, dh, dl);
+      const df32 rho2 = df_add(df_from_f(1.0f), df32{-dh, -dl + dh * dh});
+      const df32 q = df_mul(q0, rho2);
+      const df32 ra = df_mul(na2, q), rb = df_mul(nb2v, q);
+      *na = make_float2(ra.hi, ra.lo);
+      *nb = make_float2(rb.hi, rb.lo);
     }
     __syncwarp();
     return 1;
   };
-  // squared norms of the columns this CTA holds (start of every sweep)
+  // squared norms of the columns this CTA holds (start of every sweep), FP64
   auto renorm = [&](int p) {
     for (int q = wid; q < 2 * b; q += nw) {
       const int slot = q / b, j = q - slot * b;
@@ -137,7 +163,11 @@ __global__ void __launch_bounds__(256, 1) k_jacobi_rows_cl(JacRowsArgs a) {
       double t = 0.0;
       for (int i = lane; i < rs; i += 32) t = fma(x[i], x[i], t);
       t = warp_sum(t);
-      if (lane == 0) nrm[(p * 2 + slot) * b + j] = t;
+      if (lane == 0) {
+        float h, l;
+        split_f64_f2(t, h, l);
+        nrm[(p * 2 + slot) * b + j] = make_float2(h, l);
+      }
     }
   };
 
@@ -150,8 +180,8 @@ __global__ void __launch_bounds__(256, 1) k_jacobi_rows_cl(JacRowsArgs a) {
     for (int round = 0; round < nb2 - 1; ++round) {
       double* A0 = buf + (par * 2 + 0) * blk;
       double* B0 = buf + (par * 2 + 1) * blk;
-      double* nA = nrm + (par * 2 + 0) * b;
-      double* nB = nrm + (par * 2 + 1) * b;
+      float2* nA = nrm + (par * 2 + 0) * b;
+      float2* nB = nrm + (par * 2 + 1) * b;
       const int* idA = ids + (par * 2 + 0) * b;
       const int* idB = ids + (par * 2 + 1) * b;
       if (round == 0) {
@@ -173,7 +203,7 @@ __global__ void __launch_bounds__(256, 1) k_jacobi_rows_cl(JacRowsArgs a) {
             const int* id = which == 0 ? idA : idB;
             if (id[p] < 0 || id[q] < 0) continue;
             double* base = which == 0 ? A0 : B0;
-            double* nn = which == 0 ? nA : nB;
+            float2* nn = which == 0 ? nA : nB;
             nrot += rotate(base + p * rs, base + q * rs, nn + p, nn + q);
           }
           __syncthreads();
@@ -199,11 +229,11 @@ __global__ void __launch_bounds__(256, 1) k_jacobi_rows_cl(JacRowsArgs a) {
         const int dcta = dpos < NC ? dpos : nb2 - 1 - dpos;
         const int dslot = dpos < NC ? 0 : 1;
         double* dst = cl.map_shared_rank(buf + (npar * 2 + dslot) * blk, dcta);
-        double* dnr = cl.map_shared_rank(nrm + (npar * 2 + dslot) * b, dcta);
+        float2* dnr = cl.map_shared_rank(nrm + (npar * 2 + dslot) * b, dcta);
         int* did = cl.map_shared_rank(ids + (npar * 2 + dslot) * b, dcta);
         const double* src = buf + (par * 2 + slot) * blk;
         for (int e = tid; e < blk; e += nth) dst[e] = src[e];
-        const double* snr = nrm + (par * 2 + slot) * b;
+        const float2* snr = nrm + (par * 2 + slot) * b;
         const int* sid = ids + (par * 2 + slot) * b;
         for (int e = tid; e < b; e += nth) { dnr[e] = snr[e]; did[e] = sid[e]; }
       }
@@ -274,7 +304,8 @@ struct ClusterPlan {
 };
 
 size_t rows_smem(int b, int rs) {
-  return sizeof(double) * (size_t)(4 * b * rs + 4 * b) + sizeof(int) * (size_t)(4 * b + kMaxSweeps) + 64;
+  return sizeof(double) * (size_t)(4 * b * rs) + sizeof(float2) * (size_t)(4 * b) +
+         sizeof(int) * (size_t)(4 * b + kMaxSweeps) + 64;
 }
 
 bool cluster_fits(int nc, int threads, size_t smem) {

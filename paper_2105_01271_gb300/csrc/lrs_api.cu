@@ -359,10 +359,10 @@ static size_t cpwr_ws(lrs_ctx* ctx, int64_t m, int64_t l, int64_t nI, int32_t pr
   need += align256(8 * (size_t)(nI * wmax)) + 2 * align256(8 * (size_t)(m * wmax));
   need += align256(8 * (size_t)(nI * wmax));                        // orthonormal T
   if (tc) need += align256(4 * (size_t)(nI * wmax)) + align256(4 * (size_t)(m * wmax));  // FP32 operands
-  // the factor chain of the iterate without re-orthonormalisation: two
-  // products of at most 128 x l and one factor of at most 128 x max(l, 128)
+  // the factor chain of the iterate without re-orthonormalisation: the
+  // sketch's factor (at most 128 x l) and six 128 x 128 buffers
   const int64_t lc = l > 128 ? l : 128;
-  need += 3 * align256(8 * (size_t)(128 * lc));
+  need += align256(8 * (size_t)(128 * lc)) + 6 * align256(8 * 128 * 128) + 1024;
   const size_t o1 = orth_ws(m, l, ctx->num_sms), o2 = orth_ws(nI, wmax, ctx->num_sms);
   size_t inner = o1 > o2 ? o1 : o2;
   if (tc) {
@@ -383,48 +383,67 @@ static size_t cpwr_ws(lrs_ctx* ctx, int64_t m, int64_t l, int64_t nI, int32_t pr
 // G <- W^T G; [QR]; G <- W G; [QR].  Loop buffers come from the workspace
 // above the caller's mark; the result is copied to G (ldg), *g_cols columns.
 //
-// Gid (optional, with reorth, q > 0): the iterate WITHOUT re-orthonormalisation,
-// (W W^T)^q Y, formed from the factors of this re-orthonormalised loop.  Every
-// QR(.) returns its factor with (input) = Q Rt, so
-//   (W W^T)^q Y = Q_q (Rt_g,q Rt_t,q ... Rt_g,1 Rt_t,1 Rt_np)
-// up to the directions the rank truncation drops; the product of the small
-// factors and the final Q_q times it run in FP64.  Products W^T G and W T in
+// Gid (optional, with reorth, q > 0): the row ID's iterate WITHOUT
+// re-orthonormalisation, (W W^T)^q Y, from the factors of this
+// re-orthonormalised loop.  Every QR(.) returns its factor with
+// (input) = Q Rt, so
+//   (W W^T)^q Y = Q_q M Rt_np,   M = Rt_g,q Rt_t,q ... Rt_g,1 Rt_t,1,
+// up to the directions the rank truncation drops.  The row ID depends on the
+// iterate only through the inner products of its rows, so Gid receives the
+// m x r_np matrix H = Q_q M Ra^T with Ra^T Ra = Rt_np Rt_np^T (Cholesky of
+// that small Gram): H H^T = (W W^T)^q Y ((W W^T)^q Y)^T, and the row ID of H
+// (its CPQR on r_np instead of l rows of the transpose) is the iterate's.
+// All of it runs in FP64 on r x r factors.  Products W^T G and W T in
 // FP32-level arithmetic resolve each direction of an ORTHONORMAL iterate to
 // FP32 accuracy relative to that direction's own scale, whereas the direct
 // (W W^T)^q Y scales direction j by s_j^(2q+1) and buries every direction
-// below ~1e-7 of the top under the products' rounding.
-// *gid_done tells whether Gid was written (the chain holds at most 128
-// directions; wider iterates leave it to the caller).
+// below ~1e-7 of the top under the products' rounding; squaring Rt_np in the
+// Gram costs direction j a factor (s_1/s_j)^2 of FP64 rounding, relative to
+// its own scale.  *gid_cols returns the columns of Gid (0 when it was not
+// written: an iterate of more than 128 directions, or a Cholesky breakdown,
+// is left to the caller).
 static lrs_status cpwr_loop(lrs_ctx* ctx, const void* W, const void* WT, int64_t m, int64_t l, int64_t nI,
                             const double* Y, int64_t ldy, int32_t q, int32_t reorth, double rtol, int32_t prec,
                             double* G, int64_t ldg, int64_t* g_cols, double* Gid = nullptr, int64_t ldgid = 0,
-                            bool* gid_done = nullptr) {
+                            int64_t* gid_cols = nullptr) {
   const int64_t wmax = l > m ? l : m;
   const bool tc = prec >= LRS_PREC_SPLIT_BF16;
   const int32_t wdt = tc ? LRS_F32 : LRS_F64;
   bool chain = Gid && reorth && q > 0;
-  if (gid_done) *gid_done = false;
+  if (gid_cols) *gid_cols = 0;
   const int64_t lc = l > 128 ? l : 128;
-  double* Nc = chain ? (double*)ws_alloc(ctx, 8 * (size_t)(128 * lc)) : nullptr;   // the product so far
-  double* Nn = chain ? (double*)ws_alloc(ctx, 8 * (size_t)(128 * lc)) : nullptr;
-  double* Rf = chain ? (double*)ws_alloc(ctx, 8 * (size_t)(128 * lc)) : nullptr;   // one factor
-  if (chain && (!Nc || !Nn || !Rf)) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (power_pass chain)");
-  int64_t nrows = 0;                   // rows of the product so far (its columns: l)
-  // Nn <- Rf (rr x nrows) * Nc (nrows x l); swap
+  const size_t sq = 8 * 128 * 128;
+  double* RtY = chain ? (double*)ws_alloc(ctx, 8 * (size_t)(128 * lc)) : nullptr;   // QR(Y)'s factor
+  double* Mc = chain ? (double*)ws_alloc(ctx, sq) : nullptr;                          // the product M so far
+  double* Mn = chain ? (double*)ws_alloc(ctx, sq) : nullptr;
+  double* Rf = chain ? (double*)ws_alloc(ctx, sq) : nullptr;                          // one factor
+  double* Ga = chain ? (double*)ws_alloc(ctx, sq) : nullptr;
+  double* Ra = chain ? (double*)ws_alloc(ctx, sq) : nullptr;
+  double* Kf = chain ? (double*)ws_alloc(ctx, sq) : nullptr;
+  int32_t* cperm = chain ? (int32_t*)ws_alloc(ctx, 4 * 128) : nullptr;
+  int32_t* crank = chain ? (int32_t*)ws_alloc(ctx, 8) : nullptr;
+  if (chain && (!RtY || !Mc || !Mn || !Rf || !Ga || !Ra || !Kf || !cperm || !crank))
+    return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (power_pass chain)");
+  int64_t rnp = 0, mrows = 0;          // columns of M (= rank of QR(Y)); rows of M so far
+  // M <- Rf (rr x mrows) M, the first factor taken as it is
   auto chain_mul = [&](int64_t rr) -> lrs_status {
-    lrs_status s2 = spc_small_gemm(ctx, rr, l, nrows, Rf, nrows, 1, Nc, l, 1, nullptr, nullptr, Nn, l);
-    if (s2) return s2;
-    double* t = Nc; Nc = Nn; Nn = t;
-    nrows = rr;
+    if (mrows == 0) {
+      double* t = Mc; Mc = Rf; Rf = t;
+    } else {
+      lrs_status s2 = spc_small_gemm(ctx, rr, rnp, mrows, Rf, mrows, 1, Mc, rnp, 1, nullptr, nullptr, Mn, rnp);
+      if (s2) return s2;
+      double* t = Mc; Mc = Mn; Mn = t;
+    }
+    mrows = rr;
     return LRS_OK;
   };
   double* Tm = (double*)ws_alloc(ctx, 8 * (size_t)(nI * wmax));
   double* To = (double*)ws_alloc(ctx, 8 * (size_t)(nI * wmax));
-  double* Ga = (double*)ws_alloc(ctx, 8 * (size_t)(m * wmax));
-  double* Gb = (double*)ws_alloc(ctx, 8 * (size_t)(m * wmax));
+  double* Ga_ = (double*)ws_alloc(ctx, 8 * (size_t)(m * wmax));
+  double* Gb_ = (double*)ws_alloc(ctx, 8 * (size_t)(m * wmax));
   float* T32 = tc ? (float*)ws_alloc(ctx, 4 * (size_t)(nI * wmax)) : nullptr;
   float* G32 = tc ? (float*)ws_alloc(ctx, 4 * (size_t)(m * wmax)) : nullptr;
-  if (!Tm || !To || !Ga || !Gb || (tc && (!T32 || !G32)))
+  if (!Tm || !To || !Ga_ || !Gb_ || (tc && (!T32 || !G32)))
     return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (power_pass)");
   const size_t mark = ctx->ws_top;
   lrs_status st = LRS_OK;
@@ -435,11 +454,11 @@ static lrs_status cpwr_loop(lrs_ctx* ctx, const void* W, const void* WT, int64_t
   if (reorth) {
     // Q_np only feeds W^T Q_np, which is orthonormalised again: a
     // well-conditioned basis of the same range suffices (no refinement pass)
-    st = orth(ctx, Y, m, l, ldy, rtol, Ga, wmax, &gc, /*intermediate=*/q > 0, nullptr, 0, chain ? Nc : nullptr);
+    st = orth(ctx, Y, m, l, ldy, rtol, Ga_, wmax, &gc, /*intermediate=*/q > 0, nullptr, 0, chain ? RtY : nullptr);
     if (st) return st;
     ctx->ws_top = mark;
-    Gcur = Ga; ldcur = wmax;
-    nrows = gc;                        // Y = Q_np Rt_np
+    Gcur = Ga_; ldcur = wmax;
+    rnp = gc;                          // Y = Q_np Rt_np
     if (gc > 128) chain = false;       // no factor chain beyond 128 directions
   }
   for (int it = 0; it < q; ++it) {
@@ -479,13 +498,13 @@ static lrs_status cpwr_loop(lrs_ctx* ctx, const void* W, const void* WT, int64_t
     }
     // G = W T   (m x tc_cols)  computed as (W^T)^T T; tensor-core modes form
     // G^T = T^T W^T with the narrow T prepared and W^T streamed, stored transposed
-    double* Gn = (Gcur == Ga) ? Gb : Ga;
+    double* Gn = (Gcur == Ga_) ? Gb_ : Ga_;
     if (tc && tc_cols <= 256) st = gemm(ctx, prec, tc_cols, m, nI, Tcur, tdt, gc, WT, wdt, m, Gn, 1, 1, wmax);
     else st = gemm(ctx, prec, m, tc_cols, nI, WT, wdt, m, Tcur, tdt, gc, Gn, 1, 0, wmax);
     if (st) return st;
     ctx->ws_top = mark;
     if (reorth) {
-      double* Go = (Gn == Ga) ? Gb : Ga;
+      double* Go = (Gn == Ga_) ? Gb_ : Ga_;
       // only the last iterate is returned as the orthonormal basis G_q
       st = orth(ctx, Gn, m, tc_cols, wmax, rtol, Go, wmax, &gc, /*intermediate=*/it + 1 < q, nullptr, 0,
                 chain ? Rf : nullptr);
@@ -501,11 +520,23 @@ static lrs_status cpwr_loop(lrs_ctx* ctx, const void* W, const void* WT, int64_t
   }
   LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(G, ldg * 8, Gcur, ldcur * 8, gc * 8, m, cudaMemcpyDeviceToDevice, ctx->stream));
   *g_cols = gc;
-  if (chain) {
-    // (W W^T)^q Y = Q_q N, N = the factor product (gc x l), in FP64
-    st = spc_small_gemm(ctx, m, l, gc, Gcur, ldcur, 1, Nc, l, 1, nullptr, nullptr, Gid, ldgid);
+  if (chain && mrows == gc) {
+    // Ra^T Ra = Rt_np Rt_np^T (rnp x rnp), plain Cholesky in FP64
+    st = spc_small_gemm(ctx, rnp, rnp, l, RtY, l, 1, RtY, 1, l, nullptr, nullptr, Ga, rnp);
     if (st) return st;
-    if (gid_done) *gid_done = true;
+    st = launch_pchol(ctx, Ga, (int)rnp, (int)rnp, 0.0, 0, cperm, Ra, rnp, crank);
+    if (st) return st;
+    int32_t* hr = (int32_t*)ctx->host_scratch;
+    LRS_CUDA_TRY(ctx, cudaMemcpyAsync(hr + 46, crank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (hr[46] == (int32_t)rnp) {
+      // H = Q_q (M Ra^T): m x rnp
+      st = spc_small_gemm(ctx, gc, rnp, rnp, Mc, rnp, 1, Ra, 1, rnp, nullptr, nullptr, Kf, rnp);
+      if (st) return st;
+      st = spc_small_gemm(ctx, m, rnp, gc, Gcur, ldcur, 1, Kf, rnp, 1, nullptr, nullptr, Gid, ldgid);
+      if (st) return st;
+      if (gid_cols) *gid_cols = rnp;
+    }
   }
   return LRS_OK;
 }
@@ -580,13 +611,12 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
     double* Gs = (double*)ws_alloc(ctx, 8 * (size_t)(m * l));
     if (!Gs) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (power_pass)");
     const size_t mark = ctx->ws_top;
-    int64_t gq = 0;
-    bool done = false;
-    st = cpwr_loop(ctx, W, WT, m, l, nI, Y, ldy, q, 1, rtol, prec, Gs, l, &gq, G, ldg, &done);
+    int64_t gq = 0, gid = 0;
+    st = cpwr_loop(ctx, W, WT, m, l, nI, Y, ldy, q, 1, rtol, prec, Gs, l, &gq, G, ldg, &gid);
     if (st) return st;
     ctx->ws_top = mark;
-    if (done) {
-      *g_cols = l;
+    if (gid > 0) {
+      *g_cols = gid;
       LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
       return LRS_OK;
     }
@@ -599,14 +629,14 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
 
 lrs_status lrs_power_pass2(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t lda,
                            const lrs_grid* sketch, const lrs_grid* gram, int32_t q, double rtol, int32_t prec,
-                           double* Y, int64_t ldy, double* G0, int64_t ldg0, double* G, int64_t ldg,
-                           int64_t* g_cols) {
+                           double* Y, int64_t ldy, double* G0, int64_t ldg0, int64_t* g0_cols, double* G,
+                           int64_t ldg, int64_t* g_cols) {
   if (!ctx) return LRS_EINVAL;
   ctx->err[0] = 0;
   GridDev gs, gg;
   lrs_status st = power_pass_check(ctx, A, dtype, m, lda, sketch, gram, q, rtol, prec, &gs, &gg);
   if (st) return st;
-  if (!Y || !G || !G0 || !g_cols) return lrs_fail(ctx, LRS_EINVAL, "power_pass2: NULL pointer");
+  if (!Y || !G || !G0 || !g_cols || !g0_cols) return lrs_fail(ctx, LRS_EINVAL, "power_pass2: NULL pointer");
   if (ldy < gs.l || ldg < gs.l || ldg0 < gs.l) return lrs_fail(ctx, LRS_EINVAL, "power_pass2: strides too small");
   LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   const int64_t l = gs.l;
@@ -620,6 +650,7 @@ lrs_status lrs_power_pass2(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m
     LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(G0, ldg0 * 8, Y, ldy * 8, l * 8, m, cudaMemcpyDeviceToDevice, ctx->stream));
     LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(G, ldg * 8, Y, ldy * 8, l * 8, m, cudaMemcpyDeviceToDevice, ctx->stream));
     *g_cols = l;
+    *g0_cols = l;
     return LRS_OK;
   }
   // The SVD's re-orthonormalised loop; its factors also give the ID's
@@ -627,14 +658,14 @@ lrs_status lrs_power_pass2(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m
   // products, or a chain wider than 128 directions: the ID's loop runs on its
   // own.  The loop buffers are reused, W and W^T stay below the mark.
   const size_t mark = ctx->ws_top;
-  bool done = false;
+  int64_t gid = 0;
   st = cpwr_loop(ctx, W, WT, m, l, nI, Y, ldy, q, 1, rtol, prec, G, ldg, g_cols,
-                 prec != LRS_PREC_FP64 ? G0 : nullptr, ldg0, &done);
+                 prec != LRS_PREC_FP64 ? G0 : nullptr, ldg0, &gid);
   if (st) return st;
   ctx->ws_top = mark;
-  if (!done) {
-    int64_t g0 = 0;
-    st = cpwr_loop(ctx, W, WT, m, l, nI, Y, ldy, q, 0, rtol, prec, G0, ldg0, &g0);
+  *g0_cols = gid;
+  if (gid == 0) {
+    st = cpwr_loop(ctx, W, WT, m, l, nI, Y, ldy, q, 0, rtol, prec, G0, ldg0, g0_cols);
     if (st) return st;
   }
   LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
@@ -845,7 +876,9 @@ lrs_status lrs_id_k(lrs_ctx* ctx, const double* Ysk, int64_t m, int64_t l, int64
   ctx->err[0] = 0;
   if (!Ysk || !J || !P) return lrs_fail(ctx, LRS_EINVAL, "id_k: NULL pointer");
   if (m < 1 || l < 1 || k < 1) return lrs_fail(ctx, LRS_EINVAL, "id_k: m=%lld l=%lld k=%d", (long long)m, (long long)l, k);
-  if (k > m || k > l) return lrs_fail(ctx, LRS_EINVAL, "id_k: k=%d exceeds min(m,l)", k);
+  if (k > m) return lrs_fail(ctx, LRS_EINVAL, "id_k: k=%d exceeds m=%lld", k, (long long)m);
+  // a sketch of l < k columns has rank below k: a rank-k ID does not exist
+  if (k > l) return lrs_fail(ctx, LRS_ERANK, "id_k: sketch rank <= l=%lld < k=%d", (long long)l, k);
   if (ldy < l || ldp < k) return lrs_fail(ctx, LRS_EINVAL, "id_k: strides too small");
   LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   size_t need = align256(8 * (size_t)(m * l)) + align256(4 * (size_t)m) +

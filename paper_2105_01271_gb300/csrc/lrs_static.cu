@@ -52,7 +52,8 @@ extern "C" lrs_status lrs_id_k_static(lrs_ctx* ctx, const double* Ysk, int64_t m
   ctx->err[0] = 0;
   if (!Ysk || !J || !P) return lrs_fail(ctx, LRS_EINVAL, "id_k_static: NULL pointer");
   if (m < 1 || l < 1 || k < 1) return lrs_fail(ctx, LRS_EINVAL, "id_k_static: m=%lld l=%lld k=%d", (long long)m, (long long)l, k);
-  if (k > m || k > l) return lrs_fail(ctx, LRS_EINVAL, "id_k_static: k=%d exceeds min(m,l)", k);
+  if (k > m) return lrs_fail(ctx, LRS_EINVAL, "id_k_static: k=%d exceeds m=%lld", k, (long long)m);
+  if (k > l) return lrs_fail(ctx, LRS_ERANK, "id_k_static: sketch rank <= l=%lld < k=%d", (long long)l, k);
   if (ldy < l || ldp < k) return lrs_fail(ctx, LRS_EINVAL, "id_k_static: strides too small");
   // exact scratch of this call: copy of the sketch, CPQR outputs and scratch, ||.||^2 partials
   const int64_t nfro = m < (int64_t)ctx->num_sms * 8 ? m : (int64_t)ctx->num_sms * 8;

@@ -487,6 +487,11 @@ static lrs_status launch_trmm_upper(lrs_ctx* ctx, const double* U, int64_t r, co
   return LRS_OK;
 }
 
+lrs_status launch_pchol(lrs_ctx* ctx, const double* G, int c, int kmax, double rtol, int pivot, int32_t* perm,
+                        double* R, int64_t ldr, int32_t* rank) {
+  return pchol(ctx, G, c, kmax, rtol, pivot, perm, R, ldr, rank);
+}
+
 bool orth_gram_eligible(int64_t p, int64_t c, double rtol) {
   return c >= 1 && c <= kMaxC && p >= 4 * c && rtol >= kOrthGramRtolMin;
 }

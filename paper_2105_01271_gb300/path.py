@@ -93,16 +93,16 @@ def id_path(ctx: Context, A: torch.Tensor, dtype: str, grid, k: int, q: int = 0,
     l = int(grid.l)
     gg = grid_of(gram) if (gram is not None and q > 0) else None
     b = bufs or Buffers(m, n, l, k, A.device, prec == LRS_PREC_FP64)
-    ctx.power_pass(A, dt, m, n, g, gg, q, 0, rtol, prec, b.Yid, l, b.Gid, l)
-    err, st = ctx.id_k(b.Gid, m, l, l, k, b.J, b.P, k)
+    g0 = ctx.power_pass(A, dt, m, n, g, gg, q, 0, rtol, prec, b.Yid, l, b.Gid, l)
+    err, st = ctx.id_k(b.Gid, m, g0, l, k, b.J, b.P, k)
     return IdResult(b.J, b.P, err, st)
 
 
 def power_pass2(ctx: Context, A: torch.Tensor, dtype: str, grid, q: int = 0, gram=None, rtol: float = 1e-12,
-                prec: int | None = None, bufs: Buffers | None = None) -> int:
+                prec: int | None = None, bufs: Buffers | None = None):
     """One touch of A_f for both paths: the sketch into bufs.Y, the ID's C-PWR
-    iterate into bufs.Gid, the SVD's orthonormal one into bufs.G; returns the
-    SVD basis width."""
+    iterate into bufs.Gid, the SVD's orthonormal one into bufs.G; returns
+    (columns of the ID's iterate, SVD basis width)."""
     m, n = A.shape
     prec = default_prec(dtype) if prec is None else prec
     l = int(grid.l)
@@ -113,7 +113,8 @@ def power_pass2(ctx: Context, A: torch.Tensor, dtype: str, grid, q: int = 0, gra
 
 def svd_from_pass(ctx: Context, A: torch.Tensor, dtype: str, grid, k: int, q: int, gc: int, rtol: float,
                   prec: int, bufs: Buffers) -> SvdResult:
-    """The SVD path after power_pass2 (the basis of bufs.G, gc columns)."""
+    """The SVD path after power_pass2 (the basis of bufs.G, gc columns: the
+    second value power_pass2 returns)."""
     m, n = A.shape
     l = int(grid.l)
     if q > 0:
@@ -127,10 +128,11 @@ def svd_from_pass(ctx: Context, A: torch.Tensor, dtype: str, grid, k: int, q: in
     return SvdResult(bufs.U[:, :kk], bufs.S[:kk], bufs.V[:, :kk], err, r, gc, st)
 
 
-def id_from_pass(ctx: Context, m: int, grid, k: int, bufs: Buffers) -> IdResult:
-    """The row ID after power_pass2 (the iterate in bufs.Gid)."""
+def id_from_pass(ctx: Context, m: int, grid, k: int, g0: int, bufs: Buffers) -> IdResult:
+    """The row ID after power_pass2 (the iterate in bufs.Gid, g0 columns: the
+    first value power_pass2 returns)."""
     l = int(grid.l)
-    err, st = ctx.id_k(bufs.Gid, m, l, l, k, bufs.J, bufs.P, k)
+    err, st = ctx.id_k(bufs.Gid, m, g0, l, k, bufs.J, bufs.P, k)
     return IdResult(bufs.J, bufs.P, err, st)
 
 

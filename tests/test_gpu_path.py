@@ -355,11 +355,33 @@ def test_power_pass2_equals_two_passes(lrs, blob, prec, q):
     f64 = dict(dtype=torch.float64, device="cuda")
     Y1, G1, Y2, G2 = (torch.full((m, l), np.nan, **f64) for _ in range(4))
     Y, G0, G = (torch.full((m, l), np.nan, **f64) for _ in range(3))
-    lrs.power_pass(Ad, b.LRS_F32, m, n, g, gg, q, 0, c["rtol"], prec, Y1, l, G1, l)
+    g1 = lrs.power_pass(Ad, b.LRS_F32, m, n, g, gg, q, 0, c["rtol"], prec, Y1, l, G1, l)
     gc2 = lrs.power_pass(Ad, b.LRS_F32, m, n, g, gg, q, 1, c["rtol"], prec, Y2, l, G2, l)
-    gc = lrs.power_pass2(Ad, b.LRS_F32, m, n, g, gg, q, c["rtol"], prec, Y, l, G0, l, G, l)
+    g0, gc = lrs.power_pass2(Ad, b.LRS_F32, m, n, g, gg, q, c["rtol"], prec, Y, l, G0, l, G, l)
     torch.cuda.synchronize()
-    assert gc == gc2
+    assert gc == gc2 and g0 == g1
+    # q > 0: the row-Gram form of the iterate, as many columns as the basis of QR(A_f D)
+    assert (g0 == l) if q == 0 else (0 < g0 <= 128)
     assert torch.equal(Y, Y1) and torch.equal(Y, Y2)
-    assert torch.equal(G0, G1)
+    assert torch.equal(G0[:, :g0], G1[:, :g1])
     assert torch.equal(G[:, :gc], G2[:, :gc])
+
+
+def test_row_gram_form_of_the_iterate(lrs, blob):
+    """The m x r form H of the ID's iterate has the row inner products of the
+    iterate (W W^T)^q A_f D: H H^T against the oracle's G G^T, within the
+    products' accuracy (FP32-level, relative to ||G||^2)."""
+    torch = _torch()
+    from paper_2105_01271_gb300 import binding as b
+    A, _, d = blob
+    c = BLOB_SMALL
+    m, n, l = A.shape[0], A.shape[1], c["grid"].l
+    Y, G = (torch.full((m, l), np.nan, dtype=torch.float64, device="cuda") for _ in range(2))
+    g0 = lrs.power_pass(_dev(A), b.LRS_F32, m, n, b.grid_of(c["grid"]), b.grid_of(c["gram"]), 1, 0, c["rtol"],
+                        b.LRS_PREC_FP32, Y, l, G, l)
+    H = _np(G)[:, :g0]
+    Go = d["G"]
+    GG = Go @ Go.T
+    # FP32 FMA products over m and |I| terms, FP32 operands: a few hundred u32 of ||G||^2
+    assert np.max(np.abs(H @ H.T - GG)) <= 256 * U32 * np.max(np.abs(GG))
+    assert abs(np.linalg.norm(H) / np.linalg.norm(Go) - 1.0) <= 1e-5
