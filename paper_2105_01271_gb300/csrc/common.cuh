@@ -91,6 +91,20 @@ __device__ __forceinline__ df32 df_mul_f(df32 a, float b) {
   return df_norm(p, __fmaf_rn(a.lo, b, e));
 }
 __device__ __forceinline__ df32 df_from_f(float a) { return {a, 0.0f}; }
+// a / b: the FP32 quotient and one correction from the double-float remainder
+__device__ __forceinline__ df32 df_div(df32 a, df32 b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const df32 r = df_add(a, df_neg(df_mul_f(b, q1)));
+  return df_norm(q1, __fdiv_rn(r.hi, b.hi));
+}
+// sqrt(a), a > 0: the FP32 root and one correction, (a - s^2) / (2 s)
+__device__ __forceinline__ df32 df_sqrt(df32 a) {
+  const float s = sqrtf(a.hi);
+  const float p = __fmul_rn(s, s);
+  const float e = __fmaf_rn(s, s, -p);
+  const float r = __fadd_rn(__fsub_rn(a.hi, p), __fsub_rn(a.lo, e));
+  return df_norm(s, __fdiv_rn(r, 2.0f * s));
+}
 __device__ __forceinline__ df32 df_from_f64(double x) {
   df32 r;
   split_f64_f2(x, r.hi, r.lo);
@@ -134,6 +148,22 @@ __device__ __forceinline__ bool pivot_better(double a, int pa, double b, int pb)
 __device__ __forceinline__ double rsqrt_newton(double x) {
   if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
   double y = (double)rsqrtf((float)x);
+  const double hx = 0.5 * x;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) y = y * fma(-hx * y, y, 1.5);
+  return y;
+}
+
+// 1/sqrt(x) for x > 0 with the short dependency chain this part's FP64 pipe
+// wants (each dependent FP64 instruction waits ~64 cycles): the FP32 seed
+// comes from the integer-pipe split and widening (no conversion
+// instructions), then two Newton-Raphson steps y <- y (3 - x y^2) / 2 in
+// FP64 reach FP64 precision.  Outside the seed's range, 1 / sqrt(x).
+__device__ __forceinline__ double rsqrt_fast(double x) {
+  if (!(x > 1e-22 && x < 1e38)) return 1.0 / sqrt(x);
+  float xh, xl;
+  split_f64_f2(x, xh, xl);
+  double y = widen_f32(rsqrtf(xh));
   const double hx = 0.5 * x;
 #pragma unroll
   for (int it = 0; it < 2; ++it) y = y * fma(-hx * y, y, 1.5);

@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kCpqrThreads, 1) k_cpqr(CpqrState s) {
       }
       // thread 0 holds the global winner
       if (threadIdx.x == 0) {
-        const double nrm = bv > 0.0 ? bv * rsqrt_newton(bv) : 0.0;
+        const double nrm = bv > 0.0 ? bv * rsqrt_fast(bv) : 0.0;
         if (j == 0) top = nrm;
         const bool stop = (j >= s.kmax) || bf < 0 || bv <= 0.0 || (j > 0 && nrm <= s.rtol * top);
         s_stop = stop ? 1 : 0;
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kCpqrThreads, 1) k_cpqr(CpqrState s) {
           const double sgn = x0 >= 0.0 ? 1.0 : -1.0;
           const double vn2 = 2.0 * nrm * (nrm + fabs(x0));     // ||x + sgn ||x|| e_j||^2
           s_alpha = nrm; s_sgn = sgn; s_x0 = x0;
-          s_inv = vn2 > 0.0 ? rsqrt_newton(vn2) : 0.0;
+          s_inv = vn2 > 0.0 ? rsqrt_fast(vn2) : 0.0;
         }
       }
       __syncthreads();
@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(kColsThreads, 1) k_cpqr_cols(CpqrColsState s) 
       if (threadIdx.x == 0) {
         for (int w = 1; w < nw; ++w)
           if (pivot_better(sv[w], sp[w], bv, bp)) { bv = sv[w]; bp = sp[w]; bf = sf[w]; }
-        const double nrm = bv > 0.0 ? bv * rsqrt_newton(bv) : 0.0;
+        const double nrm = bv > 0.0 ? bv * rsqrt_fast(bv) : 0.0;
         if (j == 0) s_top = nrm;
         const bool stop = (j >= s.kmax) || bf < 0 || !(bv > 0.0) || (j > 0 && nrm <= s.rtol * s_top);
         s_stop = stop ? 1 : 0;
@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(kColsThreads, 1) k_cpqr_cols(CpqrColsState s) 
         const double sgn = x0 >= 0.0 ? 1.0 : -1.0;
         const double vn2 = 2.0 * nrm * (nrm + fabs(x0));
         s_sgn = sgn;
-        s_inv = vn2 > 0.0 ? rsqrt_newton(vn2) : 0.0;
+        s_inv = vn2 > 0.0 ? rsqrt_fast(vn2) : 0.0;
       }
       __syncthreads();
       const double inv = s_inv;

@@ -60,13 +60,13 @@ struct JacRowsArgs {
 //   * The squared column norms a, b are tracked through the rotations in
 //     double-float (a' = (a - 2 t g + t^2 b) / (1 + t^2)), recomputed from the
 //     columns in FP64 at the start of every sweep.
-//   * The angle t = tan(theta) is solved in FP32 from them and g.
+//   * The angle t = tan(theta) is solved in double-float from them and g.
 //   * c and s are built in FP64 from the FP32 c~ = (1 + t^2)^-1/2: with
-//     kappa = c~^2 (1 + t^2) (FP64; c~^2 and c~ t are exact products),
-//     c = c~ rho, s = c~ t rho, rho = kappa^-1/2 = 1 - d/2 + 3 d^2 / 8 for
-//     d = kappa - 1 ~ 1e-7, so c^2 + s^2 = 1 to FP64 rounding: the rotation
-//     is orthogonal whatever the accuracy of t (a less accurate angle only
-//     leaves a smaller off-diagonal for the next sweep).
+//     kappa = c~^2 (1 + t^2) (FP64; c~^2 is an exact product), c = c~ rho,
+//     s = c~ t rho, rho = kappa^-1/2 = 1 - d/2 + 3 d^2 / 8 for d = kappa - 1
+//     ~ 1e-7, so c^2 + s^2 = 1 to FP64 rounding: the rotation is orthogonal
+//     whatever the accuracy of t (a less accurate angle only leaves a smaller
+//     off-diagonal for the next sweep).
 //
 // shared layout per CTA: buf[parity][slot] = b columns of rs doubles,
 // nrm[parity][slot][b] (tracked squared norms, double-float), ids[parity]
@@ -116,34 +116,42 @@ __global__ void __launch_bounds__(256, 1) k_jacobi_rows_cl(JacRowsArgs a) {
     const float2 av = *na, bv = *nb;
     const df32 aa{av.x, av.y}, bb{bv.x, bv.y};
     if (g.hi == 0.0f || fabsf(g.hi) <= tolf * (sqrtf(aa.hi) * sqrtf(bb.hi))) return 0;
-    // zeta = (b - a) / (2 g) with the difference in double-float, then
-    // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), all FP32
+    // zeta = (b - a) / (2 g), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+    // in double-float: an angle accurate to ~1e-14 keeps the convergence of
+    // the last sweeps quadratic
     const df32 dd = df_add(bb, df_neg(aa));
-    const float zf = __fdiv_rn(dd.hi + dd.lo, 2.0f * g.hi);
-    const float tf = copysignf(1.0f, zf) / (fabsf(zf) + sqrtf(fmaf(zf, zf, 1.0f)));
+    const df32 zeta = df_div(dd, df32{2.0f * g.hi, 2.0f * g.lo});
+    df32 t;
+    if (fabsf(zeta.hi) > 1e18f) {
+      t = df_div(df_from_f(0.5f), zeta);                 // 1 / (2 zeta): 1 + zeta^2 overflows
+    } else {
+      const df32 w = df_sqrt(df_add(df_from_f(1.0f), df_mul(zeta, zeta)));
+      const df32 den = df_add(zeta.hi < 0.0f ? df_neg(zeta) : zeta, w);
+      t = df_div(df_from_f(zeta.hi < 0.0f ? -1.0f : 1.0f), den);
+    }
+    const float tf = t.hi;
     if (!(tf != 0.0f)) return 0;
     const float cf = rsqrtf(fmaf(tf, tf, 1.0f));
-    const double td = widen_f32(tf), cd = widen_f32(cf);
-    const double sd = cd * td;                           // exact (24 x 24 bits)
+    const double td = widen_f32(tf) + widen_f32(t.lo), cd = widen_f32(cf);
+    const double sd = cd * td;
     const double kap = (cd * cd) * fma(td, td, 1.0);     // c~^2 exact, one rounding each after
     const double dlt = kap - 1.0;                        // exact (kappa ~ 1)
     const double rho = fma(dlt, fma(dlt, 0.375, -0.5), 1.0);
-    const double cs = cd * rho, sn = sd * rho;
+    const double cs = cd * rho, sn = sd * rho;           // cs^2 + sn^2 = rho^2 kappa = 1 + O(u64)
     for (int i = lane; i < rs; i += 32) {
       const double u = x[i], v = y[i];
       x[i] = fma(-sn, v, cs * u);
       y[i] = fma(sn, u, cs * v);
     }
     if (lane == 0) {
-      // a' = (a - 2 t g + t^2 b) / (1 + t^2), b' = (b + 2 t g + t^2 a) / (1 + t^2)
-      const df32 tg2 = df_mul_f(g, 2.0f * tf);
-      const float t2 = __fmul_rn(tf, tf);
-      const df32 t2df{t2, __fmaf_rn(tf, tf, -t2)};
+      // a' = (a - 2 t g + t^2 b) / (1 + t^2), b' = (b + 2 t g + t^2 a) / (1 + t^2),
+      // 1 / (1 + t^2) = c~^2 / kappa = c~^2 (1 - d + d^2)
+      const df32 tg2 = df_mul(g, df32{2.0f * t.hi, 2.0f * t.lo});
+      const df32 t2df = df_mul(t, t);
       const df32 na2 = df_add(df_add(aa, df_neg(tg2)), df_mul(t2df, bb));
       const df32 nb2v = df_add(df_add(bb, tg2), df_mul(t2df, aa));
       const float c2 = __fmul_rn(cf, cf);
-      const df32 q0{c2, __fmaf_rn(cf, cf, -c2)};         // c~^2 = 1 / kappa(1 + t^2) ... times rho^2 below
-      // 1 / (1 + t^2) = c~^2 rho^2, rho^2 = 1 - d + d^2 (d = kappa - 1, from the FP64 value)
+      const df32 q0{c2, __fmaf_rn(cf, cf, -c2)};
       float dh, dl;
       split_f64_f2(dlt, dh, dl);
       const df32 rho2 = df_add(df_from_f(1.0f), df32{-dh, -dl + dh * dh});

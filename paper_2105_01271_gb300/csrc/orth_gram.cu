@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(256) k_pchol(const double* __restrict__ Gin, i
     if (threadIdx.x == 0) {
       // R_jj = sqrt(d), 1 / R_jj = rsqrt(d); the stop test |R_jj| <= rtol |R_00|
       // is taken on the squares, d <= rtol^2 d_0
-      const double y = bv > 0.0 ? rsqrt_newton(bv) : 0.0;
+      const double y = bv > 0.0 ? rsqrt_fast(bv) : 0.0;
       if (j == 0) s_top = bv;
       const bool stop = (j >= kmax) || j >= c || !(bv > 0.0) || (j > 0 && bv <= rtol * rtol * s_top);
       s_stop = stop ? 1 : 0;
@@ -201,9 +201,22 @@ __global__ void __launch_bounds__(256) k_pchol(const double* __restrict__ Gin, i
     }
     __syncthreads();
     // ---- Schur complement, upper triangle: S_ab -= R_ja R_jb (j < a <= b) -----
-    for (int a = j + 1 + wid; a < c; a += nw) {
-      const double ra = G[j * ld + a];
-      for (int b2 = a + lane; b2 < c; b2 += 32) G[a * ld + b2] = fma(-ra, G[j * ld + b2], G[a * ld + b2]);
+    // the n (n + 1) / 2 entries dealt evenly over the block (one FMA each; a
+    // row per warp would leave the short rows' lanes idle), entry e counted
+    // from the end: f = T - 1 - e lies in the k-th row from the bottom with
+    // k (k + 1) / 2 <= f < (k + 1) (k + 2) / 2
+    {
+      const int n = c - j - 1;
+      const int T = n * (n + 1) / 2;
+      for (int e = threadIdx.x; e < T; e += blockDim.x) {
+        const int f = T - 1 - e;
+        int k = (int)((sqrtf(8.0f * (float)f + 1.0f) - 1.0f) * 0.5f);
+        if ((k + 1) * (k + 2) / 2 <= f) ++k;
+        if (k * (k + 1) / 2 > f) --k;
+        const int a = j + 1 + (n - 1 - k);
+        const int b2 = j + 1 + (n - 1 - (f - k * (k + 1) / 2));
+        G[a * ld + b2] = fma(-G[j * ld + a], G[j * ld + b2], G[a * ld + b2]);
+      }
     }
     __syncthreads();
   }
@@ -744,7 +757,7 @@ __global__ void __launch_bounds__(kLpThreads, 1) k_lpchol(LpcholState s) {
         phys_at[j] = bf; phys_at[bp] = pj;
         pos_of[bf] = (int)j; pos_of[pj] = bp;
         // L(piv, j) = sqrt(d_piv) and its reciprocal, once per step
-        const double y = rsqrt_newton(bv);
+        const double y = rsqrt_fast(bv);
         s_piv = bf; s_ljj = bv * y; s_inv = y;
         if (bf >= o_lo && bf < o_hi) s_done[bf - o_lo] = 1;
       }
