@@ -42,8 +42,8 @@ UNIT = "decomps/s"
 # DRAM bytes (read + write) of one A-pass launch from an ncu capture of the
 # current kernel (profiles/k_apass_<workload>.md); set to None when the kernel
 # changes until it is captured again.
-APASS_TRAFFIC = {("blob2d_m2000_512x512_f32", "split_bf16"): 2.107053e9 + 72.585728e6,
-                 ("heat3d_m500_256c_bf16", "split_bf16"): 16.779508e9 + 7.618061e9}
+APASS_TRAFFIC = {("blob2d_m2000_512x512_f32", "split_bf16"): 2107083264 + 68712448,
+                 ("heat3d_m500_256c_bf16", "split_bf16"): None}
 # FP64 nominal of the part: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
