@@ -303,6 +303,12 @@ WORKLOADS = {
     "blob2d_m2000_512x512_f32": _wl("blob2d_m2000_512x512_f32", "blob", 2000, 512, 2, "f32",
                                     "fullweight", 16, 50, 1, s_gram=4, nblobs=8, seed=1,
                                     kappa=1e-5),
+    # the same blob recipe on 256^2 with the headline's sketch sizes (full weighting s = 8 onto
+    # 32^2, l = 1024; C-PWR on the 2x injection subsample, |I| = 16384): a 0.5 GB case for
+    # counter captures of the same kernels
+    "blob2d_m2000_256x256_f32": _wl("blob2d_m2000_256x256_f32", "blob", 2000, 256, 2, "f32",
+                                    "fullweight", 8, 50, 1, s_gram=2, nblobs=8, seed=1,
+                                    kappa=1e-5),
     # 500 snapshots of the 3-D heat field on 256^3, BF16, injection onto 8^3 (l = 512), k = 64
     "heat3d_m500_256c_bf16": _wl("heat3d_m500_256c_bf16", "heat", 500, 256, 3, "bf16",
                                  "inject", 32, 64, 0, K=12, seed=2),
