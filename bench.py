@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--phases", action="store_true", help="print a per-call time breakdown to stderr")
     p.add_argument("--no-compare", action="store_true", help="skip the plain FP32 GPU comparison run")
+    p.add_argument("--no-others", action="store_true",
+                   help="skip the other configurations' runs added to the default line")
     return p.parse_args()
 
 
@@ -235,7 +237,9 @@ def cpu_baseline(w, rtol, budget_s=25.0):
             break
     dt = (time.perf_counter() - t0) / reps
     return {"value": (ms / w.m) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{reps} run(s) on the first {ms} of {w.m} snapshots (k = {ks}), scaled by {ms}/{w.m}"}
+            "sample": f"{reps} run(s) on the first {ms} of {w.m} snapshots (k = {ks}), scaled by {ms}/{w.m}",
+            "estimate": "the full matrix's rate is extrapolated from the sample, linear in the snapshot "
+                        "count (the oracle's cost is dominated by its passes over the m x n rows)"}
 
 
 # ---------------------------------------------------------------------------
@@ -721,6 +725,37 @@ def spc_cpu_baseline(w, k, r_lift, c, taus):
             "sample": f"one run on the first {ms} of {w.m} snapshots (k = {ks}), scaled by {ms}/{w.m}"}
 
 
+# the other workloads, run after the headline (default workload, N = 1) as their own
+# bench.py processes and added to its line: the FP64 heat field, the precision form on the
+# BF16-stored 3-D heat field, the single-pass (SPC) path, the 256-matrix batch and the
+# learned proposal
+OTHER_WORKLOADS = [("heat2d_m200_64x64_f64", 20, 300), ("heat3d_m500_256c_bf16", 5, 400), (SPC_WORKLOAD, 5, 300),
+                   (BATCH_WORKLOAD, 3, 400), (LEARNED_WORKLOAD, 3, 400)]
+
+
+def run_others():
+    out = {}
+    for name, steps, limit in OTHER_WORKLOADS:
+        cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", name, "--steps", str(steps),
+               "--warmup", "3", "--no-cpu-baseline", "--no-others"]
+        t0 = time.time()
+        try:
+            p = subprocess.run(cmd, capture_output=True, text=True, timeout=limit)
+            lines = [x for x in p.stdout.splitlines() if x.startswith("{")]
+            if p.returncode != 0 or not lines:
+                out[name] = {"error": f"rc {p.returncode}: {p.stderr.strip().splitlines()[-1:] if p.stderr else ''}"}
+                continue
+            d = json.loads(lines[-1])
+            keep = {k: d[k] for k in ("value", "unit", "ms_per_step", "dtype", "config", "roofline", "e2e",
+                                      "plain_fp32_gpu", "per_matrix_loop", "learned_vs_adaptive", "result",
+                                      "items", "autotune", "gpu_launches", "clocks") if k in d}
+            keep["wall_s"] = round(time.time() - t0, 1)
+            out[name] = keep
+        except subprocess.TimeoutExpired:
+            out[name] = {"error": f"timed out after {limit} s"}
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -1007,6 +1042,15 @@ def run_ours(args, rank, world):
     stream.synchronize()
     barrier()
     e2e_ms = max_over_ranks(f0.elapsed_time(f1) / e2e_steps, world, f"cuda:{dev}")
+    # the bare pinned host -> device copy rate of the same buffer, for scale
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(cstream):
+        c0.record(cstream)
+        for _ in range(3):
+            dbuf[1].copy_(A_h, non_blocking=True)
+        c1.record(cstream)
+    cstream.synchronize()
+    h2d_gbs = 3 * h2d / (c0.elapsed_time(c1) * 1e-3) / 1e9
     del dbuf[1]
 
     # ---- the plain FP32 GPU method on the same matrix, for comparison ----
@@ -1044,7 +1088,8 @@ def run_ours(args, rank, world):
            "gpu_launches": int(launches),
            "e2e": {"value": job_throughput(world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms, "steps": e2e_steps,
-                   "overlap": "H2D of step i+1 on a copy stream during step i (two device buffers)"},
+                   "overlap": "H2D of step i+1 on a copy stream during step i (two device buffers)",
+                   "h2d_copy_gbs": h2d_gbs},
            "result": {"err_est_svd": s.err_est, "r": s.r, "err_est_id": d.err_est},
            "phases_ms": phases,
            "other_arrangement_ms_per_step": other_ms}
@@ -1055,6 +1100,8 @@ def run_ours(args, rank, world):
         out["plain_fp32_gpu"] = plain
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(w, rtol)
+    if not args.no_others and world == 1 and args.workload == "blob2d_m2000_512x512_f32":
+        out["other_workloads"] = run_others()
     print(json.dumps(out), flush=True)
 
 
