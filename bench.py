@@ -60,6 +60,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--phases", action="store_true", help="print a per-call time breakdown to stderr")
     p.add_argument("--no-compare", action="store_true", help="skip the plain FP32 GPU comparison run")
+    p.add_argument("--split", choices=["none", "columns"], default="none",
+                   help="columns: one matrix split by column slabs over the ranks (NCCL sums; strong scaling)")
+    p.add_argument("--virtual-ranks", type=int, default=1,
+                   help="with --split columns on one GPU: this many ranks, one context each, on that GPU")
     p.add_argument("--no-others", action="store_true",
                    help="skip the other configurations' runs added to the default line")
     return p.parse_args()
@@ -756,6 +760,108 @@ def run_others():
     return out
 
 
+def run_split_bench(args, rank, world):
+    """One matrix split by column slabs (whole coarse cells of the slowest
+    axis) over the ranks: each rank touches and projects only its own
+    columns; the sketch and subsample columns and the r x r Gram are summed
+    over the ranks (NCCL all-reduce), C-PWR, the range basis and the row ID
+    run on every rank.  Total work is fixed as N grows (strong scaling).  On
+    one GPU, --virtual-ranks V runs V ranks there (one context each, sums on
+    the device): the split's own overhead, not a speed-up."""
+    import torch
+    import synth
+    from paper_2105_01271_gb300 import binding, shard
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    w, rtol = workload_params(args.workload)
+    if args.rtol is not None:
+        rtol = args.rtol
+    prec_map = {"fp64": binding.LRS_PREC_FP64, "fp32": binding.LRS_PREC_FP32,
+                "split_bf16": binding.LRS_PREC_SPLIT_BF16, "bf16x3": binding.LRS_PREC_BF16X3}
+    prec_name = args.prec if args.prec != "auto" else ("fp64" if w.dtype == "f64" else "split_bf16")
+    prec = prec_map[prec_name]
+    P = world if world > 1 else max(1, args.virtual_ranks)
+    gram = w.gram if w.q > 0 else None
+    slabs = shard.plan_slabs(w.grid, gram, P)
+    mine = [slabs[rank]] if world > 1 else slabs
+    A_np = synth.make_workload(w)                       # the one matrix; each rank keeps its columns
+    tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.int16}[w.dtype]
+    hosts, local = [], []
+    stream = torch.cuda.current_stream()
+    for sl in mine:
+        blk = np.ascontiguousarray(A_np[:, sl.cols[0]:sl.cols[1]])
+        h = torch.from_numpy(blk.view(np.int16) if w.dtype == "bf16" else blk).pin_memory()
+        Ad = torch.empty(h.shape, dtype=tdt, device=f"cuda:{dev}")
+        Ad.copy_(h)
+        hosts.append(h)
+        local.append((shard.DeviceOps(binding.load(dev, stream)), Ad, sl))
+    del A_np
+    comm = shard.DistComm() if world > 1 else shard.LocalComm()
+    cs = shard.ColumnSplit(local, comm, w.m, w.dtype, w.grid, gram, w.q, w.k, rtol, prec)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        res = cs.step()
+    torch.cuda.synchronize(dev)
+    clk = clocks_start(dev)
+    skip = clocks_mark(clk)
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = sum(op.ctx.launches for op, _, _ in local)
+    e0.record(stream)
+    for _ in range(args.steps):
+        res = cs.step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    launches = sum(op.ctx.launches for op, _, _ in local) - launches0
+    clocks = clocks_stop(clk, skip)
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, f"cuda:{dev}")
+    # end to end: each step copies the ranks' slabs in from pinned host memory
+    # and U, S, the slab's V, J, P out, inside the timed region
+    h2d = sum(h.numel() * h.element_size() for h in hosts)
+    x0 = res[0]
+    outs = [(x.U, x.S, x.V, x.J, x.P) for x in res]
+    d2h = sum(t.numel() * t.element_size() for o in outs for t in o)
+    host_outs = [[torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in o] for o in outs]
+    e2e_steps = max(2, min(args.steps, 5))
+    barrier()
+    torch.cuda.synchronize(dev)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        for (_, Ad, _), h in zip(local, hosts):
+            Ad.copy_(h, non_blocking=True)
+        res = cs.step()
+        for x, ho in zip(res, host_outs):
+            for t, hh in zip((x.U, x.S, x.V, x.J, x.P), ho):
+                hh.copy_(t, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1) / e2e_steps, world, f"cuda:{dev}")
+    if rank != 0:
+        return
+    cfg = cfg_dict(w, rtol, prec_name)
+    cfg.update({"split": "columns", "ranks": P, "virtual_ranks_on_one_gpu": world == 1 and P > 1,
+                "slab_axis_extent": [sl.z1 - sl.z0 for sl in slabs], "factor": "gram" if x0.mode == 0 else "r"})
+    out = {"metric": METRIC, "value": 1e3 / ms, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+           "vs_baseline": None, "dtype": w.dtype if prec != binding.LRS_PREC_FP64 else "f64",
+           "data": "synthetic", "config": cfg, "clocks": clocks, "gpu_launches": int(launches),
+           "e2e": {"value": 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                   "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms, "steps": e2e_steps},
+           "result": {"err_est_svd": x0.err_svd, "r": x0.r, "err_est_id": x0.err_id},
+           "roofline": None}
+    print(json.dumps(out), flush=True)
+
+
 def run_ours(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -1114,6 +1220,8 @@ def main():
         dist.init_process_group("nccl")
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.split == "columns":
+        run_split_bench(args, rank, world)
     elif args.workload == BATCH_WORKLOAD:
         run_batch_bench(args, rank, world)
     elif args.workload == SPC_WORKLOAD:

@@ -217,6 +217,103 @@ lrs_status lrs_id_k(lrs_ctx* ctx, const double* Ysk, int64_t m, int64_t l, int64
                     int32_t* J, double* P, int64_t ldp, double* err_est);
 
 /*
+ * Column split of one matrix over several devices (data parallel over
+ * slabs of A_f's columns).  The sketch A_f D and the subsample A_f(:, I)
+ * (Sec. 2, Alg. 7) act on each coarse cell's own fine points, and Alg. 2's
+ * B = Q^T A_f and B B^T are sums over column slabs, so a device that holds
+ * the columns of whole coarse cells needs no other device's columns.  The
+ * calls below are the per-device steps; the caller runs the two exchanges
+ * between them (sums over devices, e.g. NCCL all-reduce):
+ *   1. lrs_touch on the device's slab, into its columns of a zero-filled
+ *      m x l sketch Y and m x |I| subsample W            -> sum Y, W (exact:
+ *      the devices' columns are disjoint)
+ *   2. lrs_power_pass_from(Y, W) -> G0, G (the same on every device)
+ *   3. Q = G (q > 0), else lrs_range_find(G) (the same on every device)
+ *   4. lrs_apass_slab: B_p = Q^T A_p for the slab's columns, ||A_p||_F^2
+ *   5. lrs_slab_factor: F_p with F_p F_p^T = B_p B_p^T    -> sum the r x r
+ *      Grams (LRS_FACTOR_GRAM), or place the F_p side by side in a
+ *      zero-filled r x (P r) matrix and sum (LRS_FACTOR_R); sum the fro2
+ *   6. lrs_svd_from_factor: U, S (the same on every device) and V_p, the
+ *      slab's rows of V
+ *   7. lrs_id_k(G0): J, P (the same on every device)
+ * A slab is a range of the slowest axis (y in 2-D, z in 3-D) whose ends are
+ * multiples of both grids' s on that axis; with full weighting that s must
+ * be >= 3 (the 3-point stencil then stays inside its cell).  The slab's
+ * grids are the full grids with that axis cut to the slab; its dof, coarse
+ * and subsample indices are then contiguous ranges of the full ones.
+ */
+#define LRS_FACTOR_GRAM 0   /* F = B B^T (r x r): FP32 B, r <= 128 */
+#define LRS_FACTOR_R 1      /* F = R^T (r x r), R^T R = B B^T: any B with n >= r */
+
+/*
+ * lrs_touch -- the touch of A_f alone (the first step of lrs_power_pass):
+ * the sketch Y = A_f D (m x l FP64, row stride ldy) and, when gram is not
+ * NULL, the subsample W = A_f(:, I) (m x |I|, row stride ldw) at the
+ * injection points of `gram`.  W's type follows prec: FP32 for
+ * LRS_PREC_SPLIT_BF16 and LRS_PREC_BF16X3 (exact: A_f's values), FP64
+ * otherwise.  Asynchronous (no host read-back).
+ * EINVAL as lrs_sketch, and gram's n differing from sketch's.
+ */
+lrs_status lrs_touch(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t lda, const lrs_grid* sketch,
+                     const lrs_grid* gram, int32_t prec, double* Y, int64_t ldy, void* W, int64_t ldw);
+
+/*
+ * lrs_power_pass_from -- lrs_power_pass2 from a given sketch and subsample:
+ * Y (m x l FP64, row stride ldy) and W (m x |I| = nI, row stride ldw, typed
+ * as lrs_touch writes it for prec).  Same outputs (G0, *g0_cols; G,
+ * *g_cols) and the same bits as lrs_power_pass2 on the A_f they came from.
+ * W may be NULL when q = 0.  Synchronises.
+ */
+lrs_status lrs_power_pass_from(lrs_ctx* ctx, const double* Y, int64_t ldy, const void* W, int64_t ldw, int64_t m,
+                               int64_t l, int64_t nI, int32_t q, double rtol, int32_t prec, double* G0,
+                               int64_t ldg0, int64_t* g0_cols, double* G, int64_t ldg, int64_t* g_cols);
+
+/*
+ * lrs_apass_slab -- B = Q^T A (Alg. 2; the A-pass of lrs_svd_k) for the
+ * columns a device holds, and ||A||_F^2 of them into fro2 (device, one
+ * double).  A m x n in dtype (row stride lda); Q m x r FP64 (row stride
+ * ldq); B r x n, row stride n, FP64 when prec == LRS_PREC_FP64, else FP32.
+ * Asynchronous.
+ */
+lrs_status lrs_apass_slab(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                          const double* Q, int64_t ldq, int64_t r, int32_t prec, void* B, double* fro2);
+
+/*
+ * lrs_slab_factor -- F (r x r FP64, row stride ldf) with F F^T = B B^T for
+ * B from lrs_apass_slab (r x n, row stride n, typed by prec).
+ *   LRS_FACTOR_GRAM  F = B B^T by the double-float Gram of lrs_svd_k
+ *                    (FP32 B, r <= 128); the devices' F add up to the full
+ *                    Gram.
+ *   LRS_FACTOR_R     F = R^T, R the R factor of B^T (pivoted QR for FP64 B,
+ *                    Householder TSQR otherwise; n >= r); [F_1 ... F_P]
+ *                    then has the full Gram as its Gram, without squaring
+ *                    B's condition number.
+ * Asynchronous except for the pivoted QR's rank read-back.
+ */
+lrs_status lrs_slab_factor(lrs_ctx* ctx, const void* B, int64_t r, int64_t n, int32_t prec, int32_t mode, double* F,
+                           int64_t ldf);
+
+/*
+ * lrs_svd_from_factor -- the rest of lrs_svd_k from the summed factor:
+ *   LRS_FACTOR_GRAM  F r x r (nf = r): pivoted FP64 Cholesky, then the FP64
+ *                    one-sided Jacobi on the rows of its factor.  LRS_ERANK
+ *                    with *err_est = -1 (nothing written) when the Cholesky
+ *                    stops early: the caller then takes LRS_FACTOR_R.
+ *   LRS_FACTOR_R     F r x nf (nf >= r, e.g. [F_1 ... F_P]): the R factor of
+ *                    F^T, then the FP64 Jacobi on its columns.
+ * U = Q U_B(:,1:k) (m x k, row stride ldu), S (k), and V = B^T U_B S^-1 for
+ * this device's B (r x n, row stride n, typed by prec): the device's rows of
+ * V (n x k, row stride ldv; FP64 when prec == LRS_PREC_FP64, else FP32).
+ * fro2 (device): ||A_f||_F^2 of the WHOLE matrix, for err_est (host, may be
+ * NULL) as lrs_svd_k.  Signs as lrs_svd_k.  Returns LRS_ERANK when r < k.
+ * Synchronises.
+ */
+lrs_status lrs_svd_from_factor(lrs_ctx* ctx, const double* F, int64_t ldf, int64_t nf, int32_t mode,
+                               const double* Q, int64_t ldq, int64_t m, int64_t r, int32_t k, int32_t prec,
+                               const void* B, int64_t n, const double* fro2, double* U, int64_t ldu, double* S,
+                               void* V, int64_t ldv, double* err_est);
+
+/*
  * lrs_sketch_svd -- the leading r singular triplets of a sketch Y = A_c
  * (m x l FP64), the SVD step of SPC-ID (Alg. 5: U_c, S_c, V_c of A_c).
  *   The pivoted QR of lrs_range_find (tolerance rtol), stopped after at most

@@ -19,6 +19,7 @@ LRS_OK, LRS_EINVAL, LRS_ENOMEM, LRS_ECUDA, LRS_ERANK, LRS_ETIMEOUT = range(6)
 LRS_F64, LRS_F32, LRS_BF16 = 0, 1, 2
 LRS_INJECT, LRS_FULLWEIGHT, LRS_BLOCKAVG = 0, 1, 2
 LRS_PREC_FP64, LRS_PREC_FP32, LRS_PREC_SPLIT_BF16, LRS_PREC_BF16X3 = 0, 1, 2, 3
+LRS_FACTOR_GRAM, LRS_FACTOR_R = 0, 1
 
 KIND = {"inject": LRS_INJECT, "fullweight": LRS_FULLWEIGHT, "blockavg": LRS_BLOCKAVG}
 DTYPE = {"f64": LRS_F64, "f32": LRS_F32, "bf16": LRS_BF16}
@@ -84,6 +85,20 @@ _SIG = {
                                   C.POINTER(lrs_grid), C.POINTER(lrs_grid), C.c_int32, C.c_double,
                                   C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                   C.POINTER(C.c_int64), C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
+    "lrs_touch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.POINTER(lrs_grid),
+                            C.POINTER(lrs_grid), C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64]),
+    "lrs_power_pass_from": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int64,
+                                      C.c_int64, C.c_int64, C.c_int32, C.c_double, C.c_int32, C.c_void_p,
+                                      C.c_int64, C.POINTER(C.c_int64), C.c_void_p, C.c_int64,
+                                      C.POINTER(C.c_int64)]),
+    "lrs_apass_slab": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_int64,
+                                 C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]),
+    "lrs_slab_factor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_int32,
+                                  C.c_void_p, C.c_int64]),
+    "lrs_svd_from_factor": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p,
+                                      C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_void_p,
+                                      C.c_int64, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                      C.c_int64, C.POINTER(C.c_double)]),
     "lrs_range_find": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64,
                                  C.c_double, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "lrs_range_find_diag": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64,
@@ -243,6 +258,34 @@ class Context:
                                              q, rtol, prec, _ptr(Y), ldy, _ptr(G0), ldg0, C.byref(g0),
                                              _ptr(G), ldg, C.byref(gc)))
         return g0.value, gc.value
+
+    def touch(self, A, dtype, m, lda, sketch: lrs_grid, gram, prec, Y, ldy, W, ldw):
+        gp = C.byref(gram) if gram is not None else None
+        return self._check(self.lib.lrs_touch(self.h, _ptr(A), dtype, m, lda, C.byref(sketch), gp, prec,
+                                              _ptr(Y), ldy, _ptr(W), ldw))
+
+    def power_pass_from(self, Y, ldy, W, ldw, m, l, nI, q, rtol, prec, G0, ldg0, G, ldg):
+        """Returns (columns of G0, columns of G)."""
+        gc = C.c_int64(0)
+        g0 = C.c_int64(0)
+        self._check(self.lib.lrs_power_pass_from(self.h, _ptr(Y), ldy, _ptr(W), ldw, m, l, nI, q, rtol, prec,
+                                                 _ptr(G0), ldg0, C.byref(g0), _ptr(G), ldg, C.byref(gc)))
+        return g0.value, gc.value
+
+    def apass_slab(self, A, dtype, m, n, lda, Q, ldq, r, prec, B, fro2):
+        return self._check(self.lib.lrs_apass_slab(self.h, _ptr(A), dtype, m, n, lda, _ptr(Q), ldq, r, prec,
+                                                   _ptr(B), _ptr(fro2)))
+
+    def slab_factor(self, B, r, n, prec, mode, F, ldf):
+        return self._check(self.lib.lrs_slab_factor(self.h, _ptr(B), r, n, prec, mode, _ptr(F), ldf))
+
+    def svd_from_factor(self, F, ldf, nf, mode, Q, ldq, m, r, k, prec, B, n, fro2, U, ldu, S, V, ldv):
+        """Returns (err_est, status); LRS_ERANK is returned, not raised."""
+        err = C.c_double(0.0)
+        st = self._check(self.lib.lrs_svd_from_factor(self.h, _ptr(F), ldf, nf, mode, _ptr(Q), ldq, m, r, k, prec,
+                                                      _ptr(B), n, _ptr(fro2), _ptr(U), ldu, _ptr(S), _ptr(V), ldv,
+                                                      C.byref(err)), allow_rank=True)
+        return err.value, st
 
     def range_find(self, G, m, l, ldg, rtol, Q, ldq) -> int:
         r = C.c_int64(0)

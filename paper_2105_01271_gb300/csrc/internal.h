@@ -63,7 +63,7 @@ lrs_status launch_gather(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int
                          const GridDev& g, double* W, int64_t ldw);
 // *out = sum of part[0..np) (device, one block, fixed order)
 lrs_status launch_sum(lrs_ctx* ctx, const double* part, int np, double* out);
-// W (m x |I|) and W^T (|I| x m), FP32, from one pass over A
+// W (m x |I|) and W^T (|I| x m), FP32, from one pass over A (WT NULL: W alone)
 lrs_status launch_gather32_both(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int64_t lda,
                                 const GridDev& g, float* W, int64_t ldw, float* WT, int64_t ldwt);
 // sum of squares of A (m x n), FP64, into *out (device)
@@ -218,6 +218,9 @@ lrs_status launch_jacobi_rows(lrs_ctx* ctx, const double* R, int64_t r, int64_t 
 // transposed copy of a row-major FP64 matrix: dst (cols x rows) = src^T
 lrs_status launch_transpose(lrs_ctx* ctx, const double* src, int64_t rows, int64_t cols,
                             int64_t lds, double* dst, int64_t ldd);
+// the same for FP32
+lrs_status launch_transpose32(lrs_ctx* ctx, const float* src, int64_t rows, int64_t cols, int64_t lds,
+                              float* dst, int64_t ldd);
 // two-block cooperative launch whose barrier wait runs out (lrs_selftest_barrier_timeout)
 lrs_status launch_barrier_selftest(lrs_ctx* ctx, int64_t spin_limit);
 // FP64 -> FP32 copy (round to nearest)

@@ -577,6 +577,37 @@ static lrs_status touch(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, i
   return launch_transpose(ctx, (const double*)*W, m, nI, nI, (double*)*WT, m);
 }
 
+// Both C-PWR iterates from the touched Y, W, W^T (lrs_power_pass2 after its
+// touch; lrs_power_pass_from).  The SVD's re-orthonormalised loop; its
+// factors also give the ID's iterate (the same result as lrs_power_pass with
+// reorth = 0).  FP64 products, or a chain wider than 128 directions: the ID's
+// loop runs on its own.  The loop buffers are reused; W and W^T stay below
+// the mark.
+static lrs_status pass2_from(lrs_ctx* ctx, const void* W, const void* WT, int64_t m, int64_t l, int64_t nI,
+                             const double* Y, int64_t ldy, int32_t q, double rtol, int32_t prec, double* G0,
+                             int64_t ldg0, int64_t* g0_cols, double* G, int64_t ldg, int64_t* g_cols) {
+  if (q == 0) {
+    LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(G0, ldg0 * 8, Y, ldy * 8, l * 8, m, cudaMemcpyDeviceToDevice, ctx->stream));
+    LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(G, ldg * 8, Y, ldy * 8, l * 8, m, cudaMemcpyDeviceToDevice, ctx->stream));
+    *g_cols = l;
+    *g0_cols = l;
+    return LRS_OK;
+  }
+  const size_t mark = ctx->ws_top;
+  int64_t gid = 0;
+  lrs_status st = cpwr_loop(ctx, W, WT, m, l, nI, Y, ldy, q, 1, rtol, prec, G, ldg, g_cols,
+                            prec != LRS_PREC_FP64 ? G0 : nullptr, ldg0, &gid);
+  if (st) return st;
+  ctx->ws_top = mark;
+  *g0_cols = gid;
+  if (gid == 0) {
+    st = cpwr_loop(ctx, W, WT, m, l, nI, Y, ldy, q, 0, rtol, prec, G0, ldg0, g0_cols);
+    if (st) return st;
+  }
+  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return LRS_OK;
+}
+
 }  // namespace lrs
 
 extern "C" {
@@ -646,30 +677,63 @@ lrs_status lrs_power_pass2(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m
   void *W = nullptr, *WT = nullptr;
   st = touch(ctx, A, dtype, m, lda, gs, gg, q, prec, Y, ldy, &W, &WT);
   if (st) return st;
-  if (q == 0) {
-    LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(G0, ldg0 * 8, Y, ldy * 8, l * 8, m, cudaMemcpyDeviceToDevice, ctx->stream));
-    LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(G, ldg * 8, Y, ldy * 8, l * 8, m, cudaMemcpyDeviceToDevice, ctx->stream));
-    *g_cols = l;
-    *g0_cols = l;
-    return LRS_OK;
-  }
-  // The SVD's re-orthonormalised loop; its factors also give the ID's
-  // iterate (the same result as lrs_power_pass with reorth = 0).  FP64
-  // products, or a chain wider than 128 directions: the ID's loop runs on its
-  // own.  The loop buffers are reused, W and W^T stay below the mark.
-  const size_t mark = ctx->ws_top;
-  int64_t gid = 0;
-  st = cpwr_loop(ctx, W, WT, m, l, nI, Y, ldy, q, 1, rtol, prec, G, ldg, g_cols,
-                 prec != LRS_PREC_FP64 ? G0 : nullptr, ldg0, &gid);
+  return lrs::pass2_from(ctx, W, WT, m, l, nI, Y, ldy, q, rtol, prec, G0, ldg0, g0_cols, G, ldg, g_cols);
+}
+
+lrs_status lrs_touch(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t lda, const lrs_grid* sketch,
+                     const lrs_grid* gram, int32_t prec, double* Y, int64_t ldy, void* W, int64_t ldw) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  GridDev gs, gg;
+  lrs_status st = power_pass_check(ctx, A, dtype, m, lda, sketch, gram, gram ? 1 : 0, 0.0, prec, &gs, &gg);
   if (st) return st;
-  ctx->ws_top = mark;
-  *g0_cols = gid;
-  if (gid == 0) {
-    st = cpwr_loop(ctx, W, WT, m, l, nI, Y, ldy, q, 0, rtol, prec, G0, ldg0, g0_cols);
+  if (!Y || (gram && !W)) return lrs_fail(ctx, LRS_EINVAL, "touch: NULL pointer");
+  if (ldy < gs.l || (gram && ldw < gg.l)) return lrs_fail(ctx, LRS_EINVAL, "touch: strides too small");
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  st = launch_sketch(ctx, A, dtype, m, lda, gs, Y, ldy);
+  if (st || !gram) return st;
+  if (prec >= LRS_PREC_SPLIT_BF16)
+    return launch_gather32_both(ctx, A, dtype, m, lda, gg, (float*)W, ldw, nullptr, 0);
+  return launch_gather(ctx, A, dtype, m, lda, gg, (double*)W, ldw);
+}
+
+lrs_status lrs_power_pass_from(lrs_ctx* ctx, const double* Y, int64_t ldy, const void* W, int64_t ldw, int64_t m,
+                               int64_t l, int64_t nI, int32_t q, double rtol, int32_t prec, double* G0,
+                               int64_t ldg0, int64_t* g0_cols, double* G, int64_t ldg, int64_t* g_cols) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  if (!Y || !G || !G0 || !g_cols || !g0_cols || (q > 0 && !W))
+    return lrs_fail(ctx, LRS_EINVAL, "power_pass_from: NULL pointer");
+  if (!prec_ok(prec)) return lrs_fail(ctx, LRS_EINVAL, "power_pass_from: bad prec");
+  if (m < 1 || l < 1 || q < 0 || q > 16 || (q > 0 && nI < 1))
+    return lrs_fail(ctx, LRS_EINVAL, "power_pass_from: m=%lld l=%lld |I|=%lld q=%d", (long long)m, (long long)l,
+                    (long long)nI, q);
+  if (!(rtol >= 0.0) || rtol >= 1.0) return lrs_fail(ctx, LRS_EINVAL, "power_pass_from: rtol=%g not in [0,1)", rtol);
+  if (ldy < l || ldg < l || ldg0 < l || (q > 0 && ldw < nI))
+    return lrs_fail(ctx, LRS_EINVAL, "power_pass_from: strides too small");
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  lrs_status st = ws_reserve(ctx, q > 0 ? cpwr_ws(ctx, m, l, nI, prec) : 0);
+  if (st) return st;
+  const void* Wc = W;
+  void* WT = nullptr;
+  if (q > 0) {
+    // the loop takes W with row stride |I| and its transpose
+    const bool tc = prec >= LRS_PREC_SPLIT_BF16;
+    const size_t wsz = tc ? 4 : 8;
+    if (ldw != nI) {
+      void* Wd = ws_alloc(ctx, wsz * (size_t)(m * nI));
+      if (!Wd) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (power_pass_from)");
+      LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(Wd, nI * wsz, W, ldw * wsz, nI * wsz, m, cudaMemcpyDeviceToDevice,
+                                          ctx->stream));
+      Wc = Wd;
+    }
+    WT = ws_alloc(ctx, wsz * (size_t)(m * nI));
+    if (!WT) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (power_pass_from)");
+    st = tc ? launch_transpose32(ctx, (const float*)Wc, m, nI, nI, (float*)WT, m)
+            : launch_transpose(ctx, (const double*)Wc, m, nI, nI, (double*)WT, m);
     if (st) return st;
   }
-  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-  return LRS_OK;
+  return lrs::pass2_from(ctx, Wc, WT, m, l, nI, Y, ldy, q, rtol, prec, G0, ldg0, g0_cols, G, ldg, g_cols);
 }
 
 }  // extern "C"
@@ -709,6 +773,54 @@ static lrs_status r_of_bt_cpqr(lrs_ctx* ctx, const double* B, int64_t r, int64_t
   return LRS_OK;
 }
 
+// The rest of the SVD once B's right singular structure is known: Vr (r x r,
+// row-major, columns = U_B) and sv (r, descending).  U = Q U_B(:, :kk) with
+// the sign convention, S, V = B^T U_B(:, :kk) S^-1 for B r x n (row stride n;
+// FP64 when prec is FP64, else FP32), err_est from the tail of sv and fro2.
+static lrs_status svd_finish(lrs_ctx* ctx, double* Vr, const double* sv, int64_t r, int64_t kk, const double* Q,
+                             int64_t ldq, int64_t m, const void* B, int64_t n, int32_t prec, double* U, int64_t ldu,
+                             double* S, void* V, int64_t ldv, const double* fro2, double* err_est) {
+  const int f64 = prec == LRS_PREC_FP64;
+  double* Wk = (double*)ws_alloc(ctx, 8 * (size_t)(r * kk));
+  double* sgn = (double*)ws_alloc(ctx, 8 * (size_t)kk);
+  if (!Wk || !sgn) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd)");
+  // U = Q Vr(:, :kk): m x kk x r in FP64, 16 x 16 output tiles over the SMs
+  lrs_status st = spc_small_gemm(ctx, m, kk, r, Q, ldq, 1, Vr, r, 1, nullptr, nullptr, U, ldu);
+  if (st) return st;
+  // sign convention on U, then V = B^T Vr_k diag(sign) S_k^{-1} carries the same signs
+  st = launch_sign_fix(ctx, U, m, kk, ldu, sgn);
+  if (st) return st;
+  st = launch_scale_cols(ctx, Vr, r, r, sv, sgn, kk, Wk, kk);
+  if (st) return st;
+  if (prec >= LRS_PREC_SPLIT_BF16 && !f64) {
+    // V^T (kk x n) = Wk^T B on the tensor cores (B streamed once, V stored
+    // n-major), three BF16 pieces per operand: V carries the reconstruction,
+    // so it keeps FP32-level accuracy whatever the A-pass precision
+    GemmArgs gv{kk, n, r, Wk, LRS_F64, kk, B, LRS_F32, n, V, 0, 1, ldv, 1.0};
+    st = apass_eligible(gv, LRS_PREC_BF16X3) ? launch_gemm_tc(ctx, gv, LRS_PREC_BF16X3)
+                                             : gemm(ctx, LRS_PREC_FP32, n, kk, r, B, LRS_F32, n, Wk, LRS_F64, kk,
+                                                    V, 0, 0, ldv);
+  } else {
+    st = gemm(ctx, f64 ? LRS_PREC_FP64 : LRS_PREC_FP32, n, kk, r, B, f64 ? LRS_F64 : LRS_F32, n, Wk,
+              LRS_F64, kk, V, f64, 0, ldv);
+  }
+  if (st) return st;
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(S, sv, 8 * (size_t)kk, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (err_est) {
+    double* h = (double*)ctx->host_scratch;
+    if (fro2) LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h, fro2, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<double> s_h((size_t)r);
+    LRS_CUDA_TRY(ctx, cudaMemcpyAsync(s_h.data(), sv, 8 * (size_t)r, cudaMemcpyDeviceToHost, ctx->stream));
+    LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    // energy of B beyond rank k, summed smallest first
+    double tail = 0.0;
+    for (int64_t i = r - 1; i >= kk; --i) tail += s_h[(size_t)i] * s_h[(size_t)i];
+    const double f = fro2 ? h[0] : 0.0;
+    *err_est = f > 0.0 ? sqrt(tail / f) : 0.0;
+  }
+  return LRS_OK;
+}
+
 size_t svd_from_b_ws(int64_t r, int64_t n, int64_t m, int64_t kk, int32_t prec, int num_sms) {
   const size_t bsz = prec == LRS_PREC_FP64 ? 8 : 4;
   size_t need = tsqr_ws(r, n, bsz) + r_of_bt_gram_ws(r, num_sms);
@@ -731,10 +843,8 @@ lrs_status svd_from_b(lrs_ctx* ctx, const void* B, int64_t r, int64_t n, const d
   double* Rm = (double*)ws_alloc(ctx, 8 * (size_t)(r * r));
   double* Vr = (double*)ws_alloc(ctx, 8 * (size_t)(r * r));
   double* sv = (double*)ws_alloc(ctx, 8 * (size_t)r);
-  double* Wk = (double*)ws_alloc(ctx, 8 * (size_t)(r * kk));
   double* QT = (double*)ws_alloc(ctx, 8 * (size_t)(m * r));
-  double* sgn = (double*)ws_alloc(ctx, 8 * (size_t)kk);
-  if (!Rm || !Vr || !sv || !Wk || !QT || !sgn) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd)");
+  if (!Rm || !Vr || !sv || !QT) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd)");
   // SVD(B), all in FP64 once B exists.  FP32 B: R from the double-float Gram
   // and a PIVOTED FP64 Cholesky (P^T B B^T P = R^T R), then the FP64
   // one-sided Jacobi on the rows of R across a thread-block cluster, U_B =
@@ -783,41 +893,35 @@ lrs_status svd_from_b(lrs_ctx* ctx, const void* B, int64_t r, int64_t n, const d
     st = launch_jacobi(ctx, Rm, r, Vr, sv, 1);
   }
   if (st) return st;
-  // U = Q Vr(:, :kk): m x kk x r in FP64, 16 x 16 output tiles over the SMs
   (void)QT;
-  st = spc_small_gemm(ctx, m, kk, r, Q, ldq, 1, Vr, r, 1, nullptr, nullptr, U, ldu);
-  if (st) return st;
-  // sign convention on U, then V = B^T Vr_k diag(sign) S_k^{-1} carries the same signs
-  st = launch_sign_fix(ctx, U, m, kk, ldu, sgn);
-  if (st) return st;
-  st = launch_scale_cols(ctx, Vr, r, r, sv, sgn, kk, Wk, kk);
-  if (st) return st;
-  if (prec >= LRS_PREC_SPLIT_BF16 && !f64) {
-    // V^T (kk x n) = Wk^T B on the tensor cores (B streamed once, V stored
-    // n-major), three BF16 pieces per operand: V carries the reconstruction,
-    // so it keeps FP32-level accuracy whatever the A-pass precision
-    GemmArgs gv{kk, n, r, Wk, LRS_F64, kk, B, LRS_F32, n, V, 0, 1, ldv, 1.0};
-    st = apass_eligible(gv, LRS_PREC_BF16X3) ? launch_gemm_tc(ctx, gv, LRS_PREC_BF16X3)
-                                             : gemm(ctx, LRS_PREC_FP32, n, kk, r, B, LRS_F32, n, Wk, LRS_F64, kk,
-                                                    V, 0, 0, ldv);
+  return svd_finish(ctx, Vr, sv, r, kk, Q, ldq, m, B, n, prec, U, ldu, S, V, ldv, fro2, err_est);
+}
+
+// (a4) B = Q^T A_f (r x n, row stride n; FP64 when prec is FP64, else FP32)
+// -- the one full read of A_f -- and ||A_f||_F^2 into fro2 (device; fused
+// into the tensor-core A-pass, a separate pass otherwise)
+static size_t apass_b_ws(lrs_ctx* ctx, int64_t m, int64_t n, int64_t r, int32_t prec) {
+  return prec >= LRS_PREC_SPLIT_BF16
+             ? gemm_tc_workspace(r, m, prec) + gemm_tc_splitk_workspace(r, n, m, ctx->num_sms) + 4096
+             : 0;
+}
+
+static lrs_status apass_b(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                          const double* Q, int64_t ldq, int64_t r, int32_t prec, void* B, double* fro2) {
+  const int f64 = prec == LRS_PREC_FP64;
+  GemmArgs ga{r, n, m, Q, LRS_F64, ldq, A, dtype, lda, B, f64, 0, n, 1.0};
+  const size_t mark = ctx->ws_top;
+  lrs_status st;
+  if (prec >= LRS_PREC_SPLIT_BF16 && (r <= 128 || apass_eligible(ga, prec))) {
+    st = launch_gemm_tc(ctx, ga, prec, fro2);
+    if (st) return st;
   } else {
-    st = gemm(ctx, f64 ? LRS_PREC_FP64 : LRS_PREC_FP32, n, kk, r, B, f64 ? LRS_F64 : LRS_F32, n, Wk,
-              LRS_F64, kk, V, f64, 0, ldv);
+    st = gemm(ctx, prec, r, n, m, Q, LRS_F64, ldq, A, dtype, lda, B, f64, 0, n);
+    if (st) return st;
+    st = launch_fro2(ctx, A, dtype, m, n, lda, fro2);
+    if (st) return st;
   }
-  if (st) return st;
-  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(S, sv, 8 * (size_t)kk, cudaMemcpyDeviceToDevice, ctx->stream));
-  if (err_est) {
-    double* h = (double*)ctx->host_scratch;
-    if (fro2) LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h, fro2, 8, cudaMemcpyDeviceToHost, ctx->stream));
-    std::vector<double> s_h((size_t)r);
-    LRS_CUDA_TRY(ctx, cudaMemcpyAsync(s_h.data(), sv, 8 * (size_t)r, cudaMemcpyDeviceToHost, ctx->stream));
-    LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-    // energy of B beyond rank k, summed smallest first
-    double tail = 0.0;
-    for (int64_t i = r - 1; i >= kk; --i) tail += s_h[(size_t)i] * s_h[(size_t)i];
-    const double f = fro2 ? h[0] : 0.0;
-    *err_est = f > 0.0 ? sqrt(tail / f) : 0.0;
-  }
+  ctx->ws_top = mark;
   return LRS_OK;
 }
 
@@ -844,30 +948,175 @@ lrs_status lrs_svd_k(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int6
   LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   const int f64 = prec == LRS_PREC_FP64;
   const size_t bsz = f64 ? 8 : 4;
-  size_t need = align256(bsz * (size_t)(r * n)) + 256 + svd_from_b_ws(r, n, m, kk, prec, ctx->num_sms);
-  if (prec >= LRS_PREC_SPLIT_BF16)
-    need += gemm_tc_workspace(r, m, prec) + gemm_tc_splitk_workspace(r, n, m, ctx->num_sms) + 4096;
+  size_t need = align256(bsz * (size_t)(r * n)) + 256 + svd_from_b_ws(r, n, m, kk, prec, ctx->num_sms) +
+                lrs::apass_b_ws(ctx, m, n, r, prec);
   lrs_status st = ws_reserve(ctx, need);
   if (st) return st;
   void* B = ws_alloc(ctx, bsz * (size_t)(r * n));
   double* fro2 = (double*)ws_alloc(ctx, 8);
   if (!B || !fro2) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd_k)");
-  // (a4) B = Q^T A_f -- the one full read of A_f (||A_f||_F^2 fused on the tensor-core path)
-  GemmArgs ga{r, n, m, Q, LRS_F64, ldq, A, dtype, lda, B, f64, 0, n, 1.0};
-  const size_t mark = ctx->ws_top;
-  if (prec >= LRS_PREC_SPLIT_BF16 && (r <= 128 || apass_eligible(ga, prec))) {
-    st = launch_gemm_tc(ctx, ga, prec, fro2);
-    if (st) return st;
-  } else {
-    st = gemm(ctx, prec, r, n, m, Q, LRS_F64, ldq, A, dtype, lda, B, f64, 0, n);
-    if (st) return st;
-    st = launch_fro2(ctx, A, dtype, m, n, lda, fro2);
-    if (st) return st;
-  }
-  ctx->ws_top = mark;
+  st = lrs::apass_b(ctx, A, dtype, m, n, lda, Q, ldq, r, prec, B, fro2);
+  if (st) return st;
   st = svd_from_b(ctx, B, r, n, Q, ldq, m, k, prec, U, ldu, S, V, ldv, fro2, err_est);
   if (st) return st;
   return r < k ? lrs_fail(ctx, LRS_ERANK, "svd_k: rank r=%lld < k=%d", (long long)r, k) : LRS_OK;
+}
+
+lrs_status lrs_apass_slab(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, int64_t n, int64_t lda,
+                          const double* Q, int64_t ldq, int64_t r, int32_t prec, void* B, double* fro2) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  if (!A || !Q || !B || !fro2) return lrs_fail(ctx, LRS_EINVAL, "apass_slab: NULL pointer");
+  if (!dtype_ok(dtype) || !prec_ok(prec)) return lrs_fail(ctx, LRS_EINVAL, "apass_slab: bad dtype/prec");
+  if (m < 1 || n < 1 || r < 1 || r > m)
+    return lrs_fail(ctx, LRS_EINVAL, "apass_slab: m=%lld n=%lld r=%lld", (long long)m, (long long)n, (long long)r);
+  if (lda < n || ldq < r) return lrs_fail(ctx, LRS_EINVAL, "apass_slab: strides too small");
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  lrs_status st = ws_reserve(ctx, lrs::apass_b_ws(ctx, m, n, r, prec) + 256);
+  if (st) return st;
+  return lrs::apass_b(ctx, A, dtype, m, n, lda, Q, ldq, r, prec, B, fro2);
+}
+
+lrs_status lrs_slab_factor(lrs_ctx* ctx, const void* B, int64_t r, int64_t n, int32_t prec, int32_t mode, double* F,
+                           int64_t ldf) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  if (!B || !F) return lrs_fail(ctx, LRS_EINVAL, "slab_factor: NULL pointer");
+  if (!prec_ok(prec)) return lrs_fail(ctx, LRS_EINVAL, "slab_factor: bad prec");
+  if (r < 1 || n < 1 || ldf < r) return lrs_fail(ctx, LRS_EINVAL, "slab_factor: r=%lld n=%lld ldf=%lld",
+                                                 (long long)r, (long long)n, (long long)ldf);
+  const int f64 = prec == LRS_PREC_FP64;
+  if (mode == LRS_FACTOR_GRAM) {
+    if (f64 || r > 128) return lrs_fail(ctx, LRS_EINVAL, "slab_factor: the Gram form takes FP32 B with r <= 128");
+  } else if (mode == LRS_FACTOR_R) {
+    if (n < r) return lrs_fail(ctx, LRS_EINVAL, "slab_factor: the R form needs n=%lld >= r=%lld", (long long)n,
+                               (long long)r);
+  } else {
+    return lrs_fail(ctx, LRS_EINVAL, "slab_factor: mode %d", mode);
+  }
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  size_t need = 2 * align256(8 * (size_t)(r * r)) + 1024;
+  if (mode == LRS_FACTOR_GRAM) need += gram_df_ws(r, ctx->num_sms);
+  else need += tsqr_ws(r, n, f64 ? 8 : 4) + 2 * align256(8 * (size_t)(n * r)) + cpqr_ws(n, r, r) + 1024;
+  lrs_status st = ws_reserve(ctx, need);
+  if (st) return st;
+  double* Rm = (double*)ws_alloc(ctx, 8 * (size_t)(r * r));
+  if (!Rm) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (slab_factor)");
+  if (mode == LRS_FACTOR_GRAM) {
+    // F = B B^T, the double-float Gram of the SVD path, rounded to FP64
+    st = launch_gram_df(ctx, (const float*)B, r, n, n, ldf == r ? F : Rm);
+    if (st) return st;
+    if (ldf != r)
+      LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(F, ldf * 8, Rm, r * 8, r * 8, r, cudaMemcpyDeviceToDevice, ctx->stream));
+    return LRS_OK;
+  }
+  // F = R^T with R^T R = B B^T: the cooperative pivoted QR of B^T (FP64 B),
+  // else the Householder TSQR of the SVD path
+  st = LRS_ERANK;
+  if (f64 && r >= 24 && ctx->coop_ok) {
+    const size_t mark = ctx->ws_top;
+    st = r_of_bt_cpqr(ctx, (const double*)B, r, n, Rm);
+    ctx->ws_top = mark;
+    if (st != LRS_OK && st != LRS_ERANK) return st;
+  }
+  if (st == LRS_ERANK) st = launch_tsqr(ctx, B, f64, r, n, n, Rm);
+  if (st) return st;
+  return launch_transpose(ctx, Rm, r, r, r, F, ldf);
+}
+
+lrs_status lrs_svd_from_factor(lrs_ctx* ctx, const double* F, int64_t ldf, int64_t nf, int32_t mode,
+                               const double* Q, int64_t ldq, int64_t m, int64_t r, int32_t k, int32_t prec,
+                               const void* B, int64_t n, const double* fro2, double* U, int64_t ldu, double* S,
+                               void* V, int64_t ldv, double* err_est) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  if (!F || !Q || !B || !U || !S || !V) return lrs_fail(ctx, LRS_EINVAL, "svd_from_factor: NULL pointer");
+  if (!prec_ok(prec)) return lrs_fail(ctx, LRS_EINVAL, "svd_from_factor: bad prec");
+  if (m < 1 || n < 1 || r < 1 || k < 1 || r > m)
+    return lrs_fail(ctx, LRS_EINVAL, "svd_from_factor: m=%lld n=%lld r=%lld k=%d", (long long)m, (long long)n,
+                    (long long)r, k);
+  const int f64 = prec == LRS_PREC_FP64;
+  if (mode == LRS_FACTOR_GRAM) {
+    if (f64 || r > 128 || nf != r)
+      return lrs_fail(ctx, LRS_EINVAL, "svd_from_factor: the Gram form takes FP32 B, r <= 128 and nf == r");
+  } else if (mode == LRS_FACTOR_R) {
+    if (nf < r) return lrs_fail(ctx, LRS_EINVAL, "svd_from_factor: nf=%lld < r=%lld", (long long)nf, (long long)r);
+  } else {
+    return lrs_fail(ctx, LRS_EINVAL, "svd_from_factor: mode %d", mode);
+  }
+  const int64_t kk = k < r ? k : r;
+  if (ldf < nf || ldq < r || ldu < kk || ldv < kk) return lrs_fail(ctx, LRS_EINVAL, "svd_from_factor: strides too small");
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  size_t need = 4 * align256(8 * (size_t)(r * r)) + 2 * align256(8 * (size_t)r) + jacobi_ws(r, r) +
+                jacobi_rows_ws(r) + align256(8 * (size_t)(r * kk)) + 65536;
+  if (mode == LRS_FACTOR_R)
+    need += align256(8 * (size_t)(nf * r)) + 2 * align256(8 * (size_t)(nf * r)) + cpqr_ws(nf, r, r) +
+            tsqr_ws(r, nf, 8) + 1024;
+  if (prec >= LRS_PREC_SPLIT_BF16) need += gemm_tc_workspace(kk, r, LRS_PREC_BF16X3) + 4096;
+  lrs_status st = ws_reserve(ctx, need);
+  if (st) return st;
+  double* Rm = (double*)ws_alloc(ctx, 8 * (size_t)(r * r));
+  double* Vr = (double*)ws_alloc(ctx, 8 * (size_t)(r * r));
+  double* sv = (double*)ws_alloc(ctx, 8 * (size_t)r);
+  int32_t* piv = (int32_t*)ws_alloc(ctx, 4 * (size_t)r);
+  int32_t* rank = (int32_t*)ws_alloc(ctx, 8);
+  if (!Rm || !Vr || !sv || !piv || !rank) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd_from_factor)");
+  if (mode == LRS_FACTOR_GRAM) {
+    // the pivoted FP64 Cholesky of the summed Gram and the cluster Jacobi on
+    // the rows of its factor, as lrs_svd_k takes them for FP32 B
+    const double* G = F;
+    if (ldf != r) {
+      double* Gc = (double*)ws_alloc(ctx, 8 * (size_t)(r * r));
+      if (!Gc) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd_from_factor)");
+      LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(Gc, r * 8, F, ldf * 8, r * 8, r, cudaMemcpyDeviceToDevice, ctx->stream));
+      G = Gc;
+    }
+    st = launch_pchol(ctx, G, (int)r, (int)r, 0.0, 1, piv, Rm, r, rank);
+    if (st) return st;
+    int32_t* h = (int32_t*)ctx->host_scratch;
+    LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 44, rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (h[44] != (int32_t)r) {
+      if (err_est) *err_est = -1.0;       // nothing written: the caller takes LRS_FACTOR_R
+      return lrs_fail(ctx, LRS_ERANK,
+                      "svd_from_factor: the FP64 Gram of B is not positive definite (Cholesky rank %d < r=%lld); "
+                      "LRS_FACTOR_R factors B without squaring it", h[44], (long long)r);
+    }
+    const size_t mark = ctx->ws_top;
+    st = launch_jacobi_rows(ctx, Rm, r, r, piv, Vr, sv);
+    ctx->ws_top = mark;
+    if (st != LRS_OK && st != LRS_ERANK) return st;
+    if (st == LRS_ERANK) {
+      // no cluster fits: the unpivoted factor and the Jacobi on its columns
+      st = launch_pchol(ctx, G, (int)r, (int)r, 0.0, 0, piv, Rm, r, rank);
+      if (st) return st;
+      st = launch_jacobi(ctx, Rm, r, Vr, sv, 1);
+      if (st) return st;
+    }
+  } else {
+    // R of F^T (r x r, F F^T = B B^T), then the FP64 Jacobi on its columns
+    const double* Fc = F;
+    if (ldf != nf) {
+      double* t = (double*)ws_alloc(ctx, 8 * (size_t)(nf * r));
+      if (!t) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd_from_factor)");
+      LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(t, nf * 8, F, ldf * 8, nf * 8, r, cudaMemcpyDeviceToDevice, ctx->stream));
+      Fc = t;
+    }
+    st = LRS_ERANK;
+    if (r >= 24 && ctx->coop_ok) {
+      const size_t mark = ctx->ws_top;
+      st = r_of_bt_cpqr(ctx, Fc, r, nf, Rm);
+      ctx->ws_top = mark;
+      if (st != LRS_OK && st != LRS_ERANK) return st;
+    }
+    if (st == LRS_ERANK) st = launch_tsqr(ctx, Fc, 1, r, nf, nf, Rm);
+    if (st) return st;
+    st = launch_jacobi(ctx, Rm, r, Vr, sv, 1);
+    if (st) return st;
+  }
+  st = lrs::svd_finish(ctx, Vr, sv, r, kk, Q, ldq, m, B, n, prec, U, ldu, S, V, ldv, fro2, err_est);
+  if (st) return st;
+  return r < k ? lrs_fail(ctx, LRS_ERANK, "svd_from_factor: rank r=%lld < k=%d", (long long)r, k) : LRS_OK;
 }
 
 lrs_status lrs_id_k(lrs_ctx* ctx, const double* Ysk, int64_t m, int64_t l, int64_t ldy, int32_t k,

@@ -24,8 +24,20 @@ __global__ void k_transpose(const TI* __restrict__ src, int64_t rows, int64_t co
 lrs_status launch_transpose(lrs_ctx* ctx, const double* src, int64_t rows, int64_t cols, int64_t lds,
                             double* dst, int64_t ldd) {
   if (rows <= 0 || cols <= 0) return LRS_OK;
+  if ((rows + 31) / 32 > 65535) return lrs_fail(ctx, LRS_EINVAL, "transpose: %lld rows", (long long)rows);
   dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
   k_transpose<double, double><<<grid, dim3(32, 8), 0, ctx->stream>>>(src, rows, cols, lds, dst, ldd);
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
+
+lrs_status launch_transpose32(lrs_ctx* ctx, const float* src, int64_t rows, int64_t cols, int64_t lds,
+                              float* dst, int64_t ldd) {
+  if (rows <= 0 || cols <= 0) return LRS_OK;
+  if ((rows + 31) / 32 > 65535) return lrs_fail(ctx, LRS_EINVAL, "transpose: %lld rows", (long long)rows);
+  dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+  k_transpose<float, float><<<grid, dim3(32, 8), 0, ctx->stream>>>(src, rows, cols, lds, dst, ldd);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
   return LRS_OK;

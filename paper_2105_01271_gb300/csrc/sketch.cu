@@ -150,7 +150,8 @@ lrs_status launch_sketch(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int
   return LRS_OK;
 }
 
-// W = A_f(:, I) and its transpose W^T in one pass (FP32 outputs): a thread
+// W = A_f(:, I) and its transpose W^T in one pass (FP32 outputs; WT NULL:
+// W alone): a thread
 // takes one subsample point j and 8 consecutive snapshots, writes W[t, j]
 // (coalesced over j) and the 8 values W^T[j, t0..t0+7] as 32 contiguous
 // bytes (two 16-byte stores when the row stride and base allow).
@@ -174,6 +175,7 @@ __global__ void __launch_bounds__(256) k_gather_both(const void* __restrict__ A,
 #pragma unroll
       for (int u = 0; u < kGtRows; ++u)
         if (u < nt) W[(t0 + u) * ldw + j] = v[u];
+      if (!WT) continue;                 // W alone (lrs_touch)
       float* dst = WT + (int64_t)j * ldwt + t0;
       if (vec && nt == kGtRows) {
         reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
