@@ -751,7 +751,7 @@ def run_others():
                 continue
             d = json.loads(lines[-1])
             keep = {k: d[k] for k in ("value", "unit", "ms_per_step", "dtype", "config", "roofline", "e2e",
-                                      "plain_fp32_gpu", "per_matrix_loop", "learned_vs_adaptive", "result",
+                                      "plain_fp32_gpu", "per_matrix_loop", "adaptive", "learned", "train", "result",
                                       "items", "autotune", "gpu_launches", "clocks") if k in d}
             keep["wall_s"] = round(time.time() - t0, 1)
             out[name] = keep
