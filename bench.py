@@ -930,6 +930,14 @@ def run_ours(args, rank, world):
         d_ = path.id_from_pass(ctx, w.m, w.grid, w.k, g0, bufs)
         return s_, d_
 
+    # FP64 FMA throughput of this GPU (the FP64 kernels' roofline denominator),
+    # measured on the library's stream before the timed region
+    try:
+        fp64_peak = ctx.fp64_peak()
+        fp64_src = "measured by lrs_fp64_peak (8 dependent FMA chains per thread, 4 x 256 threads per SM)"
+    except Exception:
+        fp64_peak, fp64_src = FP64_PEAK_TFLOPS, "nominal FP64 from unit counts: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"
+
     clk = clocks_start(dev)
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -1054,7 +1062,7 @@ def run_ours(args, rank, world):
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     # FP32 (or FP64) FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x clock
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    alu_peak = nsm * (128 if bsz == 4 else 2) * 2 * sm_max * 1e6 / 1e12     # TFLOP/s
+    alu_peak = nsm * 128 * 2 * sm_max * 1e6 / 1e12 if bsz == 4 else fp64_peak     # TFLOP/s
     gbs = alg_bytes / (apass_ms * 1e-3) / 1e9
     tfl = alg_flops / (apass_ms * 1e-3) / 1e12
     ridge_hbm_t = alg_bytes / (hbm_peak * 1e9)
@@ -1068,7 +1076,7 @@ def run_ours(args, rank, world):
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"}
     else:
         roof = {"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s", "frac": tfl / alu_peak,
-                "peak_source": f"{nsm} SMs x {'128 FP32' if bsz == 4 else '2 FP64'} FMA/clk x 2 x {sm_max:.0f} MHz"}
+                "peak_source": f"{nsm} SMs x 128 FP32 FMA/clk x 2 x {sm_max:.0f} MHz" if bsz == 4 else fp64_src}
     roof.update({"kernel": "A-pass B = Q^T A_f (lrs_gemm_tn)",
                  "traffic": APASS_TRAFFIC.get((w.name, prec_name)),
                  "algorithmic_bytes": alg_bytes, "algorithmic_flops": alg_flops, "ms": apass_ms,
@@ -1093,11 +1101,46 @@ def run_ours(args, rank, world):
     pq, cq = g0, w.m
     cpqr_flops = sum(6.0 * (pq - j) * (cq - j) for j in range(min(w.k, pq, cq)))
     roof_qr = {"bound": "alu", "kernel": f"pivoted QR of the {g0} x {w.m} row-ID iterate (k_cpqr_cols via lrs_id_k)",
-               "achieved": cpqr_flops / (id_ms * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+               "achieved": cpqr_flops / (id_ms * 1e-3) / 1e12, "peak": fp64_peak,
                "unit": "TFLOP/s (FP64)", "ms": id_ms, "algorithmic_flops": cpqr_flops,
-               "peak_source": "nominal FP64 from unit counts: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
-               "traffic": None}
+               "peak_source": fp64_src, "nominal_fp64_tflops": FP64_PEAK_TFLOPS, "traffic": None}
     roof_qr["frac"] = roof_qr["achieved"] / roof_qr["peak"]
+
+    # ---- the paper-literal full-rank basis: Q of the sketch at rtol 1e-12 (r ~ l), so
+    # the A-pass B = Q^T A_f is a tensor-bound product (the generic tensor-core kernel
+    # for r > 256); its kernel alone timed with the library's events ----
+    roof_wide = None
+    if prec >= binding.LRS_PREC_SPLIT_BF16 and w.dtype == "f32" and w.grid.l >= 512 and \
+            min(w.m, w.grid.l) * w.n * 4 <= 4 * 2 ** 30:
+        lw = w.grid.l
+        Qw = torch.empty((w.m, min(w.m, lw)), dtype=torch.float64, device=A_d.device)
+        with torch.cuda.stream(stream):
+            rw = ctx.range_find(bufs.Y, w.m, lw, lw, 1e-12, Qw, Qw.shape[1])
+            Bw = torch.empty((rw, w.n), dtype=torch.float32, device=A_d.device)
+            ctx.gemm_tn(rw, w.n, w.m, Qw, 0, Qw.shape[1], A_d, binding.DTYPE[w.dtype], w.n, Bw, 0, 0, w.n, prec)
+            w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ctx.set_kernel_timing(True)
+            wk = []
+            w0.record(stream)
+            for _ in range(3):
+                ctx.gemm_tn(rw, w.n, w.m, Qw, 0, Qw.shape[1], A_d, binding.DTYPE[w.dtype], w.n, Bw, 0, 0, w.n, prec)
+                wk.append(ctx.last_kernel_ms())
+            w1.record(stream)
+            ctx.set_kernel_timing(False)
+        stream.synchronize()
+        wcall = w0.elapsed_time(w1) / 3
+        wkern = statistics.mean(wk) if min(wk) > 0 else wcall
+        pieces = 3 if prec == binding.LRS_PREC_SPLIT_BF16 else 6
+        fl = 2.0 * w.m * w.n * rw
+        bf16_burst = peaks.get("bf16_tflops", 1966.7)
+        roof_wide = {"bound": "tensor", "kernel": f"A-pass B = Q^T A_f with r = {rw} (k_gemm_tc, {pieces} BF16 products)",
+                     "r": rw, "rtol": 1e-12, "ms": wkern, "call_ms": wcall,
+                     "algorithmic_flops": fl, "issued_bf16_flops": fl * pieces,
+                     "achieved": fl * pieces / (wkern * 1e-3) / 1e12, "unit": "TFLOP/s (BF16 issued)",
+                     "peak": bf16_burst, "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops, burst)",
+                     "method_tflops": fl / (wkern * 1e-3) / 1e12, "traffic": None}
+        roof_wide["frac"] = roof_wide["achieved"] / bf16_burst
+        del Bw, Qw
 
     # ---- end to end through the public API, host buffers in and out ----
     # Every step copies its matrix in from pinned host memory and its results
@@ -1190,7 +1233,9 @@ def run_ours(args, rank, world):
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": w.dtype if prec != binding.LRS_PREC_FP64 else "f64",
            "data": "synthetic", "config": cfg_dict(w, rtol, prec_name),
-           "roofline": roof, "roofline_pivoted_qr": roof_qr, "clocks": clocks,
+           "roofline": roof, "roofline_pivoted_qr": roof_qr, "roofline_wide_apass": roof_wide,
+           "fp64_peak_measured_tflops": fp64_peak if fp64_src.startswith("measured") else None,
+           "clocks": clocks,
            "gpu_launches": int(launches),
            "e2e": {"value": job_throughput(world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms, "steps": e2e_steps,

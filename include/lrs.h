@@ -458,16 +458,24 @@ lrs_status lrs_id_k_static(lrs_ctx* ctx, const double* Ysk, int64_t m, int64_t l
 int64_t lrs_launch_count(const lrs_ctx* ctx);
 
 /* Kernel timing (measurement support; the paper has no counterpart).
- * lrs_set_kernel_timing(ctx, 1) makes every later call that runs the
- * tensor-core A-pass kernel (the one full read of A_f inside lrs_svd_k and
- * lrs_gemm_tn, and the SPC lifting read) bracket that kernel alone with two
- * CUDA events on ctx's stream; lrs_last_kernel_ms then returns its duration
- * in milliseconds for the most recent such call, or -1 when none was timed.
+ * lrs_set_kernel_timing(ctx, 1) makes every later call that runs a
+ * tensor-core product kernel (the TMA A-pass -- the one full read of A_f
+ * inside lrs_svd_k and lrs_gemm_tn, and the SPC lifting read -- or the
+ * generic product of wide operands) bracket that kernel alone with two CUDA
+ * events on ctx's stream; lrs_last_kernel_ms then returns its duration in
+ * milliseconds for the most recent such call, or -1 when none was timed.
  * The events are created on the first call with on = 1 (LRS_ECUDA if that
  * fails) and released by lrs_destroy.  Timing costs one event record on
  * each side of the kernel; the calls synchronise ctx's stream anyway. */
 lrs_status lrs_set_kernel_timing(lrs_ctx* ctx, int32_t on);
 double lrs_last_kernel_ms(const lrs_ctx* ctx);
+
+/* FP64 FMA throughput of ctx's device (measurement support: the roofline
+ * denominator of the FP64 kernels).  One launch of 4 blocks per SM x 256
+ * threads, each thread running 8 independent chains of `iters` dependent
+ * FP64 FMAs, timed with CUDA events on ctx's stream; *tflops = 2 x FMAs /
+ * time (best of 3 launches).  iters in [16, 1 << 20].  Synchronises. */
+lrs_status lrs_fp64_peak(lrs_ctx* ctx, int32_t iters, double* tflops);
 
 /* Failure injection for tests (the paper has no counterpart).
  * lrs_set_workspace_limit caps the device workspace later calls on ctx may

@@ -74,6 +74,7 @@ _SIG = {
     "lrs_set_kernel_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "lrs_last_kernel_ms": (C.c_double, [C.c_void_p]),
     "lrs_set_workspace_limit": (C.c_int, [C.c_void_p, C.c_size_t]),
+    "lrs_fp64_peak": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double)]),
     "lrs_selftest_barrier_timeout": (C.c_int, [C.c_void_p, C.c_int64]),
     "lrs_sketch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64,
                              C.POINTER(lrs_grid), C.c_void_p, C.c_int64]),
@@ -226,6 +227,12 @@ class Context:
 
     def last_kernel_ms(self) -> float:
         return float(self.lib.lrs_last_kernel_ms(self.h))
+
+    def fp64_peak(self, iters: int = 4096) -> float:
+        """Measured FP64 FMA throughput of the device, TFLOP/s (lrs_fp64_peak)."""
+        t = C.c_double(0.0)
+        self._check(self.lib.lrs_fp64_peak(self.h, int(iters), C.byref(t)))
+        return t.value
 
     def set_workspace_limit(self, nbytes: int):
         return self._check(self.lib.lrs_set_workspace_limit(self.h, int(nbytes)))

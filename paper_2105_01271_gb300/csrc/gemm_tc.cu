@@ -497,9 +497,12 @@ static lrs_status run_tc(lrs_ctx* ctx, const GemmArgs& a, double* fro2_out) {
   { const lrs_status _s = raise_dyn_smem(ctx, (const void*)kern, (size_t)(Cfg::kSmem)); if (_s) return _s; }
   const int64_t ntiles = P.Mt * P.Nt * P.splits;
   const unsigned grid = (unsigned)(ntiles < ctx->num_sms ? ntiles : ctx->num_sms);
+  const bool timing = ctx->time_kernels && ctx->kev0 && ctx->kev1;
+  if (timing) LRS_CUDA_TRY(ctx, cudaEventRecord(ctx->kev0, ctx->stream));
   kern<<<grid, kThreads, Cfg::kSmem, ctx->stream>>>(P);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
+  if (timing) LRS_CUDA_TRY(ctx, cudaEventRecord(ctx->kev1, ctx->stream));
   if (P.splits > 1) {
     const int64_t tot = a.M * a.N;
     int64_t nb = (tot + 255) / 256;
@@ -517,6 +520,11 @@ static lrs_status run_tc(lrs_ctx* ctx, const GemmArgs& a, double* fro2_out) {
   LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 16, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   if (h[16] != 0) return lrs_fail(ctx, LRS_ETIMEOUT, "tensor-core gemm: a pipeline wait gave up");
+  if (timing) {
+    float ms = 0.f;
+    LRS_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->kev0, ctx->kev1));
+    ctx->last_kernel_ms = ms;
+  }
   ctx->ws_top = ws_mark;
   return LRS_OK;
 }

@@ -157,3 +157,65 @@ lrs_status launch_barrier_selftest(lrs_ctx* ctx, int64_t spin_limit) {
 }
 
 }  // namespace lrs
+
+// ---------------------------------------------------------------------------
+// FP64 FMA throughput probe (lrs_fp64_peak): 8 independent dependent chains
+// per thread hide the FMA latency; the result feeds one store per thread so
+// the chains stay live.
+// ---------------------------------------------------------------------------
+namespace lrs {
+
+__global__ void __launch_bounds__(256) k_dfma_chains(int32_t iters, double seed, double* __restrict__ out) {
+  double a[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) a[c] = seed + 1e-3 * (threadIdx.x + c);
+  const double b = 0.999999, d = 1e-7;
+  for (int32_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[c] = fma(a[c], b, d);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s += a[c];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace lrs
+
+extern "C" lrs_status lrs_fp64_peak(lrs_ctx* ctx, int32_t iters, double* tflops) {
+  if (!ctx) return LRS_EINVAL;
+  ctx->err[0] = 0;
+  if (!tflops || iters < 16 || iters > (1 << 20)) return lrs_fail(ctx, LRS_EINVAL, "fp64_peak: iters=%d", iters);
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const unsigned blocks = (unsigned)ctx->num_sms * 4;
+  lrs_status st = lrs::ws_reserve(ctx, sizeof(double) * (size_t)blocks * 256 + 256);
+  if (st) return st;
+  double* out = (double*)lrs::ws_alloc(ctx, sizeof(double) * (size_t)blocks * 256);
+  if (!out) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (fp64_peak)");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  LRS_CUDA_TRY(ctx, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return lrs_fail(ctx, LRS_ECUDA, "fp64_peak: event creation failed");
+  }
+  double best = 0.0;
+  lrs_status res = LRS_OK;
+  for (int rep = 0; rep < 4 && res == LRS_OK; ++rep) {
+    cudaEventRecord(e0, ctx->stream);
+    lrs::k_dfma_chains<<<blocks, 256, 0, ctx->stream>>>(iters, 1.0 + rep, out);
+    ctx->launches++;
+    cudaEventRecord(e1, ctx->stream);
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      res = lrs_fail(ctx, LRS_ECUDA, "fp64_peak: launch failed");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double t = 2.0 * 8.0 * (double)iters * (double)blocks * 256.0 / (ms * 1e-3) / 1e12;
+    if (rep > 0 && t > best) best = t;            // the first launch warms up
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (res == LRS_OK) *tflops = best;
+  return res;
+}
