@@ -16,7 +16,8 @@ numpy/scipy (LAPACK) as the only library steps:
                   subsample A_f(:, I).
   cpqr.py         Sec. 4: Householder QR with column pivoting (own code).
   rangefinder.py  Algs. 2/3/7 "QR(.)": rank-revealing orthonormal basis.
-  cpwr.py         Sec. 5, Alg. 7: coarse-grid power iteration.
+  cpwr.py         Sec. 5, Alg. 7: coarse-grid power iteration; its single-read
+                  form (the final basis as W M, B = M^T (W^T A_f)).
   svd.py          Sec. 3.1, Alg. 2: TPC-SVD projection B = Q^T A_f and SVD(B).
   interp.py       Sec. 4, Alg. 4: TPC-ID (row ID of the sketch by CPQR of A_c^T).
   spc.py          Sec. 4, Algs. 5/6: SPC-ID lifting operator T_r, the

@@ -35,3 +35,45 @@ def cpwr(Y: np.ndarray, W: np.ndarray, q: int, reorth: bool, rtol: float):
         if reorth:
             G, _ = range_find(G, rtol)
     return G, Qnp
+
+
+def single_read_basis(Y: np.ndarray, W: np.ndarray, q: int, rtol: float):
+    """Alg. 7 with re-orthonormalisation (q >= 1), the final basis written in
+    the subsample's coordinates: returns (Q_b, M) with Q_b = QR(G_q) and
+    Q_b = W M (m x r and |I| x r).
+
+    The last iteration forms G_q = W T from the orthonormal T = QR(W^T G), so
+    range(Q_b) lies in range(W T) and Q_b = W T X for the X that solves
+    (W T) X = Q_b (least squares; exact since Q_b lies in that range);
+    M = T X.  This is what lets B = Q_b^T A_f be formed as M^T (W^T A_f)
+    from products accumulated in the same read of A_f as the sketch (reading
+    of Sec. 5 for a single pass: W^T A_f is a sum over snapshot blocks, like
+    A_c^T A_f in Alg. 3)."""
+    if q < 1:
+        raise ValueError("the single-read form needs q >= 1")
+    Qnp, _ = range_find(Y, rtol)
+    G = Qnp
+    T = None
+    for it in range(q):
+        T, _ = range_find(W.T @ G, rtol)
+        G = W @ T
+        if it + 1 < q:
+            G, _ = range_find(G, rtol)
+    Qb, r = range_find(G, rtol)
+    X = np.linalg.lstsq(G, Qb, rcond=None)[0]
+    return Qb, T @ X
+
+
+def single_read_svd(A: np.ndarray, Y: np.ndarray, W: np.ndarray, k: int, q: int, rtol: float):
+    """TPC-SVD (Alg. 2) with C-PWR from one read of A_f: Z^T = W^T A_f
+    (|I| x n), B = M^T Z^T = Q_b^T A_f, then SVD(B) as svd.tpc_svd.  Returns
+    (U, S, V, err_est, spectrum of B, ||A_f||_F^2, Q_b)."""
+    from .svd import svd_of_projection
+    from .sketch import as_f64
+    Af = as_f64(A)
+    Qb, M = single_read_basis(Y, W, q, rtol)
+    Zt = W.T @ Af
+    B = M.T @ Zt
+    fro2 = float(np.sum(Af * Af))
+    U, S, V, err, s_all = svd_of_projection(B, Qb, k, fro2)
+    return U, S, V, err, s_all, fro2, Qb
