@@ -72,6 +72,7 @@ def parse():
 BATCH_WORKLOAD = "batch256_mixed_f32"
 SPC_WORKLOAD = "spc_blob2d_m2000_512x512_f32"
 STREAM_WORKLOAD = "spcstream_blob2d_m2000_512x512_f32"
+STREAM_CPWR_WORKLOAD = "spcstream_cpwr_blob2d_m2000_512x512_f32"
 LEARNED_WORKLOAD = "learned_mixed2d_tol1e-3"
 
 
@@ -607,6 +608,99 @@ def run_stream_bench(args, rank, world):
            "result": {"err_est_svd": err_svd, "eps_hat_min": min(eps)}}
     print(json.dumps(out), flush=True)
     st.close()
+
+
+def run_stream_cpwr_bench(args, rank, world):
+    """C-PWR inside the single read of streamed snapshots on the 2000 x 512^2
+    FP32 blob field: row blocks of 250 snapshots pushed through lrs_spc_stream
+    with lrs_spc_stream_cpwr (the sketch rows, the subsample rows W at the 16x
+    injection points (|I| = l = 1024) and Z^T += W^T a_f in FP64, no H^T),
+    then the SVD from B = M^T Z^T (q = 1, rtol 1e-6, k = 50) and the row ID of
+    the iterate (W W^T) A_c.  value: rows pushed from device memory; e2e:
+    from pinned host memory."""
+    import torch
+    import synth
+    from paper_2105_01271_gb300 import binding
+
+    w = synth.WORKLOADS["blob2d_m2000_512x512_f32"]
+    k, block, q, rtol = 50, 250, 1, 1e-6
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    A_h = torch.from_numpy(synth.make_workload(w, seed_offset=rank)).pin_memory()
+    m, n, l = w.m, w.n, w.grid.l
+    gram = synth.GridSpec(w.grid.N, w.grid.s, "inject")          # |I| = l
+    stream = torch.cuda.Stream(dev)
+    ctx = binding.Context(dev, stream)
+    A_d = torch.empty(A_h.shape, dtype=torch.float32, device=f"cuda:{dev}")
+    A_d.copy_(A_h)
+    torch.cuda.synchronize(dev)
+    st = binding.SpcStream(ctx, binding.LRS_F32, m, binding.grid_of(w.grid), block, 0, binding.LRS_PREC_SPLIT_BF16)
+    st.enable_cpwr(binding.grid_of(gram), spc_too=False)
+    U = torch.empty((m, k), dtype=torch.float64, device=A_d.device)
+    S = torch.empty((k,), dtype=torch.float64, device=A_d.device)
+    V = torch.empty((n, k), dtype=torch.float64, device=A_d.device)
+    J = torch.empty((k,), dtype=torch.int32, device=A_d.device)
+    P = torch.empty((m, k), dtype=torch.float64, device=A_d.device)
+    fp64_peak = ctx.fp64_peak()
+
+    def step(src, on_device):
+        st.reset()
+        for r0 in range(0, m, block):
+            st.push(src.data_ptr() + r0 * n * 4, min(block, m - r0), n, on_device)
+        e1, r, _ = st.cpwr_svd(q, rtol, k, U, k, S, V, k)
+        e2 = st.cpwr_id(q, rtol, k, J, P, k)
+        return e1, e2, r
+
+    clk = clocks_start(dev)
+    for _ in range(max(args.warmup, 1)):
+        step(A_d, True)
+    torch.cuda.synchronize(dev)
+    mark = clocks_mark(clk)
+    l0 = ctx.launches
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        err_svd, err_id, r = step(A_d, True)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = clocks_stop(clk, mark)
+    launches = (ctx.launches - l0) // max(args.steps, 1)
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, f"cuda:{dev}")
+    # the pushes alone: the one read of A_f with its FP64 W^T a_f products
+    st.reset()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for r0 in range(0, m, block):
+        st.push(A_d.data_ptr() + r0 * n * 4, min(block, m - r0), n, True)
+    p1.record(stream)
+    torch.cuda.synchronize(dev)
+    push_ms = p0.elapsed_time(p1)
+    st.cpwr_svd(q, rtol, k, U, k, S, V, k)
+    t0 = time.perf_counter()
+    step(A_h, False)
+    V_h = V.cpu()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, world, f"cuda:{dev}")
+    if rank != 0:
+        return
+    flops = 2.0 * gram.l * n * m
+    tfl = flops / (push_ms * 1e-3) / 1e12
+    out = {"metric": METRIC, "value": job_throughput(world, ms), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": STREAM_CPWR_WORKLOAD, "m": m, "n": n, "grid": "512x512",
+                      "sketch": f"fullweight s=16 (l={l})", "gram": f"inject s=16 (|I|={gram.l})", "q": q,
+                      "rtol": rtol, "block_rows": block, "k": k, "prec": "fp64 (single-read C-PWR products)",
+                      "storage": "f32", "l2": "inputs larger than L2, no flush"},
+           "roofline": {"bound": "alu", "achieved": tfl, "peak": fp64_peak, "unit": "TFLOP/s (FP64)",
+                        "frac": tfl / fp64_peak, "peak_source": "measured by lrs_fp64_peak",
+                        "kernel": "the pushes: sketch rows, W rows, Z^T += W^T a_f (k_gemm_tn FP64)",
+                        "traffic": None, "algorithmic_flops": flops, "ms": push_ms,
+                        "ms_covers": "all pushes of one matrix from device memory (8 blocks of 250 rows)"},
+           "clocks": clocks, "gpu_launches": launches,
+           "e2e": {"value": job_throughput(world, e2e_ms), "unit": UNIT,
+                   "h2d_bytes_per_step": int(A_h.numel() * 4), "d2h_bytes_per_step": int(V_h.numel() * 8)},
+           "result": {"err_est_svd": err_svd, "err_est_id": err_id, "r": r}}
+    print(json.dumps(out), flush=True)
 
 
 def run_learned_bench(args, rank, world):
@@ -1273,6 +1367,8 @@ def main():
         run_spc_bench(args, rank, world)
     elif args.workload == STREAM_WORKLOAD:
         run_stream_bench(args, rank, world)
+    elif args.workload == STREAM_CPWR_WORKLOAD:
+        run_stream_cpwr_bench(args, rank, world)
     elif args.workload == LEARNED_WORKLOAD:
         run_learned_bench(args, rank, world)
     else:

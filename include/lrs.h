@@ -414,6 +414,36 @@ lrs_status lrs_spc_stream_reset(lrs_spc_stream* s);
 void lrs_spc_stream_destroy(lrs_spc_stream* s);
 
 /*
+ * C-PWR in the same single read (Sec. 5, Alg. 7 with re-orthonormalisation).
+ * lrs_spc_stream_cpwr (before the first push) makes every pushed block also
+ * gather its rows of the subsample W = A_f(:, I) (grid `gram`, injection
+ * points; m x |I| FP64) and accumulate Z^T += W(rows,:)^T a_f (|I| x n,
+ * FP64).  Allocates 8 m |I| + 8 |I| n + 16 m l bytes.  spc_too = 0 drops
+ * the H^T products from the pushes (the SPC finishers then return
+ * LRS_EINVAL).
+ *   lrs_spc_stream_cpwr_svd  the C-PWR basis from A_c and W alone: Q_np =
+ *       QR(A_c); q times T = QR(W^T G), G = W T (G re-orthonormalised between
+ *       iterations); Q_b = QR(G) by pivoted Householder QR (rtol) and one
+ *       Cholesky-QR pass, written as Q_b = W M with M = T(:, piv) R_11^-1
+ *       R_2^-1 (the same triangular solves that give Q_b from G); then
+ *       B = M^T Z^T = Q_b^T A_f (r x n FP64) and the SVD of B as lrs_svd_k
+ *       (U m x k, S, V n x k FP64, err_est).  *r_out = r (host).  1 <= q <= 16;
+ *       LRS_ERANK when r < k (the first r columns written).
+ *   lrs_spc_stream_cpwr_id   the row ID of the iterate without
+ *       re-orthonormalisation, (W W^T)^q A_c (lrs_power_pass_from in FP64,
+ *       then lrs_id_k): J, P, err_est as lrs_id_k.
+ * The products run in FP64 whatever the stream's prec: B = M^T Z^T carries
+ * Z^T's rounding amplified by ||M|| ||W||, up to the condition number of
+ * W T (~1/rtol), and FP32-level products would leave the trailing
+ * directions of B at the rounding level.  Synchronises.
+ */
+lrs_status lrs_spc_stream_cpwr(lrs_spc_stream* s, const lrs_grid* gram, int32_t spc_too);
+lrs_status lrs_spc_stream_cpwr_svd(lrs_spc_stream* s, int32_t q, double rtol, int32_t k, double* U, int64_t ldu,
+                                   double* S, double* V, int64_t ldv, double* err_est, int64_t* r_out);
+lrs_status lrs_spc_stream_cpwr_id(lrs_spc_stream* s, int32_t q, double rtol, int32_t k, int32_t* J, double* P,
+                                  int64_t ldp, double* err_est);
+
+/*
  * lrs_gemm_tn -- the dense contraction every A-pass uses:
  *   C (M x N) = X^T A,   X: K x M,  A: K x N  (both row-major, K rows).
  * Exposed for tests and benchmarks of the A-pass kernel alone.

@@ -138,6 +138,12 @@ _SIG = {
     "lrs_spc_stream_id": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                     C.c_int64, C.c_void_p, C.c_int64, C.POINTER(C.c_double)]),
     "lrs_spc_stream_err": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_double)]),
+    "lrs_spc_stream_cpwr": (C.c_int, [C.c_void_p, C.POINTER(lrs_grid), C.c_int32]),
+    "lrs_spc_stream_cpwr_svd": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_int32, C.c_void_p, C.c_int64,
+                                          C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double),
+                                          C.POINTER(C.c_int64)]),
+    "lrs_spc_stream_cpwr_id": (C.c_int, [C.c_void_p, C.c_int32, C.c_double, C.c_int32, C.c_void_p, C.c_void_p,
+                                         C.c_int64, C.POINTER(C.c_double)]),
     "lrs_spc_stream_sketch": (C.c_void_p, [C.c_void_p]),
     "lrs_spc_stream_destroy": (None, [C.c_void_p]),
     "lrs_spc_stream_reset": (C.c_int, [C.c_void_p]),
@@ -403,6 +409,23 @@ class SpcStream:
         out = (C.c_double * nt)()
         self.ctx._check(self.lib.lrs_spc_stream_err(self.h, t, nt, out))
         return list(out)
+
+    def enable_cpwr(self, gram: lrs_grid, spc_too: bool = True):
+        """lrs_spc_stream_cpwr: C-PWR's subsample and W^T A_f in the same read
+        (spc_too = False: without the SPC finishers' H^T)."""
+        return self.ctx._check(self.lib.lrs_spc_stream_cpwr(self.h, C.byref(gram), 1 if spc_too else 0))
+
+    def cpwr_svd(self, q, rtol, k, U, ldu, S, V, ldv):
+        """Returns (err_est, r, status); LRS_ERANK is returned, not raised."""
+        err, r = C.c_double(0.0), C.c_int64(0)
+        st = self.ctx._check(self.lib.lrs_spc_stream_cpwr_svd(self.h, q, rtol, k, _ptr(U), ldu, _ptr(S), _ptr(V), ldv,
+                                                              C.byref(err), C.byref(r)), allow_rank=True)
+        return err.value, r.value, st
+
+    def cpwr_id(self, q, rtol, k, J, P, ldp) -> float:
+        err = C.c_double(0.0)
+        self.ctx._check(self.lib.lrs_spc_stream_cpwr_id(self.h, q, rtol, k, _ptr(J), _ptr(P), ldp, C.byref(err)))
+        return err.value
 
     def sketch_ptr(self) -> int:
         return int(self.lib.lrs_spc_stream_sketch(self.h) or 0)

@@ -166,6 +166,13 @@ lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c,
 // R (rows 0..rank-1, row stride ldr, pivoted order, zeros below the diagonal)
 lrs_status launch_pchol(lrs_ctx* ctx, const double* G, int c, int kmax, double rtol, int pivot, int32_t* perm,
                         double* R, int64_t ldr, int32_t* rank);
+// G (c x c, full, row-major) = M^T M for M p x c (row stride ldm, c <= 128);
+// workspace num_sms * c (c + 1) / 2 doubles
+lrs_status launch_gram(lrs_ctx* ctx, const double* M, int64_t p, int c, int64_t ldm, double* G);
+// Q (p x r, row stride ldq) = M(:, perm[0..r)) R^{-1}, R the leading r x r
+// upper triangle of an ldr-strided matrix (perm NULL: the first r columns)
+lrs_status launch_trsm_rows(lrs_ctx* ctx, const double* M, int64_t p, int64_t ldm, const int32_t* perm,
+                            const double* R, int64_t ldr, int r, double* Q, int64_t ldq);
 // Rt(t, perm[j]) = R(t, j) for the pivoted factor R (rows 0..r-1, row stride ldr)
 lrs_status launch_rt_scatter(lrs_ctx* ctx, const double* R, int64_t ldr, const int32_t* perm, int64_t r, int64_t c,
                              double* Rt);

@@ -505,6 +505,15 @@ lrs_status launch_pchol(lrs_ctx* ctx, const double* G, int c, int kmax, double r
   return pchol(ctx, G, c, kmax, rtol, pivot, perm, R, ldr, rank);
 }
 
+lrs_status launch_gram(lrs_ctx* ctx, const double* M, int64_t p, int c, int64_t ldm, double* G) {
+  return gram(ctx, M, p, c, ldm, G);
+}
+
+lrs_status launch_trsm_rows(lrs_ctx* ctx, const double* M, int64_t p, int64_t ldm, const int32_t* perm,
+                            const double* R, int64_t ldr, int r, double* Q, int64_t ldq) {
+  return trsm_rows(ctx, M, p, ldm, perm, R, ldr, r, Q, ldq);
+}
+
 bool orth_gram_eligible(int64_t p, int64_t c, double rtol) {
   return c >= 1 && c <= kMaxC && p >= 4 * c && rtol >= kOrthGramRtolMin;
 }

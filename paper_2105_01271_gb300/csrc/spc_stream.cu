@@ -40,6 +40,12 @@ struct lrs_spc_stream {
   // leading triplets of A_c, computed once per r by the finishers
   int32_t svd_r = 0;
   double *Q = nullptr, *Ur = nullptr, *Sr = nullptr, *Vr = nullptr;
+  // single-read C-PWR (lrs_spc_stream_cpwr): the subsample rows W (m x |I|)
+  // and Z^T = W^T A_f (|I| x n), FP64; G0 / Gs (m x l) hold the ID's iterate
+  int cpwr = 0, skip_ht = 0;
+  lrs::GridDev ggrid{};
+  int64_t nI = 0;
+  double *W = nullptr, *Zt = nullptr, *G0 = nullptr, *Gs = nullptr;
 };
 
 namespace lrs {
@@ -67,7 +73,8 @@ void destroy(lrs_spc_stream* s) {
   if (!s) return;
   if (s->ctx) cudaStreamSynchronize(s->ctx->stream);
   if (s->copy) cudaStreamSynchronize(s->copy);
-  void* bufs[] = {s->Ac, s->Ht, s->stage[0], s->stage[1], s->kept, s->fro2_parts, s->fro2, s->Q, s->Ur, s->Sr, s->Vr};
+  void* bufs[] = {s->Ac, s->Ht, s->stage[0], s->stage[1], s->kept, s->fro2_parts, s->fro2, s->Q, s->Ur, s->Sr, s->Vr,
+                  s->W, s->Zt, s->G0, s->Gs};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int i = 0; i < 2; ++i) {
@@ -214,7 +221,9 @@ lrs_status lrs_spc_stream_push(lrs_spc_stream* s, const void* rows, int64_t nrow
     st = launch_sketch(ctx, blk, s->dtype, b, ldb, s->grid, s->Ac + (size_t)r0 * (size_t)s->l, s->l);
     if (st) return st;
     const size_t mark = ctx->ws_top;
-    if (!tc) {
+    if (s->skip_ht) {
+      // C-PWR alone (lrs_spc_stream_cpwr with spc_too = 0): no H^T
+    } else if (!tc) {
       GemmArgs ga{s->l, s->n, b, s->Ac + (size_t)r0 * (size_t)s->l, LRS_F64, s->l, blk, s->dtype, ldb,
                   s->Ht, hf64, 0, s->n, 1.0, r0 > 0 ? 1 : 0};
       st = launch_gemm_simt(ctx, ga, hf64);
@@ -232,6 +241,15 @@ lrs_status lrs_spc_stream_push(lrs_spc_stream* s, const void* rows, int64_t nrow
       }
     }
     ctx->ws_top = mark;
+    if (s->cpwr) {
+      // the block's subsample rows, then Z^T += W(rows,:)^T a_f in FP64
+      double* Wb = s->W + (size_t)r0 * (size_t)s->nI;
+      st = launch_gather(ctx, blk, s->dtype, b, ldb, s->ggrid, Wb, s->nI);
+      if (st) return st;
+      GemmArgs gz{s->nI, s->n, b, Wb, LRS_F64, s->nI, blk, s->dtype, ldb, s->Zt, 1, 0, s->n, 1.0, r0 > 0 ? 1 : 0};
+      st = launch_gemm_simt(ctx, gz, 1);
+      if (st) return st;
+    }
     st = launch_fro2(ctx, blk, s->dtype, b, s->n, ldb, s->fro2_parts + s->blocks);
     if (st) return st;
     // rows i (global) with (i + 1) % c == 0 are kept for SPC-ID-ERR
@@ -269,6 +287,7 @@ lrs_status lrs_spc_stream_svd(lrs_spc_stream* s, double rtol, int32_t r, int32_t
   ctx->err[0] = 0;
   lrs_status st = check_complete(s);
   if (st) return st;
+  if (s->skip_ht) return lrs_fail(ctx, LRS_EINVAL, "spc_stream_svd: the stream keeps no H^T (C-PWR only)");
   if (!U || !S || !V || k < 1 || r < k || r > kStreamMaxR) return lrs_fail(ctx, LRS_EINVAL, "spc_stream_svd: bad r / k");
   if (ldu < k || ldv < k) return lrs_fail(ctx, LRS_EINVAL, "spc_stream_svd: strides too small");
   LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
@@ -307,6 +326,7 @@ lrs_status lrs_spc_stream_id(lrs_spc_stream* s, double rtol, int32_t r, int32_t 
   ctx->err[0] = 0;
   lrs_status st = check_complete(s);
   if (st) return st;
+  if (s->skip_ht) return lrs_fail(ctx, LRS_EINVAL, "spc_stream_id: the stream keeps no H^T (C-PWR only)");
   if (!J || !P || !Sf || k < 1 || r < k || r > kStreamMaxR) return lrs_fail(ctx, LRS_EINVAL, "spc_stream_id: bad r / k");
   if (ldp < k || ldsf < s->n) return lrs_fail(ctx, LRS_EINVAL, "spc_stream_id: strides too small");
   LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
@@ -348,6 +368,188 @@ lrs_status lrs_spc_stream_err(lrs_spc_stream* s, const double* taus, int32_t nta
   const int64_t c = s->err_c;
   return spc_err_from_rows(ctx, s->kept, s->dtype, s->m / c, s->n, s->n, s->Ac + (size_t)(c - 1) * (size_t)s->l, s->l,
                            c * s->l, (double)c, taus, ntau, eps_hat);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// single-read C-PWR
+// ---------------------------------------------------------------------------
+extern "C" {
+
+lrs_status lrs_spc_stream_cpwr(lrs_spc_stream* s, const lrs_grid* gram, int32_t spc_too) {
+  if (!s) return LRS_EINVAL;
+  lrs_ctx* ctx = s->ctx;
+  ctx->err[0] = 0;
+  if (s->pushed != 0) return lrs_fail(ctx, LRS_EINVAL, "spc_stream_cpwr: rows were already pushed");
+  if (s->cpwr) return lrs_fail(ctx, LRS_EINVAL, "spc_stream_cpwr: already enabled");
+  GridDev g;
+  char why[256];
+  if (!grid_from_abi(gram, &g, why, sizeof why)) return lrs_fail(ctx, LRS_EINVAL, "spc_stream_cpwr: gram grid: %s", why);
+  if (g.n != s->n) return lrs_fail(ctx, LRS_EINVAL, "spc_stream_cpwr: gram grid has n=%lld, sketch n=%lld",
+                                   (long long)g.n, (long long)s->n);
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const size_t bw = 8 * (size_t)(s->m * g.l), bz = 8 * (size_t)(g.l * s->n), bg = 8 * (size_t)(s->m * s->l);
+  bool ok = cudaMalloc((void**)&s->W, bw) == cudaSuccess && cudaMalloc((void**)&s->Zt, bz) == cudaSuccess &&
+            cudaMalloc((void**)&s->G0, bg) == cudaSuccess && cudaMalloc((void**)&s->Gs, bg) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    double* bufs[] = {s->W, s->Zt, s->G0, s->Gs};
+    for (double* b : bufs)
+      if (b) cudaFree(b);
+    s->W = s->Zt = s->G0 = s->Gs = nullptr;
+    return lrs_fail(ctx, LRS_ENOMEM, "spc_stream_cpwr: cannot allocate W and Z^T (%zu + %zu bytes)", bw, bz);
+  }
+  g.kind = LRS_INJECT;
+  s->ggrid = g;
+  s->nI = g.l;
+  s->cpwr = 1;
+  s->skip_ht = spc_too ? 0 : 1;
+  return LRS_OK;
+}
+
+lrs_status lrs_spc_stream_cpwr_svd(lrs_spc_stream* s, int32_t q, double rtol, int32_t k, double* U, int64_t ldu,
+                                   double* S, double* V, int64_t ldv, double* err_est, int64_t* r_out) {
+  if (!s) return LRS_EINVAL;
+  lrs_ctx* ctx = s->ctx;
+  ctx->err[0] = 0;
+  lrs_status st = check_complete(s);
+  if (st) return st;
+  if (!s->cpwr) return lrs_fail(ctx, LRS_EINVAL, "spc_stream_cpwr_svd: lrs_spc_stream_cpwr was not called");
+  if (!U || !S || !V || k < 1 || q < 1 || q > 16) return lrs_fail(ctx, LRS_EINVAL, "spc_stream_cpwr_svd: bad q / k");
+  if (!(rtol >= 0.0) || rtol >= 1.0) return lrs_fail(ctx, LRS_EINVAL, "spc_stream_cpwr_svd: rtol=%g", rtol);
+  if (ldu < k || ldv < k) return lrs_fail(ctx, LRS_EINVAL, "spc_stream_cpwr_svd: strides too small");
+  LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const int64_t m = s->m, l = s->l, nI = s->nI, n = s->n;
+  const int64_t cmax = m < l ? m : l;              // columns of any iterate
+  const int64_t tmax = cmax < 128 ? cmax : 128;    // the final basis: Cholesky-QR refinement holds <= 128
+  const size_t a = 256;
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t o1 = orth_ws_of(m, cmax, ctx->num_sms), o2 = orth_ws_of(nI, cmax, ctx->num_sms);
+  size_t need = al(8 * (size_t)(nI * m)) +                       // W^T
+                al(8 * (size_t)(m * cmax)) * 4 +                 // Q_np, G, G2, Q_b
+                al(8 * (size_t)(nI * cmax)) * 3 +                // T0, T, M
+                al(8 * (size_t)(cmax * m)) * 2 +                 // G column-major, Householder vectors
+                al(8 * (size_t)(cmax * cmax)) * 3 + al(4 * (size_t)cmax) * 2 + 4 * a +
+                al(8 * (size_t)(m * cmax)) + al(8 * (size_t)(nI * cmax)) +   // Q1, M1
+                al(8 * (size_t)(tmax * n)) +                                   // B
+                cpqr_scratch_bytes(m, cmax, cmax, ctx->num_sms) +
+                al(8 * (size_t)ctx->num_sms * (size_t)(tmax * (tmax + 1) / 2)) +
+                (o1 > o2 ? o1 : o2) + svd_from_b_ws(tmax, n, m, k < tmax ? k : tmax, LRS_PREC_FP64, ctx->num_sms) +
+                65536;
+  st = ws_reserve(ctx, need);
+  if (st) return st;
+  double* WT = (double*)ws_alloc(ctx, 8 * (size_t)(nI * m));
+  double* Qnp = (double*)ws_alloc(ctx, 8 * (size_t)(m * cmax));
+  double* G = (double*)ws_alloc(ctx, 8 * (size_t)(m * cmax));
+  double* G2 = (double*)ws_alloc(ctx, 8 * (size_t)(m * cmax));
+  double* T0 = (double*)ws_alloc(ctx, 8 * (size_t)(nI * cmax));
+  double* T = (double*)ws_alloc(ctx, 8 * (size_t)(nI * cmax));
+  if (!WT || !Qnp || !G || !G2 || !T0 || !T) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (cpwr_svd)");
+  st = launch_transpose(ctx, s->W, m, nI, nI, WT, m);
+  if (st) return st;
+  const size_t mark = ctx->ws_top;
+  int64_t gc = 0, t = 0;
+  st = orth_basis(ctx, s->Ac, m, l, l, rtol, Qnp, cmax, &gc);
+  if (st) return st;
+  ctx->ws_top = mark;
+  const double* Gcur = Qnp;
+  for (int it = 0; it < q; ++it) {
+    // T = QR(W^T G)  (|I| x t), then G = W T  (m x t)
+    st = gemm_prec(ctx, LRS_PREC_FP64, nI, gc, m, s->W, LRS_F64, nI, Gcur, LRS_F64, cmax, T0, 1, 0, cmax);
+    if (st) return st;
+    ctx->ws_top = mark;
+    st = orth_basis(ctx, T0, nI, gc, cmax, rtol, T, cmax, &t);
+    if (st) return st;
+    ctx->ws_top = mark;
+    st = gemm_prec(ctx, LRS_PREC_FP64, m, t, nI, WT, LRS_F64, m, T, LRS_F64, cmax, G, 1, 0, cmax);
+    if (st) return st;
+    ctx->ws_top = mark;
+    if (it + 1 < q) {
+      st = orth_basis(ctx, G, m, t, cmax, rtol, G2, cmax, &gc);
+      if (st) return st;
+      ctx->ws_top = mark;
+      Gcur = G2;
+    }
+  }
+  if (t > 128) return lrs_fail(ctx, LRS_EINVAL, "spc_stream_cpwr_svd: %lld directions (the final basis holds <= 128)",
+                               (long long)t);
+  // Q_b = QR(G): pivoted Householder QR of G (column-major copy), then
+  // Q_1 = G(:, piv) R_11^-1 and the same solve on T (M_1 = T(:, piv) R_11^-1)
+  double* GT = (double*)ws_alloc(ctx, 8 * (size_t)(t * m));
+  CpqrOut o{};
+  o.perm = (int32_t*)ws_alloc(ctx, 4 * (size_t)t);
+  o.R = (double*)ws_alloc(ctx, 8 * (size_t)(t * t));
+  o.V = (double*)ws_alloc(ctx, 8 * (size_t)(m * t));
+  o.tail2 = (double*)ws_alloc(ctx, 8);
+  o.rank = (int32_t*)ws_alloc(ctx, 8);
+  double* Q1 = (double*)ws_alloc(ctx, 8 * (size_t)(m * t));
+  double* M1 = (double*)ws_alloc(ctx, 8 * (size_t)(nI * t));
+  double* Gr = (double*)ws_alloc(ctx, 8 * (size_t)(t * t));
+  double* R2 = (double*)ws_alloc(ctx, 8 * (size_t)(t * t));
+  int32_t* p2 = (int32_t*)ws_alloc(ctx, 4 * (size_t)t);
+  int32_t* rk2 = (int32_t*)ws_alloc(ctx, 8);
+  double* Qb = (double*)ws_alloc(ctx, 8 * (size_t)(m * t));
+  double* Mb = (double*)ws_alloc(ctx, 8 * (size_t)(nI * t));
+  double* f2 = (double*)ws_alloc(ctx, 8);
+  if (!GT || !o.perm || !o.R || !o.V || !o.tail2 || !o.rank || !Q1 || !M1 || !Gr || !R2 || !p2 || !rk2 || !Qb ||
+      !Mb || !f2)
+    return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (cpwr_svd)");
+  st = launch_transpose(ctx, G, m, t, cmax, GT, m);
+  if (st) return st;
+  st = launch_cpqr(ctx, GT, m, t, m, t, rtol, o);
+  if (st) return st;
+  int32_t* h = (int32_t*)ctx->host_scratch;
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 48, o.rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  const int r = h[48];
+  if (r < 1) return lrs_fail(ctx, LRS_ERANK, "spc_stream_cpwr_svd: the C-PWR basis is empty");
+  st = launch_trsm_rows(ctx, G, m, cmax, o.perm, o.R, t, r, Q1, t);
+  if (st) return st;
+  st = launch_trsm_rows(ctx, T, nI, cmax, o.perm, o.R, t, r, M1, t);
+  if (st) return st;
+  // one Cholesky-QR pass: Q_1^T Q_1 = R_2^T R_2, Q_b = Q_1 R_2^-1, M = M_1 R_2^-1
+  st = launch_gram(ctx, Q1, m, r, t, Gr);
+  if (st) return st;
+  st = launch_pchol(ctx, Gr, r, r, 0.0, 0, p2, R2, r, rk2);
+  if (st) return st;
+  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 49, rk2, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (h[49] != r) return lrs_fail(ctx, LRS_ERANK, "spc_stream_cpwr_svd: Cholesky-QR refinement broke down (%d < %d)",
+                                  h[49], r);
+  st = launch_trsm_rows(ctx, Q1, m, t, nullptr, R2, r, r, Qb, r);
+  if (st) return st;
+  st = launch_trsm_rows(ctx, M1, nI, t, nullptr, R2, r, r, Mb, r);
+  if (st) return st;
+  // B = M^T Z^T = Q_b^T A_f  (r x n, FP64)
+  double* B = (double*)ws_alloc(ctx, 8 * (size_t)(r * n));
+  if (!B) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (cpwr_svd)");
+  const size_t mark2 = ctx->ws_top;
+  st = gemm_prec(ctx, LRS_PREC_FP64, r, n, nI, Mb, LRS_F64, r, s->Zt, LRS_F64, n, B, 1, 0, n);
+  if (st) return st;
+  ctx->ws_top = mark2;
+  st = launch_sum(ctx, s->fro2_parts, (int)s->blocks, f2);
+  if (st) return st;
+  st = svd_from_b(ctx, B, r, n, Qb, r, m, k, LRS_PREC_FP64, U, ldu, S, V, ldv, f2, err_est);
+  if (st) return st;
+  if (r_out) *r_out = r;
+  return r < k ? lrs_fail(ctx, LRS_ERANK, "spc_stream_cpwr_svd: rank r=%d < k=%d", r, k) : LRS_OK;
+}
+
+lrs_status lrs_spc_stream_cpwr_id(lrs_spc_stream* s, int32_t q, double rtol, int32_t k, int32_t* J, double* P,
+                                  int64_t ldp, double* err_est) {
+  if (!s) return LRS_EINVAL;
+  lrs_ctx* ctx = s->ctx;
+  ctx->err[0] = 0;
+  lrs_status st = check_complete(s);
+  if (st) return st;
+  if (!s->cpwr) return lrs_fail(ctx, LRS_EINVAL, "spc_stream_cpwr_id: lrs_spc_stream_cpwr was not called");
+  if (q < 1 || q > 16) return lrs_fail(ctx, LRS_EINVAL, "spc_stream_cpwr_id: q=%d", q);
+  int64_t g0 = 0, gc = 0;
+  st = lrs_power_pass_from(ctx, s->Ac, s->l, s->W, s->nI, s->m, s->l, s->nI, q, rtol, LRS_PREC_FP64, s->G0, s->l, &g0,
+                           s->Gs, s->l, &gc);
+  if (st) return st;
+  return lrs_id_k(ctx, s->G0, s->m, g0, s->l, k, J, P, ldp, err_est);
 }
 
 }  // extern "C"
