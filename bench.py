@@ -64,6 +64,8 @@ def parse():
                    help="columns: one matrix split by column slabs over the ranks (NCCL sums; strong scaling)")
     p.add_argument("--virtual-ranks", type=int, default=1,
                    help="with --split columns on one GPU: this many ranks, one context each, on that GPU")
+    p.add_argument("--heldout-count", type=int, default=1000,
+                   help="matrices of the learned proposal's held-out evaluation")
     p.add_argument("--no-others", action="store_true",
                    help="skip the other configurations' runs added to the default line")
     return p.parse_args()
@@ -74,6 +76,7 @@ SPC_WORKLOAD = "spc_blob2d_m2000_512x512_f32"
 STREAM_WORKLOAD = "spcstream_blob2d_m2000_512x512_f32"
 STREAM_CPWR_WORKLOAD = "spcstream_cpwr_blob2d_m2000_512x512_f32"
 LEARNED_WORKLOAD = "learned_mixed2d_tol1e-3"
+LEARNED_HELDOUT_WORKLOAD = "learned_heldout1000_m1000_128-512"
 
 
 def workload_params(name):
@@ -804,6 +807,97 @@ def run_learned_bench(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def _heldout_matrix(sp):
+    import synth
+    return synth.learned_matrix(sp)
+
+
+def run_learned_heldout(args, rank, world):
+    """The learned proposal on its held-out set: trained (by the library's own
+    kernels) on the stored 20k-matrix set (N 32-128, m 64-512), evaluated on
+    unseen matrices of 1000 snapshots on 128^2-512^2 grids (heat / blob /
+    tanh fields, FP32) against the plain adaptive enlargement, both to a
+    relative range error of 1e-3.  The matrices are generated by a host
+    process pool (started before any GPU work) while the GPU decomposes the
+    previous ones; value = matrices per second of GPU-side decomposition time
+    with the learned start."""
+    import multiprocessing as mp
+    import synth
+    specs = synth.learned_heldout_specs(args.heldout_count, seed=9 + rank)
+    pool = mp.get_context("spawn").Pool(max(1, (os.cpu_count() or 4) - 2))
+    gen = pool.imap(_heldout_matrix, specs, chunksize=1)
+    import torch
+    from paper_2105_01271_gb300 import binding, learned
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    d = np.load(os.path.join(ROOT, "tests", "golden", "learned_set.npz"))
+    ctx = binding.Context(dev)
+    model = learned.Proposal(ctx, seed=0)
+    t0 = time.perf_counter()
+    hist = model.train(d["X_train"], d["y_train"], epochs=120, batch=128, lr=2e-3, seed=0)
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+    acc_test = float(np.mean(model.predict(d["X_test"]) == d["y_test"]))
+    bufs = learned.buffers(1000, 512, f"cuda:{dev}")
+    tol = 1e-3
+    rows = []
+    clk = clocks_start(dev)
+    mark = clocks_mark(clk)
+    t_all = time.perf_counter()
+    try:
+        for i, (sp, a) in enumerate(zip(specs, gen)):
+            A = torch.from_numpy(a).to(f"cuda:{dev}")
+            rl = learned.decompose_to_tolerance(ctx, A, sp["m"], sp["N"], tol, bufs, model=model)
+            ra = learned.decompose_to_tolerance(ctx, A, sp["m"], sp["N"], tol, bufs)
+            rows.append((sp["N"], sp["field"], rl.seconds, len(rl.tried), rl.predicted, rl.accepted, rl.tried[-1][1],
+                         ra.seconds, len(ra.tried), ra.accepted, ra.tried[-1][1]))
+            print(f"heldout {i}: N={sp['N']} {sp['field']} learned {rl.seconds:.3f} s / {len(rl.tried)} tries "
+                  f"(start {rl.predicted}, accepted {rl.accepted}), adaptive {ra.seconds:.3f} s / {len(ra.tried)} "
+                  f"(accepted {ra.accepted})", file=sys.stderr, flush=True)
+            del A
+    finally:
+        pool.terminate()
+        pool.join()
+    wall = time.perf_counter() - t_all
+    clocks = clocks_stop(clk, mark)
+    if rank != 0:
+        return
+    R = rows
+    sl, sa = sum(r[2] for r in R), sum(r[7] for r in R)
+    last = len(learned.CONFIGS) - 1
+    met_l = sum(1 for r in R if r[6] <= tol or r[5] == last)
+    met_a = sum(1 for r in R if r[10] <= tol or r[9] == last)
+    per_n = {}
+    for N in (128, 256, 512):
+        sub = [r for r in R if r[0] == N]
+        if sub:
+            per_n[str(N)] = {"matrices": len(sub), "learned_s": sum(r[2] for r in sub),
+                             "adaptive_s": sum(r[7] for r in sub),
+                             "tries_learned": sum(r[3] for r in sub), "tries_adaptive": sum(r[8] for r in sub)}
+    out = {"metric": METRIC, "value": len(R) / sl * world, "unit": "matrices/s", "n_gpus": world, "steps": 1,
+           "warmup": 0, "ms_per_step": sl * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": LEARNED_HELDOUT_WORKLOAD, "matrices": len(R), "snapshots": 1000,
+                      "grids": "128^2, 256^2, 512^2 (uniform)", "fields": "heat/blob/tanh", "tolerance": tol,
+                      "configurations": "(s, q) = (8,0) (8,1) (4,0) (4,1) (2,0) (2,1), split_bf16",
+                      "timing": "host wall clock around each decomposition (synchronised), generation excluded"},
+           "clocks": clocks, "roofline": None,
+           "adaptive": {"value": len(R) / sa * world, "seconds": sa, "tries": sum(r[8] for r in R),
+                        "speedup_of_learned": sa / sl},
+           "learned": {"seconds": sl, "tries": sum(r[3] for r in R),
+                       "start_was_accepted": sum(1 for r in R if r[4] == r[5]),
+                       "start_equals_adaptive_choice": sum(1 for r in R if r[4] == r[9]),
+                       "start_above_adaptive_choice": sum(1 for r in R if r[4] > r[9])},
+           "met_tolerance": {"learned": met_l, "adaptive": met_a},
+           "per_grid": per_n,
+           "train": {"samples": int(len(d["y_train"])), "epochs": 120, "seconds": train_s,
+                     "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "test_accuracy": acc_test,
+                     "test_samples": int(len(d["y_test"]))},
+           "wall_s": wall}
+    print(json.dumps(out), flush=True)
+
+
 def spc_cpu_baseline(w, k, r_lift, c, taus):
     import oracle
     import oracle.spc as spc
@@ -1371,6 +1465,8 @@ def main():
         run_stream_cpwr_bench(args, rank, world)
     elif args.workload == LEARNED_WORKLOAD:
         run_learned_bench(args, rank, world)
+    elif args.workload == LEARNED_HELDOUT_WORKLOAD:
+        run_learned_heldout(args, rank, world)
     else:
         run_ours(args, rank, world)
     if world > 1 and args.impl == "ours":

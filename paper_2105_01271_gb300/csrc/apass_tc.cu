@@ -507,7 +507,13 @@ struct ApCfg {
   size_t smem;
 };
 
-bool plan(int64_t M, int esize, int SA, int SX, ApCfg* c) {
+// MMAs a chunk may accumulate before its round-to-nearest add: 16 for two
+// pieces of FP32 data, 32 for BF16 data (one exact piece, whose split
+// products' own error, 2^-16, is far above a 32-ulp truncation), 48 for
+// three pieces
+int chunk_mmas(int SA, int SX) { return SX >= 3 ? 48 : (SA == 1 ? 32 : 16); }
+
+bool plan(int64_t M, int64_t Kt, int esize, int SA, int SX, ApCfg* c) {
   if (M < 1 || M > kMaxR) return false;
   c->rN = (int)((M + 15) / 16 * 16);
   c->raw_bytes = (uint32_t)(TK * TN * esize);
@@ -525,21 +531,29 @@ bool plan(int64_t M, int esize, int SA, int SX, ApCfg* c) {
   // stacking needs the widest MMA, max(SA, SX) pieces of rN, within UMMA N <= 256.
   // Preference: K-chunked accumulation (accuracy) over stacking (fewer operand
   // reads): stacked + chunked, unstacked + chunked, then the whole-K forms.
+  // A K sweep no longer than one chunk takes the whole-K form: the same
+  // accumulation, without the running-sum region.
   const int kp = SA > SX ? SA : SX;
   const bool can_stack = LRS_APASS_STACK && kp * c->rN <= kMaxR;
   auto pow2 = [](uint32_t need) { uint32_t cols = 32; while (cols < need) cols <<= 1; return cols; };
   const uint32_t sum_cols = (uint32_t)c->rN;
+  int npairs = 0;
+  for (int i = 0; i < SA; ++i)
+    for (int j = 0; j < SX; ++j) npairs += (i + j < kp) ? 1 : 0;
   for (int form = 0; form < 4; ++form) {
     const int stacked = (form == 0 || form == 2) ? 1 : 0;
     const bool chunked = form < 2;
     if (stacked && !can_stack) continue;
+    const int per_k = 4 * (stacked ? SA : npairs);              // MMAs per slab into one accumulator
+    int kc = chunk_mmas(SA, SX) / per_k;
+    if (kc < 1) kc = 1;
     const int width = stacked ? SX * c->rN : c->rN;
     const uint32_t acc_cols = (uint32_t)((width + 63) / 64 * 64);
-    if (chunked) {
+    if (chunked && Kt > kc) {
       const uint32_t cols = pow2(2 * acc_cols + sum_cols);
       if (cols > 512) continue;
       c->stacked = stacked; c->acc_cols = acc_cols; c->nacc = 2; c->tmem_cols = cols;
-      c->sum_col = 2 * acc_cols; c->kc = kChunkSlabs;
+      c->sum_col = 2 * acc_cols; c->kc = kc;
       return true;
     }
     c->stacked = stacked; c->acc_cols = acc_cols; c->sum_col = 0; c->kc = 0;
@@ -560,7 +574,8 @@ template <int RAW, int SA, int SX>
 lrs_status run_apass(lrs_ctx* ctx, const GemmArgs& a, double* fro2_out) {
   constexpr int esize = RAW == LRS_F32 ? 4 : 2;
   ApCfg cfg;
-  if (!plan(a.M, esize, SA, SX, &cfg)) return lrs_fail(ctx, LRS_EINVAL, "a-pass: r=%lld out of range", (long long)a.M);
+  if (!plan(a.M, (a.K + TK - 1) / TK, esize, SA, SX, &cfg))
+    return lrs_fail(ctx, LRS_EINVAL, "a-pass: r=%lld out of range", (long long)a.M);
   EncodeTiled enc = encode_fn();
   if (!enc) return lrs_fail(ctx, LRS_ECUDA, "a-pass: cuTensorMapEncodeTiled unavailable");
   CUtensorMap map;
@@ -646,7 +661,7 @@ bool apass_eligible(const GemmArgs& a, int prec) {
   const int sa = a.adt == LRS_BF16 ? 1 : (prec == LRS_PREC_BF16X3 ? 3 : 2);
   const int sx = prec == LRS_PREC_BF16X3 ? 3 : 2;
   ApCfg cfg;
-  if (!plan(a.M, esize, sa, sx, &cfg)) return false;
+  if (!plan(a.M, (a.K + TK - 1) / TK, esize, sa, sx, &cfg)) return false;
   return encode_fn() != nullptr;
 }
 

@@ -139,7 +139,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcParams P) {
   uint8_t* smem = smem_raw + pad;                      // 1024-B aligned stage buffers
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t ntiles = P.Mt * P.Nt * P.splits;
-  // tile -> (split, mt, nt), nt fastest
+  // tile -> (split, mt, nt).  One row tile: nt fastest.  Several: mt fastest,
+  // so the CTAs that need the same A columns (every row tile of one nt) run
+  // side by side and the A slab comes from HBM once, from L2 for the others.
+  const bool mfast = P.Mt > 1;
+  auto tile_nt = [&](int64_t tile) -> int64_t { return mfast ? (tile / P.Mt) % P.Nt : tile % P.Nt; };
+  auto tile_mt = [&](int64_t tile) -> int64_t { return mfast ? tile % P.Mt : (tile / P.Nt) % P.Mt; };
   auto kt_range = [&](int64_t tile, int64_t& lo, int64_t& hi) {
     const int64_t ks = tile / (P.Mt * P.Nt);
     lo = ks * P.KS;
@@ -174,7 +179,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcParams P) {
     bool have_cur = false;
     double fro2 = 0.0;
     for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tcount) {
-      const int64_t nt = tile % P.Nt, mt = (tile / P.Nt) % P.Mt;
+      const int64_t nt = tile_nt(tile), mt = tile_mt(tile);
       const int64_t n = nt * TBN + nl;
       int64_t kt_lo, kt_hi;
       kt_range(tile, kt_lo, kt_hi);
@@ -195,7 +200,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcParams P) {
         if (pf) {
           int64_t kt2 = kt + 1;
           if (last) { int64_t h2; kt_range(ntile, kt2, h2); }
-          const int64_t n2 = last ? ((ntile % P.Nt) * TBN + nl) : n;
+          const int64_t n2 = last ? (tile_nt(ntile) * TBN + nl) : n;
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const int64_t k0 = kt2 * TBK + (int64_t)(ch + 2 * i) * 8;
@@ -362,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcParams P) {
     if (lane == 0) {
       int64_t it = 0;
       for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t mt = (tile / P.Nt) % P.Mt, nt = tile % P.Nt;
+        const int64_t mt = tile_mt(tile), nt = tile_nt(tile);
         int64_t kt_lo, kt_hi;
         kt_range(tile, kt_lo, kt_hi);
         bool ok = true;

@@ -25,6 +25,10 @@ struct lrs_ctx {
   void* aux = nullptr;
   size_t aux_cap = 0;
   int64_t launches = 0;
+  // a second stream for independent work inside one call (forked from and
+  // joined back into `stream` with the two events); created on first use
+  cudaStream_t side = nullptr;
+  cudaEvent_t side_fork = nullptr, side_join = nullptr;
   // optional timing of the A-pass kernel (lrs_set_kernel_timing)
   int time_kernels = 0;
   cudaEvent_t kev0 = nullptr, kev1 = nullptr;

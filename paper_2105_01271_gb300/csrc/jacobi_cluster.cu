@@ -40,6 +40,11 @@ namespace lrs {
 namespace {
 
 constexpr int kMaxSweeps = 40;
+// A sweep whose largest rotated pair had |x.y| <= kStopRatio ||x|| ||y||
+// ends the iteration: one-sided Jacobi converges quadratically, so the next
+// sweep would start below (kStopRatio)^2 times a modest constant, under the
+// rotation threshold r u64, and would only confirm convergence.
+constexpr float kStopRatio = 3e-9f;
 
 struct JacRowsArgs {
   const double* R;      // r x r row-major (ldr), upper triangular
@@ -82,7 +87,9 @@ __global__ void __launch_bounds__(256, 1) k_jacobi_rows_cl(JacRowsArgs a) {
   float2* nrm = reinterpret_cast<float2*>(buf + 4 * blk);   // [2][2][b] (hi, lo)
   int* ids = reinterpret_cast<int*>(nrm + 4 * b);       // [2][2][b]
   int* rotc = ids + 4 * b;                              // [kMaxSweeps] (CTA 0's copy is the sum)
+  unsigned* rmx = reinterpret_cast<unsigned*>(rotc + kMaxSweeps);   // [kMaxSweeps] largest pair ratio (float bits)
   __shared__ int s_rot;
+  __shared__ unsigned s_rmx;
   const int tid = threadIdx.x, nth = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nw = nth >> 5;
   const int nb2 = 2 * NC;
@@ -101,12 +108,13 @@ __global__ void __launch_bounds__(256, 1) k_jacobi_rows_cl(JacRowsArgs a) {
     const int c = blockid * b + j;
     ids[slot * b + j] = c < r ? c : -1;
   }
-  for (int e = tid; e < kMaxSweeps; e += nth) rotc[e] = 0;
+  for (int e = tid; e < kMaxSweeps; e += nth) { rotc[e] = 0; rmx[e] = 0u; }
   cl.sync();                                            // every CTA started; DSMEM usable
 
   // a pair is orthogonal once |x.y| <= tol ||x|| ||y||
   const float tolf = 1.1102230246251565e-16f * (float)(r > 16 ? r : 16);
 
+  float mxr = 0.f;                                      // this warp's largest rotated pair ratio this sweep
   // rotate the pair (x, y) with tracked squared norms (na, nb) in place (one warp)
   auto rotate = [&](double* x, double* y, float2* na, float2* nb) -> int {
     double gg = 0.0;
@@ -116,6 +124,7 @@ __global__ void __launch_bounds__(256, 1) k_jacobi_rows_cl(JacRowsArgs a) {
     const float2 av = *na, bv = *nb;
     const df32 aa{av.x, av.y}, bb{bv.x, bv.y};
     if (g.hi == 0.0f || fabsf(g.hi) <= tolf * (sqrtf(aa.hi) * sqrtf(bb.hi))) return 0;
+    mxr = fmaxf(mxr, fabsf(g.hi) / (sqrtf(aa.hi) * sqrtf(bb.hi)));
     // zeta = (b - a) / (2 g), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
     // in double-float: an angle accurate to ~1e-14 keeps the convergence of
     // the last sweeps quadratic
@@ -181,7 +190,8 @@ __global__ void __launch_bounds__(256, 1) k_jacobi_rows_cl(JacRowsArgs a) {
 
   int par = 0, sweep = 0;
   for (; sweep < kMaxSweeps; ++sweep) {
-    if (tid == 0) s_rot = 0;
+    if (tid == 0) { s_rot = 0; s_rmx = 0u; }
+    mxr = 0.f;
     renorm(par);
     __syncthreads();
     int nrot = 0;                                       // lane 0 of each warp counts
@@ -247,15 +257,18 @@ __global__ void __launch_bounds__(256, 1) k_jacobi_rows_cl(JacRowsArgs a) {
       }
       if (round == nb2 - 2) {
         if (lane == 0 && nrot) atomicAdd(&s_rot, nrot);
-        __syncthreads();                                 // s_rot complete
+        if (lane == 0 && mxr > 0.f) atomicMax(&s_rmx, __float_as_uint(mxr));
+        __syncthreads();                                 // s_rot, s_rmx complete
         if (tid == 0 && s_rot) atomicAdd(cl.map_shared_rank(rotc + sweep, 0), s_rot);
+        if (tid == 0 && s_rmx) atomicMax(cl.map_shared_rank(rmx + sweep, 0), s_rmx);
       }
       cl.sync();
       par = npar;
     }
     // every CTA reads the same sum, after the barrier that ordered the adds
     const int total = *cl.map_shared_rank(rotc + sweep, 0);
-    if (total == 0) { ++sweep; break; }
+    const float biggest = __uint_as_float(*cl.map_shared_rank(rmx + sweep, 0));
+    if (total == 0 || biggest <= kStopRatio) { ++sweep; break; }
   }
   // rotated columns out, by global column index
   for (int slot = 0; slot < 2; ++slot) {
@@ -313,7 +326,7 @@ struct ClusterPlan {
 
 size_t rows_smem(int b, int rs) {
   return sizeof(double) * (size_t)(4 * b * rs) + sizeof(float2) * (size_t)(4 * b) +
-         sizeof(int) * (size_t)(4 * b + kMaxSweeps) + 64;
+         sizeof(int) * (size_t)(4 * b + 2 * kMaxSweeps) + 64;
 }
 
 bool cluster_fits(int nc, int threads, size_t smem) {

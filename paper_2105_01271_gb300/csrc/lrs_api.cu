@@ -263,6 +263,9 @@ void lrs_destroy(lrs_ctx* ctx) {
   if (ctx->kev1) cudaEventDestroy(ctx->kev1);
   if (ctx->ws) { cudaStreamSynchronize(ctx->stream); cudaFree(ctx->ws); }
   if (ctx->aux) { cudaStreamSynchronize(ctx->stream); cudaFree(ctx->aux); }
+  if (ctx->side) { cudaStreamSynchronize(ctx->side); cudaStreamDestroy(ctx->side); }
+  if (ctx->side_fork) cudaEventDestroy(ctx->side_fork);
+  if (ctx->side_join) cudaEventDestroy(ctx->side_join);
   if (ctx->host_scratch) cudaFreeHost(ctx->host_scratch);
   delete ctx;
 }
@@ -350,8 +353,14 @@ lrs_status lrs_range_find_diag(lrs_ctx* ctx, const double* G, int64_t m, int64_t
 namespace lrs {
 
 // workspace of one C-PWR pass (W, W^T and the loop buffers)
-static size_t cpwr_ws(lrs_ctx* ctx, int64_t m, int64_t l, int64_t nI, int32_t prec) {
-  const int64_t wmax = l > m ? l : m;
+// Iterate widths: with re-orthonormalisation every iterate has at most
+// min(m, l) columns (the rank of QR(Y)); without it W^T Y has l.
+static int64_t cpwr_width(int64_t m, int64_t l, bool reorth_only) {
+  return reorth_only ? (l < m ? l : m) : (l > m ? l : m);
+}
+
+static size_t cpwr_ws(lrs_ctx* ctx, int64_t m, int64_t l, int64_t nI, int32_t prec, bool reorth_only = false) {
+  const int64_t wmax = cpwr_width(m, l, reorth_only);
   const bool tc = prec >= LRS_PREC_SPLIT_BF16;
   const size_t wsz = tc ? 4 : 8;
   size_t need = 0;
@@ -377,6 +386,32 @@ static size_t cpwr_ws(lrs_ctx* ctx, int64_t m, int64_t l, int64_t nI, int32_t pr
   }
   return need + inner;
 }
+
+// The side stream: work queued there between side_fork() and the join runs
+// beside the context's stream; the join makes the context's stream wait for it.
+static lrs_status side_fork(lrs_ctx* ctx) {
+  if (!ctx->side) {
+    LRS_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+    LRS_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->side_fork, cudaEventDisableTiming));
+    LRS_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->side_join, cudaEventDisableTiming));
+  }
+  LRS_CUDA_TRY(ctx, cudaEventRecord(ctx->side_fork, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->side, ctx->side_fork, 0));
+  return LRS_OK;
+}
+
+// joins the side stream back into the context's stream on every exit once armed
+struct SideJoin {
+  lrs_ctx* ctx;
+  bool armed = false;
+  explicit SideJoin(lrs_ctx* c) : ctx(c) {}
+  void join() {
+    if (!armed) return;
+    cudaStreamWaitEvent(ctx->stream, ctx->side_join, 0);
+    armed = false;
+  }
+  ~SideJoin() { join(); }
+};
 
 // The C-PWR loop of Alg. 7 from a given sketch Y (m x l, ldy) and the
 // gathered subsample W (m x nI) and W^T (nI x m), both in wdt: q iterations
@@ -406,7 +441,7 @@ static lrs_status cpwr_loop(lrs_ctx* ctx, const void* W, const void* WT, int64_t
                             const double* Y, int64_t ldy, int32_t q, int32_t reorth, double rtol, int32_t prec,
                             double* G, int64_t ldg, int64_t* g_cols, double* Gid = nullptr, int64_t ldgid = 0,
                             int64_t* gid_cols = nullptr) {
-  const int64_t wmax = l > m ? l : m;
+  const int64_t wmax = cpwr_width(m, l, reorth != 0);
   const bool tc = prec >= LRS_PREC_SPLIT_BF16;
   const int32_t wdt = tc ? LRS_F32 : LRS_F64;
   bool chain = Gid && reorth && q > 0;
@@ -460,6 +495,23 @@ static lrs_status cpwr_loop(lrs_ctx* ctx, const void* W, const void* WT, int64_t
     Gcur = Ga_; ldcur = wmax;
     rnp = gc;                          // Y = Q_np Rt_np
     if (gc > 128) chain = false;       // no factor chain beyond 128 directions
+  }
+  // The chain's Cholesky, Ra^T Ra = Rt_np Rt_np^T (rnp x rnp, plain FP64),
+  // needs only QR(Y)'s factor: it runs on the side stream (one block, no
+  // workspace) while the loop's products and QRs run on the context's stream.
+  SideJoin side(ctx);
+  if (chain) {
+    st = side_fork(ctx);
+    if (st) return st;
+    cudaStream_t main_stream = ctx->stream;
+    ctx->stream = ctx->side;
+    lrs_status s1 = spc_small_gemm(ctx, rnp, rnp, l, RtY, l, 1, RtY, 1, l, nullptr, nullptr, Ga, rnp);
+    lrs_status s2 = s1 ? s1 : launch_pchol(ctx, Ga, (int)rnp, (int)rnp, 0.0, 0, cperm, Ra, rnp, crank);
+    const cudaError_t e = cudaEventRecord(ctx->side_join, ctx->side);
+    ctx->stream = main_stream;
+    side.armed = true;
+    if (s2) return s2;
+    if (e != cudaSuccess) return lrs_fail(ctx, LRS_ECUDA, "power_pass: side stream: %s", cudaGetErrorString(e));
   }
   for (int it = 0; it < q; ++it) {
     // T = W^T G   (nI x gc)
@@ -520,12 +572,9 @@ static lrs_status cpwr_loop(lrs_ctx* ctx, const void* W, const void* WT, int64_t
   }
   LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(G, ldg * 8, Gcur, ldcur * 8, gc * 8, m, cudaMemcpyDeviceToDevice, ctx->stream));
   *g_cols = gc;
+  side.join();
   if (chain && mrows == gc) {
-    // Ra^T Ra = Rt_np Rt_np^T (rnp x rnp), plain Cholesky in FP64
-    st = spc_small_gemm(ctx, rnp, rnp, l, RtY, l, 1, RtY, 1, l, nullptr, nullptr, Ga, rnp);
-    if (st) return st;
-    st = launch_pchol(ctx, Ga, (int)rnp, (int)rnp, 0.0, 0, cperm, Ra, rnp, crank);
-    if (st) return st;
+    // Ra (from the side stream) with Ra^T Ra = Rt_np Rt_np^T
     int32_t* hr = (int32_t*)ctx->host_scratch;
     LRS_CUDA_TRY(ctx, cudaMemcpyAsync(hr + 46, crank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
     LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
@@ -626,7 +675,8 @@ lrs_status lrs_power_pass(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
   LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   const int64_t l = gs.l;
   const int64_t nI = q > 0 ? gg.l : 0;
-  st = ws_reserve(ctx, q > 0 ? cpwr_ws(ctx, m, l, nI, prec) + align256(8 * (size_t)(m * l)) : 0);
+  // a re-orthonormalised pass keeps every iterate within min(m, l) columns
+  st = ws_reserve(ctx, q > 0 ? cpwr_ws(ctx, m, l, nI, prec, reorth != 0) + align256(8 * (size_t)(m * l)) : 0);
   if (st) return st;
   void *W = nullptr, *WT = nullptr;
   st = touch(ctx, A, dtype, m, lda, gs, gg, q, prec, Y, ldy, &W, &WT);

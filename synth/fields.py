@@ -394,6 +394,21 @@ def learned_specs(count: int, seed: int) -> list:
     return out
 
 
+def learned_heldout_specs(count: int = 1000, seed: int = 9) -> list:
+    """The held-out evaluation set of the learned proposal: 1000 snapshots on
+    N x N grids, N in {128, 256, 512} (uniform), the same field mix and
+    parameter ranges as learned_specs, seeds disjoint from the training and
+    test draws (seed * 100000 + i with seed 9)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        out.append(dict(field=LEARNED_FIELDS[int(rng.choice(3, p=[0.2, 0.4, 0.4]))],
+                        N=int(rng.choice([128, 256, 512])), m=1000,
+                        nfronts=int(rng.integers(1, 5)), nblobs=int(rng.integers(2, 17)),
+                        seed=int(seed * 100000 + i)))
+    return out
+
+
 def learned_matrix(sp: dict) -> np.ndarray:
     if sp["field"] == "heat":
         return heat_field(sp["m"], sp["N"], 2, 16, sp["seed"], "f32")

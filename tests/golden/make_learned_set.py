@@ -2,7 +2,7 @@
 sketch proposal for seeded synthetic matrices, computed by the FP64 oracle
 only (oracle.learned) from synth's generators.
 
-    python tests/golden/make_learned_set.py [--train 1600] [--test 400] [--procs N]
+    python tests/golden/make_learned_set.py [--train 20000] [--test 1000] [--procs N]
 
 Matrices: 2-D fields on N x N grids, N in {32, 64, 128}, m in [64, 512]
 snapshots, FP32 storage: the heat field (16 modes; 20%), advected blobs (2-16
@@ -59,8 +59,8 @@ def main():
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ.setdefault(v, "1")       # one BLAS thread per worker (inherited by the spawned pool)
     ap = argparse.ArgumentParser()
-    ap.add_argument("--train", type=int, default=1200)
-    ap.add_argument("--test", type=int, default=300)
+    ap.add_argument("--train", type=int, default=20000)
+    ap.add_argument("--test", type=int, default=1000)
     ap.add_argument("--procs", type=int, default=os.cpu_count() or 4)
     ap.add_argument("--out", default=os.path.join(HERE, "learned_set.npz"))
     a = ap.parse_args()
