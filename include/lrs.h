@@ -583,6 +583,39 @@ lrs_status lrs_batch_autotune(int device, lrs_batch_item* items, int64_t n_items
                               int32_t n_candidates, int32_t* best, double* ms_per_item);
 lrs_status lrs_batch_release(int device);
 
+/*
+ * The batch as one CUDA graph (batching form; the paper has one matrix at a
+ * time).  The calls above read a few values back to the host as they run
+ * (ranks that size the next launches, breakdown checks, the bounded waits'
+ * error flags), and a stream capture cannot contain a read-back.
+ *   lrs_batch_graph_create  runs the items once as lrs_batch_run does (their
+ *       outputs, r, err and status are written: the batch's results), on
+ *       `branches` contexts and streams (largest first onto the least loaded),
+ *       each context recording every value it reads back, in call order.
+ *       Then it captures the same call sequence from all branches into one
+ *       CUDA graph: each read-back becomes the recorded value plus a
+ *       one-thread guard kernel that compares the device's value with it
+ *       when the graph runs, and the error estimates are computed on the
+ *       device.  Items must have q = 0 (LRS_EINVAL otherwise).  An item whose
+ *       recorded run failed stays out of the graph and runs eagerly at every
+ *       launch.
+ *   lrs_batch_graph_launch  one launch of the graph (the whole batch), then
+ *       the items' r, err and status; an item whose guard saw another value
+ *       (its data, changed in place since the capture, now takes another
+ *       rank or route) is run again eagerly with the single-matrix path, so
+ *       the outputs are always lrs_batch_run's.  *reruns (may be NULL) counts
+ *       those items.  `items` must describe the captured batch (the same
+ *       pointers, sizes and parameters; LRS_EINVAL otherwise): new data goes
+ *       into the same buffers.  Blocks until the batch is done.
+ *   lrs_batch_graph_destroy frees the graph, its contexts and buffers.
+ * Each branch keeps its own workspace, sized by the recorded run.
+ */
+typedef struct lrs_batch_graph lrs_batch_graph;
+lrs_status lrs_batch_graph_create(int device, lrs_batch_item* items, int64_t n_items, int32_t branches,
+                                  lrs_batch_graph** out);
+lrs_status lrs_batch_graph_launch(lrs_batch_graph* g, lrs_batch_item* items, int64_t n_items, int64_t* reruns);
+void lrs_batch_graph_destroy(lrs_batch_graph* g);
+
 /* ------------------------------------------------------------------------
  * Range error: how much of A_f a basis Q captures.
  *   *err = ||A_f - Q Q^T A_f||_F / ||A_f||_F = sqrt(1 - ||Q^T A_f||_F^2 / ||A_f||_F^2)

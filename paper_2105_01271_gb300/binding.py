@@ -118,6 +118,9 @@ _SIG = {
     "lrs_batch_autotune": (C.c_int, [C.c_int, C.c_void_p, C.c_int64, C.POINTER(C.c_int32), C.c_int32,
                                      C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "lrs_batch_release": (C.c_int, [C.c_int]),
+    "lrs_batch_graph_create": (C.c_int, [C.c_int, C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_void_p)]),
+    "lrs_batch_graph_launch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
+    "lrs_batch_graph_destroy": (None, [C.c_void_p]),
     "lrs_range_error": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_int64,
                                   C.c_void_p, C.c_int64, C.c_int64, C.POINTER(C.c_double)]),
     "lrs_sketch_svd": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_double,
@@ -473,3 +476,42 @@ def autotune_batch(items, device: int = 0, candidates=(1, 2, 4, 8)):
                if it.status not in (LRS_OK, LRS_ERANK)]
         raise LrsError(st, f"batch autotune: {len(bad)} item(s) failed, first {bad[:3]}")
     return best.value, ms.value
+
+
+class BatchGraph:
+    """lrs_batch_graph: the batch captured as one CUDA graph (items with q = 0).
+    Creating it runs the batch once (the results are written to the items);
+    launch() replays the whole batch with one graph launch."""
+
+    def __init__(self, items, device: int = 0, branches: int = 4):
+        lib = load_library()
+        self.lib = lib
+        h = C.c_void_p()
+        st = lib.lrs_batch_graph_create(int(device), C.cast(items, C.c_void_p), len(items), int(branches), C.byref(h))
+        if st != LRS_OK:
+            bad = [(i, it.status, it.error.decode(errors="replace")) for i, it in enumerate(items)
+                   if it.status not in (LRS_OK, LRS_ERANK) or it.error[:1]]
+            if not h.value:
+                raise LrsError(st, f"batch graph: {bad[:3]}")
+        self.h = h
+
+    def launch(self, items) -> int:
+        """Replays the batch; returns how many items were run again eagerly."""
+        n = C.c_int64(0)
+        st = self.lib.lrs_batch_graph_launch(self.h, C.cast(items, C.c_void_p), len(items), C.byref(n))
+        if st != LRS_OK:
+            bad = [(i, it.status, it.error.decode(errors="replace")) for i, it in enumerate(items)
+                   if it.status not in (LRS_OK, LRS_ERANK)]
+            raise LrsError(st, f"batch graph launch: {bad[:3]}")
+        return n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lrs_batch_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -652,8 +652,14 @@ lrs_status launch_cpqr_cols(lrs_ctx* ctx, double* M, int64_t p, int64_t c, int64
                                                 dim3(kColsThreads), args, g.smem, ctx->stream));
   ctx->launches++;
   int* h = (int*)ctx->host_scratch;
-  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 33, bar + 2, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->replay) {
+    const int32_t* d[1] = {(const int32_t*)(bar + 2)};
+    const lrs_status rs = replay_ints(ctx, 1, d, h + 33);
+    if (rs) return rs;
+  } else {
+    LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 33, bar + 2, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  }
   if (h[33] != 0) return lrs_fail(ctx, LRS_ETIMEOUT, "cpqr_cols: grid barrier wait gave up");
   return LRS_OK;
 }
@@ -733,8 +739,14 @@ lrs_status launch_cpqr(lrs_ctx* ctx, double* M, int64_t p, int64_t c, int64_t ld
                                                 args, dyn, ctx->stream));
   ctx->launches++;
   int* h = (int*)ctx->host_scratch;
-  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 32, bar + 2, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->replay) {
+    const int32_t* d[1] = {(const int32_t*)(bar + 2)};
+    const lrs_status rs = replay_ints(ctx, 1, d, h + 32);
+    if (rs) return rs;
+  } else {
+    LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 32, bar + 2, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  }
   if (h[32] != 0) return lrs_fail(ctx, LRS_ETIMEOUT, "cpqr: grid barrier wait gave up");
   return LRS_OK;
 }

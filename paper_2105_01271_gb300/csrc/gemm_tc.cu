@@ -522,8 +522,14 @@ static lrs_status run_tc(lrs_ctx* ctx, const GemmArgs& a, double* fro2_out) {
     if (st) return st;
   }
   int* h = (int*)ctx->host_scratch;
-  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 16, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->replay) {
+    const int32_t* d[1] = {(const int32_t*)err};
+    const lrs_status rs = replay_ints(ctx, 1, d, h + 16);
+    if (rs) return rs;
+  } else {
+    LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 16, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  }
   if (h[16] != 0) return lrs_fail(ctx, LRS_ETIMEOUT, "tensor-core gemm: a pipeline wait gave up");
   if (timing) {
     float ms = 0.f;

@@ -7,6 +7,8 @@
 
 #include "../../include/lrs.h"
 
+#include <vector>
+
 struct lrs_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -29,6 +31,19 @@ struct lrs_ctx {
   // joined back into `stream` with the two events); created on first use
   cudaStream_t side = nullptr;
   cudaEvent_t side_fork = nullptr, side_join = nullptr;
+  // Record / replay of a call sequence (the batch graph, batch.cu).  replay
+  // 0: every host read-back as usual.  1 (record): the same, and each value
+  // read back is appended to `log`.  2 (capture): the stream is being
+  // captured into a CUDA graph; a read-back takes the next logged value
+  // instead of waiting, and a guard kernel in its place ORs 1 into
+  // *cap_guard when the graph runs and the device holds another value; the
+  // error estimates are written to cap_err[0] (SVD) and cap_err[1] (ID) on
+  // the device.
+  int replay = 0;
+  std::vector<int32_t> log;
+  size_t log_pos = 0;
+  int* cap_guard = nullptr;
+  double* cap_err = nullptr;
   // optional timing of the A-pass kernel (lrs_set_kernel_timing)
   int time_kernels = 0;
   cudaEvent_t kev0 = nullptr, kev1 = nullptr;
@@ -44,6 +59,17 @@ namespace lrs {
 // across threads.  Every launch with more than 48 KB of dynamic shared memory
 // goes through it.
 lrs_status raise_dyn_smem(lrs_ctx* ctx, const void* func, size_t bytes);
+
+// record / replay of host read-backs (lrs_ctx::replay) -----------------------
+constexpr int kReplayRecord = 1, kReplayCapture = 2;
+// out[i] = the host value of the device int dev[i], i < n (n <= 8), as the
+// context's replay mode says; synchronises unless capturing
+lrs_status replay_ints(lrs_ctx* ctx, int n, const int32_t* const* dev, int32_t* out);
+// capture mode: err = sqrt(sum_{i >= kk} s_i^2 / fro2) (0 when fro2 <= 0 or
+// NULL) into *out on the device, as svd_finish computes it on the host
+lrs_status launch_err_tail(lrs_ctx* ctx, const double* s, int64_t r, int64_t kk, const double* fro2, double* out);
+// capture mode: err = sqrt(max(tail2, 0) / nrm2) (0 when nrm2 <= 0) into *out
+lrs_status launch_err_ratio(lrs_ctx* ctx, const double* tail2, const double* nrm2, double* out);
 
 // workspace ---------------------------------------------------------------
 lrs_status ws_reserve(lrs_ctx* ctx, size_t bytes);           // grow (only between calls)

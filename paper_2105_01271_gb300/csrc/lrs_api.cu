@@ -32,6 +32,8 @@ lrs_status ws_reserve(lrs_ctx* ctx, size_t bytes) {
   if (ctx->ws_limit && bytes > ctx->ws_limit)
     return lrs_fail(ctx, LRS_ENOMEM, "workspace limit: %zu bytes needed, %zu allowed", bytes, ctx->ws_limit);
   if (bytes <= ctx->ws_cap) return LRS_OK;
+  if (ctx->replay == kReplayCapture)
+    return lrs_fail(ctx, LRS_EINVAL, "replay: the workspace would grow during a capture (%zu bytes)", bytes);
   if (ctx->ws) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->ws);
@@ -49,6 +51,8 @@ lrs_status ws_reserve(lrs_ctx* ctx, size_t bytes) {
 
 lrs_status aux_reserve(lrs_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->aux_cap) return LRS_OK;
+  if (ctx->replay == kReplayCapture)
+    return lrs_fail(ctx, LRS_EINVAL, "replay: the split-K buffer would grow during a capture (%zu bytes)", bytes);
   if (ctx->aux) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->aux);
@@ -180,8 +184,14 @@ static lrs_status orth(lrs_ctx* ctx, const double* Min, int64_t p, int64_t c, in
   st = launch_cpqr(ctx, Mc, p, c, p, kmax, rtol, o);
   if (st) return st;
   int32_t r = 0;
-  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(&r, o.rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
-  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->replay) {
+    const int32_t* d[1] = {o.rank};
+    st = replay_ints(ctx, 1, d, &r);
+    if (st) return st;
+  } else {
+    LRS_CUDA_TRY(ctx, cudaMemcpyAsync(&r, o.rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  }
   if (rdiag && r > 0) {
     st = launch_abs_diag(ctx, o.R, c, r, rdiag);
     if (st) return st;
@@ -815,8 +825,14 @@ static lrs_status r_of_bt_cpqr(lrs_ctx* ctx, const double* B, int64_t r, int64_t
   lrs_status st = launch_cpqr(ctx, Mc, n, r, n, r, 0.0, o);
   if (st) return st;
   int32_t rank = 0;
-  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(&rank, o.rank, 4, cudaMemcpyDeviceToHost, ctx->stream));
-  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->replay) {
+    const int32_t* d[1] = {o.rank};
+    st = replay_ints(ctx, 1, d, &rank);
+    if (st) return st;
+  } else {
+    LRS_CUDA_TRY(ctx, cudaMemcpyAsync(&rank, o.rank, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  }
   k_unpermute_r<<<(unsigned)((r * r + 255) / 256), 256, 0, ctx->stream>>>(o.R, o.perm, rank, r, Rout);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
@@ -856,7 +872,12 @@ static lrs_status svd_finish(lrs_ctx* ctx, double* Vr, const double* sv, int64_t
   }
   if (st) return st;
   LRS_CUDA_TRY(ctx, cudaMemcpyAsync(S, sv, 8 * (size_t)kk, cudaMemcpyDeviceToDevice, ctx->stream));
-  if (err_est) {
+  if (err_est && ctx->replay == kReplayCapture) {
+    // captured: computed on the device into the decomposition's slot
+    *err_est = 0.0;
+    st = launch_err_tail(ctx, sv, r, kk, fro2, ctx->cap_err);
+    if (st) return st;
+  } else if (err_est) {
     double* h = (double*)ctx->host_scratch;
     if (fro2) LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h, fro2, 8, cudaMemcpyDeviceToHost, ctx->stream));
     std::vector<double> s_h((size_t)r);
@@ -1203,10 +1224,22 @@ lrs_status lrs_id_k(lrs_ctx* ctx, const double* Ysk, int64_t m, int64_t l, int64
   if (st) return st;
   int32_t rank = 0;
   double* h = (double*)ctx->host_scratch;
+  if (ctx->replay == kReplayCapture) {
+    // captured: the rank from the record, the error estimate on the device
+    const int32_t* d[1] = {o.rank};
+    st = replay_ints(ctx, 1, d, &rank);
+    if (st) return st;
+    if (rank < k) return lrs_fail(ctx, LRS_ERANK, "id_k: sketch rank %d < k=%d", rank, k);
+    st = launch_id_coeffs(ctx, o.R, k, m, o.perm, J, P, ldp);
+    if (st) return st;
+    if (err_est) *err_est = 0.0;
+    return launch_err_ratio(ctx, o.tail2, nrm2, ctx->cap_err + 1);
+  }
   LRS_CUDA_TRY(ctx, cudaMemcpyAsync(&rank, o.rank, 4, cudaMemcpyDeviceToHost, ctx->stream));
   LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h, o.tail2, 8, cudaMemcpyDeviceToHost, ctx->stream));
   LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 1, nrm2, 8, cudaMemcpyDeviceToHost, ctx->stream));
   LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->replay == kReplayRecord) ctx->log.push_back(rank);
   if (rank < k) return lrs_fail(ctx, LRS_ERANK, "id_k: sketch rank %d < k=%d", rank, k);
   st = launch_id_coeffs(ctx, o.R, k, m, o.perm, J, P, ldp);
   if (st) return st;

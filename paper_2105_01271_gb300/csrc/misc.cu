@@ -219,3 +219,66 @@ extern "C" lrs_status lrs_fp64_peak(lrs_ctx* ctx, int32_t iters, double* tflops)
   if (res == LRS_OK) *tflops = best;
   return res;
 }
+
+// ---------------------------------------------------------------------------
+// record / replay of host read-backs
+// ---------------------------------------------------------------------------
+namespace lrs {
+
+__global__ void k_guard_eq(const int32_t* __restrict__ v, int32_t want, int* __restrict__ flag) {
+  if (*v != want) atomicOr(flag, 1);
+}
+
+// the same left-to-right sum as the host loop of svd_finish, no contraction
+__global__ void k_err_tail(const double* __restrict__ s, int64_t r, int64_t kk, const double* __restrict__ fro2,
+                           double* __restrict__ out) {
+  double tail = 0.0;
+  for (int64_t i = r - 1; i >= kk; --i) tail = __dadd_rn(tail, __dmul_rn(s[i], s[i]));
+  const double f = fro2 ? *fro2 : 0.0;
+  *out = f > 0.0 ? sqrt(tail / f) : 0.0;
+}
+
+__global__ void k_err_ratio(const double* __restrict__ tail2, const double* __restrict__ nrm2, double* __restrict__ out) {
+  const double n = *nrm2;
+  *out = n > 0.0 ? sqrt(fmax(*tail2, 0.0) / n) : 0.0;
+}
+
+lrs_status replay_ints(lrs_ctx* ctx, int n, const int32_t* const* dev, int32_t* out) {
+  if (n < 1 || n > 8) return lrs_fail(ctx, LRS_EINVAL, "replay: %d values", n);
+  if (ctx->replay == kReplayCapture) {
+    for (int i = 0; i < n; ++i) {
+      if (ctx->log_pos >= ctx->log.size())
+        return lrs_fail(ctx, LRS_EINVAL, "replay: the call sequence reads more values than were recorded");
+      out[i] = ctx->log[ctx->log_pos++];
+      k_guard_eq<<<1, 1, 0, ctx->stream>>>(dev[i], out[i], ctx->cap_guard);
+      ctx->launches++;
+    }
+    LRS_CUDA_TRY(ctx, cudaGetLastError());
+    return LRS_OK;
+  }
+  int32_t* h = (int32_t*)ctx->host_scratch + 512;
+  for (int i = 0; i < n; ++i)
+    LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + i, dev[i], sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < n; ++i) {
+    out[i] = h[i];
+    if (ctx->replay == kReplayRecord) ctx->log.push_back(h[i]);
+  }
+  return LRS_OK;
+}
+
+lrs_status launch_err_tail(lrs_ctx* ctx, const double* s, int64_t r, int64_t kk, const double* fro2, double* out) {
+  k_err_tail<<<1, 1, 0, ctx->stream>>>(s, r, kk, fro2, out);
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
+
+lrs_status launch_err_ratio(lrs_ctx* ctx, const double* tail2, const double* nrm2, double* out) {
+  k_err_ratio<<<1, 1, 0, ctx->stream>>>(tail2, nrm2, out);
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
+
+}  // namespace lrs

@@ -548,8 +548,14 @@ lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c,
   st = pchol(ctx, G, ci, ci, rtol, 1, perm, R, c, rank);
   if (st) return st;
   int32_t* h = (int32_t*)ctx->host_scratch;
-  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 40, rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
-  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->replay) {
+    const int32_t* d[1] = {rank};
+    st = replay_ints(ctx, 1, d, h + 40);
+    if (st) return st;
+  } else {
+    LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 40, rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  }
   const int r = h[40];
   *r_out = r;
   if (r == 0) return LRS_OK;
@@ -572,8 +578,14 @@ lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c,
   ctx->ws_top = mark;
   st = pchol(ctx, G, r, r, 0.0, 0, perm, R, r, rank);
   if (st) return st;
-  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 41, rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
-  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->replay) {
+    const int32_t* d[1] = {rank};
+    st = replay_ints(ctx, 1, d, h + 41);
+    if (st) return st;
+  } else {
+    LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 41, rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  }
   // Q_1 has full column rank r by construction; a breakdown here means the
   // first pass lost it to rounding: the caller falls back to Householder CPQR
   if (h[41] != r) return LRS_ERANK;
@@ -639,8 +651,14 @@ lrs_status launch_r_of_bt_gram(lrs_ctx* ctx, const float* B, int64_t r, int64_t 
   lrs_status st = pchol(ctx, G, ri, ri, 0.0, perm_out ? 1 : 0, perm, R, r, rank);
   if (st) return st;
   int32_t* h = (int32_t*)ctx->host_scratch;
-  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 42, rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
-  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->replay) {
+    const int32_t* d[1] = {rank};
+    st = replay_ints(ctx, 1, d, h + 42);
+    if (st) return st;
+  } else {
+    LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 42, rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  }
   return h[42] == ri ? LRS_OK : LRS_ERANK;
 }
 
@@ -907,9 +925,18 @@ lrs_status launch_orth_wide(lrs_ctx* ctx, const double* M, int64_t p, int64_t c,
                                                 args, g.smem, ctx->stream));
   ctx->launches++;
   int32_t* h = (int32_t*)ctx->host_scratch;
-  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 43, rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
-  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 44, bar + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
-  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->replay) {
+    const int32_t* d[2] = {rank, (const int32_t*)(bar + 2)};
+    int32_t v[2];
+    lrs_status rs = replay_ints(ctx, 2, d, v);
+    if (rs) return rs;
+    h[43] = v[0];
+    h[44] = v[1];
+  } else {
+    LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 43, rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 44, bar + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  }
   if (h[44] != 0) return lrs_fail(ctx, LRS_ETIMEOUT, "orth_wide: grid barrier wait gave up");
   const int r = h[43];
   // more than 128 directions: the refinement kernels cannot take it; the
@@ -943,8 +970,14 @@ lrs_status launch_orth_wide(lrs_ctx* ctx, const double* M, int64_t p, int64_t c,
   ctx->ws_top = mark;
   st = pchol(ctx, G2, r, r, 0.0, 0, perm, R2, r, rank);
   if (st) return st;
-  LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 45, rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
-  LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->replay) {
+    const int32_t* d[1] = {rank};
+    st = replay_ints(ctx, 1, d, h + 45);
+    if (st) return st;
+  } else {
+    LRS_CUDA_TRY(ctx, cudaMemcpyAsync(h + 45, rank, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    LRS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  }
   if (h[45] != r) return LRS_ERANK;
   if (Rt) {
     st = launch_trmm_upper(ctx, R2, r, R1t, c, Rt);

@@ -490,8 +490,14 @@ static bool jacobi_coop(lrs_ctx* ctx, const double* R, int64_t r, int64_t len, i
   e = cudaGetLastError();
   if (e != cudaSuccess) { st = lrs_fail(ctx, LRS_ECUDA, "jacobi: %s", cudaGetErrorString(e)); return true; }
   int* h = (int*)ctx->host_scratch;
-  e = cudaMemcpyAsync(h + 48, J.bar.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (ctx->replay) {
+    const int32_t* d[1] = {(const int32_t*)J.bar.err};
+    st = replay_ints(ctx, 1, d, h + 48);
+    if (st) return true;
+  } else {
+    e = cudaMemcpyAsync(h + 48, J.bar.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  }
   if (e != cudaSuccess) { st = lrs_fail(ctx, LRS_ECUDA, "jacobi: %s", cudaGetErrorString(e)); return true; }
   if (h[48] != 0) st = lrs_fail(ctx, LRS_ETIMEOUT, "svd: Jacobi grid barrier wait gave up");
   return true;
