@@ -755,11 +755,14 @@ lrs_status launch_cpqr(lrs_ctx* ctx, double* M, int64_t p, int64_t c, int64_t ld
 // Q = H_0 ... H_{r-1} [I_r; 0]: column c only sees H_c .. H_0 (reflectors
 // with index > c leave e_c untouched), so each block builds one column.
 // ---------------------------------------------------------------------------
+// work NULL: the column lives in shared memory (p doubles); else in work +
+// c p (global memory, for columns longer than shared memory holds)
 __global__ void __launch_bounds__(512) k_form_q(const double* __restrict__ V, int64_t p, int64_t r,
-                                                double* __restrict__ Q, int64_t ldq) {
-  extern __shared__ double q[];
+                                                double* __restrict__ Q, int64_t ldq, double* __restrict__ work) {
+  extern __shared__ double qs[];
   __shared__ double red[32];
   const int64_t c = blockIdx.x;
+  double* q = work ? work + c * p : qs;
   const int64_t bs = blockDim.x;
   for (int64_t i = threadIdx.x; i < p; i += bs) q[i] = (i == c) ? 1.0 : 0.0;
   __syncthreads();
@@ -790,11 +793,18 @@ __global__ void __launch_bounds__(512) k_form_q(const double* __restrict__ V, in
 
 lrs_status launch_form_q(lrs_ctx* ctx, const double* V, int64_t p, int64_t r, double* Q, int64_t ldq) {
   if (r <= 0) return LRS_OK;
-  const size_t dyn = sizeof(double) * (size_t)p;
-  if (dyn > 200 * 1024) return lrs_fail(ctx, LRS_EINVAL, "form_q: p=%lld too large", (long long)p);
+  size_t dyn = sizeof(double) * (size_t)p;
+  double* work = nullptr;
+  if (dyn > 200 * 1024) {
+    // columns too long for shared memory: each block works in its own
+    // column of global scratch (form_q_ws bytes, from the caller's reserve)
+    work = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(p * r));
+    if (!work) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (form_q, p=%lld)", (long long)p);
+    dyn = 0;
+  }
   if (dyn > 48 * 1024)
     { const lrs_status _s = raise_dyn_smem(ctx, (const void*)k_form_q, (size_t)(dyn)); if (_s) return _s; }
-  k_form_q<<<(unsigned)r, 512, dyn, ctx->stream>>>(V, p, r, Q, ldq);
+  k_form_q<<<(unsigned)r, 512, dyn, ctx->stream>>>(V, p, r, Q, ldq, work);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
   return LRS_OK;

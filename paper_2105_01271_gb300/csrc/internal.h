@@ -154,6 +154,11 @@ size_t cpqr_scratch_bytes(int64_t p, int64_t c, int64_t kmax, int num_sms);
 // Q (p x r, row-major ldq) = H_0 ... H_{r-1} [I_r; 0]
 lrs_status launch_form_q(lrs_ctx* ctx, const double* V, int64_t p, int64_t r,
                          double* Q, int64_t ldq);
+// workspace launch_form_q takes for p rows and r columns (0 when a column fits
+// in shared memory)
+inline size_t form_q_ws(int64_t p, int64_t r) {
+  return 8 * (size_t)p > 200 * 1024 ? ((8 * (size_t)(p * r) + 255) & ~size_t(255)) : 0;
+}
 // ID: P (m x k) from R (k x m, pivoted order) and perm.
 lrs_status launch_id_coeffs(lrs_ctx* ctx, const double* R, int64_t k, int64_t m,
                             const int32_t* perm, int32_t* J, double* P, int64_t ldp);
@@ -260,6 +265,8 @@ lrs_status launch_transpose32(lrs_ctx* ctx, const float* src, int64_t rows, int6
                               float* dst, int64_t ldd);
 // two-block cooperative launch whose barrier wait runs out (lrs_selftest_barrier_timeout)
 lrs_status launch_barrier_selftest(lrs_ctx* ctx, int64_t spin_limit);
+// FP32 -> FP64 copy of n contiguous values (exact)
+lrs_status launch_widen_f32(lrs_ctx* ctx, const float* src, int64_t n, double* dst);
 // FP64 -> FP32 copy (round to nearest)
 lrs_status launch_to_f32(lrs_ctx* ctx, const double* src, int64_t rows, int64_t cols, int64_t lds,
                          float* dst, int64_t ldd);

@@ -121,6 +121,7 @@ static size_t orth_ws(int64_t p, int64_t c, int num_sms) {
   b += align256(8 * (size_t)(p * kmax));         // V
   b += 2 * 256;                                  // scalars
   b += cpqr_ws(p, c, kmax);
+  b += form_q_ws(p, kmax);                       // Q's columns when too long for shared memory
   if (b < g) b = g;
   if (c > 128) {
     const size_t w = orth_wide_ws(p, c, num_sms);
@@ -892,9 +893,20 @@ static lrs_status svd_finish(lrs_ctx* ctx, double* Vr, const double* sv, int64_t
   return LRS_OK;
 }
 
+// The TSQR tree halves its height per level only while a leaf tile holds at
+// least 2r rows; wider, it degenerates into many levels of nearly the full
+// height (the same rows again and again)
+static bool tsqr_halves(int64_t r, size_t tsz) {
+  int64_t C = (int64_t)((200 * 1024) / (tsz * (size_t)r));
+  if (C > 1024) C = 1024;
+  return C >= 2 * r;
+}
+
 size_t svd_from_b_ws(int64_t r, int64_t n, int64_t m, int64_t kk, int32_t prec, int num_sms) {
   const size_t bsz = prec == LRS_PREC_FP64 ? 8 : 4;
-  size_t need = tsqr_ws(r, n, bsz) + r_of_bt_gram_ws(r, num_sms);
+  size_t need = (tsqr_halves(r, bsz) ? tsqr_ws(r, n, bsz) : 0) + r_of_bt_gram_ws(r, num_sms);
+  if (prec != LRS_PREC_FP64 && !tsqr_halves(r, bsz))   // the FP64 copy of B and its pivoted QR
+    need += 3 * align256(8 * (size_t)(n * r)) + align256(8 * (size_t)(r * r)) + cpqr_ws(n, r, r) + 1024;
   need += 4 * align256(8 * (size_t)(r * r)) + align256(8 * (size_t)(m * r)) + jacobi_ws(r, r) + 65536;
   need += jacobi_rows_ws(r) + align256(4 * (size_t)r);
   if (prec == LRS_PREC_FP64)                     // R of B^T by the pivoted QR
@@ -940,6 +952,18 @@ lrs_status svd_from_b(lrs_ctx* ctx, const void* B, int64_t r, int64_t n, const d
     ctx->ws_top = mark;
     if (st != LRS_OK && st != LRS_ERANK) return st;
     pivoted = st == LRS_OK;
+  }
+  if (st == LRS_ERANK && !f64 && !tsqr_halves(r, 4) && ctx->coop_ok) {
+    // FP32 B too tall for the TSQR tree (r > 160): R of B^T by the
+    // cooperative pivoted QR of B's FP64 copy
+    const size_t mark = ctx->ws_top;
+    double* B64 = (double*)ws_alloc(ctx, 8 * (size_t)(r * n));
+    if (!B64) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd: FP64 copy of B)");
+    st = launch_widen_f32(ctx, (const float*)B, r * n, B64);
+    if (st) return st;
+    st = r_of_bt_cpqr(ctx, B64, r, n, Rm);
+    ctx->ws_top = mark;
+    if (st != LRS_OK && st != LRS_ERANK) return st;
   }
   if (st == LRS_ERANK) st = launch_tsqr(ctx, B, f64, r, n, n, Rm);
   if (st) return st;

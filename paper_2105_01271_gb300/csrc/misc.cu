@@ -282,3 +282,22 @@ lrs_status launch_err_ratio(lrs_ctx* ctx, const double* tail2, const double* nrm
 }
 
 }  // namespace lrs
+
+namespace lrs {
+
+__global__ void k_widen_f32(const float* __restrict__ src, int64_t n, double* __restrict__ dst) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = (double)src[e];
+}
+
+lrs_status launch_widen_f32(lrs_ctx* ctx, const float* src, int64_t n, double* dst) {
+  if (n <= 0) return LRS_OK;
+  int64_t nb = (n + 255) / 256;
+  if (nb > (int64_t)ctx->num_sms * 16) nb = (int64_t)ctx->num_sms * 16;
+  k_widen_f32<<<(unsigned)nb, 256, 0, ctx->stream>>>(src, n, dst);
+  ctx->launches++;
+  LRS_CUDA_TRY(ctx, cudaGetLastError());
+  return LRS_OK;
+}
+
+}  // namespace lrs

@@ -318,8 +318,12 @@ lrs_status trsm_rows(lrs_ctx* ctx, const double* M, int64_t p, int64_t ldm, cons
   const int64_t want = (int64_t)ctx->num_sms * 8 * 32;
   int T = 1;
   while (T < 32 && p * T < want) T <<= 1;
+  // the block's rows (256 / T of them) and R must fit in shared memory: for a
+  // wide R, teams grow (fewer rows per block) until they do
+  auto dyn_of = [&](int t) { return sizeof(double) * (size_t)(r * r + r + (256 / t) * (r + 1)); };
+  while (T < 32 && dyn_of(T) > 200 * 1024) T <<= 1;
   const int rows = 256 / T;
-  const size_t dyn = sizeof(double) * (size_t)(r * r + r + rows * (r + 1));
+  const size_t dyn = dyn_of(T);
   if (dyn > 48 * 1024)
     { const lrs_status _s = raise_dyn_smem(ctx, (const void*)k_trsm_rows, (size_t)(dyn)); if (_s) return _s; }
   const unsigned nb = (unsigned)((p + rows - 1) / rows);

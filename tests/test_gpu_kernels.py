@@ -301,3 +301,40 @@ def test_kernel_timing(lrs):
     assert 0.0 < t < 1000.0
     assert lrs.last_kernel_ms() == -1.0
     assert np.array_equal(_np(Cd), _np(ref))
+
+
+@pytest.mark.parametrize("p,c", [(40000, 100), (70000, 128)])
+def test_range_find_very_tall_wide_basis(lrs, p, c):
+    """Tall-skinny range finder with many rows and a basis near the Gram
+    route's 128 columns: the triangular solve's teams grow until its rows
+    and R fit in shared memory.  The basis spans the input's columns
+    (projector against numpy's QR) and is orthonormal to FP64 level."""
+    torch = _torch()
+    rng = np.random.default_rng(41)
+    M = rng.standard_normal((p, c)) * (0.93 ** np.arange(c))
+    Qd = torch.empty((p, c), dtype=torch.float64, device="cuda")
+    r = lrs.range_find(_dev(M), p, c, c, 1e-6, Qd, c)
+    assert r == c
+    Q = _np(Qd)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(c), atol=1e-12)
+    Qo = np.linalg.qr(M)[0]
+    # the same range: every principal cosine between the two bases is 1
+    s = np.linalg.svd(Q.T @ Qo, compute_uv=False)
+    assert np.min(s) >= 1.0 - 1e-9
+
+
+def test_range_find_householder_long_columns(lrs):
+    """Householder route (rtol below the Gram route's 1e-6) on columns longer
+    than shared memory holds (p = 30000 doubles > 200 KB): Q is formed with
+    each column in global scratch; orthonormal to FP64 level, same range."""
+    torch = _torch()
+    p, c = 30000, 150
+    rng = np.random.default_rng(43)
+    M = rng.standard_normal((p, c)) * (0.95 ** np.arange(c))
+    Qd = torch.empty((p, c), dtype=torch.float64, device="cuda")
+    r = lrs.range_find(_dev(M), p, c, c, 1e-10, Qd, c)
+    assert r == c
+    Q = _np(Qd)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(c), atol=1e-12)
+    s = np.linalg.svd(Q.T @ np.linalg.qr(M)[0], compute_uv=False)
+    assert np.min(s) >= 1.0 - 1e-9

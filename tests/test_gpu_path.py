@@ -385,3 +385,30 @@ def test_row_gram_form_of_the_iterate(lrs, blob):
     # FP32 FMA products over m and |I| terms, FP32 operands: a few hundred u32 of ||G||^2
     assert np.max(np.abs(H @ H.T - GG)) <= 256 * U32 * np.max(np.abs(GG))
     assert abs(np.linalg.norm(H) / np.linalg.norm(Go) - 1.0) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_svd_k_with_a_basis_wider_than_the_tsqr_tree(lrs, prec):
+    """FP32 B with r = 200 directions (beyond the Gram route's 128 and the
+    TSQR tile's 2r rows): R of B^T comes from the pivoted QR of B's FP64
+    copy.  Against the FP64 SVD of Q^T A: every singular value to the
+    products' accuracy relative to s_1, U orthonormal to FP64 level."""
+    from paper_2105_01271_gb300 import binding as b
+    torch = _torch()
+    m, n, r, k = 400, 4096, 200, 40
+    A, sig = synth.low_rank_matrix(m, n, 260, seed=31, decay=0.985, dtype="f32")
+    A64 = A.astype(np.float64)
+    Q = np.linalg.svd(A64, full_matrices=False)[0][:, :r]
+    s_ref = np.linalg.svd(Q.T @ A64, compute_uv=False)
+    U = torch.empty((m, k), dtype=torch.float64, device="cuda")
+    S = torch.empty((k,), dtype=torch.float64, device="cuda")
+    V = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    err, st = lrs.svd_k(_dev(A), b.LRS_F32, m, n, n, _dev(Q), r, r, k, prec, U, k, S, V, k)
+    assert st == b.LRS_OK
+    Sg = _np(S)
+    c = C_PIECE[prec] + (np.sqrt(m) + 1.0) * U32
+    assert np.max(np.abs(Sg - s_ref[:k])) <= 8 * c * s_ref[0], np.max(np.abs(Sg - s_ref[:k])) / s_ref[0]
+    Ug = _np(U)
+    np.testing.assert_allclose(Ug.T @ Ug, np.eye(k), atol=1e-12)
+    tail = np.sqrt(np.sum(s_ref[k:] ** 2) / np.sum(A64 * A64))
+    assert abs(err - tail) <= 1e-3 * tail
