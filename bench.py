@@ -899,7 +899,8 @@ def run_learned_heldout(args, rank, world):
                          ra.seconds, len(ra.tried), ra.accepted, ra.tried[-1][1]))
             print(f"heldout {i}: N={sp['N']} {sp['field']} learned {rl.seconds:.3f} s / {len(rl.tried)} tries "
                   f"(start {rl.predicted}, accepted {rl.accepted}), adaptive {ra.seconds:.3f} s / {len(ra.tried)} "
-                  f"(accepted {ra.accepted})", file=sys.stderr, flush=True)
+                  f"(accepted {ra.accepted}; range errors {[f'{e:.1e}' for _, e in ra.tried]}, r {ra.rank})",
+                  file=sys.stderr, flush=True)
             del A
     finally:
         pool.terminate()

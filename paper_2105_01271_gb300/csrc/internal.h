@@ -96,9 +96,11 @@ lrs_status launch_sum(lrs_ctx* ctx, const double* part, int np, double* out);
 // W (m x |I|) and W^T (|I| x m), FP32, from one pass over A (WT NULL: W alone)
 lrs_status launch_gather32_both(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int64_t lda,
                                 const GridDev& g, float* W, int64_t ldw, float* WT, int64_t ldwt);
-// sum of squares of A (m x n), FP64, into *out (device)
+// sum of squares of A (m x n), FP64, into *out (device).  FP32 rows are
+// summed in FP32 per thread segment unless exact = 1 (every square in FP64:
+// for a difference of two such sums, e.g. 1 - ||Q^T A||^2 / ||A||^2)
 lrs_status launch_fro2(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int64_t n,
-                       int64_t lda, double* out);
+                       int64_t lda, double* out, int exact = 0);
 
 // gemm_simt.cu / gemm_tc.cu -----------------------------------------------
 // C (M x N) = X^T A ; X: K x M (ldx), A: K x N (lda); row-major everything.

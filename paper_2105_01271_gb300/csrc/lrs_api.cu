@@ -1284,7 +1284,9 @@ lrs_status lrs_range_error(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m
   double* B = r > 0 ? (double*)ws_alloc(ctx, 8 * (size_t)(r * n)) : nullptr;
   double* sq = (double*)ws_alloc(ctx, 16);
   if ((r > 0 && !B) || !sq) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (range_error)");
-  st = launch_fro2(ctx, A, dtype, m, n, lda, sq);
+  // every square in FP64: err^2 = 1 - ||Q^T A||^2 / ||A||^2 cancels, and an
+  // FP32-level ||A||^2 would leave err at ~sqrt(u32) ~ 3e-4
+  st = launch_fro2(ctx, A, dtype, m, n, lda, sq, 1);
   if (st) return st;
   if (r > 0) {
     st = gemm(ctx, LRS_PREC_FP64, r, n, m, Q, LRS_F64, ldq, A, dtype, lda, B, 1, 0, n);

@@ -225,10 +225,10 @@ lrs_status launch_gather(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int
 // aligned to 16 B, FP32 partial squares per row segment, FP64 across them.
 __global__ void __launch_bounds__(256) k_fro2_partial(const void* __restrict__ A, int32_t dt,
                                                       int64_t m, int64_t n, int64_t lda,
-                                                      double* __restrict__ part) {
+                                                      double* __restrict__ part, int exact) {
   __shared__ double red[32];
   double acc = 0.0;
-  const bool vec = dt == LRS_F32 && (n % 4 == 0) && (lda % 4 == 0) &&
+  const bool vec = !exact && dt == LRS_F32 && (n % 4 == 0) && (lda % 4 == 0) &&
                    ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
   for (int64_t t = blockIdx.x; t < m; t += gridDim.x) {
     if (vec) {
@@ -266,12 +266,12 @@ lrs_status launch_sum(lrs_ctx* ctx, const double* part, int np, double* out) {
 }
 
 lrs_status launch_fro2(lrs_ctx* ctx, const void* A, int32_t dt, int64_t m, int64_t n,
-                       int64_t lda, double* out) {
+                       int64_t lda, double* out, int exact) {
   int64_t nb64 = m < (int64_t)ctx->num_sms * 8 ? m : (int64_t)ctx->num_sms * 8;
   const int nb = (int)(nb64 < 1 ? 1 : nb64);
   double* part = (double*)ws_alloc(ctx, sizeof(double) * nb);
   if (!part) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (fro2)");
-  k_fro2_partial<<<nb, 256, 0, ctx->stream>>>(A, dt, m, n, lda, part);
+  k_fro2_partial<<<nb, 256, 0, ctx->stream>>>(A, dt, m, n, lda, part, exact);
   k_sum_partials<<<1, 256, 0, ctx->stream>>>(part, nb, out);
   ctx->launches += 2;
   LRS_CUDA_TRY(ctx, cudaGetLastError());

@@ -338,3 +338,23 @@ def test_range_find_householder_long_columns(lrs):
     np.testing.assert_allclose(Q.T @ Q, np.eye(c), atol=1e-12)
     s = np.linalg.svd(Q.T @ np.linalg.qr(M)[0], compute_uv=False)
     assert np.min(s) >= 1.0 - 1e-9
+
+
+def test_range_error_resolves_small_errors(lrs):
+    """lrs_range_error = sqrt(1 - ||Q^T A||^2 / ||A||^2) cancels: both squared
+    norms are summed with FP64 squares, so a range error near 1e-5 (far below
+    sqrt(u32) ~ 3e-4, far above sqrt(u64)) comes out to a few percent of
+    itself on a wide FP32 matrix."""
+    torch = _torch()
+    from paper_2105_01271_gb300 import binding as b
+    m, n, k = 300, 65536, 20
+    rng = np.random.default_rng(47)
+    A = (rng.standard_normal((m, k)) @ rng.standard_normal((k, n)) +
+         3e-5 * rng.standard_normal((m, n))).astype(np.float32)
+    A64 = A.astype(np.float64)
+    Q = np.linalg.svd(A64, full_matrices=False)[0][:, :k]
+    B = Q.T @ A64
+    ref = np.sqrt(max(0.0, 1.0 - np.sum(B * B) / np.sum(A64 * A64)))
+    assert 1e-6 < ref < 1e-4
+    err = lrs.range_error(_dev(A), b.LRS_F32, m, n, n, _dev(Q), k, k)
+    assert abs(err - ref) <= 0.05 * ref, (err, ref)
