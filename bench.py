@@ -1393,12 +1393,20 @@ def run_ours(args, rank, world):
     copied = [torch.cuda.Event(), torch.cuda.Event()]
     released = [torch.cuda.Event(), torch.cuda.Event()]
 
+    # events around every copy and every step: the split of the e2e time
+    cev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(e2e_steps)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(e2e_steps)]
+
     def copy_in(i):
         b = i % 2
         with torch.cuda.stream(cstream):
             if i >= 2:
                 cstream.wait_event(released[b])
+            cev[i][0].record(cstream)
             dbuf[b].copy_(A_h, non_blocking=True)
+            cev[i][1].record(cstream)
             copied[b].record(cstream)
 
     barrier()
@@ -1412,6 +1420,7 @@ def run_ours(args, rank, world):
         with torch.cuda.stream(stream):
             stream.wait_event(copied[i % 2])
             stream2.wait_event(copied[i % 2])
+            kev[i][0].record(stream)
             if concurrent:
                 step_on(dbuf[i % 2])
                 join_streams()
@@ -1420,12 +1429,15 @@ def run_ours(args, rank, world):
                 path.svd_from_pass(ctx, dbuf[i % 2], w.dtype, w.grid, w.k, w.q, gc_, rtol, prec, bufs)
                 path.id_from_pass(ctx, w.m, w.grid, w.k, g0_, bufs)
             released[i % 2].record(stream)
+            kev[i][1].record(stream)
             for ho, o in zip(host_outs, outs):
                 ho.copy_(o, non_blocking=True)
     f1.record(stream)
     stream.synchronize()
     barrier()
     e2e_ms = max_over_ranks(f0.elapsed_time(f1) / e2e_steps, world, f"cuda:{dev}")
+    e2e_copy_ms = statistics.mean(a.elapsed_time(b) for a, b in cev)
+    e2e_step_ms = statistics.mean(a.elapsed_time(b) for a, b in kev)
     # the bare pinned host -> device copy rate of the same buffer, for scale
     c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(cstream):
@@ -1475,7 +1487,8 @@ def run_ours(args, rank, world):
            "e2e": {"value": job_throughput(world, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms, "steps": e2e_steps,
                    "overlap": "H2D of step i+1 on a copy stream during step i (two device buffers)",
-                   "h2d_copy_gbs": h2d_gbs},
+                   "h2d_copy_gbs": h2d_gbs, "copy_ms_in_loop": e2e_copy_ms,
+                   "step_ms_in_loop": e2e_step_ms},
            "result": {"err_est_svd": s.err_est, "r": s.r, "err_est_id": d.err_est},
            "phases_ms": phases,
            "other_arrangement_ms_per_step": other_ms}
