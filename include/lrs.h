@@ -181,8 +181,8 @@ lrs_status lrs_range_find_diag(lrs_ctx* ctx, const double* G, int64_t m, int64_t
 /*
  * lrs_svd_k -- TPC-SVD from a range basis (Sec. 3.1, Alg. 2):
  *   B = Q^T A_f (r x n; the one full read of A_f; ||A_f||_F^2 fused),
- *   SVD(B) via the R factor of B^T (FP32 B: a double-float Gram B B^T and an
- *   FP64 Cholesky; FP64 B: the pivoted QR of B^T) and one-sided Jacobi,
+ *   SVD(B) via the R factor of B^T (FP32 B: the Gram B B^T as an exact-slice
+ *   product on the tensor cores, ~2^-46 relative, and an FP64 Cholesky; FP64 B: the pivoted QR of B^T) and one-sided Jacobi,
  *   U_k = Q U_B(:,1:k), S_k, V_k = B^T U_B(:,1:k) S_k^{-1}.
  *   A   m x n in dtype, row stride lda.    Q  m x r FP64, row stride ldq.
  *   U   m x k FP64 (row stride ldu).       S  k FP64.
@@ -281,14 +281,15 @@ lrs_status lrs_apass_slab(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m,
 /*
  * lrs_slab_factor -- F (r x r FP64, row stride ldf) with F F^T = B B^T for
  * B from lrs_apass_slab (r x n, row stride n, typed by prec).
- *   LRS_FACTOR_GRAM  F = B B^T by the double-float Gram of lrs_svd_k
- *                    (FP32 B, r <= 128); the devices' F add up to the full
- *                    Gram.
+ *   LRS_FACTOR_GRAM  F = B B^T by the exact-slice tensor-core Gram of
+ *                    lrs_svd_k (FP32 B, r <= 128; B cut into six BF16
+ *                    slices per row, slice products summed exactly); the
+ *                    devices' F add up to the full Gram.
  *   LRS_FACTOR_R     F = R^T, R the R factor of B^T (pivoted QR for FP64 B,
  *                    Householder TSQR otherwise; n >= r); [F_1 ... F_P]
  *                    then has the full Gram as its Gram, without squaring
  *                    B's condition number.
- * Asynchronous except for the pivoted QR's rank read-back.
+ * Synchronises (the Gram's error flag; the pivoted QR's rank).
  */
 lrs_status lrs_slab_factor(lrs_ctx* ctx, const void* B, int64_t r, int64_t n, int32_t prec, int32_t mode, double* F,
                            int64_t ldf);
@@ -357,7 +358,7 @@ lrs_status lrs_spc_lift(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m, i
  *   eps_hat[i] = c * lambda_max(B_f B_f^T - taus[i] B_c B_c^T),  i < ntau,
  * the estimate of eps(tau) in the SPC-ID error bound, for each tau >= 0 of the
  * caller's grid (the bound minimises over tau together with its other terms).
- * Grams in FP64 (FP32 data: double-float accumulation); lambda_max by
+ * Grams in FP64 (FP32 data: the exact-slice tensor-core Gram); lambda_max by
  * Householder tridiagonalisation and Sturm-count bisection (one block per tau).
  *   A  m x n in dtype (row stride lda).   Y  m x l FP64 (row stride ldy).
  *   taus, eps_hat: HOST arrays of ntau doubles.  Synchronises.

@@ -226,16 +226,17 @@ lrs_status launch_orth_wide(lrs_ctx* ctx, const double* M, int64_t p, int64_t c,
 lrs_status launch_abs_diag(lrs_ctx* ctx, const double* R, int64_t ld, int64_t r, double* out);
 
 // R (r x r upper, row-major, positive diagonal) with R^T R = B B^T for a wide
-// FP32 B (r x n, r <= 128): double-float Gram on the FP32 pipe + FP64
+// FP32 B (r x n, r <= 128): exact-slice Gram on the tensor cores + FP64
 // Cholesky.  With perm_out (device, r entries) the Cholesky is pivoted:
 // P^T B B^T P = R^T R, perm_out[pos] = row of B.  LRS_ERANK (nothing
 // reported) when the Cholesky breaks down; the caller then runs TSQR.
 // Synchronises.
 size_t r_of_bt_gram_ws(int64_t r, int num_sms);
 // G (r x r FP64, both triangles) = B B^T for B r x n FP32 (row stride ldb),
-// double-float accumulation (r <= 128); workspace gram_df_ws(r, num_sms)
-size_t gram_df_ws(int64_t r, int num_sms);
-lrs_status launch_gram_df(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, int64_t ldb, double* G);
+// r <= 128: an exact-slice product on the tensor cores (~2^-46 relative);
+// workspace gram_oz_ws(r, num_sms).  Synchronises (error flag).
+size_t gram_oz_ws(int64_t r, int num_sms);
+lrs_status launch_gram_oz(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, int64_t ldb, double* G);
 lrs_status launch_r_of_bt_gram(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, int64_t ldb, double* R,
                                int32_t* perm_out = nullptr);
 

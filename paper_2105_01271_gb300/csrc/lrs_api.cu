@@ -928,7 +928,7 @@ lrs_status svd_from_b(lrs_ctx* ctx, const void* B, int64_t r, int64_t n, const d
   double* sv = (double*)ws_alloc(ctx, 8 * (size_t)r);
   double* QT = (double*)ws_alloc(ctx, 8 * (size_t)(m * r));
   if (!Rm || !Vr || !sv || !QT) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd)");
-  // SVD(B), all in FP64 once B exists.  FP32 B: R from the double-float Gram
+  // SVD(B), all in FP64 once B exists.  FP32 B: R from the exact-slice Gram
   // and a PIVOTED FP64 Cholesky (P^T B B^T P = R^T R), then the FP64
   // one-sided Jacobi on the rows of R across a thread-block cluster, U_B =
   // P U' (jacobi_cluster.cu); TSQR if the Cholesky breaks down.  FP64 B: R
@@ -1091,15 +1091,15 @@ lrs_status lrs_slab_factor(lrs_ctx* ctx, const void* B, int64_t r, int64_t n, in
   }
   LRS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   size_t need = 2 * align256(8 * (size_t)(r * r)) + 1024;
-  if (mode == LRS_FACTOR_GRAM) need += gram_df_ws(r, ctx->num_sms);
+  if (mode == LRS_FACTOR_GRAM) need += gram_oz_ws(r, ctx->num_sms);
   else need += tsqr_ws(r, n, f64 ? 8 : 4) + 2 * align256(8 * (size_t)(n * r)) + cpqr_ws(n, r, r) + 1024;
   lrs_status st = ws_reserve(ctx, need);
   if (st) return st;
   double* Rm = (double*)ws_alloc(ctx, 8 * (size_t)(r * r));
   if (!Rm) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (slab_factor)");
   if (mode == LRS_FACTOR_GRAM) {
-    // F = B B^T, the double-float Gram of the SVD path, rounded to FP64
-    st = launch_gram_df(ctx, (const float*)B, r, n, n, ldf == r ? F : Rm);
+    // F = B B^T, the exact-slice tensor-core Gram of the SVD path
+    st = launch_gram_oz(ctx, (const float*)B, r, n, n, ldf == r ? F : Rm);
     if (st) return st;
     if (ldf != r)
       LRS_CUDA_TRY(ctx, cudaMemcpy2DAsync(F, ldf * 8, Rm, r * 8, r * 8, r, cudaMemcpyDeviceToDevice, ctx->stream));

@@ -333,126 +333,6 @@ lrs_status trsm_rows(lrs_ctx* ctx, const double* M, int64_t p, int64_t ldm, cons
   return LRS_OK;
 }
 
-// ---------------------------------------------------------------------------
-// G = B B^T for a wide FP32 B (r x n row-major, r <= 128), accurate to ~2^-44
-// relative per entry on the FP32 pipe: each product a b is made exact as
-// p + e by Dekker's two-product (p = a b rounded, e = fma(a, b, -p)), and each
-// entry keeps a double-float sum (Knuth's two-sum carries the rounding error
-// of every addition into the low word).  Blocks take column ranges; per-block
-// (hi, lo) partials of the packed upper triangle are combined in FP64 in
-// block order.
-constexpr int kDfCols = 64;             // columns staged per pass
-
-// Thread layout: the upper triangle of G in 4 x 4 tiles (tile (ti, tj),
-// ti <= tj), dealt round-robin, TPT tiles per thread; the block has just
-// enough whole warps for its tiles (the launch sizes it), so few threads idle.
-// The staged columns are stored transposed (row index fastest): per staged
-// column a tile loads its two 4-row groups as two 16-byte words
-// (conflict-free: a warp's tiles share ti and take consecutive tj) and
-// updates 16 double-float sums.  The output is a full r x r partial per
-// block; only entries (i, j) with i/4 <= j/4 are written.
-constexpr int kDfMaxThreads = 256;
-
-template <int TPT>
-__global__ void __launch_bounds__(kDfMaxThreads) k_gram_df(const float* __restrict__ B, int r, int64_t n,
-                                                           int64_t ldb, int64_t cols_b, float* __restrict__ part_hi,
-                                                           float* __restrict__ part_lo) {
-  extern __shared__ float4 tf4[];                  // kDfCols x rp floats (column t at t * rp), rp = r rounded up to 4
-  float* tf = reinterpret_cast<float*>(tf4);
-  const int nt = (r + 3) / 4, ntiles = nt * (nt + 1) / 2, rp = nt * 4;
-  const int nth = blockDim.x;
-  const int64_t c0 = (int64_t)blockIdx.x * cols_b;
-  const int64_t c1 = min(n, c0 + cols_b);
-  // entry (u, v) of a tile lives in pair u * 2 + v / 2, half v % 2
-  uint64_t sh[TPT][8], sl[TPT][8];
-  int ti[TPT], tj[TPT];
-#pragma unroll
-  for (int q = 0; q < TPT; ++q) {
-    const int e = threadIdx.x + q * nth;
-    int a = 0, b = 0;
-    if (e < ntiles) tri_ij(e, nt, a, b);
-    ti[q] = e < ntiles ? a : -1;
-    tj[q] = b;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) { sh[q][u] = 0ull; sl[q][u] = 0ull; }
-  }
-  for (int64_t a0 = c0; a0 < c1; a0 += kDfCols) {
-    const int nc = (int)min((int64_t)kDfCols, c1 - a0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < rp * kDfCols; e += nth) {
-      const int i = e / kDfCols, t = e - i * kDfCols;     // a row's 64 columns: coalesced reads
-      tf[t * rp + i] = (t < nc && i < r) ? B[(int64_t)i * ldb + a0 + t] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < TPT; ++q) {
-      if (ti[q] < 0) continue;
-      for (int t = 0; t < nc; ++t) {
-        const float4 a4 = tf4[(t * rp) / 4 + ti[q]], b4 = tf4[(t * rp) / 4 + tj[q]];
-        const float va[4] = {a4.x, a4.y, a4.z, a4.w};
-        const uint64_t bp[2] = {f2_pack(b4.x, b4.y), f2_pack(b4.z, b4.w)};
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const uint64_t A = f2_pack(va[u], va[u]), nA = f2_pack(-va[u], -va[u]);
-#pragma unroll
-          for (int vp = 0; vp < 2; ++vp) {
-            // per lane: p = RN(a b); -pe = p - a b exactly (one FMA); two-sum of
-            // h + p; the low word collects err + pe.  Inline PTX: nothing is
-            // contracted, so the error-free transformations stay exact.
-            const uint64_t p = f2_mul(A, bp[vp]);
-            const uint64_t npe = f2_fma(nA, bp[vp], p);
-            uint64_t& h = sh[q][u * 2 + vp];
-            const uint64_t s2 = f2_add(h, p);
-            const uint64_t bb = f2_sub(s2, h);
-            const uint64_t err = f2_add(f2_sub(h, f2_sub(s2, bb)), f2_sub(p, bb));
-            h = s2;
-            sl[q][u * 2 + vp] = f2_add(sl[q][u * 2 + vp], f2_sub(err, npe));
-          }
-        }
-      }
-    }
-  }
-  float* oh = part_hi + (int64_t)blockIdx.x * r * r;
-  float* ol = part_lo + (int64_t)blockIdx.x * r * r;
-#pragma unroll
-  for (int q = 0; q < TPT; ++q) {
-    if (ti[q] < 0) continue;
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int vp = 0; vp < 2; ++vp) {
-        float h0, h1, l0, l1;
-        f2_unpack(sh[q][u * 2 + vp], h0, h1);
-        f2_unpack(sl[q][u * 2 + vp], l0, l1);
-        const int i = ti[q] * 4 + u, j = tj[q] * 4 + vp * 2;
-        if (i < r && j < r) { oh[i * r + j] = h0; ol[i * r + j] = l0; }
-        if (i < r && j + 1 < r) { oh[i * r + j + 1] = h1; ol[i * r + j + 1] = l1; }
-      }
-  }
-}
-
-// G (r x r, FP64) = sum over the block partials; entry (i, j) is read from
-// the upper tile that holds it.  A warp per entry, lanes over blocks, fixed
-// shuffle tree (deterministic).
-__global__ void k_gram_df_reduce(const float* __restrict__ hi, const float* __restrict__ lo, int nb, int r,
-                                 double* __restrict__ G) {
-  const int lane = threadIdx.x & 31;
-  const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwt = (gridDim.x * blockDim.x) >> 5;
-  for (int e = w0; e < r * r; e += nwt) {
-    const int i = e / r, j = e - i * r;
-    const int src = (i / 4 <= j / 4) ? e : j * r + i;
-    double a0 = 0.0, a1 = 0.0;
-    int b = lane;
-    for (; b + 32 < nb; b += 64) {
-      a0 += (double)hi[(int64_t)b * r * r + src] + (double)lo[(int64_t)b * r * r + src];
-      a1 += (double)hi[(int64_t)(b + 32) * r * r + src] + (double)lo[(int64_t)(b + 32) * r * r + src];
-    }
-    for (; b < nb; b += 32) a0 += (double)hi[(int64_t)b * r * r + src] + (double)lo[(int64_t)b * r * r + src];
-    const double sum = warp_sum(a0 + a1);
-    if (lane == 0) G[e] = sum;
-  }
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -604,41 +484,9 @@ lrs_status launch_orth_gram(lrs_ctx* ctx, const double* M, int64_t p, int64_t c,
 
 namespace lrs {
 
-size_t gram_df_ws(int64_t r, int num_sms) {
-  auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
-  return 2 * a256(sizeof(float) * 2 * (size_t)num_sms * (size_t)(r * r)) + 512;
-}
-
 size_t r_of_bt_gram_ws(int64_t r, int num_sms) {
   auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
-  return gram_df_ws(r, num_sms) + a256(sizeof(double) * (size_t)(r * r)) + a256(4 * (size_t)r) + a256(8) + 512;
-}
-
-lrs_status launch_gram_df(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, int64_t ldb, double* G) {
-  if (r < 1 || r > kMaxC || n < 1) return lrs_fail(ctx, LRS_EINVAL, "gram: r=%lld n=%lld out of range", (long long)r, (long long)n);
-  const int ri = (int)r;
-  const int nt = (ri + 3) / 4, ntiles = nt * (nt + 1) / 2;
-  int64_t nb = 2 * (int64_t)ctx->num_sms;         // two blocks per SM: few tiles leave warps idle
-  int64_t cols_b = (n + nb - 1) / nb;
-  if (cols_b < kDfCols) cols_b = kDfCols;
-  nb = (n + cols_b - 1) / cols_b;
-  float* hi = (float*)ws_alloc(ctx, sizeof(float) * (size_t)(nb * r * r));
-  float* lo = (float*)ws_alloc(ctx, sizeof(float) * (size_t)(nb * r * r));
-  if (!hi || !lo) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (double-float gram)");
-  const size_t dyn = sizeof(float) * (size_t)(nt * 4 * kDfCols);
-  // tiles per thread and just enough whole warps for them
-  int tpt = 1;
-  while (tpt < 3 && (ntiles + tpt - 1) / tpt > kDfMaxThreads) ++tpt;
-  int th = ((ntiles + tpt - 1) / tpt + 31) / 32 * 32;
-  if (th > kDfMaxThreads) th = kDfMaxThreads;
-  if (tpt == 1) k_gram_df<1><<<(unsigned)nb, th, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
-  else if (tpt == 2) k_gram_df<2><<<(unsigned)nb, th, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
-  else k_gram_df<3><<<(unsigned)nb, th, dyn, ctx->stream>>>(B, ri, n, ldb, cols_b, hi, lo);
-  ctx->launches++;
-  k_gram_df_reduce<<<(ri * ri + 7) / 8, 256, 0, ctx->stream>>>(hi, lo, (int)nb, ri, G);
-  ctx->launches++;
-  LRS_CUDA_TRY(ctx, cudaGetLastError());
-  return LRS_OK;
+  return gram_oz_ws(r, num_sms) + a256(sizeof(double) * (size_t)(r * r)) + a256(4 * (size_t)r) + a256(8) + 512;
 }
 
 lrs_status launch_r_of_bt_gram(lrs_ctx* ctx, const float* B, int64_t r, int64_t n, int64_t ldb, double* R,
@@ -649,7 +497,7 @@ lrs_status launch_r_of_bt_gram(lrs_ctx* ctx, const float* B, int64_t r, int64_t 
   int32_t* perm = perm_out ? perm_out : (int32_t*)ws_alloc(ctx, 4 * (size_t)r);
   int32_t* rank = (int32_t*)ws_alloc(ctx, 8);
   if (!G || !perm || !rank) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (svd gram)");
-  lrs_status gs = launch_gram_df(ctx, B, r, n, ldb, G);
+  lrs_status gs = launch_gram_oz(ctx, B, r, n, ldb, G);
   if (gs) return gs;
   // pivoted when the caller takes the permutation (P^T B B^T P = R^T R)
   lrs_status st = pchol(ctx, G, ri, ri, 0.0, perm_out ? 1 : 0, perm, R, r, rank);

@@ -14,7 +14,7 @@
 // Error estimate.  Every c-th snapshot, B_f = A_f(J,:), B_c = A_c(J,:):
 //     eps_hat(tau) = c lambda_max(B_f B_f^T - tau B_c B_c^T)
 // for each tau of a caller-given grid.  The m_c x m_c Grams are FP64 (FP32
-// data: the double-float Gram of the SVD path), and lambda_max comes from one
+// data: the exact-slice Gram of the SVD path), and lambda_max comes from one
 // block per tau: Householder tridiagonalisation in shared memory, then
 // bisection on Sturm counts.
 #include "common.cuh"
@@ -287,7 +287,7 @@ lrs_status spc_err_rows(lrs_ctx* ctx, const void* Bf, int32_t dtype, int64_t mc,
     return lrs_fail(ctx, LRS_EINVAL, "spc_err: m_c = %lld kept rows outside [1, %d]", (long long)mc, kEigMax);
   for (int32_t i = 0; i < ntau; ++i)
     if (!(taus[i] >= 0.0) || !isfinite(taus[i])) return lrs_fail(ctx, LRS_EINVAL, "spc_err: tau[%d] = %g", i, taus[i]);
-  const size_t gram_ws = dtype == LRS_F32 ? gram_df_ws(mc, ctx->num_sms) : row_gram_ws(mc, ctx->num_sms);
+  const size_t gram_ws = dtype == LRS_F32 ? gram_oz_ws(mc, ctx->num_sms) : row_gram_ws(mc, ctx->num_sms);
   const size_t need = 2 * 8 * (size_t)(mc * mc) + 16 * (size_t)ntau + 4 * (size_t)ntau + gram_ws +
                       row_gram_ws(mc, ctx->num_sms) + 8192;
   lrs_status st = ws_reserve(ctx, need);
@@ -298,7 +298,7 @@ lrs_status spc_err_rows(lrs_ctx* ctx, const void* Bf, int32_t dtype, int64_t mc,
   double* dout = (double*)ws_alloc(ctx, 8 * (size_t)ntau);
   if (!Gf || !Gc || !dtau || !dout) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (spc_err)");
   const size_t mark = ctx->ws_top;
-  if (dtype == LRS_F32) st = launch_gram_df(ctx, (const float*)Bf, mc, n, ldb, Gf);
+  if (dtype == LRS_F32) st = launch_gram_oz(ctx, (const float*)Bf, mc, n, ldb, Gf);
   else st = row_gram(ctx, Bf, dtype, mc, n, ldb, Gf);
   if (st) return st;
   ctx->ws_top = mark;
