@@ -115,12 +115,13 @@ __device__ __forceinline__ bool better(double a, int pa, double b, int pb) { ret
 // block is always [j+1, c)^2 and row j of the working matrix becomes row j of
 // R (rows < j hold R, and their columns j and piv are swapped with the rest).
 // Only the upper triangle is stored and updated (sym(a, b) = G[min][max]).
-// Per step: every warp finds the argmax of the remaining diagonal itself (the
-// remaining column norm^2, lowest position on ties; the same answer in every
-// warp, no barrier) and one lane takes the square root and the stop test |
-// swap and scale row j (each thread owns one index a and the two cells of a)
-// | Schur update of the remaining upper triangle, a warp per row.  Three
-// block barriers per step.
+// Per step, two block barriers:
+//   swap and scale row j (each thread owns one index a and the two cells of a)
+//   | Schur update of the remaining upper triangle: warp 0 takes the diagonal
+//     and, from the values it just wrote, the next pivot (the largest remaining
+//     diagonal, lowest position on ties), its inverse square root and the stop
+//     test; warps 1.. take the entries above the diagonal, rows k and n-2-k of
+//     the n remaining paired into one run of n entries so every run is as long.
 // Outputs: perm[pos] = physical column, R (rows 0..rank-1, row-major ldr,
 // pivoted order, zero below the diagonal), *rank.
 __global__ void __launch_bounds__(256) k_pchol(const double* __restrict__ Gin, int c, int kmax, double rtol,
@@ -137,38 +138,43 @@ __global__ void __launch_bounds__(256) k_pchol(const double* __restrict__ Gin, i
     for (int b2 = lane; b2 < c; b2 += 32) G[a * ld + b2] = Gin[a * c + b2];
   for (int q = threadIdx.x; q < c; q += blockDim.x) phys_at[q] = q;
   __syncthreads();
-  int j = 0;
-  for (;; ++j) {
-    // ---- pivot: every warp reduces the remaining diagonal itself -------------
-    double bv = -1.0;
-    int bp = 0x7fffffff;
-    if (pivot) {
-      for (int q = j + lane; q < c; q += 32) {
-        const double d = G[q * ld + q];
-        if (norm_key(d) > norm_key(bv)) { bv = d; bp = q; }
-      }
+
+  // the pivot of step jn from the remaining diagonal, one warp; the lane
+  // holding position q has its (just written) value in dval when mine(q)
+  auto decide = [&](int jn, double bv, int bp) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        const int op = __shfl_xor_sync(0xffffffffu, bp, o);
-        if (better(ov, op, bv, bp)) { bv = ov; bp = op; }
-      }
-    } else if (j < c) {
-      bv = G[j * ld + j]; bp = j;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+      if (better(ov, op, bv, bp)) { bv = ov; bp = op; }
     }
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
+      if (!pivot) { bp = jn; bv = jn < c ? G[jn * ld + jn] : -1.0; }
       // R_jj = sqrt(d), 1 / R_jj = rsqrt(d); the stop test |R_jj| <= rtol |R_00|
       // is taken on the squares, d <= rtol^2 d_0
       const double y = bv > 0.0 ? rsqrt_fast(bv) : 0.0;
-      if (j == 0) s_top = bv;
-      const bool stop = (j >= kmax) || j >= c || !(bv > 0.0) || (j > 0 && bv <= rtol * rtol * s_top);
+      if (jn == 0) s_top = bv;
+      const bool stop = (jn >= kmax) || jn >= c || !(bv > 0.0) || (jn > 0 && bv <= rtol * rtol * s_top);
       s_stop = stop ? 1 : 0;
       if (!stop) {
-        if (bp != j) { const int t = phys_at[j]; phys_at[j] = phys_at[bp]; phys_at[bp] = t; }
+        if (bp != jn) { const int t = phys_at[jn]; phys_at[jn] = phys_at[bp]; phys_at[bp] = t; }
         s_piv = bp; s_ljj = bv * y; s_inv = y;
       }
     }
-    __syncthreads();
+  };
+  if (wid == 0) {
+    double bv = -1.0;
+    int bp = 0x7fffffff;
+    if (pivot)
+      for (int q = lane; q < c; q += 32) {
+        const double d = G[q * ld + q];
+        if (norm_key(d) > norm_key(bv)) { bv = d; bp = q; }
+      }
+    decide(0, bv, bp);
+  }
+  __syncthreads();
+  int j = 0;
+  for (;; ++j) {
     if (s_stop) break;
     const int pv = s_piv;
     const double inv = s_inv;
@@ -201,21 +207,36 @@ __global__ void __launch_bounds__(256) k_pchol(const double* __restrict__ Gin, i
     }
     __syncthreads();
     // ---- Schur complement, upper triangle: S_ab -= R_ja R_jb (j < a <= b) -----
-    // the n (n + 1) / 2 entries dealt evenly over the block (one FMA each; a
-    // row per warp would leave the short rows' lanes idle), entry e counted
-    // from the end: f = T - 1 - e lies in the k-th row from the bottom with
-    // k (k + 1) / 2 <= f < (k + 1) (k + 2) / 2
-    {
-      const int n = c - j - 1;
-      const int T = n * (n + 1) / 2;
-      for (int e = threadIdx.x; e < T; e += blockDim.x) {
-        const int f = T - 1 - e;
-        int k = (int)((sqrtf(8.0f * (float)f + 1.0f) - 1.0f) * 0.5f);
-        if ((k + 1) * (k + 2) / 2 <= f) ++k;
-        if (k * (k + 1) / 2 > f) --k;
-        const int a = j + 1 + (n - 1 - k);
-        const int b2 = j + 1 + (n - 1 - (f - k * (k + 1) / 2));
-        G[a * ld + b2] = fma(-G[j * ld + a], G[j * ld + b2], G[a * ld + b2]);
+    const int n = c - j - 1;
+    if (wid == 0) {
+      // the diagonal, then the next pivot from it
+      double bv = -1.0;
+      int bp = 0x7fffffff;
+      for (int a = j + 1 + lane; a < c; a += 32) {
+        const double rja = G[j * ld + a];
+        const double d = fma(-rja, rja, G[a * ld + a]);
+        G[a * ld + a] = d;
+        if (pivot && norm_key(d) > norm_key(bv)) { bv = d; bp = a; }
+      }
+      __syncwarp();
+      decide(j + 1, bv, bp);
+    } else if (n > 1) {
+      // above the diagonal: row k (a = j+1+k) has n-1-k entries; rows k and
+      // n-2-k together have n, k < n-1-k (the middle row alone when n is even)
+      const int runs = n / 2;                       // pairs, plus the middle row when n is even
+      for (int v = wid - 1; v < runs; v += nw - 1) {
+        const int k2 = n - 2 - v;
+        const int len0 = n - 1 - v;                 // entries of row v
+        const int len = (k2 == v) ? len0 : n;       // the middle row is alone
+        const int a0 = j + 1 + v, a1 = j + 1 + k2;
+        const double r0 = G[j * ld + a0], r1 = G[j * ld + a1];
+        for (int e = lane; e < len; e += 32) {
+          int a, b2;
+          double ra;
+          if (e < len0) { a = a0; b2 = a0 + 1 + e; ra = r0; }
+          else { a = a1; b2 = a1 + 1 + (e - len0); ra = r1; }
+          G[a * ld + b2] = fma(-ra, G[j * ld + b2], G[a * ld + b2]);
+        }
       }
     }
     __syncthreads();
