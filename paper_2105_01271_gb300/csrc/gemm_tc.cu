@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcParams P) {
   using Cfg = TcCfg<ADT, SA, SX, NS>;
   using VT = typename std::conditional<ADT == LRS_F64, double, float>::type;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full_a[NS], full_x[NS], empty[NS], tmem_full, tmem_empty;
+  __shared__ __align__(8) uint64_t full_a[NS], full_x[NS], empty[NS], tmem_full[2], tmem_empty[2];
   __shared__ uint32_t tmem_base_sh;
 
   const uint32_t raw = smem_u32(smem_raw);
@@ -157,11 +157,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcParams P) {
       mbar_init(&full_x[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&tmem_full, 1);
-    mbar_init(&tmem_empty, kConvWarps);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tmem_full[b], 1);
+      mbar_init(&tmem_empty[b], kConvWarps);
+    }
     fence_mbar_init();
   }
-  if (warp == kConvWarps) tmem_alloc(&tmem_base_sh, TBN);
+  // two accumulators: the epilogue of one tile runs under the MMAs of the next
+  if (warp == kConvWarps) tmem_alloc(&tmem_base_sh, 2 * TBN);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -263,24 +266,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcParams P) {
       }
       if (!ok) break;
       // ---------------- epilogue: TMEM -> C ----------------
+      const int abuf = tcount & 1;
       {
         int w_ok = 1;
-        if (lane == 0) w_ok = mbar_wait(&tmem_full, (uint32_t)(tcount & 1), P.err) ? 1 : 0;
+        if (lane == 0) w_ok = mbar_wait(&tmem_full[abuf], (uint32_t)((tcount >> 1) & 1), P.err) ? 1 : 0;
         w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
         if (!w_ok) { ok = false; break; }
       }
       tc_fence_after();
       const int q4 = warp & 3, half = warp >> 2;
       const int64_t m = mt * TBM + q4 * 32 + lane;
+      // FP32 C with alpha = 1 and no accumulation: the values as they are (the
+      // FP64 route below rounds 1.0 * v back to v), 16-byte stores when aligned
+      const bool plain = !P.c_f64 && !P.accum && !P.c_trans && P.alpha == 1.0 && P.splits == 1;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         uint32_t v[16];
         const int col = half * 64 + j * 16;
-        tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)col, v);
+        tmem_ld16(tmem + (uint32_t)(abuf * TBN) + ((uint32_t)(q4 * 32) << 16) + (uint32_t)col, v);
         tmem_ld_wait();
         if (m < P.M) {
           const int64_t nb = nt * TBN + col;
-          if (P.splits > 1) {
+          if (plain) {
+            float* c = reinterpret_cast<float*>(P.C) + m * P.ldc + nb;
+            if (nb + 16 <= P.N && ((reinterpret_cast<uintptr_t>(c) & 15u) == 0)) {
+#pragma unroll
+              for (int e = 0; e < 16; e += 4)
+                *reinterpret_cast<float4*>(c + e) = make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]),
+                                                                __uint_as_float(v[e + 2]), __uint_as_float(v[e + 3]));
+            } else {
+#pragma unroll
+              for (int e = 0; e < 16; ++e)
+                if (nb + e < P.N) c[e] = __uint_as_float(v[e]);
+            }
+          } else if (P.splits > 1) {
             float* dst = P.partial + ((tile / (P.Mt * P.Nt)) * P.M + m) * P.N;
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
@@ -308,7 +327,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcParams P) {
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&tmem_empty);
+      if (lane == 0) mbar_arrive(&tmem_empty[abuf]);
     }
     if (P.fro2_part) {
       // per-CTA partial of ||A||_F^2 (fixed reduction order -> deterministic)
@@ -330,8 +349,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcParams P) {
       int tcount = 0;
       bool ok = true;
       for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tcount) {
-        if (!mbar_wait(&tmem_empty, (uint32_t)((tcount & 1) ^ 1), P.err)) break;
+        const int abuf = tcount & 1;
+        if (!mbar_wait(&tmem_empty[abuf], (uint32_t)(((tcount >> 1) & 1) ^ 1), P.err)) break;
         tc_fence_after();
+        const uint32_t dacc = tmem + (uint32_t)(abuf * TBN);
         int64_t kt_lo, kt_hi;
         kt_range(tile, kt_lo, kt_hi);
         for (int64_t kt = kt_lo; kt < kt_hi; ++kt, ++it) {
@@ -351,14 +372,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcParams P) {
                 if (i + j >= Cfg::kP) continue;
                 const uint64_t ad = sdesc_kmajor_sw128(x0 + j * kPieceBytes + kk * 32);
                 const uint64_t bd = sdesc_kmajor_sw128(a0 + i * kPieceBytes + kk * 32);
-                umma_bf16(tmem, ad, bd, idesc, first ? 0u : 1u);
+                umma_bf16(dacc, ad, bd, idesc, first ? 0u : 1u);
                 first = 0;
               }
           }
           umma_commit(&empty[s]);
         }
         if (!ok) break;
-        umma_commit(&tmem_full);
+        umma_commit(&tmem_full[abuf]);
       }
     }
     __syncwarp();
@@ -404,7 +425,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gemm_tc(TcParams P) {
   __syncthreads();
   if (warp == kConvWarps) {
     tc_fence_after();
-    tmem_dealloc(tmem, TBN);
+    tmem_dealloc(tmem, 2 * TBN);
   }
 }
 
