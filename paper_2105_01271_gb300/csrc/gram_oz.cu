@@ -36,9 +36,9 @@
 //
 // Diagonal.  X_33 (level 6) is dropped and acc_4 truncates; off the diagonal
 // both errors have random signs, but on it every X_tt term is >= 0, a bias
-// of ~2^-44.  So G_ii = sum_k x_ik^2 is summed apart: the slicing threads
-// square x's 24-bit significand in integer arithmetic and add it, rounded to
-// 2^-50, in int64.
+// of ~2^-44.  So G_ii = sum_k x_ik^2 is summed apart, without bias: per slab
+// the slicing threads sum eight squares error-free in FP32 (x^2 = h + l by one
+// FMA, Knuth's two-sum) and add both words, rounded to 2^-50, in int64.
 //
 // Drain.  After each chunk the accumulators are read back (tcgen05.ld) and
 // added into one int64 per entry in units of 2^-49: levels 0-3 exactly
@@ -76,20 +76,21 @@ constexpr int64_t kOzRangeMax = 16384;          // columns per int64 range
 constexpr size_t kOzSmem = (size_t)kOzStages * kOzStage + 1024;
 
 // slice products: A operand buffer, B operand buffer, accumulator
+// (grouped by A operand, so consecutive MMAs share it)
 __host__ __device__ constexpr int oz_prod_a(int p) {
-  constexpr int t[13] = {0, 0, 0, 2, 1, 0, 1, 0, 1, 6, 0, 1, 2};
+  constexpr int t[13] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 2, 2, 6};
   return t[p];
 }
 __host__ __device__ constexpr int oz_prod_b(int p) {
-  constexpr int t[13] = {0, 1, 2, 0, 1, 3, 2, 4, 3, 2, 5, 4, 3};
+  constexpr int t[13] = {0, 1, 2, 3, 4, 5, 1, 2, 3, 4, 0, 3, 2};
   return t[p];
 }
 __host__ __device__ constexpr int oz_prod_acc(int p) {
-  constexpr int t[13] = {0, 1, 2, 2, 2, 3, 3, 4, 4, 4, 4, 4, 4};
+  constexpr int t[13] = {0, 1, 2, 3, 4, 4, 2, 3, 4, 4, 2, 4, 4};
   return t[p];
 }
 // the first product of each accumulator in the table (zero-initialises it)
-__host__ __device__ constexpr bool oz_first(int p) { return p == 0 || p == 1 || p == 2 || p == 5 || p == 7; }
+__host__ __device__ constexpr bool oz_first(int p) { return p < 5; }
 
 struct OzParams {
   const float* B;
@@ -127,16 +128,18 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
                : "r"(taddr));
 }
 
-// round(x^2 2^50) for |x| < 1/2, in integer arithmetic on the significand
-// (x = m 2^(E-150), so x^2 2^50 = m^2 2^(2E-250)); round half up
-__device__ __forceinline__ long long oz_sq50(float x) {
-  const uint32_t bits = __float_as_uint(x) & 0x7fffffffu;
-  const int E = (int)(bits >> 23);
-  const uint32_t m = (bits & 0x7fffffu) | (E ? 0x800000u : 0u);
-  const int rs = 250 - 2 * (E ? E : 1);            // >= 0 for |x| < 1/2
-  if (rs >= 64) return 0;
-  const unsigned long long m2 = (unsigned long long)m * m;
-  return (long long)((m2 + ((1ull << rs) >> 1)) >> rs);
+// round(v 2^50) for |v| < 2^12, from v's significand in integer arithmetic
+// (v = m 2^(E-150)); round half up
+__device__ __forceinline__ long long oz_ll50(float v) {
+  const uint32_t bits = __float_as_uint(v);
+  const int E = (int)((bits >> 23) & 0xffu);
+  const long long m = (long long)((bits & 0x7fffffu) | (E ? 0x800000u : 0u));
+  const int sh = (E ? E : 1) - 100;                 // v 2^50 = m 2^sh
+  long long q;
+  if (sh >= 0) q = m << sh;
+  else if (sh > -63) q = (m + ((1ll << -sh) >> 1)) >> -sh;
+  else q = 0;
+  return (bits >> 31) ? -q : q;
 }
 
 // round-to-nearest integer of v, |v| <= 2^22, by FP32 addition alone: in
@@ -218,17 +221,28 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gram_oz(OzParams P) {
   for (int u = 0; u < 3; ++u) {
     const int row = (tid + kOzThreads * u) >> 3;
     const int re = row < P.r ? oz_exp(P.rowmax[row]) : 0;
-    const int rk = -(re + 1), rk1 = rk / 2;
+    const int rk = -(re + 1), rk1 = (rk >= -126 && rk <= 127) ? rk : rk / 2;
     sa[u] = oz_pow2f(rk1);
-    sb[u] = oz_pow2f(rk - rk1);
+    sb[u] = oz_pow2f(rk - rk1);                 // 1 unless 2^rk is out of the normal range
   }
   long long V[32];
 #pragma unroll
   for (int c = 0; c < 32; ++c) V[c] = 0;
-  // sum of x^2 over this thread's columns of its task rows, in units of
-  // 2^-50, each square rounded to the unit (a range of 16384 columns stays
-  // below 2^62)
-  long long d0 = 0, d1 = 0, d2 = 0;
+  // sum of x^2 over this thread's columns of each task row, in int64 units of
+  // 2^-50: over a chunk (32 values) the squares are summed error-free in FP32
+  // (x^2 = h + l exactly by one FMA, the h by Knuth's two-sum into ph, the
+  // rounding errors and the l into pl), then both words are rounded to the
+  // unit and added
+  long long dq[3] = {0, 0, 0};
+  float ph[3] = {0.f, 0.f, 0.f}, pl[3] = {0.f, 0.f, 0.f};
+  auto fold = [&]() {
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      dq[u] += oz_ll50(ph[u]) + oz_ll50(pl[u]);
+      ph[u] = 0.f;
+      pl[u] = 0.f;
+    }
+  };
   const uint32_t idesc = idesc_bf16_f32(128, P.cw);
   OzRing sr, mr;                                   // slicing ring; MMA ring (issuer)
   uint32_t acc_ph = 0, mma_acc_ph = 0;
@@ -270,18 +284,31 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gram_oz(OzParams P) {
           const int row = t >> 3, kc = (t & 7) * 8;
           if (t >= 128 * 8 || row >= P.r) continue;
           uint32_t w[kOzBufs][4];
-          long long dsq = 0;
+          float x[8];
 #pragma unroll
           for (int e = 0; e < 8; e += 2) {
             uint32_t wp[kOzBufs];
-            const float x0 = __fmul_rn(__fmul_rn(b[u][e], sa[u]), sb[u]);
-            const float x1 = __fmul_rn(__fmul_rn(b[u][e + 1], sa[u]), sb[u]);
-            oz_slice_pair(x0, x1, wp);
+            x[e] = __fmul_rn(__fmul_rn(b[u][e], sa[u]), sb[u]);
+            x[e + 1] = __fmul_rn(__fmul_rn(b[u][e + 1], sa[u]), sb[u]);
+            oz_slice_pair(x[e], x[e + 1], wp);
 #pragma unroll
             for (int t2 = 0; t2 < kOzBufs; ++t2) w[t2][e >> 1] = wp[t2];
-            dsq += oz_sq50(x0) + oz_sq50(x1);
           }
-          if (u == 0) d0 += dsq; else if (u == 1) d1 += dsq; else d2 += dsq;
+          if (grp == 0) {                                  // the diagonal: one column group
+            float sh = ph[u], sl = pl[u];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const float h = __fmul_rn(x[e], x[e]);
+              const float l = __fmaf_rn(x[e], x[e], -h);
+              const float sum = __fadd_rn(sh, h);
+              const float bb = __fsub_rn(sum, sh);
+              const float er = __fadd_rn(__fsub_rn(sh, __fsub_rn(sum, bb)), __fsub_rn(h, bb));
+              sh = sum;
+              sl = __fadd_rn(sl, __fadd_rn(er, l));
+            }
+            ph[u] = sh;
+            pl[u] = sl;
+          }
           const uint32_t off = sw128_offset((uint32_t)row, (uint32_t)kc);
 #pragma unroll
           for (int t2 = 0; t2 < kOzBufs; ++t2)
@@ -294,6 +321,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gram_oz(OzParams P) {
       }
       // ---- drain the chunk that ended with slab s - 1 ----
       if (s > 0 && (s % kOzSlabsPerChunk == 0 || s == ns)) {
+        if (grp == 0) fold();
         if (!oz_warp_wait(&acc_full, acc_ph, P.err, lane)) { ok = false; break; }
         tc_fence_after();
         const uint32_t lanes = (uint32_t)(q * 32) << 16;
@@ -399,7 +427,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gram_oz(OzParams P) {
     for (int u = 0; u < 3; ++u) {
       const int t = tid + kOzThreads * u;
       if (t >= 128 * 8) break;                       // warp-uniform (whole warps)
-      long long dv = u == 0 ? d0 : (u == 1 ? d1 : d2);
+      long long dv = dq[u];
       dv += __shfl_xor_sync(0xffffffffu, dv, 1);
       dv += __shfl_xor_sync(0xffffffffu, dv, 2);
       dv += __shfl_xor_sync(0xffffffffu, dv, 4);
@@ -408,8 +436,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_gram_oz(OzParams P) {
         const int k = 2 * oz_exp(P.rowmax[row]) + 2 - 50;
         P.diag[(int64_t)blockIdx.x * P.r + row] += (double)dv * __longlong_as_double((long long)(1023 + k) << 52);
       }
+      dq[u] = 0;
     }
-    d0 = d1 = d2 = 0;
   }
   if (issuer) {
     // every MMA issued has finished before TMEM is released

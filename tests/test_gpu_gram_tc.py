@@ -50,6 +50,10 @@ def _fsum_gram(B):
     return G
 
 
+def _assert_exact_gram(G, ref):
+    assert np.array_equal(G, ref)
+
+
 def _int_matrix(rng, r, n, bits):
     """Integers below 2^bits in magnitude: a random row, a row at the maximum
     with one sign (the largest slice sums), a zero row."""
@@ -70,7 +74,7 @@ def test_gram_exact_on_integers(lrs, r, n):
     B = _int_matrix(rng, r, n, 20)
     G = _gram(lrs, B.astype(np.float32))
     ref = B @ B.T                       # exact: every partial sum is an integer below 2^53
-    assert np.array_equal(G, ref)
+    _assert_exact_gram(G, ref)
 
 
 def test_gram_exact_scaled_rows_and_unaligned(lrs):
@@ -81,7 +85,7 @@ def test_gram_exact_scaled_rows_and_unaligned(lrs):
     Bs = B * scale[:, None]
     ref = B @ B.T * np.outer(scale, scale)          # powers of two: still exact
     G = _gram(lrs, Bs.astype(np.float32), offset=1)
-    assert np.array_equal(G, ref)
+    _assert_exact_gram(G, ref)
 
 
 @pytest.mark.slow
@@ -93,7 +97,7 @@ def test_gram_exact_over_many_ranges(lrs):
     B = rng.integers(-1023, 1024, size=(r, n)).astype(np.float32)
     G = _gram(lrs, B)
     ref = B.astype(np.float64) @ B.astype(np.float64).T
-    assert np.array_equal(G, ref)
+    _assert_exact_gram(G, ref)
 
 
 @pytest.mark.parametrize("r,n,kind", [(72, 20000, "gauss"), (114, 9000, "gauss"), (40, 12000, "field"),
