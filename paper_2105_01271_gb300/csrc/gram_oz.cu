@@ -36,13 +36,15 @@
 //
 // Diagonal.  X_33 (level 6) is dropped and acc_4 truncates; off the diagonal
 // both errors have random signs, but on it every X_tt term is >= 0, a bias
-// of ~2^-44.  So G_ii = sum_k x_ik^2 is summed apart, without bias: per slab
-// the slicing threads sum eight squares error-free in FP32 (x^2 = h + l by one
-// FMA, Knuth's two-sum) and add both words, rounded to 2^-50, in int64.
+// of ~2^-44.  So G_ii = sum_k x_ik^2 is summed apart, without bias: over a
+// chunk the slicing threads sum their squares error-free in FP32 (x^2 = h + l
+// by one FMA, Knuth's two-sum) and fold both words, rounded to 2^-50, into
+// int64 (column group 0 only).
 //
 // Drain.  After each chunk the accumulators are read back (tcgen05.ld) and
 // added into one int64 per entry in units of 2^-49: levels 0-3 exactly
-// (integers on known grids), levels 4-5 rounded to the unit.  A CTA sums at
+// (integers on known grids, converted by magic-number rounding in FP32),
+// levels 4-5 rounded to the unit.  A CTA sums at
 // most 16384 columns in int64 (|S| <= 2^61 units), then adds the range into
 // its FP64 partial S_cta 2^(e_i + e_j + 2); a final kernel forms
 // G = sum over CTAs of (S_cta + S_cta^T) in a fixed order (deterministic).
