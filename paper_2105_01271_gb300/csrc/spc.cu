@@ -39,16 +39,24 @@ __global__ void k_small_gemm(int64_t M, int64_t N, int64_t K, const double* __re
   const int64_t i0 = (int64_t)blockIdx.y * 16, j0 = (int64_t)blockIdx.x * 16;
   const int64_t bj = j0 + tx;
   const int64_t bcol = bj < N ? (cols ? (int64_t)cols[bj] : bj) : 0;
-  double acc = 0.0;
+  // four interleaved partial sums (one FP64 FMA chain would wait ~64 cycles
+  // per term), combined in a fixed order
+  double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
   for (int64_t t0 = 0; t0 < K; t0 += 16) {
     const int64_t ai = i0 + ty, at = t0 + tx, bt = t0 + ty;
     As[ty][tx] = (ai < M && at < K) ? A[ai * a_si + at * a_st] : 0.0;
     Bs[ty][tx] = (bt < K && bj < N) ? B[bt * b_st + bcol * b_sj] : 0.0;
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < 16; ++u) acc = fma(As[ty][u], Bs[u][tx], acc);
+    for (int u = 0; u < 16; u += 4) {
+      acc0 = fma(As[ty][u], Bs[u][tx], acc0);
+      acc1 = fma(As[ty][u + 1], Bs[u + 1][tx], acc1);
+      acc2 = fma(As[ty][u + 2], Bs[u + 2][tx], acc2);
+      acc3 = fma(As[ty][u + 3], Bs[u + 3][tx], acc3);
+    }
     __syncthreads();
   }
+  const double acc = (acc0 + acc1) + (acc2 + acc3);
   const int64_t i = i0 + ty;
   if (i < M && bj < N) C[i * ldc + bj] = div ? acc / div[i] : acc;
 }
