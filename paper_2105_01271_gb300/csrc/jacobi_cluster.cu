@@ -285,26 +285,37 @@ __global__ void __launch_bounds__(256, 1) k_jacobi_rows_cl(JacRowsArgs a) {
 }
 
 // s_k = column norms of W (descending, ties by index) and U_B[perm[i]][k] =
-// W[order[k]][i] / s_k (zero column when s_k = 0)
+// W[order[k]][i] / s_k (zero column when s_k = 0).  The norms are ranked by
+// their bit patterns as 64-bit integers (the order of non-negative doubles;
+// a total order on any bits, so the ranks are always a permutation) on the
+// integer pipe, and each column is scaled by one reciprocal: FP64 compares
+// and divides issue over ~64 cycles per warp instruction on this part.
 __global__ void __launch_bounds__(1024) k_jacobi_rows_finish(const double* __restrict__ W, int r, int rs,
                                                              const int32_t* __restrict__ perm,
                                                              double* __restrict__ Ub, double* __restrict__ s_out) {
   __shared__ double s_norm[1024];
+  __shared__ long long s_key[1024];
+  __shared__ double s_inv[1024];
   __shared__ int order[1024];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int c = wid; c < r; c += nw) {
     double t = 0.0;
     for (int i = lane; i < r; i += 32) t = fma(W[(int64_t)c * rs + i], W[(int64_t)c * rs + i], t);
     t = warp_sum(t);
-    if (lane == 0) s_norm[c] = sqrt(t);
+    if (lane == 0) {
+      const double sv = sqrt(t);
+      s_norm[c] = sv;
+      s_key[c] = __double_as_longlong(sv);
+      s_inv[c] = sv > 0.0 ? 1.0 / sv : 0.0;
+    }
   }
   __syncthreads();
   for (int c = threadIdx.x; c < r; c += blockDim.x) {
     int rank = 0;
-    const double v = s_norm[c];
+    const long long v = s_key[c];
     for (int d = 0; d < r; ++d) {
-      const double u = s_norm[d];
-      if (u > v || (u == v && d < c)) ++rank;
+      const long long u = s_key[d];
+      rank += (u > v || (u == v && d < c)) ? 1 : 0;
     }
     order[rank] = c;
   }
@@ -312,9 +323,10 @@ __global__ void __launch_bounds__(1024) k_jacobi_rows_finish(const double* __res
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     const int i = e / r, k = e - i * r;               // position i, singular index k
     const int c = order[k];
-    const double sv = s_norm[c];
     const int row = perm ? perm[i] : i;
-    Ub[(int64_t)row * r + k] = sv > 0.0 ? W[(int64_t)c * rs + i] / sv : 0.0;
+    const double w = W[(int64_t)c * rs + i], sv = s_norm[c];
+    // the reciprocal is finite down to 2^-1000 (far below any kept norm)
+    Ub[(int64_t)row * r + k] = sv >= 0x1p-1000 ? w * s_inv[c] : (sv > 0.0 ? w / sv : 0.0);
   }
   for (int k = threadIdx.x; k < r; k += blockDim.x) s_out[k] = s_norm[order[k]];
 }

@@ -67,20 +67,29 @@ lrs_status launch_to_f32(lrs_ctx* ctx, const double* src, int64_t rows, int64_t 
 }
 
 // One block per column: find the largest-|entry| of U[:, c] (lowest row on
-// ties); if negative flip U[:, c] and V[:, c].
+// ties); if negative flip U[:, c] and V[:, c].  |entry| is compared through
+// its bit pattern as a 64-bit integer (the order of non-negative doubles; NaN
+// entries rank below every number, as a floating-point compare would leave
+// them), on the integer pipe: an FP64 compare issues over ~64 cycles per warp
+// instruction on this part.
+__device__ __forceinline__ long long abs_key(double x) {
+  const long long k = __double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL;
+  return k > 0x7FF0000000000000LL ? -2LL : k;
+}
+
 __global__ void __launch_bounds__(256) k_sign_fix(double* __restrict__ U, int64_t m, int64_t ldu,
                                                   double* __restrict__ sign_out) {
-  __shared__ double sv[32];
+  __shared__ long long sv[32];
   __shared__ int64_t si[32];
   __shared__ double s_sign;
   const int64_t c = blockIdx.x;
-  double best = -1.0; int64_t bi = INT64_MAX;
+  long long best = -1; int64_t bi = INT64_MAX;
   for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
-    const double a = fabs(U[i * ldu + c]);
+    const long long a = abs_key(U[i * ldu + c]);
     if (a > best || (a == best && i < bi)) { best = a; bi = i; }
   }
   for (int o = 16; o > 0; o >>= 1) {
-    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
     const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
     if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
   }
@@ -88,7 +97,7 @@ __global__ void __launch_bounds__(256) k_sign_fix(double* __restrict__ U, int64_
   if (lane == 0) { sv[wid] = best; si[wid] = bi; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double b = -1.0; int64_t bj = INT64_MAX;
+    long long b = -1; int64_t bj = INT64_MAX;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
       if (sv[w] > b || (sv[w] == b && si[w] < bj)) { b = sv[w]; bj = si[w]; }
     s_sign = (bj < m && U[bj * ldu + c] < 0.0) ? -1.0 : 1.0;

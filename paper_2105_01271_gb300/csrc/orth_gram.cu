@@ -299,20 +299,36 @@ __global__ void __launch_bounds__(256) k_trsm_rows(const double* __restrict__ M,
   }
 }
 
+// the partial-Gram kernel with KPER the smallest listed count >= per: every
+// unrolled slot is an issued FP64 FMA, so slots past the last entry are pure
+// waste on the narrow FP64 pipe (per = 11 at c = 72, 13 at c = 79; the
+// counts whose unrolled form spills are left out)
+template <int K, int... Ks>
+void gram_partial_dispatch(int per, unsigned nb, size_t dyn, cudaStream_t s, const double* M, int64_t p, int c,
+                           int64_t ldm, int64_t rows_b, double* part) {
+  if constexpr (sizeof...(Ks) == 0) {
+    k_gram_partial<K><<<nb, 256, dyn, s>>>(M, p, c, ldm, rows_b, part);
+  } else {
+    if (per <= K) k_gram_partial<K><<<nb, 256, dyn, s>>>(M, p, c, ldm, rows_b, part);
+    else gram_partial_dispatch<Ks...>(per, nb, dyn, s, M, p, c, ldm, rows_b, part);
+  }
+}
+
 lrs_status gram(lrs_ctx* ctx, const double* M, int64_t p, int c, int64_t ldm, double* G) {
+  if (c < 1 || c > kMaxC) return lrs_fail(ctx, LRS_EINVAL, "gram: %d columns (1..%d)", c, kMaxC);
+  // one block per SM with an equal share of the rows (at least 8): a few
+  // thousand rows still spread over every SM's FP64 units
   int64_t nb = ctx->num_sms;
   int64_t rows_b = (p + nb - 1) / nb;
-  if (rows_b < kGramRows) rows_b = kGramRows;
+  if (rows_b < 8) rows_b = 8;
   nb = (p + rows_b - 1) / rows_b;
   const int ntri = c * (c + 1) / 2;
   double* part = (double*)ws_alloc(ctx, sizeof(double) * (size_t)(nb * ntri));
   if (!part) return lrs_fail(ctx, LRS_ENOMEM, "workspace exhausted (gram)");
   const size_t dyn = sizeof(double) * (size_t)(kGramRows * c);
   const int per = (ntri + 255) / 256;
-  if (per <= 8) k_gram_partial<8><<<(unsigned)nb, 256, dyn, ctx->stream>>>(M, p, c, ldm, rows_b, part);
-  else if (per <= 16) k_gram_partial<16><<<(unsigned)nb, 256, dyn, ctx->stream>>>(M, p, c, ldm, rows_b, part);
-  else if (per <= 24) k_gram_partial<24><<<(unsigned)nb, 256, dyn, ctx->stream>>>(M, p, c, ldm, rows_b, part);
-  else k_gram_partial<33><<<(unsigned)nb, 256, dyn, ctx->stream>>>(M, p, c, ldm, rows_b, part);
+  gram_partial_dispatch<2, 6, 8, 10, 11, 13, 14, 16, 20, 24, 28, 33>(per, (unsigned)nb, dyn, ctx->stream, M,
+                                                                          p, c, ldm, rows_b, part);
   ctx->launches++;
   k_gram_reduce<<<(ntri + 7) / 8, 256, 0, ctx->stream>>>(part, (int)nb, c, G);
   ctx->launches++;
