@@ -164,7 +164,11 @@ lrs_status lrs_power_pass2(lrs_ctx* ctx, const void* A, int32_t dtype, int64_t m
  * lrs_range_find -- orthonormal basis of the numerical range of G (the
  * "QR(A_c)" of Algs. 2/3 and "QR(G_q)" of Alg. 7), by Householder QR with
  * column pivoting in FP64, stopped before the first step whose largest
- * remaining column norm is <= rtol * |R_00|.
+ * remaining column norm is <= rtol * |R_00|.  For rtol >= 1e-6 the same
+ * pivots and stop (in exact arithmetic) come from a pivoted Cholesky of the
+ * FP64 Gram G^T G (one pivot column at a time for wide G), followed by the
+ * triangular solve and one Cholesky-QR2 pass; Q then differs from the
+ * Householder Q by column signs and rounding only.
  *   G   m x l FP64 (row stride ldg), not modified.
  *   Q   m x r FP64 (row stride ldq >= min(m,l)); caller allocates min(m,l)
  *       columns.  *r_out = r.
