@@ -1,5 +1,6 @@
 // Batching form: many independent decompositions through the single-matrix
-// C ABI, overlapped on several CUDA streams (declared in include/lrs.h).
+// C ABI, overlapped on several CUDA streams (declared in include/lrs.h), and
+// the same batch captured as one CUDA graph (lrs_batch_graph_*, below).
 //
 // Each worker thread owns one lrs_ctx on its own non-blocking stream and its
 // own sketch / C-PWR / basis buffers, kept in a per-device pool across runs
