@@ -244,9 +244,9 @@ lrs_status launch_r_of_bt_gram(lrs_ctx* ctx, const float* B, int64_t r, int64_t 
 // R factor (r x r, row-major) of B^T where B is r x n row-major in FP32 or FP64.
 lrs_status launch_tsqr(lrs_ctx* ctx, const void* B, int b_f64, int64_t r, int64_t n,
                        int64_t ldb, double* R);
-// one-sided Jacobi on the columns of R (r x r): R V = U_R diag(s); returns
+// FP64 one-sided Jacobi on the columns of R (r x r): R V = U_R diag(s); returns
 // V (r x r, row-major) and s (r), sorted descending.
-lrs_status launch_jacobi(lrs_ctx* ctx, double* R, int64_t r, double* V, double* s, int fp64);
+lrs_status launch_jacobi(lrs_ctx* ctx, double* R, int64_t r, double* V, double* s);
 // workspace of the multi-SM FP64 Jacobi on r columns of length len (launch_jacobi
 // falls back to one block without it)
 size_t jacobi_ws(int64_t r, int64_t len);

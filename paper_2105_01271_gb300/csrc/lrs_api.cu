@@ -985,7 +985,7 @@ lrs_status svd_from_b(lrs_ctx* ctx, const void* B, int64_t r, int64_t n, const d
       if (st == LRS_ERANK) st = launch_tsqr(ctx, B, f64, r, n, n, Rm);
       if (st) return st;
     }
-    st = launch_jacobi(ctx, Rm, r, Vr, sv, 1);
+    st = launch_jacobi(ctx, Rm, r, Vr, sv);
   }
   if (st) return st;
   (void)QT;
@@ -1185,7 +1185,7 @@ lrs_status lrs_svd_from_factor(lrs_ctx* ctx, const double* F, int64_t ldf, int64
       // no cluster fits: the unpivoted factor and the Jacobi on its columns
       st = launch_pchol(ctx, G, (int)r, (int)r, 0.0, 0, piv, Rm, r, rank);
       if (st) return st;
-      st = launch_jacobi(ctx, Rm, r, Vr, sv, 1);
+      st = launch_jacobi(ctx, Rm, r, Vr, sv);
       if (st) return st;
     }
   } else {
@@ -1206,7 +1206,7 @@ lrs_status lrs_svd_from_factor(lrs_ctx* ctx, const double* F, int64_t ldf, int64
     }
     if (st == LRS_ERANK) st = launch_tsqr(ctx, Fc, 1, r, nf, nf, Rm);
     if (st) return st;
-    st = launch_jacobi(ctx, Rm, r, Vr, sv, 1);
+    st = launch_jacobi(ctx, Rm, r, Vr, sv);
     if (st) return st;
   }
   st = lrs::svd_finish(ctx, Vr, sv, r, kk, Q, ldq, m, B, n, prec, U, ldu, S, V, ldv, fro2, err_est);

@@ -1,16 +1,20 @@
-// SVD of B (r x n, r small) for TPC-SVD (paper Alg. 2, "SVD(B)") without
-// squaring its condition number:
+// Pieces of the SVD of B (r x n, r small) for TPC-SVD (paper Alg. 2,
+// "SVD(B)") without squaring its condition number:
 //   1. R = the R factor of B^T by Householder TSQR: each block factors a
 //      chunk of C columns of B (a C x r slab of B^T) in shared memory and
 //      writes its r x r triangle; the triangles of all chunks, laid side by
 //      side, form a new r x (chunks * r) matrix that the same kernel reduces
-//      again, until one chunk remains.
-//   2. One-sided (Hestenes) Jacobi on the columns of R: R V = U_R diag(s).
-//      Since B = R^T Q_T^T = V diag(s) (Q_T U_R)^T, the left singular vectors
-//      of B are V and its singular values s.
-// Both run in the working precision T (float for FP32-level paths, double for
-// FP64 data).  Shared memory bounds r: r*C*sizeof(T) <= ~200 KB for TSQR and
-// 2*r*r*sizeof(T) <= ~200 KB for Jacobi.
+//      again, until one chunk remains.  In the working precision T of B (the
+//      R form of lrs_slab_factor, and the fallback when the Gram's Cholesky
+//      of an FP32 B breaks down).
+//   2. FP64 one-sided (Hestenes) Jacobi on the columns of R: R V = U_R
+//      diag(s).  Since B = R^T Q_T^T = V diag(s) (Q_T U_R)^T, the left
+//      singular vectors of B are V and its singular values s.  One block, or
+//      one warp per pair across the SMs (cooperative) from r = 24 on.
+// Shared memory bounds r: r*C*sizeof(T) <= ~200 KB for TSQR and
+// 2*r*r*8 <= ~200 KB for the one-block Jacobi.  The usual FP32-data route
+// (exact-slice Gram, pivoted Cholesky, the cluster Jacobi on the rows of R)
+// is in gram_oz.cu, orth_gram.cu and jacobi_cluster.cu.
 #include "common.cuh"
 #include "internal.h"
 
@@ -240,112 +244,6 @@ k_jacobi(const double* __restrict__ R, int64_t r, double* __restrict__ Vout, dou
 }
 
 // ---------------------------------------------------------------------------
-// The FP32 one-sided Jacobi on packed pairs: columns are stored with an even
-// stride rs (a zero pad element when r is odd), each lane of a pair's team
-// owns adjacent element pairs (2 j, 2 j + 1), and the dot products and
-// rotations run as .f32x2 instructions (half the issue slots of the scalar
-// loop; the kernel is issue-bound on one SM).  Same pairing, tests and
-// rotation formulas as k_jacobi.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024, 1)
-k_jacobi_f2(const double* __restrict__ R, int64_t r, double* __restrict__ Vout, double* __restrict__ s_out,
-            int max_sweeps) {
-  extern __shared__ unsigned char smem_raw[];
-  const int ri = (int)r, rpi = (ri + 1) & ~1, rs = rpi;      // rp columns of even length rs
-  float* Wc = reinterpret_cast<float*>(smem_raw);
-  float* Vc = Wc + rpi * rs;
-  int* order = reinterpret_cast<int*>(Vc + rpi * rs);
-  __shared__ int s_rot;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int e = threadIdx.x; e < rpi * rs; e += blockDim.x) {
-    const int c = e / rs, i = e - c * rs;
-    Wc[e] = (c < ri && i < ri) ? (float)R[(int64_t)i * ri + c] : 0.f;
-    Vc[e] = (c == i && c < ri) ? 1.f : 0.f;
-  }
-  for (int c = threadIdx.x; c < rpi; c += blockDim.x) order[c] = c;
-  __syncthreads();
-  const float tol = 5.9604645e-08f * (float)(ri > 16 ? ri : 16);
-  const int lg = threadIdx.x % kJacLanes, grp = threadIdx.x / kJacLanes, ngrp = blockDim.x / kJacLanes;
-  const unsigned gmask = ((1u << kJacLanes) - 1u) << (lane & (32 - kJacLanes));
-  const int npair = rs / 2;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) s_rot = 0;
-    __syncthreads();
-    for (int round = 0; round < rpi - 1; ++round) {
-      for (int pr = grp; pr < rpi / 2; pr += ngrp) {
-        const int sa = pr, sb = rpi - 1 - pr;
-        auto slot = [&](int sidx) -> int {
-          if (sidx == 0) return 0;
-          int v = sidx - 1 + round;
-          if (v >= rpi - 1) v -= rpi - 1;
-          return 1 + v;
-        };
-        int p = slot(sa), q = slot(sb);
-        if (p > q) { const int tmp = p; p = q; q = tmp; }
-        if (q >= ri) continue;
-        uint64_t* wp = reinterpret_cast<uint64_t*>(Wc + p * rs);
-        uint64_t* wq = reinterpret_cast<uint64_t*>(Wc + q * rs);
-        uint64_t a2 = 0ull, b2 = 0ull, g2 = 0ull;
-        for (int j = lg; j < npair; j += kJacLanes) {
-          const uint64_t x = wp[j], y = wq[j];
-          a2 = f2_fma(x, x, a2); b2 = f2_fma(y, y, b2); g2 = f2_fma(x, y, g2);
-        }
-        float a0, a1, b0, b1, g0, g1;
-        f2_unpack(a2, a0, a1); f2_unpack(b2, b0, b1); f2_unpack(g2, g0, g1);
-        float a = a0 + a1, b = b0 + b1, g = g0 + g1;
-#pragma unroll
-        for (int o = kJacLanes / 2; o > 0; o >>= 1) {
-          a += __shfl_xor_sync(gmask, a, o); b += __shfl_xor_sync(gmask, b, o); g += __shfl_xor_sync(gmask, g, o);
-        }
-        if (fabsf(g) <= tol * (sqrtf(a) * sqrtf(b)) || g == 0.f) continue;
-        const float zeta = (b - a) / (2.f * g);
-        const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-        const float cs = 1.f / sqrtf(1.f + t * t);
-        const float sn = cs * t;
-        const uint64_t c2 = f2_pack(cs, cs), s2 = f2_pack(sn, sn), ns2 = f2_pack(-sn, -sn);
-        uint64_t* vp = reinterpret_cast<uint64_t*>(Vc + p * rs);
-        uint64_t* vq = reinterpret_cast<uint64_t*>(Vc + q * rs);
-        for (int j = lg; j < npair; j += kJacLanes) {
-          const uint64_t x = wp[j], y = wq[j];
-          wp[j] = f2_fma(ns2, y, f2_mul(c2, x));        // cs x - sn y
-          wq[j] = f2_fma(s2, x, f2_mul(c2, y));         // sn x + cs y
-          const uint64_t u = vp[j], w = vq[j];
-          vp[j] = f2_fma(ns2, w, f2_mul(c2, u));
-          vq[j] = f2_fma(s2, u, f2_mul(c2, w));
-        }
-        if (lg == 0) atomicAdd(&s_rot, 1);
-      }
-      __syncthreads();
-    }
-    if (s_rot == 0) break;
-    __syncthreads();
-  }
-  __shared__ double s_norm[1024];
-  for (int c = wid; c < ri; c += nw) {
-    float a = 0.f;
-    for (int i = lane; i < ri; i += 32) a = fmaf(Wc[c * rs + i], Wc[c * rs + i], a);
-    a = warp_sum(a);
-    if (lane == 0) s_norm[c] = sqrt((double)a);
-  }
-  __syncthreads();
-  for (int c = threadIdx.x; c < ri; c += blockDim.x) {
-    int rank = 0;
-    const double v = s_norm[c];
-    for (int d = 0; d < ri; ++d) {
-      const double u = s_norm[d];
-      if (u > v || (u == v && d < c)) ++rank;
-    }
-    order[rank] = c;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < ri * ri; e += blockDim.x) {
-    const int i = e / ri, k = e - i * ri;               // V[i][k] = Vc[order[k]][i]
-    Vout[(int64_t)i * ri + k] = (double)Vc[order[k] * rs + i];
-  }
-  for (int k = threadIdx.x; k < ri; k += blockDim.x) s_out[k] = s_norm[order[k]];
-}
-
-// ---------------------------------------------------------------------------
 // FP64 one-sided Jacobi across the GPU: the pairs of one round-robin round
 // are spread over up to one block (one warp) per SM, with a grid barrier
 // between rounds.  On GB300 the FP64 pipe of one SM retires one warp-wide
@@ -504,28 +402,18 @@ static bool jacobi_coop(lrs_ctx* ctx, const double* R, int64_t r, int64_t len, i
 }
 
 
-lrs_status launch_jacobi(lrs_ctx* ctx, double* R, int64_t r, double* V, double* s, int fp64) {
+lrs_status launch_jacobi(lrs_ctx* ctx, double* R, int64_t r, double* V, double* s) {
   const int64_t rp = (r + 1) & ~int64_t(1);
-  if (fp64 && ctx->coop_ok && r >= 24 && r <= 1024) {
+  if (ctx->coop_ok && r >= 24 && r <= 1024) {
     lrs_status st = LRS_OK;
     if (jacobi_coop(ctx, R, r, r, r, 0, V, s, &st)) return st;
     // no room in the workspace: the one-block kernel below
   }
-  const size_t tsz = fp64 ? 8 : 4;
-  const size_t dyn = tsz * 2 * (size_t)(rp * r) + sizeof(int) * (size_t)rp + 64;
+  const size_t dyn = sizeof(double) * 2 * (size_t)(rp * r) + sizeof(int) * (size_t)rp + 64;
   if (dyn > kSmemCap || r > 1024)
     return lrs_fail(ctx, LRS_EINVAL, "svd: rank r=%lld too large for the Jacobi tile", (long long)r);
-  if (fp64) {
-    { const lrs_status _s = raise_dyn_smem(ctx, (const void*)k_jacobi<double>, (size_t)(dyn)); if (_s) return _s; }
-    k_jacobi<double><<<1, 1024, dyn, ctx->stream>>>(R, r, V, s, 40);
-  } else {
-    // packed pairs: columns of even length, 8-byte aligned
-    const size_t dyn2 = 4 * 2 * (size_t)(rp * rp) + sizeof(int) * (size_t)rp + 64;
-    if (dyn2 > kSmemCap)
-      return lrs_fail(ctx, LRS_EINVAL, "svd: rank r=%lld too large for the Jacobi tile", (long long)r);
-    { const lrs_status _s = raise_dyn_smem(ctx, (const void*)k_jacobi_f2, (size_t)(dyn2)); if (_s) return _s; }
-    k_jacobi_f2<<<1, 1024, dyn2, ctx->stream>>>(R, r, V, s, 40);
-  }
+  { const lrs_status _s = raise_dyn_smem(ctx, (const void*)k_jacobi<double>, (size_t)(dyn)); if (_s) return _s; }
+  k_jacobi<double><<<1, 1024, dyn, ctx->stream>>>(R, r, V, s, 40);
   ctx->launches++;
   LRS_CUDA_TRY(ctx, cudaGetLastError());
   return LRS_OK;
