@@ -139,21 +139,6 @@ __device__ __forceinline__ bool pivot_better(double a, int pa, double b, int pb)
   return (ka > kb) || (ka == kb && pa < pb);
 }
 
-// 1/sqrt(x) for x > 0 by Newton-Raphson on f(y) = y^-2 - x, i.e.
-// y <- y (3 - x y^2) / 2, from an FP32 seed (~23 correct bits; each step
-// doubles them, two steps reach FP64 precision within an ulp or two).  Keeps
-// serial pivot steps off the FP64 square-root and divide sequences, long
-// dependent chains on this part's narrow FP64 pipe.  Outside the FP32 range
-// of the seed it falls back to 1 / sqrt(x).
-__device__ __forceinline__ double rsqrt_newton(double x) {
-  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
-  double y = (double)rsqrtf((float)x);
-  const double hx = 0.5 * x;
-#pragma unroll
-  for (int it = 0; it < 2; ++it) y = y * fma(-hx * y, y, 1.5);
-  return y;
-}
-
 // 1/sqrt(x) for x > 0 with the short dependency chain this part's FP64 pipe
 // wants (each dependent FP64 instruction waits ~64 cycles): the FP32 seed
 // comes from the integer-pipe split and widening (no conversion
@@ -183,39 +168,6 @@ __device__ __forceinline__ void cand_store(PivotCand* p, double v, int pos, int 
 __device__ __forceinline__ void cand_load(const PivotCand* p, double& v, int& pos, int& phys) {
   const int4 x = __ldcg(reinterpret_cast<const int4*>(p));
   v = __hiloint2double(x.y, x.x); pos = x.z; phys = x.w;
-}
-
-// Packed FP32 pairs (sm_100+ .f32x2 instructions): each lane of the pair is
-// rounded to nearest exactly like the scalar _rn operation, so the packed
-// error-free transformations below give bit-for-bit the scalar results with
-// half the instructions.  Low half = first operand of the pack.
-__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void f2_unpack(uint64_t v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
-  uint64_t r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
-  uint64_t r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
-  uint64_t r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
 }
 
 // ---------------------------------------------------------------------------
