@@ -42,8 +42,11 @@ namespace {
 constexpr int kMaxSweeps = 40;
 // A sweep whose largest rotated pair had |x.y| <= kStopRatio ||x|| ||y||
 // ends the iteration: one-sided Jacobi converges quadratically, so the next
-// sweep would start below (kStopRatio)^2 times a modest constant, under the
-// rotation threshold r u64, and would only confirm convergence.
+// sweep would start near (kStopRatio)^2 times a constant that grows as
+// singular values cluster -- under the rotation threshold r u64 for
+// well-separated values (it would only confirm convergence), and ~1e-12 in a
+// host model with ten values equal to 1e-10, whose columns are then
+// orthogonal to that level.
 constexpr float kStopRatio = 3e-9f;
 
 struct JacRowsArgs {
